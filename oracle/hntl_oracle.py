@@ -1,0 +1,418 @@
+"""Plain, slow CPU oracle of the HNTL batched query path (FP64).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg are the only users. The product library neither imports nor
+links anything here, and this module imports nothing from the product package.
+
+What it computes, in the paper's order (HNTL technical report):
+  * grain partitioning (unspecified in the paper; k-means++ seeding with the
+    uniform draws passed in, then Lloyd iterations, sec. 2.2 "spatial grains");
+  * per-grain local PCA basis W_g (sec. 2.2), here U_g = W_g^T, r x d, from an
+    FP64 covariance centred on the stored FP32 centre and numpy's symmetric
+    eigensolver (a library primitive), eigenvalues descending;
+  * database tangent coordinates and residual norms, Eq. 1-4;
+  * the Mode B query path: routing (sec. 2.1 step 1, sec. 2.3), projection
+    (Eq. 1-4), scan with the approximate distance of Eq. 6, the pool of the C
+    best (Table 1, "Pool C"), exact L2 rerank to top k (sec. 2.1 step 4);
+  * the brute-force exact kNN used as ground truth.
+The loops live in hntl_oracle.c; the covariance, the tangent coordinates of
+the database rows and the eigendecomposition are written as numpy matmuls and
+`numpy.linalg.eigh`.
+
+Readings where the paper is silent are listed in the design notes: ties are
+broken by (distance, id) and routing by (distance, grain); the pool is global
+per query across probes; a grain with fewer rows than the basis size keeps an
+orthonormal completion (any eigenvectors of its covariance); each basis row is
+signed so that its largest-magnitude component is positive.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hntl_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# ---------------------------------------------------------------------------
+# C core
+# ---------------------------------------------------------------------------
+
+
+def build_c(force: bool = False) -> str:
+    """Compile the C core with gcc (-O2, OpenMP, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-Wall",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _c():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build_c())
+            P = ctypes.c_void_p
+            I = ctypes.c_int64
+            lib.or_bruteforce.argtypes = [P, I, I, P, I, I, P, P, P, P, P]
+            lib.or_kmeanspp.argtypes = [P, I, I, I, P, P]
+            lib.or_assign.argtypes = [P, I, I, P, I, P, P]
+            lib.or_means.argtypes = [P, I, I, P, I, P, P]
+            lib.or_means.restype = I
+            lib.or_lloyd.argtypes = [P, I, I, I, P, I, P]
+            lib.or_lloyd.restype = I
+            lib.or_search.argtypes = [P, P, I, I, I, P, P, P, P, P, P, P, I, I, I, I, P,
+                                      P, P, P, P, P, P]
+            lib.or_threads.restype = ctypes.c_int
+            lib.or_set_threads.argtypes = [ctypes.c_int]
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a), dtype=np.float32)
+
+
+def threads() -> int:
+    return int(_c().or_threads())
+
+
+def set_threads(n: int) -> None:
+    _c().or_set_threads(int(n))
+
+
+# ---------------------------------------------------------------------------
+# index build
+# ---------------------------------------------------------------------------
+
+
+def kmeans(X, G: int, u, train_idx=None, max_iter: int = 25):
+    """Grain partition of X: k-means++ seeding (draws `u`, one per centre) on
+    the training rows, Lloyd iterations there, one assignment pass of all rows
+    to the trained centres, then each centre is the exact FP64 mean of its
+    final members rounded once to FP32 (an empty final grain keeps its trained
+    centre). Returns (mu f32 [G, d], assign i32 [N], lloyd_iterations)."""
+    X = _f32(X)
+    n, d = X.shape
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    assert u.shape[0] >= G
+    Xt = X if train_idx is None else np.ascontiguousarray(X[np.asarray(train_idx)])
+    nt = Xt.shape[0]
+    if nt < G:
+        raise ValueError("fewer training rows than grains")
+    lib = _c()
+    chosen = np.zeros(G, dtype=np.int64)
+    lib.or_kmeanspp(_p(Xt), nt, d, G, _p(u), _p(chosen))
+    M = Xt[chosen].astype(np.float64)
+    at = np.zeros(nt, dtype=np.int32)
+    iters = lib.or_lloyd(_p(Xt), nt, d, G, _p(M), max_iter, _p(at))
+    assign = np.zeros(n, dtype=np.int32)
+    lib.or_assign(_p(X), n, d, _p(M), G, _p(assign), None)
+    count = np.zeros(G, dtype=np.int64)
+    Mf = M.copy()
+    lib.or_means(_p(X), n, d, _p(assign), G, _p(Mf), _p(count))
+    return Mf.astype(np.float32), assign, int(iters)
+
+
+def grain_pca(X, rows, mu32, r: int):
+    """Local PCA of one grain (sec. 2.2): FP64 covariance (1/n_g) V^T V with
+    V = X[rows] - mu (stored FP32 centre), eigenvalues descending, basis
+    U = top-r eigenvectors as rows, each signed so that its largest-magnitude
+    component is positive. Returns (U f64 [r, d], eigenvalues f64 [d])."""
+    d = mu32.shape[0]
+    if len(rows) > 0:
+        V = X[rows].astype(np.float64) - mu32.astype(np.float64)
+        cov = (V.T @ V) / float(len(rows))
+    else:
+        cov = np.zeros((d, d), dtype=np.float64)
+    w, E = np.linalg.eigh(cov)
+    order = np.argsort(-w, kind="stable")
+    w = w[order]
+    E = E[:, order]
+    U = E[:, :r].T.copy()
+    for j in range(r):
+        m = int(np.argmax(np.abs(U[j])))
+        if U[j, m] < 0:
+            U[j] = -U[j]
+    return U, w
+
+
+def tangent(X, rows, mu32, U):
+    """z = U (x - mu) (Eq. 1-2) and rho = ||(x - mu) - U^T z||^2 (Eq. 3-4), FP64."""
+    V = X[rows].astype(np.float64) - mu32.astype(np.float64)
+    Z = V @ U.T
+    E = V - Z @ U
+    return Z, np.einsum("ij,ij->i", E, E)
+
+
+def build_index(X, G: int, r: int, u, train_idx=None, max_iter: int = 25, keep_fp64: bool = False):
+    """Oracle index build: partition, per-grain PCA, database coordinates.
+
+    Rows are stored in grain order (ascending original id inside a grain).
+    Returned arrays: M f32 [G, d], U f32 [G, r, d], eig f64 [G, d],
+    grain_off i64 [G+1], ids u32 [N], Z f32 [N, r], rho f32 [N], assign i32 [N].
+    z and rho are computed from the stored FP32 basis, so database rows and
+    queries use the same basis. With keep_fp64, also Z64/rho64 computed with
+    the FP64 eigenvectors (for the PCA invariant)."""
+    X = _f32(X)
+    n, d = X.shape
+    if not (1 <= r <= d):
+        raise ValueError("need 1 <= r <= d")
+    mu, assign, iters = kmeans(X, G, u, train_idx, max_iter)
+    order = np.argsort(assign, kind="stable")
+    counts = np.bincount(assign, minlength=G)
+    grain_off = np.zeros(G + 1, dtype=np.int64)
+    grain_off[1:] = np.cumsum(counts)
+    U32 = np.zeros((G, r, d), dtype=np.float32)
+    eig = np.zeros((G, d), dtype=np.float64)
+    Z = np.zeros((n, r), dtype=np.float32)
+    rho = np.zeros(n, dtype=np.float32)
+    out = {}
+    if keep_fp64:
+        out["U64"] = np.zeros((G, r, d))
+        out["Z64"] = np.zeros((n, r))
+        out["rho64"] = np.zeros(n)
+    for g in range(G):
+        rows = order[grain_off[g]:grain_off[g + 1]]
+        U, w = grain_pca(X, rows, mu[g], r)
+        U32[g] = U.astype(np.float32)
+        eig[g] = w
+        if len(rows):
+            z, rh = tangent(X, rows, mu[g], U32[g].astype(np.float64))
+            Z[grain_off[g]:grain_off[g + 1]] = z.astype(np.float32)
+            rho[grain_off[g]:grain_off[g + 1]] = rh.astype(np.float32)
+            if keep_fp64:
+                z64, rh64 = tangent(X, rows, mu[g], U)
+                out["Z64"][grain_off[g]:grain_off[g + 1]] = z64
+                out["rho64"][grain_off[g]:grain_off[g + 1]] = rh64
+        if keep_fp64:
+            out["U64"][g] = U
+    out.update(dict(M=mu, U=U32, eig=eig, grain_off=grain_off, ids=order.astype(np.uint32), Z=Z, rho=rho,
+                    assign=assign, lloyd_iters=iters, N=n, d=d, G=G, r=r))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# search and brute force
+# ---------------------------------------------------------------------------
+
+
+def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=None, rho=None):
+    """Mode B search of every query (see hntl_oracle.c or_search). X is the
+    raw rows in original id order (FP32 values; pass BF16-rounded values for
+    the precision form); Z/rho override the index's coordinates (e.g. FP8
+    codes decoded and scaled)."""
+    X = _f32(X)
+    Q = _f32(Q)
+    nq, d = Q.shape
+    G, r = idx["G"], idx["r"]
+    if not (1 <= nprobe <= G) or k < 1 or C < 1:
+        raise ValueError("bad search parameters")
+    Zs = _f32(idx["Z"] if Z is None else Z)
+    rhos = _f32(idx["rho"] if rho is None else rho)
+    off = np.ascontiguousarray(idx["grain_off"], dtype=np.int64)
+    ids = np.ascontiguousarray(idx["ids"], dtype=np.uint32)
+    M = _f32(idx["M"])
+    U = _f32(idx["U"])
+    attr_a = None if attr is None else np.ascontiguousarray(attr, dtype=np.int64)
+    rng = None if ranges is None else np.ascontiguousarray(ranges, dtype=np.int64)
+    if rng is not None and attr_a is None:
+        raise ValueError("ranges need attr")
+    probe = np.zeros((nq, nprobe), dtype=np.int32)
+    probe_d = np.zeros((nq, nprobe + 1), dtype=np.float64)
+    cand_id = np.zeros((nq, C), dtype=np.uint32)
+    cand_d = np.zeros((nq, C + 1), dtype=np.float64)
+    out_id = np.zeros((nq, k), dtype=np.int64)
+    out_d = np.zeros((nq, k + 1), dtype=np.float64)
+    _c().or_search(_p(M), _p(U), G, d, r, _p(off), _p(ids), _p(Zs), _p(rhos), _p(X), _p(attr_a), _p(Q), nq, k,
+                   C, nprobe, _p(rng), _p(probe), _p(probe_d), _p(cand_id), _p(cand_d), _p(out_id), _p(out_d))
+    return dict(probe=probe, probe_d=probe_d, cand_id=cand_id, cand_d=cand_d, out_id=out_id, out_d=out_d)
+
+
+def brute_force(X, Q, k: int, attr=None, ranges=None):
+    """Exact kNN by (dist, id), FP64. Returns (ids i64 [nq,k], d f64 [nq,k], next f64 [nq])."""
+    X = _f32(X)
+    Q = _f32(Q)
+    nq = Q.shape[0]
+    ids = np.zeros((nq, k), dtype=np.int64)
+    dd = np.zeros((nq, k), dtype=np.float64)
+    nxt = np.zeros(nq, dtype=np.float64)
+    attr_a = None if attr is None else np.ascontiguousarray(attr, dtype=np.int64)
+    rng = None if ranges is None else np.ascontiguousarray(ranges, dtype=np.int64)
+    _c().or_bruteforce(_p(X), X.shape[0], X.shape[1], _p(Q), nq, k, _p(attr_a), _p(rng), _p(ids), _p(dd),
+                       _p(nxt))
+    return ids, dd, nxt
+
+
+# ---------------------------------------------------------------------------
+# number formats (precision form)
+# ---------------------------------------------------------------------------
+
+
+def bf16_round(x):
+    """FP32 -> BF16 (round to nearest, ties to even), returned as the 16-bit codes."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    nan = np.isnan(np.ascontiguousarray(x, dtype=np.float32))
+    lsb = (b >> np.uint64(16)) & np.uint64(1)
+    rounded = (b + np.uint64(0x7FFF) + lsb) >> np.uint64(16)
+    out = rounded.astype(np.uint16)
+    out[nan] = 0x7FC0
+    return out
+
+
+def bf16_to_f32(h):
+    return (np.ascontiguousarray(h, dtype=np.uint16).astype(np.uint32) << np.uint32(16)).view(np.float32)
+
+
+def e4m3_value(code):
+    """Value of OCP FP8 E4M3 codes: sign bit, 4 exponent bits (bias 7), 3
+    mantissa bits; exponent field 0 is subnormal (m/8 * 2^-6); S.1111.111 is
+    NaN; no infinities; largest finite 448."""
+    c = np.asarray(code, dtype=np.uint8).astype(np.int64)
+    s = np.where(c & 0x80, -1.0, 1.0)
+    e = (c >> 3) & 0xF
+    m = c & 0x7
+    val = np.where(e == 0, (m / 8.0) * 2.0 ** -6, (1.0 + m / 8.0) * np.exp2(e - 7.0))
+    val = np.where((e == 0xF) & (m == 0x7), np.nan, val)
+    return s * val
+
+
+def e4m3_encode(x):
+    """Round each value to the nearest E4M3 number (ties to the even code),
+    saturating to +-448 (satfinite). Returns the 8-bit codes. Written as a
+    search over the 127 non-negative finite codes, which is the plain
+    definition of round-to-nearest."""
+    x = np.asarray(x, dtype=np.float64)
+    codes = np.arange(0, 0x7F, dtype=np.uint8)  # 0x00..0x7E, non-negative finite
+    vals = e4m3_value(codes)
+    a = np.minimum(np.abs(x), 448.0)
+    # index of the largest value <= a
+    hi = np.searchsorted(vals, a, side="right") - 1
+    hi = np.clip(hi, 0, len(vals) - 1)
+    lo_v = vals[hi]
+    nxt = np.clip(hi + 1, 0, len(vals) - 1)
+    up_v = vals[nxt]
+    dlo = a - lo_v
+    dup = up_v - a
+    pick_up = (dup < dlo) | ((dup == dlo) & (nxt != hi) & ((hi & 1) == 1))
+    idx = np.where(pick_up, nxt, hi)
+    out = codes[idx]
+    neg = (x < 0) & (out != 0)
+    out = np.where(neg, out | 0x80, out).astype(np.uint8)
+    out = np.where(np.isnan(x), np.uint8(0x7F), out).astype(np.uint8)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# index file (format shared with the library's loader by specification only)
+# ---------------------------------------------------------------------------
+
+MAGIC = b"HNTLIDX\0"
+VERSION = 1
+F_EIG, F_FP8, F_XBF16, F_ATTR = 1, 2, 4, 8
+
+
+def _wsum(buf: bytes, state):
+    """Position-weighted 64-bit word sum: sum of w_i * (2 i + 1) mod 2^64 over
+    little-endian u64 words (zero padded). state = (sum, next_word_index)."""
+    s, pos = state
+    a = np.frombuffer(buf + b"\0" * ((-len(buf)) % 8), dtype="<u8")
+    w = (np.arange(a.size, dtype=np.uint64) + np.uint64(pos)) * np.uint64(2) + np.uint64(1)
+    with np.errstate(over="ignore"):
+        s = np.uint64(s) + np.sum(a * w, dtype=np.uint64)
+    return int(s), pos + a.size
+
+
+def write_index(path, idx, X, attr=None, precision: str = "fp32", include_eig: bool = True):
+    """Write the index file. precision="fp32": FP32 X. precision="bf16-fp8":
+    BF16 X plus FP8-E4M3 coordinates with a per-grain FP32 scale
+    s_g = max|z| / 448 over the grain (1 for an all-zero grain)."""
+    N, d, G, r = idx["N"], idx["d"], idx["G"], idx["r"]
+    flags = (F_EIG if include_eig else 0) | (F_ATTR if attr is not None else 0)
+    sections = [_f32(idx["M"]).tobytes(), _f32(idx["U"]).tobytes()]
+    if include_eig:
+        sections.append(np.ascontiguousarray(idx["eig"], dtype="<f8").tobytes())
+    sections += [np.ascontiguousarray(idx["grain_off"], dtype="<u8").tobytes(),
+                 np.ascontiguousarray(idx["ids"], dtype="<u4").tobytes(),
+                 _f32(idx["Z"]).tobytes(), _f32(idx["rho"]).tobytes()]
+    if precision == "bf16-fp8":
+        flags |= F_FP8 | F_XBF16
+        z8, scale = fp8_coords(idx)
+        sections += [z8.tobytes(), scale.astype("<f4").tobytes(), bf16_round(X).tobytes()]
+    elif precision == "fp32":
+        sections.append(_f32(X).tobytes())
+    else:
+        raise ValueError(precision)
+    if attr is not None:
+        sections.append(np.ascontiguousarray(attr, dtype="<i8").tobytes())
+    head = MAGIC + np.array([VERSION, flags], dtype="<u4").tobytes() + np.array([N], dtype="<u8").tobytes() \
+        + np.array([d, G, r, 0], dtype="<u4").tobytes()
+    state = (0, 0)
+    with open(path, "wb") as f:
+        for blob in [head] + sections:
+            f.write(blob)
+        f.flush()
+    # checksum over the whole file so far, in 8-byte words (chunks are multiples of 8 bytes)
+    with open(path, "rb") as f:
+        while True:
+            data = f.read(1 << 26)
+            if not data:
+                break
+            state = _wsum(data, state)
+    with open(path, "ab") as f:
+        f.write(np.array([state[0]], dtype="<u8").tobytes())
+
+
+def fp8_coords(idx):
+    """Per-grain FP8 coordinates: s_g = max|z_ij| / 448 over grain g (1.0 if
+    that is zero), code = E4M3(z / s_g) rounded to nearest even, saturating."""
+    G = idx["G"]
+    off = idx["grain_off"]
+    Z = np.asarray(idx["Z"], dtype=np.float32)
+    scale = np.ones(G, dtype=np.float32)
+    z8 = np.zeros(Z.shape, dtype=np.uint8)
+    for g in range(G):
+        blk = Z[off[g]:off[g + 1]]
+        if blk.size == 0:
+            continue
+        m = float(np.max(np.abs(blk)))
+        s = np.float32(m / 448.0) if m > 0 else np.float32(1.0)
+        scale[g] = s
+        z8[off[g]:off[g + 1]] = e4m3_encode(blk.astype(np.float64) / np.float64(s))
+    return z8, scale
+
+
+def fp8_decoded(idx):
+    """FP8 coordinates decoded and scaled back, as FP32 (what the FP8 scan sees)."""
+    z8, scale = fp8_coords(idx)
+    off = idx["grain_off"]
+    vals = e4m3_value(z8).astype(np.float64)
+    out = np.zeros(vals.shape, dtype=np.float32)
+    for g in range(idx["G"]):
+        out[off[g]:off[g + 1]] = (vals[off[g]:off[g + 1]] * np.float64(scale[g])).astype(np.float32)
+    return out
+
+
+def read_index_header(path):
+    with open(path, "rb") as f:
+        h = f.read(40)
+    if h[:8] != MAGIC:
+        raise ValueError("bad magic")
+    ver, flags = np.frombuffer(h[8:16], dtype="<u4")
+    N = int(np.frombuffer(h[16:24], dtype="<u8")[0])
+    d, G, r, _ = (int(v) for v in np.frombuffer(h[24:40], dtype="<u4"))
+    return dict(version=int(ver), flags=int(flags), N=N, d=d, G=G, r=r)

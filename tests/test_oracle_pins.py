@@ -1,0 +1,360 @@
+"""Pins of the CPU oracle to things other than itself: values the paper
+prints, hand-computed fixtures, closed forms, invariants and special cases
+that reduce to brute force. CPU only."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import hntl_oracle as O
+from paper_2606_08813_b300 import synth
+
+from conftest import GOLDEN
+
+
+def _load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _clustered(n, d, nc, nq, seed, sizes="equal"):
+    m = synth.make_cluster_model(n, d, nc, sizes=sizes, seed=seed)
+    X, lab = synth.sample_points(m, seed + 1)
+    Q, _ = synth.sample_queries(m, nq, seed + 2)
+    return X.numpy(), Q.numpy(), lab.numpy()
+
+
+# ---------------------------------------------------------------- k-means
+
+
+def test_kmeans_hand_fixture():
+    g = _load("kmeans_line.json")
+    X = np.array(g["points"], dtype=np.float32)
+    lib = O._c()
+    chosen = np.zeros(g["G"], dtype=np.int64)
+    u = np.array(g["u"], dtype=np.float64)
+    lib.or_kmeanspp(O._p(X), X.shape[0], X.shape[1], g["G"], O._p(u), O._p(chosen))
+    assert chosen.tolist() == g["chosen"]
+    mu, assign, iters = O.kmeans(X, g["G"], u)
+    assert assign.tolist() == g["assign"]
+    np.testing.assert_array_equal(mu, np.array(g["means"], dtype=np.float32))
+    assert iters == g["lloyd_iterations"]
+
+
+def _objective(X, M, assign):
+    X64 = X.astype(np.float64)
+    return float(((X64 - M.astype(np.float64)[assign]) ** 2).sum())
+
+
+def test_lloyd_objective_non_increasing_and_fixed_point():
+    X, _, _ = _clustered(600, 12, 6, 1, 5)
+    G = 6
+    u = synth.uniforms(G, 9).numpy()
+    objs = []
+    for it in range(1, 8):
+        mu, assign, iters = O.kmeans(X, G, u, max_iter=it)
+        objs.append(_objective(X, mu, assign))
+    for a, b in zip(objs, objs[1:]):
+        assert b <= a * (1 + 1e-12)
+    # converged run: centres are the means of their members, members are nearest to their centre
+    mu, assign, iters = O.kmeans(X, G, u, max_iter=100)
+    assert iters < 100
+    for g in range(G):
+        mem = X[assign == g].astype(np.float64)
+        if len(mem):
+            np.testing.assert_allclose(mu[g], mem.mean(0).astype(np.float32), rtol=0, atol=1e-6)
+    d2 = ((X[:, None, :].astype(np.float64) - mu[None].astype(np.float64)) ** 2).sum(-1)
+    best = d2.min(1)
+    assert np.all(d2[np.arange(len(X)), assign] <= best + 1e-9 * (1 + best))
+
+
+def test_kmeans_empty_grain_reseeded():
+    # 5 distinct points, G=5 -> every grain must end non-empty (one point each)
+    X = np.array([[0, 0], [0.1, 0], [5, 5], [5.1, 5], [20, 0]], dtype=np.float32)
+    u = np.array([0.0, 0.1, 0.2, 0.3, 0.4])
+    mu, assign, _ = O.kmeans(X, 5, u)
+    assert sorted(np.bincount(assign, minlength=5).tolist()) == [1, 1, 1, 1, 1]
+
+
+# ---------------------------------------------------------------- PCA
+
+
+def test_pca_invariant_orthonormal_and_eigen_equation():
+    X, _, _ = _clustered(3000, 48, 4, 1, 21)
+    G, r = 4, 10
+    idx = O.build_index(X, G, r, synth.uniforms(G, 3).numpy(), keep_fp64=True)
+    off = idx["grain_off"]
+    for g in range(G):
+        sl = slice(off[g], off[g + 1])
+        lam = idx["eig"][g]
+        U = idx["U64"][g]
+        # rows orthonormal
+        np.testing.assert_allclose(U @ U.T, np.eye(r), atol=1e-12)
+        # eigenvalues descending, trace = sum of eigenvalues
+        assert np.all(np.diff(lam) <= 1e-12)
+        rows = idx["ids"][sl].astype(np.int64)
+        V = X[rows].astype(np.float64) - idx["M"][g].astype(np.float64)
+        trace = float((V * V).sum() / len(rows))
+        assert abs(lam.sum() - trace) <= 1e-10 * trace
+        # eigen-equation residual of the kept directions, covariance formed row by row
+        cov = np.zeros((X.shape[1], X.shape[1]))
+        for v in V:
+            cov += np.outer(v, v)
+        cov /= len(rows)
+        for j in range(r):
+            res = cov @ U[j] - lam[j] * U[j]
+            assert np.linalg.norm(res) <= 1e-9 * max(1.0, lam[0])
+        # mean squared residual = sum of discarded eigenvalues (FP64 basis)
+        disc = lam[r:].sum()
+        assert abs(idx["rho64"][sl].mean() - disc) <= 1e-9 * disc
+        # stored FP32 basis: same invariant within FP32 rounding of the basis
+        assert abs(idx["rho"][sl].astype(np.float64).mean() - disc) <= 1e-5 * disc
+        # largest-magnitude component of each basis row is positive
+        for j in range(r):
+            assert U[j, np.argmax(np.abs(U[j]))] > 0
+
+
+def test_captured_variance_matches_generating_closed_form():
+    # one cluster, many samples: sample PCA tends to the generating spectrum
+    d, r = 64, 8
+    m = synth.make_cluster_model(40000, d, 1, seed=31)
+    X, _ = synth.sample_points(m, 32)
+    idx = O.build_index(X.numpy(), 1, r, np.array([0.5]))
+    lam = idx["eig"][0]
+    got = lam[:r].sum() / lam.sum()
+    want = synth.expected_captured_fraction(d, 8, 0.8, 0.05, r)
+    assert abs(got - want) < 0.01
+
+
+@pytest.mark.slow
+def test_isotropic_captured_variance_table1():
+    """Table 1 isotropic row: PCA at subspace dimension 32 captures 6.5% of an
+    isotropic Gaussian (d=768, N=10k). Marchenko-Pastur puts it there too."""
+    g = _load("paper_table1_isotropic.json")
+    X = synth.isotropic(10000, 768, 11).numpy()
+    idx = O.build_index(X, 1, 32, np.array([0.3]))
+    lam = idx["eig"][0]
+    got = lam[:32].sum() / lam.sum()
+    assert abs(got - g["pca_variance_captured"]) < 0.002
+
+
+@pytest.mark.slow
+def test_isotropic_mode_b_recall_table1_soft():
+    """Table 1 isotropic Mode B row (cand. recall 10.3%, rerank recall 49.4%
+    at C=200). The paper's query set is unstated; in-sample queries are used,
+    so this is a soft pin (a few points)."""
+    g = _load("paper_table1_isotropic.json")
+    X = synth.isotropic(10000, 768, 11).numpy()
+    idx = O.build_index(X, 1, 32, np.array([0.3]))
+    Q = X[np.arange(0, 10000, 10)]
+    res = O.search(idx, X, Q, 10, 200, 1)
+    bf, _, _ = O.brute_force(X, Q, 10)
+    rer = np.mean([len(set(a.tolist()) & set(b.tolist())) / 10 for a, b in zip(res["out_id"], bf)])
+    cand = np.mean([len(set(a[:10].astype(np.int64).tolist()) & set(b.tolist())) / 10
+                    for a, b in zip(res["cand_id"], bf)])
+    assert abs(cand - g["candidate_recall_at_10"]) < 0.02
+    assert abs(rer - g["rerank_recall_at_10"]) < 0.05
+
+
+# ---------------------------------------------------------------- search
+
+
+def _hand_index(g):
+    d, r = g["d"], g["r"]
+    rows = np.array(g["rows"], dtype=np.float32)
+    U = np.array(g["basis"], dtype=np.float32).reshape(1, r, d)
+    mu = np.array(g["centre"], dtype=np.float32).reshape(1, d)
+    Z = (rows.astype(np.float64) - mu[0]) @ U[0].T.astype(np.float64)
+    E = (rows - mu[0]) - Z @ U[0]
+    return dict(M=mu, U=U, grain_off=np.array([0, len(rows)]), ids=np.arange(len(rows), dtype=np.uint32),
+                Z=Z.astype(np.float32), rho=(E * E).sum(1).astype(np.float32), G=1, r=r, d=d, N=len(rows)), rows
+
+
+def test_eq6_hand_fixture():
+    g = _load("eq6_tiny.json")
+    idx, rows = _hand_index(g)
+    Q = np.array([g["query"]], dtype=np.float32)
+    res = O.search(idx, rows, Q, g["k"], g["C"], 1)
+    assert res["cand_id"][0].tolist() == g["cand_id"]
+    np.testing.assert_allclose(res["cand_d"][0], g["cand_d"], rtol=0, atol=1e-12)
+    assert res["out_id"][0].tolist() == g["out_id"]
+    np.testing.assert_allclose(res["out_d"][0][:g["k"]], g["out_d"], rtol=0, atol=1e-12)
+    bf, bd, _ = O.brute_force(rows, Q, 3)
+    assert bf[0].tolist() == g["exact_order"]
+
+
+def test_bruteforce_ties_by_id():
+    X = np.array([[1, 0], [0, 1], [-1, 0], [2, 0], [0, -1]], dtype=np.float32)
+    Q = np.zeros((1, 2), dtype=np.float32)
+    ids, dd, nxt = O.brute_force(X, Q, 4)
+    assert ids[0].tolist() == [0, 1, 2, 4]
+    assert dd[0].tolist() == [1.0, 1.0, 1.0, 1.0]
+    assert nxt[0] == 4.0
+
+
+def test_full_basis_all_probes_reduces_to_brute_force():
+    """r = d makes every residual zero and Eq. 6 exact; with nprobe = G and
+    C = N the pool is every row, so candidates are in exact-distance order and
+    the reranked top-k equals brute-force kNN."""
+    X, Q, _ = _clustered(400, 16, 4, 25, 41)
+    G = 4
+    idx = O.build_index(X, G, 16, synth.uniforms(G, 1).numpy())
+    assert np.max(idx["rho"]) < 1e-9
+    res = O.search(idx, X, Q, 10, 400, G)
+    bf, bd, _ = O.brute_force(X, Q, 10)
+    np.testing.assert_array_equal(res["out_id"], bf)
+    np.testing.assert_allclose(res["out_d"][:, :10], bd, rtol=1e-12)
+    # candidate distances are the exact distances, up to the FP32 rounding of the stored U and z
+    ball, dall, _ = O.brute_force(X, Q, 400)
+    for qi in range(len(Q)):
+        ex = {int(i): dv for i, dv in zip(ball[qi], dall[qi])}
+        for j, cid in enumerate(res["cand_id"][qi]):
+            assert abs(res["cand_d"][qi, j] - ex[int(cid)]) <= 1e-6 * (1 + ex[int(cid)])
+
+
+def test_eq6_error_is_twice_residual_inner_product():
+    """For r < d: D - ||q - x||^2 = 2 e_q . e_i, so |D - exact| <= 2 sqrt(rho_q rho_i)
+    (Cauchy-Schwarz). rho_q is taken by Pythagoras, ||v'||^2 - ||z_q||^2."""
+    X, Q, _ = _clustered(500, 24, 3, 10, 51)
+    G, r = 3, 5
+    idx = O.build_index(X, G, r, synth.uniforms(G, 2).numpy())
+    res = O.search(idx, X, Q, 5, 500, G)
+    pos = {int(i): p for p, i in enumerate(idx["ids"])}
+    gof = np.searchsorted(idx["grain_off"], np.arange(len(X)), side="right") - 1
+    for qi in range(len(Q)):
+        q = Q[qi].astype(np.float64)
+        for j, cid in enumerate(res["cand_id"][qi]):
+            p = pos[int(cid)]
+            g = gof[p]
+            v = q - idx["M"][g].astype(np.float64)
+            zq = idx["U"][g].astype(np.float64) @ v
+            rho_q = max(0.0, v @ v - zq @ zq)
+            ex = float(((q - X[cid].astype(np.float64)) ** 2).sum())
+            bound = 2 * np.sqrt(rho_q * float(idx["rho"][p])) + 1e-6 * (1 + ex)
+            assert abs(res["cand_d"][qi, j] - ex) <= bound
+
+
+def test_basis_sign_and_rotation_invariance():
+    X, Q, _ = _clustered(300, 20, 2, 8, 61)
+    G, r = 2, 6
+    idx = O.build_index(X, G, r, synth.uniforms(G, 3).numpy())
+    base = O.search(idx, X, Q, 5, 40, G)
+    rng = np.random.default_rng(0)
+    R = np.linalg.qr(rng.standard_normal((r, r)))[0]
+    idx2 = dict(idx)
+    idx2["U"] = np.einsum("ij,gjd->gid", R, idx["U"].astype(np.float64)).astype(np.float64)
+    # keep the coordinates exactly consistent with the rotated basis, in FP64
+    idx2["Z"] = (idx["Z"].astype(np.float64) @ R.T)
+    idx2["U"] = idx2["U"].astype(np.float32)
+    idx2["Z"] = idx2["Z"].astype(np.float32)
+    rot = O.search(idx2, X, Q, 5, 40, G)
+    np.testing.assert_allclose(rot["cand_d"], base["cand_d"], rtol=2e-5)
+    idx3 = dict(idx)
+    idx3["U"] = -idx["U"]
+    idx3["Z"] = -idx["Z"]
+    flip = O.search(idx3, X, Q, 5, 40, G)
+    np.testing.assert_array_equal(flip["cand_id"], base["cand_id"])
+    np.testing.assert_array_equal(flip["cand_d"], base["cand_d"])
+
+
+def test_routing_order_and_ties():
+    # centres at distance 1, 1, 4 from the query -> probes by (dist, grain)
+    M = np.array([[0, 2], [1, 0], [0, 1], [-1, 0]], dtype=np.float32)
+    idx = dict(M=M, U=np.zeros((4, 1, 2), dtype=np.float32) + np.array([1, 0], dtype=np.float32),
+               grain_off=np.array([0, 0, 0, 0, 0]), ids=np.zeros(0, dtype=np.uint32),
+               Z=np.zeros((0, 1), dtype=np.float32), rho=np.zeros(0, dtype=np.float32), G=4, r=1, d=2, N=0)
+    Q = np.zeros((1, 2), dtype=np.float32)
+    res = O.search(idx, np.zeros((0, 2), dtype=np.float32), Q, 1, 1, 3)
+    assert res["probe"][0].tolist() == [1, 2, 3]
+    assert res["probe_d"][0].tolist() == [1.0, 1.0, 1.0, 4.0]
+    assert res["out_id"][0].tolist() == [-1]
+    assert res["cand_id"][0].tolist() == [0xFFFFFFFF]
+
+
+def test_filter_equals_search_on_filtered_subset():
+    """An in-scan range filter returns what the unfiltered path returns on the
+    rows that pass (r = d, all probes, C = N makes both exact)."""
+    X, Q, _ = _clustered(300, 8, 3, 12, 71)
+    attr = synth.attributes(300, 5, span=1000).numpy()
+    ranges = synth.range_filters(12, 6, span=1000, selectivity=0.3, frac_filtered=0.6).numpy()
+    idx = O.build_index(X, 3, 8, synth.uniforms(3, 1).numpy())
+    res = O.search(idx, X, Q, 5, 300, 3, attr=attr, ranges=ranges)
+    for qi in range(len(Q)):
+        keep = np.nonzero((attr >= ranges[qi, 0]) & (attr <= ranges[qi, 1]))[0]
+        sub_ids, sub_d, _ = O.brute_force(X[keep], Q[qi:qi + 1], 5)
+        want = [int(keep[i]) if i >= 0 else -1 for i in sub_ids[0]]
+        assert res["out_id"][qi].tolist() == want
+
+
+def test_nprobe_all_c_all_recall_one():
+    X, Q, _ = _clustered(800, 32, 8, 30, 81)
+    G = 8
+    idx = O.build_index(X, G, 4, synth.uniforms(G, 7).numpy())
+    res = O.search(idx, X, Q, 10, 800, G)
+    bf, _, _ = O.brute_force(X, Q, 10)
+    np.testing.assert_array_equal(res["out_id"], bf)
+
+
+def test_short_results_are_padded():
+    X, Q, _ = _clustered(50, 8, 2, 3, 91)
+    idx = O.build_index(X, 2, 4, synth.uniforms(2, 1).numpy())
+    res = O.search(idx, X, Q, 100, 200, 2)
+    assert np.all(res["out_id"][:, 50:] == -1)
+    assert np.all(np.isinf(res["out_d"][:, 50:]))
+    assert np.all(res["cand_id"][:, 50:] == 0xFFFFFFFF)
+
+
+# ---------------------------------------------------------------- number formats
+
+
+def test_e4m3_spec_values_and_exhaustive_round_trip():
+    g = _load("e4m3_values.json")
+    for code, val in g["codes"].items():
+        assert O.e4m3_value(np.uint8(int(code, 16))) == val
+    for code in g["nan_codes"]:
+        assert np.isnan(O.e4m3_value(np.uint8(int(code, 16))))
+    codes = np.arange(256, dtype=np.uint8)
+    vals = O.e4m3_value(codes)
+    fin = ~np.isnan(vals) & (codes != 0x80)
+    np.testing.assert_array_equal(O.e4m3_encode(vals[fin]), codes[fin])
+
+
+def test_e4m3_matches_torch_cast_and_ties_to_even():
+    # torch's float8_e4m3fn cast is an independent implementation (RNE); compare inside the finite range
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.standard_normal(20000) * s for s in (1e-3, 0.1, 1, 30, 200)])
+    x = x[np.abs(x) <= 448]
+    ours = O.e4m3_value(O.e4m3_encode(x))
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(ours, ref)
+    # exact midpoints between neighbours go to the even code
+    pos = O.e4m3_value(np.arange(0, 0x7F, dtype=np.uint8))
+    mids = (pos[:-1] + pos[1:]) / 2
+    enc = O.e4m3_encode(mids)
+    assert np.all(enc % 2 == 0)
+    # saturation to the largest finite value
+    assert O.e4m3_value(O.e4m3_encode(np.array([1000.0, -5000.0]))).tolist() == [448.0, -448.0]
+
+
+def test_bf16_matches_torch_cast():
+    rng = np.random.default_rng(4)
+    x = (rng.standard_normal(100000) * 10).astype(np.float32)
+    x[:4] = [0.0, -0.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8]  # exact ties: to even
+    ours = O.bf16_to_f32(O.bf16_round(x))
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(ours, ref)
+
+
+def test_index_file_header_and_checksum_round_trip(tmp_path):
+    X, Q, _ = _clustered(200, 8, 2, 2, 95)
+    idx = O.build_index(X, 2, 4, synth.uniforms(2, 1).numpy())
+    p = str(tmp_path / "a.hntl")
+    O.write_index(p, idx, X)
+    h = O.read_index_header(p)
+    assert (h["N"], h["d"], h["G"], h["r"], h["version"]) == (200, 8, 2, 4, 1)
+    data = open(p, "rb").read()
+    body, tail = data[:-8], data[-8:]
+    s, _ = O._wsum(body, (0, 0))
+    assert s == int(np.frombuffer(tail, dtype="<u8")[0])
