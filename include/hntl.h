@@ -1,0 +1,137 @@
+/*
+ * hntl.h - C ABI of the B300 (sm_103a) HNTL batched query path.
+ *
+ * HNTL (Hierarchical No-pointer Tangent-Local search) splits the corpus into
+ * grains, stores each row as r tangent coordinates in its grain's local PCA
+ * basis plus a residual norm, and answers a query in five steps:
+ *   1. routing to the nprobe nearest grain centres      (sec. 2.1 step 1, sec. 2.3)
+ *   2. projection into each probed grain's basis        (Eq. 1-4)
+ *   3. Block-SoA scan with D = ||z_q - z_i||^2 + rho_q + rho_i   (Eq. 6, sec. 2.4)
+ *   4. pool of the C smallest D                          (Table 1, "Pool C")
+ *   5. exact L2 rerank of the pool to the top k          (sec. 2.1 step 4, Mode B)
+ *
+ * Conventions for every call:
+ *   - Return value: HNTL_OK (0) or a negative HNTL_E* code; no exception or
+ *     abort crosses the ABI. hntl_last_error() gives a thread-local message.
+ *   - "device" pointers are CUDA global-memory addresses on the index's
+ *     device; "host" pointers are ordinary CPU memory. The caller owns every
+ *     buffer it passes; the library owns the index and frees it in
+ *     hntl_index_free().
+ *   - Asynchronous calls take a cudaStream_t passed as void* (NULL = legacy
+ *     default stream). They enqueue work and return; argument errors are
+ *     reported before anything is enqueued, launch errors from the enqueue.
+ *   - Distances are squared L2. Ordering everywhere is (distance, id)
+ *     ascending; routing is (distance, grain) ascending.
+ *   - Limits: 1 <= r <= 64, r <= d, 1 <= nprobe <= G, 1 <= k <= C <= 1024
+ *     (C below k is raised to k), G <= 8192. Violations return HNTL_EINVAL.
+ */
+#ifndef HNTL_H_
+#define HNTL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HNTL_OK 0
+#define HNTL_EINVAL (-1)   /* bad argument, size or limit */
+#define HNTL_ENOMEM (-2)   /* device or host allocation failed */
+#define HNTL_ECUDA (-3)    /* a CUDA call or kernel launch failed */
+#define HNTL_EIO (-4)      /* file could not be opened, read or written */
+#define HNTL_EFORMAT (-5)  /* index file malformed, truncated or checksum mismatch */
+#define HNTL_ETIMEOUT (-6) /* a bounded device wait gave up */
+#define HNTL_EBUSY (-7)    /* admission refused: memory budget or slots exhausted */
+
+/* Index precision. FP32: FP32 raw rows and coordinates (the plain method).
+ * BF16_FP8: BF16 raw rows, FP8-E4M3 coordinates with a per-grain FP32 scale. */
+#define HNTL_PREC_FP32 0
+#define HNTL_PREC_BF16_FP8 1
+
+typedef struct hntl_index hntl_index; /* opaque; owned by the library */
+
+typedef struct {
+  uint64_t n;              /* rows */
+  uint32_t d;              /* ambient dimension */
+  uint32_t G;              /* grains */
+  uint32_t r;              /* tangent dimension */
+  uint32_t precision;      /* HNTL_PREC_* */
+  uint32_t has_attr;       /* 1 if an int64 attribute column is loaded */
+  uint32_t block_rows;     /* rows per Block-SoA block (128) */
+  uint64_t n_blocks;       /* Block-SoA blocks over all grains */
+  uint64_t max_grain_rows; /* rows of the largest grain */
+  uint64_t device_bytes;   /* device memory held by the index */
+  int device;              /* CUDA device ordinal */
+} hntl_index_desc;
+
+/* Library version string. */
+const char* hntl_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* hntl_last_error(void);
+
+/* Load an index file (format: header "HNTLIDX\0", version 1, sections for
+ * centres, bases, optional eigenvalues, grain offsets, grain-ordered ids,
+ * coordinates and residual norms, optional FP8 coordinates + scales, raw rows
+ * in id order (FP32 or BF16), optional int64 attributes, and a trailing
+ * position-weighted 64-bit word checksum) onto `device`, laid out as 128-row
+ * Block-SoA blocks (dimension-major inside a block, grains padded to whole
+ * blocks). precision selects which coordinate/raw-row sections the search
+ * uses (HNTL_PREC_BF16_FP8 needs them in the file). Blocking; on success
+ * *out owns device memory. Errors: EIO (open/read), EFORMAT (magic, version,
+ * sizes, offsets, ids, truncation, checksum), EINVAL, ENOMEM, ECUDA. */
+int hntl_index_load(const char* path, int device, uint32_t precision, hntl_index** out);
+
+/* Describe an index. */
+int hntl_index_info(const hntl_index* idx, hntl_index_desc* out);
+
+/* Free an index and its device memory (NULL is a no-op). Blocking. */
+void hntl_index_free(hntl_index* idx);
+
+/* Bytes of device workspace hntl_search needs for these parameters (0 if
+ * the parameters are invalid; see hntl_last_error). */
+size_t hntl_search_workspace_bytes(const hntl_index* idx, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe);
+
+/* Batched Mode B search (the five steps above), asynchronous on `stream`.
+ *   d_queries  device, nq x d FP32 row-major
+ *   d_filter   device, nq x 2 int64 inclusive [lo, hi] attribute range per
+ *              query, or NULL for no filtering (needs an index with attributes)
+ *   d_ws       device workspace of ws_bytes >= hntl_search_workspace_bytes(),
+ *              256-byte aligned; contents need not be initialised
+ *   d_out_ids  device, nq x k int64 ids, (distance, id) ascending; -1 pads
+ *   d_out_dist device, nq x k FP32 exact squared distances; +inf pads
+ *   d_cand_ids device, nq x C uint32 pool ids (0xFFFFFFFF pads), or NULL
+ *   d_cand_dist device, nq x C FP32 approximate distances D of the pool
+ *              (+inf pads), or NULL (both or neither)
+ *   d_probe    device, nq x nprobe int32 probed grains, or NULL
+ * The call is reentrant across streams when each call has its own workspace. */
+int hntl_search(const hntl_index* idx, const float* d_queries, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe,
+                const int64_t* d_filter, void* d_ws, size_t ws_bytes, int64_t* d_out_ids, float* d_out_dist,
+                uint32_t* d_cand_ids, float* d_cand_dist, int32_t* d_probe, void* stream);
+
+/* Device workspace hntl_search_host needs: the search workspace followed by
+ * device staging for the queries, the filters (if with_filter) and results. */
+size_t hntl_search_host_workspace_bytes(const hntl_index* idx, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe,
+                                        int with_filter);
+
+/* Blocking convenience form with HOST buffers (pinned memory makes the
+ * copies asynchronous): copies the queries (and filters) to device staging
+ * inside d_ws, runs hntl_search on `stream`, copies ids and distances back
+ * and synchronises the stream. h_filter may be NULL. h_out_ids/h_out_dist
+ * are nq x k. */
+int hntl_search_host(const hntl_index* idx, const float* h_queries, uint32_t nq, uint32_t k, uint32_t C,
+                     uint32_t nprobe, const int64_t* h_filter, void* d_ws, size_t ws_bytes, int64_t* h_out_ids,
+                     float* h_out_dist, void* stream);
+
+/* Centroid routing alone (step 1), asynchronous: the nprobe nearest grain
+ * centres of each query by (||q - mu_g||^2, g), with their FP32 distances.
+ * d_ws/ws_bytes as for hntl_search_workspace_bytes(idx, nq, 1, 1, nprobe). */
+int hntl_route(const hntl_index* idx, const float* d_queries, uint32_t nq, uint32_t nprobe, void* d_ws,
+               size_t ws_bytes, int32_t* d_probe, float* d_probe_dist, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HNTL_H_ */

@@ -1,0 +1,86 @@
+// Internal declarations of the HNTL CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hntl.h"
+
+namespace hntl {
+
+// Rows per Block-SoA block: one thread per row in the scan, 128-row tiles.
+constexpr int kBlockRows = 128;
+constexpr int kMaxR = 64;
+constexpr int kMaxC = 1024;
+constexpr uint32_t kMaxG = 8192;
+constexpr uint32_t kInvalidId = 0xFFFFFFFFu;
+
+// Device-resident index. Grains are stored one after another, each padded to
+// whole 128-row blocks; inside a block the coordinates are dimension-major
+// (Z[b][j][t] is coordinate j of row t of block b), so the scan's 128 threads
+// read each coordinate with one coalesced 512-byte (FP32) or 128-byte (FP8)
+// transaction. Padding rows carry id 0xFFFFFFFF and are masked by row count.
+struct Index {
+  int device = 0;
+  uint64_t n = 0;
+  uint32_t d = 0, G = 0, r = 0, precision = HNTL_PREC_FP32;
+  bool has_attr = false;
+  uint64_t n_blocks = 0;
+  uint64_t max_grain_rows = 0;
+  uint64_t device_bytes = 0;
+
+  float* M = nullptr;            // [G][d] centres
+  float* U = nullptr;            // [G][r][d] bases, orthonormal rows
+  uint32_t* blk_off = nullptr;   // [G+1] first block of each grain
+  uint32_t* grain_rows = nullptr;  // [G] rows of each grain
+  uint32_t* blk_grain = nullptr;   // [n_blocks] grain of each block
+  float* Zb = nullptr;           // [n_blocks][r][128] FP32 coordinates
+  uint8_t* Z8b = nullptr;        // [n_blocks][r][128] FP8-E4M3 codes (precision form)
+  float* scale = nullptr;        // [G] FP8 scale per grain
+  float* rho = nullptr;          // [n_blocks][128] residual norms
+  uint32_t* ids = nullptr;       // [n_blocks][128] original ids
+  int64_t* attr_b = nullptr;     // [n_blocks][128] attributes in block order
+  float* X = nullptr;            // [n][d] FP32 raw rows, id order
+  uint16_t* Xh = nullptr;        // [n][d] BF16 raw rows, id order
+
+  // host copies used for workspace sizing
+  std::vector<uint32_t> h_blk_off;
+  std::vector<uint64_t> h_top_padded_prefix;  // prefix sums of padded grain sizes, largest first
+  std::vector<void*> allocations;
+};
+
+// Thread-local error message plumbing.
+int fail(int code, const std::string& msg);
+void clear_error();
+
+#define HNTL_CUDA_TRY(expr)                                                                  \
+  do {                                                                                       \
+    cudaError_t _e = (expr);                                                                 \
+    if (_e != cudaSuccess)                                                                   \
+      return ::hntl::fail(HNTL_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));   \
+  } while (0)
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Workspace carving: every sub-buffer starts on a 256-byte boundary.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = align_up(off, 256);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+}  // namespace hntl
+
+struct hntl_index {
+  hntl::Index I;
+};

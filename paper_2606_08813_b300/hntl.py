@@ -1,0 +1,206 @@
+"""Thin ctypes binding of libhntl.so (the C ABI in include/hntl.h).
+
+Argument marshalling only: every step of the search runs in the library's
+CUDA kernels. PyTorch supplies device memory (outputs and workspace) and the
+current CUDA stream. There is no CPU fallback: if the library is missing or
+fails to load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhntl.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EIO, EFORMAT, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
+PREC_FP32, PREC_BF16_FP8 = 0, 1
+INVALID_ID = 0xFFFFFFFF
+_NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EIO: "EIO", EFORMAT: "EFORMAT",
+          ETIMEOUT: "ETIMEOUT", EBUSY: "EBUSY"}
+
+
+class HntlError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libhntl.so is not built ({LIB_PATH}); run paper_2606_08813_b300/build_lib.py")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+
+class IndexDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("d", ctypes.c_uint32), ("G", ctypes.c_uint32), ("r", ctypes.c_uint32),
+                ("precision", ctypes.c_uint32), ("has_attr", ctypes.c_uint32), ("block_rows", ctypes.c_uint32),
+                ("n_blocks", ctypes.c_uint64), ("max_grain_rows", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("device", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_U32 = ctypes.c_uint32
+_SZ = ctypes.c_size_t
+lib.hntl_version.restype = ctypes.c_char_p
+lib.hntl_last_error.restype = ctypes.c_char_p
+lib.hntl_index_load.argtypes = [ctypes.c_char_p, ctypes.c_int, _U32, ctypes.POINTER(_P)]
+lib.hntl_index_info.argtypes = [_P, ctypes.POINTER(IndexDesc)]
+lib.hntl_index_free.argtypes = [_P]
+lib.hntl_index_free.restype = None
+lib.hntl_search_workspace_bytes.argtypes = [_P, _U32, _U32, _U32, _U32]
+lib.hntl_search_workspace_bytes.restype = _SZ
+lib.hntl_search_host_workspace_bytes.argtypes = [_P, _U32, _U32, _U32, _U32, ctypes.c_int]
+lib.hntl_search_host_workspace_bytes.restype = _SZ
+lib.hntl_search.argtypes = [_P, _P, _U32, _U32, _U32, _U32, _P, _P, _SZ, _P, _P, _P, _P, _P, _P]
+lib.hntl_search_host.argtypes = [_P, _P, _U32, _U32, _U32, _U32, _P, _P, _SZ, _P, _P, _P]
+lib.hntl_route.argtypes = [_P, _P, _U32, _U32, _P, _SZ, _P, _P, _P]
+
+
+def last_error() -> str:
+    return lib.hntl_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise HntlError(rc, last_error())
+
+
+def version() -> str:
+    return lib.hntl_version().decode()
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_tensor(t, dtype, shape, device, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)}")
+    if t.device.index != device:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the index is on cuda:{device}")
+    return t
+
+
+class Index:
+    """A device-resident HNTL index (owned by the library)."""
+
+    def __init__(self, handle):
+        self._h = handle
+        d = IndexDesc()
+        _check(lib.hntl_index_info(self._h, ctypes.byref(d)))
+        self.desc = d
+        self._ws = None
+
+    @classmethod
+    def load(cls, path: str, device: int = 0, precision: int = PREC_FP32) -> "Index":
+        h = _P()
+        _check(lib.hntl_index_load(os.fsencode(path), int(device), int(precision), ctypes.byref(h)))
+        return cls(h)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def device(self) -> int:
+        return int(self.desc.device)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib.hntl_index_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        d = self.desc
+        return {f: getattr(d, f) for f, _ in IndexDesc._fields_}
+
+    def workspace_bytes(self, nq: int, k: int, C: int, nprobe: int) -> int:
+        n = lib.hntl_search_workspace_bytes(self._h, nq, k, C, nprobe)
+        if n == 0:
+            raise HntlError(EINVAL, last_error())
+        return int(n)
+
+    def workspace(self, nbytes: int) -> torch.Tensor:
+        """A cached device workspace of at least nbytes (256-byte aligned)."""
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
+        return self._ws
+
+    def search(self, Q: torch.Tensor, k: int, C: int, nprobe: int, filters: torch.Tensor | None = None,
+               return_pool: bool = False, return_probe: bool = False, stream=None, out=None):
+        """Batched Mode B search of CUDA queries Q [nq, d] f32.
+
+        Returns (ids i64 [nq, k], dist f32 [nq, k]); with return_pool also the
+        pool (ids as int32 [nq, max(C, k)] holding the uint32 ids, so the
+        0xFFFFFFFF pad reads as -1, and approximate distances f32); with
+        return_probe also the probed grains int32 [nq, nprobe]."""
+        nq = int(Q.shape[0])
+        d = int(self.desc.d)
+        _dev_tensor(Q, torch.float32, (nq, d), self.device, "Q")
+        if filters is not None:
+            _dev_tensor(filters, torch.int64, (nq, 2), self.device, "filters")
+        Ce = max(C, k)
+        dev = Q.device
+        if out is None:
+            ids = torch.empty(nq, k, dtype=torch.int64, device=dev)
+            dist = torch.empty(nq, k, dtype=torch.float32, device=dev)
+        else:
+            ids, dist = out
+        pool_ids = torch.empty(nq, Ce, dtype=torch.int32, device=dev) if return_pool else None
+        pool_d = torch.empty(nq, Ce, dtype=torch.float32, device=dev) if return_pool else None
+        probe = torch.empty(nq, nprobe, dtype=torch.int32, device=dev) if return_probe else None
+        nb = self.workspace_bytes(max(nq, 1), k, C, nprobe)
+        ws = self.workspace(nb)
+        _check(lib.hntl_search(self._h, _ptr(Q), nq, k, C, nprobe, _ptr(filters), _ptr(ws), ws.numel(), _ptr(ids),
+                               _ptr(dist), _ptr(pool_ids), _ptr(pool_d), _ptr(probe), _stream(stream)))
+        res = [ids, dist]
+        if return_pool:
+            res += [pool_ids, pool_d]
+        if return_probe:
+            res.append(probe)
+        return tuple(res)
+
+    def search_host(self, Q, k: int, C: int, nprobe: int, filters=None, stream=None):
+        """Host-buffer form: Q is a CPU float32 tensor (pinned for async copies);
+        returns CPU (ids i64, dist f32). Copies happen inside the call."""
+        nq, d = int(Q.shape[0]), int(self.desc.d)
+        if Q.is_cuda or Q.dtype != torch.float32 or tuple(Q.shape) != (nq, d) or not Q.is_contiguous():
+            raise ValueError("Q must be a contiguous CPU float32 tensor [nq, d]")
+        if filters is not None and (filters.is_cuda or filters.dtype != torch.int64):
+            raise ValueError("filters must be a CPU int64 tensor [nq, 2]")
+        ids = torch.empty(nq, k, dtype=torch.int64, pin_memory=Q.is_pinned())
+        dist = torch.empty(nq, k, dtype=torch.float32, pin_memory=Q.is_pinned())
+        nb = int(lib.hntl_search_host_workspace_bytes(self._h, max(nq, 1), k, C, nprobe, int(filters is not None)))
+        if nb == 0:
+            raise HntlError(EINVAL, last_error())
+        ws = self.workspace(nb)
+        _check(lib.hntl_search_host(self._h, _ptr(Q), nq, k, C, nprobe, _ptr(filters), _ptr(ws), ws.numel(),
+                                    _ptr(ids), _ptr(dist), _stream(stream)))
+        return ids, dist
+
+    def route(self, Q: torch.Tensor, nprobe: int, stream=None):
+        nq = int(Q.shape[0])
+        _dev_tensor(Q, torch.float32, (nq, int(self.desc.d)), self.device, "Q")
+        probe = torch.empty(nq, nprobe, dtype=torch.int32, device=Q.device)
+        pd = torch.empty(nq, nprobe, dtype=torch.float32, device=Q.device)
+        nb = self.workspace_bytes(max(nq, 1), 1, 1, nprobe)
+        ws = self.workspace(nb)
+        _check(lib.hntl_route(self._h, _ptr(Q), nq, nprobe, _ptr(ws), ws.numel(), _ptr(probe), _ptr(pd),
+                              _stream(stream)))
+        return probe, pd

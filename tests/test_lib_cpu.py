@@ -1,0 +1,123 @@
+"""The C-ABI library on a machine without a GPU: it loads, exports every
+entry point declared in include/hntl.h, and rejects bad index files on the
+host before any CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import hntl_oracle as O
+
+from paper_2606_08813_b300 import build_lib
+
+build_lib.build()
+from paper_2606_08813_b300 import hntl  # noqa: E402
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hntl.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hntl_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol():
+    names = _declared()
+    assert len(names) >= 8
+    for n in names:
+        assert hasattr(hntl.lib, n), n
+
+
+def _load(path):
+    h = ctypes.c_void_p()
+    rc = hntl.lib.hntl_index_load(os.fsencode(path), 0, 0, ctypes.byref(h))
+    return rc, hntl.last_error()
+
+
+@pytest.fixture(scope="module")
+def good_file(tmp_path_factory):
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((60, 8)).astype(np.float32)
+    idx = O.build_index(X, 3, 4, np.array([0.1, 0.5, 0.9]))
+    p = str(tmp_path_factory.mktemp("idx") / "good.hntl")
+    O.write_index(p, idx, X)
+    return p
+
+
+def test_missing_file_is_eio():
+    rc, msg = _load("/nonexistent/x.hntl")
+    assert rc == hntl.EIO and "cannot open" in msg
+
+
+def test_bad_magic_is_eformat(tmp_path, good_file):
+    data = bytearray(open(good_file, "rb").read())
+    data[0:4] = b"XXXX"
+    p = tmp_path / "bad.hntl"
+    p.write_bytes(bytes(data))
+    rc, msg = _load(str(p))
+    assert rc == hntl.EFORMAT and "magic" in msg
+
+
+def test_truncated_is_eformat(tmp_path, good_file):
+    data = open(good_file, "rb").read()
+    for cut in (10, 100, len(data) - 1):
+        p = tmp_path / f"t{cut}.hntl"
+        p.write_bytes(data[:cut])
+        rc, _ = _load(str(p))
+        assert rc == hntl.EFORMAT
+
+
+def test_flipped_byte_fails_checksum(tmp_path, good_file):
+    data = bytearray(open(good_file, "rb").read())
+    data[200] ^= 0x40
+    p = tmp_path / "flip.hntl"
+    p.write_bytes(bytes(data))
+    rc, msg = _load(str(p))
+    assert rc == hntl.EFORMAT and "checksum" in msg
+
+
+def test_bad_version_is_eformat(tmp_path, good_file):
+    data = bytearray(open(good_file, "rb").read())
+    data[8] = 9
+    p = tmp_path / "ver.hntl"
+    p.write_bytes(bytes(data))
+    rc, msg = _load(str(p))
+    assert rc == hntl.EFORMAT and "version" in msg
+
+
+def test_ids_not_permutation_is_eformat(tmp_path):
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((20, 4)).astype(np.float32)
+    idx = O.build_index(X, 2, 2, np.array([0.2, 0.7]))
+    idx["ids"] = idx["ids"].copy()
+    idx["ids"][1] = idx["ids"][0]  # duplicate id; the checksum is recomputed by the writer
+    p = str(tmp_path / "dup.hntl")
+    O.write_index(p, idx, X)
+    rc, msg = _load(p)
+    assert rc == hntl.EFORMAT and "permutation" in msg
+
+
+def test_bad_offsets_is_eformat(tmp_path):
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((20, 4)).astype(np.float32)
+    idx = O.build_index(X, 2, 2, np.array([0.2, 0.7]))
+    idx["grain_off"] = np.array([0, 15, 12], dtype=np.int64)  # last != N and decreasing
+    p = str(tmp_path / "off.hntl")
+    O.write_index(p, idx, X)
+    rc, _ = _load(p)
+    assert rc == hntl.EFORMAT
+
+
+def test_precision_mismatch_is_einval(tmp_path, good_file):
+    h = ctypes.c_void_p()
+    rc = hntl.lib.hntl_index_load(os.fsencode(good_file), 0, hntl.PREC_BF16_FP8, ctypes.byref(h))
+    assert rc == hntl.EINVAL
+
+
+def test_null_arguments_are_einval():
+    assert hntl.lib.hntl_index_load(None, 0, 0, None) == hntl.EINVAL
+    assert hntl.lib.hntl_search(None, None, 1, 1, 1, 1, None, None, 0, None, None, None, None, None, None) \
+        == hntl.EINVAL
+    assert hntl.lib.hntl_search_workspace_bytes(None, 1, 1, 1, 1) == 0
