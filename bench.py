@@ -1,0 +1,414 @@
+"""Throughput benchmark of the HNTL batched query path on B300.
+
+A step is one hntl_search call over one batch of queries: routing, bucketing,
+projection, Block-SoA scan, pool selection and exact rerank, all in the
+library's CUDA kernels, with the index and the queries resident in HBM. The
+index is built once on the GPU by the library's builder (not timed).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank holds a replica of the index and searches
+its own query stream; no data-path collective (weak scaling). value = all
+ranks' queries / max over ranks of the timed seconds.
+
+--impl reference times the CPU oracle (the plain FP64 program the tests use
+as ground truth) on the host cores, on a bounded sample of the same
+workload's queries against the same index, and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2606_08813_b300 import synth  # noqa: E402
+
+METRIC = "QPS at Recall@10>=0.95"
+L2_BYTES = 126 * 1024 * 1024
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6400.0, 1800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.remove(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(name: str, device, rank: int = 0):
+    w = dict(synth.WORKLOADS[name])
+    sd = synth.seeds(w["seed"])
+    model = synth.make_cluster_model(w["n"], w["d"], w["n_clusters"], sizes=w["sizes"], seed=sd["data"])
+    X, _ = synth.sample_points(model, sd["data"] + 11, device=device, chunk=65536)
+    Q, _ = synth.sample_queries(model, w["nq"], sd["queries"] + 7919 * rank, device=device, chunk=65536)
+    return w, sd, X, Q
+
+
+def exact_topk(X: torch.Tensor, Q: torch.Tensor, k: int, shortlist: int = 64, qblock: int = 512,
+               chunk: int = 1 << 20):
+    """Ground-truth kNN for recall (evaluation only, not the search path): an
+    FP32 matmul shortlist per row chunk, then the shortlist re-ranked by FP64
+    direct-form distances with ties broken by id."""
+    out = []
+    for q0 in range(0, Q.shape[0], qblock):
+        Qb = Q[q0:q0 + qblock]
+        nq = Qb.shape[0]
+        best_d = torch.full((nq, shortlist), float("inf"), device=Q.device)
+        best_i = torch.zeros((nq, shortlist), dtype=torch.int64, device=Q.device)
+        qn = (Qb * Qb).sum(1, keepdim=True)
+        for s in range(0, X.shape[0], chunk):
+            Xc = X[s:s + chunk]
+            dd = qn + (Xc * Xc).sum(1)[None] - 2.0 * (Qb @ Xc.T)
+            v, i = torch.topk(dd, min(shortlist, Xc.shape[0]), dim=1, largest=False)
+            cat_d = torch.cat([best_d, v], 1)
+            cat_i = torch.cat([best_i, i + s], 1)
+            best_d, j = torch.topk(cat_d, shortlist, dim=1, largest=False)
+            best_i = torch.gather(cat_i, 1, j)
+        exact = ((X[best_i].double() - Qb.double()[:, None, :]) ** 2).sum(-1).cpu().numpy()
+        ids = best_i.cpu().numpy()
+        for qi in range(nq):
+            order = np.lexsort((ids[qi], exact[qi]))[:k]
+            out.append(ids[qi][order])
+    return torch.from_numpy(np.stack(out))
+
+
+def recall_at_k(found: torch.Tensor, truth: torch.Tensor) -> float:
+    f = found.cpu().numpy()
+    t = truth.cpu().numpy()
+    k = t.shape[1]
+    return float(np.mean([len(set(a[:k].tolist()) & set(b.tolist())) / k for a, b in zip(f, t)]))
+
+
+def stage_bytes(idx, rows_g, probe: np.ndarray, w: dict, batch: int):
+    """Algorithmic bytes per launch of each stage for one batch, from the
+    batch's probes (grains hit at least once are read once per batch)."""
+    r, d, G = w["r"], w["d"], w["G"]
+    hit = np.zeros(G, dtype=bool)
+    hit[np.unique(probe)] = True
+    union_rows = int(rows_g[hit].sum())
+    return {
+        "scan": union_rows * (4 * r + 4),               # FP32 coordinates + residual norm per row
+        "project": int(hit.sum()) * r * d * 4 + int(hit.sum()) * d * 4,  # probed bases + centres
+        "rerank": batch * w["C"] * d * 4,                # gathered raw FP32 rows
+        "route": G * d * 4 + batch * d * 4,
+    }
+
+
+def traffic_from_profiles(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, when it
+    was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(p)).get(kernel)
+        src = open(os.path.join(ROOT, "paper_2606_08813_b300", "csrc", rec["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha"]:
+            return None
+        return rec["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def cpu_oracle_qps(idx_host, X_np, Q_np, k, C, nprobe, budget_s: float = 15.0):
+    from oracle import hntl_oracle as O
+
+    O.build_c()
+    n = 16
+    t = 0.0
+    done = 0
+    while t < budget_s and done < Q_np.shape[0]:
+        m = min(n, Q_np.shape[0] - done)
+        t0 = time.perf_counter()
+        O.search(idx_host, X_np, Q_np[done:done + m], k, C, nprobe)
+        t += time.perf_counter() - t0
+        done += m
+        n = min(4 * n, 4096)
+    return done / t, done, O.threads()
+
+
+def run_ours(a, world, rank, local):
+    from paper_2606_08813_b300 import build_lib
+
+    build_lib.build()
+    from paper_2606_08813_b300 import hntl
+
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    w, sd, X, Q = make_workload(a.workload, dev, rank)
+    B = a.batch or w.get("batch", w["nq"])
+    k, C, nprobe = w["k"], w["C"], w["nprobe"]
+    t0 = time.perf_counter()
+    gi = hntl.Index.build(X, w["G"], w["r"], u=synth.uniforms(w["G"], sd["kmeans"]).numpy(), seed=sd["kmeans"])
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    rows_g = gi.grain_rows().astype(np.int64)
+    nb = w["nq"] // B
+    batches = [Q[i * B:(i + 1) * B].contiguous() for i in range(nb)]
+    out = (torch.empty(B, k, dtype=torch.int64, device=dev), torch.empty(B, k, dtype=torch.float32, device=dev))
+    # probes of every batch (untimed) for algorithmic bytes; results of batch 0 for recall
+    probes = []
+    found = []
+    for b in batches:
+        ids, dist, probe = gi.search(b, k, C, nprobe, return_probe=True)
+        probes.append(probe.cpu().numpy())
+        found.append(ids)
+    torch.cuda.synchronize()
+    n_recall = min(w["nq"], a.recall_queries)
+    truth = exact_topk(X, Q[:n_recall], 10)
+    rec = recall_at_k(torch.cat(found)[:n_recall], truth)
+    sbytes = [stage_bytes(gi, rows_g, p, w, B) for p in probes]
+
+    st = torch.cuda.current_stream()
+    for i in range(a.warmup):
+        gi.search(batches[i % nb], k, C, nprobe, out=out)
+    torch.cuda.synchronize()
+    hntl.profile_read()  # discard warm-up records
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    hntl.profile_enable(True)
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        ev[0].record(st)
+        for i in range(a.steps):
+            gi.search(batches[i % nb], k, C, nprobe, out=out)
+            ev[i + 1].record(st)
+        torch.cuda.synchronize()
+        barrier(world)
+    hntl.profile_enable(False)
+    stage_ms, calls = hntl.profile_read()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(a.steps)]
+    total_ms = ev[0].elapsed_time(ev[a.steps])
+    total_ms_max = max_over_ranks(total_ms, world)
+    qps = world * a.steps * B / (total_ms_max / 1e3)
+    clocks = clk.summary()
+
+    # e2e: host queries (pinned) -> device -> search -> host results, per step
+    hq = [b.cpu().pin_memory() for b in batches]
+    for i in range(min(3, a.warmup)):
+        gi.search_host(hq[i % nb], k, C, nprobe)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    e2e_steps = a.steps
+    for i in range(e2e_steps):
+        gi.search_host(hq[i % nb], k, C, nprobe)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_qps = world * e2e_steps * B / e2e_s
+
+    # roofline of the dominant stage
+    hbm, bf16, src = _peaks()
+    per_launch_ms = {s: stage_ms[s] / max(calls, 1) for s in stage_ms}
+    used = [sbytes[i % nb] for i in range(a.steps)]
+    mean_bytes = {s: float(np.mean([u[s] for u in used])) for s in used[0]}
+    dom = max(("scan", "rerank", "project", "select", "route"), key=lambda s: per_launch_ms.get(s, 0.0))
+    if dom in mean_bytes:
+        ach = mean_bytes[dom] / (per_launch_ms[dom] / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "traffic": traffic_from_profiles(dom), "peak_source": src,
+                "algorithmic_bytes_per_launch": int(mean_bytes[dom])}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None, "peak_source": src, "note": "no algorithmic byte model for this stage"}
+    others = {s: {"ms_per_launch": round(per_launch_ms[s], 4),
+                  "GBps": (round(mean_bytes[s] / (per_launch_ms[s] / 1e3) / 1e9, 1)
+                           if s in mean_bytes and per_launch_ms[s] > 0 else None)} for s in per_launch_ms}
+
+    line = {
+        "metric": METRIC, "value": round(qps, 1), "unit": "queries/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(total_ms_max / a.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": a.workload, "N": w["n"], "d": w["d"], "G": w["G"], "r": w["r"], "batch": B,
+                   "nprobe": nprobe, "C": C, "k": k, "recall_at_10": round(rec, 4), "recall_queries": n_recall,
+                   "sizes": w["sizes"], "l2": "no flush; per-step working set (probed coordinates, bases and "
+                   "gathered rows, ~0.5 GB) exceeds the 126 MB L2", "index_build_s": round(build_s, 2),
+                   "parallelism": f"replicas x{world}", "batch_latency_ms_p50": round(float(np.percentile(step_ms, 50)), 4),
+                   "batch_latency_ms_p99": round(float(np.percentile(step_ms, 99)), 4)},
+        "roofline": roof, "stages": others,
+        "e2e": {"value": round(e2e_qps, 1), "unit": "queries/s", "h2d_bytes_per_step": B * w["d"] * 4,
+                "d2h_bytes_per_step": B * k * 12},
+        "gpu_launches": 9 * a.steps, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        host = gi.export()
+        Xn = X.cpu().numpy()
+        Qn = Q[:4096].cpu().numpy()
+        q, nq_done, cores = cpu_oracle_qps(host, Xn, Qn, k, C, nprobe, budget_s=a.cpu_budget)
+        line["cpu_baseline"] = {"value": round(q, 2), "unit": "queries/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{nq_done} queries of the same workload against the same index "
+                                          f"(FP64 oracle search, OpenMP over queries)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(a, world, rank, local):
+    if rank != 0:
+        return
+    from paper_2606_08813_b300 import build_lib
+
+    build_lib.build()
+    from oracle import hntl_oracle as O
+    from paper_2606_08813_b300 import hntl
+
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    w, sd, X, Q = make_workload(a.workload, dev, 0)
+    k, C, nprobe = w["k"], w["C"], w["nprobe"]
+    gi = hntl.Index.build(X, w["G"], w["r"], u=synth.uniforms(w["G"], sd["kmeans"]).numpy(), seed=sd["kmeans"])
+    host = gi.export()
+    Xn = X.cpu().numpy()
+    Qn = Q.cpu().numpy()
+    del gi
+    O.build_c()
+    per_step = a.ref_queries
+    for i in range(a.warmup):
+        O.search(host, Xn, Qn[(i * per_step) % len(Qn):][:per_step], k, C, nprobe)
+    t0 = time.perf_counter()
+    for i in range(a.steps):
+        s = (i * per_step) % max(1, len(Qn) - per_step)
+        O.search(host, Xn, Qn[s:s + per_step], k, C, nprobe)
+    el = time.perf_counter() - t0
+    qps = a.steps * per_step / el
+    line = {"metric": METRIC, "value": round(qps, 2), "unit": "queries/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(el / a.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": a.workload, "N": w["n"], "d": w["d"], "G": w["G"], "r": w["r"],
+                       "batch": per_step, "nprobe": nprobe, "C": C, "k": k},
+            "cpu_baseline": {"value": round(qps, 2), "unit": "queries/s", "cores": O.threads(), "kind": "oracle",
+                             "sample": f"{per_step} queries per step against the GPU-built index of the same "
+                                       f"workload"},
+            "e2e": {"value": round(qps, 2), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain-1m-zipf", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--recall-queries", type=int, default=2048)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-queries", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    a = ap.parse_args()
+    if a.warmup < 3:
+        a.warmup = 3
+    world, rank, local = dist_setup()
+    try:
+        if a.impl == "reference":
+            run_reference(a, world, rank, local)
+        else:
+            run_ours(a, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -83,6 +83,33 @@ const char* hntl_last_error(void);
  * sizes, offsets, ids, truncation, checksum), EINVAL, ENOMEM, ECUDA. */
 int hntl_index_load(const char* path, int device, uint32_t precision, hntl_index** out);
 
+/* Parameters of hntl_index_build (zero-initialise, then set what you need). */
+typedef struct {
+  uint32_t precision;     /* HNTL_PREC_*: FP32, or BF16 rows + FP8 coordinates */
+  uint32_t max_iter;      /* Lloyd iterations on the training rows (0 = 10) */
+  uint64_t n_train;       /* k-means training rows, strided over the data (0 = min(N, 256 G)) */
+  uint64_t n_seed;        /* k-means++ seeding rows, strided over the training rows (0 = min(n_train, 32 G)) */
+  uint32_t pca_iters;     /* orthogonal iterations for each grain's basis (0 = 12) */
+  uint32_t reserved;
+  uint64_t seed;          /* initial bases, and the k-means++ draws when u is NULL */
+  const double* u;        /* host, G uniform draws in [0, 1) consumed by k-means++, or NULL */
+  const int64_t* d_attr;  /* device, N int64 attributes in id order (for filtered search), or NULL */
+} hntl_build_params;
+
+/* Build an index on the GPU from raw rows d_X (device, N x d FP32 row-major;
+ * the index keeps its own copy, BF16 in the precision form) and return it in
+ * *out. Grains: k-means++ seeding and Lloyd iterations (the paper leaves the
+ * partitioning open, sec. 2.2), then every row goes to its nearest centre and
+ * each centre becomes the mean of its members. Basis of each grain (sec. 2.2):
+ * the dominant r-dimensional subspace of the grain covariance by orthogonal
+ * iteration; coordinates and residual norms by Eq. 1-4. Precision form: FP8
+ * E4M3 coordinates with scale s_g = max|z| / 448 per grain, BF16 rows.
+ * Blocking (synchronises `stream`). Temporary device memory: about
+ * 4 (256 G + 32 G) d + 12 N + min(8 GiB, 4 G d^2) bytes plus the index.
+ * Errors: EINVAL (sizes, 1 <= r <= min(d, 64), G <= min(N, 8192)), ENOMEM, ECUDA. */
+int hntl_index_build(const float* d_X, uint64_t N, uint32_t d, uint32_t G, uint32_t r, const hntl_build_params* params,
+                     int device, void* stream, hntl_index** out);
+
 /* Describe an index. */
 int hntl_index_info(const hntl_index* idx, hntl_index_desc* out);
 
@@ -123,6 +150,26 @@ size_t hntl_search_host_workspace_bytes(const hntl_index* idx, uint32_t nq, uint
 int hntl_search_host(const hntl_index* idx, const float* h_queries, uint32_t nq, uint32_t k, uint32_t C,
                      uint32_t nprobe, const int64_t* h_filter, void* d_ws, size_t ws_bytes, int64_t* h_out_ids,
                      float* h_out_dist, void* stream);
+
+/* Per-grain row counts (host array of G entries). */
+int hntl_index_grain_rows(const hntl_index* idx, uint32_t* h_rows);
+
+/* Copy the index's arrays to HOST memory in grain order (any pointer may be
+ * NULL to skip it): centres G x d, bases G x r x d, grain offsets G+1, ids N
+ * (original id of each grain-ordered row), coordinates N x r (FP8 indices:
+ * codes decoded and multiplied by the grain scale) and residual norms N.
+ * Blocking. */
+int hntl_index_export(const hntl_index* idx, float* h_M, float* h_U, uint64_t* h_grain_off, uint32_t* h_ids,
+                      float* h_Z, float* h_rho);
+
+/* Stage timing. While enabled, every hntl_search records CUDA events on its
+ * own stream between its stages: 0 routing, 1 bucketing, 2 projection,
+ * 3 scan, 4 pool selection, 5 rerank. hntl_profile_read waits for the
+ * recorded events, adds their elapsed milliseconds per stage into ms[0..5],
+ * returns the number of searches covered in *calls and clears the record. */
+#define HNTL_NSTAGES 6
+int hntl_profile_enable(int on);
+int hntl_profile_read(double* ms, uint64_t* calls);
 
 /* Centroid routing alone (step 1), asynchronous: the nprobe nearest grain
  * centres of each query by (||q - mu_g||^2, g), with their FP32 distances.

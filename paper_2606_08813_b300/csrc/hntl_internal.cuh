@@ -52,6 +52,9 @@ struct Index {
   std::vector<void*> allocations;
 };
 
+// Frees an index's device memory (safe to call twice).
+void release(Index& I);
+
 // Thread-local error message plumbing.
 int fail(int code, const std::string& msg);
 void clear_error();

@@ -5,6 +5,8 @@
 // trailing checksum, then re-lays the grain-ordered rows into 128-row blocks
 // per grain (dimension-major inside a block, sec. 2.4's Block-SoA idea with
 // the block sized for one GPU thread per row) and uploads them.
+#include <cuda_fp8.h>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -320,3 +322,96 @@ void hntl_index_free(hntl_index* idx) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ export
+
+namespace hntl {
+namespace {
+
+__global__ void k_export_rows(const uint32_t* __restrict__ blk_off, const uint32_t* __restrict__ grain_rows, int G,
+                              int r, const float* __restrict__ Zb, const uint8_t* __restrict__ Z8b,
+                              const float* __restrict__ scale, const float* __restrict__ rho_b,
+                              const uint32_t* __restrict__ ids_b, const uint64_t* __restrict__ goff, float* __restrict__ Z,
+                              float* __restrict__ rho, uint32_t* __restrict__ ids, uint64_t N) {
+  uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  int lo = 0, hi = G;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (goff[mid] <= p) lo = mid;
+    else hi = mid;
+  }
+  const int g = lo;
+  const uint64_t i = p - goff[g];
+  const size_t b = blk_off[g] + i / kBlockRows, t = i % kBlockRows;
+  for (int j = 0; j < r; ++j) {
+    float v;
+    if (Zb) {
+      v = Zb[(b * r + j) * kBlockRows + t];
+    } else {
+      __nv_fp8_e4m3 c;
+      c.__x = Z8b[(b * r + j) * kBlockRows + t];
+      v = (float)c * scale[g];
+    }
+    Z[p * r + j] = v;
+  }
+  rho[p] = rho_b[b * kBlockRows + t];
+  ids[p] = ids_b[b * kBlockRows + t];
+}
+
+}  // namespace
+}  // namespace hntl
+
+extern "C" int hntl_index_grain_rows(const hntl_index* idx, uint32_t* h_rows) {
+  hntl::clear_error();
+  if (!idx || !h_rows) return hntl::fail(HNTL_EINVAL, "null argument");
+  HNTL_CUDA_TRY(cudaMemcpy(h_rows, idx->I.grain_rows, sizeof(uint32_t) * idx->I.G, cudaMemcpyDeviceToHost));
+  return HNTL_OK;
+}
+
+extern "C" int hntl_index_export(const hntl_index* idx, float* h_M, float* h_U, uint64_t* h_grain_off,
+                                 uint32_t* h_ids, float* h_Z, float* h_rho) {
+  hntl::clear_error();
+  if (!idx) return hntl::fail(HNTL_EINVAL, "null index");
+  const hntl::Index& I = idx->I;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(I.device);
+  std::vector<uint32_t> rows(I.G);
+  HNTL_CUDA_TRY(cudaMemcpy(rows.data(), I.grain_rows, sizeof(uint32_t) * I.G, cudaMemcpyDeviceToHost));
+  std::vector<uint64_t> goff(I.G + 1, 0);
+  for (uint32_t g = 0; g < I.G; ++g) goff[g + 1] = goff[g] + rows[g];
+  if (h_grain_off) std::memcpy(h_grain_off, goff.data(), sizeof(uint64_t) * (I.G + 1));
+  if (h_M) HNTL_CUDA_TRY(cudaMemcpy(h_M, I.M, sizeof(float) * I.G * I.d, cudaMemcpyDeviceToHost));
+  if (h_U) HNTL_CUDA_TRY(cudaMemcpy(h_U, I.U, sizeof(float) * I.G * I.r * I.d, cudaMemcpyDeviceToHost));
+  if (h_ids || h_Z || h_rho) {
+    void *dZ = nullptr, *drho = nullptr, *dids = nullptr, *dgoff = nullptr;
+    int rc = HNTL_OK;
+    if (cudaMalloc(&dZ, std::max<size_t>(16, sizeof(float) * I.n * I.r)) != cudaSuccess ||
+        cudaMalloc(&drho, std::max<size_t>(16, sizeof(float) * I.n)) != cudaSuccess ||
+        cudaMalloc(&dids, std::max<size_t>(16, sizeof(uint32_t) * I.n)) != cudaSuccess ||
+        cudaMalloc(&dgoff, sizeof(uint64_t) * (I.G + 1)) != cudaSuccess) {
+      rc = hntl::fail(HNTL_ENOMEM, "export staging allocation failed");
+    }
+    if (rc == HNTL_OK) {
+      cudaMemcpy(dgoff, goff.data(), sizeof(uint64_t) * (I.G + 1), cudaMemcpyHostToDevice);
+      hntl::k_export_rows<<<(unsigned)((I.n + 255) / 256), 256>>>(
+          I.blk_off, I.grain_rows, (int)I.G, (int)I.r, I.Zb, I.Z8b, I.scale, I.rho, I.ids,
+          static_cast<uint64_t*>(dgoff), static_cast<float*>(dZ), static_cast<float*>(drho),
+          static_cast<uint32_t*>(dids), I.n);
+      cudaError_t e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) rc = hntl::fail(HNTL_ECUDA, std::string("export: ") + cudaGetErrorString(e));
+    }
+    if (rc == HNTL_OK && h_Z) cudaMemcpy(h_Z, dZ, sizeof(float) * I.n * I.r, cudaMemcpyDeviceToHost);
+    if (rc == HNTL_OK && h_rho) cudaMemcpy(h_rho, drho, sizeof(float) * I.n, cudaMemcpyDeviceToHost);
+    if (rc == HNTL_OK && h_ids) cudaMemcpy(h_ids, dids, sizeof(uint32_t) * I.n, cudaMemcpyDeviceToHost);
+    cudaFree(dZ);
+    cudaFree(drho);
+    cudaFree(dids);
+    cudaFree(dgoff);
+    if (prev >= 0) cudaSetDevice(prev);
+    return rc;
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  return HNTL_OK;
+}

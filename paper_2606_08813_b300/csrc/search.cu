@@ -13,17 +13,20 @@
 // method states it: routing sum (q_t - mu_t)^2; projection of the centred
 // query v' = q - mu_g; residual e = v' - U^T z and rho_q = ||e||^2; scan
 // ||z_q - z_i||^2 + rho_q + rho_i; rerank sum (q_t - x_t)^2.
+#include <array>
 #include <cfloat>
 #include <cstdint>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "hntl_internal.cuh"
+#include "kernels_common.cuh"
 
 namespace hntl {
 
 namespace {
 
-constexpr int kPairsPerGroup = 8;   // pairs sharing one staged basis in k_project
 constexpr int kSelThreads = 512;
 constexpr int kTieCap = 1024;
 
@@ -136,35 +139,6 @@ __global__ void k_bucket_count(const int32_t* __restrict__ probe, int n, uint32_
   if (i < n) atomicAdd(&gcnt[probe[i]], 1u);
 }
 
-// Block-wide exclusive scan of one value per thread (1024 threads).
-template <typename T>
-__device__ T block_exclusive_scan(T v, T* tot, T* warp_sums) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  T x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    T y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) warp_sums[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    T w = lane < nw ? warp_sums[lane] : T(0);
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      T y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    if (lane < nw) warp_sums[lane] = w;
-    if (lane == nw - 1) *tot = w;
-  }
-  __syncthreads();
-  T base = warp > 0 ? warp_sums[warp - 1] : T(0);
-  T r = base + x - v;
-  __syncthreads();
-  return r;
-}
-
 // Single CTA: exclusive scans over grains of the pair counts (pair offsets),
 // of count x padded rows (distance-buffer bases) and of projection groups.
 __global__ void __launch_bounds__(1024) k_bucket_scan(const uint32_t* __restrict__ gcnt,
@@ -211,95 +185,6 @@ __global__ void k_bucket_scatter(const int32_t* __restrict__ probe, int nq, int 
   uint32_t pos = pair_off[g] + atomicAdd(&gcur[g], 1u);
   pair_q[pos] = (uint32_t)(i / nprobe);
   pair_of[i] = pos;
-}
-
-// ------------------------------------------------------------------ projection
-
-// One CTA per group of up to 8 (query, grain) pairs of one grain:
-//   v' = q - mu_g (Eq. 1), z = U_g v' (Eq. 2), e = v' - U_g^T z (Eq. 3), rho_q = ||e||^2 (Eq. 4).
-// The basis rows are read once per group and applied to all its pairs.
-__global__ void __launch_bounds__(256) k_project(const float* __restrict__ Q, const float* __restrict__ M,
-                                                 const float* __restrict__ U, int d, int r, int G,
-                                                 const uint32_t* __restrict__ grp_off,
-                                                 const uint32_t* __restrict__ pair_off,
-                                                 const uint32_t* __restrict__ pair_q, float* __restrict__ zq,
-                                                 float* __restrict__ rhoq) {
-  extern __shared__ float sv[];  // [kPairsPerGroup][d]
-  __shared__ float sz[kPairsPerGroup][kMaxR];
-  __shared__ float sred[kPairsPerGroup][8];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t total = grp_off[G];
-  for (uint32_t w = blockIdx.x; w < total; w += gridDim.x) {
-    int lo = 0, hi = G;  // largest g with grp_off[g] <= w
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (grp_off[mid] <= w) lo = mid;
-      else hi = mid;
-    }
-    const int g = lo;
-    const uint32_t p0 = pair_off[g] + (w - grp_off[g]) * kPairsPerGroup;
-    const int np = (int)min((uint32_t)kPairsPerGroup, pair_off[g + 1] - p0);
-    const float* mu = M + (size_t)g * d;
-    for (int e = threadIdx.x; e < kPairsPerGroup * d; e += blockDim.x) {
-      int p = e / d, t = e - p * d;
-      sv[e] = p < np ? Q[(size_t)pair_q[p0 + p] * d + t] - mu[t] : 0.f;
-    }
-    __syncthreads();
-    const float* Ug = U + (size_t)g * r * d;
-    for (int j = warp; j < r; j += 8) {
-      float acc[kPairsPerGroup];
-#pragma unroll
-      for (int p = 0; p < kPairsPerGroup; ++p) acc[p] = 0.f;
-      for (int t = lane; t < d; t += 32) {
-        float u = __ldg(Ug + (size_t)j * d + t);
-#pragma unroll
-        for (int p = 0; p < kPairsPerGroup; ++p) acc[p] = fmaf(u, sv[p * d + t], acc[p]);
-      }
-#pragma unroll
-      for (int p = 0; p < kPairsPerGroup; ++p) {
-        float x = acc[p];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) sz[p][j] = x;
-      }
-    }
-    __syncthreads();
-    float acc2[kPairsPerGroup];
-#pragma unroll
-    for (int p = 0; p < kPairsPerGroup; ++p) acc2[p] = 0.f;
-    for (int t = threadIdx.x; t < d; t += blockDim.x) {
-      float e[kPairsPerGroup];
-#pragma unroll
-      for (int p = 0; p < kPairsPerGroup; ++p) e[p] = sv[p * d + t];
-      for (int j = 0; j < r; ++j) {
-        float u = __ldg(Ug + (size_t)j * d + t);
-#pragma unroll
-        for (int p = 0; p < kPairsPerGroup; ++p) e[p] = fmaf(-sz[p][j], u, e[p]);
-      }
-#pragma unroll
-      for (int p = 0; p < kPairsPerGroup; ++p) acc2[p] = fmaf(e[p], e[p], acc2[p]);
-    }
-#pragma unroll
-    for (int p = 0; p < kPairsPerGroup; ++p) {
-      float x = acc2[p];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) sred[p][warp] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < np) {
-      int p = threadIdx.x;
-      float s = 0.f;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) s += sred[p][i];
-      rhoq[p0 + p] = s;
-    }
-    for (int e = threadIdx.x; e < np * r; e += blockDim.x) {
-      int p = e / r, j = e - p * r;
-      zq[(size_t)(p0 + p) * r + j] = sz[p][j];
-    }
-    __syncthreads();
-  }
 }
 
 // ------------------------------------------------------------------ scan
@@ -742,6 +627,36 @@ void launch_scan(const Index& I, const Ws& w, const int64_t* filter, cudaStream_
       w.pair_q, w.zq, w.rhoq, filter, w.D);
 }
 
+// Stage timing: CUDA events recorded on the search's stream between stages.
+using StageEvents = std::array<cudaEvent_t, HNTL_NSTAGES + 1>;
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  std::vector<StageEvents> pending, pool;
+};
+Profiler& profiler() {
+  static Profiler p;
+  return p;
+}
+bool profile_begin(StageEvents& ev) {
+  Profiler& P = profiler();
+  std::lock_guard<std::mutex> lk(P.mu);
+  if (!P.on) return false;
+  if (!P.pool.empty()) {
+    ev = P.pool.back();
+    P.pool.pop_back();
+    return true;
+  }
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return false;
+  return true;
+}
+void profile_end(const StageEvents& ev) {
+  Profiler& P = profiler();
+  std::lock_guard<std::mutex> lk(P.mu);
+  P.pending.push_back(ev);
+}
+
 }  // namespace
 
 int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe,
@@ -763,14 +678,22 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
   }
   DeviceGuard dg(I.device);
   if (!dg.ok) return fail(HNTL_ECUDA, "cannot make the index's device current");
+  StageEvents ev;
+  const bool prof = profile_begin(ev);
+  auto mark = [&](int i) {
+    if (prof) cudaEventRecord(ev[i], st);
+  };
+  mark(0);
   HNTL_CUDA_TRY(cudaMemsetAsync(w.gcnt, 0, sizeof(uint32_t) * I.G, st));
   HNTL_CUDA_TRY(cudaMemsetAsync(w.gcur, 0, sizeof(uint32_t) * I.G, st));
   if ((rc = launch_route(I, Qd, nq, nprobe, w, st))) return rc;
+  mark(1);
   const int P = (int)(nq * nprobe);
   k_bucket_count<<<(P + 255) / 256, 256, 0, st>>>(w.probe, P, w.gcnt);
   k_bucket_scan<<<1, 1024, 0, st>>>(w.gcnt, I.blk_off, (int)I.G, w.pair_off, w.seg_base, w.grp_off);
   k_bucket_scatter<<<(P + 255) / 256, 256, 0, st>>>(w.probe, (int)nq, (int)nprobe, w.pair_off, w.gcur, w.pair_q,
                                                     w.pair_of);
+  mark(2);
   {
     size_t smem = (size_t)kPairsPerGroup * I.d * sizeof(float);
     if (smem > 48 * 1024)
@@ -779,12 +702,15 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
     k_project<<<grid, 256, smem, st>>>(Qd, I.M, I.U, (int)I.d, (int)I.r, (int)I.G, w.grp_off, w.pair_off, w.pair_q,
                                        w.zq, w.rhoq);
   }
+  mark(3);
   if (I.r <= 8) launch_scan<8>(I, w, filter, st);
   else if (I.r <= 16) launch_scan<16>(I, w, filter, st);
   else if (I.r <= 32) launch_scan<32>(I, w, filter, st);
   else launch_scan<64>(I, w, filter, st);
+  mark(4);
   k_select<<<nq, kSelThreads, 0, st>>>((int)nprobe, (int)C, w.probe, w.pair_of, w.pair_off, w.seg_base, I.blk_off,
                                        I.ids, w.D, w.cand_id, w.cand_d);
+  mark(5);
   {
     size_t smem = (size_t)I.d * sizeof(float);
     if (smem > 40 * 1024) {
@@ -792,6 +718,8 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
     }
     k_rerank<false><<<nq, 256, smem, st>>>(Qd, I.X, (int)I.d, (int)C, (int)k, w.cand_id, out_ids, out_d);
   }
+  mark(6);
+  if (prof) profile_end(ev);
   if (probe_out)
     HNTL_CUDA_TRY(cudaMemcpyAsync(probe_out, w.probe, sizeof(int32_t) * nq * nprobe, cudaMemcpyDeviceToDevice, st));
   HNTL_CUDA_TRY(cudaGetLastError());
@@ -823,6 +751,35 @@ int route_only(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, vo
 }  // namespace hntl
 
 extern "C" {
+
+int hntl_profile_enable(int on) {
+  hntl::clear_error();
+  hntl::Profiler& P = hntl::profiler();
+  std::lock_guard<std::mutex> lk(P.mu);
+  P.on = on != 0;
+  return HNTL_OK;
+}
+
+int hntl_profile_read(double* ms, uint64_t* calls) {
+  hntl::clear_error();
+  if (!ms || !calls) return hntl::fail(HNTL_EINVAL, "null argument");
+  hntl::Profiler& P = hntl::profiler();
+  std::lock_guard<std::mutex> lk(P.mu);
+  for (int s = 0; s < HNTL_NSTAGES; ++s) ms[s] = 0.0;
+  *calls = 0;
+  for (auto& ev : P.pending) {
+    HNTL_CUDA_TRY(cudaEventSynchronize(ev[HNTL_NSTAGES]));
+    for (int s = 0; s < HNTL_NSTAGES; ++s) {
+      float t = 0.f;
+      HNTL_CUDA_TRY(cudaEventElapsedTime(&t, ev[s], ev[s + 1]));
+      ms[s] += t;
+    }
+    ++*calls;
+    P.pool.push_back(ev);
+  }
+  P.pending.clear();
+  return HNTL_OK;
+}
 
 size_t hntl_search_workspace_bytes(const hntl_index* idx, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe) {
   hntl::clear_error();

@@ -57,6 +57,31 @@ lib.hntl_search_host_workspace_bytes.restype = _SZ
 lib.hntl_search.argtypes = [_P, _P, _U32, _U32, _U32, _U32, _P, _P, _SZ, _P, _P, _P, _P, _P, _P]
 lib.hntl_search_host.argtypes = [_P, _P, _U32, _U32, _U32, _U32, _P, _P, _SZ, _P, _P, _P]
 lib.hntl_route.argtypes = [_P, _P, _U32, _U32, _P, _SZ, _P, _P, _P]
+lib.hntl_index_build.argtypes = [_P, ctypes.c_uint64, _U32, _U32, _U32, _P, ctypes.c_int, _P, ctypes.POINTER(_P)]
+lib.hntl_index_grain_rows.argtypes = [_P, _P]
+lib.hntl_index_export.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+lib.hntl_profile_enable.argtypes = [ctypes.c_int]
+lib.hntl_profile_read.argtypes = [_P, _P]
+NSTAGES = 6
+STAGES = ("route", "bucket", "project", "scan", "select", "rerank")
+
+
+class BuildParams(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_uint32), ("max_iter", ctypes.c_uint32), ("n_train", ctypes.c_uint64),
+                ("n_seed", ctypes.c_uint64), ("pca_iters", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("u", _P), ("d_attr", _P)]
+
+
+def profile_enable(on: bool = True):
+    _check(lib.hntl_profile_enable(int(on)))
+
+
+def profile_read():
+    """(per-stage milliseconds summed over the covered searches, number of searches)."""
+    ms = (ctypes.c_double * NSTAGES)()
+    calls = ctypes.c_uint64()
+    _check(lib.hntl_profile_read(ms, ctypes.byref(calls)))
+    return dict(zip(STAGES, list(ms))), int(calls.value)
 
 
 def last_error() -> str:
@@ -106,6 +131,55 @@ class Index:
         h = _P()
         _check(lib.hntl_index_load(os.fsencode(path), int(device), int(precision), ctypes.byref(h)))
         return cls(h)
+
+    @classmethod
+    def build(cls, X: torch.Tensor, G: int, r: int, precision: int = PREC_FP32, u=None, seed: int = 0,
+              attr: torch.Tensor | None = None, max_iter: int = 0, n_train: int = 0, n_seed: int = 0,
+              pca_iters: int = 0, stream=None) -> "Index":
+        """Build an index on the GPU from CUDA rows X [N, d] f32 (see hntl_index_build)."""
+        if not X.is_cuda or X.dtype != torch.float32 or X.dim() != 2 or not X.is_contiguous():
+            raise ValueError("X must be a contiguous CUDA float32 tensor [N, d]")
+        N, d = X.shape
+        dev = X.device.index
+        if attr is not None:
+            _dev_tensor(attr, torch.int64, (N,), dev, "attr")
+        u_arr = None
+        if u is not None:
+            import numpy as np
+
+            u_np = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+            if u_np.shape[0] < G:
+                raise ValueError("need G uniform draws")
+            u_arr = u_np
+        prm = BuildParams(precision=precision, max_iter=max_iter, n_train=n_train, n_seed=n_seed,
+                          pca_iters=pca_iters, reserved=0, seed=seed,
+                          u=None if u_arr is None else u_arr.ctypes.data_as(_P),
+                          d_attr=None if attr is None else attr.data_ptr())
+        h = _P()
+        _check(lib.hntl_index_build(_ptr(X), N, d, G, r, ctypes.byref(prm), dev, _stream(stream), ctypes.byref(h)))
+        return cls(h)
+
+    def grain_rows(self):
+        import numpy as np
+
+        out = np.zeros(int(self.desc.G), dtype=np.uint32)
+        _check(lib.hntl_index_grain_rows(self._h, out.ctypes.data_as(_P)))
+        return out
+
+    def export(self):
+        """Index arrays on the host, grain order (numpy): M, U, grain_off, ids, Z, rho."""
+        import numpy as np
+
+        d = self.desc
+        M = np.zeros((d.G, d.d), dtype=np.float32)
+        U = np.zeros((d.G, d.r, d.d), dtype=np.float32)
+        off = np.zeros(d.G + 1, dtype=np.uint64)
+        ids = np.zeros(d.n, dtype=np.uint32)
+        Z = np.zeros((d.n, d.r), dtype=np.float32)
+        rho = np.zeros(d.n, dtype=np.float32)
+        _check(lib.hntl_index_export(self._h, *(a.ctypes.data_as(_P) for a in (M, U, off, ids, Z, rho))))
+        return dict(M=M, U=U, grain_off=off.astype(np.int64), ids=ids, Z=Z, rho=rho, N=int(d.n), d=int(d.d),
+                    G=int(d.G), r=int(d.r))
 
     @property
     def handle(self):

@@ -1,0 +1,117 @@
+"""The library's GPU index builder against the oracle's build on the same rows
+and the same k-means++ draws."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hntl_oracle as O
+from paper_2606_08813_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hntl():
+    from paper_2606_08813_b300 import build_lib
+
+    build_lib.build()
+    from paper_2606_08813_b300 import hntl as h
+
+    return h
+
+
+def _partition_sets(assign):
+    groups = {}
+    for i, g in enumerate(assign.tolist()):
+        groups.setdefault(g, []).append(i)
+    return sorted(tuple(v) for v in groups.values())
+
+
+@pytest.fixture(scope="module")
+def plain10k(hntl):
+    w = synth.WORKLOADS["plain-10k"]
+    m = synth.make_cluster_model(w["n"], w["d"], w["n_clusters"], sizes=w["sizes"], seed=w["seed"])
+    X, _ = synth.sample_points(m, w["seed"] + 1)
+    X = X.numpy()
+    G, r = w["G"], w["r"]
+    u = synth.uniforms(G, 12345).numpy()
+    ora = O.build_index(X, G, r, u, keep_fp64=False)
+    Xd = torch.from_numpy(X).cuda()
+    gi = hntl.Index.build(Xd, G, r, u=u, n_train=len(X), n_seed=len(X), max_iter=25, seed=3)
+    exp = gi.export()
+    return X, ora, gi, exp
+
+
+def test_partition_matches_oracle(plain10k):
+    X, ora, gi, exp = plain10k
+    g_assign = np.zeros(len(X), dtype=np.int64)
+    off = exp["grain_off"]
+    for g in range(exp["G"]):
+        g_assign[exp["ids"][off[g]:off[g + 1]]] = g
+    assert _partition_sets(g_assign) == _partition_sets(ora["assign"])
+
+
+def test_centres_are_member_means(plain10k):
+    X, ora, gi, exp = plain10k
+    off = exp["grain_off"]
+    for g in range(exp["G"]):
+        mem = X[exp["ids"][off[g]:off[g + 1]]].astype(np.float64)
+        np.testing.assert_allclose(exp["M"][g], mem.mean(0), rtol=0, atol=2e-6 * (1 + np.abs(mem).max()))
+
+
+def test_bases_orthonormal_and_capture_top_variance(plain10k):
+    X, ora, gi, exp = plain10k
+    off = exp["grain_off"]
+    r = exp["r"]
+    for g in range(exp["G"]):
+        U = exp["U"][g].astype(np.float64)
+        np.testing.assert_allclose(U @ U.T, np.eye(r), atol=2e-5)
+        rows = exp["ids"][off[g]:off[g + 1]]
+        V = X[rows].astype(np.float64) - exp["M"][g].astype(np.float64)
+        cov = V.T @ V / len(rows)
+        captured = np.trace(U @ cov @ U.T)
+        lam = np.linalg.eigvalsh(cov)[::-1]
+        assert captured >= 0.99 * lam[:r].sum(), (g, captured, lam[:r].sum())
+
+
+def test_coordinates_follow_eq1_to_eq4_under_the_built_basis(plain10k):
+    X, ora, gi, exp = plain10k
+    off = exp["grain_off"]
+    for g in range(0, exp["G"], 5):
+        rows = exp["ids"][off[g]:off[g + 1]]
+        V = X[rows].astype(np.float64) - exp["M"][g].astype(np.float64)
+        U = exp["U"][g].astype(np.float64)
+        Z = V @ U.T
+        E = V - Z @ U
+        rho = (E * E).sum(1)
+        np.testing.assert_allclose(exp["Z"][off[g]:off[g + 1]], Z, rtol=0, atol=2e-5 * np.abs(V).max())
+        np.testing.assert_allclose(exp["rho"][off[g]:off[g + 1]], rho, rtol=1e-4, atol=1e-6)
+
+
+def test_search_on_built_index_reaches_recall(plain10k, hntl):
+    X, ora, gi, exp = plain10k
+    w = synth.WORKLOADS["plain-10k"]
+    m = synth.make_cluster_model(w["n"], w["d"], w["n_clusters"], sizes=w["sizes"], seed=w["seed"])
+    Q, _ = synth.sample_queries(m, 300, w["seed"] + 2)
+    ids, dist = gi.search(Q.cuda(), 10, w["C"], w["nprobe"])
+    bf, _, _ = O.brute_force(X, Q.numpy(), 10)
+    rec = np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids.cpu().numpy().tolist(), bf.tolist())])
+    assert rec >= 0.95
+
+
+def test_small_and_degenerate_grains(hntl):
+    """More grains than distinct clusters, a grain with fewer rows than r and
+    duplicated rows: bases must still be orthonormal (completed)."""
+    rng = np.random.default_rng(3)
+    base = rng.standard_normal((5, 32)).astype(np.float32) * 5
+    dup = np.repeat(base[:1], 200, 0)                                   # 200 identical rows
+    few = base[1:2] + 0.01 * rng.standard_normal((3, 32))               # 3 rows (< r)
+    rest = base[2 + np.arange(600) % 3] + rng.standard_normal((600, 32))
+    X = np.concatenate([dup, few, rest]).astype(np.float32)
+    gi = hntl.Index.build(torch.from_numpy(X).cuda(), 12, 8, seed=1)
+    exp = gi.export()
+    for g in range(12):
+        U = exp["U"][g].astype(np.float64)
+        np.testing.assert_allclose(U @ U.T, np.eye(8), atol=2e-5)
+    assert exp["grain_off"][-1] == len(X)
+    assert sorted(exp["ids"].tolist()) == list(range(len(X)))
