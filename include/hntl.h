@@ -177,6 +177,27 @@ int hntl_profile_read(double* ms, uint64_t* calls);
 int hntl_route(const hntl_index* idx, const float* d_queries, uint32_t nq, uint32_t nprobe, void* d_ws,
                size_t ws_bytes, int32_t* d_probe, float* d_probe_dist, void* stream);
 
+/* Allocation-free centroid routing (the paper has no counterpart; this is a
+ * service to callers). Some callers cannot allocate device memory at query
+ * time, for example a host application that reserves the whole GPU at start-up
+ * and gives its plug-ins no allocator, or a latency-critical loop in which a
+ * cudaMalloc would synchronise the device. This call computes what hntl_route
+ * computes (the nprobe nearest centres of each query and their FP32 squared
+ * distances into d_probe / d_probe_dist, nq x nprobe, device) without any
+ * caller workspace and without allocating: its scratch is one fixed device
+ * array inside the library of 2^21 floats (8 MiB), held by every GPU that
+ * loads the library until the process exits.
+ *   - nq * G must not exceed 2^21 (2,097,152); larger batches return
+ *     HNTL_EINVAL with a message. Route them in slices.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - All calls share the array, so calls whose kernels may overlap on the GPU
+ *     (different streams or host threads) race; serialise them.
+ * Asynchronous on `stream`; errors as for hntl_route. */
+int hntl_route_noalloc(const hntl_index* idx, const float* d_queries, uint32_t nq, uint32_t nprobe, int32_t* d_probe,
+                       float* d_probe_dist, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,7 @@ lib.hntl_search_host_workspace_bytes.restype = _SZ
 lib.hntl_search.argtypes = [_P, _P, _U32, _U32, _U32, _U32, _P, _P, _SZ, _P, _P, _P, _P, _P, _P]
 lib.hntl_search_host.argtypes = [_P, _P, _U32, _U32, _U32, _U32, _P, _P, _SZ, _P, _P, _P]
 lib.hntl_route.argtypes = [_P, _P, _U32, _U32, _P, _SZ, _P, _P, _P]
+lib.hntl_route_noalloc.argtypes = [_P, _P, _U32, _U32, _P, _P, _P]
 lib.hntl_index_build.argtypes = [_P, ctypes.c_uint64, _U32, _U32, _U32, _P, ctypes.c_int, _P, ctypes.POINTER(_P)]
 lib.hntl_index_grain_rows.argtypes = [_P, _P]
 lib.hntl_index_export.argtypes = [_P, _P, _P, _P, _P, _P, _P]
@@ -267,6 +268,17 @@ class Index:
         _check(lib.hntl_search_host(self._h, _ptr(Q), nq, k, C, nprobe, _ptr(filters), _ptr(ws), ws.numel(),
                                     _ptr(ids), _ptr(dist), _stream(stream)))
         return ids, dist
+
+    def route_noalloc(self, Q: torch.Tensor, nprobe: int, probe: torch.Tensor, probe_d: torch.Tensor,
+                      stream=None):
+        """Routing into caller-provided outputs with no workspace and no
+        allocation inside the library (see hntl_route_noalloc)."""
+        nq = int(Q.shape[0])
+        _dev_tensor(Q, torch.float32, (nq, int(self.desc.d)), self.device, "Q")
+        _dev_tensor(probe, torch.int32, (nq, nprobe), self.device, "probe")
+        _dev_tensor(probe_d, torch.float32, (nq, nprobe), self.device, "probe_d")
+        _check(lib.hntl_route_noalloc(self._h, _ptr(Q), nq, nprobe, _ptr(probe), _ptr(probe_d), _stream(stream)))
+        return probe, probe_d
 
     def route(self, Q: torch.Tensor, nprobe: int, stream=None):
         nq = int(Q.shape[0])
