@@ -242,7 +242,13 @@ def run_ours(a, world, rank, local):
     gi = hntl.Index.build(X, w["G"], w["r"], u=synth.uniforms(w["G"], sd["kmeans"]).numpy(), seed=sd["kmeans"])
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
+    if a.profile_mode:
+        del X
+        torch.cuda.empty_cache()
+        X = None
     rows_g = gi.grain_rows().astype(np.int64)
+    print(f"index: build {build_s:.2f} s, grain rows max {rows_g.max()} median {int(np.median(rows_g))} "
+          f"min {rows_g.min()}", file=sys.stderr)
     nb = w["nq"] // B
     batches = [Q[i * B:(i + 1) * B].contiguous() for i in range(nb)]
     out = (torch.empty(B, k, dtype=torch.int64, device=dev), torch.empty(B, k, dtype=torch.float32, device=dev))
@@ -254,9 +260,11 @@ def run_ours(a, world, rank, local):
         probes.append(probe.cpu().numpy())
         found.append(ids)
     torch.cuda.synchronize()
-    n_recall = min(w["nq"], a.recall_queries)
-    truth = exact_topk(X, Q[:n_recall], 10)
-    rec = recall_at_k(torch.cat(found)[:n_recall], truth)
+    n_recall = 0 if a.profile_mode else min(w["nq"], a.recall_queries)
+    rec = float("nan")
+    if n_recall:
+        truth = exact_topk(X, Q[:n_recall], 10)
+        rec = recall_at_k(torch.cat(found)[:n_recall], truth)
     sbytes = [stage_bytes(gi, rows_g, p, w, B) for p in probes]
 
     st = torch.cuda.current_stream()
@@ -284,25 +292,25 @@ def run_ours(a, world, rank, local):
     clocks = clk.summary()
 
     # e2e: host queries (pinned) -> device -> search -> host results, per step
+    e2e_steps = 0 if a.profile_mode else a.steps
     hq = [b.cpu().pin_memory() for b in batches]
     for i in range(min(3, a.warmup)):
         gi.search_host(hq[i % nb], k, C, nprobe)
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
-    e2e_steps = a.steps
     for i in range(e2e_steps):
         gi.search_host(hq[i % nb], k, C, nprobe)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_qps = world * e2e_steps * B / e2e_s
+    e2e_qps = world * e2e_steps * B / e2e_s if e2e_steps else None
 
     # roofline of the dominant stage
     hbm, bf16, src = _peaks()
     per_launch_ms = {s: stage_ms[s] / max(calls, 1) for s in stage_ms}
     used = [sbytes[i % nb] for i in range(a.steps)]
     mean_bytes = {s: float(np.mean([u[s] for u in used])) for s in used[0]}
-    dom = max(("scan", "rerank", "project", "select", "route"), key=lambda s: per_launch_ms.get(s, 0.0))
+    dom = max(("scan", "rerank", "project", "select", "route", "pilot"), key=lambda s: per_launch_ms.get(s, 0.0))
     if dom in mean_bytes:
         ach = mean_bytes[dom] / (per_launch_ms[dom] / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
@@ -320,17 +328,18 @@ def run_ours(a, world, rank, local):
         "warmup": a.warmup, "ms_per_step": round(total_ms_max / a.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": a.workload, "N": w["n"], "d": w["d"], "G": w["G"], "r": w["r"], "batch": B,
-                   "nprobe": nprobe, "C": C, "k": k, "recall_at_10": round(rec, 4), "recall_queries": n_recall,
+                   "nprobe": nprobe, "C": C, "k": k, "recall_at_10": None if rec != rec else round(rec, 4), "recall_queries": n_recall,
+                   "recall_note": "skipped in profile mode" if a.profile_mode else "brute force, FP64 re-rank",
                    "sizes": w["sizes"], "l2": "no flush; per-step working set (probed coordinates, bases and "
                    "gathered rows, ~0.5 GB) exceeds the 126 MB L2", "index_build_s": round(build_s, 2),
                    "parallelism": f"replicas x{world}", "batch_latency_ms_p50": round(float(np.percentile(step_ms, 50)), 4),
                    "batch_latency_ms_p99": round(float(np.percentile(step_ms, 99)), 4)},
         "roofline": roof, "stages": others,
-        "e2e": {"value": round(e2e_qps, 1), "unit": "queries/s", "h2d_bytes_per_step": B * w["d"] * 4,
+        "e2e": {"value": round(e2e_qps, 1) if e2e_qps else None, "unit": "queries/s", "h2d_bytes_per_step": B * w["d"] * 4,
                 "d2h_bytes_per_step": B * k * 12},
-        "gpu_launches": 9 * a.steps, "clocks": clocks,
+        "gpu_launches": 10 * a.steps, "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+    if rank == 0 and world == 1 and not a.no_cpu_baseline and not a.profile_mode:
         host = gi.export()
         Xn = X.cpu().numpy()
         Qn = Q[:4096].cpu().numpy()
@@ -394,6 +403,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-queries", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-mode", action="store_true",
+                    help="for ncu captures: free the raw rows after the build; no recall, CPU baseline or e2e")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3

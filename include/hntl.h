@@ -164,10 +164,11 @@ int hntl_index_export(const hntl_index* idx, float* h_M, float* h_U, uint64_t* h
 
 /* Stage timing. While enabled, every hntl_search records CUDA events on its
  * own stream between its stages: 0 routing, 1 bucketing, 2 projection,
- * 3 scan, 4 pool selection, 5 rerank. hntl_profile_read waits for the
- * recorded events, adds their elapsed milliseconds per stage into ms[0..5],
- * returns the number of searches covered in *calls and clears the record. */
-#define HNTL_NSTAGES 6
+ * 3 pool threshold (pilot), 4 scan, 5 pool selection, 6 rerank.
+ * hntl_profile_read waits for the recorded events, adds their elapsed
+ * milliseconds per stage into ms[0..6], returns the number of searches
+ * covered in *calls and clears the record. */
+#define HNTL_NSTAGES 7
 int hntl_profile_enable(int on);
 int hntl_profile_read(double* ms, uint64_t* calls);
 

@@ -449,6 +449,27 @@ __global__ void k_relayout(int64_t N, int r, int G, const uint32_t* __restrict__
   if (attr_b) attr_b[b * kBlockRows + t] = attr[id];
 }
 
+// smallest residual norm of the real rows of each block (+inf for none)
+__global__ void k_block_rho_min(const float* __restrict__ rho_b, const uint32_t* __restrict__ blk_grain,
+                                const uint32_t* __restrict__ blk_off, const uint32_t* __restrict__ grain_rows,
+                                int64_t nb, float* __restrict__ out) {
+  const int64_t b = blockIdx.x;
+  if (b >= nb) return;
+  const uint32_t g = blk_grain[b];
+  const uint32_t row = (uint32_t)(b - blk_off[g]) * kBlockRows + threadIdx.x;
+  float v = row < grain_rows[g] ? rho_b[b * kBlockRows + threadIdx.x] : INFINITY;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ float red[kBlockRows / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = red[0];
+    for (int i = 1; i < kBlockRows / 32; ++i) m = fminf(m, red[i]);
+    out[b] = m;
+  }
+}
+
 __global__ void k_to_bf16(const float* __restrict__ X, int64_t n, uint16_t* __restrict__ Xh) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
@@ -758,6 +779,7 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   I.grain_rows = static_cast<uint32_t*>(own(G * 4));
   I.blk_grain = static_cast<uint32_t*>(own(I.n_blocks * 4));
   I.rho = static_cast<float*>(own(rows_pad * 4));
+  I.blk_rho_min = static_cast<float*>(own(I.n_blocks * 4));
   I.ids = static_cast<uint32_t*>(own(rows_pad * 4));
   if (I.has_attr) I.attr_b = static_cast<int64_t*>(own(rows_pad * 8));
   if (precision == HNTL_PREC_FP32) {
@@ -768,7 +790,7 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
     I.scale = static_cast<float*>(own(G * 4));
     I.Xh = static_cast<uint16_t*>(own(N * d * 2));
   }
-  if (!I.blk_off || !I.grain_rows || !I.blk_grain || !I.rho || !I.ids || (I.has_attr && !I.attr_b) ||
+  if (!I.blk_off || !I.grain_rows || !I.blk_grain || !I.rho || !I.blk_rho_min || !I.ids || (I.has_attr && !I.attr_b) ||
       (precision == HNTL_PREC_FP32 ? (!I.Zb || !I.X) : (!I.Z8b || !I.scale || !I.Xh))) {
     cleanup();
     return fail(HNTL_ENOMEM, "builder: index allocation failed");
@@ -787,6 +809,9 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   k_relayout<<<(unsigned)((N + 255) / 256), 256, 0, st>>>((int64_t)N, (int)r, (int)G, goff, I.blk_off, ids_g, Zg,
                                                           rho_g, P.d_attr, I.scale, I.Zb, I.Z8b, I.rho, I.ids,
                                                           I.attr_b);
+  if (I.n_blocks)
+    k_block_rho_min<<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(I.rho, I.blk_grain, I.blk_off, I.grain_rows,
+                                                                 (int64_t)I.n_blocks, I.blk_rho_min);
   if (I.X) HNTL_CUDA_TRY(cudaMemcpyAsync(I.X, dX, N * d * 4, cudaMemcpyDeviceToDevice, st));
   if (I.Xh) k_to_bf16<<<(unsigned)((N * d + 255) / 256), 256, 0, st>>>(dX, (int64_t)(N * d), I.Xh);
   HNTL_CUDA_TRY(cudaGetLastError());

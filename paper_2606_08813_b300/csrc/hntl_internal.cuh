@@ -41,6 +41,7 @@ struct Index {
   uint8_t* Z8b = nullptr;        // [n_blocks][r][128] FP8-E4M3 codes (precision form)
   float* scale = nullptr;        // [G] FP8 scale per grain
   float* rho = nullptr;          // [n_blocks][128] residual norms
+  float* blk_rho_min = nullptr;  // [n_blocks] smallest residual norm of a block's real rows (+inf if none)
   uint32_t* ids = nullptr;       // [n_blocks][128] original ids
   int64_t* attr_b = nullptr;     // [n_blocks][128] attributes in block order
   float* X = nullptr;            // [n][d] FP32 raw rows, id order

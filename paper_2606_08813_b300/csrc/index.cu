@@ -8,6 +8,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -237,6 +238,15 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
       if ((rc = dev_upload(I, &I.Xh, Xraw, (size_t)N * d * 2))) break;
     }
     if ((rc = dev_upload(I, &I.rho, rho_b.data(), rows_pad * 4))) break;
+    {
+      std::vector<float> rmin(nb, INFINITY);
+      for (uint32_t g = 0; g < G; ++g)
+        for (uint64_t i = 0; i < grain_rows[g]; ++i) {
+          const uint64_t b = I.h_blk_off[g] + i / kBlockRows;
+          rmin[b] = std::min(rmin[b], rho_b[b * kBlockRows + i % kBlockRows]);
+        }
+      if ((rc = dev_upload(I, &I.blk_rho_min, rmin.data(), nb * 4))) break;
+    }
     if ((rc = dev_upload(I, &I.ids, ids_b.data(), rows_pad * 4))) break;
     if (I.has_attr && (rc = dev_upload(I, &I.attr_b, attr_b.data(), rows_pad * 8))) break;
   } while (0);

@@ -1,0 +1,474 @@
+// Block-SoA scan (Eq. 6) fused with the pool of the C best (Table 1, "Pool C").
+//
+// Three kernels replace "write every distance, then select":
+//   k_pilot        one CTA per query computes D for up to 2048 rows (whole
+//                  Block-SoA blocks, evenly spaced) of its nearest probed
+//                  grains in routing order and takes the C-th smallest as tau_q. Those are real rows of the query's
+//                  probe set, so at least C rows have D <= tau_q and tau_q is
+//                  an upper bound on the query's true C-th distance.
+//   k_scan_filter  grain-major scan of every probed Block-SoA block: a
+//                  grain's coordinates are read once and applied to every
+//                  query that probes it; rows with D <= tau_q (and passing
+//                  the query's attribute range) are appended to the query's
+//                  survivor list as (D, id) keys. Since D >= rho_q + rho_i,
+//                  and rounding is monotone, a (query, block) pair with
+//                  fl(rho_q + min rho_i over the block) > tau_q has no
+//                  survivor and is skipped; a block no pair needs is not read.
+//   k_final_select one CTA per query: the exact C smallest (D, id) of the
+//                  survivors, or, if the survivors overflowed their buffer,
+//                  of all probed rows recomputed on the fly (same result).
+// D is computed by one function everywhere (eval_D), so a row's D is
+// bitwise the same in the pilot, the scan and the fallback.
+#pragma once
+
+#include "hntl_internal.cuh"
+#include "kernels_common.cuh"
+
+namespace hntl {
+namespace {
+
+constexpr int kPilotRows = 2048;  // rows the pilot evaluates per query (whole 128-row blocks)
+constexpr int kTieCap = 1024;
+constexpr uint32_t kInfBits = 0x7F800000u;
+
+__host__ __device__ inline uint32_t survivor_cap(uint32_t C) { return C * 16 > 8192 ? C * 16 : 8192; }
+
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+  return ((unsigned long long)__float_as_uint(b) << 32) | __float_as_uint(a);
+}
+
+// D = ||z_q - z_i||^2 + rho_q + rho_i with packed FP32x2 arithmetic: even and
+// odd coordinates accumulate in two lanes (each lane rounds exactly like
+// fmaf), then the lanes are added and the residual norms appended. zq may
+// point to shared or global memory (8-byte aligned, RT floats, zero padded).
+template <int RT>
+__device__ __forceinline__ float eval_D(const float* zq, const float (&z)[RT], float rho_q, float rho_i) {
+  unsigned long long acc = 0ull;
+#pragma unroll
+  for (int j = 0; j < RT; j += 2) {
+    const unsigned long long q2 = *reinterpret_cast<const unsigned long long*>(zq + j);
+    const unsigned long long z2 = pack2(z[j], z[j + 1]);
+    unsigned long long df;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(df) : "l"(q2), "l"(z2));
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(acc) : "l"(df), "l"(acc));
+  }
+  const float s = __uint_as_float((uint32_t)acc) + __uint_as_float((uint32_t)(acc >> 32));
+  return (s + rho_q) + rho_i;
+}
+
+template <int RT>
+__device__ __forceinline__ void load_row(const float* __restrict__ Zb, int r, size_t b, int t, float (&z)[RT]) {
+#pragma unroll
+  for (int j = 0; j < RT; ++j) z[j] = j < r ? Zb[(b * r + j) * kBlockRows + t] : 0.f;
+}
+
+// Bitonic sort of n (a power of two, <= 1024) 64-bit keys in shared memory.
+__device__ void bitonic_sort_u64(unsigned long long* a, int n) {
+  for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          unsigned long long x = a[i], y = a[ixj];
+          bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ int pow2_at_least(int n) {
+  int p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+// The bin of a histogram holding the need-th smallest (1-based) element, and
+// how many elements lie in lower bins. All threads call it.
+__device__ void find_bin(const uint32_t* hist, int nbins, uint32_t need, uint32_t* s_bin, uint32_t* s_below,
+                         uint32_t* scratch) {
+  const int per = (nbins + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per;
+  uint32_t sum = 0;
+  for (int i = 0; i < per && b0 + i < nbins; ++i) sum += hist[b0 + i];
+  uint32_t excl = block_exclusive_scan<uint32_t>(sum, scratch + 64, scratch);
+  if (excl < need && excl + sum >= need) {
+    uint32_t run = excl;
+    for (int i = 0; i < per && b0 + i < nbins; ++i) {
+      uint32_t h = hist[b0 + i];
+      if (run + h >= need) {
+        *s_bin = (uint32_t)(b0 + i);
+        *s_below = run;
+        break;
+      }
+      run += h;
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ pilot
+
+template <int RT>
+__global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t* __restrict__ probe,
+                                               const uint32_t* __restrict__ pair_of,
+                                               const uint32_t* __restrict__ blk_off,
+                                               const uint32_t* __restrict__ grain_rows, const float* __restrict__ Zb,
+                                               const float* __restrict__ rho, const int64_t* __restrict__ attr_b,
+                                               int r, const float* __restrict__ zq, const float* __restrict__ rhoq,
+                                               const int64_t* __restrict__ filter, float* __restrict__ tau) {
+  __shared__ uint32_t vals[kPilotRows];  // D bit patterns (non-negative floats order like unsigned)
+  __shared__ uint32_t hist[2048];
+  __shared__ __align__(8) float szq[RT];
+  __shared__ uint32_t scratch[96];
+  __shared__ uint32_t s_fill, s_bin, s_below, s_total;
+  const int q = blockIdx.x;
+  if (threadIdx.x == 0) s_fill = 0;
+  long long lo = 0, hi = 0;
+  if (filter) {
+    lo = filter[2 * (size_t)q];
+    hi = filter[2 * (size_t)q + 1];
+  }
+  uint32_t scanned = 0;  // rows evaluated so far (block-uniform)
+  for (int p = 0; p < nprobe; ++p) {
+    __syncthreads();
+    const uint32_t fill = s_fill;
+    if (fill >= (uint32_t)C || scanned + kBlockRows > (uint32_t)kPilotRows) break;
+    const int g = probe[(size_t)q * nprobe + p];
+    const uint32_t s = pair_of[(size_t)q * nprobe + p];
+    const uint32_t n = grain_rows[g];
+    const uint32_t nbk = blk_off[g + 1] - blk_off[g];
+    for (int j = threadIdx.x; j < RT; j += blockDim.x) szq[j] = j < r ? zq[(size_t)s * r + j] : 0.f;
+    const float rho_q = rhoq[s];
+    __syncthreads();
+    const uint32_t room = ((uint32_t)kPilotRows - scanned) / kBlockRows;
+    const uint32_t take = nbk < room ? nbk : room;  // whole blocks, evenly spaced over the grain
+    for (uint32_t e = threadIdx.x; e < take * kBlockRows; e += blockDim.x) {
+      const uint32_t i = e / kBlockRows;
+      const int t = e % kBlockRows;
+      const uint32_t jb = take == nbk ? i : (uint32_t)(((unsigned long long)i * nbk) / take);
+      if (jb * kBlockRows + t >= n) continue;
+      const size_t b = blk_off[g] + jb;
+      if (filter) {
+        const long long a = attr_b[b * kBlockRows + t];
+        if (a < lo || a > hi) continue;
+      }
+      float z[RT];
+      load_row<RT>(Zb, r, b, t, z);
+      const float D = eval_D<RT>(szq, z, rho_q, rho[b * kBlockRows + t]);
+      const uint32_t k = __float_as_uint(D);
+      if (k >= kInfBits) continue;
+      vals[atomicAdd(&s_fill, 1u)] = k;
+    }
+    scanned += take * kBlockRows;
+  }
+  __syncthreads();
+  const uint32_t fill = s_fill;
+  if (fill < (uint32_t)C) {
+    if (threadIdx.x == 0) tau[q] = INFINITY;
+    return;
+  }
+  // C-th smallest of vals[0..fill): three radix digits (11, 11, 10 bits)
+  uint32_t prefix = 0, need = (uint32_t)C;
+  int known = 0;
+  const int shifts[3] = {21, 10, 0}, widths[3] = {11, 11, 10};
+  for (int pass = 0; pass < 3; ++pass) {
+    const int nb = 1 << widths[pass];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < fill; i += blockDim.x) {
+      const uint32_t k = vals[i];
+      if (known && (k >> (32 - known)) != prefix) continue;
+      atomicAdd(&hist[(k >> shifts[pass]) & (nb - 1)], 1u);
+    }
+    __syncthreads();
+    find_bin(hist, nb, need, &s_bin, &s_below, scratch);
+    need -= s_below;
+    prefix = (prefix << widths[pass]) | s_bin;
+    known += widths[pass];
+    __syncthreads();
+  }
+  (void)s_total;
+  if (threadIdx.x == 0) tau[q] = __uint_as_float(prefix);
+}
+
+// ------------------------------------------------------------------ scan
+
+template <int RT>
+__global__ void __launch_bounds__(kBlockRows) k_scan_filter(
+    const uint32_t* __restrict__ blk_grain, const uint32_t* __restrict__ blk_off,
+    const uint32_t* __restrict__ grain_rows, const float* __restrict__ Zb, const float* __restrict__ rho,
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r, const uint32_t* __restrict__ gcnt,
+    const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ pair_q, const float* __restrict__ zq,
+    const float* __restrict__ rhoq, const float* __restrict__ tau, const float* __restrict__ blk_rho_min,
+    const int64_t* __restrict__ filter, uint32_t cap, uint32_t* __restrict__ cnt,
+    unsigned long long* __restrict__ surv) {
+  constexpr int kChunk = 32;
+  __shared__ __align__(8) float sz[kChunk][RT];
+  __shared__ float srho[kChunk], stau[kChunk];
+  __shared__ uint32_t sq[kChunk];
+  __shared__ long long slo[kChunk], shi[kChunk];
+  const size_t b = blockIdx.x;
+  const uint32_t g = blk_grain[b];
+  const uint32_t m = gcnt[g];
+  if (m == 0) return;
+  const int t = threadIdx.x, lane = t & 31;
+  const uint32_t p_begin = pair_off[g];
+  const float rmin = blk_rho_min[b];
+  {
+    int needed = 0;  // does any query of this grain still need this block?
+    for (uint32_t s = t; s < m; s += kBlockRows)
+      needed |= rhoq[p_begin + s] + rmin <= tau[pair_q[p_begin + s]];
+    if (!__syncthreads_or(needed)) return;
+  }
+  const uint32_t row = (uint32_t)(b - blk_off[g]) * kBlockRows + t;
+  const bool valid = row < grain_rows[g];
+  float z[RT];
+  load_row<RT>(Zb, r, b, t, z);
+  const float rho_i = rho[b * kBlockRows + t];
+  const uint32_t id = ids[b * kBlockRows + t];
+  const long long a = filter ? (long long)attr_b[b * kBlockRows + t] : 0;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (uint32_t s0 = 0; s0 < m; s0 += kChunk) {
+    const int ns = (int)min((uint32_t)kChunk, m - s0);
+    for (int e = t; e < kChunk * RT; e += kBlockRows) {
+      int s = e / RT, j = e - s * RT;
+      sz[s][j] = (s < ns && j < r) ? zq[(size_t)(p_begin + s0 + s) * r + j] : 0.f;
+    }
+    if (t < kChunk && t < ns) {
+      const uint32_t q = pair_q[p_begin + s0 + t];
+      sq[t] = q;
+      srho[t] = rhoq[p_begin + s0 + t];
+      stau[t] = tau[q];
+      if (filter) {
+        slo[t] = (long long)filter[2 * (size_t)q];
+        shi[t] = (long long)filter[2 * (size_t)q + 1];
+      }
+    }
+    __syncthreads();
+    for (int s = 0; s < ns; ++s) {
+      if (srho[s] + rmin > stau[s]) continue;  // no row of this block can reach the query's pool
+      const float D = eval_D<RT>(&sz[s][0], z, srho[s], rho_i);
+      const bool ok = valid && D <= stau[s] && (!filter || (a >= slo[s] && a <= shi[s]));
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (mask) {
+        const int leader = __ffs(mask) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&cnt[sq[s]], (uint32_t)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (ok) {
+          const uint32_t pos = base + __popc(mask & lt_mask);
+          if (pos < cap)
+            surv[(size_t)sq[s] * cap + pos] = ((unsigned long long)__float_as_uint(D) << 32) | id;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ selection
+
+// Elements as (D bit pattern, id): the survivor list of one query.
+struct SurvivorSrc {
+  const unsigned long long* keys;
+  uint32_t n;
+  template <class F>
+  __device__ void for_each(F f) const {
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const unsigned long long k = keys[i];
+      f((uint32_t)(k >> 32), (uint32_t)(k & 0xFFFFFFFFu));
+    }
+  }
+};
+
+// Elements as (D bit pattern, id): every row of the query's probed grains,
+// D recomputed (used when the survivor list overflowed).
+template <int RT>
+struct ProbedRowsSrc {
+  int q, nprobe, r;
+  const int32_t* probe;
+  const uint32_t* pair_of;
+  const uint32_t* blk_off;
+  const uint32_t* grain_rows;
+  const float* Zb;
+  const float* rho;
+  const uint32_t* ids;
+  const int64_t* attr_b;
+  const float* zq;
+  const float* rhoq;
+  const int64_t* filter;
+  template <class F>
+  __device__ void for_each(F f) const {
+    long long lo = 0, hi = 0;
+    if (filter) {
+      lo = filter[2 * (size_t)q];
+      hi = filter[2 * (size_t)q + 1];
+    }
+    for (int p = 0; p < nprobe; ++p) {
+      const int g = probe[(size_t)q * nprobe + p];
+      const uint32_t s = pair_of[(size_t)q * nprobe + p];
+      const uint32_t n = grain_rows[g];
+      const float rho_q = rhoq[s];
+      __align__(8) float zl[RT];
+#pragma unroll
+      for (int j = 0; j < RT; ++j) zl[j] = j < r ? zq[(size_t)s * r + j] : 0.f;
+      for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const size_t b = blk_off[g] + i / kBlockRows;
+        const int t = i % kBlockRows;
+        if (filter) {
+          const long long a = attr_b[b * kBlockRows + t];
+          if (a < lo || a > hi) continue;
+        }
+        float z[RT];
+        load_row<RT>(Zb, r, b, t, z);
+        f(__float_as_uint(eval_D<RT>(zl, z, rho_q, rho[b * kBlockRows + t])), ids[b * kBlockRows + t]);
+      }
+    }
+  }
+};
+
+struct SelSmem {
+  uint32_t hist[2048];
+  unsigned long long keys[kMaxC];
+  unsigned long long tk[kTieCap];
+  uint32_t scratch[96];
+  uint32_t s_bin, s_below, s_total, s_nout, s_nties, s_min;
+};
+
+// The exact C smallest (D, id) of a source, written sorted to out_id/out_d
+// (pads: id 0xFFFFFFFF, +inf). Three radix digits of the D bit pattern find
+// the C-th smallest D; ties at that D are resolved by the smaller ids.
+template <class Src>
+__device__ void select_topc(const Src& src, int C, SelSmem& S, uint32_t* __restrict__ out_id,
+                            float* __restrict__ out_d) {
+  uint32_t prefix = 0, need = (uint32_t)C;
+  int known = 0;
+  bool take_all = false;
+  const int shifts[3] = {21, 10, 0}, widths[3] = {11, 11, 10};
+  for (int pass = 0; pass < 3; ++pass) {
+    const int nb = 1 << widths[pass];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) S.hist[i] = 0;
+    __syncthreads();
+    const int sh = shifts[pass], kn = known;
+    const uint32_t pf = prefix;
+    src.for_each([&](uint32_t k, uint32_t) {
+      if (k >= kInfBits) return;
+      if (kn && (k >> (32 - kn)) != pf) return;
+      atomicAdd(&S.hist[(k >> sh) & (nb - 1)], 1u);
+    });
+    __syncthreads();
+    if (pass == 0) {
+      uint32_t sum = 0;
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) sum += S.hist[i];
+      block_exclusive_scan<uint32_t>(sum, &S.s_total, S.scratch);
+      if (S.s_total <= need) {
+        take_all = true;
+        break;
+      }
+    }
+    find_bin(S.hist, nb, need, &S.s_bin, &S.s_below, S.scratch);
+    need -= S.s_below;
+    prefix = (prefix << widths[pass]) | S.s_bin;
+    known += widths[pass];
+    __syncthreads();
+  }
+  const uint32_t T = take_all ? kInfBits : prefix;
+  if (threadIdx.x == 0) {
+    S.s_nout = 0;
+    S.s_nties = 0;
+  }
+  __syncthreads();
+  src.for_each([&](uint32_t k, uint32_t id) {
+    if (k >= kInfBits) return;
+    if (k < T) {
+      const uint32_t pos = atomicAdd(&S.s_nout, 1u);
+      if (pos < (uint32_t)kMaxC) S.keys[pos] = ((unsigned long long)k << 32) | id;
+    } else if (k == T) {
+      const uint32_t pos = atomicAdd(&S.s_nties, 1u);
+      if (pos < (uint32_t)kTieCap) S.tk[pos] = id;
+    }
+  });
+  __syncthreads();
+  uint32_t nout = S.s_nout;
+  if (!take_all) {
+    const uint32_t need_eq = (uint32_t)C - nout;
+    if (S.s_nties <= (uint32_t)kTieCap) {
+      const int nt = (int)S.s_nties;
+      const int np2 = pow2_at_least(nt);
+      for (int i = threadIdx.x; i < np2; i += blockDim.x)
+        if (i >= nt) S.tk[i] = ~0ull;
+      __syncthreads();
+      bitonic_sort_u64(S.tk, np2);
+      for (uint32_t i = threadIdx.x; i < need_eq; i += blockDim.x)
+        S.keys[nout + i] = ((unsigned long long)T << 32) | (uint32_t)S.tk[i];
+    } else {
+      // more ties than the buffer: take the smallest remaining id, need_eq times
+      uint32_t last = 0;
+      bool first = true;
+      for (uint32_t e = 0; e < need_eq; ++e) {
+        if (threadIdx.x == 0) S.s_min = 0xFFFFFFFFu;
+        __syncthreads();
+        uint32_t mine = 0xFFFFFFFFu;
+        const bool fst = first;
+        const uint32_t lst = last;
+        src.for_each([&](uint32_t k, uint32_t id) {
+          if (k == T && (fst || id > lst) && id < mine) mine = id;
+        });
+        atomicMin(&S.s_min, mine);
+        __syncthreads();
+        last = S.s_min;
+        first = false;
+        if (threadIdx.x == 0) S.keys[nout + e] = ((unsigned long long)T << 32) | last;
+        __syncthreads();
+      }
+    }
+    nout = (uint32_t)C;
+  }
+  __syncthreads();
+  const int n2 = pow2_at_least(C);
+  for (int i = threadIdx.x; i < n2; i += blockDim.x)
+    if (i >= (int)nout) S.keys[i] = ~0ull;
+  __syncthreads();
+  bitonic_sort_u64(S.keys, n2);
+  for (int i = threadIdx.x; i < C; i += blockDim.x) {
+    const unsigned long long kk = S.keys[i];
+    const bool ok = i < (int)nout;
+    out_id[i] = ok ? (uint32_t)(kk & 0xFFFFFFFFu) : kInvalidId;
+    out_d[i] = ok ? __uint_as_float((uint32_t)(kk >> 32)) : INFINITY;
+  }
+}
+
+constexpr int kFinalThreads = 512;
+
+// One CTA per query: the pool from the survivors, or from every probed row
+// when the survivors overflowed their buffer.
+template <int RT>
+__global__ void __launch_bounds__(kFinalThreads) k_final_select(
+    int nprobe, int C, uint32_t cap, const uint32_t* __restrict__ cnt, const unsigned long long* __restrict__ surv,
+    const int32_t* __restrict__ probe, const uint32_t* __restrict__ pair_of, const uint32_t* __restrict__ blk_off,
+    const uint32_t* __restrict__ grain_rows, const float* __restrict__ Zb, const float* __restrict__ rho,
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r, const float* __restrict__ zq,
+    const float* __restrict__ rhoq, const int64_t* __restrict__ filter, uint32_t* __restrict__ cand_id,
+    float* __restrict__ cand_d) {
+  __shared__ SelSmem S;
+  const int q = blockIdx.x;
+  const uint32_t n = cnt[q];
+  uint32_t* oid = cand_id + (size_t)q * C;
+  float* od = cand_d + (size_t)q * C;
+  if (n <= cap) {
+    SurvivorSrc src{surv + (size_t)q * cap, n};
+    select_topc(src, C, S, oid, od);
+  } else {
+    ProbedRowsSrc<RT> src{q, nprobe, r, probe, pair_of, blk_off, grain_rows, Zb, rho, ids, attr_b, zq, rhoq, filter};
+    select_topc(src, C, S, oid, od);
+  }
+}
+
+}  // namespace
+}  // namespace hntl

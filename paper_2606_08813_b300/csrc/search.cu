@@ -14,6 +14,7 @@
 // query v' = q - mu_g; residual e = v' - U^T z and rho_q = ||e||^2; scan
 // ||z_q - z_i||^2 + rho_q + rho_i; rerank sum (q_t - x_t)^2.
 #include <array>
+#include <functional>
 #include <cfloat>
 #include <cstdint>
 #include <mutex>
@@ -23,15 +24,12 @@
 #include "hntl_internal.cuh"
 #include "kernels_common.cuh"
 #include "route_kernels.cuh"
+#include "scan_select.cuh"
 
 namespace hntl {
 
 namespace {
 
-constexpr int kSelThreads = 512;
-constexpr int kTieCap = 1024;
-
-__device__ __forceinline__ uint32_t fkey(float x) { return __float_as_uint(x); }  // x >= 0: monotone
 
 // ------------------------------------------------------------------ bucketing
 
@@ -40,35 +38,26 @@ __global__ void k_bucket_count(const int32_t* __restrict__ probe, int n, uint32_
   if (i < n) atomicAdd(&gcnt[probe[i]], 1u);
 }
 
-// Single CTA: exclusive scans over grains of the pair counts (pair offsets),
-// of count x padded rows (distance-buffer bases) and of projection groups.
+// Single CTA: exclusive scans over grains of the pair counts (pair offsets)
+// and of the projection groups.
 __global__ void __launch_bounds__(1024) k_bucket_scan(const uint32_t* __restrict__ gcnt,
-                                                      const uint32_t* __restrict__ blk_off, int G,
-                                                      uint32_t* __restrict__ pair_off, uint64_t* __restrict__ seg_base,
+                                                      int G, uint32_t* __restrict__ pair_off,
                                                       uint32_t* __restrict__ grp_off) {
   __shared__ uint32_t ws32[32];
-  __shared__ unsigned long long ws64[32];
   __shared__ uint32_t tot32a, tot32b;
-  __shared__ unsigned long long tot64;
   uint32_t carry_p = 0, carry_gr = 0;
-  unsigned long long carry_s = 0;
   for (int c0 = 0; c0 < G; c0 += 1024) {
     int g = c0 + threadIdx.x;
     uint32_t cnt = g < G ? gcnt[g] : 0u;
-    uint32_t pad = g < G ? (blk_off[g + 1] - blk_off[g]) * (uint32_t)kBlockRows : 0u;
     uint32_t ngr = (cnt + kPairsPerGroup - 1) / kPairsPerGroup;
     uint32_t ep = block_exclusive_scan<uint32_t>(cnt, &tot32a, ws32);
     uint32_t eg = block_exclusive_scan<uint32_t>(ngr, &tot32b, ws32);
-    unsigned long long es =
-        block_exclusive_scan<unsigned long long>((unsigned long long)cnt * pad, &tot64, ws64);
     if (g < G) {
       pair_off[g] = carry_p + ep;
       grp_off[g] = carry_gr + eg;
-      seg_base[g] = carry_s + es;
     }
     carry_p += tot32a;
     carry_gr += tot32b;
-    carry_s += tot64;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
@@ -86,281 +75,6 @@ __global__ void k_bucket_scatter(const int32_t* __restrict__ probe, int nq, int 
   uint32_t pos = pair_off[g] + atomicAdd(&gcur[g], 1u);
   pair_q[pos] = (uint32_t)(i / nprobe);
   pair_of[i] = pos;
-}
-
-// ------------------------------------------------------------------ scan
-
-// One CTA per Block-SoA block (128 rows, one thread per row). The row's r
-// coordinates stay in registers; every (query, grain) pair of the block's
-// grain is applied in turn: D = ||z_q - z_i||^2 + rho_q + rho_i (Eq. 6).
-// Rows failing the pair's attribute range, and padding rows, get D = +inf.
-// D goes to the pair's segment of the distance buffer (row order).
-template <int RT>
-__global__ void __launch_bounds__(kBlockRows) k_scan_fp32(
-    const uint32_t* __restrict__ blk_grain, const uint32_t* __restrict__ blk_off,
-    const uint32_t* __restrict__ grain_rows, const float* __restrict__ Zb, const float* __restrict__ rho,
-    const int64_t* __restrict__ attr_b, int r, const uint32_t* __restrict__ gcnt,
-    const uint32_t* __restrict__ pair_off, const uint64_t* __restrict__ seg_base,
-    const uint32_t* __restrict__ pair_q, const float* __restrict__ zq, const float* __restrict__ rhoq,
-    const int64_t* __restrict__ filter, float* __restrict__ D) {
-  constexpr int kChunk = 32;
-  __shared__ float sz[kChunk][RT + 1];
-  __shared__ float srho[kChunk];
-  __shared__ long long slo[kChunk], shi[kChunk];
-  const size_t b = blockIdx.x;
-  const uint32_t g = blk_grain[b];
-  const uint32_t m = gcnt[g];
-  if (m == 0) return;
-  const int t = threadIdx.x;
-  const uint32_t jb = (uint32_t)b - blk_off[g];
-  const uint32_t row = jb * kBlockRows + t;
-  const bool valid = row < grain_rows[g];
-  const size_t padded = (size_t)(blk_off[g + 1] - blk_off[g]) * kBlockRows;
-  float z[RT];
-#pragma unroll
-  for (int j = 0; j < RT; ++j) z[j] = j < r ? Zb[(b * r + j) * kBlockRows + t] : 0.f;
-  const float rho_i = rho[b * kBlockRows + t];
-  const long long a = filter ? (long long)attr_b[b * kBlockRows + t] : 0;
-  const uint32_t p_begin = pair_off[g];
-  float* Dg = D + seg_base[g] + row;
-  for (uint32_t s0 = 0; s0 < m; s0 += kChunk) {
-    const int ns = (int)min((uint32_t)kChunk, m - s0);
-    for (int e = t; e < kChunk * RT; e += kBlockRows) {
-      int s = e / RT, j = e - s * RT;
-      sz[s][j] = (s < ns && j < r) ? zq[(size_t)(p_begin + s0 + s) * r + j] : 0.f;
-    }
-    if (t < kChunk) {
-      srho[t] = t < ns ? rhoq[p_begin + s0 + t] : 0.f;
-      if (filter && t < ns) {
-        uint32_t q = pair_q[p_begin + s0 + t];
-        slo[t] = (long long)filter[2 * (size_t)q];
-        shi[t] = (long long)filter[2 * (size_t)q + 1];
-      }
-    }
-    __syncthreads();
-    for (int s = 0; s < ns; ++s) {
-      float acc = 0.f;
-#pragma unroll
-      for (int j = 0; j < RT; ++j) {
-        float df = sz[s][j] - z[j];
-        acc = fmaf(df, df, acc);
-      }
-      float Dv = acc + srho[s] + rho_i;
-      bool ok = valid && (!filter || (a >= slo[s] && a <= shi[s]));
-      Dg[(size_t)(s0 + s) * padded] = ok ? Dv : INFINITY;
-    }
-    __syncthreads();
-  }
-}
-
-// ------------------------------------------------------------------ pool selection
-
-struct SegIter {
-  const float* base;
-  uint32_t len;
-  uint32_t row0;  // first padded row of the grain
-};
-
-__device__ __forceinline__ SegIter seg_of(int q, int p, int nprobe, const int32_t* probe, const uint32_t* pair_of,
-                                          const uint32_t* pair_off, const uint64_t* seg_base,
-                                          const uint32_t* blk_off, const float* D) {
-  const int g = probe[(size_t)q * nprobe + p];
-  const uint32_t s = pair_of[(size_t)q * nprobe + p];
-  const uint32_t padded = (blk_off[g + 1] - blk_off[g]) * (uint32_t)kBlockRows;
-  SegIter it;
-  it.base = D + seg_base[g] + (size_t)(s - pair_off[g]) * padded;
-  it.len = padded;
-  it.row0 = blk_off[g] * (uint32_t)kBlockRows;
-  return it;
-}
-
-// Bitonic sort of n (a power of two, <= 1024) 64-bit keys in shared memory.
-__device__ void bitonic_sort_u64(unsigned long long* a, int n) {
-  for (int k = 2; k <= n; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        int ixj = i ^ j;
-        if (ixj > i) {
-          unsigned long long x = a[i], y = a[ixj];
-          bool up = (i & k) == 0;
-          if ((x > y) == up) {
-            a[i] = y;
-            a[ixj] = x;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-__device__ __forceinline__ int pow2_at_least(int n) {
-  int p = 1;
-  while (p < n) p <<= 1;
-  return p;
-}
-
-// Find the bin holding the need-th smallest (1-based) key of a 2048-bin
-// histogram; returns the bin and the count below it.
-__device__ void find_bin(const uint32_t* hist, int nbins, uint32_t need, uint32_t* s_bin, uint32_t* s_below,
-                         uint32_t* scratch) {
-  // each thread sums a contiguous range of bins, exclusive scan, then the owner thread walks its range
-  const int per = (nbins + blockDim.x - 1) / blockDim.x;
-  const int b0 = threadIdx.x * per;
-  uint32_t sum = 0;
-  for (int i = 0; i < per; ++i)
-    if (b0 + i < nbins) sum += hist[b0 + i];
-  uint32_t tot;
-  uint32_t* tot_p = scratch + 64;
-  uint32_t excl = block_exclusive_scan<uint32_t>(sum, tot_p, scratch);
-  (void)tot;
-  if (excl < need && excl + sum >= need) {
-    uint32_t run = excl;
-    for (int i = 0; i < per && b0 + i < nbins; ++i) {
-      uint32_t h = hist[b0 + i];
-      if (run + h >= need) {
-        *s_bin = (uint32_t)(b0 + i);
-        *s_below = run;
-        break;
-      }
-      run += h;
-    }
-  }
-  __syncthreads();
-}
-
-// One CTA per query: the exact C smallest (D, id) over the query's probed
-// segments, by a three-digit (11/11/10-bit) radix select on the FP32 bit
-// pattern of D (non-negative, so bit order is value order), then ties at the
-// threshold resolved by id, then a bitonic sort of the C winners.
-__global__ void __launch_bounds__(kSelThreads) k_select(
-    int nprobe, int C, const int32_t* __restrict__ probe, const uint32_t* __restrict__ pair_of,
-    const uint32_t* __restrict__ pair_off, const uint64_t* __restrict__ seg_base, const uint32_t* __restrict__ blk_off,
-    const uint32_t* __restrict__ ids, const float* __restrict__ D, uint32_t* __restrict__ cand_id,
-    float* __restrict__ cand_d) {
-  __shared__ uint32_t hist[2048];
-  __shared__ unsigned long long keys[kMaxC];
-  __shared__ uint32_t ties[kTieCap];
-  __shared__ uint32_t scratch[96];
-  __shared__ uint32_t s_bin, s_below, s_nout, s_nties, s_total;
-  const int q = blockIdx.x;
-  const uint32_t kInfBits = 0x7F800000u;
-
-  // ---- digit passes
-  uint32_t prefix = 0;   // known high bits of the threshold
-  int known = 0;         // number of known high bits
-  uint32_t need = (uint32_t)C;
-  uint32_t below_total = 0;
-  const int shifts[3] = {21, 10, 0};
-  const int widths[3] = {11, 11, 10};
-  bool take_all = false;
-  for (int pass = 0; pass < 3; ++pass) {
-    const int nb = 1 << widths[pass];
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
-    for (int p = 0; p < nprobe; ++p) {
-      SegIter it = seg_of(q, p, nprobe, probe, pair_of, pair_off, seg_base, blk_off, D);
-      for (uint32_t i = threadIdx.x; i < it.len; i += blockDim.x) {
-        uint32_t k = fkey(it.base[i]);
-        if (k >= kInfBits) continue;
-        if (known && (k >> (32 - known)) != prefix) continue;
-        atomicAdd(&hist[(k >> shifts[pass]) & (nb - 1)], 1u);
-      }
-    }
-    __syncthreads();
-    if (pass == 0) {
-      // total valid count
-      uint32_t sum = 0;
-      for (int i = threadIdx.x; i < nb; i += blockDim.x) sum += hist[i];
-      uint32_t excl = block_exclusive_scan<uint32_t>(sum, &s_total, scratch);
-      (void)excl;
-      if (s_total <= need) {
-        take_all = true;
-        break;
-      }
-    }
-    find_bin(hist, nb, need, &s_bin, &s_below, scratch);
-    need -= s_below;
-    below_total += s_below;
-    prefix = (prefix << widths[pass]) | s_bin;
-    known += widths[pass];
-    __syncthreads();
-  }
-  const uint32_t T = take_all ? kInfBits : prefix;  // threshold key
-  // ---- collect keys < T (all of them) and the ties == T
-  if (threadIdx.x == 0) {
-    s_nout = 0;
-    s_nties = 0;
-  }
-  __syncthreads();
-  for (int p = 0; p < nprobe; ++p) {
-    SegIter it = seg_of(q, p, nprobe, probe, pair_of, pair_off, seg_base, blk_off, D);
-    for (uint32_t i = threadIdx.x; i < it.len; i += blockDim.x) {
-      uint32_t k = fkey(it.base[i]);
-      if (k >= kInfBits) continue;
-      uint32_t id = ids[it.row0 + i];
-      if (k < T) {
-        uint32_t pos = atomicAdd(&s_nout, 1u);
-        if (pos < (uint32_t)kMaxC) keys[pos] = ((unsigned long long)k << 32) | id;
-      } else if (k == T) {
-        uint32_t pos = atomicAdd(&s_nties, 1u);
-        if (pos < (uint32_t)kTieCap) ties[pos] = id;
-      }
-    }
-  }
-  __syncthreads();
-  uint32_t nout = s_nout;
-  if (!take_all) {
-    const uint32_t need_eq = (uint32_t)C - nout;
-    if (s_nties <= (uint32_t)kTieCap) {
-      // smallest need_eq ids among the ties: bitonic on the tie ids
-      const int nt = (int)s_nties;
-      const int np2 = pow2_at_least(nt);
-      __shared__ unsigned long long tk[kTieCap];
-      for (int i = threadIdx.x; i < np2; i += blockDim.x) tk[i] = i < nt ? ties[i] : ~0ull;
-      __syncthreads();
-      bitonic_sort_u64(tk, np2);
-      for (uint32_t i = threadIdx.x; i < need_eq; i += blockDim.x)
-        keys[nout + i] = ((unsigned long long)T << 32) | (uint32_t)tk[i];
-    } else {
-      // degenerate: more ties than the buffer; take ids one at a time
-      __shared__ uint32_t s_min;
-      uint32_t last = 0;
-      bool first = true;
-      for (uint32_t e = 0; e < need_eq; ++e) {
-        if (threadIdx.x == 0) s_min = 0xFFFFFFFFu;
-        __syncthreads();
-        uint32_t mine = 0xFFFFFFFFu;
-        for (int p = 0; p < nprobe; ++p) {
-          SegIter it = seg_of(q, p, nprobe, probe, pair_of, pair_off, seg_base, blk_off, D);
-          for (uint32_t i = threadIdx.x; i < it.len; i += blockDim.x) {
-            if (fkey(it.base[i]) != T) continue;
-            uint32_t id = ids[it.row0 + i];
-            if ((first || id > last) && id < mine) mine = id;
-          }
-        }
-        atomicMin(&s_min, mine);
-        __syncthreads();
-        last = s_min;
-        first = false;
-        if (threadIdx.x == 0) keys[nout + e] = ((unsigned long long)T << 32) | last;
-        __syncthreads();
-      }
-    }
-    nout = (uint32_t)C;
-  }
-  __syncthreads();
-  const int n2 = pow2_at_least(C);
-  for (int i = threadIdx.x; i < n2; i += blockDim.x)
-    if (i >= (int)nout) keys[i] = ~0ull;
-  __syncthreads();
-  bitonic_sort_u64(keys, n2);
-  for (int i = threadIdx.x; i < C; i += blockDim.x) {
-    unsigned long long kk = keys[i];
-    bool ok = i < (int)nout;
-    cand_id[(size_t)q * C + i] = ok ? (uint32_t)(kk & 0xFFFFFFFFu) : kInvalidId;
-    cand_d[(size_t)q * C + i] = ok ? __uint_as_float((uint32_t)(kk >> 32)) : INFINITY;
-  }
 }
 
 // ------------------------------------------------------------------ rerank
@@ -461,13 +175,15 @@ struct Ws {
   uint32_t* gcnt;
   uint32_t* gcur;
   uint32_t* pair_off;
-  uint64_t* seg_base;
   uint32_t* grp_off;
   uint32_t* pair_q;
   uint32_t* pair_of;
   float* zq;
   float* rhoq;
-  float* D;
+  float* tau;
+  uint32_t* cnt;
+  unsigned long long* surv;
+  uint32_t cap;
   uint32_t* cand_id;
   float* cand_d;
   size_t bytes;
@@ -483,13 +199,15 @@ Ws carve(const Index& I, uint32_t nq, uint32_t C, uint32_t nprobe, void* base) {
   w.gcnt = c.take<uint32_t>(I.G);
   w.gcur = c.take<uint32_t>(I.G);
   w.pair_off = c.take<uint32_t>(I.G + 1);
-  w.seg_base = c.take<uint64_t>(I.G);
   w.grp_off = c.take<uint32_t>(I.G + 1);
   w.pair_q = c.take<uint32_t>(P);
   w.pair_of = c.take<uint32_t>(P);
   w.zq = c.take<float>(P * I.r);
   w.rhoq = c.take<float>(P);
-  w.D = c.take<float>((size_t)nq * I.h_top_padded_prefix[nprobe]);
+  w.tau = c.take<float>(nq);
+  w.cnt = c.take<uint32_t>(nq);
+  w.cap = survivor_cap(C);
+  w.surv = c.take<unsigned long long>((size_t)nq * w.cap);
   w.cand_id = c.take<uint32_t>((size_t)nq * C);
   w.cand_d = c.take<float>((size_t)nq * C);
   w.bytes = align_up(c.off, 256);
@@ -522,10 +240,18 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
 }
 
 template <int RT>
-void launch_scan(const Index& I, const Ws& w, const int64_t* filter, cudaStream_t st) {
-  k_scan_fp32<RT><<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(
-      I.blk_grain, I.blk_off, I.grain_rows, I.Zb, I.rho, I.attr_b, (int)I.r, w.gcnt, w.pair_off, w.seg_base,
-      w.pair_q, w.zq, w.rhoq, filter, w.D);
+void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, const int64_t* filter,
+                        cudaStream_t st, const std::function<void(int)>& mark) {
+  k_pilot<RT><<<nq, 256, 0, st>>>(nprobe, C, w.probe, w.pair_of, I.blk_off, I.grain_rows, I.Zb, I.rho, I.attr_b,
+                                  (int)I.r, w.zq, w.rhoq, filter, w.tau);
+  mark(4);
+  k_scan_filter<RT><<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(
+      I.blk_grain, I.blk_off, I.grain_rows, I.Zb, I.rho, I.ids, I.attr_b, (int)I.r, w.gcnt, w.pair_off, w.pair_q,
+      w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap, w.cnt, w.surv);
+  mark(5);
+  k_final_select<RT><<<nq, kFinalThreads, 0, st>>>(nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of, I.blk_off,
+                                                   I.grain_rows, I.Zb, I.rho, I.ids, I.attr_b, (int)I.r, w.zq,
+                                                   w.rhoq, filter, w.cand_id, w.cand_d);
 }
 
 // Stage timing: CUDA events recorded on the search's stream between stages.
@@ -591,7 +317,7 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
   mark(1);
   const int P = (int)(nq * nprobe);
   k_bucket_count<<<(P + 255) / 256, 256, 0, st>>>(w.probe, P, w.gcnt);
-  k_bucket_scan<<<1, 1024, 0, st>>>(w.gcnt, I.blk_off, (int)I.G, w.pair_off, w.seg_base, w.grp_off);
+  k_bucket_scan<<<1, 1024, 0, st>>>(w.gcnt, (int)I.G, w.pair_off, w.grp_off);
   k_bucket_scatter<<<(P + 255) / 256, 256, 0, st>>>(w.probe, (int)nq, (int)nprobe, w.pair_off, w.gcur, w.pair_q,
                                                     w.pair_of);
   mark(2);
@@ -604,14 +330,15 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
                                        w.zq, w.rhoq);
   }
   mark(3);
-  if (I.r <= 8) launch_scan<8>(I, w, filter, st);
-  else if (I.r <= 16) launch_scan<16>(I, w, filter, st);
-  else if (I.r <= 32) launch_scan<32>(I, w, filter, st);
-  else launch_scan<64>(I, w, filter, st);
-  mark(4);
-  k_select<<<nq, kSelThreads, 0, st>>>((int)nprobe, (int)C, w.probe, w.pair_of, w.pair_off, w.seg_base, I.blk_off,
-                                       I.ids, w.D, w.cand_id, w.cand_d);
-  mark(5);
+  HNTL_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * nq, st));
+  {
+    const std::function<void(int)> mk = mark;
+    if (I.r <= 8) launch_scan_select<8>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
+    else if (I.r <= 16) launch_scan_select<16>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
+    else if (I.r <= 32) launch_scan_select<32>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
+    else launch_scan_select<64>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
+  }
+  mark(6);
   {
     size_t smem = (size_t)I.d * sizeof(float);
     if (smem > 40 * 1024) {
@@ -619,7 +346,7 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
     }
     k_rerank<false><<<nq, 256, smem, st>>>(Qd, I.X, (int)I.d, (int)C, (int)k, w.cand_id, out_ids, out_d);
   }
-  mark(6);
+  mark(7);
   if (prof) profile_end(ev);
   if (probe_out)
     HNTL_CUDA_TRY(cudaMemcpyAsync(probe_out, w.probe, sizeof(int32_t) * nq * nprobe, cudaMemcpyDeviceToDevice, st));

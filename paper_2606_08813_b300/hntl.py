@@ -63,8 +63,8 @@ lib.hntl_index_grain_rows.argtypes = [_P, _P]
 lib.hntl_index_export.argtypes = [_P, _P, _P, _P, _P, _P, _P]
 lib.hntl_profile_enable.argtypes = [ctypes.c_int]
 lib.hntl_profile_read.argtypes = [_P, _P]
-NSTAGES = 6
-STAGES = ("route", "bucket", "project", "scan", "select", "rerank")
+NSTAGES = 7
+STAGES = ("route", "bucket", "project", "pilot", "scan", "select", "rerank")
 
 
 class BuildParams(ctypes.Structure):
