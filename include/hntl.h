@@ -190,6 +190,7 @@ int hntl_route(const hntl_index* idx, const float* d_queries, uint32_t nq, uint3
  * loads the library until the process exits.
  *   - nq * G must not exceed 2^21 (2,097,152); larger batches return
  *     HNTL_EINVAL with a message. Route them in slices.
+ *   - FP32 indices only (HNTL_EINVAL for the precision form).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture begins.

@@ -820,7 +820,7 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
     cleanup();
     return fail(HNTL_ECUDA, std::string("builder: ") + cudaGetErrorString(e));
   }
-  return HNTL_OK;
+  return finalize_index(I);
 }
 
 }  // namespace hntl

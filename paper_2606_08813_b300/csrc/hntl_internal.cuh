@@ -1,6 +1,7 @@
 // Internal declarations of the HNTL CUDA library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -47,6 +48,13 @@ struct Index {
   float* X = nullptr;            // [n][d] FP32 raw rows, id order
   uint16_t* Xh = nullptr;        // [n][d] BF16 raw rows, id order
 
+  // derived at load/build (finalize_index)
+  float* mnorm = nullptr;        // [G] ||mu_g||^2 (of the BF16 centres in the precision form)
+  uint16_t* Mh = nullptr;        // [G][d] BF16 centres (precision form)
+  int* d_err = nullptr;          // device error word (bounded waits that gave up)
+  bool tc_route = false;         // tensor-core routing available (TMA map built)
+  CUtensorMap mapM;              // TMA map of the centres (FP32 or BF16), 256-row boxes
+
   // host copies used for workspace sizing
   std::vector<uint32_t> h_blk_off;
   std::vector<uint64_t> h_top_padded_prefix;  // prefix sums of padded grain sizes, largest first
@@ -55,6 +63,12 @@ struct Index {
 
 // Frees an index's device memory (safe to call twice).
 void release(Index& I);
+
+// Derived device state after the arrays are in place (both loader and builder call it).
+int finalize_index(Index& I);
+
+// TMA map of a row-major matrix [rows][d] (FP32 or BF16) with 128-byte K boxes.
+bool make_tma_map(CUtensorMap* map, const void* base, bool bf16, uint64_t rows, uint64_t d, uint32_t box_rows);
 
 // Thread-local error message plumbing.
 int fail(int code, const std::string& msg);

@@ -250,6 +250,7 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
     if ((rc = dev_upload(I, &I.ids, ids_b.data(), rows_pad * 4))) break;
     if (I.has_attr && (rc = dev_upload(I, &I.attr_b, attr_b.data(), rows_pad * 8))) break;
   } while (0);
+  if (rc == HNTL_OK) rc = finalize_index(I);
   if (rc != HNTL_OK) free_all(I);
   if (prev >= 0) cudaSetDevice(prev);
   return rc;

@@ -61,6 +61,8 @@ extern "C" int hntl_route_noalloc(const hntl_index* idx, const float* d_queries,
   if (!idx) return hntl::fail(HNTL_EINVAL, "null index");
   const hntl::Index& I = idx->I;
   if (nprobe < 1 || nprobe > I.G) return hntl::fail(HNTL_EINVAL, "nprobe must be in [1, G]");
+  if (I.precision != HNTL_PREC_FP32)
+    return hntl::fail(HNTL_EINVAL, "allocation-free routing serves FP32 indices only");
   if ((size_t)nq * I.G > hntl::kNoAllocRouteFloats)
     return hntl::fail(HNTL_EINVAL, "nq * G = " + std::to_string((size_t)nq * I.G) +
                                        " exceeds the allocation-free routing limit of " +

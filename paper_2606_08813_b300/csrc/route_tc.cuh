@@ -1,0 +1,270 @@
+// Centroid routing on the tensor cores (sec. 2.1 step 1, sec. 2.3 item 1).
+//
+// k_route_tc: S = Q M^T on tcgen05 (TF32 for FP32 indices, BF16 for the
+// precision form; FP32 accumulation in TMEM), operands streamed by TMA
+// through a 4-stage shared-memory ring; the epilogue writes the approximate
+// squared distance ||q||^2 + ||mu||^2 - 2 q.mu for a 128-query x 256-centre
+// tile.
+//
+// k_route_refine: the approximate distance is within
+//   m(q, g) = 2^-7 ||q|| ||mu_g|| + 2^-16 (||q||^2 + ||mu_g||^2)
+// of the exact one: each operand rounded to TF32 costs at most 2^-10
+// relative, so a product at most 2^-9 of |q_t mu_t|, summed at most
+// 2^-9 ||q|| ||mu|| by Cauchy-Schwarz and doubled in the distance; the
+// margin doubles that again to cover FP32 accumulation (d 2^-24 relative)
+// and the rounding of the norms. BF16 operands multiply exactly. With U the
+// nprobe-th smallest approx + margin, any centre whose approx - margin exceeds
+// U cannot be among the nprobe nearest, so only the others (typically nprobe
+// plus a few) get their exact direct-form distance sum (q_t - mu_t)^2, and the
+// nprobe smallest (distance, grain) are kept: the same selection as the
+// direct-form routing, at a fraction of its arithmetic.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "hntl_internal.cuh"
+#include "kernels_common.cuh"
+#include "tc_common.cuh"
+
+namespace hntl {
+namespace {
+
+constexpr int kRTM = 128, kRTN = 256, kRStages = 4;
+constexpr int kRouteTcSmem = kRStages * (kRTM + kRTN) * 128 + 1024;
+
+template <bool kBF16>
+__global__ void __launch_bounds__(128) k_route_tc(const __grid_constant__ CUtensorMap mapQ,
+                                                  const __grid_constant__ CUtensorMap mapM, int nq, int G, int d,
+                                                  const float* __restrict__ qn, const float* __restrict__ mn,
+                                                  float* __restrict__ Dt, int* __restrict__ err) {
+  constexpr int kElem = kBF16 ? 2 : 4;
+  constexpr int kKB = 128 / kElem;       // K elements per stage (one 128-byte row)
+  constexpr int kStep = kBF16 ? 16 : 8;  // K per MMA
+  constexpr uint32_t kBytesA = kRTM * 128, kBytesB = kRTN * 128;
+  constexpr uint32_t kIdesc = tc::idesc_f32acc(kBF16 ? 1u : 2u, kRTM, kRTN);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[kRStages], empty[kRStages], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, kRTN);
+  if (tid == 32) {
+    for (int s = 0; s < kRStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(&done, 1);
+    tc::mbar_fence_init();
+    s_fail = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const int q0 = blockIdx.y * kRTM, g0 = blockIdx.x * kRTN;
+  const int nkb = (d + kKB - 1) / kKB;
+  if (tid == 0) {
+    // producer: TMA loads of the query and centre tiles of each K block
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kRStages;
+      if (kb >= kRStages && !tc::mbar_wait(&empty[s], ((kb / kRStages) - 1) & 1)) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      uint8_t* sa = smem + s * (kBytesA + kBytesB);
+      tc::mbar_expect_tx(&full[s], kBytesA + kBytesB);
+      tc::tma_load_2d(&mapQ, &full[s], sa, kb * kKB, q0);
+      tc::tma_load_2d(&mapM, &full[s], sa + kBytesA, kb * kKB, g0);
+    }
+  } else if (tid == 32) {
+    // MMA issuer
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % kRStages;
+      if (!tc::mbar_wait(&full[s], (kb / kRStages) & 1)) {
+        atomicExch(&s_fail, 1);
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t sa = tc::smem_u32(smem + s * (kBytesA + kBytesB));
+#pragma unroll
+      for (int ks = 0; ks < kKB / kStep; ++ks)
+        tc::mma<kBF16>(tmem, tc::desc_sw128(sa + ks * 32), tc::desc_sw128(sa + kBytesA + ks * 32), kIdesc,
+                       (kb | ks) != 0);
+      tc::mma_commit(&empty[s]);
+    }
+    if (ok) tc::mma_commit(&done);
+  }
+  const bool waited = tc::mbar_wait(&done, 0);
+  const bool failed = __syncthreads_or(!waited || s_fail);
+  tc::fence_after_sync();
+  if (!failed) {
+    const int row = warp * 32 + lane;
+    const int q = q0 + row;
+    const float qv = q < nq ? qn[q] : 0.f;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kRTN; c0 += 32) {
+      float v[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+      if (q < nq) {
+        float* out = Dt + (size_t)q * G;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int g = g0 + c0 + j;
+          if (g < G) out[g] = (qv + mn[g]) - 2.f * v[j];
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(err, tc::kErrTimeout);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kRTN);
+}
+
+__device__ __forceinline__ uint32_t ordered_key(float x) {  // monotone map of any float (NaN -> top) to uint32
+  if (!(x == x)) return 0xFFFFFFFFu;
+  const uint32_t b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+constexpr int kRefineThreads = 256;
+constexpr int kRefineCap = 1024;
+
+// One CTA per query: margin shortlist over the approximate distances, exact
+// direct-form distances of the shortlist, the nprobe smallest (distance, g).
+// In the precision form q and the centres are BF16 values (Mh).
+template <bool kBF16>
+__global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __restrict__ Q, const float* __restrict__ M,
+                                                                 const uint16_t* __restrict__ Mh,
+                                                                 const float* __restrict__ qn,
+                                                                 const float* __restrict__ mn,
+                                                                 const float* __restrict__ Dt, int G, int d,
+                                                                 int nprobe, int32_t* __restrict__ probe,
+                                                                 float* __restrict__ probe_d) {
+  extern __shared__ float sq[];  // [d] query (BF16-rounded in the precision form)
+  __shared__ uint32_t hist[2048];
+  __shared__ unsigned long long keys[kRefineCap];
+  __shared__ uint32_t scratch[96];
+  __shared__ uint32_t s_bin, s_below, s_cnt;
+  const int q = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < d; t += blockDim.x) {
+    float v = Q[(size_t)q * d + t];
+    if (kBF16) v = __bfloat162float(__float2bfloat16_rn(v));
+    sq[t] = v;
+  }
+  const float qv = qn[q];
+  const float* Dq = Dt + (size_t)q * G;
+  auto margin = [&](int g) { return 0.0078125f * sqrtf(qv * mn[g]) + 1.52587890625e-5f * (qv + mn[g]); };
+  // U = nprobe-th smallest of approx + margin (three radix digits on ordered keys)
+  uint32_t prefix = 0, need = (uint32_t)nprobe;
+  int known = 0;
+  const int shifts[3] = {21, 10, 0}, widths[3] = {11, 11, 10};
+  for (int pass = 0; pass < 3; ++pass) {
+    const int nb = 1 << widths[pass];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+      const uint32_t k = ordered_key(Dq[g] + margin(g));
+      if (known && (k >> (32 - known)) != prefix) continue;
+      atomicAdd(&hist[(k >> shifts[pass]) & (nb - 1)], 1u);
+    }
+    __syncthreads();
+    find_bin(hist, nb, need, &s_bin, &s_below, scratch);
+    need -= s_below;
+    prefix = (prefix << widths[pass]) | s_bin;
+    known += widths[pass];
+    __syncthreads();
+  }
+  const uint32_t Ukey = prefix;
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    if (ordered_key(Dq[g] - margin(g)) <= Ukey) {
+      const uint32_t pos = atomicAdd(&s_cnt, 1u);
+      if (pos < (uint32_t)kRefineCap) keys[pos] = (unsigned long long)g;
+    }
+  }
+  __syncthreads();
+  const uint32_t cnt = s_cnt;
+  const bool all = cnt > (uint32_t)kRefineCap;  // shortlist too long: fall back to every centre
+  const int n = all ? G : (int)cnt;
+  // exact distances, one warp per candidate; results are kept in the key list
+  // (all == true: the first kRefineCap slots hold the running best, merged below)
+  auto exact = [&](int g) {
+    float acc = 0.f;
+    for (int t = lane; t < d; t += 32) {
+      float m = kBF16 ? __uint_as_float((uint32_t)Mh[(size_t)g * d + t] << 16) : M[(size_t)g * d + t];
+      float df = sq[t] - m;
+      acc = fmaf(df, df, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (!(acc == acc)) acc = INFINITY;
+    return ((unsigned long long)__float_as_uint(acc) << 32) | (uint32_t)g;
+  };
+  if (!all) {
+    for (int i = warp; i < n; i += nw) {
+      const unsigned long long k = exact((int)(keys[i] & 0xFFFFFFFFu));
+      if (lane == 0) keys[i] = k;
+    }
+    __syncthreads();
+    const int n2 = pow2_at_least(n);
+    for (int i = threadIdx.x; i < n2; i += blockDim.x)
+      if (i >= n) keys[i] = ~0ull;
+    __syncthreads();
+    bitonic_sort_u64(keys, n2);
+  } else {
+    // rare: exact distances of all G centres, nprobe rounds of a block-wide minimum above the last pick
+    __shared__ unsigned long long s_best;
+    unsigned long long last = 0;
+    for (int p = 0; p < nprobe; ++p) {
+      if (threadIdx.x == 0) s_best = ~0ull;
+      __syncthreads();
+      unsigned long long mine = ~0ull;
+      for (int g = warp; g < G; g += nw) {
+        const unsigned long long k = exact(g);
+        if ((p == 0 || k > last) && k < mine) mine = k;
+      }
+      if (lane == 0) atomicMin(&s_best, mine);
+      __syncthreads();
+      last = s_best;
+      if (threadIdx.x == 0) keys[p] = last;
+      __syncthreads();
+    }
+  }
+  for (int p = threadIdx.x; p < nprobe; p += blockDim.x) {
+    const unsigned long long k = keys[p];
+    probe[(size_t)q * nprobe + p] = (int32_t)(k & 0xFFFFFFFFu);
+    probe_d[(size_t)q * nprobe + p] = __uint_as_float((uint32_t)(k >> 32));
+  }
+}
+
+// ||row||^2 of each row (FP32), one warp per row; BF16-rounded values when kBF16.
+template <bool kBF16>
+__global__ void k_row_norms(const float* __restrict__ X, int n, int d, float* __restrict__ out) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= n) return;
+  float acc = 0.f;
+  for (int t = lane; t < d; t += 32) {
+    float v = X[(size_t)w * d + t];
+    if (kBF16) v = __bfloat162float(__float2bfloat16_rn(v));
+    acc = fmaf(v, v, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[w] = acc;
+}
+
+// BF16 copy of FP32 rows (round to nearest even).
+__global__ void k_to_bf16_rows(const float* __restrict__ X, size_t n, uint16_t* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __bfloat16_as_ushort(__float2bfloat16_rn(X[i]));
+}
+
+}  // namespace
+}  // namespace hntl

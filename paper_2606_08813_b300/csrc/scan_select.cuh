@@ -62,56 +62,6 @@ __device__ __forceinline__ void load_row(const float* __restrict__ Zb, int r, si
   for (int j = 0; j < RT; ++j) z[j] = j < r ? Zb[(b * r + j) * kBlockRows + t] : 0.f;
 }
 
-// Bitonic sort of n (a power of two, <= 1024) 64-bit keys in shared memory.
-__device__ void bitonic_sort_u64(unsigned long long* a, int n) {
-  for (int k = 2; k <= n; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        int ixj = i ^ j;
-        if (ixj > i) {
-          unsigned long long x = a[i], y = a[ixj];
-          bool up = (i & k) == 0;
-          if ((x > y) == up) {
-            a[i] = y;
-            a[ixj] = x;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-__device__ __forceinline__ int pow2_at_least(int n) {
-  int p = 1;
-  while (p < n) p <<= 1;
-  return p;
-}
-
-// The bin of a histogram holding the need-th smallest (1-based) element, and
-// how many elements lie in lower bins. All threads call it.
-__device__ void find_bin(const uint32_t* hist, int nbins, uint32_t need, uint32_t* s_bin, uint32_t* s_below,
-                         uint32_t* scratch) {
-  const int per = (nbins + blockDim.x - 1) / blockDim.x;
-  const int b0 = threadIdx.x * per;
-  uint32_t sum = 0;
-  for (int i = 0; i < per && b0 + i < nbins; ++i) sum += hist[b0 + i];
-  uint32_t excl = block_exclusive_scan<uint32_t>(sum, scratch + 64, scratch);
-  if (excl < need && excl + sum >= need) {
-    uint32_t run = excl;
-    for (int i = 0; i < per && b0 + i < nbins; ++i) {
-      uint32_t h = hist[b0 + i];
-      if (run + h >= need) {
-        *s_bin = (uint32_t)(b0 + i);
-        *s_below = run;
-        break;
-      }
-      run += h;
-    }
-  }
-  __syncthreads();
-}
-
 // ------------------------------------------------------------------ pilot
 
 template <int RT>

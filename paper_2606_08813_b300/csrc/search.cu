@@ -13,10 +13,13 @@
 // method states it: routing sum (q_t - mu_t)^2; projection of the centred
 // query v' = q - mu_g; residual e = v' - U^T z and rho_q = ||e||^2; scan
 // ||z_q - z_i||^2 + rho_q + rho_i; rerank sum (q_t - x_t)^2.
+#include <cudaTypedefs.h>
+
 #include <array>
 #include <functional>
 #include <cfloat>
 #include <cstdint>
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -25,6 +28,7 @@
 #include "kernels_common.cuh"
 #include "route_kernels.cuh"
 #include "scan_select.cuh"
+#include "route_tc.cuh"
 
 namespace hntl {
 
@@ -169,6 +173,8 @@ struct DeviceGuard {
 };
 
 struct Ws {
+  float* qn;
+  uint16_t* Qh;
   float* route_d;
   int32_t* probe;
   float* probe_d;
@@ -193,6 +199,8 @@ Ws carve(const Index& I, uint32_t nq, uint32_t C, uint32_t nprobe, void* base) {
   Carver c(base);
   Ws w;
   const size_t P = (size_t)nq * nprobe;
+  w.qn = c.take<float>(nq);
+  w.Qh = I.precision == HNTL_PREC_BF16_FP8 ? c.take<uint16_t>((size_t)nq * I.d) : nullptr;
   w.route_d = c.take<float>((size_t)nq * I.G);
   w.probe = c.take<int32_t>(P);
   w.probe_d = c.take<float>(P);
@@ -224,6 +232,42 @@ int check_params(const Index& I, uint32_t nq, uint32_t k, uint32_t& C, uint32_t 
 }
 
 int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, const Ws& w, cudaStream_t st) {
+  const bool bf16 = I.precision == HNTL_PREC_BF16_FP8;
+  if (I.tc_route) {
+    // tensor-core approximate distances, then the exact refine of a margin shortlist
+    if (bf16) {
+      k_row_norms<true><<<(nq * 32 + 255) / 256, 256, 0, st>>>(Qd, (int)nq, (int)I.d, w.qn);
+      const size_t n = (size_t)nq * I.d;
+      k_to_bf16_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Qd, n, w.Qh);
+    } else {
+      k_row_norms<false><<<(nq * 32 + 255) / 256, 256, 0, st>>>(Qd, (int)nq, (int)I.d, w.qn);
+    }
+    CUtensorMap mapQ;
+    if (!make_tma_map(&mapQ, bf16 ? (const void*)w.Qh : (const void*)Qd, bf16, nq, I.d, kRTM))
+      return fail(HNTL_ECUDA, "cannot encode the TMA map of the queries");
+    static thread_local bool attr_tc = false;
+    if (!attr_tc) {
+      HNTL_CUDA_TRY(cudaFuncSetAttribute(k_route_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRouteTcSmem));
+      HNTL_CUDA_TRY(cudaFuncSetAttribute(k_route_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRouteTcSmem));
+      attr_tc = true;
+    }
+    dim3 grid((I.G + kRTN - 1) / kRTN, (nq + kRTM - 1) / kRTM);
+    const size_t rsmem = (size_t)I.d * sizeof(float);
+    if (bf16) {
+      k_route_tc<true><<<grid, 128, kRouteTcSmem, st>>>(mapQ, I.mapM, (int)nq, (int)I.G, (int)I.d, w.qn, I.mnorm,
+                                                        w.route_d, I.d_err);
+      k_route_refine<true><<<nq, kRefineThreads, rsmem, st>>>(Qd, I.M, I.Mh, w.qn, I.mnorm, w.route_d, (int)I.G,
+                                                              (int)I.d, (int)nprobe, w.probe, w.probe_d);
+    } else {
+      k_route_tc<false><<<grid, 128, kRouteTcSmem, st>>>(mapQ, I.mapM, (int)nq, (int)I.G, (int)I.d, w.qn, I.mnorm,
+                                                         w.route_d, I.d_err);
+      k_route_refine<false><<<nq, kRefineThreads, rsmem, st>>>(Qd, I.M, I.Mh, w.qn, I.mnorm, w.route_d, (int)I.G,
+                                                               (int)I.d, (int)nprobe, w.probe, w.probe_d);
+    }
+    HNTL_CUDA_TRY(cudaGetLastError());
+    return HNTL_OK;
+  }
+  if (bf16) return fail(HNTL_EINVAL, "the precision form needs tensor-core routing (d a multiple of 8)");
   dim3 grid((I.G + kRT - 1) / kRT, (nq + kRT - 1) / kRT);
   k_route_dist<<<grid, 256, 0, st>>>(Qd, I.M, (int)nq, (int)I.G, (int)I.d, w.route_d);
   size_t smem = (size_t)kSelWarps * I.G * sizeof(float);
@@ -374,6 +418,58 @@ int route_only(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, vo
   DeviceGuard dg(I.device);
   if (!dg.ok) return fail(HNTL_ECUDA, "cannot make the index's device current");
   return launch_route(I, Qd, nq, nprobe, w, st);
+}
+
+bool make_tma_map(CUtensorMap* map, const void* base, bool bf16, uint64_t rows, uint64_t d, uint32_t box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!encode || rows == 0) return false;
+  const uint64_t elem = bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(d * elem)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / elem), box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int finalize_index(Index& I) {
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+    I.allocations.push_back(p);
+    I.device_bytes += std::max<size_t>(bytes, 16);
+    return p;
+  };
+  const bool bf16 = I.precision == HNTL_PREC_BF16_FP8;
+  I.d_err = static_cast<int*>(alloc(sizeof(int)));
+  I.mnorm = static_cast<float*>(alloc(sizeof(float) * I.G));
+  if (bf16) I.Mh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.d));
+  if (!I.d_err || !I.mnorm || (bf16 && !I.Mh)) return fail(HNTL_ENOMEM, "index: derived arrays");
+  HNTL_CUDA_TRY(cudaMemset(I.d_err, 0, sizeof(int)));
+  if (bf16) k_row_norms<true><<<(I.G * 32 + 255) / 256, 256>>>(I.M, (int)I.G, (int)I.d, I.mnorm);
+  else k_row_norms<false><<<(I.G * 32 + 255) / 256, 256>>>(I.M, (int)I.G, (int)I.d, I.mnorm);
+  if (bf16) {
+    const size_t n = (size_t)I.G * I.d;
+    k_to_bf16_rows<<<(unsigned)((n + 255) / 256), 256>>>(I.M, n, I.Mh);
+  }
+  HNTL_CUDA_TRY(cudaGetLastError());
+  HNTL_CUDA_TRY(cudaDeviceSynchronize());
+  // tensor-core routing needs 16-byte row strides and the query row in shared memory
+  const bool shape_ok = (bf16 ? I.d % 8 == 0 : I.d % 4 == 0) && I.d <= 8192;
+  I.tc_route = shape_ok && make_tma_map(&I.mapM, bf16 ? (const void*)I.Mh : (const void*)I.M, bf16, I.G, I.d, kRTN);
+  return HNTL_OK;
 }
 
 }  // namespace hntl
