@@ -183,16 +183,20 @@ def recall_at_k(found: torch.Tensor, truth: torch.Tensor) -> float:
 
 def stage_bytes(idx, rows_g, probe: np.ndarray, w: dict, batch: int):
     """Algorithmic bytes per launch of each stage for one batch, from the
-    batch's probes (grains hit at least once are read once per batch)."""
+    batch's probes (grains hit at least once are read once per batch). FP32
+    form: 4-byte coordinates, bases and rows; precision form: 1-byte FP8
+    coordinates, BF16 bases, centres and rows."""
     r, d, G = w["r"], w["d"], w["G"]
+    p8 = w.get("precision", "fp32") == "bf16-fp8"
+    cb, eb = (1, 2) if p8 else (4, 4)
     hit = np.zeros(G, dtype=bool)
     hit[np.unique(probe)] = True
     union_rows = int(rows_g[hit].sum())
     return {
-        "scan": union_rows * (4 * r + 4),               # FP32 coordinates + residual norm per row
-        "project": int(hit.sum()) * r * d * 4 + int(hit.sum()) * d * 4,  # probed bases + centres
-        "rerank": batch * w["C"] * d * 4,                # gathered raw FP32 rows
-        "route": G * d * 4 + batch * d * 4,
+        "scan": union_rows * (cb * r + 4),               # coordinates + FP32 residual norm per row
+        "project": int(hit.sum()) * (r + 1) * d * eb,    # probed bases + centres
+        "rerank": batch * w["C"] * d * eb,               # gathered raw rows
+        "route": G * d * eb + batch * d * 4,
     }
 
 
@@ -210,17 +214,20 @@ def traffic_from_profiles(kernel: str):
         return None
 
 
-def cpu_oracle_qps(idx_host, X_np, Q_np, k, C, nprobe, budget_s: float = 15.0):
+def cpu_oracle_qps(idx_host, X_np, Q_np, k, C, nprobe, budget_s: float = 15.0, precision="fp32"):
     from oracle import hntl_oracle as O
 
     O.build_c()
+    if precision == "bf16-fp8":  # exported coordinates are already the decoded FP8 values
+        X_np = O.bf16_to_f32(O.bf16_round(X_np)).reshape(X_np.shape)
     n = 16
     t = 0.0
     done = 0
     while t < budget_s and done < Q_np.shape[0]:
         m = min(n, Q_np.shape[0] - done)
         t0 = time.perf_counter()
-        O.search(idx_host, X_np, Q_np[done:done + m], k, C, nprobe)
+        O.search(idx_host, X_np, Q_np[done:done + m], k, C, nprobe,
+                 precision="bf16-fp8-decoded" if precision == "bf16-fp8" else "fp32")
         t += time.perf_counter() - t0
         done += m
         n = min(4 * n, 4096)
@@ -239,7 +246,9 @@ def run_ours(a, world, rank, local):
     B = a.batch or w.get("batch", w["nq"])
     k, C, nprobe = w["k"], w["C"], w["nprobe"]
     t0 = time.perf_counter()
-    gi = hntl.Index.build(X, w["G"], w["r"], u=synth.uniforms(w["G"], sd["kmeans"]).numpy(), seed=sd["kmeans"])
+    prec = w.get("precision", "fp32")
+    gi = hntl.Index.build(X, w["G"], w["r"], u=synth.uniforms(w["G"], sd["kmeans"]).numpy(), seed=sd["kmeans"],
+                          precision=hntl.PREC_BF16_FP8 if prec == "bf16-fp8" else hntl.PREC_FP32)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     if a.profile_mode:
@@ -326,8 +335,9 @@ def run_ours(a, world, rank, local):
     line = {
         "metric": METRIC, "value": round(qps, 1), "unit": "queries/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": round(total_ms_max / a.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": a.workload, "N": w["n"], "d": w["d"], "G": w["G"], "r": w["r"], "batch": B,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16/fp8" if prec == "bf16-fp8" else "f32",
+        "data": "synthetic",
+        "config": {"workload": a.workload, "precision": prec, "N": w["n"], "d": w["d"], "G": w["G"], "r": w["r"], "batch": B,
                    "nprobe": nprobe, "C": C, "k": k, "recall_at_10": None if rec != rec else round(rec, 4), "recall_queries": n_recall,
                    "recall_note": "skipped in profile mode" if a.profile_mode else "brute force, FP64 re-rank",
                    "sizes": w["sizes"], "l2": "no flush; per-step working set (probed coordinates, bases and "
@@ -335,7 +345,8 @@ def run_ours(a, world, rank, local):
                    "parallelism": f"replicas x{world}", "batch_latency_ms_p50": round(float(np.percentile(step_ms, 50)), 4),
                    "batch_latency_ms_p99": round(float(np.percentile(step_ms, 99)), 4)},
         "roofline": roof, "stages": others,
-        "e2e": {"value": round(e2e_qps, 1) if e2e_qps else None, "unit": "queries/s", "h2d_bytes_per_step": B * w["d"] * 4,
+        "e2e": {"value": round(e2e_qps, 1) if e2e_qps else None, "unit": "queries/s",
+                "h2d_bytes_per_step": B * w["d"] * 4,
                 "d2h_bytes_per_step": B * k * 12},
         "gpu_launches": 10 * a.steps, "clocks": clocks,
     }
@@ -343,7 +354,7 @@ def run_ours(a, world, rank, local):
         host = gi.export()
         Xn = X.cpu().numpy()
         Qn = Q[:4096].cpu().numpy()
-        q, nq_done, cores = cpu_oracle_qps(host, Xn, Qn, k, C, nprobe, budget_s=a.cpu_budget)
+        q, nq_done, cores = cpu_oracle_qps(host, Xn, Qn, k, C, nprobe, budget_s=a.cpu_budget, precision=prec)
         line["cpu_baseline"] = {"value": round(q, 2), "unit": "queries/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{nq_done} queries of the same workload against the same index "
                                           f"(FP64 oracle search, OpenMP over queries)"}
@@ -364,19 +375,24 @@ def run_reference(a, world, rank, local):
     dev = torch.device(f"cuda:{local}")
     w, sd, X, Q = make_workload(a.workload, dev, 0)
     k, C, nprobe = w["k"], w["C"], w["nprobe"]
-    gi = hntl.Index.build(X, w["G"], w["r"], u=synth.uniforms(w["G"], sd["kmeans"]).numpy(), seed=sd["kmeans"])
+    prec = w.get("precision", "fp32")
+    gi = hntl.Index.build(X, w["G"], w["r"], u=synth.uniforms(w["G"], sd["kmeans"]).numpy(), seed=sd["kmeans"],
+                          precision=hntl.PREC_BF16_FP8 if prec == "bf16-fp8" else hntl.PREC_FP32)
     host = gi.export()
     Xn = X.cpu().numpy()
+    if prec == "bf16-fp8":
+        Xn = O.bf16_to_f32(O.bf16_round(Xn)).reshape(Xn.shape)
     Qn = Q.cpu().numpy()
     del gi
+    oprec = "bf16-fp8-decoded" if prec == "bf16-fp8" else "fp32"
     O.build_c()
     per_step = a.ref_queries
     for i in range(a.warmup):
-        O.search(host, Xn, Qn[(i * per_step) % len(Qn):][:per_step], k, C, nprobe)
+        O.search(host, Xn, Qn[(i * per_step) % len(Qn):][:per_step], k, C, nprobe, precision=oprec)
     t0 = time.perf_counter()
     for i in range(a.steps):
         s = (i * per_step) % max(1, len(Qn) - per_step)
-        O.search(host, Xn, Qn[s:s + per_step], k, C, nprobe)
+        O.search(host, Xn, Qn[s:s + per_step], k, C, nprobe, precision=oprec)
     el = time.perf_counter() - t0
     qps = a.steps * per_step / el
     line = {"metric": METRIC, "value": round(qps, 2), "unit": "queries/s", "n_gpus": world, "steps": a.steps,

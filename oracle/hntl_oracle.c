@@ -284,6 +284,9 @@ int64_t or_lloyd(const float* X, int64_t n, int64_t d, int64_t G, double* M, int
  *   rho [N] residual norms; X [N x d] raw rows in original id order
  *   (FP32, or BF16 widened by the caller); attr [N] in original id order.
  *
+ * Qp (may be NULL) is the query as routed and projected (the precision form
+ * rounds it to BF16); the rerank always uses Q.
+ *
  * Per query:
  *   1. routing: ||q - mu_g||^2 for every g, the nprobe smallest by (dist, g);
  *   2. per probed grain: v' = q - mu_g, z_q = U_g v', rho_q = ||v' - U_g^T z_q||^2;
@@ -297,9 +300,9 @@ int64_t or_lloyd(const float* X, int64_t n, int64_t d, int64_t G, double* M, int
  */
 void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, const int64_t* grain_off,
                const uint32_t* ids, const float* Z, const float* rho, const float* X, const int64_t* attr,
-               const float* Q, int64_t nq, int64_t k, int64_t C, int64_t nprobe, const int64_t* ranges,
-               int32_t* probe, double* probe_d, uint32_t* cand_id, double* cand_d, int64_t* out_id,
-               double* out_d) {
+               const float* Q, const float* Qp, int64_t nq, int64_t k, int64_t C, int64_t nprobe,
+               const int64_t* ranges, int32_t* probe, double* probe_d, uint32_t* cand_id, double* cand_d,
+               int64_t* out_id, double* out_d) {
 #pragma omp parallel
   {
     pair_t* route = (pair_t*)malloc(sizeof(pair_t) * (size_t)G);
@@ -313,9 +316,10 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
 #pragma omp for schedule(dynamic, 1)
     for (int64_t qi = 0; qi < nq; ++qi) {
       const float* q = Q + qi * d;
+      const float* qp = Qp ? Qp + qi * d : q; /* query as routed and projected */
       /* 1. centroid routing */
       for (int64_t g = 0; g < G; ++g) {
-        route[g].dist = sq_diff_f32(q, M + g * d, d);
+        route[g].dist = sq_diff_f32(qp, M + g * d, d);
         route[g].key = g;
       }
       qsort(route, (size_t)G, sizeof(pair_t), pair_cmp);
@@ -330,7 +334,7 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
         int64_t g = route[p].key;
         const float* mu = M + g * d;
         const float* Ug = U + g * r * d;
-        for (int64_t t = 0; t < d; ++t) v[t] = (double)q[t] - (double)mu[t];
+        for (int64_t t = 0; t < d; ++t) v[t] = (double)qp[t] - (double)mu[t];
         for (int64_t j = 0; j < r; ++j) {
           double s = 0.0;
           for (int64_t t = 0; t < d; ++t) s += (double)Ug[j * d + t] * v[t];

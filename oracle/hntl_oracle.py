@@ -71,7 +71,7 @@ def _c():
             lib.or_means.restype = I
             lib.or_lloyd.argtypes = [P, I, I, I, P, I, P]
             lib.or_lloyd.restype = I
-            lib.or_search.argtypes = [P, P, I, I, I, P, P, P, P, P, P, P, I, I, I, I, P,
+            lib.or_search.argtypes = [P, P, I, I, I, P, P, P, P, P, P, P, P, I, I, I, I, P,
                                       P, P, P, P, P, P]
             lib.or_threads.restype = ctypes.c_int
             lib.or_set_threads.argtypes = [ctypes.c_int]
@@ -211,23 +211,39 @@ def build_index(X, G: int, r: int, u, train_idx=None, max_iter: int = 25, keep_f
 # ---------------------------------------------------------------------------
 
 
-def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=None, rho=None):
-    """Mode B search of every query (see hntl_oracle.c or_search). X is the
-    raw rows in original id order (FP32 values; pass BF16-rounded values for
-    the precision form); Z/rho override the index's coordinates (e.g. FP8
-    codes decoded and scaled)."""
+def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=None, rho=None, precision="fp32"):
+    """Mode B search of every query (see hntl_oracle.c or_search).
+
+    precision="fp32": the plain method on the stored FP32 values.
+    precision="bf16-fp8": the precision form, defined on rounded inputs: the
+    query, centres and bases are rounded to BF16 for routing and projection,
+    the scan reads the FP8 coordinates decoded and scaled (fp8_coords), and the
+    rerank compares the FP32 query with BF16-rounded rows. X is the FP32 rows
+    in original id order; Z/rho override the index's coordinates."""
     X = _f32(X)
     Q = _f32(Q)
     nq, d = Q.shape
     G, r = idx["G"], idx["r"]
     if not (1 <= nprobe <= G) or k < 1 or C < 1:
         raise ValueError("bad search parameters")
+    M = _f32(idx["M"])
+    U = _f32(idx["U"])
+    Qp = None
+    if precision in ("bf16-fp8", "bf16-fp8-decoded"):
+        # "bf16-fp8-decoded": idx["Z"] already holds decoded FP8 values and X BF16-rounded values
+        M = bf16_to_f32(bf16_round(M)).reshape(M.shape)
+        U = bf16_to_f32(bf16_round(U)).reshape(U.shape)
+        if precision == "bf16-fp8":
+            X = bf16_to_f32(bf16_round(X)).reshape(X.shape)
+            if Z is None:
+                Z = fp8_decoded(idx)
+        Qp = np.ascontiguousarray(bf16_to_f32(bf16_round(Q)).reshape(Q.shape))
+    elif precision != "fp32":
+        raise ValueError(precision)
     Zs = _f32(idx["Z"] if Z is None else Z)
     rhos = _f32(idx["rho"] if rho is None else rho)
     off = np.ascontiguousarray(idx["grain_off"], dtype=np.int64)
     ids = np.ascontiguousarray(idx["ids"], dtype=np.uint32)
-    M = _f32(idx["M"])
-    U = _f32(idx["U"])
     attr_a = None if attr is None else np.ascontiguousarray(attr, dtype=np.int64)
     rng = None if ranges is None else np.ascontiguousarray(ranges, dtype=np.int64)
     if rng is not None and attr_a is None:
@@ -238,8 +254,8 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
     cand_d = np.zeros((nq, C + 1), dtype=np.float64)
     out_id = np.zeros((nq, k), dtype=np.int64)
     out_d = np.zeros((nq, k + 1), dtype=np.float64)
-    _c().or_search(_p(M), _p(U), G, d, r, _p(off), _p(ids), _p(Zs), _p(rhos), _p(X), _p(attr_a), _p(Q), nq, k,
-                   C, nprobe, _p(rng), _p(probe), _p(probe_d), _p(cand_id), _p(cand_d), _p(out_id), _p(out_d))
+    _c().or_search(_p(M), _p(U), G, d, r, _p(off), _p(ids), _p(Zs), _p(rhos), _p(X), _p(attr_a), _p(Q), _p(Qp), nq,
+                   k, C, nprobe, _p(rng), _p(probe), _p(probe_d), _p(cand_id), _p(cand_d), _p(out_id), _p(out_d))
     return dict(probe=probe, probe_d=probe_d, cand_id=cand_id, cand_d=cand_d, out_id=out_id, out_d=out_d)
 
 
@@ -263,15 +279,24 @@ def brute_force(X, Q, k: int, attr=None, ranges=None):
 # ---------------------------------------------------------------------------
 
 
-def bf16_round(x):
-    """FP32 -> BF16 (round to nearest, ties to even), returned as the 16-bit codes."""
-    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    nan = np.isnan(np.ascontiguousarray(x, dtype=np.float32))
-    lsb = (b >> np.uint64(16)) & np.uint64(1)
-    rounded = (b + np.uint64(0x7FFF) + lsb) >> np.uint64(16)
-    out = rounded.astype(np.uint16)
-    out[nan] = 0x7FC0
-    return out
+def bf16_round(x, chunk: int = 1 << 24):
+    """FP32 -> BF16 (round to nearest, ties to even), returned as the 16-bit
+    codes: add 0x7FFF plus the lowest kept bit, keep the top 16 bits (NaN ->
+    quiet NaN). Works in chunks with 32-bit arithmetic (finite inputs cannot
+    overflow it), so large arrays need no wide temporaries."""
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    flat = a.reshape(-1)
+    out = np.empty(flat.shape, dtype=np.uint16)
+    for s in range(0, flat.size, chunk):
+        f = flat[s:s + chunk]
+        b = f.view(np.uint32)
+        lsb = (b >> np.uint32(16)) & np.uint32(1)
+        with np.errstate(over="ignore"):
+            r = (b + np.uint32(0x7FFF) + lsb) >> np.uint32(16)
+        o = r.astype(np.uint16)
+        o[np.isnan(f)] = 0x7FC0
+        out[s:s + chunk] = o
+    return out.reshape(a.shape)
 
 
 def bf16_to_f32(h):

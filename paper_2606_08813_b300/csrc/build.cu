@@ -419,7 +419,7 @@ __global__ void k_grain_absmax(const float* __restrict__ Zg, const uint32_t* __r
 }
 
 // grain-ordered rows -> 128-row Block-SoA blocks (FP32 or FP8 coordinates)
-__global__ void k_relayout(int64_t N, int r, int G, const uint32_t* __restrict__ goff,
+__global__ void k_relayout(int64_t N, int r, int rp, int G, const uint32_t* __restrict__ goff,
                            const uint32_t* __restrict__ blk_off, const uint32_t* __restrict__ ids_g,
                            const float* __restrict__ Zg, const float* __restrict__ rho_g,
                            const int64_t* __restrict__ attr, const float* __restrict__ scale, float* __restrict__ Zb,
@@ -438,9 +438,9 @@ __global__ void k_relayout(int64_t N, int r, int G, const uint32_t* __restrict__
   const size_t b = blk_off[g] + i / kBlockRows, t = i % kBlockRows;
   for (int j = 0; j < r; ++j) {
     float z = Zg[(size_t)p * r + j];
-    if (Zb) Zb[(b * r + j) * kBlockRows + t] = z;
+    if (Zb) Zb[zoff(b, j, (int)t, rp, 4)] = z;
     if (Z8b)
-      Z8b[(b * r + j) * kBlockRows + t] =
+      Z8b[zoff(b, j, (int)t, rp, 16)] =
           (uint8_t)__nv_cvt_float_to_fp8(z / scale[g], __NV_SATFINITE, __NV_E4M3);
   }
   rho_b[b * kBlockRows + t] = rho_g[p];
@@ -583,6 +583,7 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   I.G = G;
   I.r = r;
   I.precision = precision;
+  I.rp = (uint32_t)padded_r((int)r, precision == HNTL_PREC_BF16_FP8);
   I.has_attr = P.d_attr != nullptr;
   auto own = [&](size_t bytes) -> void* {
     void* p = nullptr;
@@ -748,9 +749,9 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
     HNTL_CUDA_TRY(cudaMemcpyAsync(grp_off, h_grp.data(), (G + 1) * 4, cudaMemcpyHostToDevice, st));
     size_t smem = (size_t)kPairsPerGroup * d * sizeof(float);
     if (smem > 48 * 1024)
-      HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     unsigned grid = (unsigned)std::min<uint64_t>(h_grp[G] ? h_grp[G] : 1, 148 * 32);
-    k_project<<<grid, 256, smem, st>>>(dX, M, I.U, (int)d, (int)r, (int)G, grp_off, goff, ids_g, Zg, rho_g);
+    k_project<false><<<grid, 256, smem, st>>>(dX, M, I.U, (int)d, (int)r, (int)G, grp_off, goff, ids_g, Zg, rho_g);
     HNTL_CUDA_TRY(cudaGetLastError());
   }
 
@@ -783,10 +784,10 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   I.ids = static_cast<uint32_t*>(own(rows_pad * 4));
   if (I.has_attr) I.attr_b = static_cast<int64_t*>(own(rows_pad * 8));
   if (precision == HNTL_PREC_FP32) {
-    I.Zb = static_cast<float*>(own(rows_pad * r * 4));
+    I.Zb = static_cast<float*>(own(rows_pad * I.rp * 4));
     I.X = static_cast<float*>(own(N * d * 4));
   } else {
-    I.Z8b = static_cast<uint8_t*>(own(rows_pad * r));
+    I.Z8b = static_cast<uint8_t*>(own(rows_pad * I.rp));
     I.scale = static_cast<float*>(own(G * 4));
     I.Xh = static_cast<uint16_t*>(own(N * d * 2));
   }
@@ -801,12 +802,12 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   HNTL_CUDA_TRY(cudaMemsetAsync(I.rho, 0, rows_pad * 4, st));
   k_fill_u32<<<(unsigned)((rows_pad + 255) / 256), 256, 0, st>>>(I.ids, (int64_t)rows_pad, kInvalidId);
   if (I.attr_b) HNTL_CUDA_TRY(cudaMemsetAsync(I.attr_b, 0, rows_pad * 8, st));
-  if (I.Zb) HNTL_CUDA_TRY(cudaMemsetAsync(I.Zb, 0, rows_pad * r * 4, st));
+  if (I.Zb) HNTL_CUDA_TRY(cudaMemsetAsync(I.Zb, 0, rows_pad * I.rp * 4, st));
   if (I.Z8b) {
-    HNTL_CUDA_TRY(cudaMemsetAsync(I.Z8b, 0, rows_pad * r, st));
+    HNTL_CUDA_TRY(cudaMemsetAsync(I.Z8b, 0, rows_pad * I.rp, st));
     k_grain_absmax<<<G, 256, 0, st>>>(Zg, goff, (int)r, I.scale);
   }
-  k_relayout<<<(unsigned)((N + 255) / 256), 256, 0, st>>>((int64_t)N, (int)r, (int)G, goff, I.blk_off, ids_g, Zg,
+  k_relayout<<<(unsigned)((N + 255) / 256), 256, 0, st>>>((int64_t)N, (int)r, (int)I.rp, (int)G, goff, I.blk_off, ids_g, Zg,
                                                           rho_g, P.d_attr, I.scale, I.Zb, I.Z8b, I.rho, I.ids,
                                                           I.attr_b);
   if (I.n_blocks)

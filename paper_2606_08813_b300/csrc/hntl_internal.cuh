@@ -19,15 +19,27 @@ constexpr int kMaxC = 1024;
 constexpr uint32_t kMaxG = 8192;
 constexpr uint32_t kInvalidId = 0xFFFFFFFFu;
 
-// Device-resident index. Grains are stored one after another, each padded to
-// whole 128-row blocks; inside a block the coordinates are dimension-major
-// (Z[b][j][t] is coordinate j of row t of block b), so the scan's 128 threads
-// read each coordinate with one coalesced 512-byte (FP32) or 128-byte (FP8)
-// transaction. Padding rows carry id 0xFFFFFFFF and are masked by row count.
+// Block-SoA with 16-byte lanes. Grains are stored one after another, each
+// padded to whole 128-row blocks. Inside a block the coordinates are
+// dimension-major in lanes of V = 16 bytes (4 FP32 or 16 FP8 coordinates):
+// lane c of row t of block b holds coordinates cV .. cV+V-1 at
+//   ((b * rp/V + c) * 128 + t) * V,
+// with rp = r rounded up to V (zero padding). A thread (one row) reads its row
+// with rp/V 16-byte loads and a warp's load covers 512 contiguous bytes.
+// Padding rows carry id 0xFFFFFFFF and are masked by the grain's row count.
+__host__ __device__ inline int coord_lane(bool fp8) { return fp8 ? 16 : 4; }
+__host__ __device__ inline int padded_r(int r, bool fp8) {
+  const int V = coord_lane(fp8);
+  return (r + V - 1) / V * V;
+}
+__host__ __device__ inline size_t zoff(size_t b, int j, int t, int rp, int V) {
+  return ((b * (size_t)(rp / V) + (size_t)(j / V)) * 128 + (size_t)t) * V + (size_t)(j % V);
+}
 struct Index {
   int device = 0;
   uint64_t n = 0;
   uint32_t d = 0, G = 0, r = 0, precision = HNTL_PREC_FP32;
+  uint32_t rp = 0;               // r padded to the coordinate lane (see zoff)
   bool has_attr = false;
   uint64_t n_blocks = 0;
   uint64_t max_grain_rows = 0;
@@ -38,8 +50,8 @@ struct Index {
   uint32_t* blk_off = nullptr;   // [G+1] first block of each grain
   uint32_t* grain_rows = nullptr;  // [G] rows of each grain
   uint32_t* blk_grain = nullptr;   // [n_blocks] grain of each block
-  float* Zb = nullptr;           // [n_blocks][r][128] FP32 coordinates
-  uint8_t* Z8b = nullptr;        // [n_blocks][r][128] FP8-E4M3 codes (precision form)
+  float* Zb = nullptr;           // [n_blocks][rp/4][128][4] FP32 coordinates
+  uint8_t* Z8b = nullptr;        // [n_blocks][rp/16][128][16] FP8-E4M3 codes (precision form)
   float* scale = nullptr;        // [G] FP8 scale per grain
   float* rho = nullptr;          // [n_blocks][128] residual norms
   float* blk_rho_min = nullptr;  // [n_blocks] smallest residual norm of a block's real rows (+inf if none)
@@ -51,6 +63,7 @@ struct Index {
   // derived at load/build (finalize_index)
   float* mnorm = nullptr;        // [G] ||mu_g||^2 (of the BF16 centres in the precision form)
   uint16_t* Mh = nullptr;        // [G][d] BF16 centres (precision form)
+  uint16_t* Uh = nullptr;        // [G][r][d] BF16 bases (precision form)
   int* d_err = nullptr;          // device error word (bounded waits that gave up)
   bool tc_route = false;         // tensor-core routing available (TMA map built)
   CUtensorMap mapM;              // TMA map of the centres (FP32 or BF16), 256-row boxes

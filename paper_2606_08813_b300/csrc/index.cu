@@ -173,6 +173,7 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
   I.G = G;
   I.r = r;
   I.precision = precision;
+  I.rp = (uint32_t)padded_r((int)r, precision == HNTL_PREC_BF16_FP8);
   I.has_attr = attr_raw != nullptr;
   I.h_blk_off.assign(G + 1, 0);
   std::vector<uint32_t> grain_rows(G);
@@ -196,8 +197,9 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
 
   const size_t rows_pad = nb * kBlockRows;
   std::vector<uint32_t> blk_grain(nb);
-  std::vector<float> Zb(precision == HNTL_PREC_FP32 ? rows_pad * r : 0, 0.0f);
-  std::vector<uint8_t> Z8b(precision == HNTL_PREC_BF16_FP8 ? rows_pad * r : 0, 0);
+  const int rp = (int)I.rp, V = coord_lane(precision == HNTL_PREC_BF16_FP8);
+  std::vector<float> Zb(precision == HNTL_PREC_FP32 ? rows_pad * rp : 0, 0.0f);
+  std::vector<uint8_t> Z8b(precision == HNTL_PREC_BF16_FP8 ? rows_pad * rp : 0, 0);
   std::vector<float> rho_b(rows_pad, 0.0f);
   std::vector<uint32_t> ids_b(rows_pad, kInvalidId);
   std::vector<int64_t> attr_b(I.has_attr ? rows_pad : 0, 0);
@@ -208,9 +210,9 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
       uint64_t b = I.h_blk_off[g] + i / kBlockRows, t = i % kBlockRows;
       for (uint32_t j = 0; j < r; ++j) {
         if (precision == HNTL_PREC_FP32)
-          Zb[(b * r + j) * kBlockRows + t] = Z[p * r + j];
+          Zb[zoff(b, (int)j, (int)t, rp, V)] = Z[p * r + j];
         else
-          Z8b[(b * r + j) * kBlockRows + t] = Z8[p * r + j];
+          Z8b[zoff(b, (int)j, (int)t, rp, V)] = Z8[p * r + j];
       }
       rho_b[b * kBlockRows + t] = rho[p];
       ids_b[b * kBlockRows + t] = ids[p];
@@ -230,10 +232,10 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
     if ((rc = dev_upload(I, &I.grain_rows, grain_rows.data(), (size_t)G * 4))) break;
     if ((rc = dev_upload(I, &I.blk_grain, blk_grain.data(), nb * 4))) break;
     if (precision == HNTL_PREC_FP32) {
-      if ((rc = dev_upload(I, &I.Zb, Zb.data(), rows_pad * r * 4))) break;
+      if ((rc = dev_upload(I, &I.Zb, Zb.data(), rows_pad * rp * 4))) break;
       if ((rc = dev_upload(I, &I.X, Xraw, (size_t)N * d * 4))) break;
     } else {
-      if ((rc = dev_upload(I, &I.Z8b, Z8b.data(), rows_pad * r))) break;
+      if ((rc = dev_upload(I, &I.Z8b, Z8b.data(), rows_pad * rp))) break;
       if ((rc = dev_upload(I, &I.scale, scale, (size_t)G * 4))) break;
       if ((rc = dev_upload(I, &I.Xh, Xraw, (size_t)N * d * 2))) break;
     }
@@ -340,7 +342,7 @@ namespace hntl {
 namespace {
 
 __global__ void k_export_rows(const uint32_t* __restrict__ blk_off, const uint32_t* __restrict__ grain_rows, int G,
-                              int r, const float* __restrict__ Zb, const uint8_t* __restrict__ Z8b,
+                              int r, int rp, const float* __restrict__ Zb, const uint8_t* __restrict__ Z8b,
                               const float* __restrict__ scale, const float* __restrict__ rho_b,
                               const uint32_t* __restrict__ ids_b, const uint64_t* __restrict__ goff, float* __restrict__ Z,
                               float* __restrict__ rho, uint32_t* __restrict__ ids, uint64_t N) {
@@ -358,10 +360,10 @@ __global__ void k_export_rows(const uint32_t* __restrict__ blk_off, const uint32
   for (int j = 0; j < r; ++j) {
     float v;
     if (Zb) {
-      v = Zb[(b * r + j) * kBlockRows + t];
+      v = Zb[zoff(b, j, (int)t, rp, 4)];
     } else {
       __nv_fp8_e4m3 c;
-      c.__x = Z8b[(b * r + j) * kBlockRows + t];
+      c.__x = Z8b[zoff(b, j, (int)t, rp, 16)];
       v = (float)c * scale[g];
     }
     Z[p * r + j] = v;
@@ -407,7 +409,7 @@ extern "C" int hntl_index_export(const hntl_index* idx, float* h_M, float* h_U, 
     if (rc == HNTL_OK) {
       cudaMemcpy(dgoff, goff.data(), sizeof(uint64_t) * (I.G + 1), cudaMemcpyHostToDevice);
       hntl::k_export_rows<<<(unsigned)((I.n + 255) / 256), 256>>>(
-          I.blk_off, I.grain_rows, (int)I.G, (int)I.r, I.Zb, I.Z8b, I.scale, I.rho, I.ids,
+          I.blk_off, I.grain_rows, (int)I.G, (int)I.r, (int)I.rp, I.Zb, I.Z8b, I.scale, I.rho, I.ids,
           static_cast<uint64_t*>(dgoff), static_cast<float*>(dZ), static_cast<float*>(drho),
           static_cast<uint32_t*>(dids), I.n);
       cudaError_t e = cudaDeviceSynchronize();

@@ -1,6 +1,8 @@
 // Kernels shared by the search path and the index builder.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "hntl_internal.cuh"
 
 namespace hntl {
@@ -42,8 +44,17 @@ __device__ T block_exclusive_scan(T v, T* tot, T* warp_sums) {
 // One CTA per group of up to 8 (query, grain) pairs of one grain:
 //   v' = q - mu_g (Eq. 1), z = U_g v' (Eq. 2), e = v' - U_g^T z (Eq. 3), rho_q = ||e||^2 (Eq. 4).
 // The basis rows are read once per group and applied to all its pairs.
-__global__ void __launch_bounds__(256) k_project(const float* __restrict__ Q, const float* __restrict__ M,
-                                                 const float* __restrict__ U, int d, int r, int G,
+// kBF16 (precision form): q rounded to BF16, centres and bases read as BF16
+// (Mv/Uv point to uint16 codes), arithmetic in FP32.
+template <bool kBF16>
+__device__ __forceinline__ float ld_val(const void* p, size_t i) {
+  if (kBF16) return __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p) + i) << 16);
+  return __ldg(reinterpret_cast<const float*>(p) + i);
+}
+
+template <bool kBF16>
+__global__ void __launch_bounds__(256) k_project(const float* __restrict__ Q, const void* __restrict__ Mv,
+                                                 const void* __restrict__ Uv, int d, int r, int G,
                                                  const uint32_t* __restrict__ grp_off,
                                                  const uint32_t* __restrict__ pair_off,
                                                  const uint32_t* __restrict__ pair_q, float* __restrict__ zq,
@@ -63,19 +74,24 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ Q, co
     const int g = lo;
     const uint32_t p0 = pair_off[g] + (w - grp_off[g]) * kPairsPerGroup;
     const int np = (int)min((uint32_t)kPairsPerGroup, pair_off[g + 1] - p0);
-    const float* mu = M + (size_t)g * d;
+    const size_t mu0 = (size_t)g * d;
     for (int e = threadIdx.x; e < kPairsPerGroup * d; e += blockDim.x) {
       int p = e / d, t = e - p * d;
-      sv[e] = p < np ? Q[(size_t)pair_q[p0 + p] * d + t] - mu[t] : 0.f;
+      float qv = 0.f;
+      if (p < np) {
+        qv = Q[(size_t)pair_q[p0 + p] * d + t];
+        if (kBF16) qv = __bfloat162float(__float2bfloat16_rn(qv));
+      }
+      sv[e] = p < np ? qv - ld_val<kBF16>(Mv, mu0 + t) : 0.f;
     }
     __syncthreads();
-    const float* Ug = U + (size_t)g * r * d;
+    const size_t u0 = (size_t)g * r * d;
     for (int j = warp; j < r; j += 8) {
       float acc[kPairsPerGroup];
 #pragma unroll
       for (int p = 0; p < kPairsPerGroup; ++p) acc[p] = 0.f;
       for (int t = lane; t < d; t += 32) {
-        float u = __ldg(Ug + (size_t)j * d + t);
+        float u = ld_val<kBF16>(Uv, u0 + (size_t)j * d + t);
 #pragma unroll
         for (int p = 0; p < kPairsPerGroup; ++p) acc[p] = fmaf(u, sv[p * d + t], acc[p]);
       }
@@ -96,7 +112,7 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ Q, co
 #pragma unroll
       for (int p = 0; p < kPairsPerGroup; ++p) e[p] = sv[p * d + t];
       for (int j = 0; j < r; ++j) {
-        float u = __ldg(Ug + (size_t)j * d + t);
+        float u = ld_val<kBF16>(Uv, u0 + (size_t)j * d + t);
 #pragma unroll
         for (int p = 0; p < kPairsPerGroup; ++p) e[p] = fmaf(-sz[p][j], u, e[p]);
       }

@@ -21,6 +21,9 @@
 // bitwise the same in the pilot, the scan and the fallback.
 #pragma once
 
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "hntl_internal.cuh"
 #include "kernels_common.cuh"
 
@@ -56,22 +59,67 @@ __device__ __forceinline__ float eval_D(const float* zq, const float (&z)[RT], f
   return (s + rho_q) + rho_i;
 }
 
-template <int RT>
-__device__ __forceinline__ void load_row(const float* __restrict__ Zb, int r, size_t b, int t, float (&z)[RT]) {
+// The r coordinates of row t of block b into registers (zero padded to RT):
+// FP32 values, or FP8-E4M3 codes decoded exactly (through half precision) and
+// multiplied by the grain scale in FP32.
+struct Coords {
+  const float* Zb;      // FP32 form
+  const uint8_t* Z8b;   // precision form
+  const float* scale;   // precision form, per grain
+};
+
+template <int RT, bool kFP8>
+__device__ __forceinline__ void load_row(const Coords& c, int rp, float s_g, size_t b, int t, float (&z)[RT]) {
+  if constexpr (kFP8) {
+    static_assert(RT % 16 == 0, "FP8 rows are read in lanes of 16 codes");
 #pragma unroll
-  for (int j = 0; j < RT; ++j) z[j] = j < r ? Zb[(b * r + j) * kBlockRows + t] : 0.f;
+    for (int l = 0; l < RT / 16; ++l) {
+      if (l * 16 < rp) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(c.Z8b + ((b * (rp / 16) + l) * kBlockRows + t) * 16));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const float2 a = __half22float2(
+              __half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[h] & 0xFFFFu), __NV_E4M3)));
+          const float2 e = __half22float2(
+              __half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[h] >> 16), __NV_E4M3)));
+          z[l * 16 + 4 * h + 0] = a.x * s_g;
+          z[l * 16 + 4 * h + 1] = a.y * s_g;
+          z[l * 16 + 4 * h + 2] = e.x * s_g;
+          z[l * 16 + 4 * h + 3] = e.y * s_g;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) z[l * 16 + i] = 0.f;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int l = 0; l < RT / 4; ++l) {
+      if (l * 4 < rp) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(c.Zb + ((b * (rp / 4) + l) * kBlockRows + t) * 4));
+        z[4 * l] = v.x;
+        z[4 * l + 1] = v.y;
+        z[4 * l + 2] = v.z;
+        z[4 * l + 3] = v.w;
+      } else {
+        z[4 * l] = z[4 * l + 1] = z[4 * l + 2] = z[4 * l + 3] = 0.f;
+      }
+    }
+  }
 }
 
 // ------------------------------------------------------------------ pilot
 
-template <int RT>
+template <int RT, bool kFP8>
 __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t* __restrict__ probe,
                                                const uint32_t* __restrict__ pair_of,
                                                const uint32_t* __restrict__ blk_off,
-                                               const uint32_t* __restrict__ grain_rows, const float* __restrict__ Zb,
+                                               const uint32_t* __restrict__ grain_rows, const Coords cz,
                                                const float* __restrict__ rho, const int64_t* __restrict__ attr_b,
-                                               int r, const float* __restrict__ zq, const float* __restrict__ rhoq,
-                                               const int64_t* __restrict__ filter, float* __restrict__ tau) {
+                                               int r, int rp, const float* __restrict__ zq,
+                                               const float* __restrict__ rhoq, const int64_t* __restrict__ filter,
+                                               float* __restrict__ tau) {
   __shared__ uint32_t vals[kPilotRows];  // D bit patterns (non-negative floats order like unsigned)
   __shared__ uint32_t hist[2048];
   __shared__ __align__(8) float szq[RT];
@@ -95,6 +143,7 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
     const uint32_t nbk = blk_off[g + 1] - blk_off[g];
     for (int j = threadIdx.x; j < RT; j += blockDim.x) szq[j] = j < r ? zq[(size_t)s * r + j] : 0.f;
     const float rho_q = rhoq[s];
+    const float s_g = kFP8 ? cz.scale[g] : 1.f;
     __syncthreads();
     const uint32_t room = ((uint32_t)kPilotRows - scanned) / kBlockRows;
     const uint32_t take = nbk < room ? nbk : room;  // whole blocks, evenly spaced over the grain
@@ -109,7 +158,7 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
         if (a < lo || a > hi) continue;
       }
       float z[RT];
-      load_row<RT>(Zb, r, b, t, z);
+      load_row<RT, kFP8>(cz, rp, s_g, b, t, z);
       const float D = eval_D<RT>(szq, z, rho_q, rho[b * kBlockRows + t]);
       const uint32_t k = __float_as_uint(D);
       if (k >= kInfBits) continue;
@@ -149,20 +198,24 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
 
 // ------------------------------------------------------------------ scan
 
-template <int RT>
+constexpr int kMaxNeed = 1024;  // pairs of one grain a block can list after pruning
+
+template <int RT, bool kFP8>
 __global__ void __launch_bounds__(kBlockRows) k_scan_filter(
     const uint32_t* __restrict__ blk_grain, const uint32_t* __restrict__ blk_off,
-    const uint32_t* __restrict__ grain_rows, const float* __restrict__ Zb, const float* __restrict__ rho,
-    const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r, const uint32_t* __restrict__ gcnt,
-    const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ pair_q, const float* __restrict__ zq,
-    const float* __restrict__ rhoq, const float* __restrict__ tau, const float* __restrict__ blk_rho_min,
-    const int64_t* __restrict__ filter, uint32_t cap, uint32_t* __restrict__ cnt,
-    unsigned long long* __restrict__ surv) {
+    const uint32_t* __restrict__ grain_rows, const Coords cz, const float* __restrict__ rho,
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r, int rp,
+    const uint32_t* __restrict__ gcnt, const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ pair_q,
+    const float* __restrict__ zq, const float* __restrict__ rhoq, const float* __restrict__ tau,
+    const float* __restrict__ blk_rho_min, const int64_t* __restrict__ filter, uint32_t cap,
+    uint32_t* __restrict__ cnt, unsigned long long* __restrict__ surv) {
   constexpr int kChunk = 32;
   __shared__ __align__(8) float sz[kChunk][RT];
   __shared__ float srho[kChunk], stau[kChunk];
   __shared__ uint32_t sq[kChunk];
   __shared__ long long slo[kChunk], shi[kChunk];
+  __shared__ uint32_t s_need[kMaxNeed];
+  __shared__ uint32_t s_nneed;
   const size_t b = blockIdx.x;
   const uint32_t g = blk_grain[b];
   const uint32_t m = gcnt[g];
@@ -170,30 +223,44 @@ __global__ void __launch_bounds__(kBlockRows) k_scan_filter(
   const int t = threadIdx.x, lane = t & 31;
   const uint32_t p_begin = pair_off[g];
   const float rmin = blk_rho_min[b];
-  {
-    int needed = 0;  // does any query of this grain still need this block?
-    for (uint32_t s = t; s < m; s += kBlockRows)
-      needed |= rhoq[p_begin + s] + rmin <= tau[pair_q[p_begin + s]];
-    if (!__syncthreads_or(needed)) return;
+  // the pairs of this grain that can still reach their pool from this block
+  if (t == 0) s_nneed = 0;
+  __syncthreads();
+  for (uint32_t s = t; s < m; s += kBlockRows) {
+    if (rhoq[p_begin + s] + rmin <= tau[pair_q[p_begin + s]]) {
+      const uint32_t pos = atomicAdd(&s_nneed, 1u);
+      if (pos < (uint32_t)kMaxNeed) s_need[pos] = s;
+    }
   }
+  __syncthreads();
+  const uint32_t nneed = s_nneed;
+  if (nneed == 0) return;
+  const bool listed = nneed <= (uint32_t)kMaxNeed;  // else walk every pair and test each
+  const uint32_t nwalk = listed ? nneed : m;
   const uint32_t row = (uint32_t)(b - blk_off[g]) * kBlockRows + t;
   const bool valid = row < grain_rows[g];
   float z[RT];
-  load_row<RT>(Zb, r, b, t, z);
+  load_row<RT, kFP8>(cz, rp, kFP8 ? cz.scale[g] : 1.f, b, t, z);
   const float rho_i = rho[b * kBlockRows + t];
   const uint32_t id = ids[b * kBlockRows + t];
   const long long a = filter ? (long long)attr_b[b * kBlockRows + t] : 0;
   const unsigned lt_mask = (1u << lane) - 1u;
-  for (uint32_t s0 = 0; s0 < m; s0 += kChunk) {
-    const int ns = (int)min((uint32_t)kChunk, m - s0);
+  for (uint32_t s0 = 0; s0 < nwalk; s0 += kChunk) {
+    const int ns = (int)min((uint32_t)kChunk, nwalk - s0);
     for (int e = t; e < kChunk * RT; e += kBlockRows) {
-      int s = e / RT, j = e - s * RT;
-      sz[s][j] = (s < ns && j < r) ? zq[(size_t)(p_begin + s0 + s) * r + j] : 0.f;
+      const int s = e / RT, j = e - s * RT;
+      float v = 0.f;
+      if (s < ns && j < r) {
+        const uint32_t pr = p_begin + (listed ? s_need[s0 + s] : s0 + s);
+        v = zq[(size_t)pr * r + j];
+      }
+      sz[s][j] = v;
     }
-    if (t < kChunk && t < ns) {
-      const uint32_t q = pair_q[p_begin + s0 + t];
+    if (t < ns) {
+      const uint32_t pr = p_begin + (listed ? s_need[s0 + t] : s0 + t);
+      const uint32_t q = pair_q[pr];
       sq[t] = q;
-      srho[t] = rhoq[p_begin + s0 + t];
+      srho[t] = rhoq[pr];
       stau[t] = tau[q];
       if (filter) {
         slo[t] = (long long)filter[2 * (size_t)q];
@@ -239,14 +306,14 @@ struct SurvivorSrc {
 
 // Elements as (D bit pattern, id): every row of the query's probed grains,
 // D recomputed (used when the survivor list overflowed).
-template <int RT>
+template <int RT, bool kFP8>
 struct ProbedRowsSrc {
-  int q, nprobe, r;
+  int q, nprobe, r, rp;
   const int32_t* probe;
   const uint32_t* pair_of;
   const uint32_t* blk_off;
   const uint32_t* grain_rows;
-  const float* Zb;
+  Coords cz;
   const float* rho;
   const uint32_t* ids;
   const int64_t* attr_b;
@@ -265,6 +332,7 @@ struct ProbedRowsSrc {
       const uint32_t s = pair_of[(size_t)q * nprobe + p];
       const uint32_t n = grain_rows[g];
       const float rho_q = rhoq[s];
+      const float s_g = kFP8 ? cz.scale[g] : 1.f;
       __align__(8) float zl[RT];
 #pragma unroll
       for (int j = 0; j < RT; ++j) zl[j] = j < r ? zq[(size_t)s * r + j] : 0.f;
@@ -276,7 +344,7 @@ struct ProbedRowsSrc {
           if (a < lo || a > hi) continue;
         }
         float z[RT];
-        load_row<RT>(Zb, r, b, t, z);
+        load_row<RT, kFP8>(cz, rp, s_g, b, t, z);
         f(__float_as_uint(eval_D<RT>(zl, z, rho_q, rho[b * kBlockRows + t])), ids[b * kBlockRows + t]);
       }
     }
@@ -398,14 +466,14 @@ constexpr int kFinalThreads = 512;
 
 // One CTA per query: the pool from the survivors, or from every probed row
 // when the survivors overflowed their buffer.
-template <int RT>
+template <int RT, bool kFP8>
 __global__ void __launch_bounds__(kFinalThreads) k_final_select(
     int nprobe, int C, uint32_t cap, const uint32_t* __restrict__ cnt, const unsigned long long* __restrict__ surv,
     const int32_t* __restrict__ probe, const uint32_t* __restrict__ pair_of, const uint32_t* __restrict__ blk_off,
-    const uint32_t* __restrict__ grain_rows, const float* __restrict__ Zb, const float* __restrict__ rho,
-    const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r, const float* __restrict__ zq,
-    const float* __restrict__ rhoq, const int64_t* __restrict__ filter, uint32_t* __restrict__ cand_id,
-    float* __restrict__ cand_d) {
+    const uint32_t* __restrict__ grain_rows, const Coords cz, const float* __restrict__ rho,
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r, int rp,
+    const float* __restrict__ zq, const float* __restrict__ rhoq, const int64_t* __restrict__ filter,
+    uint32_t* __restrict__ cand_id, float* __restrict__ cand_d) {
   __shared__ SelSmem S;
   const int q = blockIdx.x;
   const uint32_t n = cnt[q];
@@ -415,7 +483,8 @@ __global__ void __launch_bounds__(kFinalThreads) k_final_select(
     SurvivorSrc src{surv + (size_t)q * cap, n};
     select_topc(src, C, S, oid, od);
   } else {
-    ProbedRowsSrc<RT> src{q, nprobe, r, probe, pair_of, blk_off, grain_rows, Zb, rho, ids, attr_b, zq, rhoq, filter};
+    ProbedRowsSrc<RT, kFP8> src{q,  nprobe, r,   rp,     probe, pair_of, blk_off, grain_rows,
+                                cz, rho,    ids, attr_b, zq,    rhoq,    filter};
     select_topc(src, C, S, oid, od);
   }
 }

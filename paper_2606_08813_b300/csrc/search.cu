@@ -283,19 +283,30 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
   return HNTL_OK;
 }
 
-template <int RT>
+template <int RT, bool kFP8>
 void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, const int64_t* filter,
                         cudaStream_t st, const std::function<void(int)>& mark) {
-  k_pilot<RT><<<nq, 256, 0, st>>>(nprobe, C, w.probe, w.pair_of, I.blk_off, I.grain_rows, I.Zb, I.rho, I.attr_b,
-                                  (int)I.r, w.zq, w.rhoq, filter, w.tau);
+  const Coords cz{I.Zb, I.Z8b, I.scale};
+  k_pilot<RT, kFP8><<<nq, 256, 0, st>>>(nprobe, C, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho,
+                                        I.attr_b, (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.tau);
   mark(4);
-  k_scan_filter<RT><<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(
-      I.blk_grain, I.blk_off, I.grain_rows, I.Zb, I.rho, I.ids, I.attr_b, (int)I.r, w.gcnt, w.pair_off, w.pair_q,
+  k_scan_filter<RT, kFP8><<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(
+      I.blk_grain, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b, (int)I.r, (int)I.rp, w.gcnt, w.pair_off,
+      w.pair_q,
       w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap, w.cnt, w.surv);
   mark(5);
-  k_final_select<RT><<<nq, kFinalThreads, 0, st>>>(nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of, I.blk_off,
-                                                   I.grain_rows, I.Zb, I.rho, I.ids, I.attr_b, (int)I.r, w.zq,
-                                                   w.rhoq, filter, w.cand_id, w.cand_d);
+  k_final_select<RT, kFP8><<<nq, kFinalThreads, 0, st>>>(nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of,
+                                                         I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b,
+                                                         (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id,
+                                                         w.cand_d);
+}
+
+template <int RT>
+void launch_scan_select_p(const Index& I, const Ws& w, int nq, int nprobe, int C, const int64_t* filter,
+                          cudaStream_t st, const std::function<void(int)>& mark) {
+  // FP8 rows are read in lanes of 16 codes, so the FP8 kernels need RT >= 16
+  if (I.precision == HNTL_PREC_BF16_FP8) launch_scan_select<(RT < 16 ? 16 : RT), true>(I, w, nq, nprobe, C, filter, st, mark);
+  else launch_scan_select<RT, false>(I, w, nq, nprobe, C, filter, st, mark);
 }
 
 // Stage timing: CUDA events recorded on the search's stream between stages.
@@ -336,7 +347,6 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
   int rc = check_params(I, nq, k, C, nprobe);
   if (rc) return rc;
   if (filter && !I.has_attr) return fail(HNTL_EINVAL, "filter given but the index has no attribute column");
-  if (I.precision != HNTL_PREC_FP32) return fail(HNTL_EINVAL, "precision form search is not built yet");
   if (nq == 0) return HNTL_OK;
   if (!Qd || !ws || !out_ids || !out_d) return fail(HNTL_EINVAL, "null buffer");
   if ((cand_ids == nullptr) != (cand_d == nullptr)) return fail(HNTL_EINVAL, "pass both pool buffers or neither");
@@ -366,29 +376,40 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
                                                     w.pair_of);
   mark(2);
   {
+    const bool bf16 = I.precision == HNTL_PREC_BF16_FP8;
     size_t smem = (size_t)kPairsPerGroup * I.d * sizeof(float);
-    if (smem > 48 * 1024)
-      HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) {
+      HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
     unsigned grid = (unsigned)std::min<size_t>((size_t)P / kPairsPerGroup + I.G, 148 * 16);
-    k_project<<<grid, 256, smem, st>>>(Qd, I.M, I.U, (int)I.d, (int)I.r, (int)I.G, w.grp_off, w.pair_off, w.pair_q,
-                                       w.zq, w.rhoq);
+    if (bf16)
+      k_project<true><<<grid, 256, smem, st>>>(Qd, I.Mh, I.Uh, (int)I.d, (int)I.r, (int)I.G, w.grp_off, w.pair_off,
+                                               w.pair_q, w.zq, w.rhoq);
+    else
+      k_project<false><<<grid, 256, smem, st>>>(Qd, I.M, I.U, (int)I.d, (int)I.r, (int)I.G, w.grp_off, w.pair_off,
+                                                w.pair_q, w.zq, w.rhoq);
   }
   mark(3);
   HNTL_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * nq, st));
   {
     const std::function<void(int)> mk = mark;
-    if (I.r <= 8) launch_scan_select<8>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
-    else if (I.r <= 16) launch_scan_select<16>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
-    else if (I.r <= 32) launch_scan_select<32>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
-    else launch_scan_select<64>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
+    if (I.r <= 8) launch_scan_select_p<8>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
+    else if (I.r <= 16) launch_scan_select_p<16>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
+    else if (I.r <= 32) launch_scan_select_p<32>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
+    else launch_scan_select_p<64>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
   }
   mark(6);
   {
     size_t smem = (size_t)I.d * sizeof(float);
     if (smem > 40 * 1024) {
       HNTL_CUDA_TRY(cudaFuncSetAttribute(k_rerank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      HNTL_CUDA_TRY(cudaFuncSetAttribute(k_rerank<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    k_rerank<false><<<nq, 256, smem, st>>>(Qd, I.X, (int)I.d, (int)C, (int)k, w.cand_id, out_ids, out_d);
+    if (I.precision == HNTL_PREC_BF16_FP8)
+      k_rerank<true><<<nq, 256, smem, st>>>(Qd, I.Xh, (int)I.d, (int)C, (int)k, w.cand_id, out_ids, out_d);
+    else
+      k_rerank<false><<<nq, 256, smem, st>>>(Qd, I.X, (int)I.d, (int)C, (int)k, w.cand_id, out_ids, out_d);
   }
   mark(7);
   if (prof) profile_end(ev);
@@ -455,14 +476,18 @@ int finalize_index(Index& I) {
   const bool bf16 = I.precision == HNTL_PREC_BF16_FP8;
   I.d_err = static_cast<int*>(alloc(sizeof(int)));
   I.mnorm = static_cast<float*>(alloc(sizeof(float) * I.G));
-  if (bf16) I.Mh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.d));
-  if (!I.d_err || !I.mnorm || (bf16 && !I.Mh)) return fail(HNTL_ENOMEM, "index: derived arrays");
+  if (bf16) {
+    I.Mh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.d));
+    I.Uh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.r * I.d));
+  }
+  if (!I.d_err || !I.mnorm || (bf16 && (!I.Mh || !I.Uh))) return fail(HNTL_ENOMEM, "index: derived arrays");
   HNTL_CUDA_TRY(cudaMemset(I.d_err, 0, sizeof(int)));
   if (bf16) k_row_norms<true><<<(I.G * 32 + 255) / 256, 256>>>(I.M, (int)I.G, (int)I.d, I.mnorm);
   else k_row_norms<false><<<(I.G * 32 + 255) / 256, 256>>>(I.M, (int)I.G, (int)I.d, I.mnorm);
   if (bf16) {
-    const size_t n = (size_t)I.G * I.d;
+    const size_t n = (size_t)I.G * I.d, nu = (size_t)I.G * I.r * I.d;
     k_to_bf16_rows<<<(unsigned)((n + 255) / 256), 256>>>(I.M, n, I.Mh);
+    k_to_bf16_rows<<<(unsigned)((nu + 255) / 256), 256>>>(I.U, nu, I.Uh);
   }
   HNTL_CUDA_TRY(cudaGetLastError());
   HNTL_CUDA_TRY(cudaDeviceSynchronize());

@@ -358,3 +358,49 @@ def test_index_file_header_and_checksum_round_trip(tmp_path):
     body, tail = data[:-8], data[-8:]
     s, _ = O._wsum(body, (0, 0))
     assert s == int(np.frombuffer(tail, dtype="<u8")[0])
+
+
+# ---------------------------------------------------------------- precision form
+
+
+def _grid_index():
+    """One grain, centre 0, basis = the first two axes; every row, query and
+    coordinate lies on a grid that BF16 holds exactly and whose coordinates
+    FP8-E4M3 holds exactly after the grain scale 2/448 (|z| in {0, 1/4, 1/2, 1, 2})."""
+    rng = np.random.default_rng(9)
+    d, r, n = 8, 2, 200
+    vals = np.array([0, 0.25, 0.5, 1.0, 2.0, -0.25, -0.5, -1.0, -2.0], dtype=np.float32)
+    X = vals[rng.integers(0, len(vals), (n, d))]
+    X[0, :2] = [2.0, -2.0]  # max |z| = 2
+    U = np.zeros((1, r, d), dtype=np.float32)
+    U[0, 0, 0] = U[0, 1, 1] = 1.0
+    Z = X[:, :2].copy()
+    rho = (X[:, 2:].astype(np.float64) ** 2).sum(1).astype(np.float32)
+    idx = dict(M=np.zeros((1, d), dtype=np.float32), U=U, grain_off=np.array([0, n]),
+               ids=np.arange(n, dtype=np.uint32), Z=Z, rho=rho, G=1, r=r, d=d, N=n)
+    Q = vals[rng.integers(0, len(vals), (12, d))].astype(np.float32)
+    return idx, X, Q
+
+
+def test_precision_form_reduces_to_plain_on_representable_inputs():
+    idx, X, Q = _grid_index()
+    z8, scale = O.fp8_coords(idx)
+    np.testing.assert_allclose(O.fp8_decoded(idx), idx["Z"], rtol=1e-6, atol=0)
+    plain = O.search(idx, X, Q, 5, 40, 1)
+    prec = O.search(idx, X, Q, 5, 40, 1, precision="bf16-fp8")
+    np.testing.assert_allclose(prec["cand_d"], plain["cand_d"], rtol=1e-6)
+    np.testing.assert_allclose(prec["out_d"], plain["out_d"], rtol=1e-12)
+
+
+def test_precision_form_recall_close_to_plain():
+    m = synth.make_cluster_model(4000, 128, 8, seed=41)
+    X, _ = synth.sample_points(m, 42)
+    Q, _ = synth.sample_queries(m, 60, 43)
+    X, Q = X.numpy(), Q.numpy()
+    idx = O.build_index(X, 8, 16, synth.uniforms(8, 44).numpy())
+    bf, _, _ = O.brute_force(X, Q, 10)
+    rec = lambda res: np.mean([len(set(a.tolist()) & set(b.tolist())) / 10 for a, b in zip(res["out_id"], bf)])
+    plain = O.search(idx, X, Q, 10, 50, 2)
+    prec = O.search(idx, X, Q, 10, 50, 2, precision="bf16-fp8")
+    assert rec(prec) >= rec(plain) - 0.02
+    assert rec(prec) >= 0.95
