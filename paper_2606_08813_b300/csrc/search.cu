@@ -29,6 +29,7 @@
 #include "route_kernels.cuh"
 #include "scan_select.cuh"
 #include "route_tc.cuh"
+#include "project_tc.cuh"
 
 namespace hntl {
 
@@ -43,41 +44,49 @@ __global__ void k_bucket_count(const int32_t* __restrict__ probe, int n, uint32_
 }
 
 // Single CTA: exclusive scans over grains of the pair counts (pair offsets)
-// and of the projection groups.
+// and of the projection work items (groups of 8 pairs for the SIMT kernel,
+// of 128 pairs for the tensor-core kernel).
 __global__ void __launch_bounds__(1024) k_bucket_scan(const uint32_t* __restrict__ gcnt,
                                                       int G, uint32_t* __restrict__ pair_off,
-                                                      uint32_t* __restrict__ grp_off) {
+                                                      uint32_t* __restrict__ grp_off,
+                                                      uint32_t* __restrict__ grp2_off) {
   __shared__ uint32_t ws32[32];
-  __shared__ uint32_t tot32a, tot32b;
-  uint32_t carry_p = 0, carry_gr = 0;
+  __shared__ uint32_t tot32a, tot32b, tot32c;
+  uint32_t carry_p = 0, carry_gr = 0, carry_g2 = 0;
   for (int c0 = 0; c0 < G; c0 += 1024) {
     int g = c0 + threadIdx.x;
     uint32_t cnt = g < G ? gcnt[g] : 0u;
     uint32_t ngr = (cnt + kPairsPerGroup - 1) / kPairsPerGroup;
     uint32_t ep = block_exclusive_scan<uint32_t>(cnt, &tot32a, ws32);
     uint32_t eg = block_exclusive_scan<uint32_t>(ngr, &tot32b, ws32);
+    uint32_t e2 = block_exclusive_scan<uint32_t>((cnt + kPGroup - 1) / kPGroup, &tot32c, ws32);
     if (g < G) {
       pair_off[g] = carry_p + ep;
       grp_off[g] = carry_gr + eg;
+      grp2_off[g] = carry_g2 + e2;
     }
     carry_p += tot32a;
     carry_gr += tot32b;
+    carry_g2 += tot32c;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     pair_off[G] = carry_p;
     grp_off[G] = carry_gr;
+    grp2_off[G] = carry_g2;
   }
 }
 
 __global__ void k_bucket_scatter(const int32_t* __restrict__ probe, int nq, int nprobe,
                                  const uint32_t* __restrict__ pair_off, uint32_t* __restrict__ gcur,
-                                 uint32_t* __restrict__ pair_q, uint32_t* __restrict__ pair_of) {
+                                 uint32_t* __restrict__ pair_q, uint32_t* __restrict__ pair_p,
+                                 uint32_t* __restrict__ pair_of) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nq * nprobe) return;
   int g = probe[i];
   uint32_t pos = pair_off[g] + atomicAdd(&gcur[g], 1u);
   pair_q[pos] = (uint32_t)(i / nprobe);
+  pair_p[pos] = (uint32_t)(i % nprobe);
   pair_of[i] = pos;
 }
 
@@ -182,7 +191,9 @@ struct Ws {
   uint32_t* gcur;
   uint32_t* pair_off;
   uint32_t* grp_off;
+  uint32_t* grp2_off;
   uint32_t* pair_q;
+  uint32_t* pair_p;
   uint32_t* pair_of;
   float* zq;
   float* rhoq;
@@ -208,7 +219,9 @@ Ws carve(const Index& I, uint32_t nq, uint32_t C, uint32_t nprobe, void* base) {
   w.gcur = c.take<uint32_t>(I.G);
   w.pair_off = c.take<uint32_t>(I.G + 1);
   w.grp_off = c.take<uint32_t>(I.G + 1);
+  w.grp2_off = c.take<uint32_t>(I.G + 1);
   w.pair_q = c.take<uint32_t>(P);
+  w.pair_p = c.take<uint32_t>(P);
   w.pair_of = c.take<uint32_t>(P);
   w.zq = c.take<float>(P * I.r);
   w.rhoq = c.take<float>(P);
@@ -281,6 +294,28 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
                                                                                   (int)nprobe, w.probe, w.probe_d);
   HNTL_CUDA_TRY(cudaGetLastError());
   return HNTL_OK;
+}
+
+template <int RN>
+int launch_project_tc_n(const Index& I, uint32_t P, uint32_t nprobe, const Ws& w, cudaStream_t st) {
+  static thread_local bool attr = false;
+  if (!attr) {
+    HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project_tc<RN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       ProjTc<RN>::kSmem));
+    attr = true;
+  }
+  const unsigned grid = (unsigned)std::min<size_t>((size_t)P / kPGroup + I.G, 148 * 3);
+  k_project_tc<RN><<<grid, 128, ProjTc<RN>::kSmem, st>>>(w.Qh, I.Mh, I.Uh, I.gram, (int)I.d, (int)I.r, (int)I.G,
+                                                         (int)nprobe, w.grp2_off, w.pair_off, w.pair_q, w.pair_p,
+                                                         w.probe_d, w.zq, w.rhoq, I.d_err);
+  HNTL_CUDA_TRY(cudaGetLastError());
+  return HNTL_OK;
+}
+
+int launch_project_tc(const Index& I, uint32_t P, uint32_t nprobe, const Ws& w, cudaStream_t st) {
+  if (I.r <= 16) return launch_project_tc_n<16>(I, P, nprobe, w, st);
+  if (I.r <= 32) return launch_project_tc_n<32>(I, P, nprobe, w, st);
+  return launch_project_tc_n<64>(I, P, nprobe, w, st);
 }
 
 template <int RT, bool kFP8>
@@ -371,24 +406,19 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
   mark(1);
   const int P = (int)(nq * nprobe);
   k_bucket_count<<<(P + 255) / 256, 256, 0, st>>>(w.probe, P, w.gcnt);
-  k_bucket_scan<<<1, 1024, 0, st>>>(w.gcnt, (int)I.G, w.pair_off, w.grp_off);
+  k_bucket_scan<<<1, 1024, 0, st>>>(w.gcnt, (int)I.G, w.pair_off, w.grp_off, w.grp2_off);
   k_bucket_scatter<<<(P + 255) / 256, 256, 0, st>>>(w.probe, (int)nq, (int)nprobe, w.pair_off, w.gcur, w.pair_q,
-                                                    w.pair_of);
+                                                    w.pair_p, w.pair_of);
   mark(2);
-  {
-    const bool bf16 = I.precision == HNTL_PREC_BF16_FP8;
+  if (I.precision == HNTL_PREC_BF16_FP8) {
+    if ((rc = launch_project_tc(I, (uint32_t)P, nprobe, w, st))) return rc;
+  } else {
     size_t smem = (size_t)kPairsPerGroup * I.d * sizeof(float);
-    if (smem > 48 * 1024) {
+    if (smem > 48 * 1024)
       HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    }
     unsigned grid = (unsigned)std::min<size_t>((size_t)P / kPairsPerGroup + I.G, 148 * 16);
-    if (bf16)
-      k_project<true><<<grid, 256, smem, st>>>(Qd, I.Mh, I.Uh, (int)I.d, (int)I.r, (int)I.G, w.grp_off, w.pair_off,
-                                               w.pair_q, w.zq, w.rhoq);
-    else
-      k_project<false><<<grid, 256, smem, st>>>(Qd, I.M, I.U, (int)I.d, (int)I.r, (int)I.G, w.grp_off, w.pair_off,
-                                                w.pair_q, w.zq, w.rhoq);
+    k_project<false><<<grid, 256, smem, st>>>(Qd, I.M, I.U, (int)I.d, (int)I.r, (int)I.G, w.grp_off, w.pair_off,
+                                              w.pair_q, w.zq, w.rhoq);
   }
   mark(3);
   HNTL_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * nq, st));
@@ -479,8 +509,10 @@ int finalize_index(Index& I) {
   if (bf16) {
     I.Mh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.d));
     I.Uh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.r * I.d));
+    I.gram = static_cast<float*>(alloc(sizeof(float) * I.G * I.r * I.r));
   }
-  if (!I.d_err || !I.mnorm || (bf16 && (!I.Mh || !I.Uh))) return fail(HNTL_ENOMEM, "index: derived arrays");
+  if (!I.d_err || !I.mnorm || (bf16 && (!I.Mh || !I.Uh || !I.gram)))
+    return fail(HNTL_ENOMEM, "index: derived arrays");
   HNTL_CUDA_TRY(cudaMemset(I.d_err, 0, sizeof(int)));
   if (bf16) k_row_norms<true><<<(I.G * 32 + 255) / 256, 256>>>(I.M, (int)I.G, (int)I.d, I.mnorm);
   else k_row_norms<false><<<(I.G * 32 + 255) / 256, 256>>>(I.M, (int)I.G, (int)I.d, I.mnorm);
@@ -488,6 +520,7 @@ int finalize_index(Index& I) {
     const size_t n = (size_t)I.G * I.d, nu = (size_t)I.G * I.r * I.d;
     k_to_bf16_rows<<<(unsigned)((n + 255) / 256), 256>>>(I.M, n, I.Mh);
     k_to_bf16_rows<<<(unsigned)((nu + 255) / 256), 256>>>(I.U, nu, I.Uh);
+    k_gram<<<I.G, 256>>>(I.Uh, (int)I.d, (int)I.r, I.gram);
   }
   HNTL_CUDA_TRY(cudaGetLastError());
   HNTL_CUDA_TRY(cudaDeviceSynchronize());
