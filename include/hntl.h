@@ -200,6 +200,69 @@ int hntl_route(const hntl_index* idx, const float* d_queries, uint32_t nq, uint3
 int hntl_route_noalloc(const hntl_index* idx, const float* d_queries, uint32_t nq, uint32_t nprobe, int32_t* d_probe,
                        float* d_probe_dist, void* stream);
 
+/* Search with caller-supplied probes (e.g. from hntl_router_route): as
+ * hntl_search, but step 1 is replaced by d_probe_in (device, nq x nprobe
+ * int32 grain ids, distinct within a query; an id outside [0, G) is replaced
+ * by 0 and sets bit 2 of the device status). The routing distances the
+ * projection needs are recomputed for the given probes. Workspace as for
+ * hntl_search_workspace_bytes. */
+int hntl_search_probes(const hntl_index* idx, const float* d_queries, uint32_t nq, uint32_t k, uint32_t C,
+                       uint32_t nprobe, const int32_t* d_probe_in, const int64_t* d_filter, void* d_ws,
+                       size_t ws_bytes, int64_t* d_out_ids, float* d_out_dist, uint32_t* d_cand_ids,
+                       float* d_cand_dist, void* stream);
+
+/* Device status word of an index (blocking read): bit 0 = a bounded
+ * device-side wait gave up (kernels then skip their results), bit 1 = an
+ * invalid probe id was supplied. Returns HNTL_ETIMEOUT if bit 0 is set,
+ * else HNTL_OK; `clear` resets the word. */
+int hntl_device_status(const hntl_index* idx, int* status, int clear);
+
+/* ---- learned grain router (the paper lists learned grain partitioning as
+ * future work, sec. 4; this router is the library's own addition) ----
+ * An MLP d -> h1 -> h2 -> G with exact GELU after each hidden layer and a
+ * softmax over the G grains. Training: soft-label cross-entropy against
+ * targets T (per row, the share of the query's brute-force top-10 neighbours
+ * stored in each grain) with AdamW (decoupled weight decay, FP32 master
+ * weights). Matrix products are tcgen05 BF16 GEMMs with FP32 accumulation;
+ * the tensors rounded to BF16 are the input, the weights, both hidden
+ * activations and the three back-propagated output/hidden gradients, and
+ * nothing else. d, h1, h2, G and training batches must be multiples of 8. */
+typedef struct hntl_router hntl_router;
+
+/* Create a router on `device` with the given initial FP32 parameters (host;
+ * W1 h1 x d, b1 h1, W2 h2 x h1, b2 h2, W3 G x h2, b3 G, row-major). Device
+ * buffers are sized for batches of at most max_batch rows. */
+int hntl_router_create(int device, uint32_t d, uint32_t h1, uint32_t h2, uint32_t G, uint32_t max_batch,
+                       const float* h_W1, const float* h_b1, const float* h_W2, const float* h_b2, const float* h_W3,
+                       const float* h_b3, hntl_router** out);
+void hntl_router_free(hntl_router* router);
+
+/* Copy the FP32 master parameters / the gradients of the last step to host (NULL skips). Blocking. */
+int hntl_router_params(const hntl_router* router, float* h_W1, float* h_b1, float* h_W2, float* h_b2, float* h_W3,
+                       float* h_b3);
+int hntl_router_grads(const hntl_router* router, float* h_dW1, float* h_db1, float* h_dW2, float* h_db2,
+                      float* h_dW3, float* h_db3);
+
+/* One training step on a batch (device X: B x d FP32, T: B x G FP32 soft
+ * targets): forward, loss (added to *d_loss, device FP32, if not NULL),
+ * backward, and with update != 0 one AdamW step (lr, weight decay wd on the
+ * weight matrices, betas 0.9 / 0.999, eps 1e-8). Asynchronous on `stream`. */
+int hntl_router_step(hntl_router* router, const float* d_X, const float* d_T, uint32_t B, float lr, float wd,
+                     int update, float* d_loss, void* stream);
+
+/* Logits (device, B x G FP32) of a batch of rows. Asynchronous. */
+int hntl_router_logits(hntl_router* router, const float* d_X, uint32_t B, float* d_logits, void* stream);
+
+/* Router routing: each query's nprobe largest-logit grains; where their
+ * softmax mass is below tau the query takes its centroid routing instead
+ * (tau = 0 never falls back, tau > 1 always does). *d_nfallback (device,
+ * optional) counts those queries. Workspace: hntl_router_route_workspace_bytes. */
+size_t hntl_router_route_workspace_bytes(const hntl_router* router, const hntl_index* idx, uint32_t nq,
+                                         uint32_t nprobe);
+int hntl_router_route(hntl_router* router, const hntl_index* idx, const float* d_queries, uint32_t nq,
+                      uint32_t nprobe, float tau, void* d_ws, size_t ws_bytes, int32_t* d_probe,
+                      uint32_t* d_nfallback, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

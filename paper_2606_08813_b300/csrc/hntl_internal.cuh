@@ -81,6 +81,11 @@ void release(Index& I);
 // Derived device state after the arrays are in place (both loader and builder call it).
 int finalize_index(Index& I);
 
+// Search internals shared with the router.
+size_t workspace_bytes(const Index& I, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe);
+int route_only(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, void* ws, size_t ws_bytes,
+               int32_t* probe, float* probe_d, cudaStream_t st);
+
 // TMA map of a row-major matrix [rows][d] (FP32 or BF16) with 128-byte K boxes.
 bool make_tma_map(CUtensorMap* map, const void* base, bool bf16, uint64_t rows, uint64_t d, uint32_t box_rows);
 

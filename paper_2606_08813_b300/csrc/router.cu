@@ -1,0 +1,503 @@
+// Learned grain router: an MLP d -> h1 -> h2 -> G (exact GELU, softmax over
+// grains) trained on the GPU with BF16 matrix products (tcgen05, FP32
+// accumulation) and FP32 AdamW master weights, and used to choose each
+// query's probed grains, with centroid routing as the fallback.
+//
+// Where values are rounded to BF16 (the only roundings besides FP32
+// arithmetic):
+//   forward:  X_b, W_b for each layer; H1_b = bf16(gelu(A1)); H2_b = bf16(gelu(A2))
+//   backward: dL_b = bf16((P - T) / B); dA2_b = bf16(dH2 * gelu'(A2)); dA1_b = bf16(dH1 * gelu'(A1))
+//   gradients: dW3 = dL_b^T H2_b, dW2 = dA2_b^T H1_b, dW1 = dA1_b^T X_b; bias gradients are
+//              FP32 column sums of dL, dA2, dA1.
+// The paper names learned grain partitioning as future work (sec. 4); the
+// router itself, its labels (the grains holding a query's brute-force top 10,
+// as soft targets) and its loss are this library's additions.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "gemm_tc.cuh"
+#include "hntl_internal.cuh"
+#include "route_kernels.cuh"
+
+namespace hntl {
+
+namespace {
+
+__global__ void k_f32_to_bf16(const float* __restrict__ x, size_t n, uint16_t* __restrict__ y) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __bfloat16_as_ushort(__float2bfloat16_rn(x[i]));
+}
+
+// dst[c][r] = src[r][c] for a BF16 matrix [R][Cn], 32 x 32 tiles through shared memory.
+__global__ void k_transpose_bf16(const uint16_t* __restrict__ src, int R, int Cn, uint16_t* __restrict__ dst) {
+  __shared__ uint16_t tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < R && c < Cn) ? src[(size_t)r * Cn + c] : 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (c < Cn && r < R) dst[(size_t)c * R + r] = tile[threadIdx.x][i];
+  }
+}
+
+__device__ float block_reduce(float v, float* red, bool is_max) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = is_max ? fmaxf(v, u) : v + u;
+  }
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  float r = red[0];
+  for (int i = 1; i < nw; ++i) r = is_max ? fmaxf(r, red[i]) : r + red[i];
+  return r;
+}
+
+// One CTA per row: P = softmax(L), loss_i = -sum T log P, dL = (P - T) / B (FP32 and BF16).
+__global__ void k_softmax_ce(const float* __restrict__ L, const float* __restrict__ T, int G, int B,
+                             float* __restrict__ dL, uint16_t* __restrict__ dLb, float* __restrict__ loss) {
+  __shared__ float red[32];
+  const int i = blockIdx.x;
+  const float* l = L + (size_t)i * G;
+  const float* t = T + (size_t)i * G;
+  float m = -INFINITY;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) m = fmaxf(m, l[g]);
+  m = block_reduce(m, red, true);
+  float s = 0.f;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) s += expf(l[g] - m);
+  s = block_reduce(s, red, false);
+  const float ls = logf(s);
+  float li = 0.f;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    const float lp = l[g] - m - ls;  // log P
+    const float p = expf(lp);
+    if (t[g] > 0.f) li -= t[g] * lp;
+    const float v = (p - t[g]) / (float)B;
+    dL[(size_t)i * G + g] = v;
+    dLb[(size_t)i * G + g] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  }
+  li = block_reduce(li, red, false);
+  if (threadIdx.x == 0 && loss) atomicAdd(loss, li / (float)B);
+}
+
+// dA = dH * gelu'(A) (FP32 and BF16)
+__global__ void k_gelu_bwd(const float* __restrict__ dH, const float* __restrict__ A, size_t n,
+                           float* __restrict__ dA, uint16_t* __restrict__ dAb) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = dH[i] * gelu_grad_f(A[i]);
+  dA[i] = v;
+  dAb[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+// out[c] = sum over rows of x[r][c] (column sums, one thread per column, fixed order)
+__global__ void k_colsum(const float* __restrict__ x, int R, int Cn, float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= Cn) return;
+  float s = 0.f;
+  for (int r = 0; r < R; ++r) s += x[(size_t)r * Cn + c];
+  out[c] = s;
+}
+
+// Decoupled weight decay Adam on FP32 masters; refreshes the BF16 copy.
+__global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                        float* __restrict__ v, size_t n, float lr, float wd, float b1, float b2, float eps, float c1,
+                        float c2, uint16_t* __restrict__ pb) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float w = p[i] - lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * p[i]);
+  p[i] = w;
+  if (pb) pb[i] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+}
+
+// Per row: m = max logit, s = sum exp(l - m); writes -l (so the routing select's ascending order picks the
+// largest logits).
+__global__ void k_logit_stats(const float* __restrict__ L, int G, float* __restrict__ negl, float* __restrict__ mx,
+                              float* __restrict__ sm) {
+  __shared__ float red[32];
+  const int i = blockIdx.x;
+  const float* l = L + (size_t)i * G;
+  float m = -INFINITY;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) m = fmaxf(m, l[g]);
+  m = block_reduce(m, red, true);
+  float s = 0.f;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    s += expf(l[g] - m);
+    negl[(size_t)i * G + g] = -l[g];
+  }
+  s = block_reduce(s, red, false);
+  if (threadIdx.x == 0) {
+    mx[i] = m;
+    sm[i] = s;
+  }
+}
+
+// Keep the router's probes where their softmax mass reaches tau; otherwise take the centroid probes.
+__global__ void k_router_merge(int nq, int nprobe, const float* __restrict__ neg_top, const float* __restrict__ mx,
+                               const float* __restrict__ sm, float tau, const int32_t* __restrict__ centroid_probe,
+                               int32_t* __restrict__ probe, uint32_t* __restrict__ nfallback) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  float mass = 0.f;
+  for (int p = 0; p < nprobe; ++p) mass += expf(-neg_top[(size_t)q * nprobe + p] - mx[q]);
+  mass /= sm[q];
+  if (!(mass >= tau)) {
+    for (int p = 0; p < nprobe; ++p) probe[(size_t)q * nprobe + p] = centroid_probe[(size_t)q * nprobe + p];
+    if (nfallback) atomicAdd(nfallback, 1u);
+  }
+}
+
+}  // namespace
+
+struct Router {
+  int device = 0;
+  uint32_t d = 0, h1 = 0, h2 = 0, G = 0, max_batch = 0;
+  uint64_t step = 0;
+  // parameters: FP32 masters, gradients, Adam moments, BF16 copies
+  float* W[6] = {};
+  float* dW[6] = {};
+  float* m[6] = {};
+  float* v[6] = {};
+  size_t n[6] = {};
+  uint16_t *W1b = nullptr, *W2b = nullptr, *W3b = nullptr, *W2bT = nullptr, *W3bT = nullptr;
+  // activations for up to max_batch rows
+  uint16_t *Xb = nullptr, *XbT = nullptr, *H1b = nullptr, *H1bT = nullptr, *H2b = nullptr, *H2bT = nullptr;
+  float *A1 = nullptr, *A2 = nullptr, *L = nullptr, *dL = nullptr, *dH2 = nullptr, *dA2 = nullptr, *dH1 = nullptr,
+        *dA1 = nullptr;
+  uint16_t *dLb = nullptr, *dLbT = nullptr, *dA2b = nullptr, *dA2bT = nullptr, *dA1b = nullptr, *dA1bT = nullptr;
+  float *mx = nullptr, *sm = nullptr;
+  int* d_err = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int ralloc(Router& R, void** p, size_t bytes) {
+  if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return fail(HNTL_ENOMEM, "router allocation");
+  R.allocs.push_back(*p);
+  return HNTL_OK;
+}
+
+void rfree(Router& R) {
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(R.device);
+  for (void* p : R.allocs) cudaFree(p);
+  R.allocs.clear();
+  if (prev >= 0) cudaSetDevice(prev);
+}
+
+int gemm(const Router& R, const uint16_t* A, const uint16_t* B, int M, int N, int K, GemmEpi epi, cudaStream_t st) {
+  CUtensorMap ma, mb;
+  if (!make_tma_map(&ma, A, true, (uint64_t)M, (uint64_t)K, kGTM) ||
+      !make_tma_map(&mb, B, true, (uint64_t)N, (uint64_t)K, kGTN))
+    return fail(HNTL_ECUDA, "router: cannot encode TMA maps");
+  static thread_local bool attr = false;
+  if (!attr) {
+    HNTL_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
+    attr = true;
+  }
+  dim3 grid((N + kGTN - 1) / kGTN, (M + kGTM - 1) / kGTM);
+  k_gemm_tn<<<grid, 128, kGemmSmem, st>>>(ma, mb, M, N, K, epi, R.d_err);
+  HNTL_CUDA_TRY(cudaGetLastError());
+  return HNTL_OK;
+}
+
+void transpose(const uint16_t* src, int rows, int cols, uint16_t* dst, cudaStream_t st) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+  k_transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, dst);
+}
+
+void to_bf16(const float* x, size_t n, uint16_t* y, cudaStream_t st) {
+  k_f32_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, n, y);
+}
+
+void refresh_bf16(Router& R, cudaStream_t st) {
+  to_bf16(R.W[0], R.n[0], R.W1b, st);
+  to_bf16(R.W[2], R.n[2], R.W2b, st);
+  to_bf16(R.W[4], R.n[4], R.W3b, st);
+  transpose(R.W2b, R.h2, R.h1, R.W2bT, st);
+  transpose(R.W3b, R.G, R.h2, R.W3bT, st);
+}
+
+int forward(Router& R, const float* X, uint32_t B, cudaStream_t st) {
+  int rc;
+  to_bf16(X, (size_t)B * R.d, R.Xb, st);
+  if ((rc = gemm(R, R.Xb, R.W1b, (int)B, (int)R.h1, (int)R.d, GemmEpi{R.A1, R.H1b, R.W[1], 1, (int)R.h1}, st)))
+    return rc;
+  if ((rc = gemm(R, R.H1b, R.W2b, (int)B, (int)R.h2, (int)R.h1, GemmEpi{R.A2, R.H2b, R.W[3], 1, (int)R.h2}, st)))
+    return rc;
+  return gemm(R, R.H2b, R.W3b, (int)B, (int)R.G, (int)R.h2, GemmEpi{R.L, nullptr, R.W[5], 0, (int)R.G}, st);
+}
+
+int check_dims(uint32_t d, uint32_t h1, uint32_t h2, uint32_t G, uint32_t B) {
+  if (!d || !h1 || !h2 || !G || !B) return fail(HNTL_EINVAL, "router sizes must be positive");
+  if (d % 8 || h1 % 8 || h2 % 8 || G % 8 || B % 8)
+    return fail(HNTL_EINVAL, "router sizes and batch must be multiples of 8 (16-byte BF16 rows)");
+  return HNTL_OK;
+}
+
+}  // namespace
+
+int router_route_probes(Router& R, const Index& I, const float* Q, uint32_t nq, uint32_t nprobe, float tau,
+                        void* ws, size_t ws_bytes, int32_t* probe, uint32_t* nfallback, cudaStream_t st);
+
+}  // namespace hntl
+
+struct hntl_router {
+  hntl::Router R;
+};
+
+using hntl::fail;
+
+extern "C" int hntl_router_create(int device, uint32_t d, uint32_t h1, uint32_t h2, uint32_t G, uint32_t max_batch,
+                                  const float* h_W1, const float* h_b1, const float* h_W2, const float* h_b2,
+                                  const float* h_W3, const float* h_b3, hntl_router** out) {
+  hntl::clear_error();
+  if (!out) return fail(HNTL_EINVAL, "null argument");
+  *out = nullptr;
+  int rc = hntl::check_dims(d, h1, h2, G, max_batch);
+  if (rc) return rc;
+  const float* init[6] = {h_W1, h_b1, h_W2, h_b2, h_W3, h_b3};
+  for (auto p : init)
+    if (!p) return fail(HNTL_EINVAL, "initial parameters are required");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) return fail(HNTL_ECUDA, "cannot select the device");
+  hntl_router* h = new (std::nothrow) hntl_router();
+  if (!h) return fail(HNTL_ENOMEM, "host allocation");
+  hntl::Router& R = h->R;
+  R.device = device;
+  R.d = d;
+  R.h1 = h1;
+  R.h2 = h2;
+  R.G = G;
+  R.max_batch = max_batch;
+  const size_t n[6] = {(size_t)h1 * d, h1, (size_t)h2 * h1, h2, (size_t)G * h2, G};
+  const size_t B = max_batch;
+  do {
+    for (int i = 0; i < 6; ++i) {
+      R.n[i] = n[i];
+      if ((rc = hntl::ralloc(R, (void**)&R.W[i], n[i] * 4)) || (rc = hntl::ralloc(R, (void**)&R.dW[i], n[i] * 4)) ||
+          (rc = hntl::ralloc(R, (void**)&R.m[i], n[i] * 4)) || (rc = hntl::ralloc(R, (void**)&R.v[i], n[i] * 4)))
+        break;
+    }
+    if (rc) break;
+    void** b16[] = {(void**)&R.W1b, (void**)&R.W2b, (void**)&R.W3b, (void**)&R.W2bT, (void**)&R.W3bT};
+    const size_t b16n[] = {n[0], n[2], n[4], n[2], n[4]};
+    for (int i = 0; i < 5 && !rc; ++i) rc = hntl::ralloc(R, b16[i], b16n[i] * 2);
+    if (rc) break;
+    struct {
+      void** p;
+      size_t bytes;
+    } acts[] = {{(void**)&R.Xb, B * d * 2},      {(void**)&R.XbT, B * d * 2},    {(void**)&R.H1b, B * h1 * 2},
+                {(void**)&R.H1bT, B * h1 * 2},   {(void**)&R.H2b, B * h2 * 2},   {(void**)&R.H2bT, B * h2 * 2},
+                {(void**)&R.A1, B * h1 * 4},     {(void**)&R.A2, B * h2 * 4},    {(void**)&R.L, B * G * 4},
+                {(void**)&R.dL, B * G * 4},      {(void**)&R.dH2, B * h2 * 4},   {(void**)&R.dA2, B * h2 * 4},
+                {(void**)&R.dH1, B * h1 * 4},    {(void**)&R.dA1, B * h1 * 4},   {(void**)&R.dLb, B * G * 2},
+                {(void**)&R.dLbT, B * G * 2},    {(void**)&R.dA2b, B * h2 * 2},  {(void**)&R.dA2bT, B * h2 * 2},
+                {(void**)&R.dA1b, B * h1 * 2},   {(void**)&R.dA1bT, B * h1 * 2}, {(void**)&R.mx, B * 4},
+                {(void**)&R.sm, B * 4},          {(void**)&R.d_err, 4}};
+    for (auto& a : acts)
+      if ((rc = hntl::ralloc(R, a.p, a.bytes))) break;
+    if (rc) break;
+    for (int i = 0; i < 6 && !rc; ++i) {
+      if (cudaMemcpy(R.W[i], init[i], n[i] * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemset(R.m[i], 0, n[i] * 4) != cudaSuccess || cudaMemset(R.v[i], 0, n[i] * 4) != cudaSuccess ||
+          cudaMemset(R.dW[i], 0, n[i] * 4) != cudaSuccess)
+        rc = fail(HNTL_ECUDA, "router: parameter upload");
+    }
+    if (rc) break;
+    cudaMemset(R.d_err, 0, 4);
+    hntl::refresh_bf16(R, nullptr);
+    if (cudaDeviceSynchronize() != cudaSuccess) rc = fail(HNTL_ECUDA, "router: initialisation");
+  } while (0);
+  if (prev >= 0) cudaSetDevice(prev);
+  if (rc) {
+    hntl::rfree(R);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return HNTL_OK;
+}
+
+extern "C" void hntl_router_free(hntl_router* h) {
+  if (!h) return;
+  hntl::rfree(h->R);
+  delete h;
+}
+
+static int copy_out(const hntl::Router& R, float* const* dst, float* const* src) {
+  for (int i = 0; i < 6; ++i)
+    if (dst[i] && cudaMemcpy(dst[i], src[i], R.n[i] * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(HNTL_ECUDA, "router: copy to host");
+  return HNTL_OK;
+}
+
+extern "C" int hntl_router_params(const hntl_router* h, float* W1, float* b1, float* W2, float* b2, float* W3,
+                                  float* b3) {
+  hntl::clear_error();
+  if (!h) return fail(HNTL_EINVAL, "null router");
+  float* dst[6] = {W1, b1, W2, b2, W3, b3};
+  return copy_out(h->R, dst, h->R.W);
+}
+
+extern "C" int hntl_router_grads(const hntl_router* h, float* dW1, float* db1, float* dW2, float* db2, float* dW3,
+                                 float* db3) {
+  hntl::clear_error();
+  if (!h) return fail(HNTL_EINVAL, "null router");
+  float* dst[6] = {dW1, db1, dW2, db2, dW3, db3};
+  return copy_out(h->R, dst, h->R.dW);
+}
+
+extern "C" int hntl_router_step(hntl_router* h, const float* d_X, const float* d_T, uint32_t B, float lr, float wd,
+                                int update, float* d_loss, void* stream) {
+  hntl::clear_error();
+  if (!h || !d_X || !d_T) return fail(HNTL_EINVAL, "null argument");
+  hntl::Router& R = h->R;
+  int rc = hntl::check_dims(R.d, R.h1, R.h2, R.G, B);
+  if (rc) return rc;
+  if (B > R.max_batch) return fail(HNTL_EINVAL, "batch larger than the router's max_batch");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((rc = hntl::forward(R, d_X, B, st))) return rc;
+  hntl::k_softmax_ce<<<B, 256, 0, st>>>(R.L, d_T, (int)R.G, (int)B, R.dL, R.dLb, d_loss);
+  // output layer
+  hntl::transpose(R.dLb, (int)B, (int)R.G, R.dLbT, st);
+  hntl::transpose(R.H2b, (int)B, (int)R.h2, R.H2bT, st);
+  if ((rc = hntl::gemm(R, R.dLbT, R.H2bT, (int)R.G, (int)R.h2, (int)B, hntl::GemmEpi{R.dW[4], nullptr, nullptr, 0, (int)R.h2}, st)))
+    return rc;
+  hntl::k_colsum<<<(R.G + 255) / 256, 256, 0, st>>>(R.dL, (int)B, (int)R.G, R.dW[5]);
+  if ((rc = hntl::gemm(R, R.dLb, R.W3bT, (int)B, (int)R.h2, (int)R.G, hntl::GemmEpi{R.dH2, nullptr, nullptr, 0, (int)R.h2}, st)))
+    return rc;
+  // second hidden layer
+  const size_t n2 = (size_t)B * R.h2, n1 = (size_t)B * R.h1;
+  hntl::k_gelu_bwd<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(R.dH2, R.A2, n2, R.dA2, R.dA2b);
+  hntl::transpose(R.dA2b, (int)B, (int)R.h2, R.dA2bT, st);
+  hntl::transpose(R.H1b, (int)B, (int)R.h1, R.H1bT, st);
+  if ((rc = hntl::gemm(R, R.dA2bT, R.H1bT, (int)R.h2, (int)R.h1, (int)B, hntl::GemmEpi{R.dW[2], nullptr, nullptr, 0, (int)R.h1}, st)))
+    return rc;
+  hntl::k_colsum<<<(R.h2 + 255) / 256, 256, 0, st>>>(R.dA2, (int)B, (int)R.h2, R.dW[3]);
+  if ((rc = hntl::gemm(R, R.dA2b, R.W2bT, (int)B, (int)R.h1, (int)R.h2, hntl::GemmEpi{R.dH1, nullptr, nullptr, 0, (int)R.h1}, st)))
+    return rc;
+  // first hidden layer
+  hntl::k_gelu_bwd<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(R.dH1, R.A1, n1, R.dA1, R.dA1b);
+  hntl::transpose(R.dA1b, (int)B, (int)R.h1, R.dA1bT, st);
+  hntl::transpose(R.Xb, (int)B, (int)R.d, R.XbT, st);
+  if ((rc = hntl::gemm(R, R.dA1bT, R.XbT, (int)R.h1, (int)R.d, (int)B, hntl::GemmEpi{R.dW[0], nullptr, nullptr, 0, (int)R.d}, st)))
+    return rc;
+  hntl::k_colsum<<<(R.h1 + 255) / 256, 256, 0, st>>>(R.dA1, (int)B, (int)R.h1, R.dW[1]);
+  if (update) {
+    ++R.step;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - powf(b1, (float)R.step), c2 = 1.f - powf(b2, (float)R.step);
+    for (int i = 0; i < 6; ++i) {
+      uint16_t* pb = i == 0 ? R.W1b : i == 2 ? R.W2b : i == 4 ? R.W3b : nullptr;
+      hntl::k_adamw<<<(unsigned)((R.n[i] + 255) / 256), 256, 0, st>>>(R.W[i], R.dW[i], R.m[i], R.v[i], R.n[i], lr,
+                                                                       (i % 2 == 0) ? wd : 0.f, b1, b2, eps, c1, c2,
+                                                                       pb);
+    }
+    hntl::transpose(R.W2b, (int)R.h2, (int)R.h1, R.W2bT, st);
+    hntl::transpose(R.W3b, (int)R.G, (int)R.h2, R.W3bT, st);
+  }
+  HNTL_CUDA_TRY(cudaGetLastError());
+  return HNTL_OK;
+}
+
+extern "C" int hntl_router_logits(hntl_router* h, const float* d_X, uint32_t B, float* d_logits, void* stream) {
+  hntl::clear_error();
+  if (!h || !d_X || !d_logits) return fail(HNTL_EINVAL, "null argument");
+  hntl::Router& R = h->R;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (uint32_t s = 0; s < B; s += R.max_batch) {
+    const uint32_t b = std::min(R.max_batch, B - s);
+    int rc = hntl::check_dims(R.d, R.h1, R.h2, R.G, (b + 7) / 8 * 8);
+    if (rc) return rc;
+    if ((rc = hntl::forward(R, d_X + (size_t)s * R.d, b, st))) return rc;
+    HNTL_CUDA_TRY(cudaMemcpyAsync(d_logits + (size_t)s * R.G, R.L, sizeof(float) * b * R.G, cudaMemcpyDeviceToDevice, st));
+  }
+  return HNTL_OK;
+}
+
+namespace hntl {
+
+// Router probes (the nprobe largest logits) for every query; where their
+// softmax mass is below tau, the query's centroid probes instead. Workspace:
+// as hntl_search_workspace_bytes(idx, nq, 1, 1, nprobe) for the centroid
+// routing, then nq * nprobe int32 + nq * nprobe floats + nq * G floats.
+int router_route_probes(Router& R, const Index& I, const float* Q, uint32_t nq, uint32_t nprobe, float tau,
+                        void* ws, size_t ws_bytes, int32_t* probe, uint32_t* nfallback, cudaStream_t st) {
+  if (R.G != I.G || R.d != I.d) return fail(HNTL_EINVAL, "router and index disagree on d or G");
+  if (nprobe < 1 || nprobe > I.G) return fail(HNTL_EINVAL, "nprobe must be in [1, G]");
+  const size_t route_ws = workspace_bytes(I, nq, 1, 1, nprobe);
+  if (!route_ws) return HNTL_EINVAL;
+  Carver c(static_cast<char*>(ws) + route_ws);
+  int32_t* cprobe = c.take<int32_t>((size_t)nq * nprobe);
+  float* cdist = c.take<float>((size_t)nq * nprobe);
+  float* negl = c.take<float>((size_t)nq * I.G);
+  float* negtop = c.take<float>((size_t)nq * nprobe);
+  if (ws_bytes < route_ws + align_up(c.off, 256)) return fail(HNTL_EINVAL, "router routing workspace too small");
+  int rc = route_only(I, Q, nq, nprobe, ws, route_ws, cprobe, cdist, st);
+  if (rc) return rc;
+  if (nfallback) HNTL_CUDA_TRY(cudaMemsetAsync(nfallback, 0, 4, st));
+  static thread_local bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_route_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kSelWarps * kMaxG * (int)sizeof(float));
+    attr = true;
+  }
+  for (uint32_t s = 0; s < nq; s += R.max_batch) {
+    const uint32_t b = std::min(R.max_batch, nq - s);
+    if ((rc = forward(R, Q + (size_t)s * R.d, b, st))) return rc;
+    k_logit_stats<<<b, 256, 0, st>>>(R.L, (int)R.G, negl + (size_t)s * R.G, R.mx, R.sm);
+    k_route_select<<<(b + kSelWarps - 1) / kSelWarps, kSelWarps * 32, (size_t)kSelWarps * R.G * sizeof(float), st>>>(
+        negl + (size_t)s * R.G, (int)b, (int)R.G, (int)nprobe, probe + (size_t)s * nprobe, negtop + (size_t)s * nprobe);
+    k_router_merge<<<(b + 127) / 128, 128, 0, st>>>((int)b, (int)nprobe, negtop + (size_t)s * nprobe, R.mx, R.sm, tau,
+                                                    cprobe + (size_t)s * nprobe, probe + (size_t)s * nprobe, nfallback);
+  }
+  HNTL_CUDA_TRY(cudaGetLastError());
+  return HNTL_OK;
+}
+
+}  // namespace hntl
+
+extern "C" size_t hntl_router_route_workspace_bytes(const hntl_router* h, const hntl_index* idx, uint32_t nq,
+                                                    uint32_t nprobe) {
+  hntl::clear_error();
+  if (!h || !idx) {
+    fail(HNTL_EINVAL, "null argument");
+    return 0;
+  }
+  const size_t route_ws = hntl::workspace_bytes(idx->I, nq, 1, 1, nprobe);
+  if (!route_ws) return 0;
+  hntl::Carver c(nullptr);
+  c.take<int32_t>((size_t)nq * nprobe);
+  c.take<float>((size_t)nq * nprobe);
+  c.take<float>((size_t)nq * idx->I.G);
+  c.take<float>((size_t)nq * nprobe);
+  return route_ws + hntl::align_up(c.off, 256);
+}
+
+extern "C" int hntl_router_route(hntl_router* h, const hntl_index* idx, const float* d_Q, uint32_t nq,
+                                 uint32_t nprobe, float tau, void* d_ws, size_t ws_bytes, int32_t* d_probe,
+                                 uint32_t* d_nfallback, void* stream) {
+  hntl::clear_error();
+  if (!h || !idx || !d_Q || !d_ws || !d_probe) return fail(HNTL_EINVAL, "null argument");
+  if (nq == 0) return HNTL_OK;
+  return hntl::router_route_probes(h->R, idx->I, d_Q, nq, nprobe, tau, d_ws, ws_bytes, d_probe, d_nfallback,
+                                   static_cast<cudaStream_t>(stream));
+}

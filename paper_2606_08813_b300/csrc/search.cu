@@ -36,6 +36,43 @@ namespace hntl {
 namespace {
 
 
+// ------------------------------------------------------------------ given probes
+
+// Routing distance ||q - mu_g||^2 of caller-supplied probes (one warp per
+// (query, probe); BF16-rounded values in the precision form). A grain id out
+// of [0, G) is replaced by 0 and flagged in the device error word.
+template <bool kBF16>
+__global__ void k_probe_dist(const float* __restrict__ Q, const float* __restrict__ M, const uint16_t* __restrict__ Mh,
+                             int nq, int nprobe, int G, int d, const int32_t* __restrict__ probe_in,
+                             int32_t* __restrict__ probe, float* __restrict__ probe_d, int* __restrict__ err) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= nq * nprobe) return;
+  int g = probe_in[w];
+  if (g < 0 || g >= G) {
+    if (lane == 0) atomicOr(err, 2);
+    g = 0;
+  }
+  const float* q = Q + (size_t)(w / nprobe) * d;
+  float acc = 0.f;
+  for (int t = lane; t < d; t += 32) {
+    float qv = q[t], mv;
+    if (kBF16) {
+      qv = __bfloat162float(__float2bfloat16_rn(qv));
+      mv = __uint_as_float((uint32_t)Mh[(size_t)g * d + t] << 16);
+    } else {
+      mv = M[(size_t)g * d + t];
+    }
+    const float df = qv - mv;
+    acc = fmaf(df, df, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    probe[w] = g;
+    probe_d[w] = acc;
+  }
+}
+
 // ------------------------------------------------------------------ bucketing
 
 __global__ void k_bucket_count(const int32_t* __restrict__ probe, int n, uint32_t* __restrict__ gcnt) {
@@ -378,7 +415,7 @@ void profile_end(const StageEvents& ev) {
 
 int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe,
            const int64_t* filter, void* ws, size_t ws_bytes, int64_t* out_ids, float* out_d, uint32_t* cand_ids,
-           float* cand_d, int32_t* probe_out, cudaStream_t st) {
+           float* cand_d, int32_t* probe_out, cudaStream_t st, const int32_t* probe_in = nullptr) {
   int rc = check_params(I, nq, k, C, nprobe);
   if (rc) return rc;
   if (filter && !I.has_attr) return fail(HNTL_EINVAL, "filter given but the index has no attribute column");
@@ -402,7 +439,23 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
   mark(0);
   HNTL_CUDA_TRY(cudaMemsetAsync(w.gcnt, 0, sizeof(uint32_t) * I.G, st));
   HNTL_CUDA_TRY(cudaMemsetAsync(w.gcur, 0, sizeof(uint32_t) * I.G, st));
-  if ((rc = launch_route(I, Qd, nq, nprobe, w, st))) return rc;
+  if (probe_in) {
+    const bool bf16 = I.precision == HNTL_PREC_BF16_FP8;
+    if (bf16) {
+      const size_t n = (size_t)nq * I.d;
+      k_to_bf16_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Qd, n, w.Qh);
+    }
+    const unsigned blocks = (unsigned)(((size_t)nq * nprobe * 32 + 255) / 256);
+    if (bf16)
+      k_probe_dist<true><<<blocks, 256, 0, st>>>(Qd, I.M, I.Mh, (int)nq, (int)nprobe, (int)I.G, (int)I.d, probe_in,
+                                                w.probe, w.probe_d, I.d_err);
+    else
+      k_probe_dist<false><<<blocks, 256, 0, st>>>(Qd, I.M, I.Mh, (int)nq, (int)nprobe, (int)I.G, (int)I.d, probe_in,
+                                                 w.probe, w.probe_d, I.d_err);
+    HNTL_CUDA_TRY(cudaGetLastError());
+  } else if ((rc = launch_route(I, Qd, nq, nprobe, w, st))) {
+    return rc;
+  }
   mark(1);
   const int P = (int)(nq * nprobe);
   k_bucket_count<<<(P + 255) / 256, 256, 0, st>>>(w.probe, P, w.gcnt);
@@ -579,6 +632,26 @@ int hntl_search(const hntl_index* idx, const float* d_queries, uint32_t nq, uint
   if (!idx) return hntl::fail(HNTL_EINVAL, "null index");
   return hntl::search(idx->I, d_queries, nq, k, C, nprobe, d_filter, d_ws, ws_bytes, d_out_ids, d_out_dist,
                       d_cand_ids, d_cand_dist, d_probe, static_cast<cudaStream_t>(stream));
+}
+
+int hntl_search_probes(const hntl_index* idx, const float* d_queries, uint32_t nq, uint32_t k, uint32_t C,
+                       uint32_t nprobe, const int32_t* d_probe_in, const int64_t* d_filter, void* d_ws,
+                       size_t ws_bytes, int64_t* d_out_ids, float* d_out_dist, uint32_t* d_cand_ids,
+                       float* d_cand_dist, void* stream) {
+  hntl::clear_error();
+  if (!idx) return hntl::fail(HNTL_EINVAL, "null index");
+  if (!d_probe_in && nq) return hntl::fail(HNTL_EINVAL, "null probe list");
+  return hntl::search(idx->I, d_queries, nq, k, C, nprobe, d_filter, d_ws, ws_bytes, d_out_ids, d_out_dist,
+                      d_cand_ids, d_cand_dist, nullptr, static_cast<cudaStream_t>(stream), d_probe_in);
+}
+
+int hntl_device_status(const hntl_index* idx, int* status, int clear) {
+  hntl::clear_error();
+  if (!idx || !status) return hntl::fail(HNTL_EINVAL, "null argument");
+  const hntl::Index& I = idx->I;
+  HNTL_CUDA_TRY(cudaMemcpy(status, I.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (clear) HNTL_CUDA_TRY(cudaMemset(I.d_err, 0, sizeof(int)));
+  return (*status & 1) ? HNTL_ETIMEOUT : HNTL_OK;
 }
 
 int hntl_route(const hntl_index* idx, const float* d_queries, uint32_t nq, uint32_t nprobe, void* d_ws,

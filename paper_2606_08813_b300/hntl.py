@@ -290,3 +290,116 @@ class Index:
         _check(lib.hntl_route(self._h, _ptr(Q), nq, nprobe, _ptr(ws), ws.numel(), _ptr(probe), _ptr(pd),
                               _stream(stream)))
         return probe, pd
+
+
+lib.hntl_search_probes.argtypes = [_P, _P, _U32, _U32, _U32, _U32, _P, _P, _P, _SZ, _P, _P, _P, _P, _P]
+lib.hntl_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+lib.hntl_router_create.argtypes = [ctypes.c_int, _U32, _U32, _U32, _U32, _U32, _P, _P, _P, _P, _P, _P,
+                                   ctypes.POINTER(_P)]
+lib.hntl_router_free.argtypes = [_P]
+lib.hntl_router_free.restype = None
+lib.hntl_router_params.argtypes = [_P] + [_P] * 6
+lib.hntl_router_grads.argtypes = [_P] + [_P] * 6
+lib.hntl_router_step.argtypes = [_P, _P, _P, _U32, ctypes.c_float, ctypes.c_float, ctypes.c_int, _P, _P]
+lib.hntl_router_logits.argtypes = [_P, _P, _U32, _P, _P]
+lib.hntl_router_route_workspace_bytes.argtypes = [_P, _P, _U32, _U32]
+lib.hntl_router_route_workspace_bytes.restype = _SZ
+lib.hntl_router_route.argtypes = [_P, _P, _P, _U32, _U32, ctypes.c_float, _P, _SZ, _P, _P, _P]
+
+
+def search_probes(index: Index, Q: torch.Tensor, probes: torch.Tensor, k: int, C: int, filters=None,
+                  return_pool: bool = False, stream=None):
+    """Mode B search with the given probed grains (int32 CUDA [nq, nprobe])."""
+    nq, nprobe = int(probes.shape[0]), int(probes.shape[1])
+    _dev_tensor(Q, torch.float32, (nq, int(index.desc.d)), index.device, "Q")
+    _dev_tensor(probes, torch.int32, (nq, nprobe), index.device, "probes")
+    Ce = max(C, k)
+    ids = torch.empty(nq, k, dtype=torch.int64, device=Q.device)
+    dist = torch.empty(nq, k, dtype=torch.float32, device=Q.device)
+    pid = torch.empty(nq, Ce, dtype=torch.int32, device=Q.device) if return_pool else None
+    pd = torch.empty(nq, Ce, dtype=torch.float32, device=Q.device) if return_pool else None
+    ws = index.workspace(index.workspace_bytes(max(nq, 1), k, C, nprobe))
+    _check(lib.hntl_search_probes(index.handle, _ptr(Q), nq, k, C, nprobe, _ptr(probes), _ptr(filters), _ptr(ws),
+                                  ws.numel(), _ptr(ids), _ptr(dist), _ptr(pid), _ptr(pd), _stream(stream)))
+    return (ids, dist, pid, pd) if return_pool else (ids, dist)
+
+
+def device_status(index: Index, clear: bool = True) -> int:
+    st = ctypes.c_int(0)
+    lib.hntl_device_status(index.handle, ctypes.byref(st), int(clear))
+    return int(st.value)
+
+
+class Router:
+    """Learned grain router (see hntl_router_* in include/hntl.h)."""
+
+    def __init__(self, params, max_batch: int, device: int = 0):
+        import numpy as np
+
+        W1, b1, W2, b2, W3, b3 = [np.ascontiguousarray(p, dtype=np.float32) for p in params]
+        self.h1, self.d = W1.shape
+        self.h2 = W2.shape[0]
+        self.G = W3.shape[0]
+        self.max_batch = int(max_batch)
+        self.device = device
+        self._keep = (W1, b1, W2, b2, W3, b3)
+        h = _P()
+        _check(lib.hntl_router_create(device, self.d, self.h1, self.h2, self.G, self.max_batch,
+                                      *(a.ctypes.data_as(_P) for a in self._keep), ctypes.byref(h)))
+        self._h = h
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.hntl_router_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _host(self, fn):
+        import numpy as np
+
+        shapes = [(self.h1, self.d), (self.h1,), (self.h2, self.h1), (self.h2,), (self.G, self.h2), (self.G,)]
+        out = [np.zeros(s, dtype=np.float32) for s in shapes]
+        _check(fn(self._h, *(a.ctypes.data_as(_P) for a in out)))
+        return out
+
+    def params(self):
+        return self._host(lib.hntl_router_params)
+
+    def grads(self):
+        return self._host(lib.hntl_router_grads)
+
+    def step(self, X: torch.Tensor, T: torch.Tensor, lr: float = 1e-3, wd: float = 0.01, update: bool = True,
+             loss: torch.Tensor | None = None, stream=None):
+        B = int(X.shape[0])
+        _dev_tensor(X, torch.float32, (B, self.d), self.device, "X")
+        _dev_tensor(T, torch.float32, (B, self.G), self.device, "T")
+        _check(lib.hntl_router_step(self._h, _ptr(X), _ptr(T), B, float(lr), float(wd), int(update), _ptr(loss),
+                                    _stream(stream)))
+
+    def logits(self, X: torch.Tensor, stream=None) -> torch.Tensor:
+        B = int(X.shape[0])
+        _dev_tensor(X, torch.float32, (B, self.d), self.device, "X")
+        out = torch.empty(B, self.G, dtype=torch.float32, device=X.device)
+        _check(lib.hntl_router_logits(self._h, _ptr(X), B, _ptr(out), _stream(stream)))
+        return out
+
+    def route(self, index: Index, Q: torch.Tensor, nprobe: int, tau: float = 0.5, stream=None):
+        """(probes int32 [nq, nprobe], number of queries that fell back to centroid routing)."""
+        nq = int(Q.shape[0])
+        _dev_tensor(Q, torch.float32, (nq, self.d), self.device, "Q")
+        nb = int(lib.hntl_router_route_workspace_bytes(self._h, index.handle, max(nq, 1), nprobe))
+        if nb == 0:
+            raise HntlError(EINVAL, last_error())
+        if self._ws is None or self._ws.numel() < nb:
+            self._ws = torch.empty(nb, dtype=torch.uint8, device=Q.device)
+        probe = torch.empty(nq, nprobe, dtype=torch.int32, device=Q.device)
+        nfb = torch.zeros(1, dtype=torch.int32, device=Q.device)
+        _check(lib.hntl_router_route(self._h, index.handle, _ptr(Q), nq, nprobe, float(tau), _ptr(self._ws),
+                                     self._ws.numel(), _ptr(probe), _ptr(nfb), _stream(stream)))
+        return probe, nfb
