@@ -147,38 +147,53 @@ def make_workload(name: str, device, rank: int = 0):
 
 
 def exact_topk(X: torch.Tensor, Q: torch.Tensor, k: int, shortlist: int = 64, qblock: int = 512,
-               chunk: int = 1 << 20):
+               chunk: int = 1 << 20, attr: torch.Tensor | None = None, ranges: torch.Tensor | None = None):
     """Ground-truth kNN for recall (evaluation only, not the search path): an
     FP32 matmul shortlist per row chunk, then the shortlist re-ranked by FP64
-    direct-form distances with ties broken by id."""
+    direct-form distances with ties broken by id. With attr [N] and ranges
+    [nq, 2] (device int64), only rows with lo <= attr <= hi count; missing
+    neighbours are -1."""
     out = []
     for q0 in range(0, Q.shape[0], qblock):
         Qb = Q[q0:q0 + qblock]
         nq = Qb.shape[0]
+        Rb = None if ranges is None else ranges[q0:q0 + qblock]
         best_d = torch.full((nq, shortlist), float("inf"), device=Q.device)
         best_i = torch.zeros((nq, shortlist), dtype=torch.int64, device=Q.device)
         qn = (Qb * Qb).sum(1, keepdim=True)
         for s in range(0, X.shape[0], chunk):
             Xc = X[s:s + chunk]
             dd = qn + (Xc * Xc).sum(1)[None] - 2.0 * (Qb @ Xc.T)
+            if Rb is not None:
+                a = attr[s:s + chunk][None]
+                dd = torch.where((a >= Rb[:, :1]) & (a <= Rb[:, 1:]), dd, float("inf"))
             v, i = torch.topk(dd, min(shortlist, Xc.shape[0]), dim=1, largest=False)
             cat_d = torch.cat([best_d, v], 1)
             cat_i = torch.cat([best_i, i + s], 1)
             best_d, j = torch.topk(cat_d, shortlist, dim=1, largest=False)
             best_i = torch.gather(cat_i, 1, j)
-        exact = ((X[best_i].double() - Qb.double()[:, None, :]) ** 2).sum(-1).cpu().numpy()
+        exact = ((X[best_i].double() - Qb.double()[:, None, :]) ** 2).sum(-1)
+        exact = torch.where(torch.isinf(best_d), float("inf"), exact).cpu().numpy()
         ids = best_i.cpu().numpy()
         for qi in range(nq):
             order = np.lexsort((ids[qi], exact[qi]))[:k]
-            out.append(ids[qi][order])
+            row = ids[qi][order]
+            row[np.isinf(exact[qi][order])] = -1
+            out.append(row)
     return torch.from_numpy(np.stack(out))
 
 
-def recall_at_k(found: torch.Tensor, truth: torch.Tensor) -> float:
-    f = found.cpu().numpy()
-    t = truth.cpu().numpy()
+def recall_at_k(found, truth) -> float:
+    """Mean share of each query's true neighbours (ids >= 0) found among its first k results."""
+    f = found.cpu().numpy() if torch.is_tensor(found) else np.asarray(found)
+    t = truth.cpu().numpy() if torch.is_tensor(truth) else np.asarray(truth)
     k = t.shape[1]
-    return float(np.mean([len(set(a[:k].tolist()) & set(b.tolist())) / k for a, b in zip(f, t)]))
+    out = []
+    for a, b in zip(f, t):
+        want = set(b[b >= 0].tolist())
+        if want:
+            out.append(len(set(a[:k].tolist()) & want) / len(want))
+    return float(np.mean(out)) if out else float("nan")
 
 
 def stage_bytes(idx, rows_g, probe: np.ndarray, w: dict, batch: int):
@@ -234,6 +249,115 @@ def cpu_oracle_qps(idx_host, X_np, Q_np, k, C, nprobe, budget_s: float = 15.0, p
     return done / t, done, O.threads()
 
 
+ATTR_SPAN = 1 << 40
+
+
+def run_serving(a, hntl, gi, X, Q, attr, w, sd):
+    """Continuous batching over the same index (the library's server): open-loop
+    Poisson arrivals at each offered rate, k in {10, 100} and C in {20, 200,
+    1000} drawn uniformly (C raised to k), half of the requests carrying a
+    20%-selectivity range on the int64 attribute column. Requests are handed
+    to the server in the chunks that have arrived by the time the client
+    loop comes round, each stamped with its scheduled arrival time, so a slow
+    client shows up as latency, not as a lower offered rate. Latency is from
+    scheduled arrival to completion (the server's clock)."""
+    rng = np.random.default_rng(sd["serve"])
+    Qh = Q.cpu().numpy()
+    nQ = len(Qh)
+    dev = Q.device
+    budget = min(int(a.serve_budget_gb * (1 << 30)), int(0.8 * torch.cuda.mem_get_info(dev)[0]))
+    t0 = time.perf_counter()
+    srv = hntl.Server(gi, mem_budget=budget, max_slots=a.serve_slots, batch=a.serve_batch, nprobe=w["nprobe"],
+                      k_max=100, C_max=1000)
+    create_s = time.perf_counter() - t0
+    slots = srv.stats()["slots"]
+    buf = np.empty((8192, 100), dtype=np.int64)
+    samples = []  # (query row, range, C, first 10 ids)
+
+    def collect(tickets, done, lo, hi, want, rec):
+        for s0 in range(lo, hi, 8192):
+            s1 = min(hi, s0 + 8192)
+            before = done[s0:s1].copy()
+            srv.poll_many(tickets[s0:s1], done[s0:s1], buf[:s1 - s0], None, 0)
+            for j in np.flatnonzero((before == 0) & (done[s0:s1] == 1)):
+                if want[s0 + j]:
+                    rec.append((s0 + j, buf[j, :10].copy()))
+
+    rates_out = []
+    for R in [int(x) for x in a.serve_rates.split(",") if x]:
+        n = max(1, int(R * a.serve_seconds))
+        qi = rng.integers(0, nQ, n)
+        k = rng.choice(np.array([10, 100], np.uint32), n)
+        C = np.maximum(rng.choice(np.array([20, 200, 1000], np.uint32), n), k)
+        ranges = synth.range_filters(n, sd["serve"] + R, span=ATTR_SPAN, selectivity=0.2,
+                                     frac_filtered=0.5).numpy()
+        want = np.zeros(n, dtype=bool)
+        want[rng.choice(n, min(n, a.serve_recall // max(1, len(a.serve_rates.split(",")))), replace=False)] = True
+        tickets = np.zeros(n, dtype=np.uint64)
+        done = np.zeros(n, dtype=np.uint8)
+        rec = []
+        srv.reset_stats()
+        start = time.monotonic_ns() + 2_000_000
+        arr = start + np.cumsum(rng.exponential(1e9 / R, n)).astype(np.int64)
+        i = lo = 0
+        busy_refusals = 0
+        while i < n:
+            now = time.monotonic_ns()
+            j = min(int(np.searchsorted(arr, now, "right")), i + 4096)
+            if j > i:
+                t = srv.submit(Qh[qi[i:j]], k[i:j], C[i:j], ranges[i:j], arr[i:j])
+                tickets[i:i + len(t)] = t
+                busy_refusals += int(len(t) < j - i)
+                i += len(t)
+            collect(tickets, done, lo, i, want, rec)
+            nz = np.flatnonzero(done[lo:i] == 0)
+            lo = lo + (int(nz[0]) if len(nz) else i - lo)
+            if i < n and j <= i:
+                wait = (arr[i] - time.monotonic_ns()) / 1e9
+                if wait > 2e-4:
+                    time.sleep(wait - 1e-4)
+        deadline = time.monotonic() + 60
+        while lo < n and time.monotonic() < deadline:
+            srv.poll_many(tickets[lo:n], done[lo:n], None, None, 50)
+            collect(tickets, done, lo, n, want, rec)
+            nz = np.flatnonzero(done[lo:n] == 0)
+            lo = lo + (int(nz[0]) if len(nz) else n - lo)
+        end = time.monotonic_ns()
+        st = srv.stats()
+        achieved = int(done.sum()) / ((end - start) / 1e9)
+        for idx, ids in rec:
+            samples.append((int(qi[idx]), ranges[idx], int(C[idx]), ids))
+        rates_out.append({"offered_qps": R, "achieved_qps": round(achieved, 1), "completed": int(done.sum()),
+                          "p50_ms": round(st["p50_us"] / 1e3, 3), "p99_ms": round(st["p99_us"] / 1e3, 3),
+                          "max_ms": round(st["max_us"] / 1e3, 3), "mean_batch": round(st["mean_batch"], 1),
+                          "admission_refusals": busy_refusals})
+        print(f"serving {R} q/s: {rates_out[-1]}", file=sys.stderr)
+    srv.close()
+    recall = {}
+    if samples and X is not None:
+        rows = torch.tensor([s[0] for s in samples], device=dev)
+        rg = torch.from_numpy(np.stack([s[1] for s in samples])).to(dev)
+        truth = exact_topk(X, Q[rows].contiguous(), 10, attr=attr, ranges=rg).numpy()
+        got = np.stack([s[3] for s in samples])
+        Cs = np.array([s[2] for s in samples])
+        filt = np.array([s[1][0] != np.iinfo(np.int64).min for s in samples])
+        recall["all"] = round(recall_at_k(got, truth), 4)
+        for c in (20, 200, 1000):
+            m = Cs == c
+            if m.any():
+                recall[f"C={c}"] = round(recall_at_k(got[m], truth[m]), 4)
+        recall["filtered"] = round(recall_at_k(got[filt], truth[filt]), 4)
+        recall["unfiltered"] = round(recall_at_k(got[~filt], truth[~filt]), 4)
+        recall["queries"] = len(samples)
+    ok = [r for r in rates_out if r["achieved_qps"] >= 0.97 * r["offered_qps"] and r["p99_ms"] <= a.serve_p99_ms]
+    return {"sustained_qps": max((r["offered_qps"] for r in ok), default=None),
+            "sustained_rule": f"highest offered rate served at >= 97% with p99 <= {a.serve_p99_ms} ms",
+            "rates": rates_out, "recall_at_10": recall, "batch": a.serve_batch, "slots": slots,
+            "mem_budget_gb": round(budget / (1 << 30), 1), "create_s": round(create_s, 2),
+            "mix": "k in {10,100}, C in {20,200,1000} uniform (C >= k), 50% with a 20%-selectivity attribute range",
+            "seconds_per_rate": a.serve_seconds}
+
+
 def run_ours(a, world, rank, local):
     from paper_2606_08813_b300 import build_lib
 
@@ -247,8 +371,10 @@ def run_ours(a, world, rank, local):
     k, C, nprobe = w["k"], w["C"], w["nprobe"]
     t0 = time.perf_counter()
     prec = w.get("precision", "fp32")
+    serve = bool(a.serve_rates) and not a.profile_mode
+    attr = synth.attributes(w["n"], sd["serve"], span=ATTR_SPAN, device=dev) if serve else None
     gi = hntl.Index.build(X, w["G"], w["r"], u=synth.uniforms(w["G"], sd["kmeans"]).numpy(), seed=sd["kmeans"],
-                          precision=hntl.PREC_BF16_FP8 if prec == "bf16-fp8" else hntl.PREC_FP32)
+                          precision=hntl.PREC_BF16_FP8 if prec == "bf16-fp8" else hntl.PREC_FP32, attr=attr)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     if a.profile_mode:
@@ -350,6 +476,8 @@ def run_ours(a, world, rank, local):
                 "d2h_bytes_per_step": B * k * 12},
         "gpu_launches": 10 * a.steps, "clocks": clocks,
     }
+    if serve:
+        line["serving"] = run_serving(a, hntl, gi, X, Q, attr, w, sd)
     if rank == 0 and world == 1 and not a.no_cpu_baseline and not a.profile_mode:
         host = gi.export()
         Xn = X.cpu().numpy()
@@ -413,12 +541,20 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain-1m-zipf", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="precision-10m", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--recall-queries", type=int, default=2048)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-queries", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-rates", default="25000,100000,200000",
+                    help="offered Poisson rates (q/s) of the serving run; empty to skip it")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-batch", type=int, default=2048)
+    ap.add_argument("--serve-slots", type=int, default=1 << 18)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-recall", type=int, default=1536, help="served requests checked against brute force")
+    ap.add_argument("--serve-p99-ms", type=float, default=50.0)
     ap.add_argument("--profile-mode", action="store_true",
                     help="for ncu captures: free the raw rows after the build; no recall, CPU baseline or e2e")
     a = ap.parse_args()

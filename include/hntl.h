@@ -217,6 +217,13 @@ int hntl_search_probes(const hntl_index* idx, const float* d_queries, uint32_t n
  * else HNTL_OK; `clear` resets the word. */
 int hntl_device_status(const hntl_index* idx, int* status, int clear);
 
+/* Test hook for the bounded device waits: launches one kernel that polls, at
+ * most `polls` times (1 .. 2^20), an mbarrier phase that nothing completes,
+ * then gives up and sets bit 0 of the index's device status, as a stalled
+ * tensor-core pipeline would. hntl_device_status then returns HNTL_ETIMEOUT.
+ * The GPU context stays usable. */
+int hntl_selftest_wait_timeout(const hntl_index* idx, uint32_t polls, void* stream);
+
 /* ---- learned grain router (the paper lists learned grain partitioning as
  * future work, sec. 4; this router is the library's own addition) ----
  * An MLP d -> h1 -> h2 -> G with exact GELU after each hidden layer and a
@@ -262,6 +269,61 @@ size_t hntl_router_route_workspace_bytes(const hntl_router* router, const hntl_i
 int hntl_router_route(hntl_router* router, const hntl_index* idx, const float* d_queries, uint32_t nq,
                       uint32_t nprobe, float tau, void* d_ws, size_t ws_bytes, int32_t* d_probe,
                       uint32_t* d_nfallback, void* stream);
+
+/* ---- continuous-batching server (the library's addition; the paper serves
+ * one query at a time on a CPU) ----
+ * A worker thread batches admitted requests as they arrive and runs each batch
+ * as one captured CUDA graph (gather from the device slot table, the whole
+ * Mode B search with each query's own k and C, result copy to pinned memory)
+ * on one of two lanes, so a batch can run while the next one forms. A
+ * request's result is the same as hntl_search of that query alone with its k
+ * and C (every stage is per query). */
+typedef struct hntl_server hntl_server;
+
+typedef struct {
+  uint64_t completed;  /* requests finished since creation or the last reset */
+  uint64_t batches;    /* batches launched */
+  double mean_batch;   /* requests per batch */
+  double p50_us, p99_us, max_us; /* latency from arrival (or submission) to completion */
+  uint32_t slots;      /* requests the memory budget admits at once */
+} hntl_server_stats;
+
+/* Create a server over `idx` (which must outlive it). mem_budget (bytes of
+ * device memory) pays first for two lanes (a search workspace for `batch`
+ * queries with k_max, C_max and nprobe, plus batch buffers), the rest for
+ * request slots (at most max_slots). ENOMEM if the budget cannot hold the
+ * lanes. Blocking (captures the graphs). */
+int hntl_server_create(const hntl_index* idx, size_t mem_budget, uint32_t max_slots, uint32_t batch, uint32_t nprobe,
+                       uint32_t k_max, uint32_t C_max, hntl_server** out);
+void hntl_server_free(hntl_server* server);
+
+/* Admit up to n requests (host queries n x d FP32, k and C per request, optional
+ * inclusive int64 ranges n x 2 for an index with attributes, optional arrival
+ * times in steady-clock nanoseconds for latency accounting). Requests are
+ * admitted in order while slots are free: *n_admitted tells how many; the
+ * call returns HNTL_EBUSY if fewer than n were admitted. tickets[i] identifies
+ * admitted request i. Blocking only for the upload of the admitted rows. */
+int hntl_server_submit(hntl_server* server, const float* h_queries, uint32_t n, const uint32_t* h_k,
+                       const uint32_t* h_C, const int64_t* h_ranges, const int64_t* h_arrival_ns, uint64_t* tickets,
+                       uint32_t* n_admitted);
+
+/* Collects many results at once. For each i < n with done[i] == 0 whose
+ * request has completed, copies its k ids and distances to row i of h_ids /
+ * h_dist (row stride `stride` >= k_max elements; either may be NULL to
+ * discard), releases the ticket and sets done[i] = 1 (entries already 1 are
+ * skipped). Waits up to timeout_ms for the rest; *n_done = results copied by
+ * this call. Returns HNTL_OK when every entry is done, HNTL_ETIMEOUT if some
+ * are still pending, HNTL_EINVAL for an unknown ticket. */
+int hntl_server_poll_many(hntl_server* server, const uint64_t* tickets, uint32_t n, int64_t* h_ids,
+                          float* h_dist, uint32_t stride, uint8_t* done, uint32_t timeout_ms, uint32_t* n_done);
+
+/* Wait up to timeout_ms for a request; on success copy its k ids and
+ * distances to host buffers and release the ticket. HNTL_ETIMEOUT if it is
+ * not done in time (the ticket stays valid), HNTL_EINVAL for an unknown ticket. */
+int hntl_server_poll(hntl_server* server, uint64_t ticket, int64_t* h_ids, float* h_dist, uint32_t timeout_ms);
+
+int hntl_server_get_stats(hntl_server* server, hntl_server_stats* out);
+int hntl_server_reset_stats(hntl_server* server);
 
 #ifdef __cplusplus
 }

@@ -119,13 +119,14 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
                                                const float* __restrict__ rho, const int64_t* __restrict__ attr_b,
                                                int r, int rp, const float* __restrict__ zq,
                                                const float* __restrict__ rhoq, const int64_t* __restrict__ filter,
-                                               float* __restrict__ tau) {
+                                               float* __restrict__ tau, const uint32_t* __restrict__ qC) {
   __shared__ uint32_t vals[kPilotRows];  // D bit patterns (non-negative floats order like unsigned)
   __shared__ uint32_t hist[2048];
   __shared__ __align__(8) float szq[RT];
   __shared__ uint32_t scratch[96];
   __shared__ uint32_t s_fill, s_bin, s_below, s_total;
   const int q = blockIdx.x;
+  if (qC) C = (int)qC[q];  // per-query pool size (mixed batches)
   if (threadIdx.x == 0) s_fill = 0;
   long long lo = 0, hi = 0;
   if (filter) {
@@ -473,12 +474,20 @@ __global__ void __launch_bounds__(kFinalThreads) k_final_select(
     const uint32_t* __restrict__ grain_rows, const Coords cz, const float* __restrict__ rho,
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r, int rp,
     const float* __restrict__ zq, const float* __restrict__ rhoq, const int64_t* __restrict__ filter,
-    uint32_t* __restrict__ cand_id, float* __restrict__ cand_d) {
+    uint32_t* __restrict__ cand_id, float* __restrict__ cand_d, const uint32_t* __restrict__ qC) {
   __shared__ SelSmem S;
   const int q = blockIdx.x;
   const uint32_t n = cnt[q];
-  uint32_t* oid = cand_id + (size_t)q * C;
+  uint32_t* oid = cand_id + (size_t)q * C;  // rows are C (the batch's largest pool) apart
   float* od = cand_d + (size_t)q * C;
+  if (qC) {  // mixed batch: this query's own pool size, the rest of its row padded
+    const int Cq = (int)qC[q];
+    for (int i = Cq + threadIdx.x; i < C; i += blockDim.x) {
+      oid[i] = kInvalidId;
+      od[i] = INFINITY;
+    }
+    C = Cq;
+  }
   if (n <= cap) {
     SurvivorSrc src{surv + (size_t)q * cap, n};
     select_topc(src, C, S, oid, od);

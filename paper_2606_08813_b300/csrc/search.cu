@@ -36,6 +36,22 @@ namespace hntl {
 namespace {
 
 
+// ------------------------------------------------------------------ bounded-wait self test
+
+// Waits, with the same bounded poll every tensor-core kernel uses, on an
+// mbarrier whose phase nothing ever completes; after `polls` polls it gives
+// up and records a timeout in the device error word, exactly as a stalled
+// pipeline would, and returns.
+__global__ void k_wait_selftest(uint32_t polls, int* __restrict__ err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, polls)) atomicOr(err, tc::kErrTimeout);
+}
+
 // ------------------------------------------------------------------ given probes
 
 // Routing distance ||q - mu_g||^2 of caller-supplied probes (one warp per
@@ -134,17 +150,30 @@ __global__ void k_bucket_scatter(const int32_t* __restrict__ probe, int nq, int 
 template <bool kBF16>
 __global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, const void* __restrict__ Xv, int d,
                                                 int C, int k, const uint32_t* __restrict__ cand_id,
-                                                int64_t* __restrict__ out_ids, float* __restrict__ out_d) {
+                                                int64_t* __restrict__ out_ids, float* __restrict__ out_d,
+                                                const uint32_t* __restrict__ qk, const uint32_t* __restrict__ qC) {
   extern __shared__ float sq[];  // [d]
   __shared__ unsigned long long keys[kMaxC];
   const int q = blockIdx.x;
+  const uint32_t* cid = cand_id + (size_t)q * C;  // rows C (the batch's largest pool) apart
+  int64_t* oid = out_ids + (size_t)q * k;         // rows k (the batch's largest k) apart
+  float* od = out_d + (size_t)q * k;
+  if (qC) {  // mixed batch: this query's own pool size and result count
+    const int kq = (int)qk[q];
+    for (int i = kq + threadIdx.x; i < k; i += blockDim.x) {
+      oid[i] = -1;
+      od[i] = INFINITY;
+    }
+    C = (int)qC[q];
+    k = kq;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int t = threadIdx.x; t < d; t += blockDim.x) sq[t] = Q[(size_t)q * d + t];
   __syncthreads();
   const int n2 = pow2_at_least(C);
   for (int c = warp; c < n2; c += 8) {
     unsigned long long key = ~0ull;
-    uint32_t id = c < C ? cand_id[(size_t)q * C + c] : kInvalidId;
+    uint32_t id = c < C ? cid[c] : kInvalidId;
     if (id != kInvalidId) {
       float acc = 0.f;
       if (!kBF16) {
@@ -196,8 +225,8 @@ __global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, con
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     unsigned long long kk = i < n2 ? keys[i] : ~0ull;
     bool ok = kk != ~0ull;
-    out_ids[(size_t)q * k + i] = ok ? (int64_t)(kk & 0xFFFFFFFFu) : -1;
-    out_d[(size_t)q * k + i] = ok ? __uint_as_float((uint32_t)(kk >> 32)) : INFINITY;
+    oid[i] = ok ? (int64_t)(kk & 0xFFFFFFFFu) : -1;
+    od[i] = ok ? __uint_as_float((uint32_t)(kk >> 32)) : INFINITY;
   }
 }
 
@@ -357,10 +386,10 @@ int launch_project_tc(const Index& I, uint32_t P, uint32_t nprobe, const Ws& w, 
 
 template <int RT, bool kFP8>
 void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, const int64_t* filter,
-                        cudaStream_t st, const std::function<void(int)>& mark) {
+                        cudaStream_t st, const std::function<void(int)>& mark, const uint32_t* qC) {
   const Coords cz{I.Zb, I.Z8b, I.scale};
   k_pilot<RT, kFP8><<<nq, 256, 0, st>>>(nprobe, C, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho,
-                                        I.attr_b, (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.tau);
+                                        I.attr_b, (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.tau, qC);
   mark(4);
   k_scan_filter<RT, kFP8><<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(
       I.blk_grain, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b, (int)I.r, (int)I.rp, w.gcnt, w.pair_off,
@@ -370,15 +399,17 @@ void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, 
   k_final_select<RT, kFP8><<<nq, kFinalThreads, 0, st>>>(nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of,
                                                          I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b,
                                                          (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id,
-                                                         w.cand_d);
+                                                         w.cand_d, qC);
 }
 
 template <int RT>
 void launch_scan_select_p(const Index& I, const Ws& w, int nq, int nprobe, int C, const int64_t* filter,
-                          cudaStream_t st, const std::function<void(int)>& mark) {
+                          cudaStream_t st, const std::function<void(int)>& mark, const uint32_t* qC) {
   // FP8 rows are read in lanes of 16 codes, so the FP8 kernels need RT >= 16
-  if (I.precision == HNTL_PREC_BF16_FP8) launch_scan_select<(RT < 16 ? 16 : RT), true>(I, w, nq, nprobe, C, filter, st, mark);
-  else launch_scan_select<RT, false>(I, w, nq, nprobe, C, filter, st, mark);
+  if (I.precision == HNTL_PREC_BF16_FP8)
+    launch_scan_select<(RT < 16 ? 16 : RT), true>(I, w, nq, nprobe, C, filter, st, mark, qC);
+  else
+    launch_scan_select<RT, false>(I, w, nq, nprobe, C, filter, st, mark, qC);
 }
 
 // Stage timing: CUDA events recorded on the search's stream between stages.
@@ -415,7 +446,8 @@ void profile_end(const StageEvents& ev) {
 
 int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe,
            const int64_t* filter, void* ws, size_t ws_bytes, int64_t* out_ids, float* out_d, uint32_t* cand_ids,
-           float* cand_d, int32_t* probe_out, cudaStream_t st, const int32_t* probe_in = nullptr) {
+           float* cand_d, int32_t* probe_out, cudaStream_t st, const int32_t* probe_in = nullptr,
+           const uint32_t* qk = nullptr, const uint32_t* qC = nullptr) {
   int rc = check_params(I, nq, k, C, nprobe);
   if (rc) return rc;
   if (filter && !I.has_attr) return fail(HNTL_EINVAL, "filter given but the index has no attribute column");
@@ -477,10 +509,10 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
   HNTL_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * nq, st));
   {
     const std::function<void(int)> mk = mark;
-    if (I.r <= 8) launch_scan_select_p<8>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
-    else if (I.r <= 16) launch_scan_select_p<16>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
-    else if (I.r <= 32) launch_scan_select_p<32>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
-    else launch_scan_select_p<64>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk);
+    if (I.r <= 8) launch_scan_select_p<8>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk, qC);
+    else if (I.r <= 16) launch_scan_select_p<16>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk, qC);
+    else if (I.r <= 32) launch_scan_select_p<32>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk, qC);
+    else launch_scan_select_p<64>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk, qC);
   }
   mark(6);
   {
@@ -490,9 +522,9 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
       HNTL_CUDA_TRY(cudaFuncSetAttribute(k_rerank<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     if (I.precision == HNTL_PREC_BF16_FP8)
-      k_rerank<true><<<nq, 256, smem, st>>>(Qd, I.Xh, (int)I.d, (int)C, (int)k, w.cand_id, out_ids, out_d);
+      k_rerank<true><<<nq, 256, smem, st>>>(Qd, I.Xh, (int)I.d, (int)C, (int)k, w.cand_id, out_ids, out_d, qk, qC);
     else
-      k_rerank<false><<<nq, 256, smem, st>>>(Qd, I.X, (int)I.d, (int)C, (int)k, w.cand_id, out_ids, out_d);
+      k_rerank<false><<<nq, 256, smem, st>>>(Qd, I.X, (int)I.d, (int)C, (int)k, w.cand_id, out_ids, out_d, qk, qC);
   }
   mark(7);
   if (prof) profile_end(ev);
@@ -643,6 +675,14 @@ int hntl_search_probes(const hntl_index* idx, const float* d_queries, uint32_t n
   if (!d_probe_in && nq) return hntl::fail(HNTL_EINVAL, "null probe list");
   return hntl::search(idx->I, d_queries, nq, k, C, nprobe, d_filter, d_ws, ws_bytes, d_out_ids, d_out_dist,
                       d_cand_ids, d_cand_dist, nullptr, static_cast<cudaStream_t>(stream), d_probe_in);
+}
+
+int hntl_selftest_wait_timeout(const hntl_index* idx, uint32_t polls, void* stream) {
+  hntl::clear_error();
+  if (!idx || polls == 0 || polls > (1u << 20)) return hntl::fail(HNTL_EINVAL, "polls must be in [1, 2^20]");
+  hntl::k_wait_selftest<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(polls, idx->I.d_err);
+  HNTL_CUDA_TRY(cudaGetLastError());
+  return HNTL_OK;
 }
 
 int hntl_device_status(const hntl_index* idx, int* status, int clear) {

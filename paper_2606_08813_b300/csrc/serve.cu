@@ -1,0 +1,548 @@
+// Continuous-batching serving loop over one index.
+//
+// Requests are admitted into slots of a device-resident table (query row, k,
+// C and attribute range stay on the device while the request lives). A host
+// worker thread forms batches from the admitted requests as they arrive and
+// launches them on one of two lanes; each lane owns a stream, a workspace
+// and a CUDA graph captured once at creation: gather the batch's slots from
+// the table, run the whole Mode B search with each query's own k and C (the
+// batch's largest k and C set the strides only), and copy the results to
+// pinned host memory. While one lane's batch runs on the GPU the worker fills
+// and launches the other, so requests that arrive meanwhile overlap with it.
+// A request's result does not depend on the batch it rides in: every stage is
+// per query (selections are total orders on (distance, id)).
+//
+// Memory admission: the budget first pays for the lanes (workspace and batch
+// buffers); what remains sets how many requests can be held at once. A
+// submission beyond the free slots is refused (its count of admitted
+// requests is short), and the caller retries after polling.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "hntl_internal.cuh"
+
+namespace hntl {
+
+int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe,
+           const int64_t* filter, void* ws, size_t ws_bytes, int64_t* out_ids, float* out_d, uint32_t* cand_ids,
+           float* cand_d, int32_t* probe_out, cudaStream_t st, const int32_t* probe_in, const uint32_t* qk,
+           const uint32_t* qC);
+
+namespace {
+
+__global__ void k_gather_batch(const uint32_t* __restrict__ slots, int B, int d, const float* __restrict__ slot_q,
+                               const uint32_t* __restrict__ slot_k, const uint32_t* __restrict__ slot_C,
+                               const int64_t* __restrict__ slot_range, float* __restrict__ Q, uint32_t* __restrict__ k,
+                               uint32_t* __restrict__ C, int64_t* __restrict__ F) {
+  const int i = blockIdx.x;
+  if (i >= B) return;
+  const uint32_t s = slots[i];
+  for (int t = threadIdx.x; t < d; t += blockDim.x) Q[(size_t)i * d + t] = slot_q[(size_t)s * d + t];
+  if (threadIdx.x == 0) {
+    k[i] = slot_k[s];
+    C[i] = slot_C[s];
+    if (F) {
+      F[2 * i] = slot_range[2 * (size_t)s];
+      F[2 * i + 1] = slot_range[2 * (size_t)s + 1];
+    }
+  }
+}
+
+// scatter a submission's rows (staged contiguously) into their slots
+__global__ void k_scatter_slots(int n, int d, const uint32_t* __restrict__ slots, const float* __restrict__ q,
+                                const uint32_t* __restrict__ k, const uint32_t* __restrict__ C,
+                                const int64_t* __restrict__ range, float* __restrict__ slot_q,
+                                uint32_t* __restrict__ slot_k, uint32_t* __restrict__ slot_C,
+                                int64_t* __restrict__ slot_range) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const uint32_t s = slots[i];
+  for (int t = threadIdx.x; t < d; t += blockDim.x) slot_q[(size_t)s * d + t] = q[(size_t)i * d + t];
+  if (threadIdx.x == 0) {
+    slot_k[s] = k[i];
+    slot_C[s] = C[i];
+    slot_range[2 * (size_t)s] = range[2 * i];
+    slot_range[2 * (size_t)s + 1] = range[2 * i + 1];
+  }
+}
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+  uint32_t slot = 0, k = 0;
+  int state = 0;  // 1 queued, 2 running, 3 done
+  int64_t arrival_ns = 0;
+  std::vector<int64_t> ids;
+  std::vector<float> dist;
+};
+
+struct Lane {
+  cudaStream_t st = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  uint32_t* d_slots = nullptr;
+  uint32_t* h_slots = nullptr;  // pinned
+  float* d_Q = nullptr;
+  uint32_t *d_k = nullptr, *d_C = nullptr;
+  int64_t* d_F = nullptr;
+  int64_t* d_ids = nullptr;
+  float* d_dist = nullptr;
+  int64_t* h_ids = nullptr;  // pinned
+  float* h_dist = nullptr;   // pinned
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  std::vector<uint64_t> tickets;
+  bool busy = false;
+};
+
+}  // namespace
+
+struct Server {
+  const Index* I = nullptr;
+  uint32_t B = 0, nprobe = 0, kmax = 0, Cmax = 0, nslots = 0;
+  // submission staging (pinned host -> device, then scattered into slots), one submission at a time
+  std::mutex submit_mu;
+  cudaStream_t up = nullptr;
+  float *h_sq = nullptr, *d_sq = nullptr;
+  uint32_t *h_ss = nullptr, *d_ss = nullptr, *h_sk = nullptr, *d_sk = nullptr, *h_sc = nullptr, *d_sc = nullptr;
+  int64_t *h_sr = nullptr, *d_sr = nullptr;
+  float* d_slot_q = nullptr;
+  uint32_t *d_slot_k = nullptr, *d_slot_C = nullptr;
+  int64_t* d_slot_range = nullptr;
+  Lane lanes[2];
+  std::vector<void*> dev, host;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::vector<uint32_t> free_slots;
+  std::unordered_map<uint64_t, Req> reqs;
+  uint64_t next_ticket = 1;
+  std::thread worker;
+  std::atomic<bool> stop{false};
+  std::vector<double> lat_us;
+  uint64_t batches = 0, batched = 0;
+  int worker_error = HNTL_OK;
+};
+
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
+}
+
+void retire(Server& S, Lane& L) {
+  // called with S.mu held, after L.done completed
+  for (size_t i = 0; i < L.tickets.size(); ++i) {
+    auto it = S.reqs.find(L.tickets[i]);
+    if (it == S.reqs.end()) continue;
+    Req& r = it->second;
+    r.ids.assign(L.h_ids + i * S.kmax, L.h_ids + i * S.kmax + r.k);
+    r.dist.assign(L.h_dist + i * S.kmax, L.h_dist + i * S.kmax + r.k);
+    r.state = 3;
+    S.free_slots.push_back(r.slot);
+    S.lat_us.push_back((double)(now_ns() - r.arrival_ns) / 1e3);
+  }
+  L.tickets.clear();
+  L.busy = false;
+}
+
+void worker_main(Server* S) {
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(S->I->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (!S->stop) {
+    bool progressed = false;
+    for (Lane& L : S->lanes) {
+      if (L.busy) {
+        cudaError_t e = cudaEventQuery(L.done);
+        if (e == cudaSuccess) {
+          retire(*S, L);
+          progressed = true;
+        } else if (e != cudaErrorNotReady) {
+          S->worker_error = HNTL_ECUDA;
+          S->stop = true;
+        }
+      }
+      if (!L.busy && !S->queue.empty()) {
+        const uint32_t n = (uint32_t)std::min<size_t>(S->B, S->queue.size());
+        uint32_t first_slot = 0;
+        for (uint32_t i = 0; i < n; ++i) {
+          const uint64_t t = S->queue.front();
+          S->queue.pop_front();
+          Req& r = S->reqs[t];
+          r.state = 2;
+          L.h_slots[i] = r.slot;
+          if (i == 0) first_slot = r.slot;
+          L.tickets.push_back(t);
+        }
+        for (uint32_t i = n; i < S->B; ++i) L.h_slots[i] = first_slot;  // padding rows, results discarded
+        cudaMemcpyAsync(L.d_slots, L.h_slots, sizeof(uint32_t) * S->B, cudaMemcpyHostToDevice, L.st);
+        cudaGraphLaunch(L.exec, L.st);
+        cudaEventRecord(L.done, L.st);
+        L.busy = true;
+        S->batches += 1;
+        S->batched += n;
+        progressed = true;
+      }
+    }
+    if (progressed) {
+      S->cv_done.notify_all();
+      continue;
+    }
+    const bool any_busy = S->lanes[0].busy || S->lanes[1].busy;
+    if (any_busy) {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
+    } else {
+      S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+    }
+  }
+  // drain lanes still on the GPU
+  for (Lane& L : S->lanes)
+    if (L.busy && cudaEventSynchronize(L.done) == cudaSuccess) retire(*S, L);
+  S->cv_done.notify_all();
+  lk.unlock();
+  if (prev >= 0) cudaSetDevice(prev);
+}
+
+void destroy(Server& S) {
+  if (S.worker.joinable()) {
+    S.stop = true;
+    S.cv_work.notify_all();
+    S.worker.join();
+  }
+  if (S.up) cudaStreamDestroy(S.up);
+  for (Lane& L : S.lanes) {
+    if (L.exec) cudaGraphExecDestroy(L.exec);
+    if (L.done) cudaEventDestroy(L.done);
+    if (L.st) cudaStreamDestroy(L.st);
+  }
+  for (void* p : S.dev) cudaFree(p);
+  for (void* p : S.host) cudaFreeHost(p);
+  S.dev.clear();
+  S.host.clear();
+}
+
+}  // namespace
+}  // namespace hntl
+
+struct hntl_server {
+  hntl::Server S;
+};
+
+using hntl::fail;
+
+extern "C" int hntl_server_create(const hntl_index* idx, size_t mem_budget, uint32_t max_slots, uint32_t batch,
+                                  uint32_t nprobe, uint32_t k_max, uint32_t C_max, hntl_server** out) {
+  hntl::clear_error();
+  if (!idx || !out) return fail(HNTL_EINVAL, "null argument");
+  *out = nullptr;
+  const hntl::Index& I = idx->I;
+  if (batch == 0 || max_slots == 0) return fail(HNTL_EINVAL, "batch and slots must be positive");
+  if (C_max < k_max) C_max = k_max;
+  const size_t ws = hntl::workspace_bytes(I, batch, k_max, C_max, nprobe);
+  if (!ws) return HNTL_EINVAL;
+  const size_t lane_bytes = ws + (size_t)batch * (I.d * 4 + 4 + 4 + 4 + 16 + k_max * 12) + 4096;
+  const size_t per_slot = (size_t)I.d * 4 + 8 + 16;
+  if (2 * lane_bytes + per_slot > mem_budget) return fail(HNTL_ENOMEM, "memory budget below one lane pair");
+  const uint32_t slots = (uint32_t)std::min<size_t>(max_slots, (mem_budget - 2 * lane_bytes) / per_slot);
+  hntl_server* h = new (std::nothrow) hntl_server();
+  if (!h) return fail(HNTL_ENOMEM, "host allocation");
+  hntl::Server& S = h->S;
+  S.I = &I;
+  S.B = batch;
+  S.nprobe = nprobe;
+  S.kmax = k_max;
+  S.Cmax = C_max;
+  S.nslots = slots;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(I.device);
+  int rc = HNTL_OK;
+  auto dalloc = [&](void** p, size_t bytes) {
+    if (rc) return;
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      rc = fail(HNTL_ENOMEM, "server: device allocation");
+      return;
+    }
+    S.dev.push_back(*p);
+  };
+  auto halloc = [&](void** p, size_t bytes) {
+    if (rc) return;
+    if (cudaMallocHost(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      rc = fail(HNTL_ENOMEM, "server: pinned allocation");
+      return;
+    }
+    S.host.push_back(*p);
+  };
+  dalloc((void**)&S.d_slot_q, (size_t)slots * I.d * 4);
+  dalloc((void**)&S.d_slot_k, (size_t)slots * 4);
+  dalloc((void**)&S.d_slot_C, (size_t)slots * 4);
+  dalloc((void**)&S.d_slot_range, (size_t)slots * 16);
+  dalloc((void**)&S.d_sq, (size_t)batch * I.d * 4);
+  dalloc((void**)&S.d_ss, batch * 4);
+  dalloc((void**)&S.d_sk, batch * 4);
+  dalloc((void**)&S.d_sc, batch * 4);
+  dalloc((void**)&S.d_sr, (size_t)batch * 16);
+  halloc((void**)&S.h_sq, (size_t)batch * I.d * 4);
+  halloc((void**)&S.h_ss, batch * 4);
+  halloc((void**)&S.h_sk, batch * 4);
+  halloc((void**)&S.h_sc, batch * 4);
+  halloc((void**)&S.h_sr, (size_t)batch * 16);
+  if (!rc && cudaStreamCreateWithFlags(&S.up, cudaStreamNonBlocking) != cudaSuccess)
+    rc = fail(HNTL_ECUDA, "server: upload stream");
+  for (hntl::Lane& L : S.lanes) {
+    dalloc((void**)&L.d_slots, batch * 4);
+    dalloc((void**)&L.d_Q, (size_t)batch * I.d * 4);
+    dalloc((void**)&L.d_k, batch * 4);
+    dalloc((void**)&L.d_C, batch * 4);
+    if (I.has_attr) dalloc((void**)&L.d_F, (size_t)batch * 16);
+    dalloc((void**)&L.d_ids, (size_t)batch * k_max * 8);
+    dalloc((void**)&L.d_dist, (size_t)batch * k_max * 4);
+    dalloc(&L.ws, ws);
+    L.ws_bytes = ws;
+    halloc((void**)&L.h_slots, batch * 4);
+    halloc((void**)&L.h_ids, (size_t)batch * k_max * 8);
+    halloc((void**)&L.h_dist, (size_t)batch * k_max * 4);
+  }
+  if (!rc) {
+    // neutral slot contents so the warm-up and padding rows are valid requests
+    std::vector<uint32_t> kk(slots, k_max), cc(slots, C_max);
+    std::vector<int64_t> rr(2 * (size_t)slots);
+    for (uint32_t i = 0; i < slots; ++i) {
+      rr[2 * i] = INT64_MIN;
+      rr[2 * i + 1] = INT64_MAX;
+    }
+    cudaMemset(S.d_slot_q, 0, (size_t)slots * I.d * 4);
+    cudaMemcpy(S.d_slot_k, kk.data(), slots * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(S.d_slot_C, cc.data(), slots * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(S.d_slot_range, rr.data(), (size_t)slots * 16, cudaMemcpyHostToDevice);
+  }
+  for (hntl::Lane& L : S.lanes) {
+    if (rc) break;
+    if (cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) {
+      rc = fail(HNTL_ECUDA, "server: stream/event");
+      break;
+    }
+    cudaMemset(L.d_slots, 0, batch * 4);
+    auto record = [&]() -> int {
+      hntl::k_gather_batch<<<batch, 128, 0, L.st>>>(L.d_slots, (int)batch, (int)I.d, S.d_slot_q, S.d_slot_k,
+                                                    S.d_slot_C, S.d_slot_range, L.d_Q, L.d_k, L.d_C, L.d_F);
+      int r = hntl::search(I, L.d_Q, batch, k_max, C_max, nprobe, L.d_F, L.ws, L.ws_bytes, L.d_ids, L.d_dist,
+                           nullptr, nullptr, nullptr, L.st, nullptr, L.d_k, L.d_C);
+      if (r) return r;
+      if (cudaMemcpyAsync(L.h_ids, L.d_ids, (size_t)batch * k_max * 8, cudaMemcpyDeviceToHost, L.st) ||
+          cudaMemcpyAsync(L.h_dist, L.d_dist, (size_t)batch * k_max * 4, cudaMemcpyDeviceToHost, L.st))
+        return fail(HNTL_ECUDA, "server: result copies");
+      return HNTL_OK;
+    };
+    // one eager run (sets kernel attributes), then capture the same sequence as a graph
+    if ((rc = record())) break;
+    if (cudaStreamSynchronize(L.st) != cudaSuccess) {
+      rc = fail(HNTL_ECUDA, "server: warm-up batch");
+      break;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(L.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = fail(HNTL_ECUDA, "server: begin capture");
+      break;
+    }
+    int rr = record();
+    cudaError_t ce = cudaStreamEndCapture(L.st, &g);
+    if (rr || ce != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      rc = rr ? rr : fail(HNTL_ECUDA, std::string("server: capture: ") + cudaGetErrorString(ce));
+      break;
+    }
+    ce = cudaGraphInstantiate(&L.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      rc = fail(HNTL_ECUDA, std::string("server: instantiate: ") + cudaGetErrorString(ce));
+      break;
+    }
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  if (rc) {
+    hntl::destroy(S);
+    delete h;
+    return rc;
+  }
+  for (uint32_t i = slots; i > 0; --i) S.free_slots.push_back(i - 1);
+  S.worker = std::thread(hntl::worker_main, &S);
+  *out = h;
+  return HNTL_OK;
+}
+
+extern "C" void hntl_server_free(hntl_server* h) {
+  if (!h) return;
+  hntl::destroy(h->S);
+  delete h;
+}
+
+extern "C" int hntl_server_submit(hntl_server* h, const float* h_queries, uint32_t n, const uint32_t* h_k,
+                                  const uint32_t* h_C, const int64_t* h_ranges, const int64_t* h_arrival_ns,
+                                  uint64_t* tickets, uint32_t* n_admitted) {
+  hntl::clear_error();
+  if (!h || !n_admitted || (n && (!h_queries || !h_k || !h_C || !tickets))) return fail(HNTL_EINVAL, "null argument");
+  hntl::Server& S = h->S;
+  *n_admitted = 0;
+  if (S.worker_error) return fail(S.worker_error, "the serving worker stopped on a CUDA error");
+  if (h_ranges && !S.I->has_attr) return fail(HNTL_EINVAL, "ranges given but the index has no attribute column");
+  for (uint32_t i = 0; i < n; ++i)
+    if (h_k[i] < 1 || h_k[i] > S.kmax || std::max(h_C[i], h_k[i]) > S.Cmax)
+      return fail(HNTL_EINVAL, "k or C beyond the server's k_max / C_max");
+  std::lock_guard<std::mutex> sub(S.submit_mu);
+  std::unique_lock<std::mutex> lk(S.mu);
+  const uint32_t take = (uint32_t)std::min<size_t>(n, S.free_slots.size());
+  std::vector<uint32_t> slots(take);
+  for (uint32_t i = 0; i < take; ++i) {
+    slots[i] = S.free_slots.back();
+    S.free_slots.pop_back();
+  }
+  lk.unlock();
+  // per-request state into the device slot table, in chunks of one batch
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(S.I->device);
+  const int64_t t0 = hntl::now_ns();
+  const uint32_t d = S.I->d;
+  for (uint32_t c0 = 0; c0 < take; c0 += S.B) {
+    const uint32_t m = std::min(S.B, take - c0);
+    std::memcpy(S.h_sq, h_queries + (size_t)c0 * d, (size_t)m * d * 4);
+    for (uint32_t i = 0; i < m; ++i) {
+      S.h_ss[i] = slots[c0 + i];
+      S.h_sk[i] = h_k[c0 + i];
+      S.h_sc[i] = std::max(h_C[c0 + i], h_k[c0 + i]);
+      S.h_sr[2 * i] = h_ranges ? h_ranges[2 * (c0 + i)] : INT64_MIN;
+      S.h_sr[2 * i + 1] = h_ranges ? h_ranges[2 * (c0 + i) + 1] : INT64_MAX;
+    }
+    cudaMemcpyAsync(S.d_sq, S.h_sq, (size_t)m * d * 4, cudaMemcpyHostToDevice, S.up);
+    cudaMemcpyAsync(S.d_ss, S.h_ss, m * 4, cudaMemcpyHostToDevice, S.up);
+    cudaMemcpyAsync(S.d_sk, S.h_sk, m * 4, cudaMemcpyHostToDevice, S.up);
+    cudaMemcpyAsync(S.d_sc, S.h_sc, m * 4, cudaMemcpyHostToDevice, S.up);
+    cudaMemcpyAsync(S.d_sr, S.h_sr, (size_t)m * 16, cudaMemcpyHostToDevice, S.up);
+    hntl::k_scatter_slots<<<m, 128, 0, S.up>>>((int)m, (int)d, S.d_ss, S.d_sq, S.d_sk, S.d_sc, S.d_sr, S.d_slot_q,
+                                               S.d_slot_k, S.d_slot_C, S.d_slot_range);
+    if (cudaStreamSynchronize(S.up) != cudaSuccess) {
+      if (prev >= 0) cudaSetDevice(prev);
+      return fail(HNTL_ECUDA, "server: slot upload");
+    }
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  lk.lock();
+  for (uint32_t i = 0; i < take; ++i) {
+    const uint64_t t = S.next_ticket++;
+    hntl::Req r;
+    r.slot = slots[i];
+    r.k = h_k[i];
+    r.state = 1;
+    r.arrival_ns = h_arrival_ns ? h_arrival_ns[i] : t0;
+    S.reqs.emplace(t, std::move(r));
+    S.queue.push_back(t);
+    tickets[i] = t;
+  }
+  lk.unlock();
+  S.cv_work.notify_one();
+  *n_admitted = take;
+  return take < n ? HNTL_EBUSY : HNTL_OK;
+}
+
+extern "C" int hntl_server_poll(hntl_server* h, uint64_t ticket, int64_t* h_ids, float* h_dist, uint32_t timeout_ms) {
+  hntl::clear_error();
+  if (!h) return fail(HNTL_EINVAL, "null server");
+  hntl::Server& S = h->S;
+  std::unique_lock<std::mutex> lk(S.mu);
+  auto it = S.reqs.find(ticket);
+  if (it == S.reqs.end()) return fail(HNTL_EINVAL, "unknown ticket");
+  const bool ok = S.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
+    auto jt = S.reqs.find(ticket);
+    return jt != S.reqs.end() && jt->second.state == 3;
+  });
+  if (!ok) return S.worker_error ? fail(S.worker_error, "the serving worker stopped") : HNTL_ETIMEOUT;
+  hntl::Req& r = S.reqs[ticket];
+  if (h_ids) std::copy(r.ids.begin(), r.ids.end(), h_ids);
+  if (h_dist) std::copy(r.dist.begin(), r.dist.end(), h_dist);
+  S.reqs.erase(ticket);
+  return HNTL_OK;
+}
+
+extern "C" int hntl_server_poll_many(hntl_server* h, const uint64_t* tickets, uint32_t n, int64_t* h_ids,
+                                     float* h_dist, uint32_t stride, uint8_t* done, uint32_t timeout_ms,
+                                     uint32_t* n_done) {
+  hntl::clear_error();
+  if (!h || !n_done || (n && (!tickets || !done))) return fail(HNTL_EINVAL, "null argument");
+  hntl::Server& S = h->S;
+  *n_done = 0;
+  if ((h_ids || h_dist) && stride < S.kmax) return fail(HNTL_EINVAL, "result stride below k_max");
+  std::unique_lock<std::mutex> lk(S.mu);
+  for (uint32_t i = 0; i < n; ++i)
+    if (!done[i] && S.reqs.find(tickets[i]) == S.reqs.end()) return fail(HNTL_EINVAL, "unknown ticket");
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  uint32_t got = 0;
+  for (;;) {
+    for (uint32_t i = 0; i < n; ++i) {
+      if (done[i]) continue;
+      auto it = S.reqs.find(tickets[i]);
+      if (it == S.reqs.end() || it->second.state != 3) continue;
+      hntl::Req& r = it->second;
+      if (h_ids) std::copy(r.ids.begin(), r.ids.end(), h_ids + (size_t)i * stride);
+      if (h_dist) std::copy(r.dist.begin(), r.dist.end(), h_dist + (size_t)i * stride);
+      S.reqs.erase(it);
+      done[i] = 1;
+      ++got;
+    }
+    uint32_t left = 0;
+    for (uint32_t i = 0; i < n; ++i) left += done[i] ? 0 : 1;
+    if (!left) break;
+    if (S.worker_error) {
+      *n_done = got;
+      return fail(S.worker_error, "the serving worker stopped");
+    }
+    if (S.cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+      *n_done = got;
+      return HNTL_ETIMEOUT;
+    }
+  }
+  *n_done = got;
+  return HNTL_OK;
+}
+
+extern "C" int hntl_server_get_stats(hntl_server* h, hntl_server_stats* out) {
+  hntl::clear_error();
+  if (!h || !out) return fail(HNTL_EINVAL, "null argument");
+  hntl::Server& S = h->S;
+  std::lock_guard<std::mutex> lk(S.mu);
+  std::vector<double> v = S.lat_us;
+  out->completed = v.size();
+  out->batches = S.batches;
+  out->mean_batch = S.batches ? (double)S.batched / (double)S.batches : 0.0;
+  out->slots = S.nslots;
+  out->p50_us = out->p99_us = out->max_us = 0.0;
+  if (!v.empty()) {
+    std::sort(v.begin(), v.end());
+    out->p50_us = v[(size_t)(0.50 * (v.size() - 1))];
+    out->p99_us = v[(size_t)(0.99 * (v.size() - 1))];
+    out->max_us = v.back();
+  }
+  return HNTL_OK;
+}
+
+extern "C" int hntl_server_reset_stats(hntl_server* h) {
+  hntl::clear_error();
+  if (!h) return fail(HNTL_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(h->S.mu);
+  h->S.lat_us.clear();
+  h->S.batches = h->S.batched = 0;
+  return HNTL_OK;
+}

@@ -403,3 +403,110 @@ class Router:
         _check(lib.hntl_router_route(self._h, index.handle, _ptr(Q), nq, nprobe, float(tau), _ptr(self._ws),
                                      self._ws.numel(), _ptr(probe), _ptr(nfb), _stream(stream)))
         return probe, nfb
+
+
+lib.hntl_selftest_wait_timeout.argtypes = [_P, _U32, _P]
+lib.hntl_server_create.argtypes = [_P, _SZ, _U32, _U32, _U32, _U32, _U32, ctypes.POINTER(_P)]
+lib.hntl_server_free.argtypes = [_P]
+lib.hntl_server_free.restype = None
+lib.hntl_server_submit.argtypes = [_P, _P, _U32, _P, _P, _P, _P, _P, ctypes.POINTER(_U32)]
+lib.hntl_server_poll.argtypes = [_P, ctypes.c_uint64, _P, _P, _U32]
+lib.hntl_server_reset_stats.argtypes = [_P]
+lib.hntl_server_poll_many.argtypes = [_P, _P, _U32, _P, _P, _U32, _P, _U32, ctypes.POINTER(_U32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("mean_batch", ctypes.c_double),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double),
+                ("slots", ctypes.c_uint32)]
+
+
+lib.hntl_server_get_stats.argtypes = [_P, ctypes.POINTER(ServerStats)]
+
+
+def selftest_wait_timeout(index: Index, polls: int = 64):
+    _check(lib.hntl_selftest_wait_timeout(index.handle, int(polls), None))
+
+
+class Server:
+    """Continuous-batching server over an index (see hntl_server_* in include/hntl.h)."""
+
+    def __init__(self, index: Index, mem_budget: int, max_slots: int, batch: int, nprobe: int, k_max: int,
+                 C_max: int):
+        h = _P()
+        _check(lib.hntl_server_create(index.handle, int(mem_budget), max_slots, batch, nprobe, k_max, C_max,
+                                      ctypes.byref(h)))
+        self._h = h
+        self.index = index
+        self.d = int(index.desc.d)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.hntl_server_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, Q, k, C, ranges=None, arrival_ns=None):
+        """Admit requests (numpy: Q [n, d] f32, k [n], C [n] uint32, ranges [n, 2] int64, arrival_ns [n]
+        int64). Returns the tickets of the admitted prefix (length < n when slots ran out)."""
+        import numpy as np
+
+        Q = np.ascontiguousarray(Q, dtype=np.float32)
+        n = Q.shape[0]
+        k = np.ascontiguousarray(k, dtype=np.uint32)
+        C = np.ascontiguousarray(C, dtype=np.uint32)
+        R = None if ranges is None else np.ascontiguousarray(ranges, dtype=np.int64)
+        A = None if arrival_ns is None else np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        tickets = np.zeros(n, dtype=np.uint64)
+        got = ctypes.c_uint32(0)
+        rc = lib.hntl_server_submit(self._h, Q.ctypes.data_as(_P), n, k.ctypes.data_as(_P), C.ctypes.data_as(_P),
+                                    None if R is None else R.ctypes.data_as(_P),
+                                    None if A is None else A.ctypes.data_as(_P), tickets.ctypes.data_as(_P),
+                                    ctypes.byref(got))
+        if rc not in (OK, EBUSY):
+            raise HntlError(rc, last_error())
+        return tickets[: got.value]
+
+    def poll(self, ticket, k, timeout_ms=10000):
+        """(ids int64 [k], dist f32 [k]), or None on timeout."""
+        import numpy as np
+
+        ids = np.zeros(k, dtype=np.int64)
+        dist = np.zeros(k, dtype=np.float32)
+        rc = lib.hntl_server_poll(self._h, int(ticket), ids.ctypes.data_as(_P), dist.ctypes.data_as(_P),
+                                  int(timeout_ms))
+        if rc == ETIMEOUT:
+            return None
+        _check(rc)
+        return ids, dist
+
+    def poll_many(self, tickets, done, ids=None, dist=None, timeout_ms=0):
+        """Collect every completed request among `tickets` (numpy uint64) whose
+        `done` flag (numpy uint8, updated in place) is 0; ids / dist (numpy
+        [n, k_max] int64 / float32) receive the rows, or None to discard.
+        Returns the number collected by this call."""
+        import numpy as np
+
+        assert tickets.dtype == np.uint64 and done.dtype == np.uint8 and tickets.flags.c_contiguous
+        stride = 0 if ids is None and dist is None else (ids if ids is not None else dist).shape[1]
+        got = ctypes.c_uint32(0)
+        rc = lib.hntl_server_poll_many(self._h, tickets.ctypes.data_as(_P), len(tickets),
+                                       None if ids is None else ids.ctypes.data_as(_P),
+                                       None if dist is None else dist.ctypes.data_as(_P), stride,
+                                       done.ctypes.data_as(_P), int(timeout_ms), ctypes.byref(got))
+        if rc not in (OK, ETIMEOUT):
+            raise HntlError(rc, last_error())
+        return got.value
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib.hntl_server_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def reset_stats(self):
+        _check(lib.hntl_server_reset_stats(self._h))
