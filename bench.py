@@ -490,6 +490,121 @@ def run_ours(a, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def knn_ids_bf16(X: torch.Tensor, Q: torch.Tensor, k: int, qblock: int = 2048, chunk: int = 1 << 20):
+    """Approximate top-k neighbour ids by a BF16 matmul (training labels only)."""
+    Xb = X.to(torch.bfloat16)
+    xn = (X * X).sum(1)
+    out = []
+    for q0 in range(0, Q.shape[0], qblock):
+        Qb = Q[q0:q0 + qblock]
+        best_d = torch.full((Qb.shape[0], k), float("inf"), device=Q.device)
+        best_i = torch.zeros((Qb.shape[0], k), dtype=torch.int64, device=Q.device)
+        for s in range(0, X.shape[0], chunk):
+            dd = xn[s:s + chunk][None] - 2.0 * (Qb.to(torch.bfloat16) @ Xb[s:s + chunk].T).float()
+            v, i = torch.topk(dd, k, dim=1, largest=False)
+            cd, ci = torch.cat([best_d, v], 1), torch.cat([best_i, i + s], 1)
+            best_d, j = torch.topk(cd, k, dim=1, largest=False)
+            best_i = torch.gather(ci, 1, j)
+        out.append(best_i)
+    return torch.cat(out)
+
+
+def run_router(a, world, rank, local):
+    """Learned grain router at its full configuration: train the MLP with the
+    library's BF16 kernels on labels the method generates (the grains holding
+    each training query's top-10), then compare recall@10 with centroid
+    routing at equal nprobe (equal grain sizes: equal probed rows)."""
+    from paper_2606_08813_b300 import build_lib
+
+    build_lib.build()
+    from paper_2606_08813_b300 import hntl
+
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    w = dict(synth.WORKLOADS["router-5m"])
+    sd = synth.seeds(w["seed"])
+    model = synth.make_cluster_model(w["n"], w["d"], w["n_clusters"], sizes=w["sizes"], seed=sd["data"])
+    X, _ = synth.sample_points(model, sd["data"] + 11, device=dev, chunk=65536)
+    Qtr, _ = synth.sample_queries(model, a.router_train, sd["router"], device=dev, chunk=65536)
+    Qev, _ = synth.sample_queries(model, w["nq"], sd["queries"], device=dev, chunk=65536)
+    G, d = w["G"], w["d"]
+    t0 = time.perf_counter()
+    gi = hntl.Index.build(X, G, w["r"], u=synth.uniforms(G, sd["kmeans"]).numpy(), seed=sd["kmeans"])
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    exp = gi.export()
+    assign_np = np.empty(w["n"], dtype=np.int64)
+    assign_np[exp["ids"].astype(np.int64)] = np.repeat(np.arange(G), np.diff(exp["grain_off"]))
+    assign = torch.from_numpy(assign_np).to(dev)
+    del exp
+    t0 = time.perf_counter()
+    nb_tr = knn_ids_bf16(X, Qtr, 10)
+    torch.cuda.synchronize()
+    label_s = time.perf_counter() - t0
+    lab = assign[nb_tr]  # [n_train, 10] grain of each neighbour
+    # MLP d -> 1024 -> 1024 -> G, uniform(+-1/sqrt(fan_in)) weights, zero biases
+    rng = np.random.default_rng(sd["router"])
+    params = []
+    for fo, fi in ((a.router_hidden, d), (a.router_hidden, a.router_hidden), (G, a.router_hidden)):
+        lim = 1.0 / np.sqrt(fi)
+        params += [rng.uniform(-lim, lim, (fo, fi)).astype(np.float32), np.zeros(fo, np.float32)]
+    B = a.router_batch
+    rt = hntl.Router(params, max_batch=B)
+    flop_per_sample = 6 * (d * a.router_hidden + a.router_hidden * a.router_hidden + a.router_hidden * G)
+    gen = torch.Generator(device=dev).manual_seed(sd["router"])
+    T = torch.empty(B, G, device=dev)
+    ones = torch.full((B, 10), 0.1, device=dev)
+    losses = []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    steps = 0
+    ev[0].record()
+    for ep in range(a.router_epochs):
+        perm = torch.randperm(Qtr.shape[0], generator=gen, device=dev)
+        lo = torch.zeros(1, device=dev)
+        for s0 in range(0, Qtr.shape[0] - B + 1, B):
+            idx = perm[s0:s0 + B]
+            T.zero_()
+            T.scatter_add_(1, lab[idx], ones)
+            rt.step(Qtr[idx].contiguous(), T, lr=a.router_lr, wd=0.01, loss=lo)
+            steps += 1
+        losses.append(float(lo.item()) * B / (Qtr.shape[0] // B * B))
+    ev[1].record()
+    torch.cuda.synchronize()
+    train_ms = ev[0].elapsed_time(ev[1])
+    # evaluation: exact ground truth, centroid vs learned routing
+    truth = exact_topk(X, Qev, 10)
+    out = []
+    for nprobe in (4, 8, 16, 32, 64):
+        ids_c, _ = gi.search(Qev, 10, w["C"], nprobe)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        probes, nfb = rt.route(gi, Qev, nprobe, tau=0.0)
+        e1.record()
+        ids_l, _ = hntl.search_probes(gi, Qev, probes, 10, w["C"])
+        torch.cuda.synchronize()
+        out.append({"nprobe": nprobe, "recall_centroid": round(recall_at_k(ids_c, truth), 4),
+                    "recall_learned": round(recall_at_k(ids_l, truth), 4),
+                    "route_ms_per_20k": round(e0.elapsed_time(e1), 3)})
+        out[-1]["gain"] = round(out[-1]["recall_learned"] - out[-1]["recall_centroid"], 4)
+        print(f"router nprobe {nprobe}: {out[-1]}", file=sys.stderr)
+    samples = steps * B
+    _, bf16, src = _peaks()
+    tflops = samples * flop_per_sample / (train_ms / 1e3) / 1e12
+    line = {"metric": "learned-router recall@10 gain over centroid routing at equal nprobe", "value":
+            max(o["gain"] for o in out), "unit": "recall points", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "router-5m", "N": w["n"], "d": d, "G": G, "r": w["r"], "C": w["C"],
+                       "mlp": f"{d}-{a.router_hidden}-{a.router_hidden}-{G}", "train_queries": Qtr.shape[0],
+                       "eval_queries": Qev.shape[0], "epochs": a.router_epochs, "batch": B, "lr": a.router_lr,
+                       "index_build_s": round(build_s, 2), "label_s": round(label_s, 2)},
+            "by_nprobe": out, "loss_by_epoch": [round(x, 4) for x in losses],
+            "train": {"samples_per_s": round(samples / (train_ms / 1e3), 1), "ms_per_step": round(train_ms / steps, 4),
+                      "achieved_tflops": round(tflops, 1), "peak_tflops": bf16, "frac": round(tflops / bf16, 4),
+                      "peak_source": src,
+                      "note": "forward + backward + AdamW, 6 flops per weight per sample (GEMMs only)"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(a, world, rank, local):
     if rank != 0:
         return
@@ -555,6 +670,11 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-recall", type=int, default=1536, help="served requests checked against brute force")
     ap.add_argument("--serve-p99-ms", type=float, default=50.0)
+    ap.add_argument("--router-train", type=int, default=200_000)
+    ap.add_argument("--router-epochs", type=int, default=8)
+    ap.add_argument("--router-batch", type=int, default=1024)
+    ap.add_argument("--router-hidden", type=int, default=1024)
+    ap.add_argument("--router-lr", type=float, default=1e-3)
     ap.add_argument("--profile-mode", action="store_true",
                     help="for ncu captures: free the raw rows after the build; no recall, CPU baseline or e2e")
     a = ap.parse_args()
@@ -564,6 +684,9 @@ def main():
     try:
         if a.impl == "reference":
             run_reference(a, world, rank, local)
+        elif a.workload == "router-5m":
+            if rank == 0:
+                run_router(a, world, rank, local)
         else:
             run_ours(a, world, rank, local)
     finally:

@@ -540,6 +540,8 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   if (prm) P = *prm;
   const uint32_t precision = P.precision;
   if (precision != HNTL_PREC_FP32 && precision != HNTL_PREC_BF16_FP8) return fail(HNTL_EINVAL, "bad precision");
+  if (precision == HNTL_PREC_BF16_FP8 && d % 8)  // BF16 rows move in 16-byte pieces
+    return fail(HNTL_EINVAL, "the precision form needs d to be a multiple of 8");
   const uint32_t max_iter = P.max_iter ? P.max_iter : 10;
   const uint32_t pca_iters = P.pca_iters ? P.pca_iters : 12;
   const uint64_t n_t = std::min<uint64_t>(N, P.n_train ? P.n_train : 256ull * G);

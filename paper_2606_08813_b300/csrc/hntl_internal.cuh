@@ -55,6 +55,7 @@ struct Index {
   float* scale = nullptr;        // [G] FP8 scale per grain
   float* rho = nullptr;          // [n_blocks][128] residual norms
   float* blk_rho_min = nullptr;  // [n_blocks] smallest residual norm of a block's real rows (+inf if none)
+  float* crow = nullptr;         // [n_blocks][128] ||z_i||^2 + rho_i of the decoded row (precision form)
   uint32_t* ids = nullptr;       // [n_blocks][128] original ids
   int64_t* attr_b = nullptr;     // [n_blocks][128] attributes in block order
   float* X = nullptr;            // [n][d] FP32 raw rows, id order
@@ -63,11 +64,15 @@ struct Index {
   // derived at load/build (finalize_index)
   float* mnorm = nullptr;        // [G] ||mu_g||^2 (of the BF16 centres in the precision form)
   uint16_t* Mh = nullptr;        // [G][d] BF16 centres (precision form)
+  uint16_t* Mrep = nullptr;      // [G][8][d] the same centres negated, each row 8 times (precision form)
+  int num_sms = 148;             // streaming multiprocessors of the index's device
   uint16_t* Uh = nullptr;        // [G][r][d] BF16 bases (precision form)
   float* gram = nullptr;         // [G][r][r] U_g U_g^T of the BF16 bases (precision form)
   int* d_err = nullptr;          // device error word (bounded waits that gave up)
   bool tc_route = false;         // tensor-core routing available (TMA map built)
   CUtensorMap mapM;              // TMA map of the centres (FP32 or BF16), 256-row boxes
+  CUtensorMap mapMrep, mapU;  // precision form: replicated -mu_b (8-row box), bases (r-row box)
+  bool tc_proj = false;
 
   // host copies used for workspace sizing
   std::vector<uint32_t> h_blk_off;

@@ -108,6 +108,8 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
   if (r > (uint32_t)kMaxR) return fail(HNTL_EINVAL, "tangent dimension r > 64 is not supported");
   if (G > kMaxG) return fail(HNTL_EINVAL, "more than 8192 grains is not supported");
   if (precision != HNTL_PREC_FP32 && precision != HNTL_PREC_BF16_FP8) return fail(HNTL_EINVAL, "bad precision");
+  if (precision == HNTL_PREC_BF16_FP8 && d % 8)  // BF16 rows move in 16-byte pieces
+    return fail(HNTL_EINVAL, "the precision form needs d to be a multiple of 8");
   bool xbf16 = flags & kFlagXbf16;
   if (precision == HNTL_PREC_FP32 && xbf16) return fail(HNTL_EINVAL, "file holds BF16 raw rows; load it as BF16_FP8");
   if (precision == HNTL_PREC_BF16_FP8 && !((flags & kFlagFp8) && xbf16))

@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(128) k_route_tc(const __grid_constant__ CUtens
   __shared__ __align__(8) uint64_t full[kRStages], empty[kRStages], done;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
+  __shared__ float smn[kRTN];  // ||mu||^2 of this tile's centres
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tc::tmem_alloc(&tmem_base, kRTN);
   if (tid == 32) {
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(128) k_route_tc(const __grid_constant__ CUtens
     }
     if (ok) tc::mma_commit(&done);
   }
+  for (int i = tid; i < kRTN; i += 128) smn[i] = g0 + i < G ? mn[g0 + i] : 0.f;
   const bool waited = tc::mbar_wait(&done, 0);
   const bool failed = __syncthreads_or(!waited || s_fail);
   tc::fence_after_sync();
@@ -104,16 +106,29 @@ __global__ void __launch_bounds__(128) k_route_tc(const __grid_constant__ CUtens
     const int row = warp * 32 + lane;
     const int q = q0 + row;
     const float qv = q < nq ? qn[q] : 0.f;
+    const bool vec = (G & 3) == 0;  // rows of Dt start on 16-byte boundaries
 #pragma unroll 1
     for (int c0 = 0; c0 < kRTN; c0 += 32) {
       float v[32];
       tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
       if (q < nq) {
-        float* out = Dt + (size_t)q * G;
+        float* out = Dt + (size_t)q * G + g0 + c0;
+        const int lim = G - (g0 + c0);  // columns of this chunk inside the matrix
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int g = g0 + c0 + j;
-          if (g < G) out[g] = (qv + mn[g]) - 2.f * v[j];
+        for (int j = 0; j < 32; j += 4) {
+          float4 o;
+          o.x = (qv + smn[c0 + j]) - 2.f * v[j];
+          o.y = (qv + smn[c0 + j + 1]) - 2.f * v[j + 1];
+          o.z = (qv + smn[c0 + j + 2]) - 2.f * v[j + 2];
+          o.w = (qv + smn[c0 + j + 3]) - 2.f * v[j + 3];
+          if (vec && j + 4 <= lim) {
+            *reinterpret_cast<float4*>(out + j) = o;
+          } else {
+            if (j < lim) out[j] = o.x;
+            if (j + 1 < lim) out[j + 1] = o.y;
+            if (j + 2 < lim) out[j + 2] = o.z;
+            if (j + 3 < lim) out[j + 3] = o.w;
+          }
         }
       }
     }
@@ -134,6 +149,8 @@ __device__ __forceinline__ uint32_t ordered_key(float x) {  // monotone map of a
 constexpr int kRefineThreads = 256;
 constexpr int kRefineCap = 1024;
 
+constexpr int kRefineSmemMax = (8192 + 2 * kMaxG) * 4;  // d <= 8192 on this path
+
 // One CTA per query: margin shortlist over the approximate distances, exact
 // direct-form distances of the shortlist, the nprobe smallest (distance, g).
 // In the precision form q and the centres are BF16 values (Mh).
@@ -145,7 +162,10 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
                                                                  const float* __restrict__ Dt, int G, int d,
                                                                  int nprobe, int32_t* __restrict__ probe,
                                                                  float* __restrict__ probe_d) {
-  extern __shared__ float sq[];  // [d] query (BF16-rounded in the precision form)
+  // dynamic: [d] query (BF16-rounded in the precision form), then the ordered
+  // keys of approx + margin and approx - margin of every centre ([G] each), so
+  // the row of approximate distances is read from memory once
+  extern __shared__ float sq[];
   __shared__ uint32_t hist[2048];
   __shared__ unsigned long long keys[kRefineCap];
   __shared__ uint32_t scratch[96];
@@ -159,7 +179,15 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
   }
   const float qv = qn[q];
   const float* Dq = Dt + (size_t)q * G;
-  auto margin = [&](int g) { return 0.0078125f * sqrtf(qv * mn[g]) + 1.52587890625e-5f * (qv + mn[g]); };
+  uint32_t* khi = reinterpret_cast<uint32_t*>(sq + d);
+  uint32_t* klo = khi + G;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    const float mg = mn[g], D = Dq[g];
+    const float m = 0.0078125f * sqrtf(qv * mg) + 1.52587890625e-5f * (qv + mg);
+    khi[g] = ordered_key(D + m);
+    klo[g] = ordered_key(D - m);
+  }
+  __syncthreads();
   // U = nprobe-th smallest of approx + margin (three radix digits on ordered keys)
   uint32_t prefix = 0, need = (uint32_t)nprobe;
   int known = 0;
@@ -169,7 +197,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
     for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     for (int g = threadIdx.x; g < G; g += blockDim.x) {
-      const uint32_t k = ordered_key(Dq[g] + margin(g));
+      const uint32_t k = khi[g];
       if (known && (k >> (32 - known)) != prefix) continue;
       atomicAdd(&hist[(k >> shifts[pass]) & (nb - 1)], 1u);
     }
@@ -184,7 +212,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
   for (int g = threadIdx.x; g < G; g += blockDim.x) {
-    if (ordered_key(Dq[g] - margin(g)) <= Ukey) {
+    if (klo[g] <= Ukey) {
       const uint32_t pos = atomicAdd(&s_cnt, 1u);
       if (pos < (uint32_t)kRefineCap) keys[pos] = (unsigned long long)g;
     }

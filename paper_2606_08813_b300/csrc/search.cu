@@ -30,6 +30,7 @@
 #include "scan_select.cuh"
 #include "route_tc.cuh"
 #include "project_tc.cuh"
+#include "scan_tc.cuh"
 
 namespace hntl {
 
@@ -96,50 +97,78 @@ __global__ void k_bucket_count(const int32_t* __restrict__ probe, int n, uint32_
   if (i < n) atomicAdd(&gcnt[probe[i]], 1u);
 }
 
-// Single CTA: exclusive scans over grains of the pair counts (pair offsets)
-// and of the projection work items (groups of 8 pairs for the SIMT kernel,
-// of 128 pairs for the tensor-core kernel).
+// Single CTA: exclusive scans over grains. Offsets of the grain-major pair
+// lists, of the 8-pair groups and of the 32-pair slots, and the slot table
+// {grain, first pair, pairs} used by the tensor-core projection (slots ==
+// nullptr skips it); the tensor-core scan's work items {grain, first block,
+// blocks} over the probed grains (scan_items == nullptr skips them).
 __global__ void __launch_bounds__(1024) k_bucket_scan(const uint32_t* __restrict__ gcnt,
                                                       int G, uint32_t* __restrict__ pair_off,
                                                       uint32_t* __restrict__ grp_off,
-                                                      uint32_t* __restrict__ grp2_off) {
+                                                      uint32_t* __restrict__ slot_off, uint4* __restrict__ slots,
+                                                      const uint32_t* __restrict__ blk_off,
+                                                      uint32_t* __restrict__ scan_off,
+                                                      uint4* __restrict__ scan_items) {
   __shared__ uint32_t ws32[32];
-  __shared__ uint32_t tot32a, tot32b, tot32c;
-  uint32_t carry_p = 0, carry_gr = 0, carry_g2 = 0;
+  __shared__ uint32_t tot32a, tot32b, tot32c, tot32d;
+  uint32_t carry_p = 0, carry_gr = 0, carry_g2 = 0, carry_sc = 0;
   for (int c0 = 0; c0 < G; c0 += 1024) {
     int g = c0 + threadIdx.x;
     uint32_t cnt = g < G ? gcnt[g] : 0u;
     uint32_t ngr = (cnt + kPairsPerGroup - 1) / kPairsPerGroup;
     uint32_t ep = block_exclusive_scan<uint32_t>(cnt, &tot32a, ws32);
     uint32_t eg = block_exclusive_scan<uint32_t>(ngr, &tot32b, ws32);
-    uint32_t e2 = block_exclusive_scan<uint32_t>((cnt + kPGroup - 1) / kPGroup, &tot32c, ws32);
+    uint32_t e2 = block_exclusive_scan<uint32_t>((cnt + kPSlot - 1) / kPSlot, &tot32c, ws32);
+    const uint32_t nbk = (scan_items && g < G && cnt) ? blk_off[g + 1] - blk_off[g] : 0u;
+    uint32_t e3 = block_exclusive_scan<uint32_t>((nbk + kSTBlocks - 1) / kSTBlocks, &tot32d, ws32);
     if (g < G) {
       pair_off[g] = carry_p + ep;
       grp_off[g] = carry_gr + eg;
-      grp2_off[g] = carry_g2 + e2;
+      slot_off[g] = carry_g2 + e2;
+      if (scan_items) scan_off[g] = carry_sc + e3;
     }
     carry_p += tot32a;
     carry_gr += tot32b;
     carry_g2 += tot32c;
+    carry_sc += tot32d;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     pair_off[G] = carry_p;
     grp_off[G] = carry_gr;
-    grp2_off[G] = carry_g2;
+    slot_off[G] = carry_g2;
+    if (scan_items) scan_off[G] = carry_sc;
+  }
+  __syncthreads();
+  if (slots) {
+    for (int g = threadIdx.x; g < G; g += 1024) {
+      const uint32_t p0 = pair_off[g], cnt = pair_off[g + 1] - p0, i0 = slot_off[g];
+      for (uint32_t j = 0; j * kPSlot < cnt; ++j)
+        slots[i0 + j] = make_uint4((uint32_t)g, p0 + j * kPSlot, min((uint32_t)kPSlot, cnt - j * kPSlot), 0u);
+    }
+  }
+  if (scan_items) {
+    for (int g = threadIdx.x; g < G; g += 1024) {
+      const uint32_t i0 = scan_off[g], n = scan_off[g + 1] - i0, bk0 = blk_off[g], nbk = blk_off[g + 1] - bk0;
+      for (uint32_t j = 0; j < n; ++j)
+        scan_items[i0 + j] =
+            make_uint4((uint32_t)g, bk0 + j * kSTBlocks, min((uint32_t)kSTBlocks, nbk - j * kSTBlocks), 0u);
+    }
   }
 }
 
 __global__ void k_bucket_scatter(const int32_t* __restrict__ probe, int nq, int nprobe,
                                  const uint32_t* __restrict__ pair_off, uint32_t* __restrict__ gcur,
                                  uint32_t* __restrict__ pair_q, uint32_t* __restrict__ pair_p,
-                                 uint32_t* __restrict__ pair_of) {
+                                 uint32_t* __restrict__ pair_of, const float* __restrict__ probe_d,
+                                 float* __restrict__ pair_vn) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nq * nprobe) return;
   int g = probe[i];
   uint32_t pos = pair_off[g] + atomicAdd(&gcur[g], 1u);
   pair_q[pos] = (uint32_t)(i / nprobe);
   pair_p[pos] = (uint32_t)(i % nprobe);
+  if (pair_vn) pair_vn[pos] = probe_d[i];
   pair_of[i] = pos;
 }
 
@@ -257,10 +286,14 @@ struct Ws {
   uint32_t* gcur;
   uint32_t* pair_off;
   uint32_t* grp_off;
-  uint32_t* grp2_off;
+  uint32_t* grp2_off;  // per-grain offsets of the 32-pair projection slots
   uint32_t* pair_q;
   uint32_t* pair_p;
   uint32_t* pair_of;
+  float* pair_vn;  // ||q - mu_g||^2 of each pair (precision form)
+  uint4* slots;    // tensor-core projection slots of <= 32 pairs (precision form)
+  uint32_t* scan_off;  // per-grain offsets of the tensor-core scan's work items (precision form)
+  uint4* scan_items;   // {grain, first block, blocks} of each probed grain (precision form)
   float* zq;
   float* rhoq;
   float* tau;
@@ -289,10 +322,15 @@ Ws carve(const Index& I, uint32_t nq, uint32_t C, uint32_t nprobe, void* base) {
   w.pair_q = c.take<uint32_t>(P);
   w.pair_p = c.take<uint32_t>(P);
   w.pair_of = c.take<uint32_t>(P);
+  const bool tcp = I.precision == HNTL_PREC_BF16_FP8;
+  w.pair_vn = tcp ? c.take<float>(P) : nullptr;
+  w.slots = tcp ? c.take<uint4>(P / kPSlot + I.G) : nullptr;
+  w.scan_off = tcp ? c.take<uint32_t>(I.G + 1) : nullptr;
+  w.scan_items = tcp ? c.take<uint4>(I.G + I.n_blocks / kSTBlocks + 1) : nullptr;
   w.zq = c.take<float>(P * I.r);
   w.rhoq = c.take<float>(P);
   w.tau = c.take<float>(nq);
-  w.cnt = c.take<uint32_t>(nq);
+  w.cnt = c.take<uint32_t>((size_t)nq + 1);  // survivor counts, then the scan's work counter
   w.cap = survivor_cap(C);
   w.surv = c.take<unsigned long long>((size_t)nq * w.cap);
   w.cand_id = c.take<uint32_t>((size_t)nq * C);
@@ -324,14 +362,18 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
     CUtensorMap mapQ;
     if (!make_tma_map(&mapQ, bf16 ? (const void*)w.Qh : (const void*)Qd, bf16, nq, I.d, kRTM))
       return fail(HNTL_ECUDA, "cannot encode the TMA map of the queries");
-    static thread_local bool attr_tc = false;
-    if (!attr_tc) {
+    static thread_local int attr_tc = -1;
+    if (attr_tc != I.device) {
       HNTL_CUDA_TRY(cudaFuncSetAttribute(k_route_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRouteTcSmem));
       HNTL_CUDA_TRY(cudaFuncSetAttribute(k_route_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRouteTcSmem));
-      attr_tc = true;
+      HNTL_CUDA_TRY(cudaFuncSetAttribute(k_route_refine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kRefineSmemMax));
+      HNTL_CUDA_TRY(cudaFuncSetAttribute(k_route_refine<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kRefineSmemMax));
+      attr_tc = I.device;
     }
     dim3 grid((I.G + kRTN - 1) / kRTN, (nq + kRTM - 1) / kRTM);
-    const size_t rsmem = (size_t)I.d * sizeof(float);
+    const size_t rsmem = ((size_t)I.d + 2 * (size_t)I.G) * sizeof(float);
     if (bf16) {
       k_route_tc<true><<<grid, 128, kRouteTcSmem, st>>>(mapQ, I.mapM, (int)nq, (int)I.G, (int)I.d, w.qn, I.mnorm,
                                                         w.route_d, I.d_err);
@@ -363,25 +405,28 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
 }
 
 template <int RN>
-int launch_project_tc_n(const Index& I, uint32_t P, uint32_t nprobe, const Ws& w, cudaStream_t st) {
-  static thread_local bool attr = false;
-  if (!attr) {
+int launch_project_tc_n(const Index& I, uint32_t nq, uint32_t P, const Ws& w, cudaStream_t st) {
+  static thread_local int attr_dev = -1;
+  if (attr_dev != I.device) {
     HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project_tc<RN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        ProjTc<RN>::kSmem));
-    attr = true;
+    attr_dev = I.device;
   }
-  const unsigned grid = (unsigned)std::min<size_t>((size_t)P / kPGroup + I.G, 148 * 3);
-  k_project_tc<RN><<<grid, 128, ProjTc<RN>::kSmem, st>>>(w.Qh, I.Mh, I.Uh, I.gram, (int)I.d, (int)I.r, (int)I.G,
-                                                         (int)nprobe, w.grp2_off, w.pair_off, w.pair_q, w.pair_p,
-                                                         w.probe_d, w.zq, w.rhoq, I.d_err);
+  // persistent: one CTA per SM at most, never more CTAs than work items can exist
+  const size_t max_items = ((size_t)P / kPSlot + I.G + kPSlots - 1) / kPSlots;
+  const unsigned grid = (unsigned)std::min<size_t>(max_items, (size_t)I.num_sms);
+  k_project_tc<RN><<<grid, kPThreads, ProjTc<RN>::kSmem, st>>>(w.Qh, I.mapMrep, I.mapU, I.gram, (int)I.d, (int)I.r,
+                                                               w.slots, w.grp2_off + I.G, w.pair_q, w.pair_vn,
+                                                               w.zq, w.rhoq, I.d_err);
   HNTL_CUDA_TRY(cudaGetLastError());
   return HNTL_OK;
 }
 
-int launch_project_tc(const Index& I, uint32_t P, uint32_t nprobe, const Ws& w, cudaStream_t st) {
-  if (I.r <= 16) return launch_project_tc_n<16>(I, P, nprobe, w, st);
-  if (I.r <= 32) return launch_project_tc_n<32>(I, P, nprobe, w, st);
-  return launch_project_tc_n<64>(I, P, nprobe, w, st);
+int launch_project_tc(const Index& I, uint32_t nq, uint32_t P, const Ws& w, cudaStream_t st) {
+  if (!I.tc_proj) return fail(HNTL_EINVAL, "the precision form needs tensor-core projection (d a multiple of 8)");
+  if (I.r <= 16) return launch_project_tc_n<16>(I, nq, P, w, st);
+  if (I.r <= 32) return launch_project_tc_n<32>(I, nq, P, w, st);
+  return launch_project_tc_n<64>(I, nq, P, w, st);
 }
 
 template <int RT, bool kFP8>
@@ -391,10 +436,23 @@ void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, 
   k_pilot<RT, kFP8><<<nq, 256, 0, st>>>(nprobe, C, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho,
                                         I.attr_b, (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.tau, qC);
   mark(4);
-  k_scan_filter<RT, kFP8><<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(
-      I.blk_grain, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b, (int)I.r, (int)I.rp, w.gcnt, w.pair_off,
-      w.pair_q,
-      w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap, w.cnt, w.surv);
+  if constexpr (kFP8) {
+    static thread_local int attr_dev = -1;
+    if (attr_dev != I.device) {
+      cudaFuncSetAttribute(k_scan_tc<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, ScanTc<RT>::kSmem);
+      attr_dev = I.device;
+    }
+    const size_t max_items = (size_t)I.G + I.n_blocks / kSTBlocks + 1;
+    const unsigned grid = (unsigned)std::min<size_t>(max_items, (size_t)I.num_sms * 2);
+    k_scan_tc<RT><<<grid, kSTThreads, ScanTc<RT>::kSmem, st>>>(
+        w.scan_items, w.scan_off + I.G, w.cnt + nq, I.blk_off, I.grain_rows, I.Z8b, I.scale, I.crow, I.rho, I.ids, I.attr_b,
+        (int)I.r, (int)I.rp, w.gcnt, w.pair_off, w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap, w.cnt,
+        w.surv, I.d_err);
+  } else {
+    k_scan_filter<RT, kFP8><<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(
+        I.blk_grain, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b, (int)I.r, (int)I.rp, w.gcnt, w.pair_off,
+        w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap, w.cnt, w.surv);
+  }
   mark(5);
   k_final_select<RT, kFP8><<<nq, kFinalThreads, 0, st>>>(nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of,
                                                          I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b,
@@ -491,12 +549,13 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
   mark(1);
   const int P = (int)(nq * nprobe);
   k_bucket_count<<<(P + 255) / 256, 256, 0, st>>>(w.probe, P, w.gcnt);
-  k_bucket_scan<<<1, 1024, 0, st>>>(w.gcnt, (int)I.G, w.pair_off, w.grp_off, w.grp2_off);
+  k_bucket_scan<<<1, 1024, 0, st>>>(w.gcnt, (int)I.G, w.pair_off, w.grp_off, w.grp2_off, w.slots, I.blk_off,
+                                    w.scan_off, w.scan_items);
   k_bucket_scatter<<<(P + 255) / 256, 256, 0, st>>>(w.probe, (int)nq, (int)nprobe, w.pair_off, w.gcur, w.pair_q,
-                                                    w.pair_p, w.pair_of);
+                                                    w.pair_p, w.pair_of, w.probe_d, w.pair_vn);
   mark(2);
   if (I.precision == HNTL_PREC_BF16_FP8) {
-    if ((rc = launch_project_tc(I, (uint32_t)P, nprobe, w, st))) return rc;
+    if ((rc = launch_project_tc(I, nq, (uint32_t)P, w, st))) return rc;
   } else {
     size_t smem = (size_t)kPairsPerGroup * I.d * sizeof(float);
     if (smem > 48 * 1024)
@@ -506,7 +565,7 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
                                               w.pair_q, w.zq, w.rhoq);
   }
   mark(3);
-  HNTL_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * nq, st));
+  HNTL_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * ((size_t)nq + 1), st));
   {
     const std::function<void(int)> mk = mark;
     if (I.r <= 8) launch_scan_select_p<8>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk, qC);
@@ -595,8 +654,10 @@ int finalize_index(Index& I) {
     I.Mh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.d));
     I.Uh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.r * I.d));
     I.gram = static_cast<float*>(alloc(sizeof(float) * I.G * I.r * I.r));
+    I.Mrep = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * 8 * I.d));
+    I.crow = static_cast<float*>(alloc(sizeof(float) * I.n_blocks * kBlockRows));
   }
-  if (!I.d_err || !I.mnorm || (bf16 && (!I.Mh || !I.Uh || !I.gram)))
+  if (!I.d_err || !I.mnorm || (bf16 && (!I.Mh || !I.Uh || !I.gram || !I.Mrep || !I.crow)))
     return fail(HNTL_ENOMEM, "index: derived arrays");
   HNTL_CUDA_TRY(cudaMemset(I.d_err, 0, sizeof(int)));
   if (bf16) k_row_norms<true><<<(I.G * 32 + 255) / 256, 256>>>(I.M, (int)I.G, (int)I.d, I.mnorm);
@@ -606,12 +667,22 @@ int finalize_index(Index& I) {
     k_to_bf16_rows<<<(unsigned)((n + 255) / 256), 256>>>(I.M, n, I.Mh);
     k_to_bf16_rows<<<(unsigned)((nu + 255) / 256), 256>>>(I.U, nu, I.Uh);
     k_gram<<<I.G, 256>>>(I.Uh, (int)I.d, (int)I.r, I.gram);
+    k_negate_rep8_bf16<<<(unsigned)((n * 8 + 255) / 256), 256>>>(I.Mh, (int)I.G, (int)I.d, I.Mrep);
+    const Coords cz{I.Zb, I.Z8b, I.scale};
+    if (I.n_blocks) {
+      if (I.r <= 16) k_row_c<16><<<(unsigned)I.n_blocks, kBlockRows>>>(cz, I.rho, I.blk_grain, (int)I.rp, I.crow);
+      else if (I.r <= 32) k_row_c<32><<<(unsigned)I.n_blocks, kBlockRows>>>(cz, I.rho, I.blk_grain, (int)I.rp, I.crow);
+      else k_row_c<64><<<(unsigned)I.n_blocks, kBlockRows>>>(cz, I.rho, I.blk_grain, (int)I.rp, I.crow);
+    }
   }
+  HNTL_CUDA_TRY(cudaDeviceGetAttribute(&I.num_sms, cudaDevAttrMultiProcessorCount, I.device));
   HNTL_CUDA_TRY(cudaGetLastError());
   HNTL_CUDA_TRY(cudaDeviceSynchronize());
   // tensor-core routing needs 16-byte row strides and the query row in shared memory
   const bool shape_ok = (bf16 ? I.d % 8 == 0 : I.d % 4 == 0) && I.d <= 8192;
   I.tc_route = shape_ok && make_tma_map(&I.mapM, bf16 ? (const void*)I.Mh : (const void*)I.M, bf16, I.G, I.d, kRTN);
+  I.tc_proj = bf16 && shape_ok && make_tma_map(&I.mapMrep, I.Mrep, true, (uint64_t)I.G * 8, I.d, 8) &&
+              make_tma_map(&I.mapU, I.Uh, true, (uint64_t)I.G * I.r, I.d, I.r);
   return HNTL_OK;
 }
 

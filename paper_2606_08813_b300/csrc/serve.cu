@@ -4,10 +4,12 @@
 // C and attribute range stay on the device while the request lives). A host
 // worker thread forms batches from the admitted requests as they arrive and
 // launches them on one of two lanes; each lane owns a stream, a workspace
-// and a CUDA graph captured once at creation: gather the batch's slots from
-// the table, run the whole Mode B search with each query's own k and C (the
-// batch's largest k and C set the strides only), and copy the results to
-// pinned host memory. While one lane's batch runs on the GPU the worker fills
+// and CUDA graphs captured once at creation for a few batch sizes (B, B/4,
+// B/16, ... down to 32 rows): gather the batch's slots from the table, run
+// the whole Mode B search with each query's own k and C (k_max and C_max set
+// the strides only), and copy the results to pinned host memory. A batch
+// takes the smallest graph that holds it, padded with copies of its first
+// request, so a lightly loaded server does not pay for full batches. While one lane's batch runs on the GPU the worker fills
 // and launches the other, so requests that arrive meanwhile overlap with it.
 // A request's result does not depend on the batch it rides in: every stage is
 // per query (selections are total orders on (distance, id)).
@@ -86,7 +88,7 @@ struct Req {
 
 struct Lane {
   cudaStream_t st = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  std::vector<std::pair<uint32_t, cudaGraphExec_t>> graphs;  // (rows, graph), ascending rows
   cudaEvent_t done = nullptr;
   uint32_t* d_slots = nullptr;
   uint32_t* h_slots = nullptr;  // pinned
@@ -174,6 +176,9 @@ void worker_main(Server* S) {
       }
       if (!L.busy && !S->queue.empty()) {
         const uint32_t n = (uint32_t)std::min<size_t>(S->B, S->queue.size());
+        size_t gi = 0;
+        while (L.graphs[gi].first < n) ++gi;  // the largest graph holds B rows
+        const uint32_t rows = L.graphs[gi].first;
         uint32_t first_slot = 0;
         for (uint32_t i = 0; i < n; ++i) {
           const uint64_t t = S->queue.front();
@@ -184,9 +189,9 @@ void worker_main(Server* S) {
           if (i == 0) first_slot = r.slot;
           L.tickets.push_back(t);
         }
-        for (uint32_t i = n; i < S->B; ++i) L.h_slots[i] = first_slot;  // padding rows, results discarded
-        cudaMemcpyAsync(L.d_slots, L.h_slots, sizeof(uint32_t) * S->B, cudaMemcpyHostToDevice, L.st);
-        cudaGraphLaunch(L.exec, L.st);
+        for (uint32_t i = n; i < rows; ++i) L.h_slots[i] = first_slot;  // padding rows, results discarded
+        cudaMemcpyAsync(L.d_slots, L.h_slots, sizeof(uint32_t) * rows, cudaMemcpyHostToDevice, L.st);
+        cudaGraphLaunch(L.graphs[gi].second, L.st);
         cudaEventRecord(L.done, L.st);
         L.busy = true;
         S->batches += 1;
@@ -223,7 +228,8 @@ void destroy(Server& S) {
   }
   if (S.up) cudaStreamDestroy(S.up);
   for (Lane& L : S.lanes) {
-    if (L.exec) cudaGraphExecDestroy(L.exec);
+    for (auto& g : L.graphs) cudaGraphExecDestroy(g.second);
+    L.graphs.clear();
     if (L.done) cudaEventDestroy(L.done);
     if (L.st) cudaStreamDestroy(L.st);
   }
@@ -336,41 +342,51 @@ extern "C" int hntl_server_create(const hntl_index* idx, size_t mem_budget, uint
       break;
     }
     cudaMemset(L.d_slots, 0, batch * 4);
-    auto record = [&]() -> int {
-      hntl::k_gather_batch<<<batch, 128, 0, L.st>>>(L.d_slots, (int)batch, (int)I.d, S.d_slot_q, S.d_slot_k,
-                                                    S.d_slot_C, S.d_slot_range, L.d_Q, L.d_k, L.d_C, L.d_F);
-      int r = hntl::search(I, L.d_Q, batch, k_max, C_max, nprobe, L.d_F, L.ws, L.ws_bytes, L.d_ids, L.d_dist,
+    auto record = [&](uint32_t rows) -> int {
+      hntl::k_gather_batch<<<rows, 128, 0, L.st>>>(L.d_slots, (int)rows, (int)I.d, S.d_slot_q, S.d_slot_k,
+                                                   S.d_slot_C, S.d_slot_range, L.d_Q, L.d_k, L.d_C, L.d_F);
+      int r = hntl::search(I, L.d_Q, rows, k_max, C_max, nprobe, L.d_F, L.ws, L.ws_bytes, L.d_ids, L.d_dist,
                            nullptr, nullptr, nullptr, L.st, nullptr, L.d_k, L.d_C);
       if (r) return r;
-      if (cudaMemcpyAsync(L.h_ids, L.d_ids, (size_t)batch * k_max * 8, cudaMemcpyDeviceToHost, L.st) ||
-          cudaMemcpyAsync(L.h_dist, L.d_dist, (size_t)batch * k_max * 4, cudaMemcpyDeviceToHost, L.st))
+      if (cudaMemcpyAsync(L.h_ids, L.d_ids, (size_t)rows * k_max * 8, cudaMemcpyDeviceToHost, L.st) ||
+          cudaMemcpyAsync(L.h_dist, L.d_dist, (size_t)rows * k_max * 4, cudaMemcpyDeviceToHost, L.st))
         return fail(HNTL_ECUDA, "server: result copies");
       return HNTL_OK;
     };
-    // one eager run (sets kernel attributes), then capture the same sequence as a graph
-    if ((rc = record())) break;
-    if (cudaStreamSynchronize(L.st) != cudaSuccess) {
-      rc = fail(HNTL_ECUDA, "server: warm-up batch");
-      break;
+    std::vector<uint32_t> sizes;
+    for (uint32_t rows = batch;; rows /= 4) {
+      sizes.insert(sizes.begin(), rows);
+      if (rows / 4 < 32) break;
     }
-    cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(L.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      rc = fail(HNTL_ECUDA, "server: begin capture");
-      break;
+    for (uint32_t rows : sizes) {
+      // one eager run (sets kernel attributes), then capture the same sequence as a graph
+      if ((rc = record(rows))) break;
+      if (cudaStreamSynchronize(L.st) != cudaSuccess) {
+        rc = fail(HNTL_ECUDA, "server: warm-up batch");
+        break;
+      }
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(L.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = fail(HNTL_ECUDA, "server: begin capture");
+        break;
+      }
+      int rr = record(rows);
+      cudaError_t ce = cudaStreamEndCapture(L.st, &g);
+      if (rr || ce != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        rc = rr ? rr : fail(HNTL_ECUDA, std::string("server: capture: ") + cudaGetErrorString(ce));
+        break;
+      }
+      cudaGraphExec_t ex = nullptr;
+      ce = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) {
+        rc = fail(HNTL_ECUDA, std::string("server: instantiate: ") + cudaGetErrorString(ce));
+        break;
+      }
+      L.graphs.emplace_back(rows, ex);
     }
-    int rr = record();
-    cudaError_t ce = cudaStreamEndCapture(L.st, &g);
-    if (rr || ce != cudaSuccess || !g) {
-      if (g) cudaGraphDestroy(g);
-      rc = rr ? rr : fail(HNTL_ECUDA, std::string("server: capture: ") + cudaGetErrorString(ce));
-      break;
-    }
-    ce = cudaGraphInstantiate(&L.exec, g, 0);
-    cudaGraphDestroy(g);
-    if (ce != cudaSuccess) {
-      rc = fail(HNTL_ECUDA, std::string("server: instantiate: ") + cudaGetErrorString(ce));
-      break;
-    }
+    if (rc) break;
   }
   if (prev >= 0) cudaSetDevice(prev);
   if (rc) {

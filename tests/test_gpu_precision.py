@@ -73,11 +73,14 @@ def test_precision_filters(hntl, tmp_path):
     assert st["checked"] >= 0.9 * len(Q), st
 
 
-def test_precision_form_needs_tma_shape(hntl, tmp_path):
-    X, Q, idx = clustered_case(500, 12, 4, 4, 4, 4, seed=5)  # d = 12: rows not a multiple of 16 bytes in BF16
-    gi = hntl.Index.load(write(tmp_path, "p12", idx, X, precision="bf16-fp8"), 0, hntl.PREC_BF16_FP8)
+def test_precision_form_needs_d_multiple_of_8(hntl, tmp_path):
+    # d = 12: BF16 rows are not a whole number of 16-byte pieces
+    X, Q, idx = clustered_case(500, 12, 4, 4, 4, 4, seed=5)
     with pytest.raises(hntl.HntlError) as e:
-        gi.search(torch.from_numpy(Q).cuda(), 5, 10, 2)
+        hntl.Index.load(write(tmp_path, "p12", idx, X, precision="bf16-fp8"), 0, hntl.PREC_BF16_FP8)
+    assert e.value.code == hntl.EINVAL
+    with pytest.raises(hntl.HntlError) as e:
+        hntl.Index.build(torch.from_numpy(X).cuda(), 4, 4, precision=hntl.PREC_BF16_FP8)
     assert e.value.code == hntl.EINVAL
 
 

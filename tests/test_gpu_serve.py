@@ -26,12 +26,13 @@ def hntl():
     return h
 
 
-@pytest.fixture(scope="module")
-def served(hntl, tmp_path_factory):
+@pytest.fixture(scope="module", params=["fp32", "bf16-fp8"])
+def served(hntl, tmp_path_factory, request):
     X, Q, idx = clustered_case(20000, 128, 48, 64, 16, 400, seed=301, sizes="zipf")
     attr = synth.attributes(len(X), 302, span=1000).numpy()
-    p = write(tmp_path_factory.mktemp("serve"), "serve", idx, X, attr=attr)
-    return hntl.Index.load(p, 0), Q, attr
+    p = write(tmp_path_factory.mktemp("serve"), "serve", idx, X, attr=attr, precision=request.param)
+    prec = hntl.PREC_BF16_FP8 if request.param == "bf16-fp8" else hntl.PREC_FP32
+    return hntl.Index.load(p, 0, prec), Q, attr
 
 
 def _mix(nq, seed):
