@@ -333,6 +333,33 @@ def run_serving(a, hntl, gi, X, Q, attr, w, sd):
                           "admission_refusals": busy_refusals})
         print(f"serving {R} q/s: {rates_out[-1]}", file=sys.stderr)
     srv.close()
+    # stage times of one search at each graph size the server captures (k_max, C_max, unfiltered)
+    sizes = []
+    rows_ = a.serve_batch
+    while rows_ >= 32:
+        sizes.insert(0, rows_)
+        if rows_ // 4 < 32:
+            break
+        rows_ //= 4
+    batch_profile = {}
+    for rows_ in sizes:
+        Qb = Q[:rows_].contiguous()
+        for _ in range(3):
+            gi.search(Qb, 100, 1000, w["nprobe"])
+        torch.cuda.synchronize()
+        hntl.profile_read()
+        hntl.profile_enable(True)
+        for _ in range(5):
+            gi.search(Qb, 100, 1000, w["nprobe"])
+        torch.cuda.synchronize()
+        hntl.profile_enable(False)
+        sm, calls = hntl.profile_read()
+        batch_profile[rows_] = {k_: round(v_ / max(calls, 1), 3) for k_, v_ in sm.items()}
+        batch_profile[rows_]["total"] = round(sum(sm.values()) / max(calls, 1), 3)
+        sv = hntl.search_survivors(gi, gi.workspace(0), rows_, 1000, w["nprobe"]).cpu().numpy()
+        batch_profile[rows_]["survivors_mean_max_overflow"] = [round(float(sv.mean()), 1), int(sv.max()),
+                                                               int((sv > 32000).sum())]
+    print(f"serving batch stage ms (k=100, C=1000): {batch_profile}", file=sys.stderr)
     recall = {}
     if samples and X is not None:
         rows = torch.tensor([s[0] for s in samples], device=dev)
@@ -353,6 +380,7 @@ def run_serving(a, hntl, gi, X, Q, attr, w, sd):
     return {"sustained_qps": max((r["offered_qps"] for r in ok), default=None),
             "sustained_rule": f"highest offered rate served at >= 97% with p99 <= {a.serve_p99_ms} ms",
             "rates": rates_out, "recall_at_10": recall, "batch": a.serve_batch, "slots": slots,
+            "batch_stage_ms_k100_C1000": batch_profile,
             "mem_budget_gb": round(budget / (1 << 30), 1), "create_s": round(create_s, 2),
             "mix": "k in {10,100}, C in {20,200,1000} uniform (C >= k), 50% with a 20%-selectivity attribute range",
             "seconds_per_rate": a.serve_seconds}
@@ -390,11 +418,19 @@ def run_ours(a, world, rank, local):
     # probes of every batch (untimed) for algorithmic bytes; results of batch 0 for recall
     probes = []
     found = []
+    surv = []
     for b in batches:
         ids, dist, probe = gi.search(b, k, C, nprobe, return_probe=True)
         probes.append(probe.cpu().numpy())
         found.append(ids)
+        if len(surv) < 4:  # pool survivors per query (rows that passed the pilot bound)
+            surv.append(hntl.search_survivors(gi, gi.workspace(0), B, C, nprobe).cpu().numpy())
     torch.cuda.synchronize()
+    surv = np.concatenate(surv).astype(np.int64)
+    cap = max(8192, 32 * C)
+    surv_stats = {"mean": round(float(surv.mean()), 1), "p50": int(np.percentile(surv, 50)),
+                  "p99": int(np.percentile(surv, 99)), "max": int(surv.max()),
+                  "overflowed": int((surv > cap).sum()), "queries": int(len(surv))}
     n_recall = 0 if a.profile_mode else min(w["nq"], a.recall_queries)
     rec = float("nan")
     if n_recall:
@@ -468,13 +504,16 @@ def run_ours(a, world, rank, local):
                    "recall_note": "skipped in profile mode" if a.profile_mode else "brute force, FP64 re-rank",
                    "sizes": w["sizes"], "l2": "no flush; per-step working set (probed coordinates, bases and "
                    "gathered rows, ~0.5 GB) exceeds the 126 MB L2", "index_build_s": round(build_s, 2),
-                   "parallelism": f"replicas x{world}", "batch_latency_ms_p50": round(float(np.percentile(step_ms, 50)), 4),
+                   "parallelism": f"replicas x{world}", "pool_survivors": surv_stats, "batch_latency_ms_p50": round(float(np.percentile(step_ms, 50)), 4),
                    "batch_latency_ms_p99": round(float(np.percentile(step_ms, 99)), 4)},
         "roofline": roof, "stages": others,
         "e2e": {"value": round(e2e_qps, 1) if e2e_qps else None, "unit": "queries/s",
                 "h2d_bytes_per_step": B * w["d"] * 4,
                 "d2h_bytes_per_step": B * k * 12},
-        "gpu_launches": 10 * a.steps, "clocks": clocks,
+        # our kernels per search: precision form = row norms, BF16 queries, route (TC + refine), bucket (3),
+        # projection, pilot, live pairs, classify, scan (sparse + TC), pool select (2), rerank;
+        # FP32 form = row norms, route (2), bucket (3), projection, pilot, scan, pool select (2), rerank
+        "gpu_launches": (16 if prec == "bf16-fp8" else 12) * a.steps, "clocks": clocks,
     }
     if serve:
         line["serving"] = run_serving(a, hntl, gi, X, Q, attr, w, sd)

@@ -56,6 +56,7 @@ struct Index {
   float* rho = nullptr;          // [n_blocks][128] residual norms
   float* blk_rho_min = nullptr;  // [n_blocks] smallest residual norm of a block's real rows (+inf if none)
   float* crow = nullptr;         // [n_blocks][128] ||z_i||^2 + rho_i of the decoded row (precision form)
+  float* grain_rho_min = nullptr;  // [G] smallest residual norm of a grain's rows (precision form)
   uint32_t* ids = nullptr;       // [n_blocks][128] original ids
   int64_t* attr_b = nullptr;     // [n_blocks][128] attributes in block order
   float* X = nullptr;            // [n][d] FP32 raw rows, id order

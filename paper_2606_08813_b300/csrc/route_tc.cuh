@@ -29,11 +29,11 @@
 namespace hntl {
 namespace {
 
-constexpr int kRTM = 128, kRTN = 256, kRStages = 4;
+constexpr int kRTM = 128, kRTN = 256, kRStages = 2;  // two CTAs per SM: one epilogue overlaps the other main loop
 constexpr int kRouteTcSmem = kRStages * (kRTM + kRTN) * 128 + 1024;
 
 template <bool kBF16>
-__global__ void __launch_bounds__(128) k_route_tc(const __grid_constant__ CUtensorMap mapQ,
+__global__ void __launch_bounds__(128, 2) k_route_tc(const __grid_constant__ CUtensorMap mapQ,
                                                   const __grid_constant__ CUtensorMap mapM, int nq, int G, int d,
                                                   const float* __restrict__ qn, const float* __restrict__ mn,
                                                   float* __restrict__ Dt, int* __restrict__ err) {
@@ -151,6 +151,70 @@ constexpr int kRefineCap = 1024;
 
 constexpr int kRefineSmemMax = (8192 + 2 * kMaxG) * 4;  // d <= 8192 on this path
 
+// ||q - mu_g||^2 in the direct form, one warp (the result in every lane). Each
+// lane sums its elements in a fixed order (with rows of at most 1024 values
+// and 16-byte strides: chunks of 8 (BF16) or 4 (FP32) consecutive values, all
+// loads issued before use; else lane-strided), then a butterfly adds the
+// lanes. Every kernel that forms a routing distance calls this, so a distance
+// is bitwise the same whoever computed it. qv(t) is the query value (already
+// BF16-rounded in the precision form).
+template <bool kBF16, class QV>
+__device__ __forceinline__ float warp_center_dist2(QV qv, const float* __restrict__ M,
+                                                   const uint16_t* __restrict__ Mh, int g, int d, int lane) {
+  float acc = 0.f;
+  if (kBF16 && (d & 7) == 0 && d <= 1024) {
+    const uint16_t* row = Mh + (size_t)g * d;
+    uint4 v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int t = lane * 8 + 256 * i;
+      v[i] = t < d ? __ldg(reinterpret_cast<const uint4*>(row + t)) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int t = lane * 8 + 256 * i;
+      if (t < d) {
+        const uint32_t w[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const float a0 = qv(t + 2 * h) - __uint_as_float(w[h] << 16);
+          const float a1 = qv(t + 2 * h + 1) - __uint_as_float(w[h] & 0xFFFF0000u);
+          acc = fmaf(a0, a0, acc);
+          acc = fmaf(a1, a1, acc);
+        }
+      }
+    }
+  } else if (!kBF16 && (d & 3) == 0 && d <= 1024) {
+    const float* row = M + (size_t)g * d;
+    float4 v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int t = lane * 4 + 128 * i;
+      v[i] = t < d ? __ldg(reinterpret_cast<const float4*>(row + t)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int t = lane * 4 + 128 * i;
+      if (t < d) {
+        const float a0 = qv(t) - v[i].x, a1 = qv(t + 1) - v[i].y, a2 = qv(t + 2) - v[i].z, a3 = qv(t + 3) - v[i].w;
+        acc = fmaf(a0, a0, acc);
+        acc = fmaf(a1, a1, acc);
+        acc = fmaf(a2, a2, acc);
+        acc = fmaf(a3, a3, acc);
+      }
+    }
+  } else {
+    for (int t = lane; t < d; t += 32) {
+      const float m = kBF16 ? __uint_as_float((uint32_t)Mh[(size_t)g * d + t] << 16) : M[(size_t)g * d + t];
+      const float df = qv(t) - m;
+      acc = fmaf(df, df, acc);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
 // One CTA per query: margin shortlist over the approximate distances, exact
 // direct-form distances of the shortlist, the nprobe smallest (distance, g).
 // In the precision form q and the centres are BF16 values (Mh).
@@ -166,7 +230,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
   // keys of approx + margin and approx - margin of every centre ([G] each), so
   // the row of approximate distances is read from memory once
   extern __shared__ float sq[];
-  __shared__ uint32_t hist[2048];
+  __shared__ uint32_t hist[256];
   __shared__ unsigned long long keys[kRefineCap];
   __shared__ uint32_t scratch[96];
   __shared__ uint32_t s_bin, s_below, s_cnt;
@@ -188,24 +252,23 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
     klo[g] = ordered_key(D - m);
   }
   __syncthreads();
-  // U = nprobe-th smallest of approx + margin (three radix digits on ordered keys)
+  // U = nprobe-th smallest of approx + margin (four 8-bit radix digits on ordered keys)
   uint32_t prefix = 0, need = (uint32_t)nprobe;
   int known = 0;
-  const int shifts[3] = {21, 10, 0}, widths[3] = {11, 11, 10};
-  for (int pass = 0; pass < 3; ++pass) {
-    const int nb = 1 << widths[pass];
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int sh = 24 - 8 * pass;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     for (int g = threadIdx.x; g < G; g += blockDim.x) {
       const uint32_t k = khi[g];
       if (known && (k >> (32 - known)) != prefix) continue;
-      atomicAdd(&hist[(k >> shifts[pass]) & (nb - 1)], 1u);
+      atomicAdd(&hist[(k >> sh) & 255u], 1u);
     }
     __syncthreads();
-    find_bin(hist, nb, need, &s_bin, &s_below, scratch);
+    find_bin(hist, 256, need, &s_bin, &s_below, scratch);
     need -= s_below;
-    prefix = (prefix << widths[pass]) | s_bin;
-    known += widths[pass];
+    prefix = (prefix << 8) | s_bin;
+    known += 8;
     __syncthreads();
   }
   const uint32_t Ukey = prefix;
@@ -224,14 +287,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
   // exact distances, one warp per candidate; results are kept in the key list
   // (all == true: the first kRefineCap slots hold the running best, merged below)
   auto exact = [&](int g) {
-    float acc = 0.f;
-    for (int t = lane; t < d; t += 32) {
-      float m = kBF16 ? __uint_as_float((uint32_t)Mh[(size_t)g * d + t] << 16) : M[(size_t)g * d + t];
-      float df = sq[t] - m;
-      acc = fmaf(df, df, acc);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    float acc = warp_center_dist2<kBF16>([&](int t) { return sq[t]; }, M, Mh, g, d, lane);
     if (!(acc == acc)) acc = INFINITY;
     return ((unsigned long long)__float_as_uint(acc) << 32) | (uint32_t)g;
   };

@@ -1,9 +1,10 @@
 // Block-SoA scan (Eq. 6) fused with the pool of the C best (Table 1, "Pool C").
 //
 // Three kernels replace "write every distance, then select":
-//   k_pilot        one CTA per query computes D for up to 2048 rows (whole
-//                  Block-SoA blocks, evenly spaced) of its nearest probed
-//                  grains in routing order and takes the C-th smallest as tau_q. Those are real rows of the query's
+//   k_pilot        one CTA per query computes D for max(1024, 4C) rows, at
+//                  most 2048 (whole Block-SoA blocks, evenly spaced), of its
+//                  nearest probed grains in routing order and takes the C-th
+//                  smallest as tau_q. Those are real rows of the query's
 //                  probe set, so at least C rows have D <= tau_q and tau_q is
 //                  an upper bound on the query's true C-th distance.
 //   k_scan_filter  grain-major scan of every probed Block-SoA block: a
@@ -30,11 +31,12 @@
 namespace hntl {
 namespace {
 
-constexpr int kPilotRows = 2048;  // rows the pilot evaluates per query (whole 128-row blocks)
+constexpr int kPilotRows = 2048;  // most rows the pilot evaluates per query (whole 128-row blocks)
+constexpr int kPilotMin = 1024;   // fewest (when 4 C is smaller)
 constexpr int kTieCap = 1024;
 constexpr uint32_t kInfBits = 0x7F800000u;
 
-__host__ __device__ inline uint32_t survivor_cap(uint32_t C) { return C * 16 > 8192 ? C * 16 : 8192; }
+__host__ __device__ inline uint32_t survivor_cap(uint32_t C) { return C * 32 > 8192 ? C * 32 : 8192; }
 
 __device__ __forceinline__ unsigned long long pack2(float a, float b) {
   return ((unsigned long long)__float_as_uint(b) << 32) | __float_as_uint(a);
@@ -121,12 +123,16 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
                                                const float* __restrict__ rhoq, const int64_t* __restrict__ filter,
                                                float* __restrict__ tau, const uint32_t* __restrict__ qC) {
   __shared__ uint32_t vals[kPilotRows];  // D bit patterns (non-negative floats order like unsigned)
-  __shared__ uint32_t hist[2048];
+  __shared__ uint32_t hist[256];
   __shared__ __align__(8) float szq[RT];
   __shared__ uint32_t scratch[96];
   __shared__ uint32_t s_fill, s_bin, s_below, s_total;
   const int q = blockIdx.x;
   if (qC) C = (int)qC[q];  // per-query pool size (mixed batches)
+  // rows to evaluate: enough that the C-th smallest is a useful bound (a larger
+  // sample only tightens tau, which costs more here than it saves downstream)
+  const uint32_t budget = (uint32_t)min(kPilotRows, max(kPilotMin, 4 * C));
+  const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) s_fill = 0;
   long long lo = 0, hi = 0;
   if (filter) {
@@ -137,7 +143,13 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
   for (int p = 0; p < nprobe; ++p) {
     __syncthreads();
     const uint32_t fill = s_fill;
-    if (fill >= (uint32_t)C || scanned + kBlockRows > (uint32_t)kPilotRows) break;
+    if (fill >= (uint32_t)C) break;
+    // unfiltered: `budget` rows in all; filtered: whole blocks until `budget` rows
+    // passed the range (the buffer holds kPilotRows), scanning at most 8 kPilotRows
+    if (!filter && scanned + kBlockRows > budget) break;
+    if (filter && (fill >= budget || fill + kBlockRows > (uint32_t)kPilotRows ||
+                   scanned + kBlockRows > 8u * kPilotRows))
+      break;
     const int g = probe[(size_t)q * nprobe + p];
     const uint32_t s = pair_of[(size_t)q * nprobe + p];
     const uint32_t n = grain_rows[g];
@@ -146,24 +158,37 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
     const float rho_q = rhoq[s];
     const float s_g = kFP8 ? cz.scale[g] : 1.f;
     __syncthreads();
-    const uint32_t room = ((uint32_t)kPilotRows - scanned) / kBlockRows;
+    const uint32_t room = filter ? min(((uint32_t)kPilotRows - fill) / kBlockRows,
+                                       (8u * kPilotRows - scanned) / kBlockRows)
+                                 : (budget - scanned) / kBlockRows;
     const uint32_t take = nbk < room ? nbk : room;  // whole blocks, evenly spaced over the grain
-    for (uint32_t e = threadIdx.x; e < take * kBlockRows; e += blockDim.x) {
-      const uint32_t i = e / kBlockRows;
-      const int t = e % kBlockRows;
-      const uint32_t jb = take == nbk ? i : (uint32_t)(((unsigned long long)i * nbk) / take);
-      if (jb * kBlockRows + t >= n) continue;
-      const size_t b = blk_off[g] + jb;
-      if (filter) {
-        const long long a = attr_b[b * kBlockRows + t];
-        if (a < lo || a > hi) continue;
+    for (uint32_t e0 = 0; e0 < take * kBlockRows; e0 += blockDim.x) {  // block-uniform trip count
+      const uint32_t e = e0 + threadIdx.x;
+      bool keep = false;
+      uint32_t k = 0;
+      if (e < take * kBlockRows) {
+        const uint32_t i = e / kBlockRows;
+        const int t = e % kBlockRows;
+        const uint32_t jb = take == nbk ? i : (uint32_t)(((unsigned long long)i * nbk) / take);
+        const size_t b = blk_off[g] + jb;
+        keep = jb * kBlockRows + t < n;
+        if (keep && filter) {
+          const long long a = attr_b[b * kBlockRows + t];
+          keep = a >= lo && a <= hi;
+        }
+        if (keep) {
+          float z[RT];
+          load_row<RT, kFP8>(cz, rp, s_g, b, t, z);
+          k = __float_as_uint(eval_D<RT>(szq, z, rho_q, rho[b * kBlockRows + t]));
+          keep = k < kInfBits;
+        }
       }
-      float z[RT];
-      load_row<RT, kFP8>(cz, rp, s_g, b, t, z);
-      const float D = eval_D<RT>(szq, z, rho_q, rho[b * kBlockRows + t]);
-      const uint32_t k = __float_as_uint(D);
-      if (k >= kInfBits) continue;
-      vals[atomicAdd(&s_fill, 1u)] = k;
+      // one shared-memory atomic per warp for the slots of its kept rows
+      const unsigned mask = __ballot_sync(0xffffffffu, keep);
+      uint32_t base = 0;
+      if (lane == 0 && mask) base = atomicAdd(&s_fill, (uint32_t)__popc(mask));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (keep) vals[base + __popc(mask & ((1u << lane) - 1u))] = k;
     }
     scanned += take * kBlockRows;
   }
@@ -173,24 +198,23 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
     if (threadIdx.x == 0) tau[q] = INFINITY;
     return;
   }
-  // C-th smallest of vals[0..fill): three radix digits (11, 11, 10 bits)
+  // C-th smallest of vals[0..fill): four 8-bit radix digits
   uint32_t prefix = 0, need = (uint32_t)C;
   int known = 0;
-  const int shifts[3] = {21, 10, 0}, widths[3] = {11, 11, 10};
-  for (int pass = 0; pass < 3; ++pass) {
-    const int nb = 1 << widths[pass];
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int sh = 24 - 8 * pass;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < fill; i += blockDim.x) {
       const uint32_t k = vals[i];
       if (known && (k >> (32 - known)) != prefix) continue;
-      atomicAdd(&hist[(k >> shifts[pass]) & (nb - 1)], 1u);
+      atomicAdd(&hist[(k >> sh) & 255u], 1u);
     }
     __syncthreads();
-    find_bin(hist, nb, need, &s_bin, &s_below, scratch);
+    find_bin(hist, 256, need, &s_bin, &s_below, scratch);
     need -= s_below;
-    prefix = (prefix << widths[pass]) | s_bin;
-    known += widths[pass];
+    prefix = (prefix << 8) | s_bin;
+    known += 8;
     __syncthreads();
   }
   (void)s_total;
@@ -352,8 +376,10 @@ struct ProbedRowsSrc {
   }
 };
 
+constexpr int kSelDigits = 4, kSelBits = 8;  // radix select on the D bit pattern, 8 bits at a time
+
 struct SelSmem {
-  uint32_t hist[2048];
+  uint32_t hist[1 << kSelBits];
   unsigned long long keys[kMaxC];
   unsigned long long tk[kTieCap];
   uint32_t scratch[96];
@@ -361,20 +387,20 @@ struct SelSmem {
 };
 
 // The exact C smallest (D, id) of a source, written sorted to out_id/out_d
-// (pads: id 0xFFFFFFFF, +inf). Three radix digits of the D bit pattern find
-// the C-th smallest D; ties at that D are resolved by the smaller ids.
+// (pads: id 0xFFFFFFFF, +inf). Four 8-bit radix digits of the D bit pattern
+// find the C-th smallest D; ties at that D are resolved by the smaller ids.
 template <class Src>
 __device__ void select_topc(const Src& src, int C, SelSmem& S, uint32_t* __restrict__ out_id,
                             float* __restrict__ out_d) {
   uint32_t prefix = 0, need = (uint32_t)C;
   int known = 0;
   bool take_all = false;
-  const int shifts[3] = {21, 10, 0}, widths[3] = {11, 11, 10};
-  for (int pass = 0; pass < 3; ++pass) {
-    const int nb = 1 << widths[pass];
+  for (int pass = 0; pass < kSelDigits; ++pass) {
+    const int nb = 1 << kSelBits;
+    const int sh = 32 - kSelBits * (pass + 1);
     for (int i = threadIdx.x; i < nb; i += blockDim.x) S.hist[i] = 0;
     __syncthreads();
-    const int sh = shifts[pass], kn = known;
+    const int kn = known;
     const uint32_t pf = prefix;
     src.for_each([&](uint32_t k, uint32_t) {
       if (k >= kInfBits) return;
@@ -393,8 +419,8 @@ __device__ void select_topc(const Src& src, int C, SelSmem& S, uint32_t* __restr
     }
     find_bin(S.hist, nb, need, &S.s_bin, &S.s_below, S.scratch);
     need -= S.s_below;
-    prefix = (prefix << widths[pass]) | S.s_bin;
-    known += widths[pass];
+    prefix = (prefix << kSelBits) | S.s_bin;
+    known += kSelBits;
     __syncthreads();
   }
   const uint32_t T = take_all ? kInfBits : prefix;
@@ -463,12 +489,15 @@ __device__ void select_topc(const Src& src, int C, SelSmem& S, uint32_t* __restr
   }
 }
 
-constexpr int kFinalThreads = 512;
+constexpr int kFinalThreads = 128;  // small CTAs: many queries in flight per SM
 
-// One CTA per query: the pool from the survivors, or from every probed row
-// when the survivors overflowed their buffer.
-template <int RT, bool kFP8>
-__global__ void __launch_bounds__(kFinalThreads) k_final_select(
+// One CTA per query: the pool from the survivors (kFallback = false), or,
+// for the queries whose survivors overflowed their buffer, from every probed
+// row recomputed (kFallback = true). Both are launched; each CTA returns at
+// once for the queries of the other kind. Keeping the rare recompute out of
+// the common kernel keeps its registers low, and its occupancy high.
+template <int RT, bool kFP8, bool kFallback>
+__global__ void __launch_bounds__(kFinalThreads, kFallback ? 1 : 8) k_final_select(
     int nprobe, int C, uint32_t cap, const uint32_t* __restrict__ cnt, const unsigned long long* __restrict__ surv,
     const int32_t* __restrict__ probe, const uint32_t* __restrict__ pair_of, const uint32_t* __restrict__ blk_off,
     const uint32_t* __restrict__ grain_rows, const Coords cz, const float* __restrict__ rho,
@@ -478,6 +507,7 @@ __global__ void __launch_bounds__(kFinalThreads) k_final_select(
   __shared__ SelSmem S;
   const int q = blockIdx.x;
   const uint32_t n = cnt[q];
+  if ((n > cap) != kFallback) return;
   uint32_t* oid = cand_id + (size_t)q * C;  // rows are C (the batch's largest pool) apart
   float* od = cand_d + (size_t)q * C;
   if (qC) {  // mixed batch: this query's own pool size, the rest of its row padded
@@ -488,7 +518,7 @@ __global__ void __launch_bounds__(kFinalThreads) k_final_select(
     }
     C = Cq;
   }
-  if (n <= cap) {
+  if constexpr (!kFallback) {
     SurvivorSrc src{surv + (size_t)q * cap, n};
     select_topc(src, C, S, oid, od);
   } else {

@@ -24,8 +24,11 @@
 // blocks) from a global counter, so grains probed by many queries (hubs, in
 // high dimension) spread over the CTAs. An item first keeps the pairs that can
 // reach their pool from one of its blocks (rho_q + min rho_block <= tau_q, as
-// D >= rho_q + rho_i); per round of up to 128 of them the B operand is built
-// (one thread per pair), and blocks then flow through a two-deep pipeline:
+// D >= rho_q + rho_i). After that pruning most items of clustered data keep
+// one or two pairs, which is no contraction: an item with fewer than
+// kSTDense live pairs evaluates them row by row in the direct form. Denser
+// items, per round of up to 128 pairs, build the B operand (one thread per
+// pair), and blocks then flow through a two-deep pipeline:
 // convert block i
 // into A[i % 2], issue its MMAs into TMEM accumulator i % 2, and run the
 // epilogue of block i - 1 while they execute. Per row the scan streams only
@@ -46,6 +49,7 @@ namespace {
 
 constexpr int kSTBlocks = 8;    // blocks per work item (consecutive blocks of one grain)
 constexpr int kSTNeed = 1024;   // pairs of a grain one item can list after pruning
+constexpr int kSTDense = 8;     // from this many live pairs an item contracts on the tensor cores
 constexpr int kSTN = 128;       // pairs per round (MMA N <= 128)
 constexpr int kSTThreads = 128;  // thread t = row t = TMEM lane t
 
@@ -62,6 +66,18 @@ struct ScanTc {
   static constexpr int kSmem = 2 * kBytesA + 2 * kBytesB + kSTN * RT * 4 + 1024;
 };
 
+// Smallest residual norm of each grain's rows (+inf for an empty grain), one warp per grain.
+__global__ void k_grain_rho_min(const float* __restrict__ blk_rho_min, const uint32_t* __restrict__ blk_off, int G,
+                                float* __restrict__ out) {
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (g >= G) return;
+  float v = INFINITY;
+  for (uint32_t b = blk_off[g] + lane; b < blk_off[g + 1]; b += 32) v = fminf(v, blk_rho_min[b]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) out[g] = v;
+}
+
 // c_i = ||z_i||^2 + rho_i of every row, z_i decoded exactly as the scan decodes it.
 template <int RT>
 __global__ void __launch_bounds__(kBlockRows) k_row_c(const Coords cz, const float* __restrict__ rho,
@@ -77,13 +93,218 @@ __global__ void __launch_bounds__(kBlockRows) k_row_c(const Coords cz, const flo
   c_out[b * kBlockRows + t] = s + rho[b * kBlockRows + t];
 }
 
+// Per probed grain, the pairs that can reach their pool from some row of the
+// grain at all (rho_q + min rho over the grain <= tau_q, as D >= rho_q +
+// rho_i): their indices within the grain's pair list, compacted at the
+// grain's pair offset, and their number. One CTA per grain.
+__global__ void __launch_bounds__(128) k_grain_needed(const uint32_t* __restrict__ gcnt,
+                                                      const uint32_t* __restrict__ pair_off,
+                                                      const uint32_t* __restrict__ pair_q,
+                                                      const float* __restrict__ rhoq, const float* __restrict__ tau,
+                                                      const float* __restrict__ grain_rho_min,
+                                                      uint32_t* __restrict__ need_list,
+                                                      uint32_t* __restrict__ need_cnt) {
+  __shared__ uint32_t s_n;
+  const uint32_t g = blockIdx.x, m = gcnt[g], p0 = pair_off[g];
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  const float rmin = grain_rho_min[g];
+  for (uint32_t s = threadIdx.x; s < m; s += blockDim.x) {
+    if (rhoq[p0 + s] + rmin <= tau[pair_q[p0 + s]]) need_list[p0 + atomicAdd(&s_n, 1u)] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) need_cnt[g] = s_n;
+}
+
+// Sorts the scan's work items by how many of their grain's live pairs can
+// still reach their pool from the item's blocks (rho_q + min rho_block <=
+// tau_q): none (dropped), a few (the direct-form kernel), at least kSTDense
+// (the tensor-core kernel). One warp per item. lists: [0] dense count, [1]
+// sparse count.
+__global__ void k_scan_classify(const uint4* __restrict__ items, const uint32_t* __restrict__ n_items,
+                                const uint32_t* __restrict__ need_cnt, const uint32_t* __restrict__ need_list,
+                                const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ pair_q,
+                                const float* __restrict__ rhoq, const float* __restrict__ tau,
+                                const float* __restrict__ blk_rho_min, uint4* __restrict__ dense,
+                                uint4* __restrict__ sparse, uint32_t* __restrict__ lists) {
+  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= *n_items) return;
+  const uint4 item = items[w];
+  float v = (uint32_t)lane < item.z ? blk_rho_min[item.y + lane] : INFINITY;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const uint32_t m = need_cnt[item.x], p0 = pair_off[item.x];
+  uint32_t n = 0;
+  for (uint32_t s0 = 0; s0 < m && n < (uint32_t)kSTDense; s0 += 32) {
+    const uint32_t s = s0 + lane;
+    bool need = false;
+    if (s < m) {
+      const uint32_t pr = p0 + need_list[p0 + s];
+      need = rhoq[pr] + v <= tau[pair_q[pr]];
+    }
+    n += __popc(__ballot_sync(0xffffffffu, need));
+  }
+  if (lane == 0 && n) {
+    if (n >= (uint32_t)kSTDense) dense[atomicAdd(&lists[0], 1u)] = item;
+    else sparse[atomicAdd(&lists[1], 1u)] = item;
+  }
+}
+
+constexpr int kSPThreads = 128;
+
+// Direct-form scan of the items with fewer than kSTDense live pairs: one row
+// per thread, the item's blocks streamed with two blocks of codes prefetched
+// in registers, each live pair evaluated by eval_D (the same function, on the
+// same decoded coordinates, as the pilot and the pool fallback).
+template <int RT>
+__global__ void __launch_bounds__(kSPThreads, 6) k_scan_sparse(
+    const uint4* __restrict__ items, const uint32_t* __restrict__ lists, uint32_t* __restrict__ next_item,
+    const uint32_t* __restrict__ blk_off, const uint32_t* __restrict__ grain_rows, const uint8_t* __restrict__ Z8b,
+    const float* __restrict__ scale, const float* __restrict__ rho, const uint32_t* __restrict__ ids,
+    const int64_t* __restrict__ attr_b, int r, int rp, const uint32_t* __restrict__ need_cnt,
+    const uint32_t* __restrict__ need_list,
+    const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ pair_q, const float* __restrict__ zq,
+    const float* __restrict__ rhoq, const float* __restrict__ tau, const float* __restrict__ blk_rho_min,
+    const int64_t* __restrict__ filter, uint32_t cap, uint32_t* __restrict__ cnt,
+    unsigned long long* __restrict__ surv) {
+  constexpr int kL = RT / 16;
+  constexpr int kP = kSTDense - 1;  // at most this many live pairs per item
+  __shared__ __align__(16) float sz[kP][RT];
+  __shared__ float4 spc[kP];  // {unused, unused, tau_q, rho_q}
+  __shared__ uint32_t sqid[kP], s_need[kP];
+  __shared__ long long slo[kP], shi[kP];
+  __shared__ uint32_t s_nneed, s_item;
+  __shared__ float s_rmin;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const uint32_t total = lists[1];
+  const int nks = rp / 16;
+  for (;;) {
+    __syncthreads();  // every thread is done with the previous item
+    if (t == 0) s_item = atomicAdd(next_item, 1u);
+    __syncthreads();
+    const uint32_t w = s_item;
+    if (w >= total) break;
+    const uint4 item = items[w];
+    const uint32_t g = item.x, b0 = item.y, nb = item.z;
+    const uint32_t m = need_cnt[g], p_begin = pair_off[g], n_g = grain_rows[g], gb0 = blk_off[g];
+    const float s_g = scale[g];
+    // prefetch the first two blocks while the pairs are gathered
+    uint4 cur[kL], nxt[kL];
+    float rho_cur = 0.f, rho_nxt = 0.f, rmin_cur = 0.f, rmin_nxt = 0.f;
+    auto load_block = [&](uint32_t i, uint4 (&codes)[kL], float& rh, float& rmin) {
+      const size_t b = b0 + i;
+#pragma unroll
+      for (int l = 0; l < kL; ++l)
+        if (l < nks)
+          codes[l] = __ldg(reinterpret_cast<const uint4*>(Z8b + ((b * (size_t)nks + l) * kBlockRows + t) * 16));
+      rh = rho[b * kBlockRows + t];
+      rmin = blk_rho_min[b];
+    };
+    load_block(0, cur, rho_cur, rmin_cur);
+    if (nb > 1) load_block(1, nxt, rho_nxt, rmin_nxt);
+    if (warp == 0) {
+      float v = (uint32_t)lane < nb ? blk_rho_min[b0 + lane] : INFINITY;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (lane == 0) {
+        s_rmin = v;
+        s_nneed = 0;
+      }
+    }
+    __syncthreads();
+    const float rmin_item = s_rmin;
+    for (uint32_t i = t; i < m; i += kSPThreads) {
+      const uint32_t sidx = need_list[p_begin + i];
+      const uint32_t pr = p_begin + sidx;
+      if (rhoq[pr] + rmin_item <= tau[pair_q[pr]]) {
+        const uint32_t pos = atomicAdd(&s_nneed, 1u);
+        if (pos < (uint32_t)kP) s_need[pos] = sidx;
+      }
+    }
+    __syncthreads();
+    const int np = (int)min(s_nneed, (uint32_t)kP);  // the classifier found fewer than kSTDense
+    for (int e = t; e < np * RT; e += kSPThreads) {
+      const int j = e / RT, a = e % RT;
+      const uint32_t pr = p_begin + s_need[j];
+      sz[j][a] = a < r ? zq[(size_t)pr * r + a] : 0.f;
+    }
+    if (t < np) {
+      const uint32_t pr = p_begin + s_need[t];
+      const uint32_t q = pair_q[pr];
+      spc[t] = make_float4(0.f, 0.f, tau[q], rhoq[pr]);
+      sqid[t] = q;
+      if (filter) {
+        slo[t] = (long long)filter[2 * (size_t)q];
+        shi[t] = (long long)filter[2 * (size_t)q + 1];
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = 0; i < nb; ++i) {
+      const size_t b = b0 + i;
+      const bool valid = (uint32_t)(b - gb0) * kBlockRows + t < n_g;
+      float z[RT];
+#pragma unroll
+      for (int l = 0; l < kL; ++l) {
+        if (l < nks) {
+          const uint32_t wv[4] = {cur[l].x, cur[l].y, cur[l].z, cur[l].w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float2 a2 = __half22float2(
+                __half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(wv[h] & 0xFFFFu), __NV_E4M3)));
+            const float2 e2 = __half22float2(
+                __half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(wv[h] >> 16), __NV_E4M3)));
+            z[l * 16 + 4 * h + 0] = a2.x * s_g;
+            z[l * 16 + 4 * h + 1] = a2.y * s_g;
+            z[l * 16 + 4 * h + 2] = e2.x * s_g;
+            z[l * 16 + 4 * h + 3] = e2.y * s_g;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) z[l * 16 + k] = 0.f;
+        }
+      }
+      const float rho_i = rho_cur, rmin = rmin_cur;
+      for (int j = 0; j < np; ++j) {
+        const float4 pc = spc[j];
+        if (pc.w + rmin > pc.z) continue;  // block-uniform: no row of this block reaches the pool
+        const float D = eval_D<RT>(&sz[j][0], z, pc.w, rho_i);
+        bool ok = valid && D <= pc.z;
+        if (ok && filter) {
+          const long long av = (long long)attr_b[b * kBlockRows + t];
+          ok = av >= slo[j] && av <= shi[j];
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, ok);
+        if (mask) {
+          const int leader = __ffs(mask) - 1;
+          uint32_t base = 0;
+          if (lane == leader) base = atomicAdd(&cnt[sqid[j]], (uint32_t)__popc(mask));
+          base = __shfl_sync(0xffffffffu, base, leader);
+          if (ok) {
+            const uint32_t pos = base + __popc(mask & lt_mask);
+            if (pos < cap)
+              surv[(size_t)sqid[j] * cap + pos] = ((unsigned long long)__float_as_uint(D) << 32) | ids[b * kBlockRows + t];
+          }
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < kL; ++l) cur[l] = nxt[l];
+      rho_cur = rho_nxt;
+      rmin_cur = rmin_nxt;
+      if (i + 2 < nb) load_block(i + 2, nxt, rho_nxt, rmin_nxt);
+    }
+  }
+}
+
 template <int RT>
 __global__ void __launch_bounds__(kSTThreads, 2) k_scan_tc(
     const uint4* __restrict__ items, const uint32_t* __restrict__ n_items, uint32_t* __restrict__ next_item,
     const uint32_t* __restrict__ blk_off, const uint32_t* __restrict__ grain_rows, const uint8_t* __restrict__ Z8b,
     const float* __restrict__ scale, const float* __restrict__ crow, const float* __restrict__ rho,
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r, int rp,
-    const uint32_t* __restrict__ gcnt, const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ pair_q,
+    const uint32_t* __restrict__ need_cnt, const uint32_t* __restrict__ need_list,
+    const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ pair_q,
     const float* __restrict__ zq, const float* __restrict__ rhoq, const float* __restrict__ tau,
     const float* __restrict__ blk_rho_min, const int64_t* __restrict__ filter, uint32_t cap,
     uint32_t* __restrict__ cnt, unsigned long long* __restrict__ surv, int* __restrict__ err) {
@@ -130,7 +351,7 @@ __global__ void __launch_bounds__(kSTThreads, 2) k_scan_tc(
     if (w >= total || failed) break;
     const uint4 item = items[w];
     const uint32_t g = item.x, b0 = item.y, nb = item.z;
-    const uint32_t m = gcnt[g], p_begin = pair_off[g], n_g = grain_rows[g], gb0 = blk_off[g];
+    const uint32_t m = need_cnt[g], p_begin = pair_off[g], n_g = grain_rows[g], gb0 = blk_off[g];
     const float s_g = scale[g];
     // pairs that can reach their pool from some block of this item (D >= rho_q + rho_i)
     if (warp == 0) {
@@ -144,16 +365,17 @@ __global__ void __launch_bounds__(kSTThreads, 2) k_scan_tc(
     }
     __syncthreads();
     const float rmin_item = s_rmin;
-    for (uint32_t s = t; s < m; s += kSTThreads) {
-      const uint32_t pr = p_begin + s;
+    for (uint32_t i = t; i < m; i += kSTThreads) {
+      const uint32_t sidx = need_list[p_begin + i];
+      const uint32_t pr = p_begin + sidx;
       if (rhoq[pr] + rmin_item <= tau[pair_q[pr]]) {
         const uint32_t pos = atomicAdd(&s_nneed, 1u);
-        if (pos < (uint32_t)kSTNeed) s_need[pos] = s;
+        if (pos < (uint32_t)kSTNeed) s_need[pos] = sidx;
       }
     }
     __syncthreads();
     const uint32_t nneed = s_nneed;
-    const bool listed = nneed <= (uint32_t)kSTNeed;  // else walk every pair of the grain
+    const bool listed = nneed <= (uint32_t)kSTNeed;  // else walk every live pair of the grain
     const uint32_t nwalk = listed ? nneed : m;
     for (uint32_t s0 = 0; s0 < nwalk && !failed; s0 += kSTN) {
       const int np = (int)min((uint32_t)kSTN, nwalk - s0);
@@ -161,7 +383,7 @@ __global__ void __launch_bounds__(kSTThreads, 2) k_scan_tc(
       __syncthreads();  // every thread is done with the previous round's pair data
       // ---- B operand and per-pair constants, one thread per pair
       if (t < np) {
-        const uint32_t pr = p_begin + (listed ? s_need[s0 + t] : s0 + t);
+        const uint32_t pr = p_begin + (listed ? s_need[s0 + t] : need_list[p_begin + s0 + t]);
         float zv[RT];
 #pragma unroll
         for (int a = 0; a < RT; ++a) zv[a] = a < r ? zq[(size_t)pr * r + a] : 0.f;
@@ -210,17 +432,78 @@ __global__ void __launch_bounds__(kSTThreads, 2) k_scan_tc(
       uint4 cur[kL], nxt[kL];
       float c_cur = 0.f, c_nxt = 0.f, c_prev = 0.f;
       float rmin_cur = 0.f, rmin_nxt = 0.f, rmin_prev = 0.f;
+      const bool dense = np >= kSTDense;
       auto load_block = [&](uint32_t i, uint4 (&codes)[kL], float& c, float& rmin) {
         const size_t b = b0 + i;
 #pragma unroll
         for (int l = 0; l < kL; ++l)
           if (l < nks)
             codes[l] = __ldg(reinterpret_cast<const uint4*>(Z8b + ((b * (size_t)nks + l) * kBlockRows + t) * 16));
-        c = crow[b * kBlockRows + t];
+        c = dense ? crow[b * kBlockRows + t] : rho[b * kBlockRows + t];  // c_i, or rho_i for the direct path
         rmin = blk_rho_min[b];
       };
       load_block(0, cur, c_cur, rmin_cur);
       if (nb > 1) load_block(1, nxt, c_nxt, rmin_nxt);
+      if (!dense) {
+        // ---- few live pairs: each thread evaluates its row against them directly (the
+        // same eval_D on the same decoded coordinates as the pilot and the fallback)
+        __syncthreads();  // pair data written
+        for (uint32_t i = 0; i < nb; ++i) {
+          const size_t b = b0 + i;
+          const bool valid = (uint32_t)(b - gb0) * kBlockRows + t < n_g;
+          float z[RT];
+#pragma unroll
+          for (int l = 0; l < kL; ++l) {
+            if (l < nks) {
+              const uint32_t wv[4] = {cur[l].x, cur[l].y, cur[l].z, cur[l].w};
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {
+                const float2 a2 = __half22float2(
+                    __half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(wv[h] & 0xFFFFu), __NV_E4M3)));
+                const float2 e2 = __half22float2(
+                    __half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(wv[h] >> 16), __NV_E4M3)));
+                z[l * 16 + 4 * h + 0] = a2.x * s_g;
+                z[l * 16 + 4 * h + 1] = a2.y * s_g;
+                z[l * 16 + 4 * h + 2] = e2.x * s_g;
+                z[l * 16 + 4 * h + 3] = e2.y * s_g;
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < 16; ++k) z[l * 16 + k] = 0.f;
+            }
+          }
+          const float rho_i = c_cur, rmin = rmin_cur;
+          for (int j = 0; j < np; ++j) {
+            const float4 pc = spc[j];
+            if (pc.w + rmin > pc.z) continue;  // block-uniform: no row of this block reaches the pool
+            const float D = eval_D<RT>(sz + j * RT, z, pc.w, rho_i);
+            bool ok = valid && D <= pc.z;
+            if (ok && filter) {
+              const long long av = (long long)attr_b[b * kBlockRows + t];
+              ok = av >= slo[j] && av <= shi[j];
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, ok);
+            if (mask) {
+              const int leader = __ffs(mask) - 1;
+              uint32_t base = 0;
+              if (lane == leader) base = atomicAdd(&cnt[sqid[j]], (uint32_t)__popc(mask));
+              base = __shfl_sync(0xffffffffu, base, leader);
+              if (ok) {
+                const uint32_t pos = base + __popc(mask & lt_mask);
+                if (pos < cap)
+                  surv[(size_t)sqid[j] * cap + pos] =
+                      ((unsigned long long)__float_as_uint(D) << 32) | ids[b * kBlockRows + t];
+              }
+            }
+          }
+#pragma unroll
+          for (int l = 0; l < kL; ++l) cur[l] = nxt[l];
+          c_cur = c_nxt;
+          rmin_cur = rmin_nxt;
+          if (i + 2 < nb) load_block(i + 2, nxt, c_nxt, rmin_nxt);
+        }
+        continue;
+      }
       for (uint32_t i = 0; i <= nb; ++i) {
         if (i < nb) {
           uint8_t* a = sA + (i & 1) * P::kBytesA;

@@ -70,20 +70,9 @@ __global__ void k_probe_dist(const float* __restrict__ Q, const float* __restric
     g = 0;
   }
   const float* q = Q + (size_t)(w / nprobe) * d;
-  float acc = 0.f;
-  for (int t = lane; t < d; t += 32) {
-    float qv = q[t], mv;
-    if (kBF16) {
-      qv = __bfloat162float(__float2bfloat16_rn(qv));
-      mv = __uint_as_float((uint32_t)Mh[(size_t)g * d + t] << 16);
-    } else {
-      mv = M[(size_t)g * d + t];
-    }
-    const float df = qv - mv;
-    acc = fmaf(df, df, acc);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  // the same arithmetic, in the same order, as the routing refine (warp_center_dist2)
+  float acc = warp_center_dist2<kBF16>(
+      [&](int t) { return kBF16 ? __bfloat162float(__float2bfloat16_rn(q[t])) : q[t]; }, M, Mh, g, d, lane);
   if (lane == 0) {
     probe[w] = g;
     probe_d[w] = acc;
@@ -294,6 +283,10 @@ struct Ws {
   uint4* slots;    // tensor-core projection slots of <= 32 pairs (precision form)
   uint32_t* scan_off;  // per-grain offsets of the tensor-core scan's work items (precision form)
   uint4* scan_items;   // {grain, first block, blocks} of each probed grain (precision form)
+  uint4* dense_items;  // the items with many live pairs (tensor-core scan)
+  uint32_t* need_list; // per grain, its pairs that can reach their pool (indices, at the grain's pair offset)
+  uint32_t* need_cnt;  // per grain, how many
+  uint4* sparse_items; // the items with a few (direct-form scan)
   float* zq;
   float* rhoq;
   float* tau;
@@ -327,10 +320,16 @@ Ws carve(const Index& I, uint32_t nq, uint32_t C, uint32_t nprobe, void* base) {
   w.slots = tcp ? c.take<uint4>(P / kPSlot + I.G) : nullptr;
   w.scan_off = tcp ? c.take<uint32_t>(I.G + 1) : nullptr;
   w.scan_items = tcp ? c.take<uint4>(I.G + I.n_blocks / kSTBlocks + 1) : nullptr;
+  w.dense_items = tcp ? c.take<uint4>(I.G + I.n_blocks / kSTBlocks + 1) : nullptr;
+  w.need_list = tcp ? c.take<uint32_t>(P) : nullptr;
+  w.need_cnt = tcp ? c.take<uint32_t>(I.G) : nullptr;
+  w.sparse_items = tcp ? c.take<uint4>(I.G + I.n_blocks / kSTBlocks + 1) : nullptr;
   w.zq = c.take<float>(P * I.r);
   w.rhoq = c.take<float>(P);
   w.tau = c.take<float>(nq);
-  w.cnt = c.take<uint32_t>((size_t)nq + 1);  // survivor counts, then the scan's work counter
+  // survivor counts, then the scan's counters: [nq] next dense item, [nq + 1] dense items,
+  // [nq + 2] sparse items, [nq + 3] next sparse item
+  w.cnt = c.take<uint32_t>((size_t)nq + 4);
   w.cap = survivor_cap(C);
   w.surv = c.take<unsigned long long>((size_t)nq * w.cap);
   w.cand_id = c.take<uint32_t>((size_t)nq * C);
@@ -443,21 +442,33 @@ void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, 
       attr_dev = I.device;
     }
     const size_t max_items = (size_t)I.G + I.n_blocks / kSTBlocks + 1;
-    const unsigned grid = (unsigned)std::min<size_t>(max_items, (size_t)I.num_sms * 2);
-    k_scan_tc<RT><<<grid, kSTThreads, ScanTc<RT>::kSmem, st>>>(
-        w.scan_items, w.scan_off + I.G, w.cnt + nq, I.blk_off, I.grain_rows, I.Z8b, I.scale, I.crow, I.rho, I.ids, I.attr_b,
-        (int)I.r, (int)I.rp, w.gcnt, w.pair_off, w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap, w.cnt,
-        w.surv, I.d_err);
+    uint32_t* lists = w.cnt + nq + 1;  // dense count, sparse count, next sparse item
+    k_grain_needed<<<I.G, 128, 0, st>>>(w.gcnt, w.pair_off, w.pair_q, w.rhoq, w.tau, I.grain_rho_min, w.need_list,
+                                        w.need_cnt);
+    k_scan_classify<<<(unsigned)((max_items * 32 + 255) / 256), 256, 0, st>>>(
+        w.scan_items, w.scan_off + I.G, w.need_cnt, w.need_list, w.pair_off, w.pair_q, w.rhoq, w.tau, I.blk_rho_min,
+        w.dense_items, w.sparse_items, lists);
+    k_scan_sparse<RT><<<(unsigned)std::min<size_t>(max_items, (size_t)I.num_sms * 16), kSPThreads, 0, st>>>(
+        w.sparse_items, lists, lists + 2, I.blk_off, I.grain_rows, I.Z8b, I.scale, I.rho, I.ids, I.attr_b, (int)I.r,
+        (int)I.rp, w.need_cnt, w.need_list, w.pair_off, w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap,
+        w.cnt, w.surv);
+    k_scan_tc<RT><<<(unsigned)std::min<size_t>(max_items, (size_t)I.num_sms * 2), kSTThreads, ScanTc<RT>::kSmem,
+                    st>>>(
+        w.dense_items, lists, w.cnt + nq, I.blk_off, I.grain_rows, I.Z8b, I.scale, I.crow, I.rho, I.ids, I.attr_b,
+        (int)I.r, (int)I.rp, w.need_cnt, w.need_list, w.pair_off, w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min,
+        filter, w.cap, w.cnt, w.surv, I.d_err);
   } else {
     k_scan_filter<RT, kFP8><<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(
         I.blk_grain, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b, (int)I.r, (int)I.rp, w.gcnt, w.pair_off,
         w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap, w.cnt, w.surv);
   }
   mark(5);
-  k_final_select<RT, kFP8><<<nq, kFinalThreads, 0, st>>>(nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of,
-                                                         I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b,
-                                                         (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id,
-                                                         w.cand_d, qC);
+  k_final_select<RT, kFP8, false><<<nq, kFinalThreads, 0, st>>>(
+      nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b,
+      (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id, w.cand_d, qC);
+  k_final_select<RT, kFP8, true><<<nq, kFinalThreads, 0, st>>>(
+      nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b,
+      (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id, w.cand_d, qC);
 }
 
 template <int RT>
@@ -565,7 +576,7 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
                                               w.pair_q, w.zq, w.rhoq);
   }
   mark(3);
-  HNTL_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * ((size_t)nq + 1), st));
+  HNTL_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * ((size_t)nq + 4), st));
   {
     const std::function<void(int)> mk = mark;
     if (I.r <= 8) launch_scan_select_p<8>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk, qC);
@@ -656,8 +667,9 @@ int finalize_index(Index& I) {
     I.gram = static_cast<float*>(alloc(sizeof(float) * I.G * I.r * I.r));
     I.Mrep = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * 8 * I.d));
     I.crow = static_cast<float*>(alloc(sizeof(float) * I.n_blocks * kBlockRows));
+    I.grain_rho_min = static_cast<float*>(alloc(sizeof(float) * I.G));
   }
-  if (!I.d_err || !I.mnorm || (bf16 && (!I.Mh || !I.Uh || !I.gram || !I.Mrep || !I.crow)))
+  if (!I.d_err || !I.mnorm || (bf16 && (!I.Mh || !I.Uh || !I.gram || !I.Mrep || !I.crow || !I.grain_rho_min)))
     return fail(HNTL_ENOMEM, "index: derived arrays");
   HNTL_CUDA_TRY(cudaMemset(I.d_err, 0, sizeof(int)));
   if (bf16) k_row_norms<true><<<(I.G * 32 + 255) / 256, 256>>>(I.M, (int)I.G, (int)I.d, I.mnorm);
@@ -668,6 +680,7 @@ int finalize_index(Index& I) {
     k_to_bf16_rows<<<(unsigned)((nu + 255) / 256), 256>>>(I.U, nu, I.Uh);
     k_gram<<<I.G, 256>>>(I.Uh, (int)I.d, (int)I.r, I.gram);
     k_negate_rep8_bf16<<<(unsigned)((n * 8 + 255) / 256), 256>>>(I.Mh, (int)I.G, (int)I.d, I.Mrep);
+    k_grain_rho_min<<<(I.G * 32 + 255) / 256, 256>>>(I.blk_rho_min, I.blk_off, (int)I.G, I.grain_rho_min);
     const Coords cz{I.Zb, I.Z8b, I.scale};
     if (I.n_blocks) {
       if (I.r <= 16) k_row_c<16><<<(unsigned)I.n_blocks, kBlockRows>>>(cz, I.rho, I.blk_grain, (int)I.rp, I.crow);
@@ -716,6 +729,19 @@ int hntl_profile_read(double* ms, uint64_t* calls) {
     P.pool.push_back(ev);
   }
   P.pending.clear();
+  return HNTL_OK;
+}
+
+int hntl_search_survivors(const hntl_index* idx, const void* d_ws, size_t ws_bytes, uint32_t nq, uint32_t C,
+                          uint32_t nprobe, uint32_t* d_counts, void* stream) {
+  hntl::clear_error();
+  if (!idx || !d_ws || !d_counts) return hntl::fail(HNTL_EINVAL, "null argument");
+  uint32_t Ce = C;
+  if (hntl::check_params(idx->I, nq, 1, Ce, nprobe)) return HNTL_EINVAL;
+  const hntl::Ws w = hntl::carve(idx->I, nq, Ce, nprobe, const_cast<void*>(d_ws));
+  if (ws_bytes < w.bytes) return hntl::fail(HNTL_EINVAL, "workspace too small");
+  HNTL_CUDA_TRY(cudaMemcpyAsync(d_counts, w.cnt, sizeof(uint32_t) * nq, cudaMemcpyDeviceToDevice,
+                                static_cast<cudaStream_t>(stream)));
   return HNTL_OK;
 }
 

@@ -424,6 +424,16 @@ class ServerStats(ctypes.Structure):
 lib.hntl_server_get_stats.argtypes = [_P, ctypes.POINTER(ServerStats)]
 
 
+lib.hntl_search_survivors.argtypes = [_P, _P, _SZ, _U32, _U32, _U32, _P, _P]
+
+
+def search_survivors(index: Index, ws: torch.Tensor, nq: int, C: int, nprobe: int) -> torch.Tensor:
+    """Pool survivors per query of the last search run in workspace `ws` (see hntl_search_survivors)."""
+    out = torch.empty(nq, dtype=torch.int32, device=ws.device)
+    _check(lib.hntl_search_survivors(index.handle, _ptr(ws), ws.numel(), nq, C, nprobe, _ptr(out), None))
+    return out
+
+
 def selftest_wait_timeout(index: Index, polls: int = 64):
     _check(lib.hntl_selftest_wait_timeout(index.handle, int(polls), None))
 

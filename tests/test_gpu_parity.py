@@ -190,7 +190,7 @@ def test_invalid_arguments(hntl, tmp_path):
 
 
 def test_survivor_overflow_falls_back_exactly(hntl, tmp_path):
-    """One 100k-row grain with C=1000: the pilot sees a 4096-row sample, so its
+    """One 100k-row grain with C=1000: the pilot sees at most a 2048-row sample, so its
     bound admits far more than the survivor buffer holds; the pool must then
     come from every probed row, recomputed, with the same result."""
     rng = np.random.default_rng(11)
