@@ -215,16 +215,19 @@ def stage_bytes(idx, rows_g, probe: np.ndarray, w: dict, batch: int):
     }
 
 
-def traffic_from_profiles(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, when it
-    was taken on the current kernel source (else None)."""
+def traffic_from_profiles(workload: str, stage: str):
+    """DRAM bytes per launch of the kernels of `stage` on `workload`, from the
+    committed ncu summary (profiles/ncu_traffic.json), when it was taken on the
+    current source of those kernels; else None. Entries captured on a smaller
+    case carry the factor that scales them to a full launch."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
-        rec = json.load(open(p)).get(kernel)
-        src = open(os.path.join(ROOT, "paper_2606_08813_b300", "csrc", rec["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha"]:
-            return None
-        return rec["dram_bytes_per_launch"]
+        rec = json.load(open(p))[workload][stage]
+        for src, sha in rec["source_sha"].items():
+            data = open(os.path.join(ROOT, "paper_2606_08813_b300", "csrc", src), "rb").read()
+            if hashlib.sha256(data).hexdigest()[:16] != sha:
+                return None
+        return int(rec["dram_bytes_per_launch"] * rec.get("scale_to_full_launch", 1.0))
     except Exception:
         return None
 
@@ -386,6 +389,48 @@ def run_serving(a, hntl, gi, X, Q, attr, w, sd):
             "seconds_per_rate": a.serve_seconds}
 
 
+def run_fp32_compare(a, hntl, X, Q, w, sd, B, n_recall, truth, line):
+    """The plain FP32 method (FP32 rows, coordinates, bases; TF32 routing with
+    an exact refine; direct-form FP32 scan) on the same data, k-means draws,
+    batch and parameters: its QPS and recall beside the precision form's."""
+    t0 = time.perf_counter()
+    gf = hntl.Index.build(X, w["G"], w["r"], u=synth.uniforms(w["G"], sd["kmeans"]).numpy(), seed=sd["kmeans"],
+                          precision=hntl.PREC_FP32)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    k, C, nprobe = w["k"], w["C"], w["nprobe"]
+    nb = w["nq"] // B
+    batches = [Q[i * B:(i + 1) * B].contiguous() for i in range(nb)]
+    found = [gf.search(batches[i], k, C, nprobe)[0] for i in range(max(1, (n_recall + B - 1) // B))]
+    rec = recall_at_k(torch.cat(found)[:n_recall], truth) if n_recall else None
+    out = (torch.empty(B, k, dtype=torch.int64, device=Q.device), torch.empty(B, k, dtype=torch.float32,
+                                                                            device=Q.device))
+    for i in range(a.warmup):
+        gf.search(batches[i % nb], k, C, nprobe, out=out)
+    torch.cuda.synchronize()
+    hntl.profile_read()
+    hntl.profile_enable(True)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(10, a.steps // 2)
+    e0.record(st)
+    for i in range(steps):
+        gf.search(batches[i % nb], k, C, nprobe, out=out)
+    e1.record(st)
+    torch.cuda.synchronize()
+    hntl.profile_enable(False)
+    sm, calls = hntl.profile_read()
+    ms = e0.elapsed_time(e1) / steps
+    qps = B / (ms / 1e3)
+    del gf
+    torch.cuda.empty_cache()
+    return {"value": round(qps, 1), "unit": "queries/s", "ms_per_step": round(ms, 4),
+            "recall_at_10": None if rec is None else round(rec, 4), "index_build_s": round(build_s, 2),
+            "stages_ms": {k_: round(v_ / max(calls, 1), 4) for k_, v_ in sm.items()},
+            "precision_form_gain": round(line["value"] / qps, 3),
+            "note": "same rows, k-means draws, batch, nprobe, C and k; FP32 rows, coordinates and bases"}
+
+
 def run_ours(a, world, rank, local):
     from paper_2606_08813_b300 import build_lib
 
@@ -433,6 +478,7 @@ def run_ours(a, world, rank, local):
                   "overflowed": int((surv > cap).sum()), "queries": int(len(surv))}
     n_recall = 0 if a.profile_mode else min(w["nq"], a.recall_queries)
     rec = float("nan")
+    truth = None
     if n_recall:
         truth = exact_topk(X, Q[:n_recall], 10)
         rec = recall_at_k(torch.cat(found)[:n_recall], truth)
@@ -485,7 +531,7 @@ def run_ours(a, world, rank, local):
     if dom in mean_bytes:
         ach = mean_bytes[dom] / (per_launch_ms[dom] / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 4), "traffic": traffic_from_profiles(dom), "peak_source": src,
+                "frac": round(ach / hbm, 4), "traffic": traffic_from_profiles(a.workload, dom), "peak_source": src,
                 "algorithmic_bytes_per_launch": int(mean_bytes[dom])}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
@@ -517,6 +563,8 @@ def run_ours(a, world, rank, local):
     }
     if serve:
         line["serving"] = run_serving(a, hntl, gi, X, Q, attr, w, sd)
+    if prec == "bf16-fp8" and a.fp32_compare and X is not None:
+        line["plain_fp32_same_data"] = run_fp32_compare(a, hntl, X, Q, w, sd, B, n_recall, truth, line)
     if rank == 0 and world == 1 and not a.no_cpu_baseline and not a.profile_mode:
         host = gi.export()
         Xn = X.cpu().numpy()
@@ -613,7 +661,7 @@ def run_router(a, world, rank, local):
     # evaluation: exact ground truth, centroid vs learned routing
     truth = exact_topk(X, Qev, 10)
     out = []
-    for nprobe in (4, 8, 16, 32, 64):
+    for nprobe in (1, 2, 4, 8, 16, 32, 64):
         ids_c, _ = gi.search(Qev, 10, w["C"], nprobe)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -709,6 +757,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-recall", type=int, default=1536, help="served requests checked against brute force")
     ap.add_argument("--serve-p99-ms", type=float, default=50.0)
+    ap.add_argument("--no-fp32-compare", dest="fp32_compare", action="store_false",
+                    help="skip timing the plain FP32 method on the same data (precision workloads)")
     ap.add_argument("--router-train", type=int, default=200_000)
     ap.add_argument("--router-epochs", type=int, default=8)
     ap.add_argument("--router-batch", type=int, default=1024)

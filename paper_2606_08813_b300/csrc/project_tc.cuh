@@ -57,10 +57,10 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int byte) {
 // quarter j, columns j*RN.., holds z of slot j's pairs; the other columns
 // (pairs against the other slots' bases) are computed and ignored.
 // CTA b takes items b, b + grid, ...
-//   warps 0-3  producers: per K block of 64 coordinates, each thread stores
-//              its pair's query row (16-byte loads prefetched two K blocks
-//              ahead, swizzled stores, proxy fence, arrival on the stage's
-//              `full` barrier); TMA brings the negated centre of each slot's
+//   warps 0-3  producers: per K block of 64 coordinates, the pairs' query
+//              rows (coalesced 16-byte loads prefetched two K blocks ahead,
+//              swizzled stores, proxy fence, arrival on the stage's `full`
+//              barrier); TMA brings the negated centre of each slot's
 //              grain (8 identical rows per load, from a replicated copy) and
 //              the 4 bases (one load each) into the same stage, counted on
 //              `full` by transaction bytes.
@@ -130,10 +130,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
 
   if (warp < 4) {
     // ------------------------------------------------------------ producers
-    // thread t owns A row t (slot t / 32, pair t % 32): its query row moves by
-    // 16-byte loads, prefetched two K blocks ahead in registers, and swizzled
-    // stores; the negated centres (8 identical rows per load) and the bases
-    // move by TMA into 1024-byte aligned boxes.
+    // A row i is pair i % 32 of slot i / 32. The query rows move by 16-byte
+    // loads, 8 lanes per row, prefetched two K blocks ahead in registers, and
+    // swizzled stores; the negated centres (8 identical rows per load) and the
+    // bases move by TMA into 1024-byte aligned boxes.
     uint32_t it = 0;  // K blocks issued by this CTA so far
     bool failed = false;  // uniform over the producers (decided by barrier reductions)
     const int my_j = tid >> 5, my_i = tid & 31;
@@ -153,9 +153,18 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
       tc::named_bar(1, 128);
       if (failed) continue;
       const uint4 mine = sslot[my_j];
-      const bool row_ok = (uint32_t)my_i < mine.z;
-      const uint16_t* qrow = Qh + (size_t)sq[tid] * d;
-      const uint32_t swz = (uint32_t)(tid & 7);
+      // query rows move 8 lanes per row (one 128-byte line per 8 lanes): thread t
+      // carries chunk t % 8 of rows t / 8 + 16 i, i < 8, so every warp load covers
+      // 4 whole lines
+      const int ch = tid & 7, rbase = tid >> 3;
+      const uint16_t* qsrc[8];
+      bool qok[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int row = rbase + 16 * i;
+        qok[i] = (uint32_t)(row & 31) < sslot[row >> 5].z;
+        qsrc[i] = Qh + (size_t)sq[row] * d + ch * 8;
+      }
       // TMA bytes one stage receives: 8-row groups of the negated centre
       // covering each slot's pairs, the bases of the slots with pairs
       uint32_t bytes = 0;
@@ -166,11 +175,11 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
       }
       uint4 qa[8], qb[8];
       auto load_q = [&](int kb, uint4 (&v)[8]) {
+        const int kk = kb * kPKB + ch * 8;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int kk = kb * kPKB + c * 8;
-          v[c] = (row_ok && kk < d) ? __ldg(reinterpret_cast<const uint4*>(qrow + kk)) : make_uint4(0, 0, 0, 0);
-        }
+        for (int i = 0; i < 8; ++i)
+          v[i] = (qok[i] && kk < d) ? __ldg(reinterpret_cast<const uint4*>(qsrc[i] + kb * kPKB))
+                                    : make_uint4(0, 0, 0, 0);
       };
       load_q(0, qa);
       if (nkb > 1) load_q(1, qb);
@@ -190,18 +199,19 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
           tc::tma_load_2d(&mapMrep, &full[s], st + kPBytesA + (my_j * 32 + my_i * 8) * 128, x, (int)mine.x * 8);
         if (tid < kPSlots && sslot[tid].z)
           tc::tma_load_2d(&mapU, &full[s], st + 2 * kPBytesA + tid * RN * 128, x, (int)sslot[tid].x * r);
-        if (row_ok) {
-          const uint32_t dst = tc::smem_u32(st) + (uint32_t)tid * 128u;
+        const uint32_t sbase = tc::smem_u32(st);
 #pragma unroll
-          for (int c = 0; c < 8; ++c)
-            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(dst + (((uint32_t)c ^ swz) << 4)),
-                         "r"(qa[c].x), "r"(qa[c].y), "r"(qa[c].z), "r"(qa[c].w)
+        for (int i = 0; i < 8; ++i) {
+          const int row = rbase + 16 * i;
+          if (qok[i])
+            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + sw128_off(row, ch * 16)),
+                         "r"(qa[i].x), "r"(qa[i].y), "r"(qa[i].z), "r"(qa[i].w)
                          : "memory");
         }
         tc::fence_proxy_async_smem();
         tc::mbar_arrive(&full[s]);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) qa[c] = qb[c];
+        for (int i = 0; i < 8; ++i) qa[i] = qb[i];
         if (kb + 2 < nkb) load_q(kb + 2, qb);
       }
     }

@@ -7,17 +7,21 @@
 // tile.
 //
 // k_route_refine: the approximate distance is within
-//   m(q, g) = 2^-7 ||q|| ||mu_g|| + 2^-16 (||q||^2 + ||mu_g||^2)
-// of the exact one: each operand rounded to TF32 costs at most 2^-10
-// relative, so a product at most 2^-9 of |q_t mu_t|, summed at most
-// 2^-9 ||q|| ||mu|| by Cauchy-Schwarz and doubled in the distance; the
-// margin doubles that again to cover FP32 accumulation (d 2^-24 relative)
-// and the rounding of the norms. BF16 operands multiply exactly. With U the
-// nprobe-th smallest approx + margin, any centre whose approx - margin exceeds
-// U cannot be among the nprobe nearest, so only the others (typically nprobe
-// plus a few) get their exact direct-form distance sum (q_t - mu_t)^2, and the
-// nprobe smallest (distance, grain) are kept: the same selection as the
-// direct-form routing, at a fraction of its arithmetic.
+//   m(q, g) = eps_dot ||q|| ||mu_g|| + eps_norm (||q||^2 + ||mu_g||^2)
+// of the exact one (route_margin() sets both, with a factor 2 of safety):
+//   eps_dot, the dot product: TF32 operands are each rounded by at most
+//     2^-10 relative, so a product by 2^-9 of |q_t mu_t|, summed at most
+//     2^-9 ||q|| ||mu|| (Cauchy-Schwarz), doubled in the distance; BF16
+//     operands multiply exactly, so only the FP32 accumulation remains: at
+//     most K/16 + 16 roundings of 2^-23 (groups of 16 products added to the
+//     accumulator, and within a group), of sum |q_t mu_t| <= ||q|| ||mu||;
+//   eps_norm, the squared norms (one warp each: d/32 sequential additions per
+//     lane, five butterfly levels) and the final sum (||q||^2 + ||mu||^2 - 2S).
+// With U the nprobe-th smallest approx + margin, any centre whose approx -
+// margin exceeds U cannot be among the nprobe nearest, so only the others
+// (typically nprobe plus a few) get their exact direct-form distance sum
+// (q_t - mu_t)^2, and the nprobe smallest (distance, grain) are kept: the same
+// selection as the direct-form routing, at a fraction of its arithmetic.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -151,6 +155,16 @@ constexpr int kRefineCap = 1024;
 
 constexpr int kRefineSmemMax = (8192 + 2 * kMaxG) * 4;  // d <= 8192 on this path
 
+// Margin coefficients of the refine shortlist (see the file header), with a
+// factor 2 of safety: {eps_dot, eps_norm}.
+inline void route_margin(bool bf16, int d, float* eps_dot, float* eps_norm) {
+  const double u23 = 1.0 / 8388608.0;  // 2^-23
+  const double dot = bf16 ? 2.0 * ((d + 15) / 16 + 16) * u23 : 2.0 * (2.0 / 512.0 + ((d + 15) / 16 + 16) * u23);
+  const double norm = 2.0 * (((d + 31) / 32 + 6) * 0.5 * u23 + u23);
+  *eps_dot = (float)dot;
+  *eps_norm = (float)norm;
+}
+
 // ||q - mu_g||^2 in the direct form, one warp (the result in every lane). Each
 // lane sums its elements in a fixed order (with rows of at most 1024 values
 // and 16-byte strides: chunks of 8 (BF16) or 4 (FP32) consecutive values, all
@@ -224,7 +238,8 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
                                                                  const float* __restrict__ qn,
                                                                  const float* __restrict__ mn,
                                                                  const float* __restrict__ Dt, int G, int d,
-                                                                 int nprobe, int32_t* __restrict__ probe,
+                                                                 int nprobe, float eps_dot, float eps_norm,
+                                                                 int32_t* __restrict__ probe,
                                                                  float* __restrict__ probe_d) {
   // dynamic: [d] query (BF16-rounded in the precision form), then the ordered
   // keys of approx + margin and approx - margin of every centre ([G] each), so
@@ -245,17 +260,70 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
   const float* Dq = Dt + (size_t)q * G;
   uint32_t* khi = reinterpret_cast<uint32_t*>(sq + d);
   uint32_t* klo = khi + G;
+  uint32_t my_min = 0xFFFFFFFFu;  // this thread's smallest approx + margin
   for (int g = threadIdx.x; g < G; g += blockDim.x) {
     const float mg = mn[g], D = Dq[g];
-    const float m = 0.0078125f * sqrtf(qv * mg) + 1.52587890625e-5f * (qv + mg);
-    khi[g] = ordered_key(D + m);
+    const float m = eps_dot * sqrtf(qv * mg) + eps_norm * (qv + mg);
+    const uint32_t hi = ordered_key(D + m);
+    khi[g] = hi;
     klo[g] = ordered_key(D - m);
+    my_min = min(my_min, hi);
   }
-  __syncthreads();
-  // U = nprobe-th smallest of approx + margin (four 8-bit radix digits on ordered keys)
-  uint32_t prefix = 0, need = (uint32_t)nprobe;
+  // U: any upper bound on the nprobe-th smallest approx + margin keeps the shortlist
+  // exact. The nprobe-th smallest of the threads' minima is one (a subset's order
+  // statistic is at least the full set's) and is rarely above the true one. Each
+  // warp sorts its lanes' minima; one warp merges the sorted runs up to the
+  // nprobe-th value.
+  uint32_t prefix = 0;
+  bool have_u = false;
+  if (nprobe <= (int)blockDim.x) {
+    uint32_t v = my_min;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+        const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+        v = (lower == up) ? min(v, o) : max(v, o);
+      }
+    }
+    uint32_t* lists = reinterpret_cast<uint32_t*>(keys);  // nw sorted runs of 32
+    lists[warp * 32 + lane] = v;
+    __syncthreads();
+    if (warp == 0) {  // merge the runs: the nprobe-th value taken is U
+      uint32_t h = 0;
+      uint32_t head = lane < nw ? lists[lane * 32] : 0xFFFFFFFFu, val = 0xFFFFFFFFu;
+      for (int step = 0; step < nprobe; ++step) {
+        uint32_t m = head;
+        int src = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const uint32_t om = __shfl_xor_sync(0xffffffffu, m, o);
+          const int os = __shfl_xor_sync(0xffffffffu, src, o);
+          if (om < m || (om == m && os < src)) {
+            m = om;
+            src = os;
+          }
+        }
+        val = m;
+        if (lane == src) {
+          ++h;
+          head = h < 32 ? lists[lane * 32 + h] : 0xFFFFFFFFu;
+        }
+      }
+      if (lane == 0) s_bin = val;
+    }
+    __syncthreads();
+    prefix = s_bin;
+    have_u = true;
+    __syncthreads();  // the key runs are reused below
+  } else {
+    __syncthreads();
+  }
+  // else: U = nprobe-th smallest of approx + margin exactly (four 8-bit radix digits on ordered keys)
+  uint32_t need = (uint32_t)nprobe;
   int known = 0;
-  for (int pass = 0; pass < 4; ++pass) {
+  for (int pass = 0; pass < 4 && !have_u; ++pass) {
     const int sh = 24 - 8 * pass;
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();

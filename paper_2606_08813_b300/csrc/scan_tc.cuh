@@ -116,17 +116,25 @@ __global__ void __launch_bounds__(128) k_grain_needed(const uint32_t* __restrict
   if (threadIdx.x == 0) need_cnt[g] = s_n;
 }
 
+// A sparse work item as the classifier leaves it: the item and the pairs
+// (indices into the batch's pair arrays) live in it.
+struct SparseRec {
+  uint4 item;                    // grain, first block, blocks, live pairs
+  uint32_t pr[kSTDense - 1];     // live pairs
+  uint32_t pad;
+};
+
 // Sorts the scan's work items by how many of their grain's live pairs can
 // still reach their pool from the item's blocks (rho_q + min rho_block <=
-// tau_q): none (dropped), a few (the direct-form kernel), at least kSTDense
-// (the tensor-core kernel). One warp per item. lists: [0] dense count, [1]
-// sparse count.
+// tau_q): none (dropped), a few (recorded with those pairs for the
+// direct-form kernel), at least kSTDense (the tensor-core kernel). One warp
+// per item. lists: [0] dense count, [1] sparse count.
 __global__ void k_scan_classify(const uint4* __restrict__ items, const uint32_t* __restrict__ n_items,
                                 const uint32_t* __restrict__ need_cnt, const uint32_t* __restrict__ need_list,
                                 const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ pair_q,
                                 const float* __restrict__ rhoq, const float* __restrict__ tau,
                                 const float* __restrict__ blk_rho_min, uint4* __restrict__ dense,
-                                uint4* __restrict__ sparse, uint32_t* __restrict__ lists) {
+                                SparseRec* __restrict__ sparse, uint32_t* __restrict__ lists) {
   const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= *n_items) return;
@@ -135,20 +143,35 @@ __global__ void k_scan_classify(const uint4* __restrict__ items, const uint32_t*
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
   const uint32_t m = need_cnt[item.x], p0 = pair_off[item.x];
-  uint32_t n = 0;
+  uint32_t n = 0, mine = 0xFFFFFFFFu;  // lane i < n keeps the i-th live pair
   for (uint32_t s0 = 0; s0 < m && n < (uint32_t)kSTDense; s0 += 32) {
     const uint32_t s = s0 + lane;
     bool need = false;
+    uint32_t pr = 0;
     if (s < m) {
-      const uint32_t pr = p0 + need_list[p0 + s];
+      pr = p0 + need_list[p0 + s];
       need = rhoq[pr] + v <= tau[pair_q[pr]];
     }
-    n += __popc(__ballot_sync(0xffffffffu, need));
+    const unsigned mask = __ballot_sync(0xffffffffu, need);
+    const uint32_t slot = n + __popc(mask & ((1u << lane) - 1u));
+    // hand the pair to lane `slot` (one pass: each live pair has a distinct slot)
+    for (int src = 0; src < 32; ++src) {
+      const uint32_t p_src = __shfl_sync(0xffffffffu, pr, src);
+      const uint32_t slot_src = __shfl_sync(0xffffffffu, slot, src);
+      if (((mask >> src) & 1u) && slot_src == (uint32_t)lane) mine = p_src;
+    }
+    n += __popc(mask);
   }
-  if (lane == 0 && n) {
-    if (n >= (uint32_t)kSTDense) dense[atomicAdd(&lists[0], 1u)] = item;
-    else sparse[atomicAdd(&lists[1], 1u)] = item;
+  if (!n) return;
+  if (n >= (uint32_t)kSTDense) {
+    if (lane == 0) dense[atomicAdd(&lists[0], 1u)] = item;
+    return;
   }
+  uint32_t pos = 0;
+  if (lane == 0) pos = atomicAdd(&lists[1], 1u);
+  pos = __shfl_sync(0xffffffffu, pos, 0);
+  if (lane == 0) sparse[pos].item = make_uint4(item.x, item.y, item.z, n);
+  if ((uint32_t)lane < n) sparse[pos].pr[lane] = mine;
 }
 
 constexpr int kSPThreads = 128;
@@ -159,38 +182,36 @@ constexpr int kSPThreads = 128;
 // same decoded coordinates, as the pilot and the pool fallback).
 template <int RT>
 __global__ void __launch_bounds__(kSPThreads, 6) k_scan_sparse(
-    const uint4* __restrict__ items, const uint32_t* __restrict__ lists, uint32_t* __restrict__ next_item,
-    const uint32_t* __restrict__ blk_off, const uint32_t* __restrict__ grain_rows, const uint8_t* __restrict__ Z8b,
-    const float* __restrict__ scale, const float* __restrict__ rho, const uint32_t* __restrict__ ids,
-    const int64_t* __restrict__ attr_b, int r, int rp, const uint32_t* __restrict__ need_cnt,
-    const uint32_t* __restrict__ need_list,
-    const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ pair_q, const float* __restrict__ zq,
-    const float* __restrict__ rhoq, const float* __restrict__ tau, const float* __restrict__ blk_rho_min,
-    const int64_t* __restrict__ filter, uint32_t cap, uint32_t* __restrict__ cnt,
-    unsigned long long* __restrict__ surv) {
+    const SparseRec* __restrict__ recs, const uint32_t* __restrict__ lists, uint32_t* __restrict__ next_item,
+    const uint32_t* __restrict__ blk_off,
+    const uint32_t* __restrict__ grain_rows, const uint8_t* __restrict__ Z8b, const float* __restrict__ scale,
+    const float* __restrict__ rho, const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r,
+    int rp, const uint32_t* __restrict__ pair_q, const float* __restrict__ zq, const float* __restrict__ rhoq,
+    const float* __restrict__ tau, const float* __restrict__ blk_rho_min, const int64_t* __restrict__ filter,
+    uint32_t cap, uint32_t* __restrict__ cnt, unsigned long long* __restrict__ surv) {
   constexpr int kL = RT / 16;
   constexpr int kP = kSTDense - 1;  // at most this many live pairs per item
   __shared__ __align__(16) float sz[kP][RT];
   __shared__ float4 spc[kP];  // {unused, unused, tau_q, rho_q}
-  __shared__ uint32_t sqid[kP], s_need[kP];
+  __shared__ uint32_t sqid[kP], spr[kP];
   __shared__ long long slo[kP], shi[kP];
-  __shared__ uint32_t s_nneed, s_item;
-  __shared__ float s_rmin;
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int t = threadIdx.x, lane = t & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const uint32_t total = lists[1];
   const int nks = rp / 16;
-  for (;;) {
-    __syncthreads();  // every thread is done with the previous item
-    if (t == 0) s_item = atomicAdd(next_item, 1u);
-    __syncthreads();
-    const uint32_t w = s_item;
-    if (w >= total) break;
-    const uint4 item = items[w];
+  // items taken from a global counter (their costs vary; a static split left a
+  // tail); the next item's index is claimed while the current one is scanned
+  __shared__ uint32_t s_item;
+  if (t == 0) s_item = atomicAdd(next_item, 1u);
+  __syncthreads();
+  uint32_t w = s_item;
+  while (w < total) {
+    const uint4 item = recs[w].item;
+    const uint32_t my_pr = t < kP ? recs[w].pr[t] : 0u;
     const uint32_t g = item.x, b0 = item.y, nb = item.z;
-    const uint32_t m = need_cnt[g], p_begin = pair_off[g], n_g = grain_rows[g], gb0 = blk_off[g];
+    const int np = (int)item.w;
+    const uint32_t n_g = grain_rows[g], gb0 = blk_off[g];
     const float s_g = scale[g];
-    // prefetch the first two blocks while the pairs are gathered
     uint4 cur[kL], nxt[kL];
     float rho_cur = 0.f, rho_nxt = 0.f, rmin_cur = 0.f, rmin_nxt = 0.f;
     auto load_block = [&](uint32_t i, uint4 (&codes)[kL], float& rh, float& rmin) {
@@ -204,43 +225,25 @@ __global__ void __launch_bounds__(kSPThreads, 6) k_scan_sparse(
     };
     load_block(0, cur, rho_cur, rmin_cur);
     if (nb > 1) load_block(1, nxt, rho_nxt, rmin_nxt);
-    if (warp == 0) {
-      float v = (uint32_t)lane < nb ? blk_rho_min[b0 + lane] : INFINITY;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if (lane == 0) {
-        s_rmin = v;
-        s_nneed = 0;
-      }
-    }
+    __syncthreads();  // every thread is done with the previous item's pair data
+    if (t < np) spr[t] = my_pr;  // threads 0..kP-1 hold the item's pairs
     __syncthreads();
-    const float rmin_item = s_rmin;
-    for (uint32_t i = t; i < m; i += kSPThreads) {
-      const uint32_t sidx = need_list[p_begin + i];
-      const uint32_t pr = p_begin + sidx;
-      if (rhoq[pr] + rmin_item <= tau[pair_q[pr]]) {
-        const uint32_t pos = atomicAdd(&s_nneed, 1u);
-        if (pos < (uint32_t)kP) s_need[pos] = sidx;
-      }
-    }
-    __syncthreads();
-    const int np = (int)min(s_nneed, (uint32_t)kP);  // the classifier found fewer than kSTDense
     for (int e = t; e < np * RT; e += kSPThreads) {
       const int j = e / RT, a = e % RT;
-      const uint32_t pr = p_begin + s_need[j];
-      sz[j][a] = a < r ? zq[(size_t)pr * r + a] : 0.f;
+      sz[j][a] = a < r ? zq[(size_t)spr[j] * r + a] : 0.f;
     }
     if (t < np) {
-      const uint32_t pr = p_begin + s_need[t];
-      const uint32_t q = pair_q[pr];
-      spc[t] = make_float4(0.f, 0.f, tau[q], rhoq[pr]);
+      const uint32_t q = pair_q[my_pr];
+      spc[t] = make_float4(0.f, 0.f, tau[q], rhoq[my_pr]);
       sqid[t] = q;
       if (filter) {
         slo[t] = (long long)filter[2 * (size_t)q];
         shi[t] = (long long)filter[2 * (size_t)q + 1];
       }
     }
+    if (t == 0) s_item = atomicAdd(next_item, 1u);  // read after the barrier below
     __syncthreads();
+    w = s_item;
     for (uint32_t i = 0; i < nb; ++i) {
       const size_t b = b0 + i;
       const bool valid = (uint32_t)(b - gb0) * kBlockRows + t < n_g;

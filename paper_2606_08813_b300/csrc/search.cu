@@ -98,35 +98,78 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(const uint32_t* __restrict
                                                       const uint32_t* __restrict__ blk_off,
                                                       uint32_t* __restrict__ scan_off,
                                                       uint4* __restrict__ scan_items) {
-  __shared__ uint32_t ws32[32];
-  __shared__ uint32_t tot32a, tot32b, tot32c, tot32d;
-  uint32_t carry_p = 0, carry_gr = 0, carry_g2 = 0, carry_sc = 0;
-  for (int c0 = 0; c0 < G; c0 += 1024) {
-    int g = c0 + threadIdx.x;
-    uint32_t cnt = g < G ? gcnt[g] : 0u;
-    uint32_t ngr = (cnt + kPairsPerGroup - 1) / kPairsPerGroup;
-    uint32_t ep = block_exclusive_scan<uint32_t>(cnt, &tot32a, ws32);
-    uint32_t eg = block_exclusive_scan<uint32_t>(ngr, &tot32b, ws32);
-    uint32_t e2 = block_exclusive_scan<uint32_t>((cnt + kPSlot - 1) / kPSlot, &tot32c, ws32);
+  // thread t owns grains [t per, (t + 1) per): one pass of local sums, one
+  // block-wide scan of the four counts at once, then the offsets
+  __shared__ uint4 wsum[32];
+  __shared__ uint4 s_tot;
+  const int per = (G + 1023) / 1024;  // G <= 8192: at most 8 grains per thread
+  const int g0 = threadIdx.x * per;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto counts = [&](int g) {
+    const uint32_t cnt = g < G ? gcnt[g] : 0u;
     const uint32_t nbk = (scan_items && g < G && cnt) ? blk_off[g + 1] - blk_off[g] : 0u;
-    uint32_t e3 = block_exclusive_scan<uint32_t>((nbk + kSTBlocks - 1) / kSTBlocks, &tot32d, ws32);
-    if (g < G) {
-      pair_off[g] = carry_p + ep;
-      grp_off[g] = carry_gr + eg;
-      slot_off[g] = carry_g2 + e2;
-      if (scan_items) scan_off[g] = carry_sc + e3;
+    return make_uint4(cnt, (cnt + kPairsPerGroup - 1) / kPairsPerGroup, (cnt + kPSlot - 1) / kPSlot,
+                      (nbk + kSTBlocks - 1) / kSTBlocks);
+  };
+  uint4 loc = make_uint4(0, 0, 0, 0);
+  for (int i = 0; i < per; ++i) {
+    const uint4 c = counts(g0 + i);
+    loc.x += c.x;
+    loc.y += c.y;
+    loc.z += c.z;
+    loc.w += c.w;
+  }
+  uint4 x = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t a = __shfl_up_sync(0xffffffffu, x.x, o), b = __shfl_up_sync(0xffffffffu, x.y, o);
+    const uint32_t c = __shfl_up_sync(0xffffffffu, x.z, o), e = __shfl_up_sync(0xffffffffu, x.w, o);
+    if (lane >= o) {
+      x.x += a;
+      x.y += b;
+      x.z += c;
+      x.w += e;
     }
-    carry_p += tot32a;
-    carry_gr += tot32b;
-    carry_g2 += tot32c;
-    carry_sc += tot32d;
-    __syncthreads();
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint4 v = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t a = __shfl_up_sync(0xffffffffu, v.x, o), b = __shfl_up_sync(0xffffffffu, v.y, o);
+      const uint32_t c = __shfl_up_sync(0xffffffffu, v.z, o), e = __shfl_up_sync(0xffffffffu, v.w, o);
+      if (lane >= o) {
+        v.x += a;
+        v.y += b;
+        v.z += c;
+        v.w += e;
+      }
+    }
+    wsum[lane] = v;
+    if (lane == 31) s_tot = v;
+  }
+  __syncthreads();
+  const uint4 base = warp > 0 ? wsum[warp - 1] : make_uint4(0, 0, 0, 0);
+  uint4 run = make_uint4(base.x + x.x - loc.x, base.y + x.y - loc.y, base.z + x.z - loc.z, base.w + x.w - loc.w);
+  for (int i = 0; i < per; ++i) {
+    const int g = g0 + i;
+    if (g >= G) break;
+    pair_off[g] = run.x;
+    grp_off[g] = run.y;
+    slot_off[g] = run.z;
+    if (scan_items) scan_off[g] = run.w;
+    const uint4 c = counts(g);
+    run.x += c.x;
+    run.y += c.y;
+    run.z += c.z;
+    run.w += c.w;
   }
   if (threadIdx.x == 0) {
-    pair_off[G] = carry_p;
-    grp_off[G] = carry_gr;
-    slot_off[G] = carry_g2;
-    if (scan_items) scan_off[G] = carry_sc;
+    pair_off[G] = s_tot.x;
+    grp_off[G] = s_tot.y;
+    slot_off[G] = s_tot.z;
+    if (scan_items) scan_off[G] = s_tot.w;
   }
   __syncthreads();
   if (slots) {
@@ -286,7 +329,7 @@ struct Ws {
   uint4* dense_items;  // the items with many live pairs (tensor-core scan)
   uint32_t* need_list; // per grain, its pairs that can reach their pool (indices, at the grain's pair offset)
   uint32_t* need_cnt;  // per grain, how many
-  uint4* sparse_items; // the items with a few (direct-form scan)
+  SparseRec* sparse_items;  // the items with a few, with those pairs (direct-form scan)
   float* zq;
   float* rhoq;
   float* tau;
@@ -323,7 +366,7 @@ Ws carve(const Index& I, uint32_t nq, uint32_t C, uint32_t nprobe, void* base) {
   w.dense_items = tcp ? c.take<uint4>(I.G + I.n_blocks / kSTBlocks + 1) : nullptr;
   w.need_list = tcp ? c.take<uint32_t>(P) : nullptr;
   w.need_cnt = tcp ? c.take<uint32_t>(I.G) : nullptr;
-  w.sparse_items = tcp ? c.take<uint4>(I.G + I.n_blocks / kSTBlocks + 1) : nullptr;
+  w.sparse_items = tcp ? c.take<SparseRec>(I.G + I.n_blocks / kSTBlocks + 1) : nullptr;
   w.zq = c.take<float>(P * I.r);
   w.rhoq = c.take<float>(P);
   w.tau = c.take<float>(nq);
@@ -373,16 +416,20 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
     }
     dim3 grid((I.G + kRTN - 1) / kRTN, (nq + kRTM - 1) / kRTM);
     const size_t rsmem = ((size_t)I.d + 2 * (size_t)I.G) * sizeof(float);
+    float eps_dot = 0.f, eps_norm = 0.f;
+    route_margin(bf16, (int)I.d, &eps_dot, &eps_norm);
     if (bf16) {
       k_route_tc<true><<<grid, 128, kRouteTcSmem, st>>>(mapQ, I.mapM, (int)nq, (int)I.G, (int)I.d, w.qn, I.mnorm,
                                                         w.route_d, I.d_err);
       k_route_refine<true><<<nq, kRefineThreads, rsmem, st>>>(Qd, I.M, I.Mh, w.qn, I.mnorm, w.route_d, (int)I.G,
-                                                              (int)I.d, (int)nprobe, w.probe, w.probe_d);
+                                                              (int)I.d, (int)nprobe, eps_dot, eps_norm, w.probe,
+                                                              w.probe_d);
     } else {
       k_route_tc<false><<<grid, 128, kRouteTcSmem, st>>>(mapQ, I.mapM, (int)nq, (int)I.G, (int)I.d, w.qn, I.mnorm,
                                                          w.route_d, I.d_err);
       k_route_refine<false><<<nq, kRefineThreads, rsmem, st>>>(Qd, I.M, I.Mh, w.qn, I.mnorm, w.route_d, (int)I.G,
-                                                               (int)I.d, (int)nprobe, w.probe, w.probe_d);
+                                                               (int)I.d, (int)nprobe, eps_dot, eps_norm, w.probe,
+                                                               w.probe_d);
     }
     HNTL_CUDA_TRY(cudaGetLastError());
     return HNTL_OK;
@@ -448,10 +495,10 @@ void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, 
     k_scan_classify<<<(unsigned)((max_items * 32 + 255) / 256), 256, 0, st>>>(
         w.scan_items, w.scan_off + I.G, w.need_cnt, w.need_list, w.pair_off, w.pair_q, w.rhoq, w.tau, I.blk_rho_min,
         w.dense_items, w.sparse_items, lists);
-    k_scan_sparse<RT><<<(unsigned)std::min<size_t>(max_items, (size_t)I.num_sms * 16), kSPThreads, 0, st>>>(
+    k_scan_sparse<RT><<<(unsigned)std::min<size_t>(max_items, (size_t)I.num_sms * 6), kSPThreads, 0, st>>>(
         w.sparse_items, lists, lists + 2, I.blk_off, I.grain_rows, I.Z8b, I.scale, I.rho, I.ids, I.attr_b, (int)I.r,
-        (int)I.rp, w.need_cnt, w.need_list, w.pair_off, w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap,
-        w.cnt, w.surv);
+        (int)I.rp,
+        w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap, w.cnt, w.surv);
     k_scan_tc<RT><<<(unsigned)std::min<size_t>(max_items, (size_t)I.num_sms * 2), kSTThreads, ScanTc<RT>::kSmem,
                     st>>>(
         w.dense_items, lists, w.cnt + nq, I.blk_off, I.grain_rows, I.Z8b, I.scale, I.crow, I.rho, I.ids, I.attr_b,
