@@ -25,6 +25,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -389,6 +390,42 @@ def run_serving(a, hntl, gi, X, Q, attr, w, sd):
             "seconds_per_rate": a.serve_seconds}
 
 
+class MultiStream:
+    """Batches of one search call alternate over S streams, each with its own
+    workspace and outputs, so one batch's small kernels and tails overlap the
+    next batch's work (the server's two lanes do the same)."""
+
+    def __init__(self, gi, B, k, C, nprobe, S, dev):
+        self.gi, self.k, self.C, self.nprobe = gi, k, C, nprobe
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(S)]
+        nb = gi.workspace_bytes(B, k, C, nprobe)
+        self.ws = [torch.empty(nb, dtype=torch.uint8, device=dev) for _ in range(S)]
+        self.outs = [(torch.empty(B, k, dtype=torch.int64, device=dev), torch.empty(B, k, dtype=torch.float32,
+                                                                                   device=dev)) for _ in range(S)]
+
+    def run(self, batches, steps, events=None):
+        """Launch `steps` searches; with events, record (start, end) per batch and
+        bracket the whole on the current stream: returns the bracket's ms."""
+        st = torch.cuda.current_stream()
+        S = len(self.streams)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for s_ in self.streams:
+            s_.wait_stream(st)
+        for i in range(steps):
+            j = i % S
+            if events is not None:
+                events[i][0].record(self.streams[j])
+            self.gi.search(batches[i % len(batches)], self.k, self.C, self.nprobe, out=self.outs[j],
+                           ws=self.ws[j], stream=self.streams[j])
+            if events is not None:
+                events[i][1].record(self.streams[j])
+        for s_ in self.streams:
+            st.wait_stream(s_)
+        e1.record(st)
+        return e0, e1
+
+
 def run_fp32_compare(a, hntl, X, Q, w, sd, B, n_recall, truth, line):
     """The plain FP32 method (FP32 rows, coordinates, bases; TF32 routing with
     an exact refine; direct-form FP32 scan) on the same data, k-means draws,
@@ -403,23 +440,20 @@ def run_fp32_compare(a, hntl, X, Q, w, sd, B, n_recall, truth, line):
     batches = [Q[i * B:(i + 1) * B].contiguous() for i in range(nb)]
     found = [gf.search(batches[i], k, C, nprobe)[0] for i in range(max(1, (n_recall + B - 1) // B))]
     rec = recall_at_k(torch.cat(found)[:n_recall], truth) if n_recall else None
-    out = (torch.empty(B, k, dtype=torch.int64, device=Q.device), torch.empty(B, k, dtype=torch.float32,
-                                                                            device=Q.device))
-    for i in range(a.warmup):
-        gf.search(batches[i % nb], k, C, nprobe, out=out)
+    ms_ = MultiStream(gf, B, k, C, nprobe, a.streams, Q.device)
+    ms_.run(batches, a.warmup)
     torch.cuda.synchronize()
-    hntl.profile_read()
-    hntl.profile_enable(True)
-    st = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = max(10, a.steps // 2)
-    e0.record(st)
+    hntl.profile_read()
+    hntl.profile_enable(True)  # stage times: one stream
+    out = ms_.outs[0]
     for i in range(steps):
-        gf.search(batches[i % nb], k, C, nprobe, out=out)
-    e1.record(st)
+        gf.search(batches[i % nb], k, C, nprobe, out=out, ws=ms_.ws[0])
     torch.cuda.synchronize()
     hntl.profile_enable(False)
     sm, calls = hntl.profile_read()
+    e0, e1 = ms_.run(batches, steps)
+    torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     qps = B / (ms / 1e3)
     del gf
@@ -428,7 +462,8 @@ def run_fp32_compare(a, hntl, X, Q, w, sd, B, n_recall, truth, line):
             "recall_at_10": None if rec is None else round(rec, 4), "index_build_s": round(build_s, 2),
             "stages_ms": {k_: round(v_ / max(calls, 1), 4) for k_, v_ in sm.items()},
             "precision_form_gain": round(line["value"] / qps, 3),
-            "note": "same rows, k-means draws, batch, nprobe, C and k; FP32 rows, coordinates and bases"}
+            "streams": a.streams,
+            "note": "same rows, k-means draws, batch, nprobe, C, k and streams; FP32 rows, coordinates and bases"}
 
 
 def run_ours(a, world, rank, local):
@@ -485,39 +520,57 @@ def run_ours(a, world, rank, local):
     sbytes = [stage_bytes(gi, rows_g, p, w, B) for p in probes]
 
     st = torch.cuda.current_stream()
-    for i in range(a.warmup):
-        gi.search(batches[i % nb], k, C, nprobe, out=out)
+    ms_ = MultiStream(gi, B, k, C, nprobe, a.streams, dev)
+    ms_.run(batches, a.warmup)
     torch.cuda.synchronize()
+    # stage times for the roofline: the same K batches on one stream, CUDA
+    # events between stages on that stream (under two streams a kernel's
+    # bracket would also hold the other stream's kernels)
     hntl.profile_read()  # discard warm-up records
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
     hntl.profile_enable(True)
+    for i in range(a.steps):
+        gi.search(batches[i % nb], k, C, nprobe, out=out, ws=ms_.ws[0])
+    torch.cuda.synchronize()
+    hntl.profile_enable(False)
+    stage_ms, calls = hntl.profile_read()
+    # the timed region: K batches over the streams
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
     with ClockSampler(local) as clk:
         barrier(world)
         torch.cuda.synchronize()
-        ev[0].record(st)
-        for i in range(a.steps):
-            gi.search(batches[i % nb], k, C, nprobe, out=out)
-            ev[i + 1].record(st)
+        e0, e1 = ms_.run(batches, a.steps, ev)
         torch.cuda.synchronize()
         barrier(world)
-    hntl.profile_enable(False)
-    stage_ms, calls = hntl.profile_read()
-    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(a.steps)]
-    total_ms = ev[0].elapsed_time(ev[a.steps])
+    step_ms = [x.elapsed_time(y) for x, y in ev]
+    total_ms = e0.elapsed_time(e1)
     total_ms_max = max_over_ranks(total_ms, world)
     qps = world * a.steps * B / (total_ms_max / 1e3)
     clocks = clk.summary()
 
-    # e2e: host queries (pinned) -> device -> search -> host results, per step
+    # e2e: host queries (pinned) -> device -> search -> host results, per step;
+    # one host thread per stream, each with its own workspace
     e2e_steps = 0 if a.profile_mode else a.steps
     hq = [b.cpu().pin_memory() for b in batches]
-    for i in range(min(3, a.warmup)):
-        gi.search_host(hq[i % nb], k, C, nprobe)
+    hnb = int(hntl.lib.hntl_search_host_workspace_bytes(gi.handle, B, k, C, nprobe, 0))
+    hws = [torch.empty(hnb, dtype=torch.uint8, device=dev) for _ in range(a.streams)]
+
+    def e2e_worker(j, n):
+        torch.cuda.set_device(local)
+        for i in range(j, n, a.streams):
+            gi.search_host(hq[i % nb], k, C, nprobe, stream=ms_.streams[j], ws=hws[j])
+
+    def e2e_run(n):
+        th = [threading.Thread(target=e2e_worker, args=(j, n)) for j in range(a.streams)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+
+    e2e_run(min(3, a.warmup) * a.streams)
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
-    for i in range(e2e_steps):
-        gi.search_host(hq[i % nb], k, C, nprobe)
+    e2e_run(e2e_steps)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e_qps = world * e2e_steps * B / e2e_s if e2e_steps else None
@@ -550,7 +603,9 @@ def run_ours(a, world, rank, local):
                    "recall_note": "skipped in profile mode" if a.profile_mode else "brute force, FP64 re-rank",
                    "sizes": w["sizes"], "l2": "no flush; per-step working set (probed coordinates, bases and "
                    "gathered rows, ~0.5 GB) exceeds the 126 MB L2", "index_build_s": round(build_s, 2),
-                   "parallelism": f"replicas x{world}", "pool_survivors": surv_stats, "batch_latency_ms_p50": round(float(np.percentile(step_ms, 50)), 4),
+                   "parallelism": f"replicas x{world}", "streams": a.streams,
+                   "stage_timing": "CUDA events between stages, the same K batches on one stream",
+                   "pool_survivors": surv_stats, "batch_latency_ms_p50": round(float(np.percentile(step_ms, 50)), 4),
                    "batch_latency_ms_p99": round(float(np.percentile(step_ms, 99)), 4)},
         "roofline": roof, "stages": others,
         "e2e": {"value": round(e2e_qps, 1) if e2e_qps else None, "unit": "queries/s",
@@ -745,6 +800,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="precision-10m", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--streams", type=int, default=3, help="CUDA streams the timed batches alternate over")
     ap.add_argument("--recall-queries", type=int, default=2048)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-queries", type=int, default=64)

@@ -65,14 +65,13 @@ struct Index {
   // derived at load/build (finalize_index)
   float* mnorm = nullptr;        // [G] ||mu_g||^2 (of the BF16 centres in the precision form)
   uint16_t* Mh = nullptr;        // [G][d] BF16 centres (precision form)
-  uint16_t* Mrep = nullptr;      // [G][8][d] the same centres negated, each row 8 times (precision form)
   int num_sms = 148;             // streaming multiprocessors of the index's device
   uint16_t* Uh = nullptr;        // [G][r][d] BF16 bases (precision form)
   float* gram = nullptr;         // [G][r][r] U_g U_g^T of the BF16 bases (precision form)
   int* d_err = nullptr;          // device error word (bounded waits that gave up)
   bool tc_route = false;         // tensor-core routing available (TMA map built)
   CUtensorMap mapM;              // TMA map of the centres (FP32 or BF16), 256-row boxes
-  CUtensorMap mapMrep, mapU;  // precision form: replicated -mu_b (8-row box), bases (r-row box)
+  CUtensorMap mapU;              // precision form: bases (r-row box)
   bool tc_proj = false;
 
   // host copies used for workspace sizing

@@ -58,12 +58,12 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int byte) {
 // (pairs against the other slots' bases) are computed and ignored.
 // CTA b takes items b, b + grid, ...
 //   warps 0-3  producers: per K block of 64 coordinates, the pairs' query
-//              rows (coalesced 16-byte loads prefetched two K blocks ahead,
-//              swizzled stores, proxy fence, arrival on the stage's `full`
-//              barrier); TMA brings the negated centre of each slot's
-//              grain (8 identical rows per load, from a replicated copy) and
-//              the 4 bases (one load each) into the same stage, counted on
-//              `full` by transaction bytes.
+//              rows and, on the same rows, the negated centre of each slot's
+//              grain (coalesced 16-byte loads prefetched one K block ahead,
+//              sign flip, swizzled stores, proxy fence, arrival on the
+//              stage's `full` barrier); TMA brings the 4 bases (one load
+//              each) into the same stage, counted on `full` by transaction
+//              bytes.
 //   warp 4     one thread issues the MMAs (+U q_b then -U mu_b per 16
 //              coordinates) into one of two TMEM accumulators, frees each
 //              stage through `empty` and hands the item on through `accf`.
@@ -73,7 +73,7 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int byte) {
 // RN = basis rows padded to a multiple of 16, r <= RN; d % 8 == 0 (16-byte TMA row strides).
 template <int RN>
 __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
-    const uint16_t* __restrict__ Qh, const __grid_constant__ CUtensorMap mapMrep,
+    const uint16_t* __restrict__ Qh, const uint16_t* __restrict__ Mh,
     const __grid_constant__ CUtensorMap mapU, const float* __restrict__ gram, int d, int r,
     const uint4* __restrict__ slots,
     const uint32_t* __restrict__ n_slots, const uint32_t* __restrict__ pair_q, const float* __restrict__ pair_vn,
@@ -130,10 +130,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
 
   if (warp < 4) {
     // ------------------------------------------------------------ producers
-    // A row i is pair i % 32 of slot i / 32. The query rows move by 16-byte
-    // loads, 8 lanes per row, prefetched two K blocks ahead in registers, and
-    // swizzled stores; the negated centres (8 identical rows per load) and the
-    // bases move by TMA into 1024-byte aligned boxes.
+    // A row i is pair i % 32 of slot i / 32. Query rows and centre chunks move
+    // by 16-byte loads, 8 lanes per row, prefetched one K block ahead in
+    // registers, and swizzled stores; the bases move by TMA into
+    // 1024-byte aligned boxes.
     uint32_t it = 0;  // K blocks issued by this CTA so far
     bool failed = false;  // uniform over the producers (decided by barrier reductions)
     const int my_j = tid >> 5, my_i = tid & 31;
@@ -152,37 +152,35 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
       if (w + gridDim.x < total) prefetch(w + gridDim.x);
       tc::named_bar(1, 128);
       if (failed) continue;
-      const uint4 mine = sslot[my_j];
-      // query rows move 8 lanes per row (one 128-byte line per 8 lanes): thread t
-      // carries chunk t % 8 of rows t / 8 + 16 i, i < 8, so every warp load covers
-      // 4 whole lines
+      // thread t carries chunk t % 8 of rows t / 8 + 16 i, i < 8 (so every warp
+      // load covers 4 whole 128-byte lines); row t / 8 + 16 i belongs to slot i / 2,
+      // whose centre chunk the thread also loads
       const int ch = tid & 7, rbase = tid >> 3;
-      const uint16_t* qsrc[8];
-      bool qok[8];
+      uint32_t qok = 0;  // bit i: row rbase + 16 i holds a pair
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int row = rbase + 16 * i;
-        qok[i] = (uint32_t)(row & 31) < sslot[row >> 5].z;
-        qsrc[i] = Qh + (size_t)sq[row] * d + ch * 8;
+        qok |= (uint32_t)((uint32_t)(row & 31) < sslot[row >> 5].z) << i;
       }
-      // TMA bytes one stage receives: 8-row groups of the negated centre
-      // covering each slot's pairs, the bases of the slots with pairs
+      // TMA bytes one stage receives: the bases of the slots with pairs
       uint32_t bytes = 0;
 #pragma unroll
-      for (int j = 0; j < kPSlots; ++j) {
-        const uint32_t n = sslot[j].z;
-        bytes += ((n + 7) / 8) * 8u * 128u + (n ? (uint32_t)r * 128u : 0u);
-      }
-      uint4 qa[8], qb[8];
-      auto load_q = [&](int kb, uint4 (&v)[8]) {
+      for (int j = 0; j < kPSlots; ++j) bytes += sslot[j].z ? (uint32_t)r * 128u : 0u;
+      uint4 qa[8], ma[kPSlots];
+      auto load_q = [&](int kb) {
         const int kk = kb * kPKB + ch * 8;
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-          v[i] = (qok[i] && kk < d) ? __ldg(reinterpret_cast<const uint4*>(qsrc[i] + kb * kPKB))
-                                    : make_uint4(0, 0, 0, 0);
+          qa[i] = ((qok >> i) & 1u) && kk < d
+                      ? __ldg(reinterpret_cast<const uint4*>(Qh + (size_t)sq[rbase + 16 * i] * d + kk))
+                      : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int j = 0; j < kPSlots; ++j)
+          ma[j] = ((qok >> (2 * j)) & 3u) && kk < d
+                      ? __ldg(reinterpret_cast<const uint4*>(Mh + (size_t)sslot[j].x * d + kk))
+                      : make_uint4(0, 0, 0, 0);
       };
-      load_q(0, qa);
-      if (nkb > 1) load_q(1, qb);
+      load_q(0);
       for (int kb = 0; kb < nkb; ++kb, ++it) {
         const int s = (int)(it % S);
         if (it >= (uint32_t)S) {  // the MMAs that read this stage S K blocks ago must be done
@@ -195,24 +193,26 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
         uint8_t* st = smem + s * P::kStage;
         const int x = kb * kPKB;
         if (tid == 0) tc::mbar_add_tx(&full[s], bytes);  // before this thread's arrival below
-        if (my_i < 4 && (uint32_t)(my_i * 8) < mine.z)    // 8 identical rows of -mu per TMA
-          tc::tma_load_2d(&mapMrep, &full[s], st + kPBytesA + (my_j * 32 + my_i * 8) * 128, x, (int)mine.x * 8);
         if (tid < kPSlots && sslot[tid].z)
           tc::tma_load_2d(&mapU, &full[s], st + 2 * kPBytesA + tid * RN * 128, x, (int)sslot[tid].x * r);
         const uint32_t sbase = tc::smem_u32(st);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int row = rbase + 16 * i;
-          if (qok[i])
-            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + sw128_off(row, ch * 16)),
-                         "r"(qa[i].x), "r"(qa[i].y), "r"(qa[i].z), "r"(qa[i].w)
+          if ((qok >> i) & 1u) {
+            const uint32_t off = sbase + sw128_off(rbase + 16 * i, ch * 16);
+            const uint4 m = ma[i >> 1];  // -mu_b: flip the sign bit of each BF16 (exact)
+            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(off), "r"(qa[i].x), "r"(qa[i].y),
+                         "r"(qa[i].z), "r"(qa[i].w)
                          : "memory");
+            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(off + kPBytesA),
+                         "r"(m.x ^ 0x80008000u), "r"(m.y ^ 0x80008000u), "r"(m.z ^ 0x80008000u),
+                         "r"(m.w ^ 0x80008000u)
+                         : "memory");
+          }
         }
         tc::fence_proxy_async_smem();
         tc::mbar_arrive(&full[s]);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) qa[i] = qb[i];
-        if (kb + 2 < nkb) load_q(kb + 2, qb);
+        if (kb + 1 < nkb) load_q(kb + 1);
       }
     }
     if (tid == 0) {
@@ -361,16 +361,6 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
     tc::tmem_dealloc(tmem, P::kTmemCols);
   }
   if (tid == 0 && s_fail) atomicOr(err, tc::kErrTimeout);
-}
-
-// Negated BF16 centres, each row repeated 8 times ([G][8][d]; the sign flip is
-// exact): the projection loads 8 identical rows of -mu_b per TMA.
-__global__ void k_negate_rep8_bf16(const uint16_t* __restrict__ in, int G, int d, uint16_t* __restrict__ out) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t n = (size_t)G * 8 * d;
-  if (i >= n) return;
-  const size_t g = i / ((size_t)8 * d), t = i % d;
-  out[i] = in[g * d + t] ^ 0x8000u;
 }
 
 // Per grain (BF16 form): the Gram matrix U_g U_g^T (r x r, FP32 sums of exact products).

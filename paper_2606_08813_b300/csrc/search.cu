@@ -461,7 +461,7 @@ int launch_project_tc_n(const Index& I, uint32_t nq, uint32_t P, const Ws& w, cu
   // persistent: one CTA per SM at most, never more CTAs than work items can exist
   const size_t max_items = ((size_t)P / kPSlot + I.G + kPSlots - 1) / kPSlots;
   const unsigned grid = (unsigned)std::min<size_t>(max_items, (size_t)I.num_sms);
-  k_project_tc<RN><<<grid, kPThreads, ProjTc<RN>::kSmem, st>>>(w.Qh, I.mapMrep, I.mapU, I.gram, (int)I.d, (int)I.r,
+  k_project_tc<RN><<<grid, kPThreads, ProjTc<RN>::kSmem, st>>>(w.Qh, I.Mh, I.mapU, I.gram, (int)I.d, (int)I.r,
                                                                w.slots, w.grp2_off + I.G, w.pair_q, w.pair_vn,
                                                                w.zq, w.rhoq, I.d_err);
   HNTL_CUDA_TRY(cudaGetLastError());
@@ -712,11 +712,10 @@ int finalize_index(Index& I) {
     I.Mh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.d));
     I.Uh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.r * I.d));
     I.gram = static_cast<float*>(alloc(sizeof(float) * I.G * I.r * I.r));
-    I.Mrep = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * 8 * I.d));
     I.crow = static_cast<float*>(alloc(sizeof(float) * I.n_blocks * kBlockRows));
     I.grain_rho_min = static_cast<float*>(alloc(sizeof(float) * I.G));
   }
-  if (!I.d_err || !I.mnorm || (bf16 && (!I.Mh || !I.Uh || !I.gram || !I.Mrep || !I.crow || !I.grain_rho_min)))
+  if (!I.d_err || !I.mnorm || (bf16 && (!I.Mh || !I.Uh || !I.gram || !I.crow || !I.grain_rho_min)))
     return fail(HNTL_ENOMEM, "index: derived arrays");
   HNTL_CUDA_TRY(cudaMemset(I.d_err, 0, sizeof(int)));
   if (bf16) k_row_norms<true><<<(I.G * 32 + 255) / 256, 256>>>(I.M, (int)I.G, (int)I.d, I.mnorm);
@@ -726,7 +725,6 @@ int finalize_index(Index& I) {
     k_to_bf16_rows<<<(unsigned)((n + 255) / 256), 256>>>(I.M, n, I.Mh);
     k_to_bf16_rows<<<(unsigned)((nu + 255) / 256), 256>>>(I.U, nu, I.Uh);
     k_gram<<<I.G, 256>>>(I.Uh, (int)I.d, (int)I.r, I.gram);
-    k_negate_rep8_bf16<<<(unsigned)((n * 8 + 255) / 256), 256>>>(I.Mh, (int)I.G, (int)I.d, I.Mrep);
     k_grain_rho_min<<<(I.G * 32 + 255) / 256, 256>>>(I.blk_rho_min, I.blk_off, (int)I.G, I.grain_rho_min);
     const Coords cz{I.Zb, I.Z8b, I.scale};
     if (I.n_blocks) {
@@ -741,8 +739,7 @@ int finalize_index(Index& I) {
   // tensor-core routing needs 16-byte row strides and the query row in shared memory
   const bool shape_ok = (bf16 ? I.d % 8 == 0 : I.d % 4 == 0) && I.d <= 8192;
   I.tc_route = shape_ok && make_tma_map(&I.mapM, bf16 ? (const void*)I.Mh : (const void*)I.M, bf16, I.G, I.d, kRTN);
-  I.tc_proj = bf16 && shape_ok && make_tma_map(&I.mapMrep, I.Mrep, true, (uint64_t)I.G * 8, I.d, 8) &&
-              make_tma_map(&I.mapU, I.Uh, true, (uint64_t)I.G * I.r, I.d, I.r);
+  I.tc_proj = bf16 && shape_ok && make_tma_map(&I.mapU, I.Uh, true, (uint64_t)I.G * I.r, I.d, I.r);
   return HNTL_OK;
 }
 

@@ -217,14 +217,24 @@ class Index:
             self._ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
         return self._ws
 
+    def _caller_ws(self, ws, nbytes: int) -> torch.Tensor:
+        if ws is None:
+            return self.workspace(nbytes)
+        if not ws.is_cuda or ws.dtype != torch.uint8 or ws.numel() < nbytes or not ws.is_contiguous():
+            raise ValueError(f"ws must be a contiguous CUDA uint8 tensor of at least {nbytes} bytes")
+        return ws
+
     def search(self, Q: torch.Tensor, k: int, C: int, nprobe: int, filters: torch.Tensor | None = None,
-               return_pool: bool = False, return_probe: bool = False, stream=None, out=None):
+               return_pool: bool = False, return_probe: bool = False, stream=None, out=None, ws=None):
         """Batched Mode B search of CUDA queries Q [nq, d] f32.
 
         Returns (ids i64 [nq, k], dist f32 [nq, k]); with return_pool also the
         pool (ids as int32 [nq, max(C, k)] holding the uint32 ids, so the
         0xFFFFFFFF pad reads as -1, and approximate distances f32); with
-        return_probe also the probed grains int32 [nq, nprobe]."""
+        return_probe also the probed grains int32 [nq, nprobe]. `ws` is a
+        caller-owned uint8 device workspace (for concurrent searches on
+        several streams, each with its own); by default the index's cached
+        one is used, which searches on different streams must not share."""
         nq = int(Q.shape[0])
         d = int(self.desc.d)
         _dev_tensor(Q, torch.float32, (nq, d), self.device, "Q")
@@ -241,7 +251,7 @@ class Index:
         pool_d = torch.empty(nq, Ce, dtype=torch.float32, device=dev) if return_pool else None
         probe = torch.empty(nq, nprobe, dtype=torch.int32, device=dev) if return_probe else None
         nb = self.workspace_bytes(max(nq, 1), k, C, nprobe)
-        ws = self.workspace(nb)
+        ws = self._caller_ws(ws, nb)
         _check(lib.hntl_search(self._h, _ptr(Q), nq, k, C, nprobe, _ptr(filters), _ptr(ws), ws.numel(), _ptr(ids),
                                _ptr(dist), _ptr(pool_ids), _ptr(pool_d), _ptr(probe), _stream(stream)))
         res = [ids, dist]
@@ -251,9 +261,10 @@ class Index:
             res.append(probe)
         return tuple(res)
 
-    def search_host(self, Q, k: int, C: int, nprobe: int, filters=None, stream=None):
+    def search_host(self, Q, k: int, C: int, nprobe: int, filters=None, stream=None, ws=None):
         """Host-buffer form: Q is a CPU float32 tensor (pinned for async copies);
-        returns CPU (ids i64, dist f32). Copies happen inside the call."""
+        returns CPU (ids i64, dist f32). Copies happen inside the call. `ws`
+        as for search (sized by hntl_search_host_workspace_bytes)."""
         nq, d = int(Q.shape[0]), int(self.desc.d)
         if Q.is_cuda or Q.dtype != torch.float32 or tuple(Q.shape) != (nq, d) or not Q.is_contiguous():
             raise ValueError("Q must be a contiguous CPU float32 tensor [nq, d]")
@@ -264,7 +275,7 @@ class Index:
         nb = int(lib.hntl_search_host_workspace_bytes(self._h, max(nq, 1), k, C, nprobe, int(filters is not None)))
         if nb == 0:
             raise HntlError(EINVAL, last_error())
-        ws = self.workspace(nb)
+        ws = self._caller_ws(ws, nb)
         _check(lib.hntl_search_host(self._h, _ptr(Q), nq, k, C, nprobe, _ptr(filters), _ptr(ws), ws.numel(),
                                     _ptr(ids), _ptr(dist), _stream(stream)))
         return ids, dist
