@@ -70,36 +70,15 @@ struct Coords {
   const float* scale;   // precision form, per grain
 };
 
-// The raw 16-byte lanes of row t of block b (split from the decode so that a
-// caller can issue several rows' loads before using any).
 template <int RT, bool kFP8>
-struct RawRow {
-  static constexpr int kLanes = kFP8 ? RT / 16 : RT / 4;
-  uint4 v[kLanes];
-};
-
-template <int RT, bool kFP8>
-__device__ __forceinline__ void load_raw(const Coords& c, int rp, size_t b, int t, RawRow<RT, kFP8>& raw) {
-  static_assert(!kFP8 || RT % 16 == 0, "FP8 rows are read in lanes of 16 codes");
-#pragma unroll
-  for (int l = 0; l < RawRow<RT, kFP8>::kLanes; ++l) {
-    if constexpr (kFP8)
-      raw.v[l] = l * 16 < rp
-                     ? __ldg(reinterpret_cast<const uint4*>(c.Z8b + ((b * (rp / 16) + l) * kBlockRows + t) * 16))
-                     : make_uint4(0, 0, 0, 0);
-    else
-      raw.v[l] = l * 4 < rp ? __ldg(reinterpret_cast<const uint4*>(c.Zb + ((b * (rp / 4) + l) * kBlockRows + t) * 4))
-                            : make_uint4(0, 0, 0, 0);
-  }
-}
-
-template <int RT, bool kFP8>
-__device__ __forceinline__ void decode_row(const RawRow<RT, kFP8>& raw, int rp, float s_g, float (&z)[RT]) {
+__device__ __forceinline__ void load_row(const Coords& c, int rp, float s_g, size_t b, int t, float (&z)[RT]) {
   if constexpr (kFP8) {
+    static_assert(RT % 16 == 0, "FP8 rows are read in lanes of 16 codes");
 #pragma unroll
     for (int l = 0; l < RT / 16; ++l) {
       if (l * 16 < rp) {
-        const uint32_t w[4] = {raw.v[l].x, raw.v[l].y, raw.v[l].z, raw.v[l].w};
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(c.Z8b + ((b * (rp / 16) + l) * kBlockRows + t) * 16));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
           const float2 a = __half22float2(
@@ -119,25 +98,23 @@ __device__ __forceinline__ void decode_row(const RawRow<RT, kFP8>& raw, int rp, 
   } else {
 #pragma unroll
     for (int l = 0; l < RT / 4; ++l) {
-      z[4 * l] = __uint_as_float(raw.v[l].x);
-      z[4 * l + 1] = __uint_as_float(raw.v[l].y);
-      z[4 * l + 2] = __uint_as_float(raw.v[l].z);
-      z[4 * l + 3] = __uint_as_float(raw.v[l].w);
+      if (l * 4 < rp) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(c.Zb + ((b * (rp / 4) + l) * kBlockRows + t) * 4));
+        z[4 * l] = v.x;
+        z[4 * l + 1] = v.y;
+        z[4 * l + 2] = v.z;
+        z[4 * l + 3] = v.w;
+      } else {
+        z[4 * l] = z[4 * l + 1] = z[4 * l + 2] = z[4 * l + 3] = 0.f;
+      }
     }
   }
-}
-
-template <int RT, bool kFP8>
-__device__ __forceinline__ void load_row(const Coords& c, int rp, float s_g, size_t b, int t, float (&z)[RT]) {
-  RawRow<RT, kFP8> raw;
-  load_raw<RT, kFP8>(c, rp, b, t, raw);
-  decode_row<RT, kFP8>(raw, rp, s_g, z);
 }
 
 // ------------------------------------------------------------------ pilot
 
 template <int RT, bool kFP8>
-__global__ void __launch_bounds__(256, (kFP8 && RT > 32) ? 1 : 2) k_pilot(int nprobe, int C, const int32_t* __restrict__ probe,
+__global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t* __restrict__ probe,
                                                const uint32_t* __restrict__ pair_of,
                                                const uint32_t* __restrict__ blk_off,
                                                const uint32_t* __restrict__ grain_rows, const Coords cz,
@@ -185,56 +162,33 @@ __global__ void __launch_bounds__(256, (kFP8 && RT > 32) ? 1 : 2) k_pilot(int np
                                        (8u * kPilotRows - scanned) / kBlockRows)
                                  : (budget - scanned) / kBlockRows;
     const uint32_t take = nbk < room ? nbk : room;  // whole blocks, evenly spaced over the grain
-    // kU rows per thread per round, all loads issued before the first row is evaluated
-    constexpr int kU = RawRow<RT, kFP8>::kLanes <= 2 ? 4 : (RawRow<RT, kFP8>::kLanes == 4 && !kFP8 ? 2 : 1);
-    const uint32_t nrows = take * kBlockRows;
-    for (uint32_t e0 = 0; e0 < nrows; e0 += kU * blockDim.x) {  // block-uniform trip count
-      bool keep[kU];
-      size_t bb[kU];
-      int tt[kU];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const uint32_t e = e0 + u * blockDim.x + threadIdx.x;
-        keep[u] = false;
-        bb[u] = 0;
-        tt[u] = 0;
-        if (e < nrows) {
-          const uint32_t i = e / kBlockRows;
-          tt[u] = (int)(e % kBlockRows);
-          const uint32_t jb = take == nbk ? i : (uint32_t)(((unsigned long long)i * nbk) / take);
-          bb[u] = blk_off[g] + jb;
-          keep[u] = jb * kBlockRows + tt[u] < n;
-          if (keep[u] && filter) {
-            const long long a = attr_b[bb[u] * kBlockRows + tt[u]];
-            keep[u] = a >= lo && a <= hi;
-          }
+    for (uint32_t e0 = 0; e0 < take * kBlockRows; e0 += blockDim.x) {  // block-uniform trip count
+      const uint32_t e = e0 + threadIdx.x;
+      bool keep = false;
+      uint32_t k = 0;
+      if (e < take * kBlockRows) {
+        const uint32_t i = e / kBlockRows;
+        const int t = e % kBlockRows;
+        const uint32_t jb = take == nbk ? i : (uint32_t)(((unsigned long long)i * nbk) / take);
+        const size_t b = blk_off[g] + jb;
+        keep = jb * kBlockRows + t < n;
+        if (keep && filter) {
+          const long long a = attr_b[b * kBlockRows + t];
+          keep = a >= lo && a <= hi;
         }
-      }
-      RawRow<RT, kFP8> raw[kU];
-      float rh[kU];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        if (keep[u]) {
-          load_raw<RT, kFP8>(cz, rp, bb[u], tt[u], raw[u]);
-          rh[u] = rho[bb[u] * kBlockRows + tt[u]];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        uint32_t k = 0;
-        if (keep[u]) {
+        if (keep) {
           float z[RT];
-          decode_row<RT, kFP8>(raw[u], rp, s_g, z);
-          k = __float_as_uint(eval_D<RT>(szq, z, rho_q, rh[u]));
-          keep[u] = k < kInfBits;
+          load_row<RT, kFP8>(cz, rp, s_g, b, t, z);
+          k = __float_as_uint(eval_D<RT>(szq, z, rho_q, rho[b * kBlockRows + t]));
+          keep = k < kInfBits;
         }
-        // one shared-memory atomic per warp for the slots of its kept rows
-        const unsigned mask = __ballot_sync(0xffffffffu, keep[u]);
-        uint32_t base = 0;
-        if (lane == 0 && mask) base = atomicAdd(&s_fill, (uint32_t)__popc(mask));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (keep[u]) vals[base + __popc(mask & ((1u << lane) - 1u))] = k;
       }
+      // one shared-memory atomic per warp for the slots of its kept rows
+      const unsigned mask = __ballot_sync(0xffffffffu, keep);
+      uint32_t base = 0;
+      if (lane == 0 && mask) base = atomicAdd(&s_fill, (uint32_t)__popc(mask));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (keep) vals[base + __popc(mask & ((1u << lane) - 1u))] = k;
     }
     scanned += take * kBlockRows;
   }

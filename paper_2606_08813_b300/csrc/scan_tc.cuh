@@ -181,7 +181,7 @@ constexpr int kSPThreads = 128;
 // in registers, each live pair evaluated by eval_D (the same function, on the
 // same decoded coordinates, as the pilot and the pool fallback).
 template <int RT>
-__global__ void __launch_bounds__(kSPThreads, RT > 32 ? 3 : 5) k_scan_sparse(
+__global__ void __launch_bounds__(kSPThreads, 6) k_scan_sparse(
     const SparseRec* __restrict__ recs, const uint32_t* __restrict__ lists, uint32_t* __restrict__ next_item,
     const uint32_t* __restrict__ blk_off,
     const uint32_t* __restrict__ grain_rows, const uint8_t* __restrict__ Z8b, const float* __restrict__ scale,

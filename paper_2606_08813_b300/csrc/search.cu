@@ -209,7 +209,7 @@ __global__ void k_bucket_scatter(const int32_t* __restrict__ probe, int nq, int 
 // One CTA per query: exact sum_t (q_t - x_t)^2 of every pool member (one warp
 // per member, 16-byte loads of the raw row), then the k smallest (dist, id).
 template <bool kBF16>
-__global__ void __launch_bounds__(256, kBF16 ? 3 : 2) k_rerank(const float* __restrict__ Q, const void* __restrict__ Xv, int d,
+__global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, const void* __restrict__ Xv, int d,
                                                 int C, int k, const uint32_t* __restrict__ cand_id,
                                                 int64_t* __restrict__ out_ids, float* __restrict__ out_d,
                                                 const uint32_t* __restrict__ qk, const uint32_t* __restrict__ qC) {
@@ -229,76 +229,9 @@ __global__ void __launch_bounds__(256, kBF16 ? 3 : 2) k_rerank(const float* __re
     k = kq;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n2 = pow2_at_least(C);
-  constexpr int kVec = kBF16 ? 8 : 4;           // values per 16-byte load
-  constexpr int kLoads = 1024 / (32 * kVec);    // 16-byte loads per lane for rows of up to 1024 values
-  if ((d % kVec) == 0 && d <= 1024) {
-    // Lane l always covers values (l + 32 i) * kVec + h, so its query values
-    // stay in registers; a warp takes two members per round with all their
-    // loads issued before use, and the ids of its next round are fetched
-    // meanwhile. Per lane the sum runs over i then h, as in the general loop
-    // below, so both give the same bits.
-    float qr[kLoads][kVec];
-#pragma unroll
-    for (int i = 0; i < kLoads; ++i)
-#pragma unroll
-      for (int h = 0; h < kVec; ++h) {
-        const int t = (lane + 32 * i) * kVec + h;
-        qr[i][h] = t < d ? Q[(size_t)q * d + t] : 0.f;
-      }
-    auto id_at = [&](int c) { return c < C ? cid[c] : kInvalidId; };
-    int c0 = 2 * warp;
-    uint32_t nid0 = id_at(c0), nid1 = id_at(c0 + 1);
-    for (; c0 < n2; c0 += 16) {
-      const uint32_t id[2] = {nid0, nid1};
-      uint4 v[2][kLoads];
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int i = 0; i < kLoads; ++i) {
-          const int t = (lane + 32 * i) * kVec;
-          v[j][i] = (id[j] != kInvalidId && t < d)
-                        ? __ldg(reinterpret_cast<const uint4*>(static_cast<const char*>(Xv) +
-                                                               ((size_t)id[j] * d + t) * (kBF16 ? 2 : 4)))
-                        : make_uint4(0, 0, 0, 0);
-        }
-      nid0 = id_at(c0 + 16);
-      nid1 = id_at(c0 + 17);
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        float acc = 0.f;
-#pragma unroll
-        for (int i = 0; i < kLoads; ++i) {
-          if ((lane + 32 * i) * kVec < d) {
-            const uint32_t w[4] = {v[j][i].x, v[j][i].y, v[j][i].z, v[j][i].w};
-            if (kBF16) {
-#pragma unroll
-              for (int h = 0; h < 4; ++h) {
-                const float a0 = qr[i][2 * h] - __uint_as_float(w[h] << 16);
-                const float a1 = qr[i][2 * h + 1] - __uint_as_float(w[h] & 0xFFFF0000u);
-                acc = fmaf(a0, a0, acc);
-                acc = fmaf(a1, a1, acc);
-              }
-            } else {
-#pragma unroll
-              for (int h = 0; h < 4; ++h) {
-                const float a0 = qr[i][h] - __uint_as_float(w[h]);
-                acc = fmaf(a0, a0, acc);
-              }
-            }
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        const unsigned long long key =
-            id[j] != kInvalidId ? ((unsigned long long)__float_as_uint(acc) << 32) | id[j] : ~0ull;
-        if (lane == 0 && c0 + j < n2) keys[c0 + j] = key;
-      }
-    }
-    __syncthreads();
-  } else {
   for (int t = threadIdx.x; t < d; t += blockDim.x) sq[t] = Q[(size_t)q * d + t];
   __syncthreads();
+  const int n2 = pow2_at_least(C);
   for (int c = warp; c < n2; c += 8) {
     unsigned long long key = ~0ull;
     uint32_t id = c < C ? cid[c] : kInvalidId;
@@ -349,7 +282,6 @@ __global__ void __launch_bounds__(256, kBF16 ? 3 : 2) k_rerank(const float* __re
     if (lane == 0) keys[c] = key;
   }
   __syncthreads();
-  }
   bitonic_sort_u64(keys, n2);
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     unsigned long long kk = i < n2 ? keys[i] : ~0ull;
