@@ -155,6 +155,11 @@ constexpr int kRefineCap = 1024;
 
 constexpr int kRefineSmemMax = (8192 + 2 * kMaxG) * 4;  // d <= 8192 on this path
 
+// Dynamic shared memory of k_route_refine: the query row and one or two key arrays.
+inline size_t refine_smem_bytes(int d, int G, int nprobe) {
+  return ((size_t)d + (nprobe > kRefineThreads ? 2 : 1) * (size_t)G) * sizeof(float);
+}
+
 // Margin coefficients of the refine shortlist (see the file header), with a
 // factor 2 of safety: {eps_dot, eps_norm}.
 inline void route_margin(bool bf16, int d, float* eps_dot, float* eps_norm) {
@@ -229,6 +234,28 @@ __device__ __forceinline__ float warp_center_dist2(QV qv, const float* __restric
   return acc;
 }
 
+// Ascending bitonic sort of 64 keys held by one warp, key i in lane i % 32
+// (a for i < 32, b above); stage j = 32 compares a lane's own two keys.
+__device__ __forceinline__ void warp_sort64(unsigned long long& a, unsigned long long& b, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j == 32) {
+        const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
+        a = lo;
+        b = hi;
+      } else {
+        const unsigned long long oa = __shfl_xor_sync(0xffffffffu, a, j), ob = __shfl_xor_sync(0xffffffffu, b, j);
+        const bool lower = (lane & j) == 0;
+        const bool up_a = (lane & k) == 0, up_b = ((lane + 32) & k) == 0;
+        a = (lower == up_a) ? (oa < a ? oa : a) : (oa > a ? oa : a);
+        b = (lower == up_b) ? (ob < b ? ob : b) : (ob > b ? ob : b);
+      }
+    }
+  }
+}
+
 // One CTA per query: margin shortlist over the approximate distances, exact
 // direct-form distances of the shortlist, the nprobe smallest (distance, g).
 // In the precision form q and the centres are BF16 values (Mh).
@@ -258,14 +285,17 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
   }
   const float qv = qn[q];
   const float* Dq = Dt + (size_t)q * G;
+  // khi is only kept for the radix path (nprobe > blockDim.x); the host sizes
+  // the dynamic memory to match (refine_smem_bytes)
+  const bool keep_hi = nprobe > (int)blockDim.x;
   uint32_t* khi = reinterpret_cast<uint32_t*>(sq + d);
-  uint32_t* klo = khi + G;
+  uint32_t* klo = keep_hi ? khi + G : khi;
   uint32_t my_min = 0xFFFFFFFFu;  // this thread's smallest approx + margin
   for (int g = threadIdx.x; g < G; g += blockDim.x) {
     const float mg = mn[g], D = Dq[g];
     const float m = eps_dot * sqrtf(qv * mg) + eps_norm * (qv + mg);
     const uint32_t hi = ordered_key(D + m);
-    khi[g] = hi;
+    if (keep_hi) khi[g] = hi;
     klo[g] = ordered_key(D - m);
     my_min = min(my_min, hi);
   }
@@ -365,11 +395,21 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
       if (lane == 0) keys[i] = k;
     }
     __syncthreads();
-    const int n2 = pow2_at_least(n);
-    for (int i = threadIdx.x; i < n2; i += blockDim.x)
-      if (i >= n) keys[i] = ~0ull;
-    __syncthreads();
-    bitonic_sort_u64(keys, n2);
+    if (n <= 64) {  // the usual case: one warp sorts, no block barriers
+      if (warp == 0) {
+        unsigned long long a = lane < n ? keys[lane] : ~0ull, b = lane + 32 < n ? keys[lane + 32] : ~0ull;
+        warp_sort64(a, b, lane);
+        keys[lane] = a;
+        keys[lane + 32] = b;
+      }
+      __syncthreads();
+    } else {
+      const int n2 = pow2_at_least(n);
+      for (int i = threadIdx.x; i < n2; i += blockDim.x)
+        if (i >= n) keys[i] = ~0ull;
+      __syncthreads();
+      bitonic_sort_u64(keys, n2);
+    }
   } else {
     // rare: exact distances of all G centres, nprobe rounds of a block-wide minimum above the last pick
     __shared__ unsigned long long s_best;

@@ -128,13 +128,17 @@ struct SparseRec {
 // still reach their pool from the item's blocks (rho_q + min rho_block <=
 // tau_q): none (dropped), a few (recorded with those pairs for the
 // direct-form kernel), at least kSTDense (the tensor-core kernel). One warp
-// per item. lists: [0] dense count, [1] sparse count.
+// per item. lists: [0] dense count, [1] light sparse count, [3] heavy sparse
+// count. Sparse records of light items fill the buffer (n_cap records) from
+// the front and those of heavy items (blocks x (1 + live pairs) >= 24) from
+// the back, so the scan can take the costly items first and finish on short
+// ones.
 __global__ void k_scan_classify(const uint4* __restrict__ items, const uint32_t* __restrict__ n_items,
                                 const uint32_t* __restrict__ need_cnt, const uint32_t* __restrict__ need_list,
                                 const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ pair_q,
                                 const float* __restrict__ rhoq, const float* __restrict__ tau,
                                 const float* __restrict__ blk_rho_min, uint4* __restrict__ dense,
-                                SparseRec* __restrict__ sparse, uint32_t* __restrict__ lists) {
+                                SparseRec* __restrict__ sparse, uint32_t n_cap, uint32_t* __restrict__ lists) {
   const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= *n_items) return;
@@ -168,7 +172,8 @@ __global__ void k_scan_classify(const uint4* __restrict__ items, const uint32_t*
     return;
   }
   uint32_t pos = 0;
-  if (lane == 0) pos = atomicAdd(&lists[1], 1u);
+  if (lane == 0)
+    pos = item.z * (1u + n) >= 24u ? n_cap - 1u - atomicAdd(&lists[3], 1u) : atomicAdd(&lists[1], 1u);
   pos = __shfl_sync(0xffffffffu, pos, 0);
   if (lane == 0) sparse[pos].item = make_uint4(item.x, item.y, item.z, n);
   if ((uint32_t)lane < n) sparse[pos].pr[lane] = mine;
@@ -182,7 +187,8 @@ constexpr int kSPThreads = 128;
 // same decoded coordinates, as the pilot and the pool fallback).
 template <int RT>
 __global__ void __launch_bounds__(kSPThreads, 6) k_scan_sparse(
-    const SparseRec* __restrict__ recs, const uint32_t* __restrict__ lists, uint32_t* __restrict__ next_item,
+    const SparseRec* __restrict__ recs, uint32_t n_cap, const uint32_t* __restrict__ lists,
+    uint32_t* __restrict__ next_item,
     const uint32_t* __restrict__ blk_off,
     const uint32_t* __restrict__ grain_rows, const uint8_t* __restrict__ Z8b, const float* __restrict__ scale,
     const float* __restrict__ rho, const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r,
@@ -197,7 +203,7 @@ __global__ void __launch_bounds__(kSPThreads, 6) k_scan_sparse(
   __shared__ long long slo[kP], shi[kP];
   const int t = threadIdx.x, lane = t & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const uint32_t total = lists[1];
+  const uint32_t heavy = lists[3], total = lists[1] + heavy;  // heavy items (at the back) first
   const int nks = rp / 16;
   // items taken from a global counter (their costs vary; a static split left a
   // tail); the next item's index is claimed while the current one is scanned
@@ -206,8 +212,9 @@ __global__ void __launch_bounds__(kSPThreads, 6) k_scan_sparse(
   __syncthreads();
   uint32_t w = s_item;
   while (w < total) {
-    const uint4 item = recs[w].item;
-    const uint32_t my_pr = t < kP ? recs[w].pr[t] : 0u;
+    const SparseRec& rec = recs[w < heavy ? n_cap - 1u - w : w - heavy];
+    const uint4 item = rec.item;
+    const uint32_t my_pr = t < kP ? rec.pr[t] : 0u;
     const uint32_t g = item.x, b0 = item.y, nb = item.z;
     const int np = (int)item.w;
     const uint32_t n_g = grain_rows[g], gb0 = blk_off[g];

@@ -371,8 +371,8 @@ Ws carve(const Index& I, uint32_t nq, uint32_t C, uint32_t nprobe, void* base) {
   w.rhoq = c.take<float>(P);
   w.tau = c.take<float>(nq);
   // survivor counts, then the scan's counters: [nq] next dense item, [nq + 1] dense items,
-  // [nq + 2] sparse items, [nq + 3] next sparse item
-  w.cnt = c.take<uint32_t>((size_t)nq + 4);
+  // [nq + 2] light sparse items, [nq + 3] next sparse item, [nq + 4] heavy sparse items
+  w.cnt = c.take<uint32_t>((size_t)nq + 5);
   w.cap = survivor_cap(C);
   w.surv = c.take<unsigned long long>((size_t)nq * w.cap);
   w.cand_id = c.take<uint32_t>((size_t)nq * C);
@@ -415,7 +415,7 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
       attr_tc = I.device;
     }
     dim3 grid((I.G + kRTN - 1) / kRTN, (nq + kRTM - 1) / kRTM);
-    const size_t rsmem = ((size_t)I.d + 2 * (size_t)I.G) * sizeof(float);
+    const size_t rsmem = refine_smem_bytes((int)I.d, (int)I.G, (int)nprobe);
     float eps_dot = 0.f, eps_norm = 0.f;
     route_margin(bf16, (int)I.d, &eps_dot, &eps_norm);
     if (bf16) {
@@ -489,14 +489,14 @@ void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, 
       attr_dev = I.device;
     }
     const size_t max_items = (size_t)I.G + I.n_blocks / kSTBlocks + 1;
-    uint32_t* lists = w.cnt + nq + 1;  // dense count, sparse count, next sparse item
+    uint32_t* lists = w.cnt + nq + 1;  // dense count, light sparse count, next sparse item, heavy sparse count
     k_grain_needed<<<I.G, 128, 0, st>>>(w.gcnt, w.pair_off, w.pair_q, w.rhoq, w.tau, I.grain_rho_min, w.need_list,
                                         w.need_cnt);
     k_scan_classify<<<(unsigned)((max_items * 32 + 255) / 256), 256, 0, st>>>(
         w.scan_items, w.scan_off + I.G, w.need_cnt, w.need_list, w.pair_off, w.pair_q, w.rhoq, w.tau, I.blk_rho_min,
-        w.dense_items, w.sparse_items, lists);
+        w.dense_items, w.sparse_items, (uint32_t)max_items, lists);
     k_scan_sparse<RT><<<(unsigned)std::min<size_t>(max_items, (size_t)I.num_sms * 6), kSPThreads, 0, st>>>(
-        w.sparse_items, lists, lists + 2, I.blk_off, I.grain_rows, I.Z8b, I.scale, I.rho, I.ids, I.attr_b, (int)I.r,
+        w.sparse_items, (uint32_t)max_items, lists, lists + 2, I.blk_off, I.grain_rows, I.Z8b, I.scale, I.rho, I.ids, I.attr_b, (int)I.r,
         (int)I.rp,
         w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap, w.cnt, w.surv);
     k_scan_tc<RT><<<(unsigned)std::min<size_t>(max_items, (size_t)I.num_sms * 2), kSTThreads, ScanTc<RT>::kSmem,
@@ -623,7 +623,7 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
                                               w.pair_q, w.zq, w.rhoq);
   }
   mark(3);
-  HNTL_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * ((size_t)nq + 4), st));
+  HNTL_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * ((size_t)nq + 5), st));
   {
     const std::function<void(int)> mk = mark;
     if (I.r <= 8) launch_scan_select_p<8>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk, qC);
