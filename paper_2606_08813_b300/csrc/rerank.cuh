@@ -1,0 +1,97 @@
+// Exact rerank of the pool (sec. 2.1 step 4, Mode B): sum_t (q_t - x_t)^2
+// of every pool member against the FP32 query, the k smallest (dist, id).
+#pragma once
+
+#include "hntl_internal.cuh"
+#include "kernels_common.cuh"
+
+namespace hntl {
+namespace {
+
+// One CTA per query: exact sum_t (q_t - x_t)^2 of every pool member (one warp
+// per member, 16-byte loads of the raw row), then the k smallest (dist, id).
+template <bool kBF16>
+__global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, const void* __restrict__ Xv, int d,
+                                                int C, int k, const uint32_t* __restrict__ cand_id,
+                                                int64_t* __restrict__ out_ids, float* __restrict__ out_d,
+                                                const uint32_t* __restrict__ qk, const uint32_t* __restrict__ qC) {
+  extern __shared__ float sq[];  // [d]
+  __shared__ unsigned long long keys[kMaxC];
+  const int q = blockIdx.x;
+  const uint32_t* cid = cand_id + (size_t)q * C;  // rows C (the batch's largest pool) apart
+  int64_t* oid = out_ids + (size_t)q * k;         // rows k (the batch's largest k) apart
+  float* od = out_d + (size_t)q * k;
+  if (qC) {  // mixed batch: this query's own pool size and result count
+    const int kq = (int)qk[q];
+    for (int i = kq + threadIdx.x; i < k; i += blockDim.x) {
+      oid[i] = -1;
+      od[i] = INFINITY;
+    }
+    C = (int)qC[q];
+    k = kq;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = threadIdx.x; t < d; t += blockDim.x) sq[t] = Q[(size_t)q * d + t];
+  __syncthreads();
+  const int n2 = pow2_at_least(C);
+  for (int c = warp; c < n2; c += 8) {
+    unsigned long long key = ~0ull;
+    uint32_t id = c < C ? cid[c] : kInvalidId;
+    if (id != kInvalidId) {
+      float acc = 0.f;
+      if (!kBF16) {
+        const float* x = reinterpret_cast<const float*>(Xv) + (size_t)id * d;
+        if ((d & 3) == 0) {
+          for (int t = lane * 4; t < d; t += 128) {
+            float4 v = __ldg(reinterpret_cast<const float4*>(x + t));
+            float a0 = sq[t] - v.x, a1 = sq[t + 1] - v.y, a2 = sq[t + 2] - v.z, a3 = sq[t + 3] - v.w;
+            acc = fmaf(a0, a0, acc);
+            acc = fmaf(a1, a1, acc);
+            acc = fmaf(a2, a2, acc);
+            acc = fmaf(a3, a3, acc);
+          }
+        } else {
+          for (int t = lane; t < d; t += 32) {
+            float a0 = sq[t] - __ldg(x + t);
+            acc = fmaf(a0, a0, acc);
+          }
+        }
+      } else {
+        const uint16_t* x = reinterpret_cast<const uint16_t*>(Xv) + (size_t)id * d;
+        if ((d & 7) == 0) {
+          for (int t = lane * 8; t < d; t += 256) {
+            uint4 v = __ldg(reinterpret_cast<const uint4*>(x + t));
+            uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              float lo = __uint_as_float(w[h] << 16), hi = __uint_as_float(w[h] & 0xFFFF0000u);
+              float a0 = sq[t + 2 * h] - lo, a1 = sq[t + 2 * h + 1] - hi;
+              acc = fmaf(a0, a0, acc);
+              acc = fmaf(a1, a1, acc);
+            }
+          }
+        } else {
+          for (int t = lane; t < d; t += 32) {
+            float a0 = sq[t] - __uint_as_float((uint32_t)__ldg(x + t) << 16);
+            acc = fmaf(a0, a0, acc);
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      key = ((unsigned long long)__float_as_uint(acc) << 32) | id;
+    }
+    if (lane == 0) keys[c] = key;
+  }
+  __syncthreads();
+  bitonic_sort_u64(keys, n2);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    unsigned long long kk = i < n2 ? keys[i] : ~0ull;
+    bool ok = kk != ~0ull;
+    oid[i] = ok ? (int64_t)(kk & 0xFFFFFFFFu) : -1;
+    od[i] = ok ? __uint_as_float((uint32_t)(kk >> 32)) : INFINITY;
+  }
+}
+
+}  // namespace
+}  // namespace hntl
