@@ -2,7 +2,8 @@
 //
 // k_route_tc: S = Q M^T on tcgen05 (TF32 for FP32 indices, BF16 for the
 // precision form; FP32 accumulation in TMEM), operands streamed by TMA
-// through a 4-stage shared-memory ring; the epilogue writes the approximate
+// through a 2-stage shared-memory ring (two CTAs per SM, so one CTA's
+// epilogue overlaps the other's main loop); the epilogue writes the approximate
 // squared distance ||q||^2 + ||mu||^2 - 2 q.mu for a 128-query x 256-centre
 // tile.
 //
