@@ -1,11 +1,11 @@
 // Centroid routing on the tensor cores (sec. 2.1 step 1, sec. 2.3 item 1).
 //
 // k_route_tc: S = Q M^T on tcgen05 (TF32 for FP32 indices, BF16 for the
-// precision form; FP32 accumulation in TMEM), operands streamed by TMA
-// through a 2-stage shared-memory ring (two CTAs per SM, so one CTA's
-// epilogue overlaps the other's main loop); the epilogue writes the approximate
-// squared distance ||q||^2 + ||mu||^2 - 2 q.mu for a 128-query x 256-centre
-// tile.
+// precision form; FP32 accumulation in TMEM), persistent and
+// warp-specialised: operands streamed by TMA through a 4-stage shared-memory
+// ring, two TMEM accumulators so that the epilogue of one 128-query x
+// 256-centre tile (the approximate squared distance ||q||^2 + ||mu||^2 -
+// 2 q.mu) overlaps the MMAs of the next.
 //
 // k_route_refine: the approximate distance is within
 //   m(q, g) = eps_dot ||q|| ||mu_g|| + eps_norm (||q||^2 + ||mu_g||^2)
@@ -34,14 +34,27 @@
 namespace hntl {
 namespace {
 
-constexpr int kRTM = 128, kRTN = 256, kRStages = 2;  // two CTAs per SM: one epilogue overlaps the other main loop
+constexpr int kRTM = 128, kRTN = 256, kRStages = 4;
+constexpr int kRThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kRouteTcSmem = kRStages * (kRTM + kRTN) * 128 + 1024;
 
+// Persistent, warp-specialised: CTA b takes the 128-query x 256-centre tiles
+// b, b + grid, ... (centre blocks vary fastest, so CTAs working at the same
+// time share their query tile in L2).
+//   warp 0     one thread streams each tile's K blocks (query and centre
+//              rows, 128 bytes of K each) by TMA through the stage ring.
+//   warp 1     one thread issues the MMAs of a tile into one of two TMEM
+//              accumulators (256 columns each) and hands it on through `accf`.
+//   warps 2-5  epilogue, warp w for TMEM lane quarter w % 4: reads its 32
+//              rows of the finished accumulator, frees it through `acce`, and
+//              writes ||q||^2 + ||mu||^2 - 2 q.mu while the next tile's MMAs run.
 template <bool kBF16>
-__global__ void __launch_bounds__(128, 2) k_route_tc(const __grid_constant__ CUtensorMap mapQ,
-                                                  const __grid_constant__ CUtensorMap mapM, int nq, int G, int d,
-                                                  const float* __restrict__ qn, const float* __restrict__ mn,
-                                                  float* __restrict__ Dt, int* __restrict__ err) {
+__global__ void __launch_bounds__(kRThreads, 1) k_route_tc(const __grid_constant__ CUtensorMap mapQ,
+                                                        const __grid_constant__ CUtensorMap mapM, int nq, int G,
+                                                        int d, const float* __restrict__ qn,
+                                                        const float* __restrict__ mn, float* __restrict__ Dt,
+                                                        int* __restrict__ err) {
+  constexpr int S = kRStages;
   constexpr int kElem = kBF16 ? 2 : 4;
   constexpr int kKB = 128 / kElem;       // K elements per stage (one 128-byte row)
   constexpr int kStep = kBF16 ? 16 : 8;  // K per MMA
@@ -49,100 +62,154 @@ __global__ void __launch_bounds__(128, 2) k_route_tc(const __grid_constant__ CUt
   constexpr uint32_t kIdesc = tc::idesc_f32acc(kBF16 ? 1u : 2u, kRTM, kRTN);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[kRStages], empty[kRStages], done;
+  __shared__ __align__(8) uint64_t full[S], empty[S], accf[2], acce[2], fin;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
-  __shared__ float smn[kRTN];  // ||mu||^2 of this tile's centres
+  __shared__ uint32_t s_it_prod, s_it_mma;  // K blocks loaded by the producer / consumed by the MMA thread
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) tc::tmem_alloc(&tmem_base, kRTN);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 2 * kRTN);
   if (tid == 32) {
-    for (int s = 0; s < kRStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(&done, 1);
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(&accf[a], 1);
+      tc::mbar_init(&acce[a], 4);
+    }
+    tc::mbar_init(&fin, 1);
     tc::mbar_fence_init();
     s_fail = 0;
+    s_it_prod = s_it_mma = 0;
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
-  const int q0 = blockIdx.y * kRTM, g0 = blockIdx.x * kRTN;
+  const int n_gb = (G + kRTN - 1) / kRTN;
+  const int total = n_gb * ((nq + kRTM - 1) / kRTM);
   const int nkb = (d + kKB - 1) / kKB;
-  if (tid == 0) {
-    // producer: TMA loads of the query and centre tiles of each K block
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % kRStages;
-      if (kb >= kRStages && !tc::mbar_wait(&empty[s], ((kb / kRStages) - 1) & 1)) {
-        atomicExch(&s_fail, 1);
-        break;
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      uint32_t it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        const int q0 = (t / n_gb) * kRTM, g0 = (t % n_gb) * kRTN;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % S);
+          if (it >= (uint32_t)S && !tc::mbar_wait(&empty[s], ((it / S) - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + s * (kBytesA + kBytesB);
+          tc::mbar_expect_tx(&full[s], kBytesA + kBytesB);
+          tc::tma_load_2d(&mapQ, &full[s], sa, kb * kKB, q0);
+          tc::tma_load_2d(&mapM, &full[s], sa + kBytesA, kb * kKB, g0);
+        }
       }
-      uint8_t* sa = smem + s * (kBytesA + kBytesB);
-      tc::mbar_expect_tx(&full[s], kBytesA + kBytesB);
-      tc::tma_load_2d(&mapQ, &full[s], sa, kb * kKB, q0);
-      tc::tma_load_2d(&mapM, &full[s], sa + kBytesA, kb * kKB, g0);
+      s_it_prod = it;
+      if (!ok) atomicExch(&s_fail, 1);
     }
-  } else if (tid == 32) {
-    // MMA issuer
-    bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % kRStages;
-      if (!tc::mbar_wait(&full[s], (kb / kRStages) & 1)) {
-        atomicExch(&s_fail, 1);
-        ok = false;
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issue
+      uint32_t it = 0, li = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++li) {
+        const int a = (int)(li & 1);
+        if (li >= 2 && !tc::mbar_wait(&acce[a], ((li >> 1) - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t acc = tmem + (uint32_t)(a * kRTN);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % S);
+          if (!tc::mbar_wait(&full[s], (it / S) & 1)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t sa = tc::smem_u32(smem + s * (kBytesA + kBytesB));
+#pragma unroll
+          for (int ks = 0; ks < kKB / kStep; ++ks)
+            tc::mma<kBF16>(acc, tc::desc_sw128(sa + ks * 32), tc::desc_sw128(sa + kBytesA + ks * 32), kIdesc,
+                           (kb | ks) != 0);
+          tc::mma_commit(&empty[s]);
+        }
+        if (ok) tc::mma_commit(&accf[a]);
+      }
+      s_it_mma = it;
+      if (!ok) atomicExch(&s_fail, 1);
+      if (it > 0) {
+        tc::mma_commit(&fin);  // arrives once every MMA issued above has completed
+        if (!tc::mbar_wait(&fin, 0)) atomicExch(&s_fail, 1);
+      }
+    }
+    __syncwarp();
+  } else {
+    // epilogue: TMEM lane quarter j = rows 32 j .. 32 j + 31 of each tile
+    const int j = warp & 3;
+    const bool vec = (G & 3) == 0;  // rows of Dt start on 16-byte boundaries
+    bool failed = false;
+    uint32_t li = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++li) {
+      const int a = (int)(li & 1);
+      const int q0 = (t / n_gb) * kRTM, g0 = (t % n_gb) * kRTN;
+      const int q = q0 + j * 32 + lane;
+      const float qv = q < nq ? qn[q] : 0.f;
+      if (__any_sync(0xffffffffu, !tc::mbar_wait(&accf[a], (li >> 1) & 1))) {  // warp-uniform
+        failed = true;
         break;
       }
       tc::fence_after_sync();
-      const uint32_t sa = tc::smem_u32(smem + s * (kBytesA + kBytesB));
-#pragma unroll
-      for (int ks = 0; ks < kKB / kStep; ++ks)
-        tc::mma<kBF16>(tmem, tc::desc_sw128(sa + ks * 32), tc::desc_sw128(sa + kBytesA + ks * 32), kIdesc,
-                       (kb | ks) != 0);
-      tc::mma_commit(&empty[s]);
-    }
-    if (ok) tc::mma_commit(&done);
-  }
-  for (int i = tid; i < kRTN; i += 128) smn[i] = g0 + i < G ? mn[g0 + i] : 0.f;
-  const bool waited = tc::mbar_wait(&done, 0);
-  const bool failed = __syncthreads_or(!waited || s_fail);
-  tc::fence_after_sync();
-  if (!failed) {
-    const int row = warp * 32 + lane;
-    const int q = q0 + row;
-    const float qv = q < nq ? qn[q] : 0.f;
-    const bool vec = (G & 3) == 0;  // rows of Dt start on 16-byte boundaries
 #pragma unroll 1
-    for (int c0 = 0; c0 < kRTN; c0 += 32) {
-      float v[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
-      if (q < nq) {
+      for (int c0 = 0; c0 < kRTN; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(j * 32) << 16) + (uint32_t)(a * kRTN + c0), v);
+        if (c0 + 32 == kRTN) {  // every column of this accumulator is in registers: free it
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&acce[a]);
+        }
+        const float mv = g0 + c0 + lane < G ? mn[g0 + c0 + lane] : 0.f;  // ||mu||^2 of column c0 + lane
         float* out = Dt + (size_t)q * G + g0 + c0;
         const int lim = G - (g0 + c0);  // columns of this chunk inside the matrix
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-          float4 o;
-          o.x = (qv + smn[c0 + j]) - 2.f * v[j];
-          o.y = (qv + smn[c0 + j + 1]) - 2.f * v[j + 1];
-          o.z = (qv + smn[c0 + j + 2]) - 2.f * v[j + 2];
-          o.w = (qv + smn[c0 + j + 3]) - 2.f * v[j + 3];
-          if (vec && j + 4 <= lim) {
-            *reinterpret_cast<float4*>(out + j) = o;
-          } else {
-            if (j < lim) out[j] = o.x;
-            if (j + 1 < lim) out[j + 1] = o.y;
-            if (j + 2 < lim) out[j + 2] = o.z;
-            if (j + 3 < lim) out[j + 3] = o.w;
+        for (int c = 0; c < 32; c += 4) {
+          const float m0 = __shfl_sync(0xffffffffu, mv, c), m1 = __shfl_sync(0xffffffffu, mv, c + 1);
+          const float m2 = __shfl_sync(0xffffffffu, mv, c + 2), m3 = __shfl_sync(0xffffffffu, mv, c + 3);
+          if (q < nq) {
+            float4 o;
+            o.x = (qv + m0) - 2.f * v[c];
+            o.y = (qv + m1) - 2.f * v[c + 1];
+            o.z = (qv + m2) - 2.f * v[c + 2];
+            o.w = (qv + m3) - 2.f * v[c + 3];
+            if (vec && c + 4 <= lim) {
+              *reinterpret_cast<float4*>(out + c) = o;
+            } else {
+              if (c < lim) out[c] = o.x;
+              if (c + 1 < lim) out[c + 1] = o.y;
+              if (c + 2 < lim) out[c + 2] = o.z;
+              if (c + 3 < lim) out[c + 3] = o.w;
+            }
           }
         }
       }
     }
-  } else if (tid == 0) {
-    atomicOr(err, tc::kErrTimeout);
+    if (failed) atomicExch(&s_fail, 1);
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, kRTN);
+  if (tid == 0 && s_fail) {
+    // loads issued but never waited for (a wait gave up): let them land before the CTA exits
+    for (uint32_t i = s_it_mma; i < s_it_prod; ++i) tc::mbar_wait(&full[i % S], (i / S) & 1, 1u << 16);
+    atomicOr(err, tc::kErrTimeout);
+  }
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 2 * kRTN);
+  }
 }
 
 __device__ __forceinline__ uint32_t ordered_key(float x) {  // monotone map of any float (NaN -> top) to uint32
@@ -303,8 +370,8 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
   // U: any upper bound on the nprobe-th smallest approx + margin keeps the shortlist
   // exact. The nprobe-th smallest of the threads' minima is one (a subset's order
   // statistic is at least the full set's) and is rarely above the true one. Each
-  // warp sorts its lanes' minima; one warp merges the sorted runs up to the
-  // nprobe-th value.
+  // warp sorts its lanes' minima; the nprobe-th value of the union is found by
+  // ranking every value against the other warps' sorted runs.
   uint32_t prefix = 0;
   bool have_u = false;
   if (nprobe <= (int)blockDim.x) {
@@ -321,28 +388,24 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
     uint32_t* lists = reinterpret_cast<uint32_t*>(keys);  // nw sorted runs of 32
     lists[warp * 32 + lane] = v;
     __syncthreads();
-    if (warp == 0) {  // merge the runs: the nprobe-th value taken is U
-      uint32_t h = 0;
-      uint32_t head = lane < nw ? lists[lane * 32] : 0xFFFFFFFFu, val = 0xFFFFFFFFu;
-      for (int step = 0; step < nprobe; ++step) {
-        uint32_t m = head;
-        int src = lane;
+    {  // U = the value of rank nprobe - 1 in the union of the runs, ties ordered by run
+      // then position; each thread ranks its own value by a binary search of
+      // every other run, and the one thread of that rank publishes it
+      uint32_t rank = (uint32_t)lane;  // its own run: the lanes before it
+      for (int w2 = 0; w2 < nw; ++w2) {
+        if (w2 == warp) continue;
+        const uint32_t* run = lists + w2 * 32;
+        const bool before = w2 < warp;  // equal values of earlier runs rank lower
+        int pos = 0;  // how many of run[] rank below v (a prefix of the sorted run)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const uint32_t om = __shfl_xor_sync(0xffffffffu, m, o);
-          const int os = __shfl_xor_sync(0xffffffffu, src, o);
-          if (om < m || (om == m && os < src)) {
-            m = om;
-            src = os;
-          }
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t e = run[pos + step - 1];
+          if (before ? e <= v : e < v) pos += step;
         }
-        val = m;
-        if (lane == src) {
-          ++h;
-          head = h < 32 ? lists[lane * 32 + h] : 0xFFFFFFFFu;
-        }
+        if (pos < 32 && (before ? run[pos] <= v : run[pos] < v)) ++pos;
+        rank += (uint32_t)pos;
       }
-      if (lane == 0) s_bin = val;
+      if (rank == (uint32_t)(nprobe - 1)) s_bin = v;
     }
     __syncthreads();
     prefix = s_bin;

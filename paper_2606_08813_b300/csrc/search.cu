@@ -328,18 +328,20 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
                                          kRefineSmemMax));
       attr_tc = I.device;
     }
-    dim3 grid((I.G + kRTN - 1) / kRTN, (nq + kRTM - 1) / kRTM);
+    // persistent: one CTA per SM at most
+    const size_t tiles = (size_t)((I.G + kRTN - 1) / kRTN) * ((nq + kRTM - 1) / kRTM);
+    const unsigned grid = (unsigned)std::min<size_t>(tiles, (size_t)I.num_sms);
     const size_t rsmem = refine_smem_bytes((int)I.d, (int)I.G, (int)nprobe);
     float eps_dot = 0.f, eps_norm = 0.f;
     route_margin(bf16, (int)I.d, &eps_dot, &eps_norm);
     if (bf16) {
-      k_route_tc<true><<<grid, 128, kRouteTcSmem, st>>>(mapQ, I.mapM, (int)nq, (int)I.G, (int)I.d, w.qn, I.mnorm,
+      k_route_tc<true><<<grid, kRThreads, kRouteTcSmem, st>>>(mapQ, I.mapM, (int)nq, (int)I.G, (int)I.d, w.qn, I.mnorm,
                                                         w.route_d, I.d_err);
       k_route_refine<true><<<nq, kRefineThreads, rsmem, st>>>(Qd, I.M, I.Mh, w.qn, I.mnorm, w.route_d, (int)I.G,
                                                               (int)I.d, (int)nprobe, eps_dot, eps_norm, w.probe,
                                                               w.probe_d);
     } else {
-      k_route_tc<false><<<grid, 128, kRouteTcSmem, st>>>(mapQ, I.mapM, (int)nq, (int)I.G, (int)I.d, w.qn, I.mnorm,
+      k_route_tc<false><<<grid, kRThreads, kRouteTcSmem, st>>>(mapQ, I.mapM, (int)nq, (int)I.G, (int)I.d, w.qn, I.mnorm,
                                                          w.route_d, I.d_err);
       k_route_refine<false><<<nq, kRefineThreads, rsmem, st>>>(Qd, I.M, I.Mh, w.qn, I.mnorm, w.route_d, (int)I.G,
                                                                (int)I.d, (int)nprobe, eps_dot, eps_norm, w.probe,
