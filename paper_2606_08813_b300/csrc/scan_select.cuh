@@ -6,7 +6,9 @@
 //                  nearest probed grains in routing order and takes the C-th
 //                  smallest as tau_q. Those are real rows of the query's
 //                  probe set, so at least C rows have D <= tau_q and tau_q is
-//                  an upper bound on the query's true C-th distance.
+//                  an upper bound on the query's true C-th distance. tau_q is
+//                  taken to 16 bits (two radix passes) and rounded up to the
+//                  top of that bin: still a bound, at most 2^-7 looser.
 //   k_scan_filter  grain-major scan of every probed Block-SoA block: a
 //                  grain's coordinates are read once and applied to every
 //                  query that probes it; rows with D <= tau_q (and passing
@@ -198,10 +200,14 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
     if (threadIdx.x == 0) tau[q] = INFINITY;
     return;
   }
-  // C-th smallest of vals[0..fill): four 8-bit radix digits
+  // the C-th smallest of vals[0..fill) to its top 16 bits (two 8-bit radix
+  // digits); tau_q is the top of that bin, at most 2^-7 relative above the
+  // C-th smallest value, so still an upper bound on the query's true C-th
+  // distance (the pool is selected exactly downstream; a looser tau only
+  // admits a few more survivors)
   uint32_t prefix = 0, need = (uint32_t)C;
   int known = 0;
-  for (int pass = 0; pass < 4; ++pass) {
+  for (int pass = 0; pass < 2; ++pass) {
     const int sh = 24 - 8 * pass;
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
     __syncthreads();
   }
   (void)s_total;
-  if (threadIdx.x == 0) tau[q] = __uint_as_float(prefix);
+  if (threadIdx.x == 0) tau[q] = __uint_as_float((prefix << 16) | 0xFFFFu);  // finite: every value is below +inf
 }
 
 // ------------------------------------------------------------------ scan
