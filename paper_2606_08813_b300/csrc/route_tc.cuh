@@ -359,13 +359,26 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
   uint32_t* khi = reinterpret_cast<uint32_t*>(sq + d);
   uint32_t* klo = keep_hi ? khi + G : khi;
   uint32_t my_min = 0xFFFFFFFFu;  // this thread's smallest approx + margin
-  for (int g = threadIdx.x; g < G; g += blockDim.x) {
-    const float mg = mn[g], D = Dq[g];
-    const float m = eps_dot * sqrtf(qv * mg) + eps_norm * (qv + mg);
-    const uint32_t hi = ordered_key(D + m);
-    if (keep_hi) khi[g] = hi;
-    klo[g] = ordered_key(D - m);
-    my_min = min(my_min, hi);
+  constexpr int kChunk = 8;        // loads of a thread issued together
+  for (int g0 = threadIdx.x; g0 < G; g0 += kChunk * blockDim.x) {
+    float Dv[kChunk], mv[kChunk];
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      const int g = g0 + u * blockDim.x;
+      Dv[u] = g < G ? Dq[g] : 0.f;
+      mv[u] = g < G ? mn[g] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      const int g = g0 + u * blockDim.x;
+      if (g < G) {
+        const float m = eps_dot * sqrtf(qv * mv[u]) + eps_norm * (qv + mv[u]);
+        const uint32_t hi = ordered_key(Dv[u] + m);
+        if (keep_hi) khi[g] = hi;
+        klo[g] = ordered_key(Dv[u] - m);
+        my_min = min(my_min, hi);
+      }
+    }
   }
   // U: any upper bound on the nprobe-th smallest approx + margin keeps the shortlist
   // exact. The nprobe-th smallest of the threads' minima is one (a subset's order

@@ -383,6 +383,7 @@ struct ProbedRowsSrc {
 };
 
 constexpr int kSelDigits = 4, kSelBits = 8;  // radix select on the D bit pattern, 8 bits at a time
+constexpr int kSelBinCap = 256;              // bin size below which two digits suffice
 
 struct SelSmem {
   uint32_t hist[1 << kSelBits];
@@ -400,7 +401,7 @@ __device__ void select_topc(const Src& src, int C, SelSmem& S, uint32_t* __restr
                             float* __restrict__ out_d) {
   uint32_t prefix = 0, need = (uint32_t)C;
   int known = 0;
-  bool take_all = false;
+  bool take_all = false, short_bin = false;
   for (int pass = 0; pass < kSelDigits; ++pass) {
     const int nb = 1 << kSelBits;
     const int sh = 32 - kSelBits * (pass + 1);
@@ -427,14 +428,42 @@ __device__ void select_topc(const Src& src, int C, SelSmem& S, uint32_t* __restr
     need -= S.s_below;
     prefix = (prefix << kSelBits) | S.s_bin;
     known += kSelBits;
+    // after two digits the bin holding the C-th key is usually small: finish
+    // by ordering that bin's keys instead of two more passes over the source
+    const bool small_bin = pass == 1 && S.hist[S.s_bin] <= (uint32_t)kSelBinCap;  // block-uniform
     __syncthreads();
+    if (small_bin) {
+      short_bin = true;
+      break;
+    }
   }
-  const uint32_t T = take_all ? kInfBits : prefix;
   if (threadIdx.x == 0) {
     S.s_nout = 0;
     S.s_nties = 0;
   }
   __syncthreads();
+  uint32_t nout;
+  if (short_bin) {
+    // keys whose top 16 bits are below the bin's are in the pool; the bin's
+    // keys (at most kSelBinCap) are ranked by (D, id) and the first `need` kept
+    const uint32_t T16 = prefix;
+    src.for_each([&](uint32_t k, uint32_t id) {
+      if (k >= kInfBits) return;
+      const unsigned long long key = ((unsigned long long)k << 32) | id;
+      if ((k >> 16) < T16) S.keys[atomicAdd(&S.s_nout, 1u)] = key;
+      else if ((k >> 16) == T16) S.tk[atomicAdd(&S.s_nties, 1u)] = key;
+    });
+    __syncthreads();
+    const uint32_t nb_ = S.s_nout, nt = S.s_nties;
+    for (uint32_t i = threadIdx.x; i < nt; i += blockDim.x) {
+      const unsigned long long me = S.tk[i];
+      uint32_t rank = 0;
+      for (uint32_t j = 0; j < nt; ++j) rank += S.tk[j] < me ? 1u : 0u;
+      if (rank < need) S.keys[nb_ + rank] = me;
+    }
+    nout = (uint32_t)C;
+  } else {
+  const uint32_t T = take_all ? kInfBits : prefix;
   src.for_each([&](uint32_t k, uint32_t id) {
     if (k >= kInfBits) return;
     if (k < T) {
@@ -446,7 +475,7 @@ __device__ void select_topc(const Src& src, int C, SelSmem& S, uint32_t* __restr
     }
   });
   __syncthreads();
-  uint32_t nout = S.s_nout;
+  nout = S.s_nout;
   if (!take_all) {
     const uint32_t need_eq = (uint32_t)C - nout;
     if (S.s_nties <= (uint32_t)kTieCap) {
@@ -481,17 +510,20 @@ __device__ void select_topc(const Src& src, int C, SelSmem& S, uint32_t* __restr
     }
     nout = (uint32_t)C;
   }
+  }
   __syncthreads();
-  const int n2 = pow2_at_least(C);
-  for (int i = threadIdx.x; i < n2; i += blockDim.x)
-    if (i >= (int)nout) S.keys[i] = ~0ull;
-  __syncthreads();
-  bitonic_sort_u64(S.keys, n2);
-  for (int i = threadIdx.x; i < C; i += blockDim.x) {
-    const unsigned long long kk = S.keys[i];
-    const bool ok = i < (int)nout;
-    out_id[i] = ok ? (uint32_t)(kk & 0xFFFFFFFFu) : kInvalidId;
-    out_d[i] = ok ? __uint_as_float((uint32_t)(kk >> 32)) : INFINITY;
+  // output in (D, id) order: the keys are distinct (each id once), so a key's
+  // position is the number of smaller keys
+  for (uint32_t i = threadIdx.x; i < nout; i += blockDim.x) {
+    const unsigned long long me = S.keys[i];
+    uint32_t rank = 0;
+    for (uint32_t j = 0; j < nout; ++j) rank += S.keys[j] < me ? 1u : 0u;
+    out_id[rank] = (uint32_t)(me & 0xFFFFFFFFu);
+    out_d[rank] = __uint_as_float((uint32_t)(me >> 32));
+  }
+  for (int i = (int)nout + threadIdx.x; i < C; i += blockDim.x) {
+    out_id[i] = kInvalidId;
+    out_d[i] = INFINITY;
   }
 }
 
