@@ -84,23 +84,12 @@ __global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, con
     if (lane == 0) keys[c] = key;
   }
   __syncthreads();
-  // the k smallest in (dist, id) order: real keys are distinct (each id once)
-  // and below the ~0 pads, so a real key's position is the number of smaller
-  // keys; the slots no real key reaches keep the pads written first
+  bitonic_sort_u64(keys, n2);
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    oid[i] = -1;
-    od[i] = INFINITY;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-    const unsigned long long me = keys[i];
-    if (me == ~0ull) continue;
-    int rank = 0;
-    for (int j = 0; j < n2; ++j) rank += keys[j] < me ? 1 : 0;
-    if (rank < k) {
-      oid[rank] = (int64_t)(me & 0xFFFFFFFFu);
-      od[rank] = __uint_as_float((uint32_t)(me >> 32));
-    }
+    unsigned long long kk = i < n2 ? keys[i] : ~0ull;
+    bool ok = kk != ~0ull;
+    oid[i] = ok ? (int64_t)(kk & 0xFFFFFFFFu) : -1;
+    od[i] = ok ? __uint_as_float((uint32_t)(kk >> 32)) : INFINITY;
   }
 }
 
