@@ -121,9 +121,7 @@ __global__ void __launch_bounds__(128) k_grain_needed(const uint32_t* __restrict
 struct SparseRec {
   uint4 item;                    // grain, first block, blocks, live pairs
   uint32_t pr[kSTDense - 1];     // live pairs
-  uint32_t q[kSTDense - 1];      // their queries
-  float tau[kSTDense - 1];       // the queries' pool bounds tau_q
-  float rhoq[kSTDense - 1];      // the pairs' residual norms rho_q
+  uint32_t pad;
 };
 
 // Sorts the scan's work items by how many of their grain's live pairs can
@@ -178,13 +176,7 @@ __global__ void k_scan_classify(const uint4* __restrict__ items, const uint32_t*
     pos = item.z * (1u + n) >= 24u ? n_cap - 1u - atomicAdd(&lists[3], 1u) : atomicAdd(&lists[1], 1u);
   pos = __shfl_sync(0xffffffffu, pos, 0);
   if (lane == 0) sparse[pos].item = make_uint4(item.x, item.y, item.z, n);
-  if ((uint32_t)lane < n) {  // what the scan needs of each live pair, so it reads one record
-    const uint32_t q = pair_q[mine];
-    sparse[pos].pr[lane] = mine;
-    sparse[pos].q[lane] = q;
-    sparse[pos].tau[lane] = tau[q];
-    sparse[pos].rhoq[lane] = rhoq[mine];
-  }
+  if ((uint32_t)lane < n) sparse[pos].pr[lane] = mine;
 }
 
 constexpr int kSPThreads = 128;
@@ -207,43 +199,26 @@ __global__ void __launch_bounds__(kSPThreads, 6) k_scan_sparse(
   constexpr int kP = kSTDense - 1;  // at most this many live pairs per item
   __shared__ __align__(16) float sz[kP][RT];
   __shared__ float4 spc[kP];  // {unused, unused, tau_q, rho_q}
-  __shared__ uint32_t sqid[kP];
+  __shared__ uint32_t sqid[kP], spr[kP];
   __shared__ long long slo[kP], shi[kP];
   const int t = threadIdx.x, lane = t & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const uint32_t heavy = lists[3], total = lists[1] + heavy;  // heavy items (at the back) first
   const int nks = rp / 16;
   // items taken from a global counter (their costs vary; a static split left a
-  // tail); the next item's index is claimed, and its record and grain data
-  // fetched into registers, while the current one is scanned
+  // tail); the next item's index is claimed while the current one is scanned
   __shared__ uint32_t s_item;
-  uint4 n_item = make_uint4(0, 0, 0, 0);
-  uint32_t n_q = 0, n_ng = 0, n_gb0 = 0;
-  float n_tau = 0.f, n_rho = 0.f, n_sg = 0.f;
-  const SparseRec* n_rec = recs;
-  auto fetch = [&](uint32_t w) {
-    if (w >= total) return;
-    n_rec = recs + (w < heavy ? n_cap - 1u - w : w - heavy);
-    n_item = n_rec->item;
-    if (t < (int)n_item.w) {
-      n_q = n_rec->q[t];
-      n_tau = n_rec->tau[t];
-      n_rho = n_rec->rhoq[t];
-    }
-    n_ng = grain_rows[n_item.x];
-    n_gb0 = blk_off[n_item.x];
-    n_sg = scale[n_item.x];
-  };
   if (t == 0) s_item = atomicAdd(next_item, 1u);
   __syncthreads();
   uint32_t w = s_item;
-  fetch(w);
   while (w < total) {
-    const uint4 item = n_item;
-    const uint32_t b0 = item.y, nb = item.z;
+    const SparseRec& rec = recs[w < heavy ? n_cap - 1u - w : w - heavy];
+    const uint4 item = rec.item;
+    const uint32_t my_pr = t < kP ? rec.pr[t] : 0u;
+    const uint32_t g = item.x, b0 = item.y, nb = item.z;
     const int np = (int)item.w;
-    const uint32_t n_g = n_ng, gb0 = n_gb0;
-    const float s_g = n_sg;
+    const uint32_t n_g = grain_rows[g], gb0 = blk_off[g];
+    const float s_g = scale[g];
     uint4 cur[kL], nxt[kL];
     float rho_cur = 0.f, rho_nxt = 0.f, rmin_cur = 0.f, rmin_nxt = 0.f;
     auto load_block = [&](uint32_t i, uint4 (&codes)[kL], float& rh, float& rmin) {
@@ -258,22 +233,24 @@ __global__ void __launch_bounds__(kSPThreads, 6) k_scan_sparse(
     load_block(0, cur, rho_cur, rmin_cur);
     if (nb > 1) load_block(1, nxt, rho_nxt, rmin_nxt);
     __syncthreads();  // every thread is done with the previous item's pair data
+    if (t < np) spr[t] = my_pr;  // threads 0..kP-1 hold the item's pairs
+    __syncthreads();
     for (int e = t; e < np * RT; e += kSPThreads) {
       const int j = e / RT, a = e % RT;
-      sz[j][a] = a < r ? zq[(size_t)n_rec->pr[j] * r + a] : 0.f;
+      sz[j][a] = a < r ? zq[(size_t)spr[j] * r + a] : 0.f;
     }
     if (t < np) {
-      spc[t] = make_float4(0.f, 0.f, n_tau, n_rho);
-      sqid[t] = n_q;
+      const uint32_t q = pair_q[my_pr];
+      spc[t] = make_float4(0.f, 0.f, tau[q], rhoq[my_pr]);
+      sqid[t] = q;
       if (filter) {
-        slo[t] = (long long)filter[2 * (size_t)n_q];
-        shi[t] = (long long)filter[2 * (size_t)n_q + 1];
+        slo[t] = (long long)filter[2 * (size_t)q];
+        shi[t] = (long long)filter[2 * (size_t)q + 1];
       }
     }
     if (t == 0) s_item = atomicAdd(next_item, 1u);  // read after the barrier below
     __syncthreads();
     w = s_item;
-    fetch(w);  // in flight while this item's blocks are scanned
     for (uint32_t i = 0; i < nb; ++i) {
       const size_t b = b0 + i;
       const bool valid = (uint32_t)(b - gb0) * kBlockRows + t < n_g;
