@@ -153,6 +153,49 @@ def test_more_ties_than_tie_buffer(hntl, tmp_path):
         assert gpu["ids"][qi].tolist() == list(range(10))
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16-fp8"])
+def test_duplicated_rows_keep_ties_in_id_order(hntl, tmp_path, precision):
+    """Every row three times (ids i, i + n, i + 2 n have one D): the pool holds
+    all copies of every D below its last value, and of the last value's copies
+    the smallest ids; equal D are listed by ascending id. Against the oracle,
+    the pool sets agree at every gap between copy groups."""
+    n0 = 3000
+    X0, Q, idx0 = clustered_case(n0, 32, 6, 6, 8, 64, seed=131)
+    assign0 = np.zeros(n0, dtype=np.int64)
+    for g in range(len(idx0["grain_off"]) - 1):
+        assign0[idx0["ids"][idx0["grain_off"][g]:idx0["grain_off"][g + 1]]] = g
+    X = np.concatenate([X0, X0, X0])
+    idx = partition_index(X, np.tile(assign0, 3), 6, 8)
+    p = write(tmp_path, "dup" + precision, idx, X, precision=precision)
+    C = 100  # not a multiple of 3: the last copy group is cut
+    prec = hntl.PREC_BF16_FP8 if precision == "bf16-fp8" else hntl.PREC_FP32
+    _, gpu = run_gpu(hntl, p, Q, 10, C, 2, precision=prec)
+    cut_groups = 0
+    for qi in range(len(Q)):
+        ids = gpu["pool_ids"][qi].astype(np.int64)
+        d = gpu["pool_d"][qi]
+        assert (ids != 0xFFFFFFFF).all()
+        key = list(zip(d.tolist(), ids.tolist()))
+        assert key == sorted(key) and len(set(ids.tolist())) == C, f"query {qi}: not in (D, id) order"
+        present = set(ids.tolist())
+        last = d[-1]
+        for i, dv in zip(ids.tolist(), d.tolist()):
+            copies = [i % n0 + c * n0 for c in range(3)]
+            if dv < last:
+                assert all(c in present for c in copies), f"query {qi}: copies of {i} missing"
+        tail = sorted(i for i, dv in zip(ids.tolist(), d.tolist()) if dv == last)
+        base = {i % n0 for i in tail}
+        group = sorted(b + c * n0 for b in base for c in range(3))
+        if len(base) == 1:  # one copy group at the edge: its smallest ids are kept
+            assert tail == group[:len(tail)], f"query {qi}: edge copies {tail} of {group}"
+            cut_groups += len(tail) < 3
+    assert cut_groups > 0  # the cut group really occurred
+    if precision == "fp32":
+        ora = O.search(idx, X, Q, 10, C, 2)
+        st = compare_search(gpu, ora, 10, C, 2)
+        assert st["checked"] >= 0.9 * len(Q), st
+
+
 def test_host_form_matches_device_form(hntl, tmp_path):
     X, Q, idx = clustered_case(2000, 32, 4, 4, 8, 50, seed=99)
     p = write(tmp_path, "host", idx, X)
