@@ -384,6 +384,7 @@ struct ProbedRowsSrc {
 
 constexpr int kSelDigits = 4, kSelBits = 8;  // radix select on the D bit pattern, 8 bits at a time
 constexpr int kSelBinCap = 256;              // bin size below which two digits suffice
+constexpr int kSelRankMax = 256;             // pool size up to which the output is ordered by counting
 
 struct SelSmem {
   uint32_t hist[1 << kSelBits];
@@ -512,14 +513,29 @@ __device__ void select_topc(const Src& src, int C, SelSmem& S, uint32_t* __restr
   }
   }
   __syncthreads();
-  // output in (D, id) order: the keys are distinct (each id once), so a key's
-  // position is the number of smaller keys
-  for (uint32_t i = threadIdx.x; i < nout; i += blockDim.x) {
-    const unsigned long long me = S.keys[i];
-    uint32_t rank = 0;
-    for (uint32_t j = 0; j < nout; ++j) rank += S.keys[j] < me ? 1u : 0u;
-    out_id[rank] = (uint32_t)(me & 0xFFFFFFFFu);
-    out_d[rank] = __uint_as_float((uint32_t)(me >> 32));
+  // output in (D, id) order. Up to kSelRankMax keys: the keys are distinct
+  // (each id once), so a key's position is the number of smaller keys (no
+  // barriers); more: a bitonic sort (its cost grows as n log^2 n, the count's
+  // as n^2)
+  if (nout <= (uint32_t)kSelRankMax) {
+    for (uint32_t i = threadIdx.x; i < nout; i += blockDim.x) {
+      const unsigned long long me = S.keys[i];
+      uint32_t rank = 0;
+      for (uint32_t j = 0; j < nout; ++j) rank += S.keys[j] < me ? 1u : 0u;
+      out_id[rank] = (uint32_t)(me & 0xFFFFFFFFu);
+      out_d[rank] = __uint_as_float((uint32_t)(me >> 32));
+    }
+  } else {
+    const int n2 = pow2_at_least((int)nout);
+    for (int i = threadIdx.x; i < n2; i += blockDim.x)
+      if (i >= (int)nout) S.keys[i] = ~0ull;
+    __syncthreads();
+    bitonic_sort_u64(S.keys, n2);
+    for (uint32_t i = threadIdx.x; i < nout; i += blockDim.x) {
+      const unsigned long long kk = S.keys[i];
+      out_id[i] = (uint32_t)(kk & 0xFFFFFFFFu);
+      out_d[i] = __uint_as_float((uint32_t)(kk >> 32));
+    }
   }
   for (int i = (int)nout + threadIdx.x; i < C; i += blockDim.x) {
     out_id[i] = kInvalidId;
