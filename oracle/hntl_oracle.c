@@ -302,7 +302,8 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
                const uint32_t* ids, const float* Z, const float* rho, const float* X, const int64_t* attr,
                const float* Q, const float* Qp, int64_t nq, int64_t k, int64_t C, int64_t nprobe,
                const int64_t* ranges, int32_t* probe, double* probe_d, uint32_t* cand_id, double* cand_d,
-               int64_t* out_id, double* out_d) {
+               int64_t* out_id, double* out_d, int64_t mode, const int64_t* pos_of_id,
+               const int32_t* grain_of_pos) {
 #pragma omp parallel
   {
     pair_t* route = (pair_t*)malloc(sizeof(pair_t) * (size_t)G);
@@ -313,6 +314,7 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
     pool.cap = C + 1;
     pool.v = (pair_t*)malloc(sizeof(pair_t) * (size_t)(C + 1));
     pair_t* rr = (pair_t*)malloc(sizeof(pair_t) * (size_t)(C + 1));
+    double* xh = (double*)malloc(sizeof(double) * (size_t)d);
 #pragma omp for schedule(dynamic, 1)
     for (int64_t qi = 0; qi < nq; ++qi) {
       const float* q = Q + qi * d;
@@ -366,11 +368,30 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
         cand_d[qi * (C + 1) + j] = j < pool.n ? pool.v[j].dist : INFINITY;
       }
       cand_d[qi * (C + 1) + C] = C < pool.n ? pool.v[C].dist : INFINITY;
-      /* 5. exact rerank of the pool */
+      /* 5. rerank of the pool: Mode B, exact L2 to the raw row (sec. 2.1 step 4);
+       * Mode A, L2 to the row's reconstruction mu_g + W_g z_i from its grain's
+       * centre and basis and its stored coordinates, against the query as routed
+       * and projected (sec. 2.1 step 4, sec. 1) */
       int64_t m = pool.n < C ? pool.n : C;
       for (int64_t j = 0; j < m; ++j) {
         rr[j].key = pool.v[j].key;
-        rr[j].dist = sq_diff_f32(q, X + rr[j].key * d, d);
+        if (mode == 1) {
+          const int64_t i = pos_of_id[rr[j].key];
+          const int64_t g = grain_of_pos[i];
+          const float* mu = M + g * d;
+          const float* Ug = U + g * r * d;
+          for (int64_t t = 0; t < d; ++t) xh[t] = (double)mu[t];
+          for (int64_t a = 0; a < r; ++a)
+            for (int64_t t = 0; t < d; ++t) xh[t] += (double)Ug[a * d + t] * (double)Z[i * r + a];
+          double s = 0.0;
+          for (int64_t t = 0; t < d; ++t) {
+            const double df = (double)qp[t] - xh[t];
+            s += df * df;
+          }
+          rr[j].dist = s;
+        } else {
+          rr[j].dist = sq_diff_f32(q, X + rr[j].key * d, d);
+        }
       }
       qsort(rr, (size_t)m, sizeof(pair_t), pair_cmp);
       for (int64_t j = 0; j < k; ++j) {
@@ -385,6 +406,7 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
     free(zq);
     free(pool.v);
     free(rr);
+    free(xh);
   }
 }
 

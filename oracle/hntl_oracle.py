@@ -14,6 +14,8 @@ What it computes, in the paper's order (HNTL technical report):
   * the Mode B query path: routing (sec. 2.1 step 1, sec. 2.3), projection
     (Eq. 1-4), scan with the approximate distance of Eq. 6, the pool of the C
     best (Table 1, "Pool C"), exact L2 rerank to top k (sec. 2.1 step 4);
+  * Mode A: the same pool reranked by L2 to each row's reconstruction
+    mu_g + W_g z_i (sec. 2.1 step 4, sec. 1, the reconstruction of Eq. 3);
   * the brute-force exact kNN used as ground truth.
 The loops live in hntl_oracle.c; the covariance, the tangent coordinates of
 the database rows and the eigendecomposition are written as numpy matmuls and
@@ -72,7 +74,7 @@ def _c():
             lib.or_lloyd.argtypes = [P, I, I, I, P, I, P]
             lib.or_lloyd.restype = I
             lib.or_search.argtypes = [P, P, I, I, I, P, P, P, P, P, P, P, P, I, I, I, I, P,
-                                      P, P, P, P, P, P]
+                                      P, P, P, P, P, P, I, P, P]
             lib.or_threads.restype = ctypes.c_int
             lib.or_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -211,8 +213,15 @@ def build_index(X, G: int, r: int, u, train_idx=None, max_iter: int = 25, keep_f
 # ---------------------------------------------------------------------------
 
 
-def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=None, rho=None, precision="fp32"):
-    """Mode B search of every query (see hntl_oracle.c or_search).
+def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=None, rho=None, precision="fp32",
+           mode: str = "B"):
+    """Mode B (default) or Mode A search of every query (see hntl_oracle.c or_search).
+
+    mode="B": the pool is reranked by exact L2 to the raw rows (sec. 2.1 step 4).
+    mode="A": the pool is reranked by L2 to each row's reconstruction
+    mu_g + U_g^T z_i (its grain's centre and basis, its stored coordinates),
+    against the query as routed and projected; no raw row is read (sec. 2.1
+    step 4, sec. 1). Routing, projection, scan and pool are the same.
 
     precision="fp32": the plain method on the stored FP32 values.
     precision="bf16-fp8": the precision form, defined on rounded inputs: the
@@ -254,8 +263,16 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
     cand_d = np.zeros((nq, C + 1), dtype=np.float64)
     out_id = np.zeros((nq, k), dtype=np.int64)
     out_d = np.zeros((nq, k + 1), dtype=np.float64)
+    if mode not in ("A", "B"):
+        raise ValueError(mode)
+    pos_of_id = grain_of_pos = None
+    if mode == "A":  # the stored position of each id, and the grain of each position
+        pos_of_id = np.zeros(len(ids), dtype=np.int64)
+        pos_of_id[ids] = np.arange(len(ids), dtype=np.int64)
+        grain_of_pos = np.repeat(np.arange(G, dtype=np.int32), np.diff(off)).astype(np.int32)
     _c().or_search(_p(M), _p(U), G, d, r, _p(off), _p(ids), _p(Zs), _p(rhos), _p(X), _p(attr_a), _p(Q), _p(Qp), nq,
-                   k, C, nprobe, _p(rng), _p(probe), _p(probe_d), _p(cand_id), _p(cand_d), _p(out_id), _p(out_d))
+                   k, C, nprobe, _p(rng), _p(probe), _p(probe_d), _p(cand_id), _p(cand_d), _p(out_id), _p(out_d),
+                   1 if mode == "A" else 0, _p(pos_of_id), _p(grain_of_pos))
     return dict(probe=probe, probe_d=probe_d, cand_id=cand_id, cand_d=cand_d, out_id=out_id, out_d=out_d)
 
 

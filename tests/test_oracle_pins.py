@@ -236,6 +236,73 @@ def test_eq6_error_is_twice_residual_inner_product():
             assert abs(res["cand_d"][qi, j] - ex) <= bound
 
 
+# ---------------------------------------------------------------- Mode A
+
+
+def _pos_and_grain(idx, n):
+    pos = np.zeros(n, dtype=np.int64)
+    pos[idx["ids"]] = np.arange(len(idx["ids"]))
+    gof = np.searchsorted(idx["grain_off"], np.arange(len(idx["ids"])), side="right") - 1
+    return pos, gof
+
+
+def test_mode_a_is_pool_distance_minus_row_residual():
+    """With orthonormal basis rows, ||v' - U^T z_i||^2 = ||z_q - z_i||^2 + rho_q
+    (Pythagoras: the residual e_q is orthogonal to the basis), which is the
+    pool distance of Eq. 6 minus rho_i. The oracle's Mode A reconstructs
+    mu_g + U^T z_i in d dimensions; its distances must agree with the scan's,
+    and the pool is the one Mode B keeps."""
+    X, Q, _ = _clustered(1500, 24, 4, 20, 71)
+    G, r = 4, 6
+    idx = O.build_index(X, G, r, synth.uniforms(G, 3).numpy())
+    a = O.search(idx, X, Q, 10, 60, 2, mode="A")
+    b = O.search(idx, X, Q, 10, 60, 2, mode="B")
+    np.testing.assert_array_equal(a["cand_id"], b["cand_id"])
+    pos, _ = _pos_and_grain(idx, len(X))
+    for qi in range(len(Q)):
+        pool = {int(i): dv - float(idx["rho"][pos[int(i)]]) for i, dv in zip(a["cand_id"][qi], a["cand_d"][qi])}
+        want = sorted((dv, i) for i, dv in pool.items())[:10]
+        assert [i for _, i in want] == a["out_id"][qi].tolist()
+        for j in range(10):
+            assert abs(a["out_d"][qi, j] - want[j][0]) <= 1e-6 * (1.0 + want[j][0])
+
+
+def test_mode_a_full_basis_equals_brute_force():
+    """r = d: every row equals its reconstruction (zero residual), so Mode A with
+    every grain probed and the whole set pooled is exact kNN."""
+    X, Q, _ = _clustered(400, 16, 4, 25, 43)
+    G = 4
+    idx = O.build_index(X, G, 16, synth.uniforms(G, 4).numpy())
+    res = O.search(idx, X, Q, 10, 400, G, mode="A")
+    bf, bd, _ = O.brute_force(X, Q, 10)
+    np.testing.assert_array_equal(res["out_id"], bf)
+    np.testing.assert_allclose(res["out_d"][:, :10], bd, rtol=1e-6)
+
+
+def test_mode_a_precision_form_gram_expansion():
+    """Precision form: BF16 bases are not orthonormal, so Pythagoras no longer
+    applies; the reconstruction distance must still equal its expansion
+    ||v'||^2 - 2 z_i . (U_b v') + z_i^T (U_b U_b^T) z_i with v' = q_b - mu_b and
+    the decoded FP8 coordinates z_i."""
+    X, Q, _ = _clustered(1200, 32, 4, 12, 81)
+    G, r = 4, 8
+    idx = O.build_index(X, G, r, synth.uniforms(G, 5).numpy())
+    res = O.search(idx, X, Q, 10, 40, 2, mode="A", precision="bf16-fp8")
+    M = O.bf16_to_f32(O.bf16_round(idx["M"])).reshape(idx["M"].shape).astype(np.float64)
+    U = O.bf16_to_f32(O.bf16_round(idx["U"])).reshape(idx["U"].shape).astype(np.float64)
+    Zd = O.fp8_decoded(idx).astype(np.float64)
+    Qb = O.bf16_to_f32(O.bf16_round(Q)).reshape(Q.shape).astype(np.float64)
+    pos, gof = _pos_and_grain(idx, len(X))
+    for qi in range(len(Q)):
+        for j, i in enumerate(res["out_id"][qi]):
+            p = pos[int(i)]
+            g = gof[p]
+            v = Qb[qi] - M[g]
+            z = Zd[p]
+            want = v @ v - 2.0 * z @ (U[g] @ v) + z @ (U[g] @ U[g].T) @ z
+            assert abs(res["out_d"][qi, j] - want) <= 1e-9 * (1.0 + v @ v)
+
+
 def test_basis_sign_and_rotation_invariance():
     X, Q, _ = _clustered(300, 20, 2, 8, 61)
     G, r = 2, 6
