@@ -395,8 +395,8 @@ class MultiStream:
     workspace and outputs, so one batch's small kernels and tails overlap the
     next batch's work (the server's two lanes do the same)."""
 
-    def __init__(self, gi, B, k, C, nprobe, S, dev):
-        self.gi, self.k, self.C, self.nprobe = gi, k, C, nprobe
+    def __init__(self, gi, B, k, C, nprobe, S, dev, mode="B"):
+        self.gi, self.k, self.C, self.nprobe, self.mode = gi, k, C, nprobe, mode
         self.streams = [torch.cuda.Stream(device=dev) for _ in range(S)]
         nb = gi.workspace_bytes(B, k, C, nprobe)
         self.ws = [torch.empty(nb, dtype=torch.uint8, device=dev) for _ in range(S)]
@@ -417,7 +417,7 @@ class MultiStream:
             if events is not None:
                 events[i][0].record(self.streams[j])
             self.gi.search(batches[i % len(batches)], self.k, self.C, self.nprobe, out=self.outs[j],
-                           ws=self.ws[j], stream=self.streams[j])
+                           ws=self.ws[j], stream=self.streams[j], mode=self.mode)
             if events is not None:
                 events[i][1].record(self.streams[j])
         for s_ in self.streams:
@@ -464,6 +464,33 @@ def run_fp32_compare(a, hntl, X, Q, w, sd, B, n_recall, truth, line):
             "precision_form_gain": round(line["value"] / qps, 3),
             "streams": a.streams,
             "note": "same rows, k-means draws, batch, nprobe, C, k and streams; FP32 rows, coordinates and bases"}
+
+
+def run_mode_a(a, hntl, gi, Q, w, B, n_recall, truth):
+    """Mode A on the same index, batches, parameters and streams: the pool
+    reranked by L2 to each row's reconstruction (no raw row read)."""
+    k, C, nprobe = w["k"], w["C"], w["nprobe"]
+    nb = w["nq"] // B
+    batches = [Q[i * B:(i + 1) * B].contiguous() for i in range(nb)]
+    found = [gi.search(batches[i], k, C, nprobe, mode="A")[0] for i in range(max(1, (n_recall + B - 1) // B))]
+    rec = recall_at_k(torch.cat(found)[:n_recall], truth) if n_recall else None
+    ms_ = MultiStream(gi, B, k, C, nprobe, a.streams, Q.device, mode="A")
+    ms_.run(batches, a.warmup)
+    torch.cuda.synchronize()
+    hntl.profile_read()
+    hntl.profile_enable(True)  # stage times: one stream
+    for i in range(a.steps):
+        gi.search(batches[i % nb], k, C, nprobe, out=ms_.outs[0], ws=ms_.ws[0], mode="A")
+    torch.cuda.synchronize()
+    hntl.profile_enable(False)
+    sm, calls = hntl.profile_read()
+    e0, e1 = ms_.run(batches, a.steps)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    return {"value": round(B / (ms / 1e3), 1), "unit": "queries/s", "ms_per_step": round(ms, 4),
+            "recall_at_10": None if rec is None else round(rec, 4), "streams": a.streams,
+            "stages_ms": {k_: round(v_ / max(calls, 1), 4) for k_, v_ in sm.items()},
+            "note": "same index, batches, nprobe, C, k and streams; rerank by L2 to mu_g + W_g z_i"}
 
 
 def run_ours(a, world, rank, local):
@@ -618,6 +645,9 @@ def run_ours(a, world, rank, local):
     }
     if serve:
         line["serving"] = run_serving(a, hntl, gi, X, Q, attr, w, sd)
+    if a.mode_a and not a.profile_mode:
+        line["mode_a_same_data"] = run_mode_a(a, hntl, gi, Q, w, B, n_recall, truth)
+        print(f"mode A: {line['mode_a_same_data']}", file=sys.stderr)
     if prec == "bf16-fp8" and a.fp32_compare and X is not None:
         line["plain_fp32_same_data"] = run_fp32_compare(a, hntl, X, Q, w, sd, B, n_recall, truth, line)
     if rank == 0 and world == 1 and not a.no_cpu_baseline and not a.profile_mode:
@@ -813,6 +843,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-recall", type=int, default=1536, help="served requests checked against brute force")
     ap.add_argument("--serve-p99-ms", type=float, default=50.0)
+    ap.add_argument("--no-mode-a", dest="mode_a", action="store_false",
+                    help="skip timing Mode A (rerank on reconstructions) on the same index")
     ap.add_argument("--no-fp32-compare", dest="fp32_compare", action="store_false",
                     help="skip timing the plain FP32 method on the same data (precision workloads)")
     ap.add_argument("--router-train", type=int, default=200_000)

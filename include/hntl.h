@@ -137,6 +137,21 @@ int hntl_search(const hntl_index* idx, const float* d_queries, uint32_t nq, uint
                 const int64_t* d_filter, void* d_ws, size_t ws_bytes, int64_t* d_out_ids, float* d_out_dist,
                 uint32_t* d_cand_ids, float* d_cand_dist, int32_t* d_probe, void* stream);
 
+/* Batched Mode A search (sec. 2.1 step 4 "Mode A"; sec. 1, the dual-mode
+ * planner): steps 1-4 as hntl_search, then the pool is reranked by the
+ * squared distance from the query, as routed and projected, to each member's
+ * reconstruction mu_g + W_g z_i (the subspace reconstruction of Eq. 3) from
+ * its grain's centre and basis and its stored coordinates; no raw row is
+ * read. Computed as ||v'||^2 - 2 z_i . z_q + z_i^T (U_g U_g^T) z_i with
+ * v' = q - mu_g (q, mu_g, U_g BF16 and z_i the decoded FP8 coordinates in the
+ * precision form), which equals the reconstruction distance for any basis.
+ * Arguments, layout, workspace (hntl_search_workspace_bytes), ownership and
+ * errors as hntl_search; d_out_dist holds the reconstruction distances, and
+ * there is no probe output. */
+int hntl_search_mode_a(const hntl_index* idx, const float* d_queries, uint32_t nq, uint32_t k, uint32_t C,
+                       uint32_t nprobe, const int64_t* d_filter, void* d_ws, size_t ws_bytes, int64_t* d_out_ids,
+                       float* d_out_dist, uint32_t* d_cand_ids, float* d_cand_dist, void* stream);
+
 /* Device workspace hntl_search_host needs: the search workspace followed by
  * device staging for the queries, the filters (if with_filter) and results. */
 size_t hntl_search_host_workspace_bytes(const hntl_index* idx, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe,

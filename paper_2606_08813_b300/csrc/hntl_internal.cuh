@@ -67,7 +67,9 @@ struct Index {
   uint16_t* Mh = nullptr;        // [G][d] BF16 centres (precision form)
   int num_sms = 148;             // streaming multiprocessors of the index's device
   uint16_t* Uh = nullptr;        // [G][r][d] BF16 bases (precision form)
-  float* gram = nullptr;         // [G][r][r] U_g U_g^T of the BF16 bases (precision form)
+  float* gram = nullptr;         // [G][r][r] U_g U_g^T (of the BF16 bases in the precision form)
+  uint32_t* pos_of_id = nullptr; // [n] stored position (block * 128 + row) of each id (Mode A)
+  float* hrow = nullptr;         // [n_blocks][128] z_i^T G_g z_i of the decoded row (Mode A)
   int* d_err = nullptr;          // device error word (bounded waits that gave up)
   bool tc_route = false;         // tensor-core routing available (TMA map built)
   CUtensorMap mapM;              // TMA map of the centres (FP32 or BF16), 256-row boxes

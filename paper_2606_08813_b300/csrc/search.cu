@@ -32,6 +32,7 @@
 #include "project_tc.cuh"
 #include "scan_tc.cuh"
 #include "rerank.cuh"
+#include "recon.cuh"
 
 namespace hntl {
 
@@ -236,7 +237,7 @@ struct Ws {
   uint32_t* pair_q;
   uint32_t* pair_p;
   uint32_t* pair_of;
-  float* pair_vn;  // ||q - mu_g||^2 of each pair (precision form)
+  float* pair_vn;  // ||q - mu_g||^2 of each pair (exact routing distance)
   uint4* slots;    // tensor-core projection slots of <= 32 pairs (precision form)
   uint32_t* scan_off;  // per-grain offsets of the tensor-core scan's work items (precision form)
   uint4* scan_items;   // {grain, first block, blocks} of each probed grain (precision form)
@@ -273,7 +274,7 @@ Ws carve(const Index& I, uint32_t nq, uint32_t C, uint32_t nprobe, void* base) {
   w.pair_p = c.take<uint32_t>(P);
   w.pair_of = c.take<uint32_t>(P);
   const bool tcp = I.precision == HNTL_PREC_BF16_FP8;
-  w.pair_vn = tcp ? c.take<float>(P) : nullptr;
+  w.pair_vn = c.take<float>(P);  // the projection's ||v'||^2 (precision form) and Mode A's
   w.slots = tcp ? c.take<uint4>(P / kPSlot + I.G) : nullptr;
   w.scan_off = tcp ? c.take<uint32_t>(I.G + 1) : nullptr;
   w.scan_items = tcp ? c.take<uint4>(I.G + I.n_blocks / kSTBlocks + 1) : nullptr;
@@ -479,7 +480,7 @@ void profile_end(const StageEvents& ev) {
 int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe,
            const int64_t* filter, void* ws, size_t ws_bytes, int64_t* out_ids, float* out_d, uint32_t* cand_ids,
            float* cand_d, int32_t* probe_out, cudaStream_t st, const int32_t* probe_in = nullptr,
-           const uint32_t* qk = nullptr, const uint32_t* qC = nullptr) {
+           const uint32_t* qk = nullptr, const uint32_t* qC = nullptr, bool mode_a = false) {
   int rc = check_params(I, nq, k, C, nprobe);
   if (rc) return rc;
   if (filter && !I.has_attr) return fail(HNTL_EINVAL, "filter given but the index has no attribute column");
@@ -548,7 +549,23 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
     else launch_scan_select_p<64>(I, w, (int)nq, (int)nprobe, (int)C, filter, st, mk, qC);
   }
   mark(6);
-  {
+  if (mode_a) {
+    const Coords cz{I.Zb, I.Z8b, I.scale};
+    auto recon = [&](auto kern) {
+      kern<<<nq, 256, 0, st>>>((int)nprobe, (int)C, (int)k, w.cand_id, I.pos_of_id, I.blk_grain, cz, (int)I.r,
+                               (int)I.rp, I.hrow, w.probe, w.pair_of, w.zq, w.pair_vn, out_ids, out_d, qk, qC);
+    };
+    if (I.precision == HNTL_PREC_BF16_FP8) {
+      if (I.r <= 16) recon(k_rerank_recon<16, true>);
+      else if (I.r <= 32) recon(k_rerank_recon<32, true>);
+      else recon(k_rerank_recon<64, true>);
+    } else {
+      if (I.r <= 8) recon(k_rerank_recon<8, false>);
+      else if (I.r <= 16) recon(k_rerank_recon<16, false>);
+      else if (I.r <= 32) recon(k_rerank_recon<32, false>);
+      else recon(k_rerank_recon<64, false>);
+    }
+  } else {
     size_t smem = (size_t)I.d * sizeof(float);
     if (smem > 40 * 1024) {
       HNTL_CUDA_TRY(cudaFuncSetAttribute(k_rerank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -624,14 +641,17 @@ int finalize_index(Index& I) {
   const bool bf16 = I.precision == HNTL_PREC_BF16_FP8;
   I.d_err = static_cast<int*>(alloc(sizeof(int)));
   I.mnorm = static_cast<float*>(alloc(sizeof(float) * I.G));
+  I.gram = static_cast<float*>(alloc(sizeof(float) * I.G * I.r * I.r));
+  I.pos_of_id = static_cast<uint32_t*>(alloc(sizeof(uint32_t) * std::max<uint64_t>(I.n, 1)));
+  I.hrow = static_cast<float*>(alloc(sizeof(float) * I.n_blocks * kBlockRows));
   if (bf16) {
     I.Mh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.d));
     I.Uh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.r * I.d));
-    I.gram = static_cast<float*>(alloc(sizeof(float) * I.G * I.r * I.r));
     I.crow = static_cast<float*>(alloc(sizeof(float) * I.n_blocks * kBlockRows));
     I.grain_rho_min = static_cast<float*>(alloc(sizeof(float) * I.G));
   }
-  if (!I.d_err || !I.mnorm || (bf16 && (!I.Mh || !I.Uh || !I.gram || !I.crow || !I.grain_rho_min)))
+  if (!I.d_err || !I.mnorm || !I.gram || !I.pos_of_id || !I.hrow ||
+      (bf16 && (!I.Mh || !I.Uh || !I.crow || !I.grain_rho_min)))
     return fail(HNTL_ENOMEM, "index: derived arrays");
   HNTL_CUDA_TRY(cudaMemset(I.d_err, 0, sizeof(int)));
   if (bf16) k_row_norms<true><<<(I.G * 32 + 255) / 256, 256>>>(I.M, (int)I.G, (int)I.d, I.mnorm);
@@ -640,13 +660,33 @@ int finalize_index(Index& I) {
     const size_t n = (size_t)I.G * I.d, nu = (size_t)I.G * I.r * I.d;
     k_to_bf16_rows<<<(unsigned)((n + 255) / 256), 256>>>(I.M, n, I.Mh);
     k_to_bf16_rows<<<(unsigned)((nu + 255) / 256), 256>>>(I.U, nu, I.Uh);
-    k_gram<<<I.G, 256>>>(I.Uh, (int)I.d, (int)I.r, I.gram);
+    k_gram<<<I.G, 256>>>(I.Uh, (int)I.d, (int)I.r, I.gram);  // of the BF16 bases the precision form uses
     k_grain_rho_min<<<(I.G * 32 + 255) / 256, 256>>>(I.blk_rho_min, I.blk_off, (int)I.G, I.grain_rho_min);
     const Coords cz{I.Zb, I.Z8b, I.scale};
     if (I.n_blocks) {
       if (I.r <= 16) k_row_c<16><<<(unsigned)I.n_blocks, kBlockRows>>>(cz, I.rho, I.blk_grain, (int)I.rp, I.crow);
       else if (I.r <= 32) k_row_c<32><<<(unsigned)I.n_blocks, kBlockRows>>>(cz, I.rho, I.blk_grain, (int)I.rp, I.crow);
       else k_row_c<64><<<(unsigned)I.n_blocks, kBlockRows>>>(cz, I.rho, I.blk_grain, (int)I.rp, I.crow);
+    }
+  }
+  // Mode A: every id's stored position and h_i = z_i^T G_g z_i of every row
+  if (!bf16) k_gram_f32<<<I.G, 256>>>(I.U, (int)I.d, (int)I.r, I.gram);
+  HNTL_CUDA_TRY(cudaMemset(I.pos_of_id, 0, sizeof(uint32_t) * std::max<uint64_t>(I.n, 1)));
+  if (I.n_blocks) {
+    const size_t npos = (size_t)I.n_blocks * kBlockRows;
+    k_pos_of_id<<<(unsigned)((npos + 255) / 256), 256>>>(I.ids, npos, I.pos_of_id);
+    const Coords cz{I.Zb, I.Z8b, I.scale};
+    const unsigned nb = (unsigned)I.n_blocks;
+    const int r = (int)I.r, rp = (int)I.rp;
+    if (bf16) {
+      if (I.r <= 16) k_row_h<16, true><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+      else if (I.r <= 32) k_row_h<32, true><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+      else k_row_h<64, true><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+    } else {
+      if (I.r <= 8) k_row_h<8, false><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+      else if (I.r <= 16) k_row_h<16, false><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+      else if (I.r <= 32) k_row_h<32, false><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+      else k_row_h<64, false><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
     }
   }
   HNTL_CUDA_TRY(cudaDeviceGetAttribute(&I.num_sms, cudaDevAttrMultiProcessorCount, I.device));
@@ -721,6 +761,16 @@ int hntl_search(const hntl_index* idx, const float* d_queries, uint32_t nq, uint
   if (!idx) return hntl::fail(HNTL_EINVAL, "null index");
   return hntl::search(idx->I, d_queries, nq, k, C, nprobe, d_filter, d_ws, ws_bytes, d_out_ids, d_out_dist,
                       d_cand_ids, d_cand_dist, d_probe, static_cast<cudaStream_t>(stream));
+}
+
+int hntl_search_mode_a(const hntl_index* idx, const float* d_queries, uint32_t nq, uint32_t k, uint32_t C,
+                       uint32_t nprobe, const int64_t* d_filter, void* d_ws, size_t ws_bytes, int64_t* d_out_ids,
+                       float* d_out_dist, uint32_t* d_cand_ids, float* d_cand_dist, void* stream) {
+  hntl::clear_error();
+  if (!idx) return hntl::fail(HNTL_EINVAL, "null index");
+  return hntl::search(idx->I, d_queries, nq, k, C, nprobe, d_filter, d_ws, ws_bytes, d_out_ids, d_out_dist,
+                      d_cand_ids, d_cand_dist, nullptr, static_cast<cudaStream_t>(stream), nullptr, nullptr,
+                      nullptr, true);
 }
 
 int hntl_search_probes(const hntl_index* idx, const float* d_queries, uint32_t nq, uint32_t k, uint32_t C,

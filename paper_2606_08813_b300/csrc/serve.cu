@@ -36,7 +36,7 @@ namespace hntl {
 int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe,
            const int64_t* filter, void* ws, size_t ws_bytes, int64_t* out_ids, float* out_d, uint32_t* cand_ids,
            float* cand_d, int32_t* probe_out, cudaStream_t st, const int32_t* probe_in, const uint32_t* qk,
-           const uint32_t* qC);
+           const uint32_t* qC, bool mode_a);
 
 namespace {
 
@@ -346,7 +346,7 @@ extern "C" int hntl_server_create(const hntl_index* idx, size_t mem_budget, uint
       hntl::k_gather_batch<<<rows, 128, 0, L.st>>>(L.d_slots, (int)rows, (int)I.d, S.d_slot_q, S.d_slot_k,
                                                    S.d_slot_C, S.d_slot_range, L.d_Q, L.d_k, L.d_C, L.d_F);
       int r = hntl::search(I, L.d_Q, rows, k_max, C_max, nprobe, L.d_F, L.ws, L.ws_bytes, L.d_ids, L.d_dist,
-                           nullptr, nullptr, nullptr, L.st, nullptr, L.d_k, L.d_C);
+                           nullptr, nullptr, nullptr, L.st, nullptr, L.d_k, L.d_C, false);
       if (r) return r;
       if (cudaMemcpyAsync(L.h_ids, L.d_ids, (size_t)rows * k_max * 8, cudaMemcpyDeviceToHost, L.st) ||
           cudaMemcpyAsync(L.h_dist, L.d_dist, (size_t)rows * k_max * 4, cudaMemcpyDeviceToHost, L.st))

@@ -225,8 +225,11 @@ class Index:
         return ws
 
     def search(self, Q: torch.Tensor, k: int, C: int, nprobe: int, filters: torch.Tensor | None = None,
-               return_pool: bool = False, return_probe: bool = False, stream=None, out=None, ws=None):
-        """Batched Mode B search of CUDA queries Q [nq, d] f32.
+               return_pool: bool = False, return_probe: bool = False, stream=None, out=None, ws=None,
+               mode: str = "B"):
+        """Batched search of CUDA queries Q [nq, d] f32: mode "B" reranks the
+        pool by exact L2 to the raw rows (hntl_search), mode "A" by L2 to the
+        rows' reconstructions (hntl_search_mode_a; no probe output).
 
         Returns (ids i64 [nq, k], dist f32 [nq, k]); with return_pool also the
         pool (ids as int32 [nq, max(C, k)] holding the uint32 ids, so the
@@ -252,8 +255,16 @@ class Index:
         probe = torch.empty(nq, nprobe, dtype=torch.int32, device=dev) if return_probe else None
         nb = self.workspace_bytes(max(nq, 1), k, C, nprobe)
         ws = self._caller_ws(ws, nb)
-        _check(lib.hntl_search(self._h, _ptr(Q), nq, k, C, nprobe, _ptr(filters), _ptr(ws), ws.numel(), _ptr(ids),
-                               _ptr(dist), _ptr(pool_ids), _ptr(pool_d), _ptr(probe), _stream(stream)))
+        if mode == "A":
+            if return_probe:
+                raise ValueError("mode A has no probe output")
+            _check(lib.hntl_search_mode_a(self._h, _ptr(Q), nq, k, C, nprobe, _ptr(filters), _ptr(ws), ws.numel(),
+                                          _ptr(ids), _ptr(dist), _ptr(pool_ids), _ptr(pool_d), _stream(stream)))
+        elif mode == "B":
+            _check(lib.hntl_search(self._h, _ptr(Q), nq, k, C, nprobe, _ptr(filters), _ptr(ws), ws.numel(),
+                                   _ptr(ids), _ptr(dist), _ptr(pool_ids), _ptr(pool_d), _ptr(probe), _stream(stream)))
+        else:
+            raise ValueError("mode must be 'A' or 'B'")
         res = [ids, dist]
         if return_pool:
             res += [pool_ids, pool_d]
@@ -304,6 +315,7 @@ class Index:
 
 
 lib.hntl_search_probes.argtypes = [_P, _P, _U32, _U32, _U32, _U32, _P, _P, _P, _SZ, _P, _P, _P, _P, _P]
+lib.hntl_search_mode_a.argtypes = [_P, _P, _U32, _U32, _U32, _U32, _P, _P, _SZ, _P, _P, _P, _P, _P]
 lib.hntl_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
 lib.hntl_router_create.argtypes = [ctypes.c_int, _U32, _U32, _U32, _U32, _U32, _P, _P, _P, _P, _P, _P,
                                    ctypes.POINTER(_P)]

@@ -1,0 +1,82 @@
+"""Mode A (the pool reranked by L2 to each row's reconstruction mu_g + W_g z_i,
+no raw row read) on the GPU against the oracle's Mode A, element by element
+under the same gap rule and tolerances as Mode B, in both forms; and the pool
+Mode A reranks is bit for bit the one Mode B reranks."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hntl_oracle as O
+from paper_2606_08813_b300 import synth
+
+from cases import clustered_case, partition_index, write
+from parity import compare_search
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hntl():
+    from paper_2606_08813_b300 import build_lib
+
+    build_lib.build()
+    from paper_2606_08813_b300 import hntl as h
+
+    return h
+
+
+def run(h, path, Q, k, C, nprobe, precision, filters=None):
+    gi = h.Index.load(path, 0, h.PREC_BF16_FP8 if precision == "bf16-fp8" else h.PREC_FP32)
+    F = None if filters is None else torch.from_numpy(filters).cuda()
+    Qd = torch.from_numpy(np.ascontiguousarray(Q)).cuda()
+    ids, dist, pid, pd = gi.search(Qd, k, C, nprobe, filters=F, return_pool=True, mode="A")
+    torch.cuda.synchronize()
+    return gi, dict(ids=ids.cpu().numpy(), dist=dist.cpu().numpy(), pool_ids=pid.cpu().numpy().view(np.uint32),
+                    pool_d=pd.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16-fp8"])
+def test_mode_a_clustered(hntl, tmp_path, precision):
+    X, Q, idx = clustered_case(8000, 64, 8, 8, 16, 300, seed=211, sizes="zipf")
+    p = write(tmp_path, "ma" + precision, idx, X, precision=precision)
+    ora = O.search(idx, X, Q, 10, 50, 3, mode="A", precision=precision)
+    gi, gpu = run(hntl, p, Q, 10, 50, 3, precision)
+    st = compare_search(gpu, ora, 10, 50, 3)
+    assert st["checked"] >= 0.9 * len(Q), st
+    # the pool is Mode B's, bit for bit
+    Qd = torch.from_numpy(Q).cuda()
+    _, _, pid_b, pd_b = gi.search(Qd, 10, 50, 3, return_pool=True)
+    np.testing.assert_array_equal(pid_b.cpu().numpy().view(np.uint32), gpu["pool_ids"])
+    np.testing.assert_array_equal(pd_b.cpu().numpy(), gpu["pool_d"])
+    assert hntl.device_status(gi) == 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16-fp8"])
+@pytest.mark.parametrize("d,r", [(24, 5), (16, 16), (64, 8)])
+def test_mode_a_edge_shapes(hntl, tmp_path, precision, d, r):
+    """Grains of 0, 1, 127, 128, 129 and 300 rows (empty, single row, a ragged
+    last block, an exact block); a full basis (r = d); short results."""
+    sizes = [0, 1, 127, 128, 129, 300]
+    rng = np.random.default_rng(d * 7 + r)
+    centres = rng.standard_normal((len(sizes), d)) * 3
+    assign = np.repeat(np.arange(len(sizes)), sizes)
+    X = (centres[assign] + rng.standard_normal((len(assign), d)) * 0.7).astype(np.float32)
+    idx = partition_index(X, assign, len(sizes), r)
+    Q = (centres[rng.integers(0, len(sizes), 30)] + rng.standard_normal((30, d)) * 0.7).astype(np.float32)
+    p = write(tmp_path, f"mae{precision}{d}_{r}", idx, X, precision=precision)
+    for k, C, nprobe in [(10, 20, 2), (5, 200, 3), (10, 685, 6)]:
+        ora = O.search(idx, X, Q, k, C, nprobe, mode="A", precision=precision)
+        _, gpu = run(hntl, p, Q, k, C, nprobe, precision)
+        st = compare_search(gpu, ora, k, C, nprobe)
+        assert st["checked"] >= len(Q) // 2, (k, C, nprobe, st)
+
+
+def test_mode_a_filters(hntl, tmp_path):
+    X, Q, idx = clustered_case(3000, 32, 8, 8, 6, 60, seed=187)
+    attr = synth.attributes(len(X), 7, span=1 << 40).numpy()
+    ranges = synth.range_filters(len(Q), 8, span=1 << 40, selectivity=0.2, frac_filtered=0.5).numpy()
+    p = write(tmp_path, "mafilt", idx, X, attr=attr, precision="bf16-fp8")
+    ora = O.search(idx, X, Q, 10, 50, 3, attr=attr, ranges=ranges, mode="A", precision="bf16-fp8")
+    _, gpu = run(hntl, p, Q, 10, 50, 3, "bf16-fp8", filters=ranges)
+    st = compare_search(gpu, ora, 10, 50, 3)
+    assert st["checked"] >= 0.9 * len(Q), st
