@@ -1,7 +1,8 @@
 """Mode A (the pool reranked by L2 to each row's reconstruction mu_g + W_g z_i,
-no raw row read) on the GPU against the oracle's Mode A, element by element
-under the same gap rule and tolerances as Mode B, in both forms; and the pool
-Mode A reranks is bit for bit the one Mode B reranks."""
+no raw row read) on the GPU against the oracle's Mode A, element by element,
+in both forms (routing and pool under the Mode B rules; the reranked
+distances under the tolerance derived below); and the pool Mode A reranks is
+bit for bit the one Mode B reranks."""
 import numpy as np
 import pytest
 import torch
@@ -10,9 +11,52 @@ from oracle import hntl_oracle as O
 from paper_2606_08813_b300 import synth
 
 from cases import clustered_case, partition_index, write
-from parity import compare_search
+from parity import GAP, _rel_gap, check_ranked
 
 pytestmark = pytest.mark.gpu
+
+# The GPU forms a Mode A distance as ||v'||^2 - 2 z_i . z_q + z_i^T G z_i in
+# FP32: every term is of the size of ||v'||^2 (the member's routing distance),
+# the result can be far smaller, and FP32 rounding of about
+# (d / 32 + r + 10) 2^-24 of those terms (under 1e-5 of them for d <= 768,
+# r <= 32) is what separates it from the oracle's FP64 reconstruction. So a
+# distance is checked to 1e-5 (d_A + 2 ||v'||^2), and sets of ids are
+# compared wherever the oracle's gap exceeds twice that.
+ATOL_SCALE = 1e-5
+
+
+def compare_mode_a(gpu, ora, k, C, nprobe):
+    nq = ora["out_id"].shape[0]
+    Ce = max(C, k)
+    stats = dict(route_excluded=0, topk_excluded=0, checked=0)
+    for qi in range(nq):
+        pd = ora["probe_d"][qi]
+        if _rel_gap(pd[nprobe - 1], pd[nprobe]) <= GAP and np.isfinite(pd[nprobe]):
+            stats["route_excluded"] += 1
+            continue
+        check_ranked(gpu["pool_ids"][qi].astype(np.uint32), gpu["pool_d"][qi], ora["cand_id"][qi], ora["cand_d"][qi],
+                     "pool", qi, invalid=0xFFFFFFFF)
+        cd = ora["cand_d"][qi]
+        if _rel_gap(cd[Ce - 1], cd[Ce]) <= GAP and np.isfinite(cd[Ce]):
+            stats["topk_excluded"] += 1
+            continue
+        vn = float(np.max(pd[:nprobe]))  # the largest ||v'||^2 of the query's probed grains
+        g_ids, o_ids = [int(x) for x in gpu["ids"][qi]], [int(x) for x in ora["out_id"][qi]]
+        od = ora["out_d"][qi]
+        n_valid = sum(1 for x in o_ids if x != -1)
+        assert n_valid == sum(1 for x in g_ids if x != -1), f"q{qi}: valid entries"
+        assert np.all(np.diff(gpu["dist"][qi][:n_valid].astype(np.float64)) >= 0), f"q{qi}: not sorted"
+        for m in range(1, n_valid + 1):
+            tol = ATOL_SCALE * (od[m - 1] + 2 * vn)
+            if not np.isfinite(od[m]) or od[m] - od[m - 1] > 2 * tol:
+                assert set(g_ids[:m]) == set(o_ids[:m]), f"q{qi}: first {m} ids differ"
+        ref = {i: od[j] for j, i in enumerate(o_ids) if i != -1}
+        for j, i in enumerate(g_ids):
+            if i in ref:
+                d = float(gpu["dist"][qi][j])
+                assert abs(d - ref[i]) <= ATOL_SCALE * (ref[i] + 2 * vn), f"q{qi} id {i}: {d} vs {ref[i]}"
+        stats["checked"] += 1
+    return stats
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +85,7 @@ def test_mode_a_clustered(hntl, tmp_path, precision):
     p = write(tmp_path, "ma" + precision, idx, X, precision=precision)
     ora = O.search(idx, X, Q, 10, 50, 3, mode="A", precision=precision)
     gi, gpu = run(hntl, p, Q, 10, 50, 3, precision)
-    st = compare_search(gpu, ora, 10, 50, 3)
+    st = compare_mode_a(gpu, ora, 10, 50, 3)
     assert st["checked"] >= 0.9 * len(Q), st
     # the pool is Mode B's, bit for bit
     Qd = torch.from_numpy(Q).cuda()
@@ -67,7 +111,7 @@ def test_mode_a_edge_shapes(hntl, tmp_path, precision, d, r):
     for k, C, nprobe in [(10, 20, 2), (5, 200, 3), (10, 685, 6)]:
         ora = O.search(idx, X, Q, k, C, nprobe, mode="A", precision=precision)
         _, gpu = run(hntl, p, Q, k, C, nprobe, precision)
-        st = compare_search(gpu, ora, k, C, nprobe)
+        st = compare_mode_a(gpu, ora, k, C, nprobe)
         assert st["checked"] >= len(Q) // 2, (k, C, nprobe, st)
 
 
@@ -78,5 +122,5 @@ def test_mode_a_filters(hntl, tmp_path):
     p = write(tmp_path, "mafilt", idx, X, attr=attr, precision="bf16-fp8")
     ora = O.search(idx, X, Q, 10, 50, 3, attr=attr, ranges=ranges, mode="A", precision="bf16-fp8")
     _, gpu = run(hntl, p, Q, 10, 50, 3, "bf16-fp8", filters=ranges)
-    st = compare_search(gpu, ora, 10, 50, 3)
+    st = compare_mode_a(gpu, ora, 10, 50, 3)
     assert st["checked"] >= 0.9 * len(Q), st
