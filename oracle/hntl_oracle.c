@@ -303,7 +303,7 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
                const float* Q, const float* Qp, int64_t nq, int64_t k, int64_t C, int64_t nprobe,
                const int64_t* ranges, int32_t* probe, double* probe_d, uint32_t* cand_id, double* cand_d,
                int64_t* out_id, double* out_d, int64_t mode, const int64_t* pos_of_id,
-               const int32_t* grain_of_pos) {
+               const int32_t* grain_of_pos, const double* qdelta, const double* qdres) {
 #pragma omp parallel
   {
     pair_t* route = (pair_t*)malloc(sizeof(pair_t) * (size_t)G);
@@ -347,6 +347,25 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
           for (int64_t t = 0; t < d; ++t) e[t] -= zq[j] * (double)Ug[j * d + t];
         double rho_q = 0.0;
         for (int64_t t = 0; t < d; ++t) rho_q += e[t] * e[t];
+        if (qdelta) {
+          /* 16-bit form (Eq. 5): the query's coordinates and residual norm are
+           * quantised with the grain's steps; a coordinate beyond the signed
+           * 16-bit range saturates, and a grain where more than a quarter of
+           * them saturate is left out (Quantization Envelope Filter, sec. 2.3) */
+          int64_t sat = 0;
+          for (int64_t j = 0; j < r; ++j) {
+            double t = rint(zq[j] / qdelta[g]);
+            if (fabs(t) > 32767.0) {
+              ++sat;
+              t = t > 0 ? 32767.0 : -32767.0;
+            }
+            zq[j] = t * qdelta[g];
+          }
+          if (4 * sat > r) continue;
+          double tr = rint(rho_q / qdres[g]);
+          if (tr > 65535.0) tr = 65535.0;
+          rho_q = tr * qdres[g];
+        }
         for (int64_t i = grain_off[g]; i < grain_off[g + 1]; ++i) {
           uint32_t id = ids[i];
           if (ranges) {

@@ -74,7 +74,7 @@ def _c():
             lib.or_lloyd.argtypes = [P, I, I, I, P, I, P]
             lib.or_lloyd.restype = I
             lib.or_search.argtypes = [P, P, I, I, I, P, P, P, P, P, P, P, P, I, I, I, I, P,
-                                      P, P, P, P, P, P, I, P, P]
+                                      P, P, P, P, P, P, I, P, P, P, P]
             lib.or_threads.restype = ctypes.c_int
             lib.or_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -224,6 +224,10 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
     step 4, sec. 1). Routing, projection, scan and pool are the same.
 
     precision="fp32": the plain method on the stored FP32 values.
+    precision="int16": the paper's 16-bit form (Eq. 5): rows on their grain's
+    16-bit grids (int16_form), the query's coordinates and residual norm
+    quantised with the same steps, and a grain left out of a query's scan when
+    more than a quarter of its coordinates saturate (sec. 2.3).
     precision="bf16-fp8": the precision form, defined on rounded inputs: the
     query, centres and bases are rounded to BF16 for routing and projection,
     the scan reads the FP8 coordinates decoded and scaled (fp8_coords), and the
@@ -247,10 +251,16 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
             if Z is None:
                 Z = fp8_decoded(idx)
         Qp = np.ascontiguousarray(bf16_to_f32(bf16_round(Q)).reshape(Q.shape))
-    elif precision != "fp32":
+    elif precision not in ("fp32", "int16"):
         raise ValueError(precision)
+    qdelta = qdres = None
     Zs = _f32(idx["Z"] if Z is None else Z)
     rhos = _f32(idx["rho"] if rho is None else rho)
+    if precision == "int16":  # rows and queries on the grains' 16-bit grids (Eq. 5)
+        q16 = int16_form(idx)
+        Zs = q16["Zf32"]
+        rhos = q16["rhof32"]
+        qdelta, qdres = q16["delta"].astype(np.float64), q16["dres"].astype(np.float64)
     off = np.ascontiguousarray(idx["grain_off"], dtype=np.int64)
     ids = np.ascontiguousarray(idx["ids"], dtype=np.uint32)
     attr_a = None if attr is None else np.ascontiguousarray(attr, dtype=np.int64)
@@ -272,8 +282,44 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
         grain_of_pos = np.repeat(np.arange(G, dtype=np.int32), np.diff(off)).astype(np.int32)
     _c().or_search(_p(M), _p(U), G, d, r, _p(off), _p(ids), _p(Zs), _p(rhos), _p(X), _p(attr_a), _p(Q), _p(Qp), nq,
                    k, C, nprobe, _p(rng), _p(probe), _p(probe_d), _p(cand_id), _p(cand_d), _p(out_id), _p(out_d),
-                   1 if mode == "A" else 0, _p(pos_of_id), _p(grain_of_pos))
+                   1 if mode == "A" else 0, _p(pos_of_id), _p(grain_of_pos), _p(qdelta), _p(qdres))
     return dict(probe=probe, probe_d=probe_d, cand_id=cand_id, cand_d=cand_d, out_id=out_id, out_d=out_d)
+
+
+def int16_form(idx):
+    """The paper's 16-bit form of the stored rows (Eq. 5), per grain g:
+    delta_g = fl32(max |z| / 16383) and dres_g = fl32(max rho / 32767) (1 for a
+    grain whose values are all zero), so the rows use half of the signed and
+    unsigned 16-bit ranges and a query's values up to twice the grain's extent
+    stay representable (the paper leaves the steps open; saturation, which the
+    envelope filter counts, then means a query well outside the grain); codes
+    rint(fl32(z / delta_g)) and rint(fl32(rho / dres_g)) (round half to even),
+    all in IEEE single precision so that any implementation of these steps
+    gets the same codes. Returns the codes, the steps and the values the scan
+    uses, fl32(code * step)."""
+    Z = _f32(idx["Z"])
+    rho = _f32(idx["rho"])
+    off = np.asarray(idx["grain_off"], dtype=np.int64)
+    G = len(off) - 1
+    delta = np.ones(G, dtype=np.float32)
+    dres = np.ones(G, dtype=np.float32)
+    codes = np.zeros(Z.shape, dtype=np.int16)
+    rcodes = np.zeros(rho.shape, dtype=np.uint16)
+    for g in range(G):
+        a, b = off[g], off[g + 1]
+        if b > a:
+            m = np.max(np.abs(Z[a:b])) if Z.shape[1] else np.float32(0)
+            if m > 0:
+                delta[g] = np.float32(m) / np.float32(16383)
+            mr = np.max(rho[a:b])
+            if mr > 0:
+                dres[g] = np.float32(mr) / np.float32(32767)
+            codes[a:b] = np.clip(np.rint(Z[a:b] / delta[g]), -32767, 32767).astype(np.int16)
+            rcodes[a:b] = np.clip(np.rint(rho[a:b] / dres[g]), 0, 65535).astype(np.uint16)
+    gof = np.repeat(np.arange(G), np.diff(off))
+    Zf32 = np.ascontiguousarray(codes.astype(np.float32) * delta[gof][:, None])
+    rhof32 = np.ascontiguousarray(rcodes.astype(np.float32) * dres[gof])
+    return dict(codes=codes, rcodes=rcodes, delta=delta, dres=dres, Zf32=Zf32, rhof32=rhof32)
 
 
 def brute_force(X, Q, k: int, attr=None, ranges=None):

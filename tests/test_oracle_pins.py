@@ -11,6 +11,7 @@ import torch
 from oracle import hntl_oracle as O
 from paper_2606_08813_b300 import synth
 
+from cases import partition_index
 from conftest import GOLDEN
 
 
@@ -301,6 +302,81 @@ def test_mode_a_precision_form_gram_expansion():
             z = Zd[p]
             want = v @ v - 2.0 * z @ (U[g] @ v) + z @ (U[g] @ U[g].T) @ z
             assert abs(res["out_d"][qi, j] - want) <= 1e-9 * (1.0 + v @ v)
+
+
+# ---------------------------------------------------------------- 16-bit form (Eq. 5)
+
+
+def test_int16_codes_round_trip():
+    """Per grain the rows use half of each 16-bit range, the largest |z| of a
+    grain maps to +-16383 and the largest residual to 32767, and every value
+    the scan uses is within half a step (plus FP32 rounding) of the stored one."""
+    X, Q, _ = _clustered(2000, 24, 5, 5, 91)
+    idx = O.build_index(X, 5, 6, synth.uniforms(5, 6).numpy())
+    f = O.int16_form(idx)
+    off = idx["grain_off"]
+    for g in range(5):
+        a, b = off[g], off[g + 1]
+        c = f["codes"][a:b].astype(np.int64)
+        assert np.abs(c).max() == 16383 and f["rcodes"][a:b].max() == 32767
+        z = idx["Z"][a:b].astype(np.float64)
+        err = np.abs(f["Zf32"][a:b].astype(np.float64) - z)
+        assert np.all(err <= 0.5 * float(f["delta"][g]) * (1 + 1e-6) + 1e-6 * np.abs(z))
+        rr = np.abs(f["rhof32"][a:b].astype(np.float64) - idx["rho"][a:b])
+        assert np.all(rr <= 0.5 * float(f["dres"][g]) * (1 + 1e-6) + 1e-6 * idx["rho"][a:b])
+
+
+def test_int16_envelope_filter_drops_a_far_grain():
+    """Grain B is tight and far from a query that sits in grain A: in B's frame
+    the query's coordinates are far beyond twice B's extent, every one
+    saturates, and the envelope filter keeps B's rows out of the pool, which
+    the FP32 form (no filter) fills with them."""
+    rng = np.random.default_rng(17)
+    A = rng.standard_normal((50, 8))
+    B = 60.0 + 0.01 * rng.standard_normal((50, 8))
+    X = np.concatenate([A, B]).astype(np.float32)
+    assign = np.repeat([0, 1], 50)
+    idx = partition_index(X, assign, 2, 4)
+    Q = (0.1 * rng.standard_normal((3, 8))).astype(np.float32)
+    f32 = O.search(idx, X, Q, 10, 80, 2, precision="fp32")
+    i16 = O.search(idx, X, Q, 10, 80, 2, precision="int16")
+    for qi in range(3):
+        assert (f32["cand_id"][qi] >= 50).sum() == 30  # B's rows fill the rest of the FP32 pool
+        ids = i16["cand_id"][qi]
+        assert set(ids[ids != 0xFFFFFFFF].tolist()) == set(range(50))  # only A's rows
+        assert (ids == 0xFFFFFFFF).sum() == 30
+
+
+def test_int16_distances_within_quantisation_bound():
+    """Each coordinate of a query or row moves by at most half a step, so a
+    pool distance of the 16-bit form differs from the FP32 form's by at most
+    sum_j (2 |z_qj - z_ij| delta + delta^2) + dres (the two residuals), for
+    every pair whose query residual is inside the grain's residual range."""
+    X, Q, _ = _clustered(2000, 24, 4, 20, 93)
+    idx = O.build_index(X, 4, 6, synth.uniforms(4, 8).numpy())
+    f = O.int16_form(idx)
+    a = O.search(idx, X, Q, 10, 40, 1, precision="int16")
+    b = O.search(idx, X, Q, 10, 40, 1, precision="fp32")
+    pos = np.zeros(len(X), dtype=np.int64)
+    pos[idx["ids"]] = np.arange(len(X))
+    checked = 0
+    for qi in range(len(Q)):
+        g = int(b["probe"][qi, 0])
+        v = Q[qi].astype(np.float64) - idx["M"][g].astype(np.float64)
+        U = idx["U"][g].astype(np.float64)
+        zq = U @ v
+        rho_q = float(((v - U.T @ zq) ** 2).sum())
+        dl, dr = float(f["delta"][g]), float(f["dres"][g])
+        if rho_q > 65535 * dr or np.abs(zq).max() > 32767 * dl:
+            continue  # clipped: outside the bound's premise
+        d32 = dict(zip(b["cand_id"][qi].tolist(), b["cand_d"][qi].tolist()))
+        for i, d16 in zip(a["cand_id"][qi].tolist(), a["cand_d"][qi].tolist()):
+            if i in d32:
+                dz = np.abs(zq - idx["Z"][pos[i]].astype(np.float64))
+                bound = float(np.sum(2 * dz * dl + dl * dl)) + dr + 1e-6 * d32[i]
+                assert abs(d16 - d32[i]) <= bound
+                checked += 1
+    assert checked > 100
 
 
 def test_basis_sign_and_rotation_invariance():
