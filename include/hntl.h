@@ -45,9 +45,18 @@ extern "C" {
 #define HNTL_EBUSY (-7)    /* admission refused: memory budget or slots exhausted */
 
 /* Index precision. FP32: FP32 raw rows and coordinates (the plain method).
- * BF16_FP8: BF16 raw rows, FP8-E4M3 coordinates with a per-grain FP32 scale. */
+ * BF16_FP8: BF16 raw rows, FP8-E4M3 coordinates with a per-grain FP32 scale.
+ * INT16: the paper's 16-bit form (Eq. 5), built at load from an FP32 file:
+ * per grain the steps delta_g = fl32(max |z| / 16383) and
+ * dres_g = fl32(max rho / 32767) (rows use half of each 16-bit range),
+ * int16 coordinates rint(fl32(z / delta_g)) and uint16 residual norms
+ * rint(fl32(rho / dres_g)), all in IEEE single precision; queries are
+ * quantised with the same steps (saturating), and a grain where more than a
+ * quarter of a query's coordinates saturate is left out of that query's scan
+ * (the Quantization Envelope Filter, sec. 2.3). FP32 raw rows for the rerank. */
 #define HNTL_PREC_FP32 0
 #define HNTL_PREC_BF16_FP8 1
+#define HNTL_PREC_INT16 2
 
 typedef struct hntl_index hntl_index; /* opaque; owned by the library */
 

@@ -585,7 +585,7 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   I.G = G;
   I.r = r;
   I.precision = precision;
-  I.rp = (uint32_t)padded_r((int)r, precision == HNTL_PREC_BF16_FP8);
+  I.rp = (uint32_t)padded_r((int)r, (int)precision);
   I.has_attr = P.d_attr != nullptr;
   auto own = [&](size_t bytes) -> void* {
     void* p = nullptr;

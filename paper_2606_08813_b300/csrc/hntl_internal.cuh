@@ -27,9 +27,12 @@ constexpr uint32_t kInvalidId = 0xFFFFFFFFu;
 // with rp = r rounded up to V (zero padding). A thread (one row) reads its row
 // with rp/V 16-byte loads and a warp's load covers 512 contiguous bytes.
 // Padding rows carry id 0xFFFFFFFF and are masked by the grain's row count.
-__host__ __device__ inline int coord_lane(bool fp8) { return fp8 ? 16 : 4; }
-__host__ __device__ inline int padded_r(int r, bool fp8) {
-  const int V = coord_lane(fp8);
+// Coordinate storage kinds (equal to the HNTL_PREC_* value of the index).
+constexpr int kCoordF32 = 0, kCoordFP8 = 1, kCoordI16 = 2;
+// Coordinates per 16-byte lane of the Block-SoA layout.
+__host__ __device__ inline int coord_lane(int kind) { return kind == kCoordFP8 ? 16 : (kind == kCoordI16 ? 8 : 4); }
+__host__ __device__ inline int padded_r(int r, int kind) {
+  const int V = coord_lane(kind);
   return (r + V - 1) / V * V;
 }
 __host__ __device__ inline size_t zoff(size_t b, int j, int t, int rp, int V) {
@@ -52,7 +55,9 @@ struct Index {
   uint32_t* blk_grain = nullptr;   // [n_blocks] grain of each block
   float* Zb = nullptr;           // [n_blocks][rp/4][128][4] FP32 coordinates
   uint8_t* Z8b = nullptr;        // [n_blocks][rp/16][128][16] FP8-E4M3 codes (precision form)
-  float* scale = nullptr;        // [G] FP8 scale per grain
+  int16_t* Z16b = nullptr;       // [n_blocks][rp/8][128][8] int16 codes (16-bit form)
+  float* scale = nullptr;        // [G] FP8 scale, or the 16-bit form's coordinate step, per grain
+  float* dres = nullptr;         // [G] the 16-bit form's residual step per grain
   float* rho = nullptr;          // [n_blocks][128] residual norms
   float* blk_rho_min = nullptr;  // [n_blocks] smallest residual norm of a block's real rows (+inf if none)
   float* crow = nullptr;         // [n_blocks][128] ||z_i||^2 + rho_i of the decoded row (precision form)

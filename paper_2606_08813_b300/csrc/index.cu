@@ -107,11 +107,13 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
     return fail(HNTL_EFORMAT, "bad sizes in header");
   if (r > (uint32_t)kMaxR) return fail(HNTL_EINVAL, "tangent dimension r > 64 is not supported");
   if (G > kMaxG) return fail(HNTL_EINVAL, "more than 8192 grains is not supported");
-  if (precision != HNTL_PREC_FP32 && precision != HNTL_PREC_BF16_FP8) return fail(HNTL_EINVAL, "bad precision");
+  if (precision != HNTL_PREC_FP32 && precision != HNTL_PREC_BF16_FP8 && precision != HNTL_PREC_INT16)
+    return fail(HNTL_EINVAL, "bad precision");
   if (precision == HNTL_PREC_BF16_FP8 && d % 8)  // BF16 rows move in 16-byte pieces
     return fail(HNTL_EINVAL, "the precision form needs d to be a multiple of 8");
   bool xbf16 = flags & kFlagXbf16;
-  if (precision == HNTL_PREC_FP32 && xbf16) return fail(HNTL_EINVAL, "file holds BF16 raw rows; load it as BF16_FP8");
+  if (precision != HNTL_PREC_BF16_FP8 && xbf16)
+    return fail(HNTL_EINVAL, "file holds BF16 raw rows; load it as BF16_FP8");
   if (precision == HNTL_PREC_BF16_FP8 && !((flags & kFlagFp8) && xbf16))
     return fail(HNTL_EINVAL, "file has no FP8 coordinates / BF16 rows for the precision form");
 
@@ -175,7 +177,7 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
   I.G = G;
   I.r = r;
   I.precision = precision;
-  I.rp = (uint32_t)padded_r((int)r, precision == HNTL_PREC_BF16_FP8);
+  I.rp = (uint32_t)padded_r((int)r, (int)precision);
   I.has_attr = attr_raw != nullptr;
   I.h_blk_off.assign(G + 1, 0);
   std::vector<uint32_t> grain_rows(G);
@@ -199,10 +201,26 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
 
   const size_t rows_pad = nb * kBlockRows;
   std::vector<uint32_t> blk_grain(nb);
-  const int rp = (int)I.rp, V = coord_lane(precision == HNTL_PREC_BF16_FP8);
+  const int rp = (int)I.rp, V = coord_lane((int)precision);
   std::vector<float> Zb(precision == HNTL_PREC_FP32 ? rows_pad * rp : 0, 0.0f);
   std::vector<uint8_t> Z8b(precision == HNTL_PREC_BF16_FP8 ? rows_pad * rp : 0, 0);
+  std::vector<int16_t> Z16b(precision == HNTL_PREC_INT16 ? rows_pad * rp : 0, 0);
   std::vector<float> rho_b(rows_pad, 0.0f);
+  // 16-bit form (Eq. 5): per grain the steps delta = fl32(max |z| / 16383) and
+  // dres = fl32(max rho / 32767) (1 for a grain of zeros), codes rint(fl32(v / step));
+  // IEEE single precision throughout, so the codes are the same wherever computed
+  std::vector<float> delta(precision == HNTL_PREC_INT16 ? G : 0, 1.0f), dres(delta.size(), 1.0f);
+  if (precision == HNTL_PREC_INT16) {
+    for (uint32_t g = 0; g < G; ++g) {
+      float m = 0.0f, mr = 0.0f;
+      for (uint64_t p = goff[g]; p < goff[g + 1]; ++p) {
+        for (uint32_t j = 0; j < r; ++j) m = std::max(m, std::fabs(Z[p * r + j]));
+        mr = std::max(mr, rho[p]);
+      }
+      if (m > 0.0f) delta[g] = m / 16383.0f;
+      if (mr > 0.0f) dres[g] = mr / 32767.0f;
+    }
+  }
   std::vector<uint32_t> ids_b(rows_pad, kInvalidId);
   std::vector<int64_t> attr_b(I.has_attr ? rows_pad : 0, 0);
   for (uint32_t g = 0; g < G; ++g) {
@@ -211,12 +229,19 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
       uint64_t p = goff[g] + i;
       uint64_t b = I.h_blk_off[g] + i / kBlockRows, t = i % kBlockRows;
       for (uint32_t j = 0; j < r; ++j) {
-        if (precision == HNTL_PREC_FP32)
+        if (precision == HNTL_PREC_FP32) {
           Zb[zoff(b, (int)j, (int)t, rp, V)] = Z[p * r + j];
-        else
+        } else if (precision == HNTL_PREC_INT16) {
+          const float c = std::rint(Z[p * r + j] / delta[g]);
+          Z16b[zoff(b, (int)j, (int)t, rp, V)] = (int16_t)std::max(-32767.0f, std::min(32767.0f, c));
+        } else {
           Z8b[zoff(b, (int)j, (int)t, rp, V)] = Z8[p * r + j];
+        }
       }
-      rho_b[b * kBlockRows + t] = rho[p];
+      if (precision == HNTL_PREC_INT16)  // the residual on its grid, as the scan uses it
+        rho_b[b * kBlockRows + t] = std::max(0.0f, std::min(65535.0f, std::rint(rho[p] / dres[g]))) * dres[g];
+      else
+        rho_b[b * kBlockRows + t] = rho[p];
       ids_b[b * kBlockRows + t] = ids[p];
       if (I.has_attr) attr_b[b * kBlockRows + t] = attr[ids[p]];
     }
@@ -235,6 +260,11 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
     if ((rc = dev_upload(I, &I.blk_grain, blk_grain.data(), nb * 4))) break;
     if (precision == HNTL_PREC_FP32) {
       if ((rc = dev_upload(I, &I.Zb, Zb.data(), rows_pad * rp * 4))) break;
+      if ((rc = dev_upload(I, &I.X, Xraw, (size_t)N * d * 4))) break;
+    } else if (precision == HNTL_PREC_INT16) {
+      if ((rc = dev_upload(I, &I.Z16b, Z16b.data(), rows_pad * rp * 2))) break;
+      if ((rc = dev_upload(I, &I.scale, delta.data(), (size_t)G * 4))) break;
+      if ((rc = dev_upload(I, &I.dres, dres.data(), (size_t)G * 4))) break;
       if ((rc = dev_upload(I, &I.X, Xraw, (size_t)N * d * 4))) break;
     } else {
       if ((rc = dev_upload(I, &I.Z8b, Z8b.data(), rows_pad * rp))) break;
@@ -345,6 +375,7 @@ namespace {
 
 __global__ void k_export_rows(const uint32_t* __restrict__ blk_off, const uint32_t* __restrict__ grain_rows, int G,
                               int r, int rp, const float* __restrict__ Zb, const uint8_t* __restrict__ Z8b,
+                              const int16_t* __restrict__ Z16b,
                               const float* __restrict__ scale, const float* __restrict__ rho_b,
                               const uint32_t* __restrict__ ids_b, const uint64_t* __restrict__ goff, float* __restrict__ Z,
                               float* __restrict__ rho, uint32_t* __restrict__ ids, uint64_t N) {
@@ -363,6 +394,8 @@ __global__ void k_export_rows(const uint32_t* __restrict__ blk_off, const uint32
     float v;
     if (Zb) {
       v = Zb[zoff(b, j, (int)t, rp, 4)];
+    } else if (Z16b) {
+      v = (float)Z16b[zoff(b, j, (int)t, rp, 8)] * scale[g];
     } else {
       __nv_fp8_e4m3 c;
       c.__x = Z8b[zoff(b, j, (int)t, rp, 16)];
@@ -411,7 +444,7 @@ extern "C" int hntl_index_export(const hntl_index* idx, float* h_M, float* h_U, 
     if (rc == HNTL_OK) {
       cudaMemcpy(dgoff, goff.data(), sizeof(uint64_t) * (I.G + 1), cudaMemcpyHostToDevice);
       hntl::k_export_rows<<<(unsigned)((I.n + 255) / 256), 256>>>(
-          I.blk_off, I.grain_rows, (int)I.G, (int)I.r, (int)I.rp, I.Zb, I.Z8b, I.scale, I.rho, I.ids,
+          I.blk_off, I.grain_rows, (int)I.G, (int)I.r, (int)I.rp, I.Zb, I.Z8b, I.Z16b, I.scale, I.rho, I.ids,
           static_cast<uint64_t*>(dgoff), static_cast<float*>(dZ), static_cast<float*>(drho),
           static_cast<uint32_t*>(dids), I.n);
       cudaError_t e = cudaDeviceSynchronize();

@@ -41,7 +41,7 @@ __global__ void k_gram_f32(const float* __restrict__ U, int d, int r, float* __r
 
 // h_i = z_i^T G_g z_i of every stored row, z_i decoded exactly as the scan
 // decodes it (padding rows get a harmless value that is never read).
-template <int RT, bool kFP8>
+template <int RT, int kC>
 __global__ void __launch_bounds__(kBlockRows) k_row_h(const Coords cz, const uint32_t* __restrict__ blk_grain,
                                                       const float* __restrict__ gram, int r, int rp,
                                                       float* __restrict__ h_out) {
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kBlockRows) k_row_h(const Coords cz, const uin
   const int t = threadIdx.x;
   const uint32_t g = blk_grain[b];
   float z[RT];
-  load_row<RT, kFP8>(cz, rp, kFP8 ? cz.scale[g] : 1.f, b, t, z);
+  load_row<RT, kC>(cz, rp, kC != kCoordF32 ? cz.scale[g] : 1.f, b, t, z);
   const float* Gg = gram + (size_t)g * r * r;
   float h = 0.f;
 #pragma unroll
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kBlockRows) k_row_h(const Coords cz, const uin
 // thread each), then the k smallest (dist, id). A member's grain is one of
 // the query's probes (the pool only holds rows of probed grains), which
 // gives its (query, grain) pair: z_q and ||v'||^2.
-template <int RT, bool kFP8>
+template <int RT, int kC>
 __global__ void __launch_bounds__(256) k_rerank_recon(int nprobe, int C, int k, const uint32_t* __restrict__ cand_id,
                                                       const uint32_t* __restrict__ pos_of_id,
                                                       const uint32_t* __restrict__ blk_grain, const Coords cz,
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) k_rerank_recon(int nprobe, int C, int k, 
       while (p + 1 < nprobe && (uint32_t)pq[p] != g) ++p;
       const uint32_t pr = po[p];
       float z[RT];
-      load_row<RT, kFP8>(cz, rp, kFP8 ? cz.scale[g] : 1.f, b, t, z);
+      load_row<RT, kC>(cz, rp, kC != kCoordF32 ? cz.scale[g] : 1.f, b, t, z);
       const float* zp = zq + (size_t)pr * r;
       float dot = 0.f;
 #pragma unroll

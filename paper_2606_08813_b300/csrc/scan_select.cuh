@@ -69,12 +69,13 @@ __device__ __forceinline__ float eval_D(const float* zq, const float (&z)[RT], f
 struct Coords {
   const float* Zb;      // FP32 form
   const uint8_t* Z8b;   // precision form
-  const float* scale;   // precision form, per grain
+  const float* scale;   // precision form (FP8 scale) and 16-bit form (coordinate step), per grain
+  const int16_t* Z16b;  // 16-bit form
 };
 
-template <int RT, bool kFP8>
+template <int RT, int kC>
 __device__ __forceinline__ void load_row(const Coords& c, int rp, float s_g, size_t b, int t, float (&z)[RT]) {
-  if constexpr (kFP8) {
+  if constexpr (kC == kCoordFP8) {
     static_assert(RT % 16 == 0, "FP8 rows are read in lanes of 16 codes");
 #pragma unroll
     for (int l = 0; l < RT / 16; ++l) {
@@ -97,6 +98,24 @@ __device__ __forceinline__ void load_row(const Coords& c, int rp, float s_g, siz
         for (int i = 0; i < 16; ++i) z[l * 16 + i] = 0.f;
       }
     }
+  } else if constexpr (kC == kCoordI16) {
+    // 16-bit form: 8 int16 codes per lane, times the grain's step (the code is exact in FP32)
+    static_assert(RT % 8 == 0, "16-bit rows are read in lanes of 8 codes");
+#pragma unroll
+    for (int l = 0; l < RT / 8; ++l) {
+      if (l * 8 < rp) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(c.Z16b + ((b * (rp / 8) + l) * kBlockRows + t) * 8));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          z[l * 8 + 2 * h] = (float)(int16_t)(w[h] & 0xFFFFu) * s_g;
+          z[l * 8 + 2 * h + 1] = (float)(int16_t)(w[h] >> 16) * s_g;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) z[l * 8 + i] = 0.f;
+      }
+    }
   } else {
 #pragma unroll
     for (int l = 0; l < RT / 4; ++l) {
@@ -115,7 +134,7 @@ __device__ __forceinline__ void load_row(const Coords& c, int rp, float s_g, siz
 
 // ------------------------------------------------------------------ pilot
 
-template <int RT, bool kFP8>
+template <int RT, int kC>
 __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t* __restrict__ probe,
                                                const uint32_t* __restrict__ pair_of,
                                                const uint32_t* __restrict__ blk_off,
@@ -158,7 +177,7 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
     const uint32_t nbk = blk_off[g + 1] - blk_off[g];
     for (int j = threadIdx.x; j < RT; j += blockDim.x) szq[j] = j < r ? zq[(size_t)s * r + j] : 0.f;
     const float rho_q = rhoq[s];
-    const float s_g = kFP8 ? cz.scale[g] : 1.f;
+    const float s_g = kC != kCoordF32 ? cz.scale[g] : 1.f;
     __syncthreads();
     const uint32_t room = filter ? min(((uint32_t)kPilotRows - fill) / kBlockRows,
                                        (8u * kPilotRows - scanned) / kBlockRows)
@@ -180,7 +199,7 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
         }
         if (keep) {
           float z[RT];
-          load_row<RT, kFP8>(cz, rp, s_g, b, t, z);
+          load_row<RT, kC>(cz, rp, s_g, b, t, z);
           k = __float_as_uint(eval_D<RT>(szq, z, rho_q, rho[b * kBlockRows + t]));
           keep = k < kInfBits;
         }
@@ -231,7 +250,7 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
 
 constexpr int kMaxNeed = 1024;  // pairs of one grain a block can list after pruning
 
-template <int RT, bool kFP8>
+template <int RT, int kC>
 __global__ void __launch_bounds__(kBlockRows) k_scan_filter(
     const uint32_t* __restrict__ blk_grain, const uint32_t* __restrict__ blk_off,
     const uint32_t* __restrict__ grain_rows, const Coords cz, const float* __restrict__ rho,
@@ -271,7 +290,7 @@ __global__ void __launch_bounds__(kBlockRows) k_scan_filter(
   const uint32_t row = (uint32_t)(b - blk_off[g]) * kBlockRows + t;
   const bool valid = row < grain_rows[g];
   float z[RT];
-  load_row<RT, kFP8>(cz, rp, kFP8 ? cz.scale[g] : 1.f, b, t, z);
+  load_row<RT, kC>(cz, rp, kC != kCoordF32 ? cz.scale[g] : 1.f, b, t, z);
   const float rho_i = rho[b * kBlockRows + t];
   const uint32_t id = ids[b * kBlockRows + t];
   const long long a = filter ? (long long)attr_b[b * kBlockRows + t] : 0;
@@ -337,7 +356,7 @@ struct SurvivorSrc {
 
 // Elements as (D bit pattern, id): every row of the query's probed grains,
 // D recomputed (used when the survivor list overflowed).
-template <int RT, bool kFP8>
+template <int RT, int kC>
 struct ProbedRowsSrc {
   int q, nprobe, r, rp;
   const int32_t* probe;
@@ -363,7 +382,7 @@ struct ProbedRowsSrc {
       const uint32_t s = pair_of[(size_t)q * nprobe + p];
       const uint32_t n = grain_rows[g];
       const float rho_q = rhoq[s];
-      const float s_g = kFP8 ? cz.scale[g] : 1.f;
+      const float s_g = kC != kCoordF32 ? cz.scale[g] : 1.f;
       __align__(8) float zl[RT];
 #pragma unroll
       for (int j = 0; j < RT; ++j) zl[j] = j < r ? zq[(size_t)s * r + j] : 0.f;
@@ -375,7 +394,7 @@ struct ProbedRowsSrc {
           if (a < lo || a > hi) continue;
         }
         float z[RT];
-        load_row<RT, kFP8>(cz, rp, s_g, b, t, z);
+        load_row<RT, kC>(cz, rp, s_g, b, t, z);
         f(__float_as_uint(eval_D<RT>(zl, z, rho_q, rho[b * kBlockRows + t])), ids[b * kBlockRows + t]);
       }
     }
@@ -550,7 +569,7 @@ constexpr int kFinalThreads = 128;  // small CTAs: many queries in flight per SM
 // row recomputed (kFallback = true). Both are launched; each CTA returns at
 // once for the queries of the other kind. Keeping the rare recompute out of
 // the common kernel keeps its registers low, and its occupancy high.
-template <int RT, bool kFP8, bool kFallback>
+template <int RT, int kC, bool kFallback>
 __global__ void __launch_bounds__(kFinalThreads, kFallback ? 1 : 8) k_final_select(
     int nprobe, int C, uint32_t cap, const uint32_t* __restrict__ cnt, const unsigned long long* __restrict__ surv,
     const int32_t* __restrict__ probe, const uint32_t* __restrict__ pair_of, const uint32_t* __restrict__ blk_off,
@@ -576,7 +595,7 @@ __global__ void __launch_bounds__(kFinalThreads, kFallback ? 1 : 8) k_final_sele
     SurvivorSrc src{surv + (size_t)q * cap, n};
     select_topc(src, C, S, oid, od);
   } else {
-    ProbedRowsSrc<RT, kFP8> src{q,  nprobe, r,   rp,     probe, pair_of, blk_off, grain_rows,
+    ProbedRowsSrc<RT, kC> src{q,  nprobe, r,   rp,     probe, pair_of, blk_off, grain_rows,
                                 cz, rho,    ids, attr_b, zq,    rhoq,    filter};
     select_topc(src, C, S, oid, od);
   }

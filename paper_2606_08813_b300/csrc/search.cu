@@ -81,6 +81,38 @@ __global__ void k_probe_dist(const float* __restrict__ Q, const float* __restric
   }
 }
 
+// ------------------------------------------------------------------ 16-bit form
+
+// The 16-bit form's query side (Eq. 5, sec. 2.3), one CTA per grain over its
+// (query, grain) pairs: each coordinate of z_q is put on the grain's grid
+// (rint(fl32(z / delta_g)), saturating at +-32767) and replaced by its grid
+// value; a pair with more than a quarter of its coordinates saturated is left
+// out (rho_q = +inf, so every downstream stage drops its rows); otherwise
+// rho_q goes on the residual grid (saturating at 65535 steps).
+__global__ void k_quant_pairs(const uint32_t* __restrict__ pair_off, int r, const float* __restrict__ delta,
+                              const float* __restrict__ dres, float* __restrict__ zq, float* __restrict__ rhoq) {
+  const uint32_t g = blockIdx.x, p0 = pair_off[g], p1 = pair_off[g + 1];
+  const float dl = delta[g], dr = dres[g];
+  for (uint32_t pr = p0 + threadIdx.x; pr < p1; pr += blockDim.x) {
+    float* z = zq + (size_t)pr * r;
+    int sat = 0;
+    for (int j = 0; j < r; ++j) {
+      float t = rintf(z[j] / dl);
+      if (fabsf(t) > 32767.f) {
+        ++sat;
+        t = t > 0.f ? 32767.f : -32767.f;
+      }
+      z[j] = t * dl;
+    }
+    if (4 * sat > r) {
+      rhoq[pr] = INFINITY;
+    } else {
+      const float tr = fminf(rintf(rhoq[pr] / dr), 65535.f);
+      rhoq[pr] = tr * dr;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ bucketing
 
 __global__ void k_bucket_count(const int32_t* __restrict__ probe, int n, uint32_t* __restrict__ gcnt) {
@@ -392,14 +424,14 @@ int launch_project_tc(const Index& I, uint32_t nq, uint32_t P, const Ws& w, cuda
   return launch_project_tc_n<64>(I, nq, P, w, st);
 }
 
-template <int RT, bool kFP8>
+template <int RT, int kC>
 void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, const int64_t* filter,
                         cudaStream_t st, const std::function<void(int)>& mark, const uint32_t* qC) {
-  const Coords cz{I.Zb, I.Z8b, I.scale};
-  k_pilot<RT, kFP8><<<nq, 256, 0, st>>>(nprobe, C, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho,
+  const Coords cz{I.Zb, I.Z8b, I.scale, I.Z16b};
+  k_pilot<RT, kC><<<nq, 256, 0, st>>>(nprobe, C, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho,
                                         I.attr_b, (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.tau, qC);
   mark(4);
-  if constexpr (kFP8) {
+  if constexpr (kC == kCoordFP8) {
     static thread_local int attr_dev = -1;
     if (attr_dev != I.device) {
       cudaFuncSetAttribute(k_scan_tc<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, ScanTc<RT>::kSmem);
@@ -422,15 +454,15 @@ void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, 
         (int)I.r, (int)I.rp, w.need_cnt, w.need_list, w.pair_off, w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min,
         filter, w.cap, w.cnt, w.surv, I.d_err);
   } else {
-    k_scan_filter<RT, kFP8><<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(
+    k_scan_filter<RT, kC><<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(
         I.blk_grain, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b, (int)I.r, (int)I.rp, w.gcnt, w.pair_off,
         w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap, w.cnt, w.surv);
   }
   mark(5);
-  k_final_select<RT, kFP8, false><<<nq, kFinalThreads, 0, st>>>(
+  k_final_select<RT, kC, false><<<nq, kFinalThreads, 0, st>>>(
       nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b,
       (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id, w.cand_d, qC);
-  k_final_select<RT, kFP8, true><<<nq, kFinalThreads, 0, st>>>(
+  k_final_select<RT, kC, true><<<nq, kFinalThreads, 0, st>>>(
       nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b,
       (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id, w.cand_d, qC);
 }
@@ -438,11 +470,13 @@ void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, 
 template <int RT>
 void launch_scan_select_p(const Index& I, const Ws& w, int nq, int nprobe, int C, const int64_t* filter,
                           cudaStream_t st, const std::function<void(int)>& mark, const uint32_t* qC) {
-  // FP8 rows are read in lanes of 16 codes, so the FP8 kernels need RT >= 16
+  // FP8 rows are read in lanes of 16 codes, 16-bit rows in lanes of 8
   if (I.precision == HNTL_PREC_BF16_FP8)
-    launch_scan_select<(RT < 16 ? 16 : RT), true>(I, w, nq, nprobe, C, filter, st, mark, qC);
+    launch_scan_select<(RT < 16 ? 16 : RT), kCoordFP8>(I, w, nq, nprobe, C, filter, st, mark, qC);
+  else if (I.precision == HNTL_PREC_INT16)
+    launch_scan_select<(RT < 8 ? 8 : RT), kCoordI16>(I, w, nq, nprobe, C, filter, st, mark, qC);
   else
-    launch_scan_select<RT, false>(I, w, nq, nprobe, C, filter, st, mark, qC);
+    launch_scan_select<RT, kCoordF32>(I, w, nq, nprobe, C, filter, st, mark, qC);
 }
 
 // Stage timing: CUDA events recorded on the search's stream between stages.
@@ -484,6 +518,8 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
   int rc = check_params(I, nq, k, C, nprobe);
   if (rc) return rc;
   if (filter && !I.has_attr) return fail(HNTL_EINVAL, "filter given but the index has no attribute column");
+  if (mode_a && I.precision == HNTL_PREC_INT16)
+    return fail(HNTL_EINVAL, "Mode A is not available for the 16-bit form");
   if (nq == 0) return HNTL_OK;
   if (!Qd || !ws || !out_ids || !out_d) return fail(HNTL_EINVAL, "null buffer");
   if ((cand_ids == nullptr) != (cand_d == nullptr)) return fail(HNTL_EINVAL, "pass both pool buffers or neither");
@@ -538,6 +574,8 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
     unsigned grid = (unsigned)std::min<size_t>((size_t)P / kPairsPerGroup + I.G, 148 * 16);
     k_project<false><<<grid, 256, smem, st>>>(Qd, I.M, I.U, (int)I.d, (int)I.r, (int)I.G, w.grp_off, w.pair_off,
                                               w.pair_q, w.zq, w.rhoq);
+    if (I.precision == HNTL_PREC_INT16)
+      k_quant_pairs<<<I.G, 128, 0, st>>>(w.pair_off, (int)I.r, I.scale, I.dres, w.zq, w.rhoq);
   }
   mark(3);
   HNTL_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * ((size_t)nq + 5), st));
@@ -550,20 +588,20 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
   }
   mark(6);
   if (mode_a) {
-    const Coords cz{I.Zb, I.Z8b, I.scale};
+    const Coords cz{I.Zb, I.Z8b, I.scale, I.Z16b};
     auto recon = [&](auto kern) {
       kern<<<nq, 256, 0, st>>>((int)nprobe, (int)C, (int)k, w.cand_id, I.pos_of_id, I.blk_grain, cz, (int)I.r,
                                (int)I.rp, I.hrow, w.probe, w.pair_of, w.zq, w.pair_vn, out_ids, out_d, qk, qC);
     };
     if (I.precision == HNTL_PREC_BF16_FP8) {
-      if (I.r <= 16) recon(k_rerank_recon<16, true>);
-      else if (I.r <= 32) recon(k_rerank_recon<32, true>);
-      else recon(k_rerank_recon<64, true>);
+      if (I.r <= 16) recon(k_rerank_recon<16, kCoordFP8>);
+      else if (I.r <= 32) recon(k_rerank_recon<32, kCoordFP8>);
+      else recon(k_rerank_recon<64, kCoordFP8>);
     } else {
-      if (I.r <= 8) recon(k_rerank_recon<8, false>);
-      else if (I.r <= 16) recon(k_rerank_recon<16, false>);
-      else if (I.r <= 32) recon(k_rerank_recon<32, false>);
-      else recon(k_rerank_recon<64, false>);
+      if (I.r <= 8) recon(k_rerank_recon<8, kCoordF32>);
+      else if (I.r <= 16) recon(k_rerank_recon<16, kCoordF32>);
+      else if (I.r <= 32) recon(k_rerank_recon<32, kCoordF32>);
+      else recon(k_rerank_recon<64, kCoordF32>);
     }
   } else {
     size_t smem = (size_t)I.d * sizeof(float);
@@ -662,7 +700,7 @@ int finalize_index(Index& I) {
     k_to_bf16_rows<<<(unsigned)((nu + 255) / 256), 256>>>(I.U, nu, I.Uh);
     k_gram<<<I.G, 256>>>(I.Uh, (int)I.d, (int)I.r, I.gram);  // of the BF16 bases the precision form uses
     k_grain_rho_min<<<(I.G * 32 + 255) / 256, 256>>>(I.blk_rho_min, I.blk_off, (int)I.G, I.grain_rho_min);
-    const Coords cz{I.Zb, I.Z8b, I.scale};
+    const Coords cz{I.Zb, I.Z8b, I.scale, I.Z16b};
     if (I.n_blocks) {
       if (I.r <= 16) k_row_c<16><<<(unsigned)I.n_blocks, kBlockRows>>>(cz, I.rho, I.blk_grain, (int)I.rp, I.crow);
       else if (I.r <= 32) k_row_c<32><<<(unsigned)I.n_blocks, kBlockRows>>>(cz, I.rho, I.blk_grain, (int)I.rp, I.crow);
@@ -675,18 +713,20 @@ int finalize_index(Index& I) {
   if (I.n_blocks) {
     const size_t npos = (size_t)I.n_blocks * kBlockRows;
     k_pos_of_id<<<(unsigned)((npos + 255) / 256), 256>>>(I.ids, npos, I.pos_of_id);
-    const Coords cz{I.Zb, I.Z8b, I.scale};
+    const Coords cz{I.Zb, I.Z8b, I.scale, I.Z16b};
     const unsigned nb = (unsigned)I.n_blocks;
     const int r = (int)I.r, rp = (int)I.rp;
     if (bf16) {
-      if (I.r <= 16) k_row_h<16, true><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
-      else if (I.r <= 32) k_row_h<32, true><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
-      else k_row_h<64, true><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+      if (I.r <= 16) k_row_h<16, kCoordFP8><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+      else if (I.r <= 32) k_row_h<32, kCoordFP8><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+      else k_row_h<64, kCoordFP8><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+    } else if (I.precision == HNTL_PREC_INT16) {
+      // no Mode A for the 16-bit form (its query coordinates are replaced by grid values)
     } else {
-      if (I.r <= 8) k_row_h<8, false><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
-      else if (I.r <= 16) k_row_h<16, false><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
-      else if (I.r <= 32) k_row_h<32, false><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
-      else k_row_h<64, false><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+      if (I.r <= 8) k_row_h<8, kCoordF32><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+      else if (I.r <= 16) k_row_h<16, kCoordF32><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+      else if (I.r <= 32) k_row_h<32, kCoordF32><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
+      else k_row_h<64, kCoordF32><<<nb, kBlockRows>>>(cz, I.blk_grain, I.gram, r, rp, I.hrow);
     }
   }
   HNTL_CUDA_TRY(cudaDeviceGetAttribute(&I.num_sms, cudaDevAttrMultiProcessorCount, I.device));
