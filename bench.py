@@ -466,6 +466,41 @@ def run_fp32_compare(a, hntl, X, Q, w, sd, B, n_recall, truth, line):
             "note": "same rows, k-means draws, batch, nprobe, C, k and streams; FP32 rows, coordinates and bases"}
 
 
+def run_int16(a, hntl, X, Q, w, sd, B, n_recall, truth):
+    """The paper's 16-bit form (Eq. 5, with the envelope filter) built from the
+    same rows and k-means draws: QPS over the same batches and streams, recall."""
+    t0 = time.perf_counter()
+    g16 = hntl.Index.build(X, w["G"], w["r"], u=synth.uniforms(w["G"], sd["kmeans"]).numpy(), seed=sd["kmeans"],
+                           precision=hntl.PREC_INT16)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    k, C, nprobe = w["k"], w["C"], w["nprobe"]
+    nb = w["nq"] // B
+    batches = [Q[i * B:(i + 1) * B].contiguous() for i in range(nb)]
+    found = [g16.search(batches[i], k, C, nprobe)[0] for i in range(max(1, (n_recall + B - 1) // B))]
+    rec = recall_at_k(torch.cat(found)[:n_recall], truth) if n_recall else None
+    ms_ = MultiStream(g16, B, k, C, nprobe, a.streams, Q.device)
+    ms_.run(batches, a.warmup)
+    torch.cuda.synchronize()
+    hntl.profile_read()
+    hntl.profile_enable(True)  # stage times: one stream
+    for i in range(a.steps):
+        g16.search(batches[i % nb], k, C, nprobe, out=ms_.outs[0], ws=ms_.ws[0])
+    torch.cuda.synchronize()
+    hntl.profile_enable(False)
+    sm, calls = hntl.profile_read()
+    e0, e1 = ms_.run(batches, a.steps)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    del ms_, g16
+    torch.cuda.empty_cache()
+    return {"value": round(B / (ms / 1e3), 1), "unit": "queries/s", "ms_per_step": round(ms, 4),
+            "recall_at_10": None if rec is None else round(rec, 4), "index_build_s": round(build_s, 2),
+            "streams": a.streams, "stages_ms": {k_: round(v_ / max(calls, 1), 4) for k_, v_ in sm.items()},
+            "note": "same rows, k-means draws, batches, nprobe, C, k and streams; int16 coordinates with per-grain "
+                    "steps, uint16 residuals, quantised queries and the envelope filter; FP32 raw rows"}
+
+
 def run_mode_a(a, hntl, gi, Q, w, B, n_recall, truth):
     """Mode A on the same index, batches, parameters and streams: the pool
     reranked by L2 to each row's reconstruction (no raw row read)."""
@@ -648,6 +683,9 @@ def run_ours(a, world, rank, local):
     if a.mode_a and not a.profile_mode:
         line["mode_a_same_data"] = run_mode_a(a, hntl, gi, Q, w, B, n_recall, truth)
         print(f"mode A: {line['mode_a_same_data']}", file=sys.stderr)
+    if a.int16 and X is not None and not a.profile_mode:
+        line["int16_form_same_data"] = run_int16(a, hntl, X, Q, w, sd, B, n_recall, truth)
+        print(f"16-bit form: {line['int16_form_same_data']}", file=sys.stderr)
     if prec == "bf16-fp8" and a.fp32_compare and X is not None:
         line["plain_fp32_same_data"] = run_fp32_compare(a, hntl, X, Q, w, sd, B, n_recall, truth, line)
     if rank == 0 and world == 1 and not a.no_cpu_baseline and not a.profile_mode:
@@ -843,6 +881,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-recall", type=int, default=1536, help="served requests checked against brute force")
     ap.add_argument("--serve-p99-ms", type=float, default=50.0)
+    ap.add_argument("--no-int16", dest="int16", action="store_false",
+                    help="skip timing the paper's 16-bit form built from the same rows")
     ap.add_argument("--no-mode-a", dest="mode_a", action="store_false",
                     help="skip timing Mode A (rerank on reconstructions) on the same index")
     ap.add_argument("--no-fp32-compare", dest="fp32_compare", action="store_false",

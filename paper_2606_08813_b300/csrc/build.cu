@@ -539,7 +539,8 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   hntl_build_params P{};
   if (prm) P = *prm;
   const uint32_t precision = P.precision;
-  if (precision != HNTL_PREC_FP32 && precision != HNTL_PREC_BF16_FP8) return fail(HNTL_EINVAL, "bad precision");
+  if (precision != HNTL_PREC_FP32 && precision != HNTL_PREC_BF16_FP8 && precision != HNTL_PREC_INT16)
+    return fail(HNTL_EINVAL, "bad precision");
   if (precision == HNTL_PREC_BF16_FP8 && d % 8)  // BF16 rows move in 16-byte pieces
     return fail(HNTL_EINVAL, "the precision form needs d to be a multiple of 8");
   const uint32_t max_iter = P.max_iter ? P.max_iter : 10;
@@ -785,7 +786,7 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   I.blk_rho_min = static_cast<float*>(own(I.n_blocks * 4));
   I.ids = static_cast<uint32_t*>(own(rows_pad * 4));
   if (I.has_attr) I.attr_b = static_cast<int64_t*>(own(rows_pad * 8));
-  if (precision == HNTL_PREC_FP32) {
+  if (precision == HNTL_PREC_FP32 || precision == HNTL_PREC_INT16) {  // the 16-bit form is derived below
     I.Zb = static_cast<float*>(own(rows_pad * I.rp * 4));
     I.X = static_cast<float*>(own(N * d * 4));
   } else {
@@ -794,7 +795,7 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
     I.Xh = static_cast<uint16_t*>(own(N * d * 2));
   }
   if (!I.blk_off || !I.grain_rows || !I.blk_grain || !I.rho || !I.blk_rho_min || !I.ids || (I.has_attr && !I.attr_b) ||
-      (precision == HNTL_PREC_FP32 ? (!I.Zb || !I.X) : (!I.Z8b || !I.scale || !I.Xh))) {
+      (precision != HNTL_PREC_BF16_FP8 ? (!I.Zb || !I.X) : (!I.Z8b || !I.scale || !I.Xh))) {
     cleanup();
     return fail(HNTL_ENOMEM, "builder: index allocation failed");
   }
@@ -822,6 +823,47 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   if (e != cudaSuccess) {
     cleanup();
     return fail(HNTL_ECUDA, std::string("builder: ") + cudaGetErrorString(e));
+  }
+  if (precision == HNTL_PREC_INT16) {
+    // the 16-bit form from the FP32 coordinates, by the loader's own quantiser
+    std::vector<float> hz((size_t)N * r), hrho(N);
+    HNTL_CUDA_TRY(cudaMemcpy(hz.data(), Zg, hz.size() * 4, cudaMemcpyDeviceToHost));
+    HNTL_CUDA_TRY(cudaMemcpy(hrho.data(), rho_g, N * 4, cudaMemcpyDeviceToHost));
+    std::vector<uint64_t> go(G + 1);
+    for (uint32_t g = 0; g <= G; ++g) go[g] = h_goff[g];
+    std::vector<float> delta, dres, rho16;
+    std::vector<int16_t> codes;
+    int16_quantize(hz.data(), hrho.data(), go, r, delta, dres, codes, rho16);
+    const int rp = (int)I.rp;
+    std::vector<int16_t> z16(rows_pad * rp, 0);
+    std::vector<float> rho_b(rows_pad, 0.0f);
+    for (uint32_t g = 0; g < G; ++g)
+      for (uint64_t i = 0; i < go[g + 1] - go[g]; ++i) {
+        const uint64_t p = go[g] + i, b = I.h_blk_off[g] + i / kBlockRows, t = i % kBlockRows;
+        for (uint32_t j = 0; j < r; ++j) z16[zoff(b, (int)j, (int)t, rp, 8)] = codes[p * r + j];
+        rho_b[b * kBlockRows + t] = rho16[p];
+      }
+    I.Z16b = static_cast<int16_t*>(own(rows_pad * rp * 2));
+    I.scale = static_cast<float*>(own(G * 4));
+    I.dres = static_cast<float*>(own(G * 4));
+    if (!I.Z16b || !I.scale || !I.dres) {
+      cleanup();
+      return fail(HNTL_ENOMEM, "builder: 16-bit form allocation failed");
+    }
+    HNTL_CUDA_TRY(cudaMemcpy(I.Z16b, z16.data(), z16.size() * 2, cudaMemcpyHostToDevice));
+    HNTL_CUDA_TRY(cudaMemcpy(I.scale, delta.data(), G * 4, cudaMemcpyHostToDevice));
+    HNTL_CUDA_TRY(cudaMemcpy(I.dres, dres.data(), G * 4, cudaMemcpyHostToDevice));
+    HNTL_CUDA_TRY(cudaMemcpy(I.rho, rho_b.data(), rows_pad * 4, cudaMemcpyHostToDevice));
+    if (I.n_blocks)
+      k_block_rho_min<<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(I.rho, I.blk_grain, I.blk_off, I.grain_rows,
+                                                                   (int64_t)I.n_blocks, I.blk_rho_min);
+    I.Zb = nullptr;  // the scan reads the 16-bit codes (the FP32 array stays with the index's allocations)
+    HNTL_CUDA_TRY(cudaGetLastError());
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      cleanup();
+      return fail(HNTL_ECUDA, std::string("builder: ") + cudaGetErrorString(e));
+    }
   }
   return finalize_index(I);
 }

@@ -93,6 +93,15 @@ void release(Index& I);
 // Derived device state after the arrays are in place (both loader and builder call it).
 int finalize_index(Index& I);
 
+// The 16-bit form (Eq. 5) of grain-ordered rows (Z: N x r, rho: N; goff: G + 1
+// grain offsets), in IEEE single precision: per grain the steps
+// delta = fl32(max |z| / 16383) and dres = fl32(max rho / 32767) (1 for a grain
+// of zeros), codes rint(fl32(z / delta)), and rho on its grid,
+// fl32(rint(fl32(rho / dres)) * dres). Host code shared by loader and builder.
+void int16_quantize(const float* Z, const float* rho, const std::vector<uint64_t>& goff, uint32_t r,
+                    std::vector<float>& delta, std::vector<float>& dres, std::vector<int16_t>& codes,
+                    std::vector<float>& rho_q);
+
 // Search internals shared with the router.
 size_t workspace_bytes(const Index& I, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe);
 int route_only(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, void* ws, size_t ws_bytes,

@@ -89,6 +89,33 @@ void free_all(Index& I) {
 
 }  // namespace
 
+void int16_quantize(const float* Z, const float* rho, const std::vector<uint64_t>& goff, uint32_t r,
+                    std::vector<float>& delta, std::vector<float>& dres, std::vector<int16_t>& codes,
+                    std::vector<float>& rho_q) {
+  const uint32_t G = (uint32_t)goff.size() - 1;
+  const uint64_t N = goff[G];
+  delta.assign(G, 1.0f);
+  dres.assign(G, 1.0f);
+  codes.assign(N * r, 0);
+  rho_q.assign(N, 0.0f);
+  for (uint32_t g = 0; g < G; ++g) {
+    float m = 0.0f, mr = 0.0f;
+    for (uint64_t p = goff[g]; p < goff[g + 1]; ++p) {
+      for (uint32_t j = 0; j < r; ++j) m = std::max(m, std::fabs(Z[p * r + j]));
+      mr = std::max(mr, rho[p]);
+    }
+    if (m > 0.0f) delta[g] = m / 16383.0f;
+    if (mr > 0.0f) dres[g] = mr / 32767.0f;
+    for (uint64_t p = goff[g]; p < goff[g + 1]; ++p) {
+      for (uint32_t j = 0; j < r; ++j) {
+        const float c = std::rint(Z[p * r + j] / delta[g]);
+        codes[p * r + j] = (int16_t)std::max(-32767.0f, std::min(32767.0f, c));
+      }
+      rho_q[p] = std::max(0.0f, std::min(65535.0f, std::rint(rho[p] / dres[g]))) * dres[g];
+    }
+  }
+}
+
 int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t precision, Index& I) {
   if (size < kHeaderBytes + 8) return fail(HNTL_EFORMAT, "index file truncated (no header)");
   if (std::memcmp(buf, kMagic, 8) != 0) return fail(HNTL_EFORMAT, "bad magic (not an HNTL index file)");
@@ -206,21 +233,9 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
   std::vector<uint8_t> Z8b(precision == HNTL_PREC_BF16_FP8 ? rows_pad * rp : 0, 0);
   std::vector<int16_t> Z16b(precision == HNTL_PREC_INT16 ? rows_pad * rp : 0, 0);
   std::vector<float> rho_b(rows_pad, 0.0f);
-  // 16-bit form (Eq. 5): per grain the steps delta = fl32(max |z| / 16383) and
-  // dres = fl32(max rho / 32767) (1 for a grain of zeros), codes rint(fl32(v / step));
-  // IEEE single precision throughout, so the codes are the same wherever computed
-  std::vector<float> delta(precision == HNTL_PREC_INT16 ? G : 0, 1.0f), dres(delta.size(), 1.0f);
-  if (precision == HNTL_PREC_INT16) {
-    for (uint32_t g = 0; g < G; ++g) {
-      float m = 0.0f, mr = 0.0f;
-      for (uint64_t p = goff[g]; p < goff[g + 1]; ++p) {
-        for (uint32_t j = 0; j < r; ++j) m = std::max(m, std::fabs(Z[p * r + j]));
-        mr = std::max(mr, rho[p]);
-      }
-      if (m > 0.0f) delta[g] = m / 16383.0f;
-      if (mr > 0.0f) dres[g] = mr / 32767.0f;
-    }
-  }
+  std::vector<float> delta, dres, rho16;
+  std::vector<int16_t> codes16;
+  if (precision == HNTL_PREC_INT16) int16_quantize(Z, rho, goff, r, delta, dres, codes16, rho16);
   std::vector<uint32_t> ids_b(rows_pad, kInvalidId);
   std::vector<int64_t> attr_b(I.has_attr ? rows_pad : 0, 0);
   for (uint32_t g = 0; g < G; ++g) {
@@ -232,14 +247,13 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
         if (precision == HNTL_PREC_FP32) {
           Zb[zoff(b, (int)j, (int)t, rp, V)] = Z[p * r + j];
         } else if (precision == HNTL_PREC_INT16) {
-          const float c = std::rint(Z[p * r + j] / delta[g]);
-          Z16b[zoff(b, (int)j, (int)t, rp, V)] = (int16_t)std::max(-32767.0f, std::min(32767.0f, c));
+          Z16b[zoff(b, (int)j, (int)t, rp, V)] = codes16[p * r + j];
         } else {
           Z8b[zoff(b, (int)j, (int)t, rp, V)] = Z8[p * r + j];
         }
       }
       if (precision == HNTL_PREC_INT16)  // the residual on its grid, as the scan uses it
-        rho_b[b * kBlockRows + t] = std::max(0.0f, std::min(65535.0f, std::rint(rho[p] / dres[g]))) * dres[g];
+        rho_b[b * kBlockRows + t] = rho16[p];
       else
         rho_b[b * kBlockRows + t] = rho[p];
       ids_b[b * kBlockRows + t] = ids[p];

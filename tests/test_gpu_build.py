@@ -115,3 +115,27 @@ def test_small_and_degenerate_grains(hntl):
         np.testing.assert_allclose(U @ U.T, np.eye(8), atol=2e-5)
     assert exp["grain_off"][-1] == len(X)
     assert sorted(exp["ids"].tolist()) == list(range(len(X)))
+
+
+def test_built_int16_form_matches_oracle_quantisation_and_search(hntl, plain10k):
+    """The builder's 16-bit form is the oracle's quantisation (int16_form) of the
+    same build's FP32 coordinates, value for value, and searching it agrees
+    with the oracle's 16-bit search on that index."""
+    X, ora, gi, exp = plain10k
+    w = synth.WORKLOADS["plain-10k"]
+    G, r = w["G"], w["r"]
+    u = synth.uniforms(G, 12345).numpy()
+    gi16 = hntl.Index.build(torch.from_numpy(X).cuda(), G, r, u=u, n_train=len(X), n_seed=len(X), max_iter=25,
+                            seed=3, precision=hntl.PREC_INT16)
+    e16 = gi16.export()
+    np.testing.assert_array_equal(e16["ids"], exp["ids"])  # the same partition and order
+    f = O.int16_form(exp)
+    np.testing.assert_array_equal(e16["Z"], f["Zf32"])
+    np.testing.assert_array_equal(e16["rho"], f["rhof32"])
+    Q, _ = synth.sample_queries(synth.make_cluster_model(w["n"], w["d"], w["n_clusters"], sizes=w["sizes"],
+                                                         seed=w["seed"]), 200, 77)
+    Q = Q.numpy()
+    ids, dist = gi16.search(torch.from_numpy(Q).cuda(), 10, 20, 4)
+    ref = O.search(exp, X, Q, 10, 20, 4, precision="int16")
+    agree = np.mean([len(set(a.tolist()) & set(b.tolist())) / 10 for a, b in zip(ids.cpu().numpy(), ref["out_id"])])
+    assert agree > 0.99, agree
