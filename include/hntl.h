@@ -51,9 +51,10 @@ extern "C" {
  * dres_g = fl32(max rho / 32767) (rows use half of each 16-bit range),
  * int16 coordinates rint(fl32(z / delta_g)) and uint16 residual norms
  * rint(fl32(rho / dres_g)), all in IEEE single precision; queries are
- * quantised with the same steps (saturating), and a grain where more than a
- * quarter of a query's coordinates saturate is left out of that query's scan
- * (the Quantization Envelope Filter, sec. 2.3). FP32 raw rows for the rerank. */
+ * quantised with the same steps (saturating), and a grain is left out of a
+ * query's scan when more than a quarter of the query's coordinates saturate
+ * (the Quantization Envelope Filter, sec. 2.3) or its residual norm does.
+ * FP32 raw rows for the rerank. Mode A is not available for this form. */
 #define HNTL_PREC_FP32 0
 #define HNTL_PREC_BF16_FP8 1
 #define HNTL_PREC_INT16 2

@@ -349,9 +349,11 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
         for (int64_t t = 0; t < d; ++t) rho_q += e[t] * e[t];
         if (qdelta) {
           /* 16-bit form (Eq. 5): the query's coordinates and residual norm are
-           * quantised with the grain's steps; a coordinate beyond the signed
-           * 16-bit range saturates, and a grain where more than a quarter of
-           * them saturate is left out (Quantization Envelope Filter, sec. 2.3) */
+           * quantised with the grain's steps; a value beyond its 16-bit range
+           * saturates. The grain is left out when more than a quarter of the
+           * coordinates saturate (Quantization Envelope Filter, sec. 2.3) or
+           * when the residual norm does (the same test on the out-of-subspace
+           * energy: more than twice any of the grain's rows) */
           int64_t sat = 0;
           for (int64_t j = 0; j < r; ++j) {
             double t = rint(zq[j] / qdelta[g]);
@@ -362,8 +364,8 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
             zq[j] = t * qdelta[g];
           }
           if (4 * sat > r) continue;
-          double tr = rint(rho_q / qdres[g]);
-          if (tr > 65535.0) tr = 65535.0;
+          const double tr = rint(rho_q / qdres[g]);
+          if (tr > 65535.0) continue;
           rho_q = tr * qdres[g];
         }
         for (int64_t i = grain_off[g]; i < grain_off[g + 1]; ++i) {

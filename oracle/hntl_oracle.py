@@ -227,7 +227,8 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
     precision="int16": the paper's 16-bit form (Eq. 5): rows on their grain's
     16-bit grids (int16_form), the query's coordinates and residual norm
     quantised with the same steps, and a grain left out of a query's scan when
-    more than a quarter of its coordinates saturate (sec. 2.3).
+    more than a quarter of its coordinates saturate (sec. 2.3) or its residual
+    norm does.
     precision="bf16-fp8": the precision form, defined on rounded inputs: the
     query, centres and bases are rounded to BF16 for routing and projection,
     the scan reads the FP8 coordinates decoded and scaled (fp8_coords), and the

@@ -83,32 +83,32 @@ __global__ void k_probe_dist(const float* __restrict__ Q, const float* __restric
 
 // ------------------------------------------------------------------ 16-bit form
 
-// The 16-bit form's query side (Eq. 5, sec. 2.3), one CTA per grain over its
-// (query, grain) pairs: each coordinate of z_q is put on the grain's grid
-// (rint(fl32(z / delta_g)), saturating at +-32767) and replaced by its grid
-// value; a pair with more than a quarter of its coordinates saturated is left
-// out (rho_q = +inf, so every downstream stage drops its rows); otherwise
-// rho_q goes on the residual grid (saturating at 65535 steps).
+// The 16-bit form's query side (Eq. 5, sec. 2.3), one CTA per grain, one warp
+// per (query, grain) pair, lanes over coordinates: each coordinate of z_q is
+// put on the grain's grid (rint(fl32(z / delta_g)), saturating at +-32767) and
+// replaced by its grid value, and rho_q likewise on the residual grid. A pair
+// is left out (rho_q = +inf, so every downstream stage drops its rows) when
+// more than a quarter of its coordinates saturate or its residual norm does
+// (beyond 65535 steps: twice any row of the grain).
 __global__ void k_quant_pairs(const uint32_t* __restrict__ pair_off, int r, const float* __restrict__ delta,
                               const float* __restrict__ dres, float* __restrict__ zq, float* __restrict__ rhoq) {
   const uint32_t g = blockIdx.x, p0 = pair_off[g], p1 = pair_off[g + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const float dl = delta[g], dr = dres[g];
-  for (uint32_t pr = p0 + threadIdx.x; pr < p1; pr += blockDim.x) {
+  for (uint32_t pr = p0 + warp; pr < p1; pr += nw) {
     float* z = zq + (size_t)pr * r;
     int sat = 0;
-    for (int j = 0; j < r; ++j) {
-      float t = rintf(z[j] / dl);
-      if (fabsf(t) > 32767.f) {
-        ++sat;
-        t = t > 0.f ? 32767.f : -32767.f;
-      }
-      z[j] = t * dl;
+    for (int j0 = 0; j0 < r; j0 += 32) {  // r <= 64
+      const int j = j0 + lane;
+      float t = 0.f;
+      if (j < r) t = rintf(z[j] / dl);
+      const bool s = j < r && fabsf(t) > 32767.f;
+      sat += __popc(__ballot_sync(0xffffffffu, s));
+      if (j < r) z[j] = fmaxf(-32767.f, fminf(32767.f, t)) * dl;
     }
-    if (4 * sat > r) {
-      rhoq[pr] = INFINITY;
-    } else {
-      const float tr = fminf(rintf(rhoq[pr] / dr), 65535.f);
-      rhoq[pr] = tr * dr;
+    if (lane == 0) {
+      const float tr = rintf(rhoq[pr] / dr);
+      rhoq[pr] = (4 * sat > r || tr > 65535.f) ? INFINITY : tr * dr;
     }
   }
 }

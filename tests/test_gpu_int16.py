@@ -168,3 +168,25 @@ def test_int16_filters(hntl, tmp_path):
     _, gpu = run(hntl, p, Q, 10, 50, 3, filters=ranges)
     st = compare_int16(gpu, ora, nxt, idx, len(X), 10, 50, 3)
     assert st["checked"] >= 0.85 * len(Q), st
+
+
+def test_int16_envelope_filter_drops_a_grain_on_residual_saturation(hntl, tmp_path):
+    """Grain B varies only inside its own subspace; the queries sit off it: their
+    coordinates in B's frame stay in range but the residual norm saturates, and
+    B's rows stay out of the pool."""
+    rng = np.random.default_rng(19)
+    A = rng.standard_normal((50, 8))
+    B = np.zeros((50, 8))
+    B[:, :4] = rng.standard_normal((50, 4))
+    B[:, 4:] = 20.0 + 1e-3 * rng.standard_normal((50, 4))
+    X = np.concatenate([A, B]).astype(np.float32)
+    idx = partition_index(X, np.repeat([0, 1], 50), 2, 4)
+    Q = (0.1 * rng.standard_normal((3, 8))).astype(np.float32)
+    p = write(tmp_path, "i16res", idx, X)
+    ora = O.search(idx, X, Q, 10, 80, 2, precision="int16")
+    _, gpu = run(hntl, p, Q, 10, 80, 2)
+    for qi in range(3):
+        ids = gpu["pool_ids"][qi]
+        assert set(ids[ids != 0xFFFFFFFF].tolist()) == set(range(50)) == set(
+            ora["cand_id"][qi][ora["cand_id"][qi] != 0xFFFFFFFF].tolist())
+        np.testing.assert_array_equal(gpu["ids"][qi], ora["out_id"][qi])

@@ -347,6 +347,31 @@ def test_int16_envelope_filter_drops_a_far_grain():
         assert (ids == 0xFFFFFFFF).sum() == 30
 
 
+def test_int16_envelope_filter_drops_a_grain_on_residual_saturation():
+    """Grain B varies only inside its own 4-dimensional subspace; a query near
+    grain A projects into B's frame with coordinates inside B's range (no
+    coordinate saturates) but with a residual norm far beyond any of B's rows:
+    that saturation leaves B out of the 16-bit form's pool."""
+    rng = np.random.default_rng(19)
+    A = rng.standard_normal((50, 8))
+    B = np.zeros((50, 8))
+    B[:, :4] = rng.standard_normal((50, 4))
+    B[:, 4:] = 20.0 + 1e-3 * rng.standard_normal((50, 4))
+    X = np.concatenate([A, B]).astype(np.float32)
+    idx = partition_index(X, np.repeat([0, 1], 50), 2, 4)
+    Q = (0.1 * rng.standard_normal((3, 8))).astype(np.float32)
+    f = O.int16_form(idx)
+    for q in Q:  # the premise: no coordinate of the query saturates in B's frame
+        zq = idx["U"][1].astype(np.float64) @ (q - idx["M"][1].astype(np.float64))
+        assert np.abs(zq).max() < 32767 * float(f["delta"][1])
+    f32 = O.search(idx, X, Q, 10, 80, 2, precision="fp32")
+    i16 = O.search(idx, X, Q, 10, 80, 2, precision="int16")
+    for qi in range(3):
+        assert (f32["cand_id"][qi] >= 50).sum() == 30
+        ids = i16["cand_id"][qi]
+        assert set(ids[ids != 0xFFFFFFFF].tolist()) == set(range(50))
+
+
 def test_int16_distances_within_quantisation_bound():
     """Each coordinate of a query or row moves by at most half a step, so a
     pool distance of the 16-bit form differs from the FP32 form's by at most
