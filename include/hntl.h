@@ -48,7 +48,8 @@ extern "C" {
  * BF16_FP8: BF16 raw rows, FP8-E4M3 coordinates with a per-grain FP32 scale.
  * INT16: the paper's 16-bit form (Eq. 5), built at load from an FP32 file:
  * per grain the steps delta_g = fl32(max |z| / 16383) and
- * dres_g = fl32(max rho / 32767) (rows use half of each 16-bit range),
+ * dres_g = fl32(max(max rho, fl32(max|z|^2) 2^-20) / 32767) (rows use at most
+ * half of each 16-bit range),
  * int16 coordinates rint(fl32(z / delta_g)) and uint16 residual norms
  * rint(fl32(rho / dres_g)), all in IEEE single precision; queries are
  * quantised with the same steps (saturating), and a grain is left out of a

@@ -289,8 +289,10 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
 
 def int16_form(idx):
     """The paper's 16-bit form of the stored rows (Eq. 5), per grain g:
-    delta_g = fl32(max |z| / 16383) and dres_g = fl32(max rho / 32767) (1 for a
-    grain whose values are all zero), so the rows use half of the signed and
+    delta_g = fl32(max |z| / 16383) and dres_g = fl32(R / 32767) with
+    R = max(max rho, fl32(max|z|^2) 2^-20) (a residual grid no finer than FP32
+    can resolve next to the coordinates' energy; 1 for a grain whose values
+    are all zero), so the rows use at most half of the signed and
     unsigned 16-bit ranges and a query's values up to twice the grain's extent
     stay representable (the paper leaves the steps open; saturation, which the
     envelope filter counts, then means a query well outside the grain); codes
@@ -312,7 +314,7 @@ def int16_form(idx):
             m = np.max(np.abs(Z[a:b])) if Z.shape[1] else np.float32(0)
             if m > 0:
                 delta[g] = np.float32(m) / np.float32(16383)
-            mr = np.max(rho[a:b])
+            mr = max(np.float32(np.max(rho[a:b])), np.float32(np.float32(m) * np.float32(m)) * np.float32(2.0 ** -20))
             if mr > 0:
                 dres[g] = np.float32(mr) / np.float32(32767)
             codes[a:b] = np.clip(np.rint(Z[a:b] / delta[g]), -32767, 32767).astype(np.int16)

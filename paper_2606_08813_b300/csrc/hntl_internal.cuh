@@ -95,8 +95,9 @@ int finalize_index(Index& I);
 
 // The 16-bit form (Eq. 5) of grain-ordered rows (Z: N x r, rho: N; goff: G + 1
 // grain offsets), in IEEE single precision: per grain the steps
-// delta = fl32(max |z| / 16383) and dres = fl32(max rho / 32767) (1 for a grain
-// of zeros), codes rint(fl32(z / delta)), and rho on its grid,
+// delta = fl32(max |z| / 16383) and dres = fl32(R / 32767) with
+// R = max(max rho, fl32(max|z|^2) 2^-20) (1 for a grain of zeros), codes
+// rint(fl32(z / delta)), and rho on its grid,
 // fl32(rint(fl32(rho / dres)) * dres). Host code shared by loader and builder.
 void int16_quantize(const float* Z, const float* rho, const std::vector<uint64_t>& goff, uint32_t r,
                     std::vector<float>& delta, std::vector<float>& dres, std::vector<int16_t>& codes,

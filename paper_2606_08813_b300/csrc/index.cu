@@ -104,6 +104,7 @@ void int16_quantize(const float* Z, const float* rho, const std::vector<uint64_t
       for (uint32_t j = 0; j < r; ++j) m = std::max(m, std::fabs(Z[p * r + j]));
       mr = std::max(mr, rho[p]);
     }
+    mr = std::max(mr, (m * m) * 0x1p-20f);  // no finer than FP32 resolves next to the coordinates' energy
     if (m > 0.0f) delta[g] = m / 16383.0f;
     if (mr > 0.0f) dres[g] = mr / 32767.0f;
     for (uint64_t p = goff[g]; p < goff[g + 1]; ++p) {
