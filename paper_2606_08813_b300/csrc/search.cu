@@ -83,33 +83,36 @@ __global__ void k_probe_dist(const float* __restrict__ Q, const float* __restric
 
 // ------------------------------------------------------------------ 16-bit form
 
-// The 16-bit form's query side (Eq. 5, sec. 2.3), one CTA per grain, one warp
-// per (query, grain) pair, lanes over coordinates: each coordinate of z_q is
-// put on the grain's grid (rint(fl32(z / delta_g)), saturating at +-32767) and
-// replaced by its grid value, and rho_q likewise on the residual grid. A pair
-// is left out (rho_q = +inf, so every downstream stage drops its rows) when
-// more than a quarter of its coordinates saturate or its residual norm does
-// (beyond 65535 steps: twice any row of the grain).
-__global__ void k_quant_pairs(const uint32_t* __restrict__ pair_off, int r, const float* __restrict__ delta,
-                              const float* __restrict__ dres, float* __restrict__ zq, float* __restrict__ rhoq) {
-  const uint32_t g = blockIdx.x, p0 = pair_off[g], p1 = pair_off[g + 1];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+// The 16-bit form's query side (Eq. 5, sec. 2.3), one warp per (query, grain)
+// pair over the whole batch (a grain probed by many queries does not
+// serialise), lanes over coordinates: each coordinate of z_q is put on the
+// grain's grid (rint(fl32(z / delta_g)), saturating at +-32767) and replaced
+// by its grid value, and rho_q likewise on the residual grid. A pair is left
+// out (rho_q = +inf, so every downstream stage drops its rows) when more than
+// a quarter of its coordinates saturate or its residual norm does (beyond
+// 65535 steps: twice any row of the grain).
+__global__ void k_quant_pairs(uint32_t P, int nprobe, const int32_t* __restrict__ probe,
+                              const uint32_t* __restrict__ pair_q, const uint32_t* __restrict__ pair_p, int r,
+                              const float* __restrict__ delta, const float* __restrict__ dres, float* __restrict__ zq,
+                              float* __restrict__ rhoq) {
+  const uint32_t pr = (uint32_t)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (pr >= P) return;
+  const int g = probe[(size_t)pair_q[pr] * nprobe + pair_p[pr]];
   const float dl = delta[g], dr = dres[g];
-  for (uint32_t pr = p0 + warp; pr < p1; pr += nw) {
-    float* z = zq + (size_t)pr * r;
-    int sat = 0;
-    for (int j0 = 0; j0 < r; j0 += 32) {  // r <= 64
-      const int j = j0 + lane;
-      float t = 0.f;
-      if (j < r) t = rintf(z[j] / dl);
-      const bool s = j < r && fabsf(t) > 32767.f;
-      sat += __popc(__ballot_sync(0xffffffffu, s));
-      if (j < r) z[j] = fmaxf(-32767.f, fminf(32767.f, t)) * dl;
-    }
-    if (lane == 0) {
-      const float tr = rintf(rhoq[pr] / dr);
-      rhoq[pr] = (4 * sat > r || tr > 65535.f) ? INFINITY : tr * dr;
-    }
+  float* z = zq + (size_t)pr * r;
+  int sat = 0;
+  for (int j0 = 0; j0 < r; j0 += 32) {  // r <= 64
+    const int j = j0 + lane;
+    float t = 0.f;
+    if (j < r) t = rintf(z[j] / dl);
+    const bool s = j < r && fabsf(t) > 32767.f;
+    sat += __popc(__ballot_sync(0xffffffffu, s));
+    if (j < r) z[j] = fmaxf(-32767.f, fminf(32767.f, t)) * dl;
+  }
+  if (lane == 0) {
+    const float tr = rintf(rhoq[pr] / dr);
+    rhoq[pr] = (4 * sat > r || tr > 65535.f) ? INFINITY : tr * dr;
   }
 }
 
@@ -575,7 +578,8 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
     k_project<false><<<grid, 256, smem, st>>>(Qd, I.M, I.U, (int)I.d, (int)I.r, (int)I.G, w.grp_off, w.pair_off,
                                               w.pair_q, w.zq, w.rhoq);
     if (I.precision == HNTL_PREC_INT16)
-      k_quant_pairs<<<I.G, 128, 0, st>>>(w.pair_off, (int)I.r, I.scale, I.dres, w.zq, w.rhoq);
+      k_quant_pairs<<<(unsigned)(((size_t)P * 32 + 255) / 256), 256, 0, st>>>(
+          (uint32_t)P, (int)nprobe, w.probe, w.pair_q, w.pair_p, (int)I.r, I.scale, I.dres, w.zq, w.rhoq);
   }
   mark(3);
   HNTL_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * ((size_t)nq + 5), st));
