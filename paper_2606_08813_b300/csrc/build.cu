@@ -424,7 +424,7 @@ __global__ void k_relayout(int64_t N, int r, int rp, int G, const uint32_t* __re
                            const float* __restrict__ Zg, const float* __restrict__ rho_g,
                            const int64_t* __restrict__ attr, const float* __restrict__ scale, float* __restrict__ Zb,
                            uint8_t* __restrict__ Z8b, float* __restrict__ rho_b, uint32_t* __restrict__ ids_b,
-                           int64_t* __restrict__ attr_b) {
+                           int64_t* __restrict__ attr_b, const uint32_t* __restrict__ slot) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   int lo = 0, hi = G;  // largest g with goff[g] <= p
@@ -434,7 +434,7 @@ __global__ void k_relayout(int64_t N, int r, int rp, int G, const uint32_t* __re
     else hi = mid;
   }
   const int g = lo;
-  const uint32_t i = (uint32_t)p - goff[g];
+  const uint32_t i = slot[p];  // the row's place within its grain (rows ordered by first coordinate)
   const size_t b = blk_off[g] + i / kBlockRows, t = i % kBlockRows;
   for (int j = 0; j < r; ++j) {
     float z = Zg[(size_t)p * r + j];
@@ -810,9 +810,28 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
     HNTL_CUDA_TRY(cudaMemsetAsync(I.Z8b, 0, rows_pad * I.rp, st));
     k_grain_absmax<<<G, 256, 0, st>>>(Zg, goff, (int)r, I.scale);
   }
-  k_relayout<<<(unsigned)((N + 255) / 256), 256, 0, st>>>((int64_t)N, (int)r, (int)I.rp, (int)G, goff, I.blk_off, ids_g, Zg,
-                                                          rho_g, P.d_attr, I.scale, I.Zb, I.Z8b, I.rho, I.ids,
-                                                          I.attr_b);
+  // within a grain, rows go to blocks in order of their first coordinate (the scan's interval bound)
+  std::vector<uint64_t> order;
+  {
+    std::vector<float> z0(N);
+    HNTL_CUDA_TRY(cudaStreamSynchronize(st));
+    HNTL_CUDA_TRY(cudaMemcpy2D(z0.data(), 4, Zg, (size_t)r * 4, 4, N, cudaMemcpyDeviceToHost));
+    std::vector<uint64_t> go(G + 1);
+    for (uint32_t g = 0; g <= G; ++g) go[g] = h_goff[g];
+    order = rows_by_first_coord(z0.data(), 1, h_ids.data(), go);
+    std::vector<uint32_t> h_slot(N);
+    for (uint32_t g = 0; g < G; ++g)
+      for (uint64_t i = go[g]; i < go[g + 1]; ++i) h_slot[order[i]] = (uint32_t)(i - go[g]);
+    uint32_t* slot = T.get<uint32_t>(N, &rc);
+    if (rc) {
+      cleanup();
+      return rc;
+    }
+    HNTL_CUDA_TRY(cudaMemcpy(slot, h_slot.data(), N * 4, cudaMemcpyHostToDevice));
+    k_relayout<<<(unsigned)((N + 255) / 256), 256, 0, st>>>((int64_t)N, (int)r, (int)I.rp, (int)G, goff, I.blk_off,
+                                                            ids_g, Zg, rho_g, P.d_attr, I.scale, I.Zb, I.Z8b, I.rho,
+                                                            I.ids, I.attr_b, slot);
+  }
   if (I.n_blocks)
     k_block_rho_min<<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(I.rho, I.blk_grain, I.blk_off, I.grain_rows,
                                                                  (int64_t)I.n_blocks, I.blk_rho_min);
@@ -839,7 +858,7 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
     std::vector<float> rho_b(rows_pad, 0.0f);
     for (uint32_t g = 0; g < G; ++g)
       for (uint64_t i = 0; i < go[g + 1] - go[g]; ++i) {
-        const uint64_t p = go[g] + i, b = I.h_blk_off[g] + i / kBlockRows, t = i % kBlockRows;
+        const uint64_t p = order[go[g] + i], b = I.h_blk_off[g] + i / kBlockRows, t = i % kBlockRows;
         for (uint32_t j = 0; j < r; ++j) z16[zoff(b, (int)j, (int)t, rp, 8)] = codes[p * r + j];
         rho_b[b * kBlockRows + t] = rho16[p];
       }

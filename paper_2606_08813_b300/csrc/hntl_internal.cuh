@@ -60,6 +60,7 @@ struct Index {
   float* dres = nullptr;         // [G] the 16-bit form's residual step per grain
   float* rho = nullptr;          // [n_blocks][128] residual norms
   float* blk_rho_min = nullptr;  // [n_blocks] smallest residual norm of a block's real rows (+inf if none)
+  float2* blk_z0 = nullptr;      // [n_blocks] [min, max] of the decoded first coordinate of a block's real rows
   float* crow = nullptr;         // [n_blocks][128] ||z_i||^2 + rho_i of the decoded row (precision form)
   float* grain_rho_min = nullptr;  // [G] smallest residual norm of a grain's rows (precision form)
   uint32_t* ids = nullptr;       // [n_blocks][128] original ids
@@ -92,6 +93,12 @@ void release(Index& I);
 
 // Derived device state after the arrays are in place (both loader and builder call it).
 int finalize_index(Index& I);
+
+// Grain-ordered row positions, each grain's rows sorted by (first coordinate,
+// id): the order in which they are laid out into blocks (host code shared by
+// loader and builder). Z: N x r grain-ordered; ids: their ids.
+std::vector<uint64_t> rows_by_first_coord(const float* Z, uint32_t r, const uint32_t* ids,
+                                          const std::vector<uint64_t>& goff);
 
 // The 16-bit form (Eq. 5) of grain-ordered rows (Z: N x r, rho: N; goff: G + 1
 // grain offsets), in IEEE single precision: per grain the steps

@@ -117,6 +117,20 @@ void int16_quantize(const float* Z, const float* rho, const std::vector<uint64_t
   }
 }
 
+std::vector<uint64_t> rows_by_first_coord(const float* Z, uint32_t r, const uint32_t* ids,
+                                          const std::vector<uint64_t>& goff) {
+  const uint32_t G = (uint32_t)goff.size() - 1;
+  std::vector<uint64_t> order(goff[G]);
+  for (uint64_t p = 0; p < goff[G]; ++p) order[p] = p;
+  for (uint32_t g = 0; g < G; ++g)
+    std::sort(order.begin() + (ptrdiff_t)goff[g], order.begin() + (ptrdiff_t)goff[g + 1],
+              [&](uint64_t a, uint64_t b) {
+                const float za = Z[a * r], zb = Z[b * r];
+                return za < zb || (za == zb && ids[a] < ids[b]);
+              });
+  return order;
+}
+
 int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t precision, Index& I) {
   if (size < kHeaderBytes + 8) return fail(HNTL_EFORMAT, "index file truncated (no header)");
   if (std::memcmp(buf, kMagic, 8) != 0) return fail(HNTL_EFORMAT, "bad magic (not an HNTL index file)");
@@ -239,10 +253,13 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
   if (precision == HNTL_PREC_INT16) int16_quantize(Z, rho, goff, r, delta, dres, codes16, rho16);
   std::vector<uint32_t> ids_b(rows_pad, kInvalidId);
   std::vector<int64_t> attr_b(I.has_attr ? rows_pad : 0, 0);
+  // within a grain, rows go to blocks in order of their first coordinate, so a
+  // block spans a short interval of it (the scan's interval bound)
+  const std::vector<uint64_t> order = rows_by_first_coord(Z, r, ids.data(), goff);
   for (uint32_t g = 0; g < G; ++g) {
     for (uint32_t b = I.h_blk_off[g]; b < I.h_blk_off[g + 1]; ++b) blk_grain[b] = g;
     for (uint64_t i = 0; i < grain_rows[g]; ++i) {
-      uint64_t p = goff[g] + i;
+      uint64_t p = order[goff[g] + i];
       uint64_t b = I.h_blk_off[g] + i / kBlockRows, t = i % kBlockRows;
       for (uint32_t j = 0; j < r; ++j) {
         if (precision == HNTL_PREC_FP32) {

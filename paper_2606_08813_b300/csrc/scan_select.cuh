@@ -132,6 +132,50 @@ __device__ __forceinline__ void load_row(const Coords& c, int rp, float s_g, siz
   }
 }
 
+// ------------------------------------------------------------------ block interval bound
+
+// Rows are laid out in each grain by their first coordinate, so a block's
+// decoded first coordinates span a short interval [lo, hi]. For a row of the
+// block, D >= (z_q0 - z_i0)^2 + rho_q + rho_i >= gap^2 + rho_q + min rho, with
+// gap the distance from z_q0 to the interval; the scan's FP32 D is at least
+// (1 - 2^-18) of that exact value, so with a 2^-16 margin on the left a block
+// for which this returns true has no row with D <= tau (the survivors are the
+// same as without the bound).
+__device__ __forceinline__ bool interval_prunes(float zq0, float2 iv, float rho_q, float rmin, float tau) {
+  const float gap = fmaxf(fmaxf(iv.x - zq0, zq0 - iv.y), 0.f);
+  return (rho_q + rmin + gap * gap) * (1.f - 0x1p-16f) > tau;
+}
+
+// [min, max] of the decoded first coordinate of each block's real rows
+// ([+inf, -inf] for a block without rows), one CTA of 128 threads per block.
+template <int RT, int kC>
+__global__ void __launch_bounds__(kBlockRows) k_block_z0(const Coords cz, const uint32_t* __restrict__ blk_grain,
+                                                         const uint32_t* __restrict__ blk_off,
+                                                         const uint32_t* __restrict__ grain_rows, int rp,
+                                                         float2* __restrict__ out) {
+  __shared__ float s_lo[4], s_hi[4];
+  const size_t b = blockIdx.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint32_t g = blk_grain[b];
+  const bool valid = (uint32_t)(b - blk_off[g]) * kBlockRows + t < grain_rows[g];
+  float z[RT];
+  load_row<RT, kC>(cz, rp, kC != kCoordF32 ? cz.scale[g] : 1.f, b, t, z);
+  float lo = valid ? z[0] : INFINITY, hi = valid ? z[0] : -INFINITY;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if (lane == 0) {
+    s_lo[warp] = lo;
+    s_hi[warp] = hi;
+  }
+  __syncthreads();
+  if (t == 0)
+    out[b] = make_float2(fminf(fminf(s_lo[0], s_lo[1]), fminf(s_lo[2], s_lo[3])),
+                         fmaxf(fmaxf(s_hi[0], s_hi[1]), fmaxf(s_hi[2], s_hi[3])));
+}
+
 // ------------------------------------------------------------------ pilot
 
 template <int RT, int kC>
@@ -257,8 +301,8 @@ __global__ void __launch_bounds__(kBlockRows) k_scan_filter(
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r, int rp,
     const uint32_t* __restrict__ gcnt, const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ pair_q,
     const float* __restrict__ zq, const float* __restrict__ rhoq, const float* __restrict__ tau,
-    const float* __restrict__ blk_rho_min, const int64_t* __restrict__ filter, uint32_t cap,
-    uint32_t* __restrict__ cnt, unsigned long long* __restrict__ surv) {
+    const float* __restrict__ blk_rho_min, const float2* __restrict__ blk_z0, const int64_t* __restrict__ filter,
+    uint32_t cap, uint32_t* __restrict__ cnt, unsigned long long* __restrict__ surv) {
   constexpr int kChunk = 32;
   __shared__ __align__(8) float sz[kChunk][RT];
   __shared__ float srho[kChunk], stau[kChunk];
@@ -276,8 +320,10 @@ __global__ void __launch_bounds__(kBlockRows) k_scan_filter(
   // the pairs of this grain that can still reach their pool from this block
   if (t == 0) s_nneed = 0;
   __syncthreads();
+  const float2 iv = blk_z0[b];
   for (uint32_t s = t; s < m; s += kBlockRows) {
-    if (rhoq[p_begin + s] + rmin <= tau[pair_q[p_begin + s]]) {
+    const float rq = rhoq[p_begin + s], tq = tau[pair_q[p_begin + s]];
+    if (rq + rmin <= tq && !interval_prunes(zq[(size_t)(p_begin + s) * r], iv, rq, rmin, tq)) {
       const uint32_t pos = atomicAdd(&s_nneed, 1u);
       if (pos < (uint32_t)kMaxNeed) s_need[pos] = s;
     }

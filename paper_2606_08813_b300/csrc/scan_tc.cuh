@@ -137,15 +137,21 @@ __global__ void k_scan_classify(const uint4* __restrict__ items, const uint32_t*
                                 const uint32_t* __restrict__ need_cnt, const uint32_t* __restrict__ need_list,
                                 const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ pair_q,
                                 const float* __restrict__ rhoq, const float* __restrict__ tau,
-                                const float* __restrict__ blk_rho_min, uint4* __restrict__ dense,
+                                const float* __restrict__ blk_rho_min, const float2* __restrict__ blk_z0,
+                                const float* __restrict__ zq, int r, uint4* __restrict__ dense,
                                 SparseRec* __restrict__ sparse, uint32_t n_cap, uint32_t* __restrict__ lists) {
   const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= *n_items) return;
   const uint4 item = items[w];
   float v = (uint32_t)lane < item.z ? blk_rho_min[item.y + lane] : INFINITY;
+  float2 iv = (uint32_t)lane < item.z ? blk_z0[item.y + lane] : make_float2(INFINITY, -INFINITY);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    iv.x = fminf(iv.x, __shfl_xor_sync(0xffffffffu, iv.x, o));
+    iv.y = fmaxf(iv.y, __shfl_xor_sync(0xffffffffu, iv.y, o));
+  }
   const uint32_t m = need_cnt[item.x], p0 = pair_off[item.x];
   uint32_t n = 0, mine = 0xFFFFFFFFu;  // lane i < n keeps the i-th live pair
   for (uint32_t s0 = 0; s0 < m && n < (uint32_t)kSTDense; s0 += 32) {
@@ -154,7 +160,8 @@ __global__ void k_scan_classify(const uint4* __restrict__ items, const uint32_t*
     uint32_t pr = 0;
     if (s < m) {
       pr = p0 + need_list[p0 + s];
-      need = rhoq[pr] + v <= tau[pair_q[pr]];
+      const float rq = rhoq[pr], tq = tau[pair_q[pr]];
+      need = rq + v <= tq && !interval_prunes(zq[(size_t)pr * r], iv, rq, v, tq);
     }
     const unsigned mask = __ballot_sync(0xffffffffu, need);
     const uint32_t slot = n + __popc(mask & ((1u << lane) - 1u));
@@ -193,8 +200,9 @@ __global__ void __launch_bounds__(kSPThreads, 6) k_scan_sparse(
     const uint32_t* __restrict__ grain_rows, const uint8_t* __restrict__ Z8b, const float* __restrict__ scale,
     const float* __restrict__ rho, const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r,
     int rp, const uint32_t* __restrict__ pair_q, const float* __restrict__ zq, const float* __restrict__ rhoq,
-    const float* __restrict__ tau, const float* __restrict__ blk_rho_min, const int64_t* __restrict__ filter,
-    uint32_t cap, uint32_t* __restrict__ cnt, unsigned long long* __restrict__ surv) {
+    const float* __restrict__ tau, const float* __restrict__ blk_rho_min, const float2* __restrict__ blk_z0,
+    const int64_t* __restrict__ filter, uint32_t cap, uint32_t* __restrict__ cnt,
+    unsigned long long* __restrict__ surv) {
   constexpr int kL = RT / 16;
   constexpr int kP = kSTDense - 1;  // at most this many live pairs per item
   __shared__ __align__(16) float sz[kP][RT];
@@ -276,9 +284,11 @@ __global__ void __launch_bounds__(kSPThreads, 6) k_scan_sparse(
         }
       }
       const float rho_i = rho_cur, rmin = rmin_cur;
+      const float2 iv = blk_z0[b];
       for (int j = 0; j < np; ++j) {
         const float4 pc = spc[j];
-        if (pc.w + rmin > pc.z) continue;  // block-uniform: no row of this block reaches the pool
+        // block-uniform: no row of this block reaches the pool
+        if (pc.w + rmin > pc.z || interval_prunes(sz[j][0], iv, pc.w, rmin, pc.z)) continue;
         const float D = eval_D<RT>(&sz[j][0], z, pc.w, rho_i);
         bool ok = valid && D <= pc.z;
         if (ok && filter) {

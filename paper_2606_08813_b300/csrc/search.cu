@@ -446,11 +446,11 @@ void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, 
                                         w.need_cnt);
     k_scan_classify<<<(unsigned)((max_items * 32 + 255) / 256), 256, 0, st>>>(
         w.scan_items, w.scan_off + I.G, w.need_cnt, w.need_list, w.pair_off, w.pair_q, w.rhoq, w.tau, I.blk_rho_min,
-        w.dense_items, w.sparse_items, (uint32_t)max_items, lists);
+        I.blk_z0, w.zq, (int)I.r, w.dense_items, w.sparse_items, (uint32_t)max_items, lists);
     k_scan_sparse<RT><<<(unsigned)std::min<size_t>(max_items, (size_t)I.num_sms * 6), kSPThreads, 0, st>>>(
         w.sparse_items, (uint32_t)max_items, lists, lists + 2, I.blk_off, I.grain_rows, I.Z8b, I.scale, I.rho, I.ids, I.attr_b, (int)I.r,
         (int)I.rp,
-        w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap, w.cnt, w.surv);
+        w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, I.blk_z0, filter, w.cap, w.cnt, w.surv);
     k_scan_tc<RT><<<(unsigned)std::min<size_t>(max_items, (size_t)I.num_sms * 2), kSTThreads, ScanTc<RT>::kSmem,
                     st>>>(
         w.dense_items, lists, w.cnt + nq, I.blk_off, I.grain_rows, I.Z8b, I.scale, I.crow, I.rho, I.ids, I.attr_b,
@@ -459,7 +459,7 @@ void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, 
   } else {
     k_scan_filter<RT, kC><<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(
         I.blk_grain, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b, (int)I.r, (int)I.rp, w.gcnt, w.pair_off,
-        w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, filter, w.cap, w.cnt, w.surv);
+        w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, I.blk_z0, filter, w.cap, w.cnt, w.surv);
   }
   mark(5);
   k_final_select<RT, kC, false><<<nq, kFinalThreads, 0, st>>>(
@@ -686,13 +686,14 @@ int finalize_index(Index& I) {
   I.gram = static_cast<float*>(alloc(sizeof(float) * I.G * I.r * I.r));
   I.pos_of_id = static_cast<uint32_t*>(alloc(sizeof(uint32_t) * std::max<uint64_t>(I.n, 1)));
   I.hrow = static_cast<float*>(alloc(sizeof(float) * I.n_blocks * kBlockRows));
+  I.blk_z0 = static_cast<float2*>(alloc(sizeof(float2) * std::max<uint64_t>(I.n_blocks, 1)));
   if (bf16) {
     I.Mh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.d));
     I.Uh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.r * I.d));
     I.crow = static_cast<float*>(alloc(sizeof(float) * I.n_blocks * kBlockRows));
     I.grain_rho_min = static_cast<float*>(alloc(sizeof(float) * I.G));
   }
-  if (!I.d_err || !I.mnorm || !I.gram || !I.pos_of_id || !I.hrow ||
+  if (!I.d_err || !I.mnorm || !I.gram || !I.pos_of_id || !I.hrow || !I.blk_z0 ||
       (bf16 && (!I.Mh || !I.Uh || !I.crow || !I.grain_rho_min)))
     return fail(HNTL_ENOMEM, "index: derived arrays");
   HNTL_CUDA_TRY(cudaMemset(I.d_err, 0, sizeof(int)));
@@ -709,6 +710,28 @@ int finalize_index(Index& I) {
       if (I.r <= 16) k_row_c<16><<<(unsigned)I.n_blocks, kBlockRows>>>(cz, I.rho, I.blk_grain, (int)I.rp, I.crow);
       else if (I.r <= 32) k_row_c<32><<<(unsigned)I.n_blocks, kBlockRows>>>(cz, I.rho, I.blk_grain, (int)I.rp, I.crow);
       else k_row_c<64><<<(unsigned)I.n_blocks, kBlockRows>>>(cz, I.rho, I.blk_grain, (int)I.rp, I.crow);
+    }
+  }
+  // every block's interval of decoded first coordinates (the scan's interval bound)
+  if (I.n_blocks) {
+    const Coords cz{I.Zb, I.Z8b, I.scale, I.Z16b};
+    const unsigned nb = (unsigned)I.n_blocks;
+    const int rp = (int)I.rp;
+    auto z0 = [&](auto kern) { kern<<<nb, kBlockRows>>>(cz, I.blk_grain, I.blk_off, I.grain_rows, rp, I.blk_z0); };
+    if (bf16) {
+      if (I.r <= 16) z0(k_block_z0<16, kCoordFP8>);
+      else if (I.r <= 32) z0(k_block_z0<32, kCoordFP8>);
+      else z0(k_block_z0<64, kCoordFP8>);
+    } else if (I.precision == HNTL_PREC_INT16) {
+      if (I.r <= 8) z0(k_block_z0<8, kCoordI16>);
+      else if (I.r <= 16) z0(k_block_z0<16, kCoordI16>);
+      else if (I.r <= 32) z0(k_block_z0<32, kCoordI16>);
+      else z0(k_block_z0<64, kCoordI16>);
+    } else {
+      if (I.r <= 8) z0(k_block_z0<8, kCoordF32>);
+      else if (I.r <= 16) z0(k_block_z0<16, kCoordF32>);
+      else if (I.r <= 32) z0(k_block_z0<32, kCoordF32>);
+      else z0(k_block_z0<64, kCoordF32>);
     }
   }
   // Mode A: every id's stored position and h_i = z_i^T G_g z_i of every row
