@@ -292,15 +292,10 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
     const int sh = 24 - 8 * pass;
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    // one shared atomic per distinct bin of a warp (the sampled rows are near
-    // the query, so their D often share a bin); block-uniform trip count
-    for (uint32_t i0 = 0; i0 < fill; i0 += blockDim.x) {
-      const uint32_t i = i0 + threadIdx.x;
-      const uint32_t k = i < fill ? vals[i] : 0u;
-      const bool ok = i < fill && !(known && (k >> (32 - known)) != prefix);
-      const uint32_t bin = ok ? (k >> sh) & 255u : 256u;
-      const unsigned peers = __match_any_sync(0xffffffffu, bin);
-      if (ok && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+    for (uint32_t i = threadIdx.x; i < fill; i += blockDim.x) {
+      const uint32_t k = vals[i];
+      if (known && (k >> (32 - known)) != prefix) continue;
+      atomicAdd(&hist[(k >> sh) & 255u], 1u);
     }
     __syncthreads();
     find_bin(hist, 256, need, &s_bin, &s_below, scratch);
