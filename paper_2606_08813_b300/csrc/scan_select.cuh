@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
   __shared__ uint32_t hist[256];
   __shared__ __align__(8) float szq[RT];
   __shared__ uint32_t scratch[96];
-  __shared__ uint32_t s_fill, s_bin, s_below, s_total, s_first;
+  __shared__ uint32_t s_fill, s_bin, s_below, s_total;
   const int q = blockIdx.x;
   if (qC) C = (int)qC[q];  // per-query pool size (mixed batches)
   // rows to evaluate: enough that the C-th smallest is a useful bound (a larger
@@ -223,7 +223,6 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
     const uint32_t n = grain_rows[g];
     const uint32_t nbk = blk_off[g + 1] - blk_off[g];
     for (int j = threadIdx.x; j < RT; j += blockDim.x) szq[j] = j < r ? zq[(size_t)s * r + j] : 0.f;
-    if (threadIdx.x == 0) s_first = nbk ? nbk - 1 : 0;
     const float rho_q = rhoq[s];
     const float s_g = kC != kCoordF32 ? cz.scale[g] : 1.f;
     __syncthreads();
@@ -235,14 +234,15 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
     // around the one holding z_q0 hold rows near the query: the C-th smallest
     // D over them is a tight bound (any real rows give a valid one)
     uint32_t first = 0;
-    if (take < nbk) {  // block-uniform
-      // first block whose interval reaches z_q0 (the last if none), all blocks tested at once
+    if (take < nbk) {
       const float z0 = szq[0];
-      for (uint32_t k = threadIdx.x; k < nbk; k += blockDim.x)
-        if (blk_z0[blk_off[g] + k].y >= z0) atomicMin(&s_first, k);
-      __syncthreads();
-      const uint32_t c = s_first;
-      first = c > take / 2 ? c - take / 2 : 0;
+      uint32_t lo = 0, hi = nbk - 1;  // first block whose interval reaches z_q0 (the last if none)
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (blk_z0[blk_off[g] + mid].y >= z0) hi = mid;
+        else lo = mid + 1;
+      }
+      first = lo > take / 2 ? lo - take / 2 : 0;
       if (first + take > nbk) first = nbk - take;
     }
     for (uint32_t e0 = 0; e0 < take * kBlockRows; e0 += blockDim.x) {  // block-uniform trip count
