@@ -2,9 +2,7 @@
 //
 // Three kernels replace "write every distance, then select":
 //   k_pilot        one CTA per query computes D for max(1024, 4C) rows, at
-//                  most 2048 (whole Block-SoA blocks: the run of blocks
-//                  around the query's first coordinate, the grains' rows
-//                  being in that order), of its
+//                  most 2048 (whole Block-SoA blocks, evenly spaced), of its
 //                  nearest probed grains in routing order and takes the C-th
 //                  smallest as tau_q. Those are real rows of the query's
 //                  probe set, so at least C rows have D <= tau_q and tau_q is
@@ -188,8 +186,7 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
                                                const float* __restrict__ rho, const int64_t* __restrict__ attr_b,
                                                int r, int rp, const float* __restrict__ zq,
                                                const float* __restrict__ rhoq, const int64_t* __restrict__ filter,
-                                               float* __restrict__ tau, const uint32_t* __restrict__ qC,
-                                               const float2* __restrict__ blk_z0) {
+                                               float* __restrict__ tau, const uint32_t* __restrict__ qC) {
   __shared__ uint32_t vals[kPilotRows];  // D bit patterns (non-negative floats order like unsigned)
   __shared__ uint32_t hist[256];
   __shared__ __align__(8) float szq[RT];
@@ -229,22 +226,7 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
     const uint32_t room = filter ? min(((uint32_t)kPilotRows - fill) / kBlockRows,
                                        (8u * kPilotRows - scanned) / kBlockRows)
                                  : (budget - scanned) / kBlockRows;
-    const uint32_t take = nbk < room ? nbk : room;  // whole blocks
-    // the grain's rows run in order of their first coordinate, so the blocks
-    // around the one holding z_q0 hold rows near the query: the C-th smallest
-    // D over them is a tight bound (any real rows give a valid one)
-    uint32_t first = 0;
-    if (take < nbk) {
-      const float z0 = szq[0];
-      uint32_t lo = 0, hi = nbk - 1;  // first block whose interval reaches z_q0 (the last if none)
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (blk_z0[blk_off[g] + mid].y >= z0) hi = mid;
-        else lo = mid + 1;
-      }
-      first = lo > take / 2 ? lo - take / 2 : 0;
-      if (first + take > nbk) first = nbk - take;
-    }
+    const uint32_t take = nbk < room ? nbk : room;  // whole blocks, evenly spaced over the grain
     for (uint32_t e0 = 0; e0 < take * kBlockRows; e0 += blockDim.x) {  // block-uniform trip count
       const uint32_t e = e0 + threadIdx.x;
       bool keep = false;
@@ -252,7 +234,7 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
       if (e < take * kBlockRows) {
         const uint32_t i = e / kBlockRows;
         const int t = e % kBlockRows;
-        const uint32_t jb = first + i;
+        const uint32_t jb = take == nbk ? i : (uint32_t)(((unsigned long long)i * nbk) / take);
         const size_t b = blk_off[g] + jb;
         keep = jb * kBlockRows + t < n;
         if (keep && filter) {

@@ -432,7 +432,7 @@ void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, 
                         cudaStream_t st, const std::function<void(int)>& mark, const uint32_t* qC) {
   const Coords cz{I.Zb, I.Z8b, I.scale, I.Z16b};
   k_pilot<RT, kC><<<nq, 256, 0, st>>>(nprobe, C, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho,
-                                        I.attr_b, (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.tau, qC, I.blk_z0);
+                                        I.attr_b, (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.tau, qC);
   mark(4);
   if constexpr (kC == kCoordFP8) {
     static thread_local int attr_dev = -1;
