@@ -89,9 +89,13 @@ const char* hntl_last_error(void);
  * position-weighted 64-bit word checksum) onto `device`, laid out as 128-row
  * Block-SoA blocks (dimension-major inside a block, grains padded to whole
  * blocks). precision selects which coordinate/raw-row sections the search
- * uses (HNTL_PREC_BF16_FP8 needs them in the file). Blocking; on success
+ * uses (HNTL_PREC_BF16_FP8 needs them in the file); OR-ing HNTL_LOAD_NO_RAW
+ * into it leaves the raw rows on the host: such an index serves Mode A
+ * (hntl_search_mode_a, which reads no raw row, as sec. 1 describes Mode A) and
+ * routing, and hntl_search (Mode B) returns HNTL_EINVAL. Blocking; on success
  * *out owns device memory. Errors: EIO (open/read), EFORMAT (magic, version,
  * sizes, offsets, ids, truncation, checksum), EINVAL, ENOMEM, ECUDA. */
+#define HNTL_LOAD_NO_RAW 0x100u
 int hntl_index_load(const char* path, int device, uint32_t precision, hntl_index** out);
 
 /* Parameters of hntl_index_build (zero-initialise, then set what you need). */

@@ -132,6 +132,8 @@ std::vector<uint64_t> rows_by_first_coord(const float* Z, uint32_t r, const uint
 }
 
 int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t precision, Index& I) {
+  const bool no_raw = precision & HNTL_LOAD_NO_RAW;  // Mode A only: the raw rows stay on the host
+  precision &= ~HNTL_LOAD_NO_RAW;
   if (size < kHeaderBytes + 8) return fail(HNTL_EFORMAT, "index file truncated (no header)");
   if (std::memcmp(buf, kMagic, 8) != 0) return fail(HNTL_EFORMAT, "bad magic (not an HNTL index file)");
   uint32_t version, flags, d, G, r, reserved;
@@ -292,16 +294,16 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
     if ((rc = dev_upload(I, &I.blk_grain, blk_grain.data(), nb * 4))) break;
     if (precision == HNTL_PREC_FP32) {
       if ((rc = dev_upload(I, &I.Zb, Zb.data(), rows_pad * rp * 4))) break;
-      if ((rc = dev_upload(I, &I.X, Xraw, (size_t)N * d * 4))) break;
+      if (!no_raw && (rc = dev_upload(I, &I.X, Xraw, (size_t)N * d * 4))) break;
     } else if (precision == HNTL_PREC_INT16) {
       if ((rc = dev_upload(I, &I.Z16b, Z16b.data(), rows_pad * rp * 2))) break;
       if ((rc = dev_upload(I, &I.scale, delta.data(), (size_t)G * 4))) break;
       if ((rc = dev_upload(I, &I.dres, dres.data(), (size_t)G * 4))) break;
-      if ((rc = dev_upload(I, &I.X, Xraw, (size_t)N * d * 4))) break;
+      if (!no_raw && (rc = dev_upload(I, &I.X, Xraw, (size_t)N * d * 4))) break;
     } else {
       if ((rc = dev_upload(I, &I.Z8b, Z8b.data(), rows_pad * rp))) break;
       if ((rc = dev_upload(I, &I.scale, scale, (size_t)G * 4))) break;
-      if ((rc = dev_upload(I, &I.Xh, Xraw, (size_t)N * d * 2))) break;
+      if (!no_raw && (rc = dev_upload(I, &I.Xh, Xraw, (size_t)N * d * 2))) break;
     }
     if ((rc = dev_upload(I, &I.rho, rho_b.data(), rows_pad * 4))) break;
     {

@@ -523,6 +523,8 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
   if (filter && !I.has_attr) return fail(HNTL_EINVAL, "filter given but the index has no attribute column");
   if (mode_a && I.precision == HNTL_PREC_INT16)
     return fail(HNTL_EINVAL, "Mode A is not available for the 16-bit form");
+  if (!mode_a && !I.X && !I.Xh)
+    return fail(HNTL_EINVAL, "the index was loaded without its raw rows: only Mode A can search it");
   if (nq == 0) return HNTL_OK;
   if (!Qd || !ws || !out_ids || !out_d) return fail(HNTL_EINVAL, "null buffer");
   if ((cand_ids == nullptr) != (cand_d == nullptr)) return fail(HNTL_EINVAL, "pass both pool buffers or neither");

@@ -255,6 +255,7 @@ extern "C" int hntl_server_create(const hntl_index* idx, size_t mem_budget, uint
   *out = nullptr;
   const hntl::Index& I = idx->I;
   if (batch == 0 || max_slots == 0) return fail(HNTL_EINVAL, "batch and slots must be positive");
+  if (!I.X && !I.Xh) return fail(HNTL_EINVAL, "the server reranks raw rows; the index was loaded without them");
   if (C_max < k_max) C_max = k_max;
   const size_t ws = hntl::workspace_bytes(I, batch, k_max, C_max, nprobe);
   if (!ws) return HNTL_EINVAL;

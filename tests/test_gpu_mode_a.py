@@ -163,3 +163,26 @@ def test_mode_a_filters(hntl, tmp_path):
     _, gpu = run(hntl, p, Q, 10, 50, 3, "bf16-fp8", filters=ranges)
     st = compare_mode_a(gpu, ora, ora_next, gof, 10, 50, 3, "bf16-fp8")
     assert st["checked"] >= 0.9 * len(Q), st
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16-fp8"])
+def test_mode_a_without_raw_rows(hntl, tmp_path, precision):
+    """An index loaded without its raw rows (HNTL_LOAD_NO_RAW) holds less device
+    memory, answers Mode A exactly as the full index does, and refuses Mode B
+    and the server, which rerank raw rows."""
+    X, Q, idx = clustered_case(4000, 64, 8, 8, 16, 50, seed=231)
+    p = write(tmp_path, "nr" + precision, idx, X, precision=precision)
+    prec = hntl.PREC_BF16_FP8 if precision == "bf16-fp8" else hntl.PREC_FP32
+    full = hntl.Index.load(p, 0, prec)
+    lean = hntl.Index.load(p, 0, prec | hntl.LOAD_NO_RAW)
+    raw_bytes = X.shape[0] * X.shape[1] * (2 if precision == "bf16-fp8" else 4)
+    assert full.info()["device_bytes"] - lean.info()["device_bytes"] >= raw_bytes
+    Qd = torch.from_numpy(Q).cuda()
+    a = [t.cpu() for t in full.search(Qd, 10, 50, 3, mode="A")]
+    b = [t.cpu() for t in lean.search(Qd, 10, 50, 3, mode="A")]
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    with pytest.raises(hntl.HntlError) as e:
+        lean.search(Qd, 10, 50, 3)
+    assert e.value.code == hntl.EINVAL
+    with pytest.raises(hntl.HntlError):
+        hntl.Server(lean, mem_budget=1 << 28, max_slots=64, batch=32, nprobe=3, k_max=10, C_max=50)
