@@ -117,7 +117,10 @@ def dist_setup():
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+        if torch.cuda.is_available():
+            dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+        else:  # host-only runs (the multi-process tests): same collectives over gloo
+            dist.init_process_group("gloo")
     return world, rank, local
 
 
@@ -133,9 +136,15 @@ def max_over_ranks(x: float, world: int) -> float:
         return x
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_qps(world: int, steps: int, batch: int, total_ms_max: float) -> float:
+    """Whole-job queries/s of replicas that each searched `steps` batches of
+    `batch` queries: every rank's queries over the slowest rank's time."""
+    return world * steps * batch / (total_ms_max / 1e3)
 
 
 def make_workload(name: str, device, rank: int = 0):
@@ -606,7 +615,7 @@ def run_ours(a, world, rank, local):
     step_ms = [x.elapsed_time(y) for x, y in ev]
     total_ms = e0.elapsed_time(e1)
     total_ms_max = max_over_ranks(total_ms, world)
-    qps = world * a.steps * B / (total_ms_max / 1e3)
+    qps = aggregate_qps(world, a.steps, B, total_ms_max)
     clocks = clk.summary()
 
     # e2e: host queries (pinned) -> device -> search -> host results, per step;
