@@ -1,8 +1,10 @@
 // General BF16 GEMM on tcgen05 for the learned router: C[M x N] = A[M x K] B[N x K]^T
 // (both operands K-major BF16, FP32 accumulation in TMEM), 128 x 128 tiles,
-// operands streamed by TMA through a 4-stage ring. The epilogue adds an
+// operands streamed by TMA through a 3-stage ring (two CTAs per SM, so one
+// CTA's epilogue overlaps the other's main loop). The epilogue adds an
 // optional bias over N, writes the FP32 result (the pre-activation) and,
-// optionally, a BF16 copy of it or of its exact (erf) GELU.
+// optionally, a BF16 copy of it or of its exact (erf) GELU; each warp's
+// 32 x 32 pieces go through shared memory so that rows are stored whole.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -13,7 +15,7 @@
 namespace hntl {
 namespace {
 
-constexpr int kGTM = 128, kGTN = 128, kGStages = 4;
+constexpr int kGTM = 128, kGTN = 128, kGStages = 3;  // 96 KB of stages: two CTAs per SM
 constexpr int kGemmSmem = kGStages * (kGTM + kGTN) * 128 + 1024;
 
 struct GemmEpi {
@@ -29,7 +31,7 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
-__global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtensorMap mapA,
+__global__ void __launch_bounds__(128, 2) k_gemm_tn(const __grid_constant__ CUtensorMap mapA,
                                                  const __grid_constant__ CUtensorMap mapB, int M, int N, int K,
                                                  GemmEpi epi, int* __restrict__ err) {
   constexpr int kKB = 64;  // BF16 elements per stage (128-byte rows)
@@ -92,22 +94,28 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtenso
   const bool failed = __syncthreads_or(!waited || s_fail);
   tc::fence_after_sync();
   if (!failed) {
-    const int row = m0 + warp * 32 + lane;
+    // every MMA has completed and every stage was consumed: the stage memory is free
+    float* tile = reinterpret_cast<float*>(smem) + warp * 32 * 33;  // this warp's 32 x 32 piece, padded
 #pragma unroll 1
     for (int c0 = 0; c0 < kGTN; c0 += 32) {
       float v[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
-      if (row < M) {
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);  // lane = row
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + c0 + j;
-          if (col >= N) continue;
-          const float pre = epi.bias ? v[j] + epi.bias[col] : v[j];
+      for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = v[j];
+      __syncwarp();
+      const int col = n0 + c0 + lane;  // lane = column from here
+      const float b = (epi.bias && col < N) ? epi.bias[col] : 0.f;
+#pragma unroll 4
+      for (int i = 0; i < 32; ++i) {
+        const int row = m0 + warp * 32 + i;
+        if (row < M && col < N) {
+          const float pre = epi.bias ? tile[i * 33 + lane] + b : tile[i * 33 + lane];
           const size_t o = (size_t)row * epi.ldc + col;
           if (epi.C) epi.C[o] = pre;
           if (epi.Cb) epi.Cb[o] = __bfloat16_as_ushort(__float2bfloat16_rn(epi.gelu ? gelu_f(pre) : pre));
         }
       }
+      __syncwarp();
     }
   } else if (tid == 0) {
     atomicOr(err, tc::kErrTimeout);
