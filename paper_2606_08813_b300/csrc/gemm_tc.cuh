@@ -59,36 +59,45 @@ __global__ void __launch_bounds__(128, 2) k_gemm_tn(const __grid_constant__ CUte
   const uint32_t tmem = tmem_base;
   const int m0 = blockIdx.y * kGTM, n0 = blockIdx.x * kGTN;
   const int nkb = (K + kKB - 1) / kKB;
-  if (tid == 0) {
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % kGStages;
-      if (kb >= kGStages && !tc::mbar_wait(&empty[s], ((kb / kGStages) - 1) & 1)) {
-        atomicExch(&s_fail, 1);
-        break;
+  // The producer and the MMA issuer are lane 0 of warps 0 and 1; the other
+  // lanes of those warps wait at __syncwarp (not on an mbarrier poll, which
+  // would hold the whole warp, the working lane included, between polls).
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % kGStages;
+        if (kb >= kGStages && !tc::mbar_wait(&empty[s], ((kb / kGStages) - 1) & 1)) {
+          atomicExch(&s_fail, 1);
+          break;
+        }
+        uint8_t* sa = smem + s * (kBytesA + kBytesB);
+        tc::mbar_expect_tx(&full[s], kBytesA + kBytesB);
+        tc::tma_load_2d(&mapA, &full[s], sa, kb * kKB, m0);
+        tc::tma_load_2d(&mapB, &full[s], sa + kBytesA, kb * kKB, n0);
       }
-      uint8_t* sa = smem + s * (kBytesA + kBytesB);
-      tc::mbar_expect_tx(&full[s], kBytesA + kBytesB);
-      tc::tma_load_2d(&mapA, &full[s], sa, kb * kKB, m0);
-      tc::tma_load_2d(&mapB, &full[s], sa + kBytesA, kb * kKB, n0);
     }
-  } else if (tid == 32) {
-    bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % kGStages;
-      if (!tc::mbar_wait(&full[s], (kb / kGStages) & 1)) {
-        atomicExch(&s_fail, 1);
-        ok = false;
-        break;
-      }
-      tc::fence_after_sync();
-      const uint32_t sa = tc::smem_u32(smem + s * (kBytesA + kBytesB));
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = true;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % kGStages;
+        if (!tc::mbar_wait(&full[s], (kb / kGStages) & 1)) {
+          atomicExch(&s_fail, 1);
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t sa = tc::smem_u32(smem + s * (kBytesA + kBytesB));
 #pragma unroll
-      for (int ks = 0; ks < kKB / 16; ++ks)
-        tc::mma<true>(tmem, tc::desc_sw128(sa + ks * 32), tc::desc_sw128(sa + kBytesA + ks * 32), kIdesc,
-                      (kb | ks) != 0);
-      tc::mma_commit(&empty[s]);
+        for (int ks = 0; ks < kKB / 16; ++ks)
+          tc::mma<true>(tmem, tc::desc_sw128(sa + ks * 32), tc::desc_sw128(sa + kBytesA + ks * 32), kIdesc,
+                        (kb | ks) != 0);
+        tc::mma_commit(&empty[s]);
+      }
+      if (ok) tc::mma_commit(&done);
     }
-    if (ok) tc::mma_commit(&done);
+    __syncwarp();
   }
   const bool waited = tc::mbar_wait(&done, 0);
   const bool failed = __syncthreads_or(!waited || s_fail);

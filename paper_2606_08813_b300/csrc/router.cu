@@ -99,13 +99,30 @@ __global__ void k_gelu_bwd(const float* __restrict__ dH, const float* __restrict
   dAb[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
-// out[c] = sum over rows of x[r][c] (column sums, one thread per column, fixed order)
-__global__ void k_colsum(const float* __restrict__ x, int R, int Cn, float* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= Cn) return;
+// out[c] = sum over rows of x[r][c] (the bias gradients). A block per 32
+// columns, blockDim (32, kColGroups): thread (c, j) sums rows j, j + kColGroups,
+// ... of its column (a warp reads 128 contiguous bytes of a row), then the
+// group sums are added in group order, so the result does not depend on
+// scheduling. One thread per column with a serial walk over the rows left
+// most SMs idle and each thread latency-bound.
+constexpr int kColGroups = 32;
+__global__ void __launch_bounds__(32 * kColGroups) k_colsum(const float* __restrict__ x, int R, int Cn,
+                                                            float* __restrict__ out) {
+  __shared__ float part[kColGroups][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
   float s = 0.f;
-  for (int r = 0; r < R; ++r) s += x[(size_t)r * Cn + c];
-  out[c] = s;
+  if (c < Cn) {
+#pragma unroll 8
+    for (int r = threadIdx.y; r < R; r += kColGroups) s += x[(size_t)r * Cn + c];
+  }
+  part[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < Cn) {
+    float t = 0.f;
+#pragma unroll
+    for (int j = 0; j < kColGroups; ++j) t += part[j][threadIdx.x];
+    out[c] = t;
+  }
 }
 
 // Decoupled weight decay Adam on FP32 masters; refreshes the BF16 copy.
@@ -220,6 +237,10 @@ int gemm(const Router& R, const uint16_t* A, const uint16_t* B, int M, int N, in
 void transpose(const uint16_t* src, int rows, int cols, uint16_t* dst, cudaStream_t st) {
   dim3 grid((cols + 31) / 32, (rows + 31) / 32);
   k_transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, dst);
+}
+
+void colsum(const float* x, int rows, int cols, float* out, cudaStream_t st) {
+  k_colsum<<<(cols + 31) / 32, dim3(32, kColGroups), 0, st>>>(x, rows, cols, out);
 }
 
 void to_bf16(const float* x, size_t n, uint16_t* y, cudaStream_t st) {
@@ -381,7 +402,7 @@ extern "C" int hntl_router_step(hntl_router* h, const float* d_X, const float* d
   hntl::transpose(R.H2b, (int)B, (int)R.h2, R.H2bT, st);
   if ((rc = hntl::gemm(R, R.dLbT, R.H2bT, (int)R.G, (int)R.h2, (int)B, hntl::GemmEpi{R.dW[4], nullptr, nullptr, 0, (int)R.h2}, st)))
     return rc;
-  hntl::k_colsum<<<(R.G + 255) / 256, 256, 0, st>>>(R.dL, (int)B, (int)R.G, R.dW[5]);
+  hntl::colsum(R.dL, (int)B, (int)R.G, R.dW[5], st);
   if ((rc = hntl::gemm(R, R.dLb, R.W3bT, (int)B, (int)R.h2, (int)R.G, hntl::GemmEpi{R.dH2, nullptr, nullptr, 0, (int)R.h2}, st)))
     return rc;
   // second hidden layer
@@ -391,7 +412,7 @@ extern "C" int hntl_router_step(hntl_router* h, const float* d_X, const float* d
   hntl::transpose(R.H1b, (int)B, (int)R.h1, R.H1bT, st);
   if ((rc = hntl::gemm(R, R.dA2bT, R.H1bT, (int)R.h2, (int)R.h1, (int)B, hntl::GemmEpi{R.dW[2], nullptr, nullptr, 0, (int)R.h1}, st)))
     return rc;
-  hntl::k_colsum<<<(R.h2 + 255) / 256, 256, 0, st>>>(R.dA2, (int)B, (int)R.h2, R.dW[3]);
+  hntl::colsum(R.dA2, (int)B, (int)R.h2, R.dW[3], st);
   if ((rc = hntl::gemm(R, R.dA2b, R.W2bT, (int)B, (int)R.h1, (int)R.h2, hntl::GemmEpi{R.dH1, nullptr, nullptr, 0, (int)R.h1}, st)))
     return rc;
   // first hidden layer
@@ -400,7 +421,7 @@ extern "C" int hntl_router_step(hntl_router* h, const float* d_X, const float* d
   hntl::transpose(R.Xb, (int)B, (int)R.d, R.XbT, st);
   if ((rc = hntl::gemm(R, R.dA1bT, R.XbT, (int)R.h1, (int)R.d, (int)B, hntl::GemmEpi{R.dW[0], nullptr, nullptr, 0, (int)R.d}, st)))
     return rc;
-  hntl::k_colsum<<<(R.h1 + 255) / 256, 256, 0, st>>>(R.dA1, (int)B, (int)R.h1, R.dW[1]);
+  hntl::colsum(R.dA1, (int)B, (int)R.h1, R.dW[1], st);
   if (update) {
     ++R.step;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
