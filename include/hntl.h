@@ -292,9 +292,25 @@ int hntl_router_grads(const hntl_router* router, float* h_dW1, float* h_db1, flo
 /* One training step on a batch (device X: B x d FP32, T: B x G FP32 soft
  * targets): forward, loss (added to *d_loss, device FP32, if not NULL),
  * backward, and with update != 0 one AdamW step (lr, weight decay wd on the
- * weight matrices, betas 0.9 / 0.999, eps 1e-8). Asynchronous on `stream`. */
+ * weight matrices, betas 0.9 / 0.999, eps 1e-8; the step count lives on the
+ * device). Asynchronous on `stream`. By default the step's launches are
+ * captured once into a CUDA graph on a private stream and the graph is
+ * launched on `stream`; a call whose arguments (pointers, B, lr, wd, update)
+ * differ from the captured ones captures again first. Not for concurrent
+ * calls on one router from several threads. */
 int hntl_router_step(hntl_router* router, const float* d_X, const float* d_T, uint32_t B, float lr, float wd,
                      int update, float* d_loss, void* stream);
+
+/* enable = 0: hntl_router_step launches its kernels directly instead of
+ * through the captured graph (the same kernels and arguments, so the same
+ * results bit for bit); enable != 0 (the default) restores the graph. */
+int hntl_router_set_graphs(hntl_router* router, int enable);
+
+/* HNTL_ETIMEOUT if a tensor-core pipeline wait of one of the router's GEMMs
+ * gave up (the kernel then skipped its output), else HNTL_OK. Blocking: reads
+ * the router's device error flag after the work queued so far on the legacy
+ * default stream. */
+int hntl_router_status(const hntl_router* router);
 
 /* Logits (device, B x G FP32) of a batch of rows. Asynchronous. */
 int hntl_router_logits(hntl_router* router, const float* d_X, uint32_t B, float* d_logits, void* stream);

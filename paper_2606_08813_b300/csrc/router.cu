@@ -125,20 +125,43 @@ __global__ void __launch_bounds__(32 * kColGroups) k_colsum(const float* __restr
   }
 }
 
-// Decoupled weight decay Adam on FP32 masters; refreshes the BF16 copy.
-__global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                        float* __restrict__ v, size_t n, float lr, float wd, float b1, float b2, float eps, float c1,
-                        float c2, uint16_t* __restrict__ pb) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float gi = g[i];
-  const float mi = b1 * m[i] + (1.f - b1) * gi;
-  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-  m[i] = mi;
-  v[i] = vi;
-  const float w = p[i] - lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * p[i]);
-  p[i] = w;
-  if (pb) pb[i] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+// Advances the AdamW step count and stores its bias corrections.
+__global__ void k_adam_tick(unsigned long long* step, float* bc, float b1, float b2) {
+  const unsigned long long t = ++*step;
+  bc[0] = 1.f - powf(b1, (float)t);
+  bc[1] = 1.f - powf(b2, (float)t);
+}
+
+// The six parameter tensors of one AdamW update; block b works on tensor i
+// where blk[i] <= b < blk[i + 1].
+struct AdamSet {
+  float* p[6];
+  const float* g[6];
+  float* m[6];
+  float* v[6];
+  uint16_t* pb[6];  // BF16 copy to refresh, or nullptr
+  size_t n[6];
+  float wd[6];
+  unsigned blk[7];
+};
+
+// Decoupled weight decay Adam on FP32 masters (all six tensors in one
+// launch); refreshes the BF16 copies.
+__global__ void k_adamw(const AdamSet S, float lr, float b1, float b2, float eps, const float* __restrict__ bc) {
+  int i = 0;
+  while (i < 5 && blockIdx.x >= S.blk[i + 1]) ++i;
+  const size_t j = (size_t)(blockIdx.x - S.blk[i]) * blockDim.x + threadIdx.x;
+  if (j >= S.n[i]) return;
+  const float c1 = bc[0], c2 = bc[1];
+  const float gi = S.g[i][j];
+  const float mi = b1 * S.m[i][j] + (1.f - b1) * gi;
+  const float vi = b2 * S.v[i][j] + (1.f - b2) * gi * gi;
+  S.m[i][j] = mi;
+  S.v[i][j] = vi;
+  const float p = S.p[i][j];
+  const float w = p - lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + S.wd[i] * p);
+  S.p[i][j] = w;
+  if (S.pb[i]) S.pb[i][j] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
 }
 
 // Per row: m = max logit, s = sum exp(l - m); writes -l (so the routing select's ascending order picks the
@@ -198,6 +221,26 @@ struct Router {
   uint16_t *dLb = nullptr, *dLbT = nullptr, *dA2b = nullptr, *dA2bT = nullptr, *dA1b = nullptr, *dA1bT = nullptr;
   float *mx = nullptr, *sm = nullptr;
   int* d_err = nullptr;
+  // AdamW step count and its bias corrections (1 - b1^t, 1 - b2^t), kept on
+  // the device so that one captured training step stays valid for every step
+  unsigned long long* d_step = nullptr;
+  float* d_bc = nullptr;
+  // the training step as a CUDA graph, captured on a private stream and
+  // re-captured (then updated in place) when its arguments change
+  bool graphs = true;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  struct StepArgs {
+    const float* X;
+    const float* T;
+    float* loss;
+    uint32_t B;
+    float lr, wd;
+    int update;
+    bool operator==(const StepArgs& o) const {
+      return X == o.X && T == o.T && loss == o.loss && B == o.B && lr == o.lr && wd == o.wd && update == o.update;
+    }
+  } gargs{};
   std::vector<void*> allocs;
 };
 
@@ -213,6 +256,10 @@ void rfree(Router& R) {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(R.device);
+  if (R.gexec) cudaGraphExecDestroy(R.gexec);
+  if (R.cap) cudaStreamDestroy(R.cap);
+  R.gexec = nullptr;
+  R.cap = nullptr;
   for (void* p : R.allocs) cudaFree(p);
   R.allocs.clear();
   if (prev >= 0) cudaSetDevice(prev);
@@ -223,11 +270,6 @@ int gemm(const Router& R, const uint16_t* A, const uint16_t* B, int M, int N, in
   if (!make_tma_map(&ma, A, true, (uint64_t)M, (uint64_t)K, kGTM) ||
       !make_tma_map(&mb, B, true, (uint64_t)N, (uint64_t)K, kGTN))
     return fail(HNTL_ECUDA, "router: cannot encode TMA maps");
-  static thread_local bool attr = false;
-  if (!attr) {
-    HNTL_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
-    attr = true;
-  }
   dim3 grid((N + kGTN - 1) / kGTN, (M + kGTM - 1) / kGTM);
   k_gemm_tn<<<grid, 128, kGemmSmem, st>>>(ma, mb, M, N, K, epi, R.d_err);
   HNTL_CUDA_TRY(cudaGetLastError());
@@ -332,7 +374,8 @@ extern "C" int hntl_router_create(int device, uint32_t d, uint32_t h1, uint32_t 
                 {(void**)&R.dH1, B * h1 * 4},    {(void**)&R.dA1, B * h1 * 4},   {(void**)&R.dLb, B * G * 2},
                 {(void**)&R.dLbT, B * G * 2},    {(void**)&R.dA2b, B * h2 * 2},  {(void**)&R.dA2bT, B * h2 * 2},
                 {(void**)&R.dA1b, B * h1 * 2},   {(void**)&R.dA1bT, B * h1 * 2}, {(void**)&R.mx, B * 4},
-                {(void**)&R.sm, B * 4},          {(void**)&R.d_err, 4}};
+                {(void**)&R.sm, B * 4},          {(void**)&R.d_err, 4},          {(void**)&R.d_step, 8},
+                {(void**)&R.d_bc, 8}};
     for (auto& a : acts)
       if ((rc = hntl::ralloc(R, a.p, a.bytes))) break;
     if (rc) break;
@@ -344,7 +387,17 @@ extern "C" int hntl_router_create(int device, uint32_t d, uint32_t h1, uint32_t 
     }
     if (rc) break;
     cudaMemset(R.d_err, 0, 4);
+    cudaMemset(R.d_step, 0, 8);
     hntl::refresh_bf16(R, nullptr);
+    // set up here, never while a step is being captured
+    CUtensorMap probe_map;
+    if (cudaFuncSetAttribute(hntl::k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, hntl::kGemmSmem) !=
+            cudaSuccess ||
+        !hntl::make_tma_map(&probe_map, R.W1b, true, h1, d, hntl::kGTN) ||
+        cudaStreamCreateWithFlags(&R.cap, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = fail(HNTL_ECUDA, "router: GEMM set-up");
+      break;
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) rc = fail(HNTL_ECUDA, "router: initialisation");
   } while (0);
   if (prev >= 0) cudaSetDevice(prev);
@@ -386,6 +439,99 @@ extern "C" int hntl_router_grads(const hntl_router* h, float* dW1, float* db1, f
   return copy_out(h->R, dst, h->R.dW);
 }
 
+namespace hntl {
+namespace {
+
+// Every launch of one training step, in order, on `st`.
+int enqueue_step(Router& R, const float* d_X, const float* d_T, uint32_t B, float lr, float wd, int update,
+                 float* d_loss, cudaStream_t st) {
+  int rc;
+  if ((rc = forward(R, d_X, B, st))) return rc;
+  k_softmax_ce<<<B, 256, 0, st>>>(R.L, d_T, (int)R.G, (int)B, R.dL, R.dLb, d_loss);
+  // output layer
+  transpose(R.dLb, (int)B, (int)R.G, R.dLbT, st);
+  transpose(R.H2b, (int)B, (int)R.h2, R.H2bT, st);
+  if ((rc = gemm(R, R.dLbT, R.H2bT, (int)R.G, (int)R.h2, (int)B, GemmEpi{R.dW[4], nullptr, nullptr, 0, (int)R.h2}, st)))
+    return rc;
+  colsum(R.dL, (int)B, (int)R.G, R.dW[5], st);
+  if ((rc = gemm(R, R.dLb, R.W3bT, (int)B, (int)R.h2, (int)R.G, GemmEpi{R.dH2, nullptr, nullptr, 0, (int)R.h2}, st)))
+    return rc;
+  // second hidden layer
+  const size_t n2 = (size_t)B * R.h2, n1 = (size_t)B * R.h1;
+  k_gelu_bwd<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(R.dH2, R.A2, n2, R.dA2, R.dA2b);
+  transpose(R.dA2b, (int)B, (int)R.h2, R.dA2bT, st);
+  transpose(R.H1b, (int)B, (int)R.h1, R.H1bT, st);
+  if ((rc = gemm(R, R.dA2bT, R.H1bT, (int)R.h2, (int)R.h1, (int)B, GemmEpi{R.dW[2], nullptr, nullptr, 0, (int)R.h1}, st)))
+    return rc;
+  colsum(R.dA2, (int)B, (int)R.h2, R.dW[3], st);
+  if ((rc = gemm(R, R.dA2b, R.W2bT, (int)B, (int)R.h1, (int)R.h2, GemmEpi{R.dH1, nullptr, nullptr, 0, (int)R.h1}, st)))
+    return rc;
+  // first hidden layer
+  k_gelu_bwd<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(R.dH1, R.A1, n1, R.dA1, R.dA1b);
+  transpose(R.dA1b, (int)B, (int)R.h1, R.dA1bT, st);
+  transpose(R.Xb, (int)B, (int)R.d, R.XbT, st);
+  if ((rc = gemm(R, R.dA1bT, R.XbT, (int)R.h1, (int)R.d, (int)B, GemmEpi{R.dW[0], nullptr, nullptr, 0, (int)R.d}, st)))
+    return rc;
+  colsum(R.dA1, (int)B, (int)R.h1, R.dW[1], st);
+  if (update) {
+    constexpr float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    k_adam_tick<<<1, 1, 0, st>>>(R.d_step, R.d_bc, b1, b2);
+    AdamSet S{};
+    unsigned nb = 0;
+    for (int i = 0; i < 6; ++i) {
+      S.p[i] = R.W[i];
+      S.g[i] = R.dW[i];
+      S.m[i] = R.m[i];
+      S.v[i] = R.v[i];
+      S.pb[i] = i == 0 ? R.W1b : i == 2 ? R.W2b : i == 4 ? R.W3b : nullptr;
+      S.n[i] = R.n[i];
+      S.wd[i] = (i % 2 == 0) ? wd : 0.f;  // decay on the weight matrices only
+      S.blk[i] = nb;
+      nb += (unsigned)((R.n[i] + 255) / 256);
+    }
+    S.blk[6] = nb;
+    k_adamw<<<nb, 256, 0, st>>>(S, lr, b1, b2, eps, R.d_bc);
+    transpose(R.W2b, (int)R.h2, (int)R.h1, R.W2bT, st);
+    transpose(R.W3b, (int)R.G, (int)R.h2, R.W3bT, st);
+  }
+  HNTL_CUDA_TRY(cudaGetLastError());
+  return HNTL_OK;
+}
+
+// Captures the step for `a` on the private stream and makes R.gexec run it:
+// updated in place when the graph's shape allows, else instantiated anew.
+int capture_step(Router& R, const Router::StepArgs& a) {
+  HNTL_CUDA_TRY(cudaStreamBeginCapture(R.cap, cudaStreamCaptureModeThreadLocal));
+  const int rc = enqueue_step(R, a.X, a.T, a.B, a.lr, a.wd, a.update, a.loss, R.cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(R.cap, &g);
+  if (rc || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (rc) return rc;
+    return fail(HNTL_ECUDA, std::string("router: step capture: ") + cudaGetErrorString(e));
+  }
+  if (R.gexec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(R.gexec, g, &info) != cudaSuccess) {
+      (void)cudaGetLastError();  // not updatable (e.g. other grid sizes): instantiate below
+      cudaGraphExecDestroy(R.gexec);
+      R.gexec = nullptr;
+    }
+  }
+  cudaError_t ie = cudaSuccess;
+  if (!R.gexec) ie = cudaGraphInstantiate(&R.gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    R.gexec = nullptr;
+    return fail(HNTL_ECUDA, std::string("router: step graph: ") + cudaGetErrorString(ie));
+  }
+  R.gargs = a;
+  return HNTL_OK;
+}
+
+}  // namespace
+}  // namespace hntl
+
 extern "C" int hntl_router_step(hntl_router* h, const float* d_X, const float* d_T, uint32_t B, float lr, float wd,
                                 int update, float* d_loss, void* stream) {
   hntl::clear_error();
@@ -395,48 +541,27 @@ extern "C" int hntl_router_step(hntl_router* h, const float* d_X, const float* d
   if (rc) return rc;
   if (B > R.max_batch) return fail(HNTL_EINVAL, "batch larger than the router's max_batch");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if ((rc = hntl::forward(R, d_X, B, st))) return rc;
-  hntl::k_softmax_ce<<<B, 256, 0, st>>>(R.L, d_T, (int)R.G, (int)B, R.dL, R.dLb, d_loss);
-  // output layer
-  hntl::transpose(R.dLb, (int)B, (int)R.G, R.dLbT, st);
-  hntl::transpose(R.H2b, (int)B, (int)R.h2, R.H2bT, st);
-  if ((rc = hntl::gemm(R, R.dLbT, R.H2bT, (int)R.G, (int)R.h2, (int)B, hntl::GemmEpi{R.dW[4], nullptr, nullptr, 0, (int)R.h2}, st)))
-    return rc;
-  hntl::colsum(R.dL, (int)B, (int)R.G, R.dW[5], st);
-  if ((rc = hntl::gemm(R, R.dLb, R.W3bT, (int)B, (int)R.h2, (int)R.G, hntl::GemmEpi{R.dH2, nullptr, nullptr, 0, (int)R.h2}, st)))
-    return rc;
-  // second hidden layer
-  const size_t n2 = (size_t)B * R.h2, n1 = (size_t)B * R.h1;
-  hntl::k_gelu_bwd<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(R.dH2, R.A2, n2, R.dA2, R.dA2b);
-  hntl::transpose(R.dA2b, (int)B, (int)R.h2, R.dA2bT, st);
-  hntl::transpose(R.H1b, (int)B, (int)R.h1, R.H1bT, st);
-  if ((rc = hntl::gemm(R, R.dA2bT, R.H1bT, (int)R.h2, (int)R.h1, (int)B, hntl::GemmEpi{R.dW[2], nullptr, nullptr, 0, (int)R.h1}, st)))
-    return rc;
-  hntl::colsum(R.dA2, (int)B, (int)R.h2, R.dW[3], st);
-  if ((rc = hntl::gemm(R, R.dA2b, R.W2bT, (int)B, (int)R.h1, (int)R.h2, hntl::GemmEpi{R.dH1, nullptr, nullptr, 0, (int)R.h1}, st)))
-    return rc;
-  // first hidden layer
-  hntl::k_gelu_bwd<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(R.dH1, R.A1, n1, R.dA1, R.dA1b);
-  hntl::transpose(R.dA1b, (int)B, (int)R.h1, R.dA1bT, st);
-  hntl::transpose(R.Xb, (int)B, (int)R.d, R.XbT, st);
-  if ((rc = hntl::gemm(R, R.dA1bT, R.XbT, (int)R.h1, (int)R.d, (int)B, hntl::GemmEpi{R.dW[0], nullptr, nullptr, 0, (int)R.d}, st)))
-    return rc;
-  hntl::colsum(R.dA1, (int)B, (int)R.h1, R.dW[1], st);
-  if (update) {
-    ++R.step;
-    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    const float c1 = 1.f - powf(b1, (float)R.step), c2 = 1.f - powf(b2, (float)R.step);
-    for (int i = 0; i < 6; ++i) {
-      uint16_t* pb = i == 0 ? R.W1b : i == 2 ? R.W2b : i == 4 ? R.W3b : nullptr;
-      hntl::k_adamw<<<(unsigned)((R.n[i] + 255) / 256), 256, 0, st>>>(R.W[i], R.dW[i], R.m[i], R.v[i], R.n[i], lr,
-                                                                       (i % 2 == 0) ? wd : 0.f, b1, b2, eps, c1, c2,
-                                                                       pb);
-    }
-    hntl::transpose(R.W2b, (int)R.h2, (int)R.h1, R.W2bT, st);
-    hntl::transpose(R.W3b, (int)R.G, (int)R.h2, R.W3bT, st);
-  }
-  HNTL_CUDA_TRY(cudaGetLastError());
+  if (!R.graphs) return hntl::enqueue_step(R, d_X, d_T, B, lr, wd, update, d_loss, st);
+  const hntl::Router::StepArgs a{d_X, d_T, d_loss, B, lr, wd, update};
+  if (!R.gexec || !(a == R.gargs))
+    if ((rc = hntl::capture_step(R, a))) return rc;
+  HNTL_CUDA_TRY(cudaGraphLaunch(R.gexec, st));
   return HNTL_OK;
+}
+
+extern "C" int hntl_router_set_graphs(hntl_router* h, int enable) {
+  hntl::clear_error();
+  if (!h) return fail(HNTL_EINVAL, "null router");
+  h->R.graphs = enable != 0;
+  return HNTL_OK;
+}
+
+extern "C" int hntl_router_status(const hntl_router* h) {
+  hntl::clear_error();
+  if (!h) return fail(HNTL_EINVAL, "null router");
+  int e = 0;
+  HNTL_CUDA_TRY(cudaMemcpy(&e, h->R.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  return e ? fail(HNTL_ETIMEOUT, "router: a tensor-core pipeline wait timed out") : HNTL_OK;
 }
 
 extern "C" int hntl_router_logits(hntl_router* h, const float* d_X, uint32_t B, float* d_logits, void* stream) {

@@ -326,6 +326,8 @@ lib.hntl_router_params.argtypes = [_P] + [_P] * 6
 lib.hntl_router_grads.argtypes = [_P] + [_P] * 6
 lib.hntl_router_step.argtypes = [_P, _P, _P, _U32, ctypes.c_float, ctypes.c_float, ctypes.c_int, _P, _P]
 lib.hntl_router_logits.argtypes = [_P, _P, _U32, _P, _P]
+lib.hntl_router_set_graphs.argtypes = [_P, ctypes.c_int]
+lib.hntl_router_status.argtypes = [_P]
 lib.hntl_router_route_workspace_bytes.argtypes = [_P, _P, _U32, _U32]
 lib.hntl_router_route_workspace_bytes.restype = _SZ
 lib.hntl_router_route.argtypes = [_P, _P, _P, _U32, _U32, ctypes.c_float, _P, _SZ, _P, _P, _P]
@@ -405,6 +407,14 @@ class Router:
         _dev_tensor(T, torch.float32, (B, self.G), self.device, "T")
         _check(lib.hntl_router_step(self._h, _ptr(X), _ptr(T), B, float(lr), float(wd), int(update), _ptr(loss),
                                     _stream(stream)))
+
+    def set_graphs(self, enable: bool):
+        """Run training steps through the captured CUDA graph (default) or as direct launches."""
+        _check(lib.hntl_router_set_graphs(self._h, int(bool(enable))))
+
+    def status(self) -> int:
+        """0, or the error code of a GEMM pipeline wait that timed out (blocking)."""
+        return lib.hntl_router_status(self._h)
 
     def logits(self, X: torch.Tensor, stream=None) -> torch.Tensor:
         B = int(X.shape[0])

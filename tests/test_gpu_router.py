@@ -71,6 +71,36 @@ def test_adamw_step_matches_oracle(hntl):
         np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-7)
 
 
+def test_step_graph_replays_direct_launches_bit_for_bit(hntl):
+    """The captured training step against the same step launched kernel by
+    kernel: new input buffers (graph updated in place), another lr, a smaller
+    batch (new grid sizes) and a gradient-only step in between."""
+    d, h1, h2, G = 32, 64, 64, 48
+    params = R.init_params(d, h1, h2, G, seed=9)
+    rng = np.random.default_rng(10)
+    routers = [hntl.Router(params, max_batch=32) for _ in range(2)]
+    routers[1].set_graphs(False)
+    bufs = []
+    for B in (32, 32, 16):
+        X = torch.from_numpy(rng.standard_normal((B, d)).astype(np.float32)).cuda()
+        T = torch.zeros(B, G, device="cuda")
+        T[torch.arange(B), torch.from_numpy(rng.integers(0, G, B)).cuda()] = 1.0
+        bufs.append((X, T))
+    plan = [(0, 1e-3, True), (1, 1e-3, True), (0, 1e-3, True), (0, 5e-4, True), (2, 5e-4, True), (1, 5e-4, False),
+            (1, 5e-4, True)]
+    losses = [torch.zeros(1, device="cuda") for _ in routers]
+    for b, lr, upd in plan:
+        for rt, lo in zip(routers, losses):
+            rt.step(bufs[b][0], bufs[b][1], lr=lr, wd=0.01, update=upd, loss=lo)
+    torch.cuda.synchronize()
+    assert float(losses[0].item()) == float(losses[1].item())
+    for a, b in zip(routers[0].params() + routers[0].grads(), routers[1].params() + routers[1].grads()):
+        np.testing.assert_array_equal(a, b)
+    assert routers[0].status() == 0 and routers[1].status() == 0
+    # the steps did move the parameters
+    assert any(not np.array_equal(a, b) for a, b in zip(routers[0].params(), params))
+
+
 def test_router_route_fallback_and_search_with_probes(hntl, tmp_path):
     m = synth.make_cluster_model(4000, 64, 8, seed=71)
     X, _ = synth.sample_points(m, 72)
