@@ -1,7 +1,8 @@
 // General BF16 GEMM on tcgen05 for the learned router: C[M x N] = A[M x K] B[N x K]^T
-// (both operands K-major BF16, FP32 accumulation in TMEM), 128 x 128 tiles,
-// operands streamed by TMA through a 3-stage ring (two CTAs per SM, so one
-// CTA's epilogue overlaps the other's main loop). The epilogue adds an
+// (both operands K-major BF16, FP32 accumulation in TMEM), 128 x BN tiles
+// (BN = 128, or 64 where 128-wide tiles would leave SMs idle), operands
+// streamed by TMA through a 3-stage ring (two or more CTAs per SM, so one
+// CTA's epilogue overlaps another's main loop). The epilogue adds an
 // optional bias over N, writes the FP32 result (the pre-activation) and,
 // optionally, a BF16 copy of it or of its exact (erf) GELU; each warp's
 // 32 x 32 pieces go through shared memory so that rows are stored whole.
@@ -15,8 +16,11 @@
 namespace hntl {
 namespace {
 
-constexpr int kGTM = 128, kGTN = 128, kGStages = 3;  // 96 KB of stages: two CTAs per SM
-constexpr int kGemmSmem = kGStages * (kGTM + kGTN) * 128 + 1024;
+constexpr int kGTM = 128, kGTN = 128, kGStages = 3;  // 96 KB of stages at BN = 128: two CTAs per SM
+template <int BN>
+constexpr int gemm_smem() {
+  return kGStages * (kGTM + BN) * 128 + 1024;
+}
 
 struct GemmEpi {
   float* C;            // [M][ldc] FP32, or nullptr
@@ -31,19 +35,21 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
+template <int BN>
 __global__ void __launch_bounds__(128, 2) k_gemm_tn(const __grid_constant__ CUtensorMap mapA,
                                                  const __grid_constant__ CUtensorMap mapB, int M, int N, int K,
                                                  GemmEpi epi, int* __restrict__ err) {
   constexpr int kKB = 64;  // BF16 elements per stage (128-byte rows)
-  constexpr uint32_t kBytesA = kGTM * 128, kBytesB = kGTN * 128;
-  constexpr uint32_t kIdesc = tc::idesc_f32acc(1u, kGTM, kGTN);
+  static_assert(BN == 64 || BN == 128, "tile width");
+  constexpr uint32_t kBytesA = kGTM * 128, kBytesB = BN * 128;
+  constexpr uint32_t kIdesc = tc::idesc_f32acc(1u, kGTM, BN);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full[kGStages], empty[kGStages], done;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) tc::tmem_alloc(&tmem_base, kGTN);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, BN);
   if (tid == 32) {
     for (int s = 0; s < kGStages; ++s) {
       tc::mbar_init(&full[s], 1);
@@ -57,7 +63,7 @@ __global__ void __launch_bounds__(128, 2) k_gemm_tn(const __grid_constant__ CUte
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
-  const int m0 = blockIdx.y * kGTM, n0 = blockIdx.x * kGTN;
+  const int m0 = blockIdx.y * kGTM, n0 = blockIdx.x * BN;
   const int nkb = (K + kKB - 1) / kKB;
   // The producer and the MMA issuer are lane 0 of warps 0 and 1; the other
   // lanes of those warps wait at __syncwarp (not on an mbarrier poll, which
@@ -106,7 +112,7 @@ __global__ void __launch_bounds__(128, 2) k_gemm_tn(const __grid_constant__ CUte
     // every MMA has completed and every stage was consumed: the stage memory is free
     float* tile = reinterpret_cast<float*>(smem) + warp * 32 * 33;  // this warp's 32 x 32 piece, padded
 #pragma unroll 1
-    for (int c0 = 0; c0 < kGTN; c0 += 32) {
+    for (int c0 = 0; c0 < BN; c0 += 32) {
       float v[32];
       tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);  // lane = row
 #pragma unroll
@@ -131,7 +137,7 @@ __global__ void __launch_bounds__(128, 2) k_gemm_tn(const __grid_constant__ CUte
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, kGTN);
+  if (warp == 0) tc::tmem_dealloc(tmem, BN);
 }
 
 }  // namespace

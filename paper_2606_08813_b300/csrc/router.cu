@@ -204,7 +204,7 @@ __global__ void k_router_merge(int nq, int nprobe, const float* __restrict__ neg
 }  // namespace
 
 struct Router {
-  int device = 0;
+  int device = 0, num_sms = 148;
   uint32_t d = 0, h1 = 0, h2 = 0, G = 0, max_batch = 0;
   uint64_t step = 0;
   // parameters: FP32 masters, gradients, Adam moments, BF16 copies
@@ -266,12 +266,18 @@ void rfree(Router& R) {
 }
 
 int gemm(const Router& R, const uint16_t* A, const uint16_t* B, int M, int N, int K, GemmEpi epi, cudaStream_t st) {
+  // 64-wide tiles where 128-wide ones would not give every SM a CTA
+  const bool narrow = (size_t)((N + kGTN - 1) / kGTN) * ((M + kGTM - 1) / kGTM) < (size_t)R.num_sms;
+  const int bn = narrow ? 64 : 128;
   CUtensorMap ma, mb;
   if (!make_tma_map(&ma, A, true, (uint64_t)M, (uint64_t)K, kGTM) ||
-      !make_tma_map(&mb, B, true, (uint64_t)N, (uint64_t)K, kGTN))
+      !make_tma_map(&mb, B, true, (uint64_t)N, (uint64_t)K, (uint32_t)bn))
     return fail(HNTL_ECUDA, "router: cannot encode TMA maps");
-  dim3 grid((N + kGTN - 1) / kGTN, (M + kGTM - 1) / kGTM);
-  k_gemm_tn<<<grid, 128, kGemmSmem, st>>>(ma, mb, M, N, K, epi, R.d_err);
+  dim3 grid((N + bn - 1) / bn, (M + kGTM - 1) / kGTM);
+  if (narrow)
+    k_gemm_tn<64><<<grid, 128, gemm_smem<64>(), st>>>(ma, mb, M, N, K, epi, R.d_err);
+  else
+    k_gemm_tn<128><<<grid, 128, gemm_smem<128>(), st>>>(ma, mb, M, N, K, epi, R.d_err);
   HNTL_CUDA_TRY(cudaGetLastError());
   return HNTL_OK;
 }
@@ -391,8 +397,11 @@ extern "C" int hntl_router_create(int device, uint32_t d, uint32_t h1, uint32_t 
     hntl::refresh_bf16(R, nullptr);
     // set up here, never while a step is being captured
     CUtensorMap probe_map;
-    if (cudaFuncSetAttribute(hntl::k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, hntl::kGemmSmem) !=
-            cudaSuccess ||
+    if (cudaFuncSetAttribute(hntl::k_gemm_tn<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             hntl::gemm_smem<128>()) != cudaSuccess ||
+        cudaFuncSetAttribute(hntl::k_gemm_tn<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             hntl::gemm_smem<64>()) != cudaSuccess ||
+        cudaDeviceGetAttribute(&R.num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         !hntl::make_tma_map(&probe_map, R.W1b, true, h1, d, hntl::kGTN) ||
         cudaStreamCreateWithFlags(&R.cap, cudaStreamNonBlocking) != cudaSuccess) {
       rc = fail(HNTL_ECUDA, "router: GEMM set-up");
