@@ -303,7 +303,9 @@ int hntl_router_step(hntl_router* router, const float* d_X, const float* d_T, ui
 
 /* enable = 0: hntl_router_step launches its kernels directly instead of
  * through the captured graph (the same kernels and arguments, so the same
- * results bit for bit); enable != 0 (the default) restores the graph. */
+ * parameters and gradients bit for bit; the loss is a sum of per-row atomic
+ * adds on both paths, so its last bits follow the order the rows finish in);
+ * enable != 0 (the default) restores the graph. */
 int hntl_router_set_graphs(hntl_router* router, int enable);
 
 /* HNTL_ETIMEOUT if a tensor-core pipeline wait of one of the router's GEMMs

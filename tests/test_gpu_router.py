@@ -93,9 +93,14 @@ def test_step_graph_replays_direct_launches_bit_for_bit(hntl):
         for rt, lo in zip(routers, losses):
             rt.step(bufs[b][0], bufs[b][1], lr=lr, wd=0.01, update=upd, loss=lo)
     torch.cuda.synchronize()
-    assert float(losses[0].item()) == float(losses[1].item())
     for a, b in zip(routers[0].params() + routers[0].grads(), routers[1].params() + routers[1].grads()):
         np.testing.assert_array_equal(a, b)
+    # the loss is a sum of per-row atomic adds, in whatever order the blocks
+    # finish (on either path): n adds to a running sum below 2^5 differ by at
+    # most n ulp(2^5) = n 2^-18 between two orders
+    n_adds = sum(bufs[b][0].shape[0] for b, _, _ in plan)
+    assert abs(float(losses[0].item()) - float(losses[1].item())) <= n_adds * 2.0 ** -18
+    assert float(losses[0].item()) < 32
     assert routers[0].status() == 0 and routers[1].status() == 0
     # the steps did move the parameters
     assert any(not np.array_equal(a, b) for a, b in zip(routers[0].params(), params))
