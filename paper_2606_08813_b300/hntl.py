@@ -108,6 +108,21 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _in_use(stream, *tensors):
+    """Mark tensors that this binding allocated (or caches) as used by `stream`
+    when the call runs on a stream other than the current one, so that the
+    caching allocator does not hand their memory to other work (a cached
+    workspace replaced by a larger one, an output the caller drops) before
+    that stream's queued kernels are done with it."""
+    if stream is None:
+        return
+    if stream.cuda_stream == torch.cuda.current_stream(getattr(stream, "device", None)).cuda_stream:
+        return
+    for t in tensors:
+        if t is not None:
+            t.record_stream(stream)
+
+
 def _dev_tensor(t, dtype, shape, device, name):
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
@@ -255,7 +270,9 @@ class Index:
         pool_d = torch.empty(nq, Ce, dtype=torch.float32, device=dev) if return_pool else None
         probe = torch.empty(nq, nprobe, dtype=torch.int32, device=dev) if return_probe else None
         nb = self.workspace_bytes(max(nq, 1), k, C, nprobe)
+        own_ws = ws is None
         ws = self._caller_ws(ws, nb)
+        _in_use(stream, ws if own_ws else None, *((ids, dist) if out is None else ()), pool_ids, pool_d, probe)
         if mode == "A":
             if return_probe:
                 raise ValueError("mode A has no probe output")
@@ -310,6 +327,7 @@ class Index:
         pd = torch.empty(nq, nprobe, dtype=torch.float32, device=Q.device)
         nb = self.workspace_bytes(max(nq, 1), 1, 1, nprobe)
         ws = self.workspace(nb)
+        _in_use(stream, ws, probe, pd)
         _check(lib.hntl_route(self._h, _ptr(Q), nq, nprobe, _ptr(ws), ws.numel(), _ptr(probe), _ptr(pd),
                               _stream(stream)))
         return probe, pd
@@ -345,6 +363,7 @@ def search_probes(index: Index, Q: torch.Tensor, probes: torch.Tensor, k: int, C
     pid = torch.empty(nq, Ce, dtype=torch.int32, device=Q.device) if return_pool else None
     pd = torch.empty(nq, Ce, dtype=torch.float32, device=Q.device) if return_pool else None
     ws = index.workspace(index.workspace_bytes(max(nq, 1), k, C, nprobe))
+    _in_use(stream, ws, ids, dist, pid, pd)
     _check(lib.hntl_search_probes(index.handle, _ptr(Q), nq, k, C, nprobe, _ptr(probes), _ptr(filters), _ptr(ws),
                                   ws.numel(), _ptr(ids), _ptr(dist), _ptr(pid), _ptr(pd), _stream(stream)))
     return (ids, dist, pid, pd) if return_pool else (ids, dist)
@@ -420,6 +439,7 @@ class Router:
         B = int(X.shape[0])
         _dev_tensor(X, torch.float32, (B, self.d), self.device, "X")
         out = torch.empty(B, self.G, dtype=torch.float32, device=X.device)
+        _in_use(stream, out)
         _check(lib.hntl_router_logits(self._h, _ptr(X), B, _ptr(out), _stream(stream)))
         return out
 
@@ -434,6 +454,7 @@ class Router:
             self._ws = torch.empty(nb, dtype=torch.uint8, device=Q.device)
         probe = torch.empty(nq, nprobe, dtype=torch.int32, device=Q.device)
         nfb = torch.zeros(1, dtype=torch.int32, device=Q.device)
+        _in_use(stream, self._ws, probe, nfb)
         _check(lib.hntl_router_route(self._h, index.handle, _ptr(Q), nq, nprobe, float(tau), _ptr(self._ws),
                                      self._ws.numel(), _ptr(probe), _ptr(nfb), _stream(stream)))
         return probe, nfb

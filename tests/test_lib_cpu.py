@@ -121,3 +121,31 @@ def test_null_arguments_are_einval():
     assert hntl.lib.hntl_search(None, None, 1, 1, 1, 1, None, None, 0, None, None, None, None, None, None) \
         == hntl.EINVAL
     assert hntl.lib.hntl_search_workspace_bytes(None, 1, 1, 1, 1) == 0
+
+
+def test_binding_marks_its_tensors_in_use_on_side_streams(monkeypatch):
+    """Tensors the binding allocates are recorded on the call's stream when it
+    is not the current one (so the allocator does not reuse them early), and
+    left alone otherwise."""
+
+    class FakeStream:
+        def __init__(self, handle):
+            self.cuda_stream = handle
+            self.device = "cuda:0"
+
+    class FakeTensor:
+        def __init__(self):
+            self.recorded = []
+
+        def record_stream(self, s):
+            self.recorded.append(s)
+
+    current = FakeStream(7)
+    monkeypatch.setattr(hntl.torch.cuda, "current_stream", lambda device=None: current)
+    a, b = FakeTensor(), FakeTensor()
+    hntl._in_use(None, a, b)
+    hntl._in_use(FakeStream(7), a, b)
+    assert a.recorded == [] and b.recorded == []
+    side = FakeStream(9)
+    hntl._in_use(side, a, None, b)
+    assert a.recorded == [side] and b.recorded == [side]
