@@ -84,3 +84,21 @@ def test_adamw_first_step_is_sign_step():
     g = [np.array([0.3, -0.01, 2.0])]
     newp, m, v = R.adamw(p, g, [np.zeros(3)], [np.zeros(3)], step=1, lr=0.1, wd=0.0, eps=0.0)
     np.testing.assert_allclose(newp[0], p[0] - 0.1 * np.sign(g[0]), rtol=1e-12)
+
+
+def test_adamw_constant_gradient_closed_form_over_steps():
+    """Under a gradient that never changes, the bias-corrected moments equal
+    g and g^2 at every step t (m_t = (1 - b1^t) g, v_t = (1 - b2^t) g^2), so
+    each step moves a weight by lr (g / (|g| + eps) + wd p): a wrong step
+    count or bias-correction exponent breaks this from the second step on."""
+    p0 = np.array([1.0, -2.0, 0.5, 3.0])
+    g = np.array([0.3, -0.01, 2.0, -5.0])
+    lr, wd, eps = 0.05, 0.1, 1e-3
+    p, m, v = [p0.copy()], [np.zeros(4)], [np.zeros(4)]
+    want = p0.copy()
+    for t in range(1, 7):
+        p, m, v = R.adamw(p, [g], m, v, step=t, lr=lr, wd=wd, eps=eps)
+        want = (1.0 - lr * wd) * want - lr * g / (np.abs(g) + eps)
+        np.testing.assert_allclose(m[0], (1.0 - 0.9 ** t) * g, rtol=1e-12)
+        np.testing.assert_allclose(v[0], (1.0 - 0.999 ** t) * g * g, rtol=1e-12)
+        np.testing.assert_allclose(p[0], want, rtol=1e-10, atol=1e-12)
