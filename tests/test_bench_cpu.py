@@ -1,5 +1,6 @@
-"""Host logic of bench.py that decides whether a timed run is kept: the
-nvidia-smi clock record read back into the line's `clocks` object."""
+"""Host logic of bench.py: the nvidia-smi clock record read back into the
+line's `clocks` object (which decides whether a timed run is kept), and the
+ground truth and recall that the quoted recall@10 comes from."""
 import os
 import sys
 
@@ -42,3 +43,59 @@ def test_clock_summary_without_samples_or_power(tmp_path):
     assert s["samples"] == 0 and s["reasons"] == ["unsampled"] and s["sm_mhz"] is None
     s = _summary(tmp_path, ["0, 2032, 2032, [N/A], 0x0, Not Active, Not Active, Not Active, Not Active"])
     assert s["samples"] == 1 and s["power_w_max"] is None
+
+
+def _brute(X, Q, k, keep=None):
+    """FP64 brute force, ties by id, -1 where fewer than k rows qualify."""
+    import numpy as np
+
+    out = np.full((len(Q), k), -1, dtype=np.int64)
+    for qi, q in enumerate(Q.astype(np.float64)):
+        d = ((X.astype(np.float64) - q) ** 2).sum(1)
+        ids = np.arange(len(X)) if keep is None else np.nonzero(keep[qi])[0]
+        order = ids[np.lexsort((ids, d[ids]))][:k]
+        out[qi, :len(order)] = order
+    return out
+
+
+def test_ground_truth_matches_brute_force_across_chunks_and_ties():
+    import numpy as np
+    import torch
+
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((3000, 16)).astype(np.float32)
+    X[2500:2510] = X[100]  # ten exact duplicates of row 100: ties broken by id
+    Q = rng.standard_normal((40, 16)).astype(np.float32)
+    Q[0] = X[100]
+    got = bench.exact_topk(torch.from_numpy(X), torch.from_numpy(Q), 10, qblock=16, chunk=512).numpy()
+    np.testing.assert_array_equal(got, _brute(X, Q, 10))
+    assert got[0].tolist() == [100] + list(range(2500, 2509))
+
+
+def test_ground_truth_with_range_filters_and_short_rows():
+    import numpy as np
+    import torch
+
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((2000, 8)).astype(np.float32)
+    Q = rng.standard_normal((30, 8)).astype(np.float32)
+    attr = rng.integers(0, 1000, 2000)
+    lo = rng.integers(0, 900, 30)
+    hi = lo + rng.integers(0, 120, 30)
+    lo[0], hi[0] = 5000, 6000  # no row qualifies
+    hi[1] = lo[1]  # about two rows qualify
+    R = np.stack([lo, hi], 1)
+    keep = (attr[None] >= lo[:, None]) & (attr[None] <= hi[:, None])
+    got = bench.exact_topk(torch.from_numpy(X), torch.from_numpy(Q), 10, chunk=700, attr=torch.from_numpy(attr),
+                           ranges=torch.from_numpy(R)).numpy()
+    np.testing.assert_array_equal(got, _brute(X, Q, 10, keep))
+    assert (got[0] == -1).all()
+
+
+def test_recall_counts_only_true_neighbours_in_the_first_k():
+    import numpy as np
+
+    truth = np.array([[1, 2, 3, 4], [5, 6, -1, -1], [-1, -1, -1, -1]])
+    found = np.array([[4, 3, 9, 8, 1], [6, 7, 5, 0, 0], [0, 1, 2, 3, 4]])
+    # query 0: {4, 3} of 4 in its first 4; query 1: {6, 5} of 2; query 2 has no neighbours
+    assert bench.recall_at_k(found, truth) == (0.5 + 1.0) / 2
