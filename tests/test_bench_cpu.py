@@ -1,6 +1,7 @@
 """Host logic of bench.py: the nvidia-smi clock record read back into the
-line's `clocks` object (which decides whether a timed run is kept), and the
-ground truth and recall that the quoted recall@10 comes from."""
+line's `clocks` object (which decides whether a timed run is kept), the
+ground truth and recall that the quoted recall@10 comes from, and the
+algorithmic bytes and profiled traffic of the roofline object."""
 import os
 import sys
 
@@ -99,3 +100,40 @@ def test_recall_counts_only_true_neighbours_in_the_first_k():
     found = np.array([[4, 3, 9, 8, 1], [6, 7, 5, 0, 0], [0, 1, 2, 3, 4]])
     # query 0: {4, 3} of 4 in its first 4; query 1: {6, 5} of 2; query 2 has no neighbours
     assert bench.recall_at_k(found, truth) == (0.5 + 1.0) / 2
+
+
+def test_stage_bytes_by_hand():
+    """Grains of 10, 20, 30, 40 rows; queries probing {0, 1} and {1, 3}: the
+    union of probed grains (70 rows, 3 bases) is read once per batch."""
+    import numpy as np
+
+    rows_g = np.array([10, 20, 30, 40])
+    probe = np.array([[0, 1], [1, 3]])
+    w = {"r": 8, "d": 16, "G": 4, "C": 5}
+    assert bench.stage_bytes(None, rows_g, probe, w, 2) == {
+        "scan": 70 * (4 * 8 + 4), "project": 3 * 9 * 16 * 4, "rerank": 2 * 5 * 16 * 4, "route": 4 * 16 * 4 + 2 * 16 * 4}
+    w["precision"] = "bf16-fp8"
+    assert bench.stage_bytes(None, rows_g, probe, w, 2) == {
+        "scan": 70 * (8 + 4), "project": 3 * 9 * 16 * 2, "rerank": 2 * 5 * 16 * 2, "route": 4 * 16 * 2 + 2 * 16 * 4}
+
+
+def test_profile_traffic_is_dropped_once_its_kernel_source_changes(tmp_path, monkeypatch):
+    """A committed DRAM-traffic figure is used only while the kernel source it
+    was captured on is unchanged (scaled to a full launch when captured on a
+    smaller case)."""
+    import hashlib
+    import json
+
+    csrc = tmp_path / "paper_2606_08813_b300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    src = b"// kernel source\n"
+    (csrc / "k.cuh").write_bytes(src)
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    rec = {"w": {"scan": {"source_sha": {"k.cuh": sha}, "dram_bytes_per_launch": 1000, "scale_to_full_launch": 4.0}}}
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_from_profiles("w", "scan") == 4000
+    assert bench.traffic_from_profiles("w", "rerank") is None
+    (csrc / "k.cuh").write_bytes(src + b"// changed\n")
+    assert bench.traffic_from_profiles("w", "scan") is None
