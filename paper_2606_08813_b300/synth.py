@@ -22,7 +22,6 @@ and CUDA draws of the points differ (each is reproducible on its own device).
 """
 from __future__ import annotations
 
-import math
 from dataclasses import dataclass
 
 import torch
@@ -195,10 +194,3 @@ def expected_captured_fraction(d: int, sub_dim: int, decay: float, sigma: float,
     lam = sorted([decay ** (2 * j) + sigma ** 2 for j in range(sub_dim)] + [sigma ** 2] * (d - sub_dim),
                  reverse=True)
     return sum(lam[:r]) / sum(lam)
-
-
-def _self_check():  # pragma: no cover - debugging aid
-    m = make_cluster_model(1000, 16, 4, seed=1)
-    x, lab = sample_points(m, 2)
-    assert x.shape == (1000, 16) and lab.shape == (1000,)
-    assert math.isfinite(float(x.abs().max()))
