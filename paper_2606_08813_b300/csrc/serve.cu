@@ -131,7 +131,7 @@ struct Server {
   std::atomic<bool> stop{false};
   std::vector<double> lat_us;
   uint64_t batches = 0, batched = 0;
-  int worker_error = HNTL_OK;
+  std::atomic<int> worker_error{HNTL_OK};  // set by the worker, read by any thread
 };
 
 namespace {
@@ -190,9 +190,17 @@ void worker_main(Server* S) {
           L.tickets.push_back(t);
         }
         for (uint32_t i = n; i < rows; ++i) L.h_slots[i] = first_slot;  // padding rows, results discarded
-        cudaMemcpyAsync(L.d_slots, L.h_slots, sizeof(uint32_t) * rows, cudaMemcpyHostToDevice, L.st);
-        cudaGraphLaunch(L.graphs[gi].second, L.st);
-        cudaEventRecord(L.done, L.st);
+        if (cudaMemcpyAsync(L.d_slots, L.h_slots, sizeof(uint32_t) * rows, cudaMemcpyHostToDevice, L.st) !=
+                cudaSuccess ||
+            cudaGraphLaunch(L.graphs[gi].second, L.st) != cudaSuccess ||
+            cudaEventRecord(L.done, L.st) != cudaSuccess) {
+          // the batch's requests stay unfinished (pollers get the error): the
+          // lane's event does not belong to this batch, so nothing may retire
+          L.tickets.clear();
+          S->worker_error = HNTL_ECUDA;
+          S->stop = true;
+          break;
+        }
         L.busy = true;
         S->batches += 1;
         S->batched += n;
@@ -453,6 +461,8 @@ extern "C" int hntl_server_submit(hntl_server* h, const float* h_queries, uint32
                                                S.d_slot_k, S.d_slot_C, S.d_slot_range);
     if (cudaStreamSynchronize(S.up) != cudaSuccess) {
       if (prev >= 0) cudaSetDevice(prev);
+      lk.lock();
+      for (uint32_t s : slots) S.free_slots.push_back(s);  // nothing was admitted
       return fail(HNTL_ECUDA, "server: slot upload");
     }
   }
@@ -482,11 +492,13 @@ extern "C" int hntl_server_poll(hntl_server* h, uint64_t ticket, int64_t* h_ids,
   std::unique_lock<std::mutex> lk(S.mu);
   auto it = S.reqs.find(ticket);
   if (it == S.reqs.end()) return fail(HNTL_EINVAL, "unknown ticket");
-  const bool ok = S.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
+  auto finished = [&] {
     auto jt = S.reqs.find(ticket);
     return jt != S.reqs.end() && jt->second.state == 3;
-  });
-  if (!ok) return S.worker_error ? fail(S.worker_error, "the serving worker stopped") : HNTL_ETIMEOUT;
+  };
+  // wake on the result or on a stopped worker (whose unfinished requests never finish)
+  S.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return finished() || S.worker_error != 0; });
+  if (!finished()) return S.worker_error ? fail(S.worker_error, "the serving worker stopped") : HNTL_ETIMEOUT;
   hntl::Req& r = S.reqs[ticket];
   if (h_ids) std::copy(r.ids.begin(), r.ids.end(), h_ids);
   if (h_dist) std::copy(r.dist.begin(), r.dist.end(), h_dist);
