@@ -60,6 +60,18 @@ extern "C" {
 #define HNTL_PREC_BF16_FP8 1
 #define HNTL_PREC_INT16 2
 
+/* The 16-bit form's quantisation of stored rows (Eq. 5, the steps above) as
+ * the loader and the builder apply it, on host arrays: Z [N][r] FP32
+ * coordinates and rho [N] FP32 residual norms of rows stored grain by grain,
+ * goff [G + 1] grain offsets (goff[0] = 0, non-decreasing, goff[G] = N).
+ * Writes delta [G] and dres [G] (1 for a grain whose values are all zero),
+ * codes [N][r] int16 and rho_grid [N] = fl32(residual code * dres_g), the
+ * residual norms the scan uses. All buffers are the caller's; host only, no
+ * device is touched. Errors: EINVAL (null pointer, G = 0, r = 0, bad offsets),
+ * ENOMEM (host allocation). */
+int hntl_int16_quantize_host(const float* Z, const float* rho, const uint64_t* goff, uint32_t G, uint32_t r,
+                             float* delta, float* dres, int16_t* codes, float* rho_grid);
+
 typedef struct hntl_index hntl_index; /* opaque; owned by the library */
 
 typedef struct {

@@ -376,6 +376,29 @@ int hntl_index_load(const char* path, int device, uint32_t precision, hntl_index
   return HNTL_OK;
 }
 
+int hntl_int16_quantize_host(const float* Z, const float* rho, const uint64_t* goff, uint32_t G, uint32_t r,
+                             float* delta, float* dres, int16_t* codes, float* rho_grid) {
+  hntl::clear_error();
+  if (!Z || !rho || !goff || !delta || !dres || !codes || !rho_grid) return hntl::fail(HNTL_EINVAL, "null argument");
+  if (G == 0 || r == 0) return hntl::fail(HNTL_EINVAL, "G and r must be positive");
+  if (goff[0] != 0) return hntl::fail(HNTL_EINVAL, "grain offsets must start at 0");
+  for (uint32_t g = 0; g < G; ++g)
+    if (goff[g + 1] < goff[g]) return hntl::fail(HNTL_EINVAL, "grain offsets decrease");
+  try {
+    const std::vector<uint64_t> off(goff, goff + G + 1);
+    std::vector<float> dl, dr, rq;
+    std::vector<int16_t> cq;
+    hntl::int16_quantize(Z, rho, off, r, dl, dr, cq, rq);
+    std::copy(dl.begin(), dl.end(), delta);
+    std::copy(dr.begin(), dr.end(), dres);
+    std::copy(cq.begin(), cq.end(), codes);
+    std::copy(rq.begin(), rq.end(), rho_grid);
+  } catch (...) {
+    return hntl::fail(HNTL_ENOMEM, "host allocation failed");
+  }
+  return HNTL_OK;
+}
+
 int hntl_index_info(const hntl_index* idx, hntl_index_desc* out) {
   hntl::clear_error();
   if (!idx || !out) return hntl::fail(HNTL_EINVAL, "null argument");

@@ -64,6 +64,7 @@ lib.hntl_index_grain_rows.argtypes = [_P, _P]
 lib.hntl_index_export.argtypes = [_P, _P, _P, _P, _P, _P, _P]
 lib.hntl_profile_enable.argtypes = [ctypes.c_int]
 lib.hntl_profile_read.argtypes = [_P, _P]
+lib.hntl_int16_quantize_host.argtypes = [_P, _P, _P, _U32, _U32, _P, _P, _P, _P]
 NSTAGES = 7
 STAGES = ("route", "bucket", "project", "pilot", "scan", "select", "rerank")
 
@@ -84,6 +85,29 @@ def profile_read():
     calls = ctypes.c_uint64()
     _check(lib.hntl_profile_read(ms, ctypes.byref(calls)))
     return dict(zip(STAGES, list(ms))), int(calls.value)
+
+
+def int16_quantize_host(Z, rho, grain_off):
+    """The 16-bit form's row quantisation as the loader and builder apply it
+    (hntl_int16_quantize_host), on host arrays: Z [N, r] and rho [N] float32
+    in grain order, grain_off [G + 1]. Returns (delta [G], dres [G],
+    codes [N, r] int16, rho_grid [N] float32)."""
+    import numpy as np
+
+    Z = np.ascontiguousarray(Z, dtype=np.float32)
+    rho = np.ascontiguousarray(rho, dtype=np.float32)
+    off = np.ascontiguousarray(grain_off, dtype=np.uint64)
+    N, r = Z.shape
+    G = len(off) - 1
+    if rho.shape != (N,) or G < 1 or int(off[-1]) != N:
+        raise ValueError("Z [N, r], rho [N] and grain_off [G + 1] ending at N are required")
+    delta = np.empty(G, np.float32)
+    dres = np.empty(G, np.float32)
+    codes = np.empty((N, r), np.int16)
+    rho_grid = np.empty(N, np.float32)
+    _check(lib.hntl_int16_quantize_host(Z.ctypes.data, rho.ctypes.data, off.ctypes.data, G, r, delta.ctypes.data,
+                                        dres.ctypes.data, codes.ctypes.data, rho_grid.ctypes.data))
+    return delta, dres, codes, rho_grid
 
 
 def last_error() -> str:

@@ -149,3 +149,49 @@ def test_binding_marks_its_tensors_in_use_on_side_streams(monkeypatch):
     side = FakeStream(9)
     hntl._in_use(side, a, None, b)
     assert a.recorded == [side] and b.recorded == [side]
+
+
+def _int16_both(idx):
+    f = O.int16_form(idx)
+    Z = np.ascontiguousarray(idx["Z"], dtype=np.float32)
+    rho = np.ascontiguousarray(idx["rho"], dtype=np.float32)
+    return f, hntl.int16_quantize_host(Z, rho, np.asarray(idx["grain_off"]))
+
+
+@pytest.mark.parametrize("case", ["clustered", "edges", "full-basis", "zero-grain"])
+def test_int16_quantisation_host_code_equals_oracle_bit_for_bit(case):
+    """The library's 16-bit quantisation (host C++, shared by the loader and
+    the builder) and the oracle's (numpy) take the same IEEE single-precision
+    steps: the same steps, codes and grid residuals, bit for bit."""
+    from cases import clustered_case, partition_index
+
+    if case == "clustered":
+        _, _, idx = clustered_case(3000, 32, 8, 8, 8, 4, seed=41, sizes="zipf")
+    else:
+        sizes = [0, 1, 127, 128, 129, 300]
+        rng = np.random.default_rng(43)
+        d, r = (16, 16) if case == "full-basis" else (24, 5)
+        centres = rng.standard_normal((len(sizes), d)) * 3
+        assign = np.repeat(np.arange(len(sizes)), sizes)
+        X = (centres[assign] + rng.standard_normal((len(assign), d)) * 0.7).astype(np.float32)
+        if case == "zero-grain":
+            X[assign == 3] = 0.0  # one grain of identical rows at the origin: every value zero
+        idx = partition_index(X, assign, len(sizes), r)
+    f, (delta, dres, codes, rho_grid) = _int16_both(idx)
+    np.testing.assert_array_equal(delta.view(np.uint32), f["delta"].view(np.uint32))
+    np.testing.assert_array_equal(dres.view(np.uint32), f["dres"].view(np.uint32))
+    np.testing.assert_array_equal(codes, f["codes"])
+    np.testing.assert_array_equal(rho_grid.view(np.uint32), f["rhof32"].view(np.uint32))
+    if case == "zero-grain":
+        g = 3
+        assert delta[g] == 1.0 and dres[g] == 1.0
+    assert np.abs(codes).max() <= 16383  # the rows use at most half of the signed range
+
+
+def test_int16_quantisation_host_rejects_bad_offsets():
+    Z = np.zeros((4, 2), np.float32)
+    rho = np.zeros(4, np.float32)
+    with pytest.raises(hntl.HntlError):
+        hntl.int16_quantize_host(Z, rho, np.array([0, 3, 2, 4]))
+    with pytest.raises(ValueError):
+        hntl.int16_quantize_host(Z, rho, np.array([0, 3]))
