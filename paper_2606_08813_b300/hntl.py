@@ -528,6 +528,7 @@ class Server:
         self._h = h
         self.index = index
         self.d = int(index.desc.d)
+        self.k_max = int(k_max)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -551,6 +552,11 @@ class Server:
         C = np.ascontiguousarray(C, dtype=np.uint32)
         R = None if ranges is None else np.ascontiguousarray(ranges, dtype=np.int64)
         A = None if arrival_ns is None else np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        # the library reads n rows of each: shapes are checked here
+        if Q.shape != (n, self.d) or k.shape != (n,) or C.shape != (n,):
+            raise ValueError(f"Q must be [n, {self.d}] and k, C [n]")
+        if (R is not None and R.shape != (n, 2)) or (A is not None and A.shape != (n,)):
+            raise ValueError("ranges must be [n, 2] and arrival_ns [n]")
         tickets = np.zeros(n, dtype=np.uint64)
         got = ctypes.c_uint32(0)
         rc = lib.hntl_server_submit(self._h, Q.ctypes.data_as(_P), n, k.ctypes.data_as(_P), C.ctypes.data_as(_P),
@@ -562,17 +568,19 @@ class Server:
         return tickets[: got.value]
 
     def poll(self, ticket, k, timeout_ms=10000):
-        """(ids int64 [k], dist f32 [k]), or None on timeout."""
+        """(ids int64 [k], dist f32 [k]) of a request submitted with this k,
+        or None on timeout."""
         import numpy as np
 
-        ids = np.zeros(k, dtype=np.int64)
-        dist = np.zeros(k, dtype=np.float32)
+        # room for the request's own k (up to k_max), whatever k the caller passes
+        ids = np.zeros(max(int(k), self.k_max), dtype=np.int64)
+        dist = np.zeros(max(int(k), self.k_max), dtype=np.float32)
         rc = lib.hntl_server_poll(self._h, int(ticket), ids.ctypes.data_as(_P), dist.ctypes.data_as(_P),
                                   int(timeout_ms))
         if rc == ETIMEOUT:
             return None
         _check(rc)
-        return ids, dist
+        return ids[:k], dist[:k]
 
     def poll_many(self, tickets, done, ids=None, dist=None, timeout_ms=0):
         """Collect every completed request among `tickets` (numpy uint64) whose
@@ -581,8 +589,16 @@ class Server:
         Returns the number collected by this call."""
         import numpy as np
 
-        assert tickets.dtype == np.uint64 and done.dtype == np.uint8 and tickets.flags.c_contiguous
+        n = len(tickets)
+        if tickets.dtype != np.uint64 or not tickets.flags.c_contiguous or tickets.ndim != 1:
+            raise ValueError("tickets must be a contiguous uint64 vector")
+        if done.dtype != np.uint8 or not done.flags.c_contiguous or done.shape != (n,):
+            raise ValueError("done must be a contiguous uint8 vector as long as tickets")
         stride = 0 if ids is None and dist is None else (ids if ids is not None else dist).shape[1]
+        for a, dt in ((ids, np.int64), (dist, np.float32)):
+            if a is not None and (a.dtype != dt or not a.flags.c_contiguous or a.ndim != 2 or a.shape[0] < n or
+                                  a.shape[1] != stride):
+                raise ValueError("ids / dist must be contiguous [len(tickets), stride] int64 / float32")
         got = ctypes.c_uint32(0)
         rc = lib.hntl_server_poll_many(self._h, tickets.ctypes.data_as(_P), len(tickets),
                                        None if ids is None else ids.ctypes.data_as(_P),

@@ -195,3 +195,28 @@ def test_int16_quantisation_host_rejects_bad_offsets():
         hntl.int16_quantize_host(Z, rho, np.array([0, 3, 2, 4]))
     with pytest.raises(ValueError):
         hntl.int16_quantize_host(Z, rho, np.array([0, 3]))
+
+
+def test_server_wrapper_checks_shapes_before_the_library_reads_them():
+    """The server's host entry points read n rows of every array they are
+    given: the binding refuses mismatched shapes before calling them (checked
+    on a wrapper with no server behind it, so no call is made)."""
+    srv = object.__new__(hntl.Server)
+    srv._h, srv.d, srv.k_max = None, 8, 10
+    Q = np.zeros((4, 8), np.float32)
+    k = np.full(4, 10, np.uint32)
+    with pytest.raises(ValueError):
+        srv.submit(np.zeros((4, 7), np.float32), k, k)  # wrong d
+    with pytest.raises(ValueError):
+        srv.submit(Q, k[:3], k)  # k shorter than Q
+    with pytest.raises(ValueError):
+        srv.submit(Q, k, k, ranges=np.zeros((4, 3), np.int64))
+    with pytest.raises(ValueError):
+        srv.submit(Q, k, k, arrival_ns=np.zeros(3, np.int64))
+    tickets = np.zeros(4, np.uint64)
+    with pytest.raises(ValueError):
+        srv.poll_many(tickets, np.zeros(3, np.uint8))  # done shorter than tickets
+    with pytest.raises(ValueError):
+        srv.poll_many(tickets, np.zeros(4, np.uint8), ids=np.zeros((3, 10), np.int64))  # too few rows
+    with pytest.raises(ValueError):
+        srv.poll_many(tickets, np.zeros(4, np.uint8), ids=np.zeros((4, 10), np.int32))  # wrong dtype
