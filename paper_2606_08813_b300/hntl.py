@@ -321,8 +321,9 @@ class Index:
         nq, d = int(Q.shape[0]), int(self.desc.d)
         if Q.is_cuda or Q.dtype != torch.float32 or tuple(Q.shape) != (nq, d) or not Q.is_contiguous():
             raise ValueError("Q must be a contiguous CPU float32 tensor [nq, d]")
-        if filters is not None and (filters.is_cuda or filters.dtype != torch.int64):
-            raise ValueError("filters must be a CPU int64 tensor [nq, 2]")
+        if filters is not None and (filters.is_cuda or filters.dtype != torch.int64 or
+                                    tuple(filters.shape) != (nq, 2) or not filters.is_contiguous()):
+            raise ValueError("filters must be a contiguous CPU int64 tensor [nq, 2]")
         ids = torch.empty(nq, k, dtype=torch.int64, pin_memory=Q.is_pinned())
         dist = torch.empty(nq, k, dtype=torch.float32, pin_memory=Q.is_pinned())
         nb = int(lib.hntl_search_host_workspace_bytes(self._h, max(nq, 1), k, C, nprobe, int(filters is not None)))
@@ -381,6 +382,8 @@ def search_probes(index: Index, Q: torch.Tensor, probes: torch.Tensor, k: int, C
     nq, nprobe = int(probes.shape[0]), int(probes.shape[1])
     _dev_tensor(Q, torch.float32, (nq, int(index.desc.d)), index.device, "Q")
     _dev_tensor(probes, torch.int32, (nq, nprobe), index.device, "probes")
+    if filters is not None:
+        _dev_tensor(filters, torch.int64, (nq, 2), index.device, "filters")
     Ce = max(C, k)
     ids = torch.empty(nq, k, dtype=torch.int64, device=Q.device)
     dist = torch.empty(nq, k, dtype=torch.float32, device=Q.device)
@@ -448,6 +451,10 @@ class Router:
         B = int(X.shape[0])
         _dev_tensor(X, torch.float32, (B, self.d), self.device, "X")
         _dev_tensor(T, torch.float32, (B, self.G), self.device, "T")
+        if loss is not None:  # the loss kernel adds into loss[0] on the device
+            _dev_tensor(loss, torch.float32, tuple(loss.shape), self.device, "loss")
+            if loss.numel() < 1:
+                raise ValueError("loss must hold at least one element")
         _check(lib.hntl_router_step(self._h, _ptr(X), _ptr(T), B, float(lr), float(wd), int(update), _ptr(loss),
                                     _stream(stream)))
 
