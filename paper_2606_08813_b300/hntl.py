@@ -409,9 +409,15 @@ class Router:
         import numpy as np
 
         W1, b1, W2, b2, W3, b3 = [np.ascontiguousarray(p, dtype=np.float32) for p in params]
+        if W1.ndim != 2 or W2.ndim != 2 or W3.ndim != 2:
+            raise ValueError("W1, W2, W3 must be matrices")
         self.h1, self.d = W1.shape
         self.h2 = W2.shape[0]
         self.G = W3.shape[0]
+        # the library reads each array at the sizes these imply
+        if (W2.shape != (self.h2, self.h1) or W3.shape != (self.G, self.h2) or b1.shape != (self.h1,) or
+                b2.shape != (self.h2,) or b3.shape != (self.G,)):
+            raise ValueError("parameters must be W1 [h1, d], b1 [h1], W2 [h2, h1], b2 [h2], W3 [G, h2], b3 [G]")
         self.max_batch = int(max_batch)
         self.device = device
         self._keep = (W1, b1, W2, b2, W3, b3)

@@ -220,3 +220,23 @@ def test_server_wrapper_checks_shapes_before_the_library_reads_them():
         srv.poll_many(tickets, np.zeros(4, np.uint8), ids=np.zeros((3, 10), np.int64))  # too few rows
     with pytest.raises(ValueError):
         srv.poll_many(tickets, np.zeros(4, np.uint8), ids=np.zeros((4, 10), np.int32))  # wrong dtype
+
+
+def test_router_parameters_must_agree_before_the_library_reads_them():
+    from oracle import router_oracle as R
+
+    params = R.init_params(16, 24, 32, 8, seed=1)
+    for i, bad in ((1, np.zeros(23, np.float32)), (2, np.zeros((32, 23), np.float32)), (5, np.zeros(9, np.float32))):
+        p = list(params)
+        p[i] = bad
+        with pytest.raises(ValueError):
+            hntl.Router(p, max_batch=8)
+
+
+def test_router_parameters_that_agree_pass_the_shape_checks():
+    from oracle import router_oracle as R
+
+    try:
+        hntl.Router(R.init_params(16, 24, 32, 8, seed=1), max_batch=8).close()
+    except hntl.HntlError:
+        pass  # no GPU here: the library itself refuses, after the checks passed
