@@ -456,6 +456,24 @@ def test_filter_equals_search_on_filtered_subset():
         assert res["out_id"][qi].tolist() == want
 
 
+def test_mode_a_filter_full_basis_equals_filtered_brute_force():
+    """Mode A with range filters: with r = d the reconstruction mu + U^T z is
+    the row itself, so with every grain probed and C = N the filtered Mode A
+    answer is brute force over the rows that pass."""
+    X, Q, _ = _clustered(300, 8, 3, 12, 73)
+    attr = synth.attributes(300, 7, span=1000).numpy()
+    ranges = synth.range_filters(12, 8, span=1000, selectivity=0.3, frac_filtered=0.6).numpy()
+    idx = O.build_index(X, 3, 8, synth.uniforms(3, 2).numpy())
+    res = O.search(idx, X, Q, 5, 300, 3, attr=attr, ranges=ranges, mode="A")
+    for qi in range(len(Q)):
+        keep = np.nonzero((attr >= ranges[qi, 0]) & (attr <= ranges[qi, 1]))[0]
+        sub_ids, sub_d, _ = O.brute_force(X[keep], Q[qi:qi + 1], 5)
+        want = [int(keep[i]) if i >= 0 else -1 for i in sub_ids[0]]
+        assert res["out_id"][qi].tolist() == want
+        ok = sub_ids[0] >= 0
+        np.testing.assert_allclose(res["out_d"][qi][:5][ok], sub_d[0][ok], rtol=1e-5, atol=1e-5)  # k + 1 kept
+
+
 def test_nprobe_all_c_all_recall_one():
     X, Q, _ = _clustered(800, 32, 8, 30, 81)
     G = 8
