@@ -387,10 +387,17 @@ int hntl_server_poll_many(hntl_server* server, const uint64_t* tickets, uint32_t
                           float* h_dist, uint32_t stride, uint8_t* done, uint32_t timeout_ms, uint32_t* n_done);
 
 /* Wait up to timeout_ms for a request; on success copy its k ids and
- * distances to host buffers and release the ticket. HNTL_ETIMEOUT if it is
- * not done in time (the ticket stays valid), HNTL_EINVAL for an unknown ticket. */
+ * distances to host buffers (each must hold the request's k entries; k_max
+ * always suffices) and release the ticket. HNTL_ETIMEOUT if it is not done in
+ * time (the ticket stays valid), HNTL_EINVAL for an unknown ticket, HNTL_ECUDA
+ * once the serving worker has stopped on a CUDA error (its unfinished
+ * requests never complete; the call returns as soon as the worker stops). */
 int hntl_server_poll(hntl_server* server, uint64_t ticket, int64_t* h_ids, float* h_dist, uint32_t timeout_ms);
 
+/* Latency record since creation or the last reset: completed requests,
+ * batches launched and their mean size, p50 / p99 / max latency from each
+ * request's arrival stamp to its completion, and the request slots the memory
+ * budget allows. hntl_server_reset_stats clears the record (not the slots). */
 int hntl_server_get_stats(hntl_server* server, hntl_server_stats* out);
 int hntl_server_reset_stats(hntl_server* server);
 
