@@ -240,3 +240,22 @@ def test_router_parameters_that_agree_pass_the_shape_checks():
         hntl.Router(R.init_params(16, 24, 32, 8, seed=1), max_batch=8).close()
     except hntl.HntlError:
         pass  # no GPU here: the library itself refuses, after the checks passed
+
+
+def test_binding_without_the_library_fails_loudly(tmp_path):
+    """No CPU fallback: a copy of the binding with no libhntl.so beside it
+    refuses to import (run in a child interpreter, so this process keeps its
+    loaded library)."""
+    import shutil
+    import subprocess
+    import sys
+
+    pkg = tmp_path / "paper_2606_08813_b300"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "paper_2606_08813_b300", "hntl.py"), pkg / "hntl.py")
+    (pkg / "__init__.py").write_text("")
+    code = "import paper_2606_08813_b300.hntl"
+    p = subprocess.run([sys.executable, "-c", code], cwd=str(tmp_path), capture_output=True, text=True,
+                       env={**os.environ, "PYTHONPATH": str(tmp_path)})
+    assert p.returncode != 0
+    assert "ImportError" in p.stderr and "libhntl.so is not built" in p.stderr
