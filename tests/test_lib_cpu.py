@@ -259,3 +259,22 @@ def test_binding_without_the_library_fails_loudly(tmp_path):
                        env={**os.environ, "PYTHONPATH": str(tmp_path)})
     assert p.returncode != 0
     assert "ImportError" in p.stderr and "libhntl.so is not built" in p.stderr
+
+
+def test_oracle_and_product_share_no_code():
+    """The oracle is test infrastructure: nothing in the product package
+    imports, loads or includes it, and it imports nothing from the package
+    (the seeded input generators are passed in by the tests)."""
+    import re
+
+    pkg = os.path.join(ROOT, "paper_2606_08813_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b|hntl_oracle|router_oracle|oracle/", src,
+                                     re.M), f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            src = open(os.path.join(ROOT, "oracle", f)).read()
+            assert not re.search(r"paper_2606_08813_b300|libhntl|hntl\.h", src), f
