@@ -278,3 +278,62 @@ def test_oracle_and_product_share_no_code():
         if f.endswith((".py", ".c", ".h")):
             src = open(os.path.join(ROOT, "oracle", f)).read()
             assert not re.search(r"paper_2606_08813_b300|libhntl|hntl\.h", src), f
+
+
+def test_server_wrapper_marshalling_against_a_fake_library(monkeypatch):
+    """submit / poll / poll_many pass pointers, counts and strides that a
+    library writing whole rows can use safely: a fake of the three calls
+    writes the request's own k results the way the library does."""
+    import ctypes as ct
+
+    k_of = {}
+
+    class Fake:
+        def hntl_server_submit(self, h, q, n, k, C, R, A, tickets, got):
+            ks = np.ctypeslib.as_array(ct.cast(k, ct.POINTER(ct.c_uint32)), (n,))
+            tk = np.ctypeslib.as_array(ct.cast(tickets, ct.POINTER(ct.c_uint64)), (n,))
+            for i in range(n):
+                tk[i] = 100 + i
+                k_of[100 + i] = int(ks[i])
+            got._obj.value = n
+            return hntl.OK
+
+        def _rows(self, t):
+            kk = k_of[int(t)]
+            return np.arange(kk, dtype=np.int64) + 1000 * int(t), np.arange(kk, dtype=np.float32) * 0.5
+
+        def hntl_server_poll(self, h, t, ids, dist, timeout):
+            a, b = self._rows(t)
+            ct.memmove(ids, a.ctypes.data, a.nbytes)  # the request's own k entries
+            ct.memmove(dist, b.ctypes.data, b.nbytes)
+            return hntl.OK
+
+        def hntl_server_poll_many(self, h, tickets, n, ids, dist, stride, done, timeout, n_done):
+            tk = np.ctypeslib.as_array(ct.cast(tickets, ct.POINTER(ct.c_uint64)), (n,))
+            dn = np.ctypeslib.as_array(ct.cast(done, ct.POINTER(ct.c_uint8)), (n,))
+            for i in range(n):
+                a, b = self._rows(tk[i])
+                if ids:
+                    ct.memmove(ids.value + i * stride * 8, a.ctypes.data, a.nbytes)
+                if dist:
+                    ct.memmove(dist.value + i * stride * 4, b.ctypes.data, b.nbytes)
+                dn[i] = 1
+            n_done._obj.value = n
+            return hntl.OK
+
+    monkeypatch.setattr(hntl, "lib", Fake())
+    srv = object.__new__(hntl.Server)
+    srv._h, srv.d, srv.k_max = None, 8, 10
+    k = np.array([10, 3, 7], np.uint32)
+    t = srv.submit(np.zeros((3, 8), np.float32), k, k)
+    assert t.tolist() == [100, 101, 102]
+    ids, dist = srv.poll(101, 3)
+    assert ids.tolist() == [101000, 101001, 101002] and dist.tolist() == [0.0, 0.5, 1.0]
+    ids, dist = srv.poll(100, 2)  # a k below the request's: the buffer still holds its 10 results
+    assert ids.tolist() == [100000, 100001]
+    done = np.zeros(3, np.uint8)
+    I = np.full((3, 10), -7, np.int64)
+    D = np.zeros((3, 10), np.float32)
+    assert srv.poll_many(t, done, I, D) == 3 and done.all()
+    assert I[1, :3].tolist() == [101000, 101001, 101002] and (I[1, 3:] == -7).all()
+    assert I[0].tolist() == list(range(100000, 100010)) and D[2, 6] == 3.0
