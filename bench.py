@@ -243,24 +243,83 @@ def traffic_from_profiles(workload: str, stage: str):
         return None
 
 
-def cpu_oracle_qps(idx_host, X_np, Q_np, k, C, nprobe, budget_s: float = 15.0, precision="fp32"):
+def _gap_sets_agree(g_ids, o_ids, o_ext, invalid, gap=1e-4):
+    """Gap rule: wherever the oracle's ranking has a relative gap above `gap`
+    after position m, the first m ids agree as sets."""
+    n_valid = sum(1 for x in o_ids if x != invalid)
+    if n_valid != sum(1 for x in g_ids if x != invalid):
+        return False
+    for m in range(1, n_valid + 1):
+        a, b = o_ext[m - 1], o_ext[m]
+        if np.isfinite(b) and (b - a) <= gap * max(abs(a), 1e-30):
+            continue
+        if set(g_ids[:m]) != set(o_ids[:m]):
+            return False
+    return True
+
+
+def parity_vs_oracle(gpu, ora, k, C, nprobe, gap=1e-4):
+    """Headline-batch rows against the oracle's search of the same queries:
+    probe sets, pools and top k under the gap rule (near ties at the routing
+    or pool boundary excluded and counted) and the largest relative distance
+    error of ids both sides hold."""
+    nq = ora["out_id"].shape[0]
+    Ce = max(C, k)
+    out = dict(queries=int(nq), route_excluded=0, topk_excluded=0, probe_sets_equal=0, pools_equal=0,
+               topk_equal=0, max_rel_err_pool=0.0, max_rel_err_topk=0.0)
+    for qi in range(nq):
+        pd = ora["probe_d"][qi]
+        if np.isfinite(pd[nprobe]) and (pd[nprobe] - pd[nprobe - 1]) <= gap * pd[nprobe - 1]:
+            out["route_excluded"] += 1
+            continue
+        out["probe_sets_equal"] += int(set(gpu["probe"][qi].tolist()) == set(ora["probe"][qi].tolist()))
+        for kind, gi_, gd_, oi_, od_, inv in (
+                ("pool", gpu["pool_ids"][qi], gpu["pool_d"][qi], ora["cand_id"][qi], ora["cand_d"][qi], 0xFFFFFFFF),
+                ("topk", gpu["ids"][qi], gpu["dist"][qi], ora["out_id"][qi], ora["out_d"][qi], -1)):
+            if kind == "topk":
+                cd = ora["cand_d"][qi]
+                if np.isfinite(cd[Ce]) and (cd[Ce] - cd[Ce - 1]) <= gap * cd[Ce - 1]:
+                    out["topk_excluded"] += 1
+                    continue
+            g_ids, o_ids = [int(x) for x in gi_], [int(x) for x in oi_]
+            out["pools_equal" if kind == "pool" else "topk_equal"] += int(_gap_sets_agree(g_ids, o_ids, od_, inv))
+            ref = {i: float(d) for i, d in zip(o_ids, od_) if i != inv}
+            errs = [abs(float(d) - ref[i]) / max(ref[i], 1e-30) for i, d in zip(g_ids, gd_) if i in ref]
+            key = "max_rel_err_pool" if kind == "pool" else "max_rel_err_topk"
+            if errs:
+                out[key] = max(out[key], max(errs))
+    out["max_rel_err_pool"] = float(f"{out['max_rel_err_pool']:.3g}")
+    out["max_rel_err_topk"] = float(f"{out['max_rel_err_topk']:.3g}")
+    return out
+
+
+def cpu_oracle_qps(idx_host, X_np, Q_np, k, C, nprobe, budget_s: float = 15.0, precision="fp32", first=None):
+    """The oracle's QPS on a bounded sample of the workload's queries. With
+    `first` (row indices), those queries are searched first (timed with the
+    rest) and their results returned for the parity sample."""
     from oracle import hntl_oracle as O
 
     O.build_c()
     if precision == "bf16-fp8":  # exported coordinates are already the decoded FP8 values
         X_np = O.bf16_to_f32(O.bf16_round(X_np)).reshape(X_np.shape)
+    oprec = "bf16-fp8-decoded" if precision == "bf16-fp8" else "fp32"
     n = 16
     t = 0.0
     done = 0
+    first_out = None
+    if first is not None:
+        t0 = time.perf_counter()
+        first_out = O.search(idx_host, X_np, Q_np[first], k, C, nprobe, precision=oprec)
+        t += time.perf_counter() - t0
+        done += len(first)
     while t < budget_s and done < Q_np.shape[0]:
         m = min(n, Q_np.shape[0] - done)
         t0 = time.perf_counter()
-        O.search(idx_host, X_np, Q_np[done:done + m], k, C, nprobe,
-                 precision="bf16-fp8-decoded" if precision == "bf16-fp8" else "fp32")
+        O.search(idx_host, X_np, Q_np[done:done + m], k, C, nprobe, precision=oprec)
         t += time.perf_counter() - t0
         done += m
         n = min(4 * n, 4096)
-    return done / t, done, O.threads()
+    return done / t, done, O.threads(), first_out
 
 
 ATTR_SPAN = 1 << 40
@@ -686,7 +745,7 @@ def run_ours(a, world, rank, local):
                    "nprobe": nprobe, "C": C, "k": k, "recall_at_10": None if rec != rec else round(rec, 4), "recall_queries": n_recall,
                    "recall_note": "skipped in profile mode" if a.profile_mode else "brute force, FP64 re-rank",
                    "sizes": w["sizes"], "l2": "no flush; per-step working set (probed coordinates, bases and "
-                   "gathered rows, ~0.5 GB) exceeds the 126 MB L2", "index_build_s": round(build_s, 2),
+                   "gathered rows: about 2 GB a 4096-query batch at 10M rows) exceeds the 126 MB L2", "index_build_s": round(build_s, 2),
                    "parallelism": f"replicas x{world}", "streams": a.streams,
                    "stage_timing": "CUDA events between stages, the same K batches on one stream",
                    "pool_survivors": surv_stats, "batch_latency_ms_p50": round(float(np.percentile(step_ms, 50)), 4),
@@ -711,13 +770,28 @@ def run_ours(a, world, rank, local):
     if prec == "bf16-fp8" and a.fp32_compare and X is not None:
         line["plain_fp32_same_data"] = run_fp32_compare(a, hntl, X, Q, w, sd, B, n_recall, truth, line)
     if rank == 0 and world == 1 and not a.no_cpu_baseline and not a.profile_mode:
+        # the headline batch 0 searched once more (untimed) with its pool and
+        # probes; 64 of its rows, spread over the batch, are the parity sample
+        # the oracle searches first inside its timed baseline
+        ids0, d0, pid0, pd0, pr0 = gi.search(batches[0], k, C, nprobe, return_pool=True, return_probe=True)
+        torch.cuda.synchronize()
+        rows = np.arange(0, B, max(1, B // 64))[:64]
+        gpu0 = dict(ids=ids0.cpu().numpy()[rows], dist=d0.cpu().numpy()[rows],
+                    pool_ids=pid0.cpu().numpy().view(np.uint32)[rows], pool_d=pd0.cpu().numpy()[rows],
+                    probe=pr0.cpu().numpy()[rows])
         host = gi.export()
         Xn = X.cpu().numpy()
-        Qn = Q[:4096].cpu().numpy()
-        q, nq_done, cores = cpu_oracle_qps(host, Xn, Qn, k, C, nprobe, budget_s=a.cpu_budget, precision=prec)
+        Qn = Q[:max(4096, B)].cpu().numpy()
+        q, nq_done, cores, ora0 = cpu_oracle_qps(host, Xn, Qn, k, C, nprobe, budget_s=a.cpu_budget,
+                                                  precision=prec, first=rows)
         line["cpu_baseline"] = {"value": round(q, 2), "unit": "queries/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{nq_done} queries of the same workload against the same index "
                                           f"(FP64 oracle search, OpenMP over queries)"}
+        line["parity_sample"] = dict(parity_vs_oracle(gpu0, ora0, k, C, nprobe),
+                                     rows="64 rows of headline batch 0 (every B/64-th), as searched in the "
+                                          "timed launch configuration, against the oracle on the exported index",
+                                     rule="ids equal as sets wherever the oracle's ranking has a gap > 1e-4 "
+                                          "relative; near ties at the routing or pool boundary excluded")
     if rank == 0:
         print(json.dumps(line), flush=True)
 

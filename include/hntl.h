@@ -224,12 +224,17 @@ int hntl_route(const hntl_index* idx, const float* d_queries, uint32_t nq, uint3
  * service to callers). Some callers cannot allocate device memory at query
  * time, for example a host application that reserves the whole GPU at start-up
  * and gives its plug-ins no allocator, or a latency-critical loop in which a
- * cudaMalloc would synchronise the device. This call computes what hntl_route
- * computes (the nprobe nearest centres of each query and their FP32 squared
- * distances into d_probe / d_probe_dist, nq x nprobe, device) without any
- * caller workspace and without allocating: its scratch is one fixed device
- * array inside the library of 2^21 floats (8 MiB), held by every GPU that
- * loads the library until the process exits.
+ * cudaMalloc would synchronise the device. This call makes the selection
+ * hntl_route makes (the nprobe nearest centres of each query by (distance,
+ * grain), with their FP32 squared distances, into d_probe / d_probe_dist,
+ * nq x nprobe, device) without any caller workspace and without allocating:
+ * its scratch is one fixed device array inside the library of 2^21 floats
+ * (8 MiB), held by every GPU that loads the library until the process exits.
+ * It always forms each distance in the direct SIMT form (one FP32 sum of
+ * (q_t - mu_t)^2 per centre), while hntl_route may take tensor-core
+ * approximations refined in another summation order; the distances then agree
+ * to FP32 rounding, and where two centres are closer than that rounding the
+ * two calls can order them, or pick the nprobe-th, differently.
  *   - nq * G must not exceed 2^21 (2,097,152); larger batches return
  *     HNTL_EINVAL with a message. Route them in slices.
  *   - FP32 indices only (HNTL_EINVAL for the precision form).
@@ -261,6 +266,27 @@ int hntl_search_probes(const hntl_index* idx, const float* d_queries, uint32_t n
  * was recomputed from every probed row. */
 int hntl_search_survivors(const hntl_index* idx, const void* d_ws, size_t ws_bytes, uint32_t nq, uint32_t C,
                           uint32_t nprobe, uint32_t* d_counts, void* stream);
+
+/* Diagnostic: the scan's work-item counters of the last hntl_search of the
+ * precision form that used this workspace with the same nq, C and nprobe,
+ * copied to d_stats (device, 5 uint32) on `stream`: [0] dense items claimed
+ * by the tensor-core scan (at least [1]), [1] dense items (at least kSTDense =
+ * 8 live pairs), [2] sparse items with few live pairs, [3] sparse items
+ * claimed by the direct-form scan (at least [2] + [4]), [4] costly sparse
+ * items (taken first). All zero for the FP32 and 16-bit forms, which scan
+ * every probed block in one kernel. */
+int hntl_search_scan_stats(const hntl_index* idx, const void* d_ws, size_t ws_bytes, uint32_t nq, uint32_t C,
+                           uint32_t nprobe, uint32_t* d_stats, void* stream);
+
+/* Test hook (the paper has no counterpart): caps the grid of every persistent
+ * kernel of the search (tensor-core routing, both projections, both scans of
+ * the precision form) at `ctas` CTAs, 0 restoring the default of about one
+ * per SM. A capped kernel still processes every work item, each CTA looping
+ * over many of them, so a small test case exercises the multi-item paths
+ * (accumulator ping-pong, mbarrier phases carried across items, prefetch of
+ * the next item) that full-size batches take. Process-wide; set it only
+ * while no search runs. Always HNTL_OK. */
+int hntl_debug_set_persistent_cap(uint32_t ctas);
 
 /* Device status word of an index (blocking read): bit 0 = a bounded
  * device-side wait gave up (kernels then skip their results), bit 1 = an

@@ -287,6 +287,11 @@ int64_t or_lloyd(const float* X, int64_t n, int64_t d, int64_t G, double* M, int
  * Qp (may be NULL) is the query as routed and projected (the precision form
  * rounds it to BF16); the rerank always uses Q.
  *
+ * probe_in (may be NULL): nq x nprobe grain ids that replace step 1 (a
+ * router's probes); each is used in the given order with its distance
+ * ||q - mu_g||^2, and the (nprobe+1)-th routing distance is reported as +inf
+ * (there is no routing boundary).
+ *
  * Per query:
  *   1. routing: ||q - mu_g||^2 for every g, the nprobe smallest by (dist, g);
  *   2. per probed grain: v' = q - mu_g, z_q = U_g v', rho_q = ||v' - U_g^T z_q||^2;
@@ -303,7 +308,8 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
                const float* Q, const float* Qp, int64_t nq, int64_t k, int64_t C, int64_t nprobe,
                const int64_t* ranges, int32_t* probe, double* probe_d, uint32_t* cand_id, double* cand_d,
                int64_t* out_id, double* out_d, int64_t mode, const int64_t* pos_of_id,
-               const int32_t* grain_of_pos, const double* qdelta, const double* qdres) {
+               const int32_t* grain_of_pos, const double* qdelta, const double* qdres,
+               const int32_t* probe_in) {
 #pragma omp parallel
   {
     pair_t* route = (pair_t*)malloc(sizeof(pair_t) * (size_t)G);
@@ -319,17 +325,25 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
     for (int64_t qi = 0; qi < nq; ++qi) {
       const float* q = Q + qi * d;
       const float* qp = Qp ? Qp + qi * d : q; /* query as routed and projected */
-      /* 1. centroid routing */
-      for (int64_t g = 0; g < G; ++g) {
-        route[g].dist = sq_diff_f32(qp, M + g * d, d);
-        route[g].key = g;
+      /* 1. centroid routing, or the given probes */
+      if (probe_in) {
+        for (int64_t p = 0; p < nprobe; ++p) {
+          const int64_t g = probe_in[qi * nprobe + p];
+          route[p].dist = sq_diff_f32(qp, M + g * d, d);
+          route[p].key = g;
+        }
+      } else {
+        for (int64_t g = 0; g < G; ++g) {
+          route[g].dist = sq_diff_f32(qp, M + g * d, d);
+          route[g].key = g;
+        }
+        qsort(route, (size_t)G, sizeof(pair_t), pair_cmp);
       }
-      qsort(route, (size_t)G, sizeof(pair_t), pair_cmp);
       for (int64_t p = 0; p < nprobe; ++p) {
         probe[qi * nprobe + p] = (int32_t)route[p].key;
         probe_d[qi * (nprobe + 1) + p] = route[p].dist;
       }
-      probe_d[qi * (nprobe + 1) + nprobe] = nprobe < G ? route[nprobe].dist : INFINITY;
+      probe_d[qi * (nprobe + 1) + nprobe] = (nprobe < G && !probe_in) ? route[nprobe].dist : INFINITY;
       /* 2-4. projection, scan, pool */
       pool.n = 0;
       for (int64_t p = 0; p < nprobe; ++p) {

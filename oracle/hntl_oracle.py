@@ -74,7 +74,7 @@ def _c():
             lib.or_lloyd.argtypes = [P, I, I, I, P, I, P]
             lib.or_lloyd.restype = I
             lib.or_search.argtypes = [P, P, I, I, I, P, P, P, P, P, P, P, P, I, I, I, I, P,
-                                      P, P, P, P, P, P, I, P, P, P, P]
+                                      P, P, P, P, P, P, I, P, P, P, P, P]
             lib.or_threads.restype = ctypes.c_int
             lib.or_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -214,8 +214,11 @@ def build_index(X, G: int, r: int, u, train_idx=None, max_iter: int = 25, keep_f
 
 
 def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=None, rho=None, precision="fp32",
-           mode: str = "B"):
+           mode: str = "B", probes=None):
     """Mode B (default) or Mode A search of every query (see hntl_oracle.c or_search).
+
+    probes (optional, [nq, nprobe] grain ids): replaces the centroid routing
+    of step 1 (a learned router's probes); the rest of the path is unchanged.
 
     mode="B": the pool is reranked by exact L2 to the raw rows (sec. 2.1 step 4).
     mode="A": the pool is reranked by L2 to each row's reconstruction
@@ -281,9 +284,14 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
         pos_of_id = np.zeros(len(ids), dtype=np.int64)
         pos_of_id[ids] = np.arange(len(ids), dtype=np.int64)
         grain_of_pos = np.repeat(np.arange(G, dtype=np.int32), np.diff(off)).astype(np.int32)
+    pin = None
+    if probes is not None:
+        pin = np.ascontiguousarray(probes, dtype=np.int32)
+        if pin.shape != (nq, nprobe) or pin.min() < 0 or pin.max() >= G:
+            raise ValueError("probes must be [nq, nprobe] grain ids")
     _c().or_search(_p(M), _p(U), G, d, r, _p(off), _p(ids), _p(Zs), _p(rhos), _p(X), _p(attr_a), _p(Q), _p(Qp), nq,
                    k, C, nprobe, _p(rng), _p(probe), _p(probe_d), _p(cand_id), _p(cand_d), _p(out_id), _p(out_d),
-                   1 if mode == "A" else 0, _p(pos_of_id), _p(grain_of_pos), _p(qdelta), _p(qdres))
+                   1 if mode == "A" else 0, _p(pos_of_id), _p(grain_of_pos), _p(qdelta), _p(qdres), _p(pin))
     return dict(probe=probe, probe_d=probe_d, cand_id=cand_id, cand_d=cand_d, out_id=out_id, out_d=out_d)
 
 

@@ -117,6 +117,27 @@ def adamw(params, grads, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, 
     return out_p, out_m, out_v
 
 
+def route(params, Q, nprobe, tau, centroid_probe, round_bf16=True):
+    """Learned routing of each query: the nprobe grains of largest logit
+    (ties to the lower grain id), kept when their softmax mass reaches tau,
+    otherwise the query's centroid probes (centroid_probe [nq, nprobe]).
+    Returns (probe i32 [nq, nprobe], fell_back bool [nq], mass f64 [nq],
+    logits f64 [nq, G])."""
+    L = forward(params, Q, round_bf16)["L"]
+    nq, G = L.shape
+    probe = np.zeros((nq, nprobe), dtype=np.int32)
+    mass = np.zeros(nq)
+    fell = np.zeros(nq, dtype=bool)
+    for i in range(nq):
+        order = sorted(range(G), key=lambda g: (-L[i, g], g))[:nprobe]
+        m = L[i].max()
+        e = np.exp(L[i] - m)
+        mass[i] = e[order].sum() / e.sum()
+        fell[i] = not (mass[i] >= tau)
+        probe[i] = np.asarray(centroid_probe[i]) if fell[i] else np.asarray(order)
+    return probe, fell, mass, L
+
+
 def soft_targets(neighbour_ids, assign, G):
     """t_g = (# of a query's neighbour ids whose grain is g) / (# neighbours)."""
     nb = np.asarray(neighbour_ids)

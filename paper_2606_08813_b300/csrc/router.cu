@@ -609,11 +609,11 @@ int router_route_probes(Router& R, const Index& I, const float* Q, uint32_t nq, 
   int rc = route_only(I, Q, nq, nprobe, ws, route_ws, cprobe, cdist, st);
   if (rc) return rc;
   if (nfallback) HNTL_CUDA_TRY(cudaMemsetAsync(nfallback, 0, 4, st));
-  static thread_local bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_route_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kSelWarps * kMaxG * (int)sizeof(float));
-    attr = true;
+  static thread_local int attr_dev = -1;  // device whose select attribute this thread has set
+  if (attr_dev != I.device) {
+    HNTL_CUDA_TRY(cudaFuncSetAttribute(k_route_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSelWarps * (int)kMaxG * (int)sizeof(float)));
+    attr_dev = I.device;
   }
   for (uint32_t s = 0; s < nq; s += R.max_batch) {
     const uint32_t b = std::min(R.max_batch, nq - s);

@@ -16,6 +16,7 @@
 #include <cudaTypedefs.h>
 
 #include <array>
+#include <atomic>
 #include <functional>
 #include <cfloat>
 #include <cstdint>
@@ -38,6 +39,17 @@ namespace hntl {
 
 namespace {
 
+// Test hook (hntl_debug_set_persistent_cap): when non-zero, the largest grid
+// any persistent kernel of the search launches, so that small cases make every
+// CTA loop over many work items the way full-size batches do.
+std::atomic<uint32_t> g_persistent_cap{0};
+
+// Grid of a persistent kernel that wants `want` CTAs (at least 1).
+unsigned persistent_grid(size_t want) {
+  const uint32_t cap = g_persistent_cap.load(std::memory_order_relaxed);
+  if (cap && want > cap) want = cap;
+  return (unsigned)std::max<size_t>(want, 1);
+}
 
 // ------------------------------------------------------------------ bounded-wait self test
 
@@ -366,7 +378,7 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
     }
     // persistent: one CTA per SM at most
     const size_t tiles = (size_t)((I.G + kRTN - 1) / kRTN) * ((nq + kRTM - 1) / kRTM);
-    const unsigned grid = (unsigned)std::min<size_t>(tiles, (size_t)I.num_sms);
+    const unsigned grid = persistent_grid(std::min<size_t>(tiles, (size_t)I.num_sms));
     const size_t rsmem = refine_smem_bytes((int)I.d, (int)I.G, (int)nprobe);
     float eps_dot = 0.f, eps_norm = 0.f;
     route_margin(bf16, (int)I.d, &eps_dot, &eps_norm);
@@ -390,11 +402,11 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
   dim3 grid((I.G + kRT - 1) / kRT, (nq + kRT - 1) / kRT);
   k_route_dist<<<grid, 256, 0, st>>>(Qd, I.M, (int)nq, (int)I.G, (int)I.d, w.route_d);
   size_t smem = (size_t)kSelWarps * I.G * sizeof(float);
-  static thread_local bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_route_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kSelWarps * kMaxG * (int)sizeof(float));
-    attr_set = true;
+  static thread_local int attr_sel = -1;  // device whose select attribute this thread has set
+  if (attr_sel != I.device) {
+    HNTL_CUDA_TRY(cudaFuncSetAttribute(k_route_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSelWarps * (int)kMaxG * (int)sizeof(float)));
+    attr_sel = I.device;
   }
   k_route_select<<<(nq + kSelWarps - 1) / kSelWarps, kSelWarps * 32, smem, st>>>(w.route_d, (int)nq, (int)I.G,
                                                                                   (int)nprobe, w.probe, w.probe_d);
@@ -412,7 +424,7 @@ int launch_project_tc_n(const Index& I, uint32_t nq, uint32_t P, const Ws& w, cu
   }
   // persistent: one CTA per SM at most, never more CTAs than work items can exist
   const size_t max_items = ((size_t)P / kPSlot + I.G + kPSlots - 1) / kPSlots;
-  const unsigned grid = (unsigned)std::min<size_t>(max_items, (size_t)I.num_sms);
+  const unsigned grid = persistent_grid(std::min<size_t>(max_items, (size_t)I.num_sms));
   k_project_tc<RN><<<grid, kPThreads, ProjTc<RN>::kSmem, st>>>(w.Qh, I.Mh, I.mapU, I.gram, (int)I.d, (int)I.r,
                                                                w.slots, w.grp2_off + I.G, w.pair_q, w.pair_vn,
                                                                w.zq, w.rhoq, I.d_err);
@@ -447,11 +459,11 @@ void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, 
     k_scan_classify<<<(unsigned)((max_items * 32 + 255) / 256), 256, 0, st>>>(
         w.scan_items, w.scan_off + I.G, w.need_cnt, w.need_list, w.pair_off, w.pair_q, w.rhoq, w.tau, I.blk_rho_min,
         I.blk_z0, w.zq, (int)I.r, w.dense_items, w.sparse_items, (uint32_t)max_items, lists);
-    k_scan_sparse<RT><<<(unsigned)std::min<size_t>(max_items, (size_t)I.num_sms * 6), kSPThreads, 0, st>>>(
+    k_scan_sparse<RT><<<persistent_grid(std::min<size_t>(max_items, (size_t)I.num_sms * 6)), kSPThreads, 0, st>>>(
         w.sparse_items, (uint32_t)max_items, lists, lists + 2, I.blk_off, I.grain_rows, I.Z8b, I.scale, I.rho, I.ids, I.attr_b, (int)I.r,
         (int)I.rp,
         w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, I.blk_z0, filter, w.cap, w.cnt, w.surv);
-    k_scan_tc<RT><<<(unsigned)std::min<size_t>(max_items, (size_t)I.num_sms * 2), kSTThreads, ScanTc<RT>::kSmem,
+    k_scan_tc<RT><<<persistent_grid(std::min<size_t>(max_items, (size_t)I.num_sms * 2)), kSTThreads, ScanTc<RT>::kSmem,
                     st>>>(
         w.dense_items, lists, w.cnt + nq, I.blk_off, I.grain_rows, I.Z8b, I.scale, I.crow, I.rho, I.ids, I.attr_b,
         (int)I.r, (int)I.rp, w.need_cnt, w.need_list, w.pair_off, w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min,
@@ -576,7 +588,7 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
     size_t smem = (size_t)kPairsPerGroup * I.d * sizeof(float);
     if (smem > 48 * 1024)
       HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    unsigned grid = (unsigned)std::min<size_t>((size_t)P / kPairsPerGroup + I.G, 148 * 16);
+    unsigned grid = persistent_grid(std::min<size_t>((size_t)P / kPairsPerGroup + I.G, (size_t)I.num_sms * 16));
     k_project<false><<<grid, 256, smem, st>>>(Qd, I.M, I.U, (int)I.d, (int)I.r, (int)I.G, w.grp_off, w.pair_off,
                                               w.pair_q, w.zq, w.rhoq);
     if (I.precision == HNTL_PREC_INT16)
@@ -851,6 +863,25 @@ int hntl_search_probes(const hntl_index* idx, const float* d_queries, uint32_t n
   if (!d_probe_in && nq) return hntl::fail(HNTL_EINVAL, "null probe list");
   return hntl::search(idx->I, d_queries, nq, k, C, nprobe, d_filter, d_ws, ws_bytes, d_out_ids, d_out_dist,
                       d_cand_ids, d_cand_dist, nullptr, static_cast<cudaStream_t>(stream), d_probe_in);
+}
+
+int hntl_debug_set_persistent_cap(uint32_t ctas) {
+  hntl::clear_error();
+  hntl::g_persistent_cap.store(ctas, std::memory_order_relaxed);
+  return HNTL_OK;
+}
+
+int hntl_search_scan_stats(const hntl_index* idx, const void* d_ws, size_t ws_bytes, uint32_t nq, uint32_t C,
+                           uint32_t nprobe, uint32_t* d_stats, void* stream) {
+  hntl::clear_error();
+  if (!idx || !d_ws || !d_stats) return hntl::fail(HNTL_EINVAL, "null argument");
+  uint32_t Ce = C;
+  if (hntl::check_params(idx->I, nq, 1, Ce, nprobe)) return HNTL_EINVAL;
+  const hntl::Ws w = hntl::carve(idx->I, nq, Ce, nprobe, const_cast<void*>(d_ws));
+  if (ws_bytes < w.bytes) return hntl::fail(HNTL_EINVAL, "workspace too small");
+  HNTL_CUDA_TRY(cudaMemcpyAsync(d_stats, w.cnt + nq, sizeof(uint32_t) * 5, cudaMemcpyDeviceToDevice,
+                                static_cast<cudaStream_t>(stream)));
+  return HNTL_OK;
 }
 
 int hntl_selftest_wait_timeout(const hntl_index* idx, uint32_t polls, void* stream) {

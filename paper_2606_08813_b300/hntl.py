@@ -526,6 +526,23 @@ def search_survivors(index: Index, ws: torch.Tensor, nq: int, C: int, nprobe: in
     return out
 
 
+lib.hntl_search_scan_stats.argtypes = [_P, _P, _SZ, _U32, _U32, _U32, _P, _P]
+lib.hntl_debug_set_persistent_cap.argtypes = [_U32]
+
+
+def search_scan_stats(index: Index, ws: torch.Tensor, nq: int, C: int, nprobe: int) -> dict:
+    """Scan work-item counters of the last search run in workspace `ws` (see hntl_search_scan_stats)."""
+    out = torch.zeros(5, dtype=torch.int32, device=ws.device)
+    _check(lib.hntl_search_scan_stats(index.handle, _ptr(ws), ws.numel(), nq, C, nprobe, _ptr(out), None))
+    v = [int(x) for x in out.cpu().tolist()]
+    return dict(dense_claimed=v[0], dense=v[1], sparse_light=v[2], sparse_claimed=v[3], sparse_heavy=v[4])
+
+
+def set_persistent_cap(ctas: int):
+    """Cap every persistent kernel's grid at `ctas` CTAs (0 = default); a test hook."""
+    _check(lib.hntl_debug_set_persistent_cap(int(ctas)))
+
+
 def selftest_wait_timeout(index: Index, polls: int = 64):
     _check(lib.hntl_selftest_wait_timeout(index.handle, int(polls), None))
 

@@ -1,0 +1,149 @@
+"""Parity of the persistent kernels on the paths full-size batches take.
+
+The routing GEMM, both projections and both scans of the precision form run
+persistent grids (about one CTA per SM) that loop over work items. Small cases
+give every CTA one item at most, so these tests either cap the grids
+(hntl_debug_set_persistent_cap) until each CTA loops over many items, carrying
+its mbarrier phases, TMEM accumulators and prefetches from item to item, or
+run a batch of the full shape (d = 768, 4096 queries, nprobe = 32, C = 200) on
+a GPU-built index and compare a sample of its queries with the oracle
+searching the exported index. Tolerances and the gap rule are those of
+tests/parity.py."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hntl_oracle as O
+from paper_2606_08813_b300 import synth
+
+from cases import clustered_case, partition_index, write
+from parity import compare_search
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hntl():
+    from paper_2606_08813_b300 import build_lib
+
+    build_lib.build()
+    from paper_2606_08813_b300 import hntl as h
+
+    yield h
+    h.set_persistent_cap(0)
+
+
+def _search(h, gi, Q, k, C, nprobe):
+    Qd = torch.from_numpy(np.ascontiguousarray(Q)).cuda()
+    ws = gi.workspace(gi.workspace_bytes(len(Q), k, C, nprobe))
+    ids, dist, pid, pd, probe = gi.search(Qd, k, C, nprobe, return_pool=True, return_probe=True, ws=ws)
+    torch.cuda.synchronize()
+    stats = h.search_scan_stats(gi, ws, len(Q), C, nprobe)
+    return dict(ids=ids.cpu().numpy(), dist=dist.cpu().numpy(), pool_ids=pid.cpu().numpy().view(np.uint32),
+                pool_d=pd.cpu().numpy(), probe=probe.cpu().numpy()), stats
+
+
+@pytest.fixture(scope="module")
+def clustered256(tmp_path_factory):
+    """8 clusters split into 64 grains (d = 256, r = 32): each query probes
+    most grains of its own cluster, so many pairs stay live in the scan."""
+    X, Q, idx = clustered_case(40000, 256, 8, 64, 32, 1024, seed=4242, train=256 * 64)
+    d = tmp_path_factory.mktemp("persist")
+    return X, Q, idx, write(d, "c256_fp32", idx, X), write(d, "c256_p", idx, X, precision="bf16-fp8")
+
+
+@pytest.mark.parametrize("cap", [1, 3, 0])
+def test_precision_form_with_capped_grids(hntl, clustered256, cap):
+    """Routing: 8 tiles of 128 queries x 256 centres; projection: 16384 pairs
+    in 32-pair slots, >= 128 items; the scans: every item of the batch. With
+    cap 1 a single CTA of each kernel walks all of them."""
+    X, Q, idx, _, pp = clustered256
+    k, C, nprobe = 10, 100, 16
+    ora = O.search(idx, X, Q, k, C, nprobe, precision="bf16-fp8")
+    hntl.set_persistent_cap(cap)
+    try:
+        gi = hntl.Index.load(pp, 0, hntl.PREC_BF16_FP8)
+        gpu, stats = _search(hntl, gi, Q, k, C, nprobe)
+    finally:
+        hntl.set_persistent_cap(0)
+    print("scan items", cap, stats)
+    st = compare_search(gpu, ora, k, C, nprobe)
+    assert st["checked"] >= 0.9 * len(Q), st
+    assert stats["sparse_light"] + stats["sparse_heavy"] > 0
+    assert hntl.device_status(gi) == 0
+
+
+@pytest.mark.parametrize("cap", [2, 0])
+def test_fp32_form_with_capped_grids(hntl, clustered256, cap):
+    """TF32 routing tiles and the grid-stride FP32 projection over many items per CTA."""
+    X, Q, idx, pf, _ = clustered256
+    k, C, nprobe = 10, 100, 16
+    ora = O.search(idx, X, Q, k, C, nprobe)
+    hntl.set_persistent_cap(cap)
+    try:
+        gi = hntl.Index.load(pf, 0)
+        gpu, _ = _search(hntl, gi, Q, k, C, nprobe)
+    finally:
+        hntl.set_persistent_cap(0)
+    st = compare_search(gpu, ora, k, C, nprobe)
+    assert st["checked"] >= 0.9 * len(Q), st
+    assert hntl.device_status(gi) == 0
+
+
+@pytest.mark.parametrize("cap", [2, 0])
+def test_dense_tensor_core_scan_items(hntl, tmp_path, cap):
+    """Isotropic rows: a query's pilot bound lies above almost every row's
+    residual floor, so most of each grain's 128 pairs stay live and the scan
+    contracts them on the tensor cores (dense items); the counters show they
+    ran, and the pool and top k match the oracle."""
+    n, d, G, r, nq = 12000, 64, 12, 16, 384
+    X = synth.isotropic(n, d, seed=501).numpy()
+    Q = synth.isotropic(nq, d, seed=502).numpy()
+    assign = np.random.default_rng(503).integers(0, G, n)
+    idx = partition_index(X, assign, G, r)
+    p = write(tmp_path, "iso", idx, X, precision="bf16-fp8")
+    k, C, nprobe = 10, 200, 4
+    ora = O.search(idx, X, Q, k, C, nprobe, precision="bf16-fp8")
+    hntl.set_persistent_cap(cap)
+    try:
+        gi = hntl.Index.load(p, 0, hntl.PREC_BF16_FP8)
+        gpu, stats = _search(hntl, gi, Q, k, C, nprobe)
+    finally:
+        hntl.set_persistent_cap(0)
+    print("scan items", cap, stats)
+    assert stats["dense"] > 0, stats
+    assert stats["dense_claimed"] >= stats["dense"]
+    st = compare_search(gpu, ora, k, C, nprobe)
+    assert st["checked"] >= 0.9 * nq, st
+    assert hntl.device_status(gi) == 0
+
+
+@pytest.mark.parametrize("precision", ["bf16-fp8", "fp32"])
+def test_full_shape_batch_sampled_against_oracle(hntl, precision):
+    """d = 768, G = 2048 grains, 200k rows, one batch of 4096 queries with
+    nprobe = 32, C = 200, k = 10 (512 routing tiles, ~4000 projection slots,
+    thousands of scan items over ~1.1 CTA-waves of each persistent grid),
+    uncapped. The index is built on the GPU and exported; the oracle searches
+    the exported arrays (decoded FP8 coordinates, BF16 rows in the precision
+    form) for 256 of the queries, and those rows of the batch must match."""
+    n, d, n_clusters, G, r, nq = 200_000, 768, 2048, 2048, 32, 4096
+    k, C, nprobe = 10, 200, 32
+    m = synth.make_cluster_model(n, d, n_clusters, seed=611)
+    X, _ = synth.sample_points(m, 612)
+    Q, _ = synth.sample_queries(m, nq, 613)
+    Xd = X.cuda()
+    prec = hntl.PREC_BF16_FP8 if precision == "bf16-fp8" else hntl.PREC_FP32
+    gi = hntl.Index.build(Xd, G, r, precision=prec, u=synth.uniforms(G, 614).numpy(), seed=614)
+    gpu, stats = _search(hntl, gi, Q.numpy(), k, C, nprobe)
+    print("scan items", precision, stats)
+    host = gi.export()
+    Xn = X.numpy()
+    if precision == "bf16-fp8":
+        Xn = O.bf16_to_f32(O.bf16_round(Xn)).reshape(Xn.shape)
+    sample = np.random.default_rng(615).choice(nq, 256, replace=False)
+    ora = O.search(host, Xn, Q.numpy()[sample], k, C, nprobe,
+                   precision="bf16-fp8-decoded" if precision == "bf16-fp8" else "fp32")
+    sub = {key: v[sample] for key, v in gpu.items()}
+    st = compare_search(sub, ora, k, C, nprobe)
+    assert st["checked"] >= 0.9 * len(sample), st
+    assert hntl.device_status(gi) == 0

@@ -9,6 +9,7 @@ from oracle import router_oracle as R
 from paper_2606_08813_b300 import synth
 
 from cases import write
+from parity import compare_search
 
 pytestmark = pytest.mark.gpu
 
@@ -123,10 +124,97 @@ def test_router_route_fallback_and_search_with_probes(hntl, tmp_path):
     ids, dist = hntl.search_probes(gi, Qd, probes, 10, 40)
     ids2, dist2 = gi.search(Qd, 10, 40, 3)
     assert torch.equal(ids, ids2) and torch.equal(dist, dist2)
-    # given probes reach the oracle run with the same probe sets
-    probes0, _ = rt.route(gi, Qd, 3, tau=0.0)
-    ids3, _ = hntl.search_probes(gi, Qd, probes0, 10, 40)
+    # the router's own probes (tau = 0: no fallback) searched on both sides:
+    # the oracle takes the same probe lists in place of its routing
+    probes0, nfb0 = rt.route(gi, Qd, 3, tau=0.0)
+    assert int(nfb0.item()) == 0
+    ids3, dist3 = hntl.search_probes(gi, Qd, probes0, 10, 40)
+    p0 = probes0.cpu().numpy()
+    ora = O.search(idx, X, Q, 10, 40, 3, probes=p0)
+    gpu = dict(ids=ids3.cpu().numpy(), dist=dist3.cpu().numpy())
+    st = compare_search(gpu, ora, 10, 40, 3)
+    assert st["route_excluded"] == 0 and st["checked"] >= 0.9 * len(Q), st
     assert hntl.device_status(gi) == 0
+
+
+def test_learned_probes_and_fallback_match_oracle(hntl, tmp_path):
+    """Top-nprobe of the GPU's logits and the tau fallback against the router
+    oracle (FP64 with the same BF16 roundings): probe sets must agree unless
+    the nprobe-th and next logits are within the logits' FP32 error, and the
+    fallback decision unless the probes' softmax mass is within that error of
+    tau; fallen-back queries carry the oracle's centroid probes."""
+    d, G, nprobe = 64, 48, 4
+    m = synth.make_cluster_model(6000, d, 12, seed=91)
+    X, _ = synth.sample_points(m, 92)
+    Q, _ = synth.sample_queries(m, 300, 93)
+    X, Q = X.numpy(), Q.numpy()
+    idx = O.build_index(X, G, 8, synth.uniforms(G, 94).numpy())
+    gi = hntl.Index.load(write(tmp_path, "lp", idx, X), 0)
+    params = R.init_params(d, 128, 128, G, seed=95)
+    rng = np.random.default_rng(96)
+    params[4] = (params[4] * 6.0).astype(np.float32)  # spread the logits so the masses vary by query
+    params[5] = rng.standard_normal(G).astype(np.float32)
+    rt = hntl.Router(params, max_batch=128)
+    Qd = torch.from_numpy(Q).cuda()
+    cent = O.search(idx, X, Q, 1, 1, nprobe)
+    for tau in (0.0, 0.35, 2.0):
+        probes, nfb = rt.route(gi, Qd, nprobe, tau=tau)
+        got = probes.cpu().numpy()
+        want, fell, mass, L = R.route(params, Q, nprobe, tau, cent["probe"])
+        Ls = -np.sort(-L, axis=1)
+        tol = 1e-4 * np.maximum(1.0, np.abs(L).max(1))  # FP32 logits: ~1e-5 of their scale
+        n_cmp = n_fb = 0
+        for i in range(len(Q)):
+            if abs(mass[i] - tau) <= 1e-4 * max(1.0, tau):
+                continue  # fallback decision within rounding
+            rd = cent["probe_d"][i]
+            if fell[i]:
+                n_fb += 1
+                if (rd[nprobe] - rd[nprobe - 1]) <= 1e-4 * rd[nprobe - 1]:
+                    continue  # centroid routing boundary is a near tie
+                assert set(got[i].tolist()) == set(want[i].tolist()), (tau, i, "fallback")
+            else:
+                if Ls[i, nprobe - 1] - Ls[i, nprobe] <= tol[i]:
+                    continue
+                assert set(got[i].tolist()) == set(want[i].tolist()), (tau, i)
+            n_cmp += 1
+        assert n_cmp >= 0.9 * len(Q), (tau, n_cmp)
+        assert abs(int(nfb.item()) - int(fell.sum())) <= len(Q) - n_cmp, (tau, int(nfb.item()), int(fell.sum()))
+        if tau == 0.0:
+            assert not fell.any()
+        if tau == 2.0:
+            assert fell.all()
+        if tau == 0.35:
+            assert 0 < n_fb < len(Q), n_fb  # a mix of kept and fallen-back queries
+
+
+def test_gradients_at_full_router_widths(hntl):
+    """The config-sized router (768 -> 1024 -> 1024 -> 4096, batch 1024):
+    the 128-wide GEMM tiles, K loops of up to 64 blocks that wrap the TMA
+    ring many times, against the FP64 oracle with the same BF16 roundings."""
+    d, h1, h2, G, B = 768, 1024, 1024, 4096, 1024
+    params = R.init_params(d, h1, h2, G, seed=13)
+    rng = np.random.default_rng(14)
+    params[1] = (0.1 * rng.standard_normal(h1)).astype(np.float32)
+    params[5] = (0.1 * rng.standard_normal(G)).astype(np.float32)
+    X = rng.standard_normal((B, d)).astype(np.float32)
+    T = np.zeros((B, G), dtype=np.float32)
+    for i in range(B):  # ten neighbours spread over up to ten grains, like the method's labels
+        for g in rng.integers(0, G, 10):
+            T[i, g] += 0.1
+    rt = hntl.Router(params, max_batch=B)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    loss = torch.zeros(1, device="cuda")
+    logits = rt.logits(Xd).cpu().numpy()
+    rt.step(Xd, Td, update=False, loss=loss)
+    torch.cuda.synchronize()
+    assert rt.status() == 0
+    f = R.forward(params, X, round_bf16=True)
+    assert _rel(logits, f["L"]) < 1e-5
+    grads, ref_loss = R.backward(params, X, T.astype(np.float64), round_bf16=True)
+    assert abs(float(loss.item()) - ref_loss) <= 1e-5 * abs(ref_loss)
+    for name, g, ref in zip(("dW1", "db1", "dW2", "db2", "dW3", "db3"), rt.grads(), grads):
+        assert _rel(g, ref) < 1e-3, (name, _rel(g, ref))
 
 
 def _labels(X, Q, assign, G, k=10):

@@ -11,7 +11,7 @@ import torch
 from oracle import hntl_oracle as O
 from paper_2606_08813_b300 import synth
 
-from cases import partition_index
+from cases import clustered_case, partition_index
 from conftest import GOLDEN
 
 
@@ -590,3 +590,20 @@ def test_precision_form_recall_close_to_plain():
     prec = O.search(idx, X, Q, 10, 50, 2, precision="bf16-fp8")
     assert rec(prec) >= rec(plain) - 0.02
     assert rec(prec) >= 0.95
+
+
+def test_given_probes_equal_routing_when_they_are_the_routed_ones():
+    """Step 1 replaced by the probes routing itself picks (in any order)
+    leaves the pool and the top k unchanged: the pool is a global (D, id)
+    order over the probed rows, whatever order the grains are visited in."""
+    X, Q, idx = clustered_case(1500, 16, 6, 6, 4, 25, seed=31)
+    ref = O.search(idx, X, Q, 5, 30, 3)
+    rev = np.ascontiguousarray(ref["probe"][:, ::-1])
+    got = O.search(idx, X, Q, 5, 30, 3, probes=rev)
+    assert np.array_equal(got["cand_id"], ref["cand_id"]) and np.array_equal(got["out_id"], ref["out_id"])
+    np.testing.assert_array_equal(got["out_d"][:, :5], ref["out_d"][:, :5])
+    assert np.isinf(got["probe_d"][:, 3]).all()
+    # a probe set that leaves out the nearest grain changes the pool
+    far = np.ascontiguousarray(np.stack([ref["probe"][:, 1], ref["probe"][:, 2]], 1))
+    got2 = O.search(idx, X, Q, 5, 30, 2, probes=far)
+    assert not np.array_equal(got2["cand_id"], ref["cand_id"][:, :30])

@@ -102,3 +102,24 @@ def test_adamw_constant_gradient_closed_form_over_steps():
         np.testing.assert_allclose(m[0], (1.0 - 0.9 ** t) * g, rtol=1e-12)
         np.testing.assert_allclose(v[0], (1.0 - 0.999 ** t) * g * g, rtol=1e-12)
         np.testing.assert_allclose(p[0], want, rtol=1e-10, atol=1e-12)
+
+
+def test_route_takes_largest_logits_and_falls_back_below_tau():
+    """With W3 = 0 the logits are b3 for every input, so the probes, their
+    softmax mass and the fallback decision follow by hand."""
+    params = R.init_params(4, 8, 8, 6, seed=3)
+    params[4] = np.zeros_like(params[4])
+    params[5] = np.array([0.0, 2.0, 1.0, 2.0, -1.0, 0.5], dtype=np.float32)  # grains 1 and 3 tie
+    Q = np.random.default_rng(1).standard_normal((3, 4))
+    centroid = np.array([[5, 4], [0, 2], [4, 0]], dtype=np.int32)
+    e = np.exp(params[5].astype(np.float64) - 2.0)
+    mass = (e[1] + e[3]) / e.sum()  # top two: grains 1, 3 (the tie keeps both; lower id first)
+    probe, fell, m, L = R.route(params, Q, 2, tau=0.0, centroid_probe=centroid)
+    assert np.allclose(L, params[5][None, :])
+    assert probe.tolist() == [[1, 3]] * 3 and not fell.any()
+    assert np.allclose(m, mass)
+    probe, fell, _, _ = R.route(params, Q, 2, tau=mass + 1e-9, centroid_probe=centroid)
+    assert fell.all() and probe.tolist() == centroid.tolist()
+    # the three largest: 1 and 3 (tied, lower id first), then 2
+    probe, _, _, _ = R.route(params, Q, 3, tau=0.0, centroid_probe=np.zeros((3, 3), np.int32))
+    assert probe[0].tolist() == [1, 3, 2]
