@@ -52,13 +52,25 @@ extern "C" {
  * half of each 16-bit range),
  * int16 coordinates rint(fl32(z / delta_g)) and uint16 residual norms
  * rint(fl32(rho / dres_g)), all in IEEE single precision; queries are
- * quantised with the same steps (saturating), and a grain is left out of a
- * query's scan when more than a quarter of the query's coordinates saturate
- * (the Quantization Envelope Filter, sec. 2.3) or its residual norm does.
- * FP32 raw rows for the rerank. Mode A is not available for this form. */
+ * quantised with the same steps, coordinates saturating at +-32767 and the
+ * residual code clipped at 65535, and a grain is left out of a query's scan
+ * when more than a quarter of the query's coordinates saturate (the
+ * Quantization Envelope Filter, sec. 2.3). The scan evaluates Eq. 6 on the
+ * codes: the exact integer S = sum_j (q_j - c_j)^2 (on the integer dot-product
+ * units), then D = fl32(fl32(delta_g^2) * fl32(S)) + fl32(rho_q + rho_i) with
+ * the residuals on their grid. FP32 raw rows for the rerank. Mode A is not
+ * available for this form. */
 #define HNTL_PREC_FP32 0
 #define HNTL_PREC_BF16_FP8 1
 #define HNTL_PREC_INT16 2
+/* OR-ed into the 16-bit form's precision (hntl_index_load, or the precision
+ * of hntl_build_params): also leave a grain out of a query's scan when the
+ * query's residual code would exceed 65535, instead of clipping it. The
+ * paper's filter counts saturated coordinates only; this option is the
+ * library's own rule for queries far outside a grain's subspace, whose clipped
+ * residual would make that grain's rows look close. HNTL_EINVAL with the
+ * other forms. */
+#define HNTL_INT16_RESID_PRUNE 0x200u
 
 /* The 16-bit form's quantisation of stored rows (Eq. 5, the steps above) as
  * the loader and the builder apply it, on host arrays: Z [N][r] FP32
@@ -277,6 +289,24 @@ int hntl_search_survivors(const hntl_index* idx, const void* d_ws, size_t ws_byt
  * every probed block in one kernel. */
 int hntl_search_scan_stats(const hntl_index* idx, const void* d_ws, size_t ws_bytes, uint32_t nq, uint32_t C,
                            uint32_t nprobe, uint32_t* d_stats, void* stream);
+
+/* Diagnostic of the 16-bit form: the query codes of the last hntl_search that
+ * used this workspace with the same nq, C and nprobe (Eq. 5 applied to each
+ * (query, probe) pair's z_q and rho_q), in query order: d_codes (device,
+ * nq x nprobe x r int16) and d_rcodes (device, nq x nprobe int32 residual
+ * codes, -1 for a pair the envelope filter left out), on `stream`. With them
+ * an oracle can evaluate the integer scan on exactly the GPU's integer inputs.
+ * HNTL_EINVAL for the other forms. */
+int hntl_search_pair_codes(const hntl_index* idx, const void* d_ws, size_t ws_bytes, uint32_t nq, uint32_t C,
+                           uint32_t nprobe, int16_t* d_codes, int32_t* d_rcodes, void* stream);
+
+/* Diagnostic: the projection step's output (Eq. 1-4) of the last hntl_search
+ * that used this workspace with the same nq, C and nprobe, in query order:
+ * d_zq (device, nq x nprobe x r FP32 z_q) and d_rhoq (device, nq x nprobe FP32
+ * rho_q), on `stream`. In the 16-bit form these are the values on the grain's
+ * grids, and rho_q is +inf for a pair the envelope filter left out. */
+int hntl_search_pair_proj(const hntl_index* idx, const void* d_ws, size_t ws_bytes, uint32_t nq, uint32_t C,
+                          uint32_t nprobe, float* d_zq, float* d_rhoq, void* stream);
 
 /* Test hook (the paper has no counterpart): caps the grid of every persistent
  * kernel of the search (tensor-core routing, both projections, both scans of

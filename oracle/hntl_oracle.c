@@ -309,13 +309,15 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
                const int64_t* ranges, int32_t* probe, double* probe_d, uint32_t* cand_id, double* cand_d,
                int64_t* out_id, double* out_d, int64_t mode, const int64_t* pos_of_id,
                const int32_t* grain_of_pos, const double* qdelta, const double* qdres,
-               const int32_t* probe_in) {
+               const int32_t* probe_in, const int16_t* Zc, int64_t i16_flags, const int16_t* qc_in,
+               const int32_t* qr_in) {
 #pragma omp parallel
   {
     pair_t* route = (pair_t*)malloc(sizeof(pair_t) * (size_t)G);
     double* v = (double*)malloc(sizeof(double) * (size_t)d);
     double* e = (double*)malloc(sizeof(double) * (size_t)d);
     double* zq = (double*)malloc(sizeof(double) * (size_t)(r > 0 ? r : 1));
+    int64_t* qc = (int64_t*)malloc(sizeof(int64_t) * (size_t)(r > 0 ? r : 1));
     heap_t pool;
     pool.cap = C + 1;
     pool.v = (pair_t*)malloc(sizeof(pair_t) * (size_t)(C + 1));
@@ -361,26 +363,45 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
           for (int64_t t = 0; t < d; ++t) e[t] -= zq[j] * (double)Ug[j * d + t];
         double rho_q = 0.0;
         for (int64_t t = 0; t < d; ++t) rho_q += e[t] * e[t];
+        float dl = 0.f, rq16 = 0.f;
         if (qdelta) {
           /* 16-bit form (Eq. 5): the query's coordinates and residual norm are
-           * quantised with the grain's steps; a value beyond its 16-bit range
-           * saturates. The grain is left out when more than a quarter of the
-           * coordinates saturate (Quantization Envelope Filter, sec. 2.3) or
-           * when the residual norm does (the same test on the out-of-subspace
-           * energy: more than twice any of the grain's rows) */
-          int64_t sat = 0;
-          for (int64_t j = 0; j < r; ++j) {
-            double t = rint(zq[j] / qdelta[g]);
-            if (fabs(t) > 32767.0) {
-              ++sat;
-              t = t > 0 ? 32767.0 : -32767.0;
+           * put on the grain's grids in IEEE single precision, code =
+           * rint(fl32(fl32(value) / step)) (round half to even). A coordinate
+           * code beyond the signed 16-bit range saturates at +-32767 and is
+           * counted; the residual code is clipped at the unsigned 16-bit
+           * maximum 65535. The grain is left out when more than a quarter of
+           * the coordinates saturate (Quantization Envelope Filter, sec. 2.3);
+           * with i16_flags bit 0 (the build's own option, not the paper's) it
+           * is also left out when the residual code would exceed 65535.
+           * Given codes (qc_in, qr_in: the same quantisation taken elsewhere;
+           * qr_in < 0 marks a pair left out) replace this step. */
+          dl = (float)qdelta[g];
+          const float dr = (float)qdres[g];
+          float tr;
+          if (qc_in) {
+            const int64_t base = (qi * nprobe + p) * r;
+            if (qr_in[qi * nprobe + p] < 0) continue;
+            for (int64_t j = 0; j < r; ++j) qc[j] = qc_in[base + j];
+            tr = (float)qr_in[qi * nprobe + p];
+          } else {
+            int64_t sat = 0;
+            for (int64_t j = 0; j < r; ++j) {
+              float t = rintf((float)zq[j] / dl);
+              if (fabsf(t) > 32767.f) {
+                ++sat;
+                t = t > 0 ? 32767.f : -32767.f;
+              }
+              qc[j] = (int64_t)t;
             }
-            zq[j] = t * qdelta[g];
+            if (4 * sat > r) continue;
+            tr = rintf((float)rho_q / dr);
+            if (tr > 65535.f) {
+              if (i16_flags & 1) continue;
+              tr = 65535.f;
+            }
           }
-          if (4 * sat > r) continue;
-          const double tr = rint(rho_q / qdres[g]);
-          if (tr > 65535.0) continue;
-          rho_q = tr * qdres[g];
+          rq16 = tr * dr; /* the query's residual on the grain's grid, fl32 */
         }
         for (int64_t i = grain_off[g]; i < grain_off[g + 1]; ++i) {
           uint32_t id = ids[i];
@@ -388,12 +409,30 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
             int64_t a = attr[id];
             if (a < ranges[2 * qi] || a > ranges[2 * qi + 1]) continue;
           }
-          double s = 0.0;
-          for (int64_t j = 0; j < r; ++j) {
-            double t = zq[j] - (double)Z[i * r + j];
-            s += t * t;
+          double dist;
+          if (qdelta) {
+            /* Eq. 6 on the 16-bit representations: the exact integer
+             * S = sum_j (zq_j - z_ij)^2 of the codes, scaled back in IEEE
+             * single precision as fl32(fl32(delta^2) * fl32(S)) plus
+             * fl32(rho_q + rho_i) of the grid residuals */
+            int64_t S = 0;
+            for (int64_t j = 0; j < r; ++j) {
+              const int64_t t = qc[j] - (int64_t)Zc[i * r + j];
+              S += t * t;
+            }
+            const float dl2 = dl * dl;
+            const float a = dl2 * (float)S;
+            const float b = rq16 + rho[i];
+            dist = (double)(float)(a + b);
+          } else {
+            double s = 0.0;
+            for (int64_t j = 0; j < r; ++j) {
+              double t = zq[j] - (double)Z[i * r + j];
+              s += t * t;
+            }
+            dist = s + rho_q + (double)rho[i];
           }
-          pair_t cand = {s + rho_q + (double)rho[i], (int64_t)id};
+          pair_t cand = {dist, (int64_t)id};
           heap_push(&pool, cand);
         }
       }
@@ -439,6 +478,7 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
     free(v);
     free(e);
     free(zq);
+    free(qc);
     free(pool.v);
     free(rr);
     free(xh);

@@ -54,7 +54,7 @@ def build_c(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-Wall",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -74,7 +74,7 @@ def _c():
             lib.or_lloyd.argtypes = [P, I, I, I, P, I, P]
             lib.or_lloyd.restype = I
             lib.or_search.argtypes = [P, P, I, I, I, P, P, P, P, P, P, P, P, I, I, I, I, P,
-                                      P, P, P, P, P, P, I, P, P, P, P, P]
+                                      P, P, P, P, P, P, I, P, P, P, P, P, P, I, P, P]
             lib.or_threads.restype = ctypes.c_int
             lib.or_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -214,7 +214,7 @@ def build_index(X, G: int, r: int, u, train_idx=None, max_iter: int = 25, keep_f
 
 
 def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=None, rho=None, precision="fp32",
-           mode: str = "B", probes=None):
+           mode: str = "B", probes=None, resid_prune: bool = False, query_codes=None):
     """Mode B (default) or Mode A search of every query (see hntl_oracle.c or_search).
 
     probes (optional, [nq, nprobe] grain ids): replaces the centroid routing
@@ -228,10 +228,17 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
 
     precision="fp32": the plain method on the stored FP32 values.
     precision="int16": the paper's 16-bit form (Eq. 5): rows on their grain's
-    16-bit grids (int16_form), the query's coordinates and residual norm
-    quantised with the same steps, and a grain left out of a query's scan when
-    more than a quarter of its coordinates saturate (sec. 2.3) or its residual
-    norm does.
+    16-bit grids (int16_form), the query's coordinates quantised with the same
+    steps (saturating at +-32767) and its residual norm clipped at 65535
+    steps, and a grain left out of a query's scan when more than a quarter of
+    its coordinates saturate (sec. 2.3). Eq. 6 is then evaluated on the codes:
+    the exact integer sum of squared code differences, scaled back by the
+    squared step in IEEE single precision (see hntl_oracle.c). resid_prune
+    (the build's own option, not the paper's): also leave the grain out when
+    the residual code would exceed 65535. query_codes (codes, rcodes) with
+    codes [nq, nprobe, r] int16 and rcodes [nq, nprobe] int32 (-1 = pair left
+    out) replace the query-side quantisation (to compare the scan on the same
+    integer inputs).
     precision="bf16-fp8": the precision form, defined on rounded inputs: the
     query, centres and bases are rounded to BF16 for routing and projection,
     the scan reads the FP8 coordinates decoded and scaled (fp8_coords), and the
@@ -260,11 +267,20 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
     qdelta = qdres = None
     Zs = _f32(idx["Z"] if Z is None else Z)
     rhos = _f32(idx["rho"] if rho is None else rho)
+    Zc = qc_in = qr_in = None
     if precision == "int16":  # rows and queries on the grains' 16-bit grids (Eq. 5)
         q16 = int16_form(idx)
         Zs = q16["Zf32"]
         rhos = q16["rhof32"]
+        Zc = np.ascontiguousarray(q16["codes"], dtype=np.int16)
         qdelta, qdres = q16["delta"].astype(np.float64), q16["dres"].astype(np.float64)
+        if query_codes is not None:
+            qc_in = np.ascontiguousarray(query_codes[0], dtype=np.int16)
+            qr_in = np.ascontiguousarray(query_codes[1], dtype=np.int32)
+            if qc_in.shape != (nq, nprobe, r) or qr_in.shape != (nq, nprobe):
+                raise ValueError("query_codes must be ([nq, nprobe, r] int16, [nq, nprobe] int32)")
+    elif query_codes is not None or resid_prune:
+        raise ValueError("query_codes and resid_prune apply to the 16-bit form")
     off = np.ascontiguousarray(idx["grain_off"], dtype=np.int64)
     ids = np.ascontiguousarray(idx["ids"], dtype=np.uint32)
     attr_a = None if attr is None else np.ascontiguousarray(attr, dtype=np.int64)
@@ -291,7 +307,8 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
             raise ValueError("probes must be [nq, nprobe] grain ids")
     _c().or_search(_p(M), _p(U), G, d, r, _p(off), _p(ids), _p(Zs), _p(rhos), _p(X), _p(attr_a), _p(Q), _p(Qp), nq,
                    k, C, nprobe, _p(rng), _p(probe), _p(probe_d), _p(cand_id), _p(cand_d), _p(out_id), _p(out_d),
-                   1 if mode == "A" else 0, _p(pos_of_id), _p(grain_of_pos), _p(qdelta), _p(qdres), _p(pin))
+                   1 if mode == "A" else 0, _p(pos_of_id), _p(grain_of_pos), _p(qdelta), _p(qdres), _p(pin),
+                   _p(Zc), 1 if resid_prune else 0, _p(qc_in), _p(qr_in))
     return dict(probe=probe, probe_d=probe_d, cand_id=cand_id, cand_d=cand_d, out_id=out_id, out_d=out_d)
 
 

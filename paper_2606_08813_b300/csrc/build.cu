@@ -538,9 +538,12 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   if (N >= (1ull << 32) - 1) return fail(HNTL_EINVAL, "too many rows");
   hntl_build_params P{};
   if (prm) P = *prm;
-  const uint32_t precision = P.precision;
+  const bool rprune = P.precision & HNTL_INT16_RESID_PRUNE;
+  const uint32_t precision = P.precision & ~HNTL_INT16_RESID_PRUNE;
   if (precision != HNTL_PREC_FP32 && precision != HNTL_PREC_BF16_FP8 && precision != HNTL_PREC_INT16)
     return fail(HNTL_EINVAL, "bad precision");
+  if (rprune && precision != HNTL_PREC_INT16)
+    return fail(HNTL_EINVAL, "residual-saturation pruning applies to the 16-bit form only");
   if (precision == HNTL_PREC_BF16_FP8 && d % 8)  // BF16 rows move in 16-byte pieces
     return fail(HNTL_EINVAL, "the precision form needs d to be a multiple of 8");
   const uint32_t max_iter = P.max_iter ? P.max_iter : 10;
@@ -586,6 +589,7 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   I.G = G;
   I.r = r;
   I.precision = precision;
+  I.i16_resid_prune = rprune;
   I.rp = (uint32_t)padded_r((int)r, (int)precision);
   I.has_attr = P.d_attr != nullptr;
   auto own = [&](size_t bytes) -> void* {

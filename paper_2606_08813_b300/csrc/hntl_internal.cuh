@@ -44,6 +44,7 @@ struct Index {
   uint32_t d = 0, G = 0, r = 0, precision = HNTL_PREC_FP32;
   uint32_t rp = 0;               // r padded to the coordinate lane (see zoff)
   bool has_attr = false;
+  bool i16_resid_prune = false;  // 16-bit form: also leave a grain out when the query residual saturates
   uint64_t n_blocks = 0;
   uint64_t max_grain_rows = 0;
   uint64_t device_bytes = 0;

@@ -133,7 +133,10 @@ std::vector<uint64_t> rows_by_first_coord(const float* Z, uint32_t r, const uint
 
 int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t precision, Index& I) {
   const bool no_raw = precision & HNTL_LOAD_NO_RAW;  // Mode A only: the raw rows stay on the host
-  precision &= ~HNTL_LOAD_NO_RAW;
+  const bool rprune = precision & HNTL_INT16_RESID_PRUNE;
+  precision &= ~(HNTL_LOAD_NO_RAW | HNTL_INT16_RESID_PRUNE);
+  if (rprune && precision != HNTL_PREC_INT16)
+    return fail(HNTL_EINVAL, "residual-saturation pruning applies to the 16-bit form only");
   if (size < kHeaderBytes + 8) return fail(HNTL_EFORMAT, "index file truncated (no header)");
   if (std::memcmp(buf, kMagic, 8) != 0) return fail(HNTL_EFORMAT, "bad magic (not an HNTL index file)");
   uint32_t version, flags, d, G, r, reserved;
@@ -221,6 +224,7 @@ int load_from_memory(const uint8_t* buf, size_t size, int device, uint32_t preci
   I.G = G;
   I.r = r;
   I.precision = precision;
+  I.i16_resid_prune = rprune;
   I.rp = (uint32_t)padded_r((int)r, (int)precision);
   I.has_attr = attr_raw != nullptr;
   I.h_blk_off.assign(G + 1, 0);

@@ -20,8 +20,9 @@
 //   k_final_select one CTA per query: the exact C smallest (D, id) of the
 //                  survivors, or, if the survivors overflowed their buffer,
 //                  of all probed rows recomputed on the fly (same result).
-// D is computed by one function everywhere (eval_D), so a row's D is
-// bitwise the same in the pilot, the scan and the fallback.
+// D is computed by one function everywhere (eval_D; eval_D_i16 in the
+// 16-bit form), so a row's D is bitwise the same in the pilot, the scan and
+// the fallback.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -132,6 +133,125 @@ __device__ __forceinline__ void load_row(const Coords& c, int rp, float s_g, siz
   }
 }
 
+// ------------------------------------------------------------------ 16-bit form: integer Eq. 6
+
+// The 16-bit form evaluates Eq. 6 on the codes themselves (Eq. 5 states the
+// integer representations the scan works on): with the query's codes q_j, a
+// row's codes c_j (both on the grain's step delta_g) and their residuals on
+// the grain's residual grid,
+//   S = sum_j (q_j - c_j)^2 = |q|^2 + |c|^2 - 2 q.c     (exact in integers)
+//   D = fl32(fl32(delta_g^2) * fl32(S)) + fl32(rho_q + rho_i)
+// in IEEE single precision with separate roundings. q.c runs on the integer
+// dot-product units: a row word holds two int16 codes, and dp2a multiplies
+// them by two 8-bit pieces of the query codes, so each query code is split as
+// q = 256 hi + lo (hi signed, lo unsigned) and q.c = 256 (c.hi) + (c.lo), each
+// partial sum within int32 (|c| <= 16383 by the row steps, |hi| <= 128,
+// lo <= 255, r <= 64). |c|^2 uses the same split of the row's own codes.
+__device__ __forceinline__ int dp2a_lo_ss(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp2a.lo.s32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ int dp2a_hi_ss(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp2a.hi.s32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ int dp2a_lo_su(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp2a.lo.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ int dp2a_hi_su(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp2a.hi.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// A row of the 16-bit form: its codes, two per word (word m = codes 2m, 2m+1,
+// the lower code in the low half), zero past rp.
+template <int RT>
+__device__ __forceinline__ void i16_load_row(const int16_t* __restrict__ Z16b, int rp, size_t b, int t,
+                                             uint32_t (&w)[RT / 2]) {
+  static_assert(RT % 8 == 0, "16-bit rows are read in lanes of 8 codes");
+#pragma unroll
+  for (int l = 0; l < RT / 8; ++l) {
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (l * 8 < rp) v = __ldg(reinterpret_cast<const uint4*>(Z16b + ((b * (rp / 8) + l) * kBlockRows + t) * 8));
+    w[4 * l] = v.x;
+    w[4 * l + 1] = v.y;
+    w[4 * l + 2] = v.z;
+    w[4 * l + 3] = v.w;
+  }
+}
+
+// |c|^2 of a row's codes: per word, its high bytes (signed) and low bytes
+// (unsigned) gathered by byte permutes, two dp2a.
+template <int RT>
+__device__ __forceinline__ long long i16_row_norm(const uint32_t (&w)[RT / 2]) {
+  int ah = 0, al = 0;
+#pragma unroll
+  for (int m = 0; m < RT / 2; ++m) {
+    ah = dp2a_lo_ss(w[m], __byte_perm(w[m], 0u, 0x0031u), ah);
+    al = dp2a_lo_su(w[m], __byte_perm(w[m], 0u, 0x0020u), al);
+  }
+  return 256ll * ah + al;
+}
+
+// The query side of one (query, grain) pair: high and low bytes of its codes,
+// four codes per word (word m = codes 4m .. 4m+3), |q|^2 and its residual.
+template <int RT>
+struct I16Query {
+  uint32_t hi[RT / 4];
+  uint32_t lo[RT / 4];
+  long long qn;
+  float rho;
+};
+
+// Packs codes[0 .. r) (zero past r) into hi/lo byte words.
+template <int RT>
+__device__ __forceinline__ void i16_pack_query(const int16_t* __restrict__ codes, int r, uint32_t* hi, uint32_t* lo) {
+#pragma unroll
+  for (int m = 0; m < RT / 4; ++m) {
+    uint32_t h = 0, l = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = 4 * m + e;
+      const int c = j < r ? (int)codes[j] : 0;
+      h |= (uint32_t)((c >> 8) & 0xFF) << (8 * e);
+      l |= (uint32_t)(c & 0xFF) << (8 * e);
+    }
+    hi[m] = h;
+    lo[m] = l;
+  }
+}
+
+// The 16-bit form's per-pair query codes (workspace, written by the
+// quantisation step): codes [pairs][rp] int16 (zero past r) and |q|^2 [pairs].
+// Null in the other forms.
+struct I16Pairs {
+  const int16_t* codes;
+  const long long* qn;
+};
+
+// D of a (pair, row) of the 16-bit form, bitwise the same wherever it is
+// evaluated (pilot, scan, pool fallback).
+template <int RT>
+__device__ __forceinline__ float eval_D_i16(const uint32_t* hi, const uint32_t* lo, long long qn, float rho_q,
+                                            const uint32_t (&w)[RT / 2], long long ni, float rho_i, float dl2) {
+  int ah = 0, al = 0;
+#pragma unroll
+  for (int m = 0; m < RT / 4; ++m) {
+    const uint32_t h = hi[m], l = lo[m];
+    ah = dp2a_lo_ss(w[2 * m], h, ah);
+    ah = dp2a_hi_ss(w[2 * m + 1], h, ah);
+    al = dp2a_lo_su(w[2 * m], l, al);
+    al = dp2a_hi_su(w[2 * m + 1], l, al);
+  }
+  const long long S = qn + ni - 2 * (256ll * ah + al);
+  return __fadd_rn(__fmul_rn(dl2, __ll2float_rn(S)), __fadd_rn(rho_q, rho_i));
+}
+
 // ------------------------------------------------------------------ block interval bound
 
 // Rows are laid out in each grain by their first coordinate, so a block's
@@ -186,10 +306,13 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
                                                const float* __restrict__ rho, const int64_t* __restrict__ attr_b,
                                                int r, int rp, const float* __restrict__ zq,
                                                const float* __restrict__ rhoq, const int64_t* __restrict__ filter,
-                                               float* __restrict__ tau, const uint32_t* __restrict__ qC) {
+                                               float* __restrict__ tau, const uint32_t* __restrict__ qC,
+                                               const I16Pairs q16) {
   __shared__ uint32_t vals[kPilotRows];  // D bit patterns (non-negative floats order like unsigned)
   __shared__ uint32_t hist[256];
   __shared__ __align__(8) float szq[RT];
+  __shared__ uint32_t s16hi[RT / 4 > 0 ? RT / 4 : 1], s16lo[RT / 4 > 0 ? RT / 4 : 1];
+  __shared__ long long s16qn;
   __shared__ uint32_t scratch[96];
   __shared__ uint32_t s_fill, s_bin, s_below, s_total;
   const int q = blockIdx.x;
@@ -220,6 +343,12 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
     const uint32_t n = grain_rows[g];
     const uint32_t nbk = blk_off[g + 1] - blk_off[g];
     for (int j = threadIdx.x; j < RT; j += blockDim.x) szq[j] = j < r ? zq[(size_t)s * r + j] : 0.f;
+    if constexpr (kC == kCoordI16) {
+      if (threadIdx.x == 0) {
+        i16_pack_query<RT>(q16.codes + (size_t)s * rp, r, s16hi, s16lo);
+        s16qn = q16.qn[s];
+      }
+    }
     const float rho_q = rhoq[s];
     const float s_g = kC != kCoordF32 ? cz.scale[g] : 1.f;
     __syncthreads();
@@ -242,9 +371,16 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
           keep = a >= lo && a <= hi;
         }
         if (keep) {
-          float z[RT];
-          load_row<RT, kC>(cz, rp, s_g, b, t, z);
-          k = __float_as_uint(eval_D<RT>(szq, z, rho_q, rho[b * kBlockRows + t]));
+          if constexpr (kC == kCoordI16) {
+            uint32_t w[RT / 2];
+            i16_load_row<RT>(cz.Z16b, rp, b, t, w);
+            k = __float_as_uint(eval_D_i16<RT>(s16hi, s16lo, s16qn, rho_q, w, i16_row_norm<RT>(w),
+                                               rho[b * kBlockRows + t], __fmul_rn(s_g, s_g)));
+          } else {
+            float z[RT];
+            load_row<RT, kC>(cz, rp, s_g, b, t, z);
+            k = __float_as_uint(eval_D<RT>(szq, z, rho_q, rho[b * kBlockRows + t]));
+          }
           keep = k < kInfBits;
         }
       }
@@ -302,9 +438,12 @@ __global__ void __launch_bounds__(kBlockRows) k_scan_filter(
     const uint32_t* __restrict__ gcnt, const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ pair_q,
     const float* __restrict__ zq, const float* __restrict__ rhoq, const float* __restrict__ tau,
     const float* __restrict__ blk_rho_min, const float2* __restrict__ blk_z0, const int64_t* __restrict__ filter,
-    uint32_t cap, uint32_t* __restrict__ cnt, unsigned long long* __restrict__ surv) {
+    uint32_t cap, uint32_t* __restrict__ cnt, unsigned long long* __restrict__ surv, const I16Pairs q16) {
   constexpr int kChunk = 32;
-  __shared__ __align__(8) float sz[kChunk][RT];
+  constexpr bool kI = kC == kCoordI16;
+  __shared__ __align__(8) float sz[kI ? 1 : kChunk][kI ? 2 : RT];
+  __shared__ uint32_t s16hi[kI ? kChunk : 1][kI ? RT / 4 : 1], s16lo[kI ? kChunk : 1][kI ? RT / 4 : 1];
+  __shared__ long long s16qn[kI ? kChunk : 1];
   __shared__ float srho[kChunk], stau[kChunk];
   __shared__ uint32_t sq[kChunk];
   __shared__ long long slo[kChunk], shi[kChunk];
@@ -335,25 +474,41 @@ __global__ void __launch_bounds__(kBlockRows) k_scan_filter(
   const uint32_t nwalk = listed ? nneed : m;
   const uint32_t row = (uint32_t)(b - blk_off[g]) * kBlockRows + t;
   const bool valid = row < grain_rows[g];
-  float z[RT];
-  load_row<RT, kC>(cz, rp, kC != kCoordF32 ? cz.scale[g] : 1.f, b, t, z);
+  float z[kI ? 1 : RT];
+  uint32_t w16[kI ? RT / 2 : 1];
+  long long ni = 0;
+  float dl2 = 0.f;
+  if constexpr (kI) {
+    i16_load_row<RT>(cz.Z16b, rp, b, t, w16);
+    ni = i16_row_norm<RT>(w16);
+    const float dl = cz.scale[g];
+    dl2 = __fmul_rn(dl, dl);
+  } else {
+    load_row<RT, kC>(cz, rp, kC != kCoordF32 ? cz.scale[g] : 1.f, b, t, z);
+  }
   const float rho_i = rho[b * kBlockRows + t];
   const uint32_t id = ids[b * kBlockRows + t];
   const long long a = filter ? (long long)attr_b[b * kBlockRows + t] : 0;
   const unsigned lt_mask = (1u << lane) - 1u;
   for (uint32_t s0 = 0; s0 < nwalk; s0 += kChunk) {
     const int ns = (int)min((uint32_t)kChunk, nwalk - s0);
-    for (int e = t; e < kChunk * RT; e += kBlockRows) {
-      const int s = e / RT, j = e - s * RT;
-      float v = 0.f;
-      if (s < ns && j < r) {
-        const uint32_t pr = p_begin + (listed ? s_need[s0 + s] : s0 + s);
-        v = zq[(size_t)pr * r + j];
+    if constexpr (!kI) {
+      for (int e = t; e < kChunk * RT; e += kBlockRows) {
+        const int s = e / RT, j = e - s * RT;
+        float v = 0.f;
+        if (s < ns && j < r) {
+          const uint32_t pr = p_begin + (listed ? s_need[s0 + s] : s0 + s);
+          v = zq[(size_t)pr * r + j];
+        }
+        sz[s][j] = v;
       }
-      sz[s][j] = v;
     }
     if (t < ns) {
       const uint32_t pr = p_begin + (listed ? s_need[s0 + t] : s0 + t);
+      if constexpr (kI) {
+        i16_pack_query<RT>(q16.codes + (size_t)pr * rp, r, s16hi[t], s16lo[t]);
+        s16qn[t] = q16.qn[pr];
+      }
       const uint32_t q = pair_q[pr];
       sq[t] = q;
       srho[t] = rhoq[pr];
@@ -366,7 +521,9 @@ __global__ void __launch_bounds__(kBlockRows) k_scan_filter(
     __syncthreads();
     for (int s = 0; s < ns; ++s) {
       if (srho[s] + rmin > stau[s]) continue;  // no row of this block can reach the query's pool
-      const float D = eval_D<RT>(&sz[s][0], z, srho[s], rho_i);
+      float D;
+      if constexpr (kI) D = eval_D_i16<RT>(s16hi[s], s16lo[s], s16qn[s], srho[s], w16, ni, rho_i, dl2);
+      else D = eval_D<RT>(&sz[s][0], z, srho[s], rho_i);
       const bool ok = valid && D <= stau[s] && (!filter || (a >= slo[s] && a <= shi[s]));
       const unsigned mask = __ballot_sync(0xffffffffu, ok);
       if (mask) {
@@ -416,6 +573,7 @@ struct ProbedRowsSrc {
   const float* zq;
   const float* rhoq;
   const int64_t* filter;
+  I16Pairs q16;
   template <class F>
   __device__ void for_each(F f) const {
     long long lo = 0, hi = 0;
@@ -429,19 +587,38 @@ struct ProbedRowsSrc {
       const uint32_t n = grain_rows[g];
       const float rho_q = rhoq[s];
       const float s_g = kC != kCoordF32 ? cz.scale[g] : 1.f;
-      __align__(8) float zl[RT];
-#pragma unroll
-      for (int j = 0; j < RT; ++j) zl[j] = j < r ? zq[(size_t)s * r + j] : 0.f;
-      for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const size_t b = blk_off[g] + i / kBlockRows;
-        const int t = i % kBlockRows;
-        if (filter) {
-          const long long a = attr_b[b * kBlockRows + t];
-          if (a < lo || a > hi) continue;
+      if constexpr (kC == kCoordI16) {
+        uint32_t qh[RT / 4], ql[RT / 4];
+        i16_pack_query<RT>(q16.codes + (size_t)s * rp, r, qh, ql);
+        const long long qn = q16.qn[s];
+        const float dl2 = __fmul_rn(s_g, s_g);
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+          const size_t b = blk_off[g] + i / kBlockRows;
+          const int t = i % kBlockRows;
+          if (filter) {
+            const long long a = attr_b[b * kBlockRows + t];
+            if (a < lo || a > hi) continue;
+          }
+          uint32_t w[RT / 2];
+          i16_load_row<RT>(cz.Z16b, rp, b, t, w);
+          f(__float_as_uint(eval_D_i16<RT>(qh, ql, qn, rho_q, w, i16_row_norm<RT>(w), rho[b * kBlockRows + t], dl2)),
+            ids[b * kBlockRows + t]);
         }
-        float z[RT];
-        load_row<RT, kC>(cz, rp, s_g, b, t, z);
-        f(__float_as_uint(eval_D<RT>(zl, z, rho_q, rho[b * kBlockRows + t])), ids[b * kBlockRows + t]);
+      } else {
+        __align__(8) float zl[RT];
+#pragma unroll
+        for (int j = 0; j < RT; ++j) zl[j] = j < r ? zq[(size_t)s * r + j] : 0.f;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+          const size_t b = blk_off[g] + i / kBlockRows;
+          const int t = i % kBlockRows;
+          if (filter) {
+            const long long a = attr_b[b * kBlockRows + t];
+            if (a < lo || a > hi) continue;
+          }
+          float z[RT];
+          load_row<RT, kC>(cz, rp, s_g, b, t, z);
+          f(__float_as_uint(eval_D<RT>(zl, z, rho_q, rho[b * kBlockRows + t])), ids[b * kBlockRows + t]);
+        }
       }
     }
   }
@@ -622,7 +799,8 @@ __global__ void __launch_bounds__(kFinalThreads, kFallback ? 1 : 8) k_final_sele
     const uint32_t* __restrict__ grain_rows, const Coords cz, const float* __restrict__ rho,
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r, int rp,
     const float* __restrict__ zq, const float* __restrict__ rhoq, const int64_t* __restrict__ filter,
-    uint32_t* __restrict__ cand_id, float* __restrict__ cand_d, const uint32_t* __restrict__ qC) {
+    uint32_t* __restrict__ cand_id, float* __restrict__ cand_d, const uint32_t* __restrict__ qC,
+    const I16Pairs q16) {
   __shared__ SelSmem S;
   const int q = blockIdx.x;
   const uint32_t n = cnt[q];
@@ -642,7 +820,7 @@ __global__ void __launch_bounds__(kFinalThreads, kFallback ? 1 : 8) k_final_sele
     select_topc(src, C, S, oid, od);
   } else {
     ProbedRowsSrc<RT, kC> src{q,  nprobe, r,   rp,     probe, pair_of, blk_off, grain_rows,
-                                cz, rho,    ids, attr_b, zq,    rhoq,    filter};
+                                cz, rho,    ids, attr_b, zq,    rhoq,    filter,  q16};
     select_topc(src, C, S, oid, od);
   }
 }

@@ -98,15 +98,19 @@ __global__ void k_probe_dist(const float* __restrict__ Q, const float* __restric
 // The 16-bit form's query side (Eq. 5, sec. 2.3), one warp per (query, grain)
 // pair over the whole batch (a grain probed by many queries does not
 // serialise), lanes over coordinates: each coordinate of z_q is put on the
-// grain's grid (rint(fl32(z / delta_g)), saturating at +-32767) and replaced
-// by its grid value, and rho_q likewise on the residual grid. A pair is left
-// out (rho_q = +inf, so every downstream stage drops its rows) when more than
-// a quarter of its coordinates saturate or its residual norm does (beyond
-// 65535 steps: twice any row of the grain).
+// grain's grid, code rint(fl32(z / delta_g)) saturating at +-32767, and the
+// codes, their squared sum and the grid values (for the scan's interval
+// bound) are stored; rho_q goes on the residual grid, its code clipped at the
+// unsigned 16-bit maximum 65535. A pair is left out (rho_q = +inf, residual
+// code -1, so every downstream stage drops its rows) when more than a quarter
+// of its coordinates saturate (the Quantization Envelope Filter), and, with
+// the index's residual-saturation option (the library's own rule), when its
+// residual code would exceed 65535.
 __global__ void k_quant_pairs(uint32_t P, int nprobe, const int32_t* __restrict__ probe,
-                              const uint32_t* __restrict__ pair_q, const uint32_t* __restrict__ pair_p, int r,
-                              const float* __restrict__ delta, const float* __restrict__ dres, float* __restrict__ zq,
-                              float* __restrict__ rhoq) {
+                              const uint32_t* __restrict__ pair_q, const uint32_t* __restrict__ pair_p, int r, int rp,
+                              const float* __restrict__ delta, const float* __restrict__ dres, bool resid_prune,
+                              float* __restrict__ zq, float* __restrict__ rhoq, int16_t* __restrict__ zq16,
+                              long long* __restrict__ qn16, int32_t* __restrict__ rc16) {
   const uint32_t pr = (uint32_t)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (pr >= P) return;
@@ -114,18 +118,44 @@ __global__ void k_quant_pairs(uint32_t P, int nprobe, const int32_t* __restrict_
   const float dl = delta[g], dr = dres[g];
   float* z = zq + (size_t)pr * r;
   int sat = 0;
-  for (int j0 = 0; j0 < r; j0 += 32) {  // r <= 64
+  long long qn = 0;
+  for (int j0 = 0; j0 < rp; j0 += 32) {  // rp <= 64
     const int j = j0 + lane;
     float t = 0.f;
     if (j < r) t = rintf(z[j] / dl);
     const bool s = j < r && fabsf(t) > 32767.f;
     sat += __popc(__ballot_sync(0xffffffffu, s));
-    if (j < r) z[j] = fmaxf(-32767.f, fminf(32767.f, t)) * dl;
+    const float c = fmaxf(-32767.f, fminf(32767.f, t));
+    if (j < r) z[j] = c * dl;
+    if (j < rp) zq16[(size_t)pr * rp + j] = (int16_t)c;
+    const int ci = (int)c;
+    qn += (long long)(ci * ci);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) qn += __shfl_xor_sync(0xffffffffu, qn, o);
   if (lane == 0) {
-    const float tr = rintf(rhoq[pr] / dr);
-    rhoq[pr] = (4 * sat > r || tr > 65535.f) ? INFINITY : tr * dr;
+    float tr = rintf(rhoq[pr] / dr);
+    bool out = 4 * sat > r;
+    if (tr > 65535.f) {
+      out = out || resid_prune;
+      tr = 65535.f;
+    }
+    rhoq[pr] = out ? INFINITY : tr * dr;
+    rc16[pr] = out ? -1 : (int32_t)tr;
+    qn16[pr] = qn;
   }
+}
+
+// Diagnostic gather of the 16-bit query codes into query order: codes
+// [nq][nprobe][r] and residual codes [nq][nprobe] (-1: pair left out).
+__global__ void k_gather_pair_codes(uint32_t n, int r, int rp, const uint32_t* __restrict__ pair_of,
+                                    const int16_t* __restrict__ zq16, const int32_t* __restrict__ rc16,
+                                    int16_t* __restrict__ codes, int32_t* __restrict__ rcodes) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t pr = pair_of[i];
+  for (int j = 0; j < r; ++j) codes[(size_t)i * r + j] = zq16[(size_t)pr * rp + j];
+  rcodes[i] = rc16[pr];
 }
 
 // ------------------------------------------------------------------ bucketing
@@ -294,6 +324,9 @@ struct Ws {
   SparseRec* sparse_items;  // the items with a few, with those pairs (direct-form scan)
   float* zq;
   float* rhoq;
+  int16_t* zq16;     // 16-bit form: per-pair query codes [P][rp]
+  long long* qn16;   // 16-bit form: per-pair sum of squared codes
+  int32_t* rc16;     // 16-bit form: per-pair residual code (-1: left out)
   float* tau;
   uint32_t* cnt;
   unsigned long long* surv;
@@ -331,6 +364,10 @@ Ws carve(const Index& I, uint32_t nq, uint32_t C, uint32_t nprobe, void* base) {
   w.sparse_items = tcp ? c.take<SparseRec>(I.G + I.n_blocks / kSTBlocks + 1) : nullptr;
   w.zq = c.take<float>(P * I.r);
   w.rhoq = c.take<float>(P);
+  const bool i16 = I.precision == HNTL_PREC_INT16;
+  w.zq16 = i16 ? c.take<int16_t>(P * I.rp) : nullptr;
+  w.qn16 = i16 ? c.take<long long>(P) : nullptr;
+  w.rc16 = i16 ? c.take<int32_t>(P) : nullptr;
   w.tau = c.take<float>(nq);
   // survivor counts, then the scan's counters: [nq] next dense item, [nq + 1] dense items,
   // [nq + 2] light sparse items, [nq + 3] next sparse item, [nq + 4] heavy sparse items
@@ -443,8 +480,9 @@ template <int RT, int kC>
 void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, const int64_t* filter,
                         cudaStream_t st, const std::function<void(int)>& mark, const uint32_t* qC) {
   const Coords cz{I.Zb, I.Z8b, I.scale, I.Z16b};
+  const I16Pairs q16{w.zq16, w.qn16};
   k_pilot<RT, kC><<<nq, 256, 0, st>>>(nprobe, C, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho,
-                                        I.attr_b, (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.tau, qC);
+                                        I.attr_b, (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.tau, qC, q16);
   mark(4);
   if constexpr (kC == kCoordFP8) {
     static thread_local int attr_dev = -1;
@@ -471,15 +509,15 @@ void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, 
   } else {
     k_scan_filter<RT, kC><<<(unsigned)I.n_blocks, kBlockRows, 0, st>>>(
         I.blk_grain, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b, (int)I.r, (int)I.rp, w.gcnt, w.pair_off,
-        w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, I.blk_z0, filter, w.cap, w.cnt, w.surv);
+        w.pair_q, w.zq, w.rhoq, w.tau, I.blk_rho_min, I.blk_z0, filter, w.cap, w.cnt, w.surv, q16);
   }
   mark(5);
   k_final_select<RT, kC, false><<<nq, kFinalThreads, 0, st>>>(
       nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b,
-      (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id, w.cand_d, qC);
+      (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id, w.cand_d, qC, q16);
   k_final_select<RT, kC, true><<<nq, kFinalThreads, 0, st>>>(
       nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b,
-      (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id, w.cand_d, qC);
+      (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id, w.cand_d, qC, q16);
 }
 
 template <int RT>
@@ -593,7 +631,8 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
                                               w.pair_q, w.zq, w.rhoq);
     if (I.precision == HNTL_PREC_INT16)
       k_quant_pairs<<<(unsigned)(((size_t)P * 32 + 255) / 256), 256, 0, st>>>(
-          (uint32_t)P, (int)nprobe, w.probe, w.pair_q, w.pair_p, (int)I.r, I.scale, I.dres, w.zq, w.rhoq);
+          (uint32_t)P, (int)nprobe, w.probe, w.pair_q, w.pair_p, (int)I.r, (int)I.rp, I.scale, I.dres,
+          I.i16_resid_prune, w.zq, w.rhoq, w.zq16, w.qn16, w.rc16);
   }
   mark(3);
   HNTL_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * ((size_t)nq + 5), st));
@@ -863,6 +902,58 @@ int hntl_search_probes(const hntl_index* idx, const float* d_queries, uint32_t n
   if (!d_probe_in && nq) return hntl::fail(HNTL_EINVAL, "null probe list");
   return hntl::search(idx->I, d_queries, nq, k, C, nprobe, d_filter, d_ws, ws_bytes, d_out_ids, d_out_dist,
                       d_cand_ids, d_cand_dist, nullptr, static_cast<cudaStream_t>(stream), d_probe_in);
+}
+
+int hntl_search_pair_codes(const hntl_index* idx, const void* d_ws, size_t ws_bytes, uint32_t nq, uint32_t C,
+                           uint32_t nprobe, int16_t* d_codes, int32_t* d_rcodes, void* stream) {
+  hntl::clear_error();
+  if (!idx || !d_ws || !d_codes || !d_rcodes) return hntl::fail(HNTL_EINVAL, "null argument");
+  const hntl::Index& I = idx->I;
+  if (I.precision != HNTL_PREC_INT16) return hntl::fail(HNTL_EINVAL, "query codes exist in the 16-bit form only");
+  uint32_t Ce = C;
+  if (hntl::check_params(I, nq, 1, Ce, nprobe)) return HNTL_EINVAL;
+  const hntl::Ws w = hntl::carve(I, nq, Ce, nprobe, const_cast<void*>(d_ws));
+  if (ws_bytes < w.bytes) return hntl::fail(HNTL_EINVAL, "workspace too small");
+  const uint32_t n = nq * nprobe;
+  if (n == 0) return HNTL_OK;
+  hntl::DeviceGuard dg(I.device);
+  hntl::k_gather_pair_codes<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      n, (int)I.r, (int)I.rp, w.pair_of, w.zq16, w.rc16, d_codes, d_rcodes);
+  HNTL_CUDA_TRY(cudaGetLastError());
+  return HNTL_OK;
+}
+
+namespace hntl {
+namespace {
+// Diagnostic gather of each pair's projection into query order: z_q [n][r] and rho_q [n].
+__global__ void k_gather_pair_proj(uint32_t n, int r, const uint32_t* __restrict__ pair_of,
+                                   const float* __restrict__ zq, const float* __restrict__ rhoq,
+                                   float* __restrict__ z_out, float* __restrict__ rho_out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t pr = pair_of[i];
+  for (int j = 0; j < r; ++j) z_out[(size_t)i * r + j] = zq[(size_t)pr * r + j];
+  rho_out[i] = rhoq[pr];
+}
+}  // namespace
+}  // namespace hntl
+
+int hntl_search_pair_proj(const hntl_index* idx, const void* d_ws, size_t ws_bytes, uint32_t nq, uint32_t C,
+                          uint32_t nprobe, float* d_zq, float* d_rhoq, void* stream) {
+  hntl::clear_error();
+  if (!idx || !d_ws || !d_zq || !d_rhoq) return hntl::fail(HNTL_EINVAL, "null argument");
+  const hntl::Index& I = idx->I;
+  uint32_t Ce = C;
+  if (hntl::check_params(I, nq, 1, Ce, nprobe)) return HNTL_EINVAL;
+  const hntl::Ws w = hntl::carve(I, nq, Ce, nprobe, const_cast<void*>(d_ws));
+  if (ws_bytes < w.bytes) return hntl::fail(HNTL_EINVAL, "workspace too small");
+  const uint32_t n = nq * nprobe;
+  if (n == 0) return HNTL_OK;
+  hntl::DeviceGuard dg(I.device);
+  hntl::k_gather_pair_proj<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      n, (int)I.r, w.pair_of, w.zq, w.rhoq, d_zq, d_rhoq);
+  HNTL_CUDA_TRY(cudaGetLastError());
+  return HNTL_OK;
 }
 
 int hntl_debug_set_persistent_cap(uint32_t ctas) {

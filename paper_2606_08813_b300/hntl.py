@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libhntl.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EIO, EFORMAT, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 PREC_FP32, PREC_BF16_FP8, PREC_INT16 = 0, 1, 2  # INT16: the 16-bit form, built at load from an FP32 file
+INT16_RESID_PRUNE = 0x200  # OR into PREC_INT16: the library's residual-saturation pruning option
 LOAD_NO_RAW = 0x100  # OR into the precision of Index.load: no raw rows on the device (Mode A only)
 INVALID_ID = 0xFFFFFFFF
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EIO: "EIO", EFORMAT: "EFORMAT",
@@ -528,6 +529,28 @@ def search_survivors(index: Index, ws: torch.Tensor, nq: int, C: int, nprobe: in
 
 lib.hntl_search_scan_stats.argtypes = [_P, _P, _SZ, _U32, _U32, _U32, _P, _P]
 lib.hntl_debug_set_persistent_cap.argtypes = [_U32]
+lib.hntl_search_pair_codes.argtypes = [_P, _P, _SZ, _U32, _U32, _U32, _P, _P, _P]
+lib.hntl_search_pair_proj.argtypes = [_P, _P, _SZ, _U32, _U32, _U32, _P, _P, _P]
+
+
+def search_pair_proj(index: Index, ws: torch.Tensor, nq: int, C: int, nprobe: int):
+    """Projection output z_q [nq, nprobe, r] and rho_q [nq, nprobe] (FP32) of the last search run in workspace
+    `ws`, in query order (see hntl_search_pair_proj)."""
+    r = int(index.desc.r)
+    z = torch.zeros(nq, nprobe, r, dtype=torch.float32, device=ws.device)
+    rho = torch.zeros(nq, nprobe, dtype=torch.float32, device=ws.device)
+    _check(lib.hntl_search_pair_proj(index.handle, _ptr(ws), ws.numel(), nq, C, nprobe, _ptr(z), _ptr(rho), None))
+    return z, rho
+
+
+def search_pair_codes(index: Index, ws: torch.Tensor, nq: int, C: int, nprobe: int):
+    """16-bit form: query codes [nq, nprobe, r] int16 and residual codes [nq, nprobe] int32 (-1 = left out) of
+    the last search run in workspace `ws` (see hntl_search_pair_codes)."""
+    r = int(index.desc.r)
+    codes = torch.zeros(nq, nprobe, r, dtype=torch.int16, device=ws.device)
+    rc = torch.zeros(nq, nprobe, dtype=torch.int32, device=ws.device)
+    _check(lib.hntl_search_pair_codes(index.handle, _ptr(ws), ws.numel(), nq, C, nprobe, _ptr(codes), _ptr(rc), None))
+    return codes, rc
 
 
 def search_scan_stats(index: Index, ws: torch.Tensor, nq: int, C: int, nprobe: int) -> dict:

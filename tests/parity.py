@@ -6,8 +6,10 @@ Gap rule: let the oracle's ranking be d_1 <= ... <= d_n <= d_{n+1} (the
 m ids as a set. Distances of ids present in both must agree within RTOL
 relative. Queries whose routing boundary (nprobe-th vs next centre distance)
 is closer than GAP relative have no fixed probe set and are excluded from the
-pool/top-k comparison (counted); queries whose pool boundary (C-th vs
-(C+1)-th) is closer than GAP are excluded from the top-k comparison.
+pool/top-k comparison (counted); where the pool boundary (C-th vs (C+1)-th)
+is closer than GAP, the top k is still compared when the members only one
+pool holds are in neither top k (both are then the top k of the common
+members), and the query is excluded (counted) otherwise.
 """
 import numpy as np
 
@@ -64,8 +66,19 @@ def compare_search(gpu, ora, k, C, nprobe, rtol=RTOL, gap=GAP):
                          ora["cand_d"][qi], "pool", qi, rtol, gap, invalid=0xFFFFFFFF)
         cd = ora["cand_d"][qi]
         if _rel_gap(cd[Ce - 1], cd[Ce]) <= gap and np.isfinite(cd[Ce]):
-            stats["topk_excluded"] += 1
-            continue
+            # the pool's edge is a near tie, so the two pools may hold different
+            # members there. Each top k is the k smallest exact distances of its
+            # pool; when no member that only one pool holds is in that pool's
+            # top k, both are the top k of the common members and must agree.
+            if "pool_ids" not in gpu:
+                stats["topk_excluded"] += 1
+                continue
+            gp = set(int(x) for x in gpu["pool_ids"][qi].astype(np.uint32).tolist()) - {0xFFFFFFFF}
+            op = set(int(x) for x in ora["cand_id"][qi].tolist()) - {0xFFFFFFFF}
+            if (gp - op) & set(int(x) for x in gpu["ids"][qi].tolist()) or \
+                    (op - gp) & set(int(x) for x in ora["out_id"][qi].tolist()):
+                stats["topk_excluded"] += 1
+                continue
         check_ranked(gpu["ids"][qi], gpu["dist"][qi], ora["out_id"][qi], ora["out_d"][qi], "topk", qi, rtol, gap,
                      invalid=-1)
         stats["checked"] += 1

@@ -35,8 +35,8 @@ def hntl():
     return h
 
 
-def run(h, path, Q, k, C, nprobe, filters=None):
-    gi = h.Index.load(path, 0, h.PREC_INT16)
+def run(h, path, Q, k, C, nprobe, filters=None, precision=None):
+    gi = h.Index.load(path, 0, h.PREC_INT16 if precision is None else precision)
     F = None if filters is None else torch.from_numpy(filters).cuda()
     ids, dist, pid, pd, probe = gi.search(torch.from_numpy(np.ascontiguousarray(Q)).cuda(), k, C, nprobe, filters=F,
                                           return_pool=True, return_probe=True)
@@ -170,10 +170,7 @@ def test_int16_filters(hntl, tmp_path):
     assert st["checked"] >= 0.85 * len(Q), st
 
 
-def test_int16_envelope_filter_drops_a_grain_on_residual_saturation(hntl, tmp_path):
-    """Grain B varies only inside its own subspace; the queries sit off it: their
-    coordinates in B's frame stay in range but the residual norm saturates, and
-    B's rows stay out of the pool."""
+def _resid_case(tmp_path):
     rng = np.random.default_rng(19)
     A = rng.standard_normal((50, 8))
     B = np.zeros((50, 8))
@@ -182,11 +179,83 @@ def test_int16_envelope_filter_drops_a_grain_on_residual_saturation(hntl, tmp_pa
     X = np.concatenate([A, B]).astype(np.float32)
     idx = partition_index(X, np.repeat([0, 1], 50), 2, 4)
     Q = (0.1 * rng.standard_normal((3, 8))).astype(np.float32)
-    p = write(tmp_path, "i16res", idx, X)
-    ora = O.search(idx, X, Q, 10, 80, 2, precision="int16")
-    _, gpu = run(hntl, p, Q, 10, 80, 2)
-    for qi in range(3):
-        ids = gpu["pool_ids"][qi]
-        assert set(ids[ids != 0xFFFFFFFF].tolist()) == set(range(50)) == set(
-            ora["cand_id"][qi][ora["cand_id"][qi] != 0xFFFFFFFF].tolist())
-        np.testing.assert_array_equal(gpu["ids"][qi], ora["out_id"][qi])
+    return X, Q, idx, write(tmp_path, "i16res", idx, X)
+
+
+def test_int16_residual_clipped_by_default_and_pruned_by_option(hntl, tmp_path):
+    """Grain B varies only inside its own subspace; the queries sit off it:
+    their coordinates in B's frame stay in range but the residual code exceeds
+    65535. Under the paper's rule (Eq. 5, the filter of sec. 2.3 counts
+    coordinates) the residual is clipped and B's rows enter the pool, on both
+    sides alike; with the library's residual-saturation option B stays out."""
+    X, Q, idx, p = _resid_case(tmp_path)
+    ws_nq, k, C, nprobe = len(Q), 10, 80, 2
+    gi = hntl.Index.load(p, 0, hntl.PREC_INT16)
+    ws = gi.workspace(gi.workspace_bytes(ws_nq, k, C, nprobe))
+    ids, dist, pid, pd = gi.search(torch.from_numpy(Q).cuda(), k, C, nprobe, return_pool=True, ws=ws)
+    codes, rc = hntl.search_pair_codes(gi, ws, ws_nq, C, nprobe)
+    torch.cuda.synchronize()
+    ora = O.search(idx, X, Q, k, C, nprobe, precision="int16",
+                   query_codes=(codes.cpu().numpy(), rc.cpu().numpy()), probes=np.tile([0, 1], (len(Q), 1)))
+    assert (rc.cpu().numpy() == 65535).any()  # the premise: a clipped residual
+    pid = pid.cpu().numpy().view(np.uint32)
+    for qi in range(len(Q)):
+        assert (pid[qi] >= 50).sum() >= 30  # B's rows crowd in with the clipped residual
+        np.testing.assert_array_equal(pid[qi], ora["cand_id"][qi])
+        np.testing.assert_array_equal(pd.cpu().numpy()[qi].astype(np.float64), ora["cand_d"][qi][:C])
+    ora_p = O.search(idx, X, Q, k, C, nprobe, precision="int16", resid_prune=True)
+    _, gp = run(hntl, p, Q, k, C, nprobe, precision=hntl.PREC_INT16 | hntl.INT16_RESID_PRUNE)
+    for qi in range(len(Q)):
+        got = gp["pool_ids"][qi]
+        assert set(got[got != 0xFFFFFFFF].tolist()) == set(range(50)) == set(
+            ora_p["cand_id"][qi][ora_p["cand_id"][qi] != 0xFFFFFFFF].tolist())
+        np.testing.assert_array_equal(gp["ids"][qi], ora_p["out_id"][qi])
+    with pytest.raises(hntl.HntlError):  # the option belongs to the 16-bit form
+        hntl.Index.load(p, 0, hntl.PREC_FP32 | hntl.INT16_RESID_PRUNE)
+
+
+@pytest.mark.parametrize("case", ["clustered", "edge"])
+def test_int16_integer_scan_bit_exact_on_the_same_codes(hntl, tmp_path, case):
+    """The integer scan against the oracle's integer Eq. 6 on the same integer
+    inputs: the GPU's quantised query codes (read back from the workspace) go
+    to the oracle in place of its own quantisation, and then every pool id and
+    pool distance must be equal bit for bit (the same integer sums, the same
+    single-precision scale-back), the top k to the parity tolerance. Covers
+    dp2a sums over r = 5 (padded lane), 16 and 64 codes, grains of 0 .. 300
+    rows, and pools that overflow into the recomputing fallback (C = 685)."""
+    if case == "clustered":
+        X, Q, idx = clustered_case(8000, 64, 8, 8, 16, 200, seed=231, sizes="zipf")
+        shapes = [(10, 50, 3), (10, 685, 8)]
+    else:
+        sizes = [0, 1, 127, 128, 129, 300]
+        rng = np.random.default_rng(77)
+        d = 64
+        centres = rng.standard_normal((len(sizes), d)) * 3
+        assign = np.repeat(np.arange(len(sizes)), sizes)
+        X = (centres[assign] + rng.standard_normal((len(assign), d)) * 0.7).astype(np.float32)
+        Q = (centres[rng.integers(0, len(sizes), 40)] + rng.standard_normal((40, d)) * 0.7).astype(np.float32)
+        shapes = []
+        for r in (5, 64):
+            idx_r = partition_index(X, assign, len(sizes), r)
+            shapes.append((idx_r, (10, 200, 3)))
+    runs = [(idx, sh) for sh in shapes] if case == "clustered" else shapes
+    for n_run, (ix, (k, C, nprobe)) in enumerate(runs):
+        p = write(tmp_path, f"i16x{case}{n_run}", ix, X)
+        gi = hntl.Index.load(p, 0, hntl.PREC_INT16)
+        nq = len(Q)
+        ws = gi.workspace(gi.workspace_bytes(nq, k, C, nprobe))
+        ids, dist, pid, pd, probe = gi.search(torch.from_numpy(Q).cuda(), k, C, nprobe, return_pool=True,
+                                              return_probe=True, ws=ws)
+        codes, rc = hntl.search_pair_codes(gi, ws, nq, C, nprobe)
+        torch.cuda.synchronize()
+        codes, rc = codes.cpu().numpy(), rc.cpu().numpy()
+        # the codes belong to the GPU's probe list, so the oracle takes that list too
+        ora = O.search(ix, X, Q, k, max(C, k), nprobe, precision="int16", query_codes=(codes, rc),
+                       probes=probe.cpu().numpy())
+        pidn = pid.cpu().numpy().view(np.uint32)
+        np.testing.assert_array_equal(pidn, ora["cand_id"])
+        np.testing.assert_array_equal(pd.cpu().numpy().astype(np.float64), ora["cand_d"][:, :C])
+        for qi in range(nq):
+            check_ranked(ids.cpu().numpy()[qi], dist.cpu().numpy()[qi], ora["out_id"][qi], ora["out_d"][qi], "topk",
+                         qi, invalid=-1)
+        assert hntl.device_status(gi) == 0

@@ -347,11 +347,100 @@ def test_int16_envelope_filter_drops_a_far_grain():
         assert (ids == 0xFFFFFFFF).sum() == 30
 
 
-def test_int16_envelope_filter_drops_a_grain_on_residual_saturation():
+def _int16_query_side(idx, f, q, g):
+    """The 16-bit form's query side written out in numpy float32 (Eq. 5):
+    codes rint(fl32(z / delta)) saturating at +-32767 (count of saturated
+    ones) and the residual code rint(fl32(rho / dres)) before any clipping."""
+    v = q.astype(np.float64) - idx["M"][g].astype(np.float64)
+    U = idx["U"][g].astype(np.float64)
+    zq = U @ v
+    rq = float(((v - U.T @ zq) ** 2).sum())
+    t = np.rint(np.float32(zq.astype(np.float32)) / np.float32(f["delta"][g])).astype(np.float64)
+    sat = int((np.abs(t) > 32767).sum())
+    codes = np.clip(t, -32767, 32767).astype(np.int64)
+    rcode = float(np.rint(np.float32(rq) / np.float32(f["dres"][g])))
+    return codes, rcode, sat
+
+
+def _int16_D(f, g, codes_q, rcode_q, row_codes, rho_grid_i):
+    """Eq. 6 on the codes: exact integer S, then fl32(fl32(delta^2) fl32(S)) + fl32(rho_q + rho_i)."""
+    S = int(sum((int(a) - int(b)) ** 2 for a, b in zip(codes_q, row_codes)))
+    dl = np.float32(f["delta"][g])
+    rq = np.float32(np.float32(rcode_q) * np.float32(f["dres"][g]))
+    return float(np.float32(np.float32(dl * dl) * np.float32(S)) + np.float32(rq + np.float32(rho_grid_i)))
+
+
+def test_int16_distance_is_integer_eq6_on_the_codes():
+    """Pool distances of the 16-bit form are Eq. 6 on the integer codes,
+    bit for bit: the integer sum written out with Python integers and the
+    scale-back with numpy float32 operations; giving the oracle the same query
+    codes reproduces its own quantisation's result exactly."""
+    X, Q, _ = _clustered(1200, 16, 3, 8, 95)
+    idx = O.build_index(X, 3, 5, synth.uniforms(3, 9).numpy())
+    f = O.int16_form(idx)
+    res = O.search(idx, X, Q, 5, 60, 2, precision="int16")
+    pos = np.zeros(len(X), dtype=np.int64)
+    pos[idx["ids"]] = np.arange(len(X))
+    gof = np.repeat(np.arange(3), np.diff(idx["grain_off"]))
+    qcodes = np.zeros((len(Q), 2, 5), dtype=np.int16)
+    qr = np.zeros((len(Q), 2), dtype=np.int32)
+    n = 0
+    for qi in range(len(Q)):
+        per = {}
+        for p, g in enumerate(res["probe"][qi]):
+            c, rc, sat = _int16_query_side(idx, f, Q[qi], int(g))
+            assert 4 * sat <= 5  # the premise: no grain is left out here
+            per[int(g)] = (c, min(rc, 65535.0))
+            qcodes[qi, p] = c
+            qr[qi, p] = int(min(rc, 65535.0))
+        for i, d in zip(res["cand_id"][qi].tolist(), res["cand_d"][qi].tolist()):
+            if i == 0xFFFFFFFF:
+                continue
+            g = int(gof[pos[i]])
+            c, rc = per[g]
+            want = _int16_D(f, g, c, rc, f["codes"][pos[i]], f["rhof32"][pos[i]])
+            assert d == want, (qi, i, d, want)
+            n += 1
+    assert n > 400
+    again = O.search(idx, X, Q, 5, 60, 2, precision="int16", query_codes=(qcodes, qr))
+    assert np.array_equal(again["cand_id"], res["cand_id"])
+    assert np.array_equal(again["cand_d"], res["cand_d"]) and np.array_equal(again["out_id"], res["out_id"])
+
+
+def test_int16_residual_is_clipped_not_pruned_by_default():
     """Grain B varies only inside its own 4-dimensional subspace; a query near
     grain A projects into B's frame with coordinates inside B's range (no
-    coordinate saturates) but with a residual norm far beyond any of B's rows:
-    that saturation leaves B out of the 16-bit form's pool."""
+    coordinate saturates) but with a residual norm far beyond any of B's rows.
+    The paper's filter counts coordinates only, so B stays in the scan with the
+    query's residual code clipped at 65535 (Eq. 5, unsigned 16 bits): B's rows
+    enter the pool at exactly the distances of that clipped residual. With the
+    residual-saturation option (the build's own rule) B is left out."""
+    rng = np.random.default_rng(19)
+    A = rng.standard_normal((50, 8))
+    B = np.zeros((50, 8))
+    B[:, :4] = rng.standard_normal((50, 4))
+    B[:, 4:] = 20.0 + 1e-3 * rng.standard_normal((50, 4))
+    X = np.concatenate([A, B]).astype(np.float32)
+    idx = partition_index(X, np.repeat([0, 1], 50), 2, 4)
+    Q = (0.1 * rng.standard_normal((3, 8))).astype(np.float32)
+    f = O.int16_form(idx)
+    pos = np.zeros(len(X), dtype=np.int64)
+    pos[idx["ids"]] = np.arange(len(X))
+    i16 = O.search(idx, X, Q, 10, 80, 2, precision="int16")
+    for qi in range(3):
+        c, rc, sat = _int16_query_side(idx, f, Q[qi], 1)
+        assert sat == 0 and rc > 65535  # the premise
+        ids = i16["cand_id"][qi]
+        b_rows = [(i, d) for i, d in zip(ids.tolist(), i16["cand_d"][qi].tolist()) if 50 <= i < 100]
+        # the clipped residual is tiny on B's fine grid, so B's rows look close and crowd the pool
+        assert len(b_rows) >= 30
+        for i, d in b_rows:
+            assert d == _int16_D(f, 1, c, 65535.0, f["codes"][pos[i]], f["rhof32"][pos[i]])
+
+
+def test_int16_residual_prune_option_drops_the_grain():
+    """The build's own option: with residual-saturation pruning on, the same
+    grain B (query residual beyond 65535 steps) is left out of the pool."""
     rng = np.random.default_rng(19)
     A = rng.standard_normal((50, 8))
     B = np.zeros((50, 8))
@@ -365,7 +454,7 @@ def test_int16_envelope_filter_drops_a_grain_on_residual_saturation():
         zq = idx["U"][1].astype(np.float64) @ (q - idx["M"][1].astype(np.float64))
         assert np.abs(zq).max() < 32767 * float(f["delta"][1])
     f32 = O.search(idx, X, Q, 10, 80, 2, precision="fp32")
-    i16 = O.search(idx, X, Q, 10, 80, 2, precision="int16")
+    i16 = O.search(idx, X, Q, 10, 80, 2, precision="int16", resid_prune=True)
     for qi in range(3):
         assert (f32["cand_id"][qi] >= 50).sum() == 30
         ids = i16["cand_id"][qi]
