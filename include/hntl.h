@@ -129,7 +129,8 @@ typedef struct {
   uint64_t n_train;       /* k-means training rows, strided over the data (0 = min(N, 256 G)) */
   uint64_t n_seed;        /* k-means++ seeding rows, strided over the training rows (0 = min(n_train, 32 G)) */
   uint32_t pca_iters;     /* orthogonal iterations for each grain's basis (0 = 12) */
-  uint32_t reserved;
+  uint32_t max_grain_rows; /* 0: every row joins its nearest centre; else grains of at most this many rows
+                              (>= ceil(N / G)) by deferred acceptance, see hntl_index_build */
   uint64_t seed;          /* initial bases, and the k-means++ draws when u is NULL */
   const double* u;        /* host, G uniform draws in [0, 1) consumed by k-means++, or NULL */
   const int64_t* d_attr;  /* device, N int64 attributes in id order (for filtered search), or NULL */
@@ -139,7 +140,12 @@ typedef struct {
  * the index keeps its own copy, BF16 in the precision form) and return it in
  * *out. Grains: k-means++ seeding and Lloyd iterations (the paper leaves the
  * partitioning open, sec. 2.2), then every row goes to its nearest centre and
- * each centre becomes the mean of its members. Basis of each grain (sec. 2.2):
+ * each centre becomes the mean of its members. With max_grain_rows = cap > 0
+ * the final assignment instead bounds every grain at cap rows: deferred
+ * acceptance with rows proposing (Gale and Shapley, 1962), rows ranking
+ * centres by (distance, grain) and centres ranking rows by (distance, row),
+ * which gives the row-optimal stable assignment (balanced work per grain; the
+ * grains are then no longer the centres' Voronoi cells). Basis of each grain (sec. 2.2):
  * the dominant r-dimensional subspace of the grain covariance by orthogonal
  * iteration; coordinates and residual norms by Eq. 1-4. Precision form: FP8
  * E4M3 coordinates with scale s_g = max|z| / 448 per grain, BF16 rows.

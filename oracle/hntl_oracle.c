@@ -273,6 +273,102 @@ int64_t or_lloyd(const float* X, int64_t n, int64_t d, int64_t G, double* M, int
 }
 
 /* ------------------------------------------------------------------ */
+/* capacity-bounded grains: deferred acceptance                        */
+/* ------------------------------------------------------------------ */
+
+/* Grains of at most cap rows (the paper leaves the partition open, sec. 2.2;
+ * bounded grain sizes are this build's reading for balanced work). Deferred
+ * acceptance with rows proposing (Gale and Shapley, 1962): every row ranks
+ * the centres by (squared distance, grain) and every centre ranks rows by
+ * (squared distance, row); a free row proposes to its best centre that has
+ * not yet refused it; a centre holding cap rows keeps the cap it ranks best
+ * among them and the proposer and refuses the other. The result is the
+ * row-optimal stable assignment, which does not depend on the order in which
+ * free rows propose. Requires cap * G >= n. Distances in FP64 (FP64 centres). */
+typedef struct {
+  double dist;
+  int64_t row;
+} held_t;
+
+static int held_worse(held_t a, held_t b) { /* a ranks below b for the centre */
+  return a.dist > b.dist || (a.dist == b.dist && a.row > b.row);
+}
+
+void or_balanced_assign(const float* X, int64_t n, int64_t d, const double* M, int64_t G, int64_t cap,
+                        int32_t* assign) {
+  int32_t* pref = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n * G));
+  double* dist = (double*)malloc(sizeof(double) * (size_t)(n * G));
+#pragma omp parallel
+  {
+    pair_t* tmp = (pair_t*)malloc(sizeof(pair_t) * (size_t)G);
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+      for (int64_t g = 0; g < G; ++g) {
+        tmp[g].dist = sq_diff_f32_f64(X + i * d, M + g * d, d);
+        tmp[g].key = g;
+        dist[i * G + g] = tmp[g].dist;
+      }
+      qsort(tmp, (size_t)G, sizeof(pair_t), pair_cmp);
+      for (int64_t g = 0; g < G; ++g) pref[i * G + g] = (int32_t)tmp[g].key;
+    }
+    free(tmp);
+  }
+  /* per centre a max-heap (worst held row on top) of at most cap rows */
+  held_t* heap = (held_t*)malloc(sizeof(held_t) * (size_t)(G * cap));
+  int64_t* hn = (int64_t*)calloc((size_t)G, sizeof(int64_t));
+  int64_t* next = (int64_t*)calloc((size_t)n, sizeof(int64_t));
+  int64_t* stack = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t top = 0;
+  for (int64_t i = n - 1; i >= 0; --i) stack[top++] = i;
+  while (top > 0) {
+    const int64_t i = stack[--top];
+    if (next[i] >= G) continue; /* cannot happen when cap * G >= n */
+    const int64_t g = pref[i * G + next[i]++];
+    held_t* h = heap + g * cap;
+    held_t me = {dist[i * G + g], i};
+    if (hn[g] < cap) {
+      int64_t k = hn[g]++;
+      h[k] = me;
+      while (k > 0) {
+        const int64_t p = (k - 1) / 2;
+        if (!held_worse(h[k], h[p])) break;
+        held_t t = h[k];
+        h[k] = h[p];
+        h[p] = t;
+        k = p;
+      }
+      assign[i] = (int32_t)g;
+    } else if (held_worse(h[0], me)) {
+      const int64_t out = h[0].row;
+      h[0] = me;
+      int64_t k = 0;
+      for (;;) {
+        const int64_t l = 2 * k + 1, r = l + 1;
+        int64_t m = k;
+        if (l < cap && held_worse(h[l], h[m])) m = l;
+        if (r < cap && held_worse(h[r], h[m])) m = r;
+        if (m == k) break;
+        held_t t = h[k];
+        h[k] = h[m];
+        h[m] = t;
+        k = m;
+      }
+      assign[i] = (int32_t)g;
+      assign[out] = -1;
+      stack[top++] = out;
+    } else {
+      stack[top++] = i; /* refused: propose to the next centre */
+    }
+  }
+  free(pref);
+  free(dist);
+  free(heap);
+  free(hn);
+  free(next);
+  free(stack);
+}
+
+/* ------------------------------------------------------------------ */
 /* Mode B search                                                       */
 /* ------------------------------------------------------------------ */
 

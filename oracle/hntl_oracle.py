@@ -73,6 +73,7 @@ def _c():
             lib.or_means.restype = I
             lib.or_lloyd.argtypes = [P, I, I, I, P, I, P]
             lib.or_lloyd.restype = I
+            lib.or_balanced_assign.argtypes = [P, I, I, P, I, I, P]
             lib.or_search.argtypes = [P, P, I, I, I, P, P, P, P, P, P, P, P, I, I, I, I, P,
                                       P, P, P, P, P, P, I, P, P, P, P, P, P, I, P, P]
             lib.or_threads.restype = ctypes.c_int
@@ -102,12 +103,29 @@ def set_threads(n: int) -> None:
 # ---------------------------------------------------------------------------
 
 
-def kmeans(X, G: int, u, train_idx=None, max_iter: int = 25):
+def balanced_assign(X, M, cap: int):
+    """Capacity-bounded grains (see or_balanced_assign in hntl_oracle.c): the
+    row-proposing stable assignment of the rows of X to the centres M with at
+    most `cap` rows per grain. Returns assign i32 [N]."""
+    X = _f32(X)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    n, d = X.shape
+    G = M.shape[0]
+    if cap * G < n:
+        raise ValueError("cap * G must be at least N")
+    out = np.full(n, -1, dtype=np.int32)
+    _c().or_balanced_assign(_p(X), n, d, _p(M), G, int(cap), _p(out))
+    return out
+
+
+def kmeans(X, G: int, u, train_idx=None, max_iter: int = 25, max_grain_rows: int = 0):
     """Grain partition of X: k-means++ seeding (draws `u`, one per centre) on
     the training rows, Lloyd iterations there, one assignment pass of all rows
-    to the trained centres, then each centre is the exact FP64 mean of its
-    final members rounded once to FP32 (an empty final grain keeps its trained
-    centre). Returns (mu f32 [G, d], assign i32 [N], lloyd_iterations)."""
+    to the trained centres (with max_grain_rows > 0, the capacity-bounded
+    assignment of balanced_assign instead), then each centre is the exact FP64
+    mean of its final members rounded once to FP32 (an empty final grain keeps
+    its trained centre). Returns (mu f32 [G, d], assign i32 [N],
+    lloyd_iterations)."""
     X = _f32(X)
     n, d = X.shape
     u = np.ascontiguousarray(u, dtype=np.float64)
@@ -123,7 +141,10 @@ def kmeans(X, G: int, u, train_idx=None, max_iter: int = 25):
     at = np.zeros(nt, dtype=np.int32)
     iters = lib.or_lloyd(_p(Xt), nt, d, G, _p(M), max_iter, _p(at))
     assign = np.zeros(n, dtype=np.int32)
-    lib.or_assign(_p(X), n, d, _p(M), G, _p(assign), None)
+    if max_grain_rows:
+        assign = balanced_assign(X, M, max_grain_rows)
+    else:
+        lib.or_assign(_p(X), n, d, _p(M), G, _p(assign), None)
     count = np.zeros(G, dtype=np.int64)
     Mf = M.copy()
     lib.or_means(_p(X), n, d, _p(assign), G, _p(Mf), _p(count))
@@ -161,7 +182,8 @@ def tangent(X, rows, mu32, U):
     return Z, np.einsum("ij,ij->i", E, E)
 
 
-def build_index(X, G: int, r: int, u, train_idx=None, max_iter: int = 25, keep_fp64: bool = False):
+def build_index(X, G: int, r: int, u, train_idx=None, max_iter: int = 25, keep_fp64: bool = False,
+                max_grain_rows: int = 0):
     """Oracle index build: partition, per-grain PCA, database coordinates.
 
     Rows are stored in grain order (ascending original id inside a grain).
@@ -174,7 +196,7 @@ def build_index(X, G: int, r: int, u, train_idx=None, max_iter: int = 25, keep_f
     n, d = X.shape
     if not (1 <= r <= d):
         raise ValueError("need 1 <= r <= d")
-    mu, assign, iters = kmeans(X, G, u, train_idx, max_iter)
+    mu, assign, iters = kmeans(X, G, u, train_idx, max_iter, max_grain_rows)
     order = np.argsort(assign, kind="stable")
     counts = np.bincount(assign, minlength=G)
     grain_off = np.zeros(G + 1, dtype=np.int64)

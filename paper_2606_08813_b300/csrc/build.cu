@@ -17,8 +17,10 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "hntl_internal.cuh"
@@ -35,8 +37,10 @@ constexpr int kNT = 64, kNK = 32;
 // packed[i] = min over g of (bits(||x_i - m_g||^2) << 32 | g): the lexicographic
 // (distance, grain) minimum. Distances are non-negative, so their bit patterns
 // order like their values. 64 x 64 tile per CTA, 4 x 4 per thread.
+template <bool kTile>
 __global__ void __launch_bounds__(256) k_nearest(const float* __restrict__ X, int64_t n, const float* __restrict__ M,
-                                                 int G, int d, unsigned long long* __restrict__ packed) {
+                                                 int G, int d, unsigned long long* __restrict__ packed,
+                                                 float* __restrict__ tile) {
   __shared__ __align__(16) float sX[kNK][kNT + 4];
   __shared__ __align__(16) float sM[kNK][kNT + 4];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -73,6 +77,18 @@ __global__ void __launch_bounds__(256) k_nearest(const float* __restrict__ X, in
     }
     __syncthreads();
   }
+  if constexpr (kTile) {  // every distance of the tile, rows of G (each sums t = 0 .. d-1 in order, by fmaf)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t q = q0 + ty * 4 + i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int g = g0 + tx * 4 + j;
+        if (q < n && g < G) tile[q * G + g] = acc[i][j];
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     unsigned long long best = ~0ull;
@@ -105,6 +121,33 @@ __global__ void k_unpack(const unsigned long long* __restrict__ packed, int64_t 
   assign[i] = g;
   if (dist) dist[i] = __uint_as_float((uint32_t)(p >> 32));
   if (prev && prev[i] != g) atomicAdd(changed, 1u);
+}
+
+// One warp per row of a distance tile [n][G]: its K smallest (distance, grain)
+// keys in ascending order (K rounds of a warp minimum above the last pick).
+__global__ void k_topk_rows(const float* __restrict__ tile, int64_t n, int G, int K,
+                            unsigned long long* __restrict__ out) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const float* row = tile + w * G;
+  unsigned long long last = 0;
+  for (int k = 0; k < K; ++k) {
+    unsigned long long best = ~0ull;
+    for (int g = lane; g < G; g += 32) {
+      float v = row[g];
+      if (!(v == v)) v = INFINITY;
+      const unsigned long long key = ((unsigned long long)__float_as_uint(v) << 32) | (uint32_t)g;
+      if ((k == 0 || key > last) && key < best) best = key;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+      best = other < best ? other : best;
+    }
+    last = best;
+    if (lane == 0) out[w * K + k] = best;
+  }
 }
 
 // ------------------------------------------------------------------ k-means++ and means
@@ -515,9 +558,105 @@ int nearest(const float* X, int64_t n, const float* M, int G, int d, unsigned lo
   for (int64_t s = 0; s < n; s += chunk) {
     int64_t m = std::min(chunk, n - s);
     dim3 grid((G + kNT - 1) / kNT, (unsigned)((m + kNT - 1) / kNT));
-    k_nearest<<<grid, 256, 0, st>>>(X + s * d, m, M, G, d, packed + s);
+    k_nearest<false><<<grid, 256, 0, st>>>(X + s * d, m, M, G, d, packed + s, nullptr);
   }
   HNTL_CUDA_TRY(cudaGetLastError());
+  return HNTL_OK;
+}
+
+// Capacity-bounded grains (hntl_build_params.max_grain_rows): deferred
+// acceptance with rows proposing (Gale and Shapley, 1962). A row proposes to
+// the centres in order of (distance, grain); a centre keeps the `cap` rows it
+// ranks best by (distance, row) and refuses the rest. The row-proposing stable
+// assignment does not depend on the order of the proposals, so the host runs
+// the classic sequential loop over lists the GPU prepares: each row's kTopK
+// nearest centres (FP32 distances summed over t = 0 .. d-1 by fmaf, as the
+// nearest-centre pass forms them). A row refused by all of them gets its full
+// ranking computed on the host with the same arithmetic. cap * G >= N.
+constexpr int kTopK = 8;
+
+int balanced_assign(const float* dX, uint64_t N, uint32_t d, uint32_t G, const float* M, uint32_t cap,
+                    int32_t* assign_dev, Tmp& T, cudaStream_t st) {
+  int rc = HNTL_OK;
+  const int64_t chunk = std::max<int64_t>(kNT, ((int64_t)1 << 28) / (int64_t)G / kNT * kNT);
+  const int64_t R = std::min<int64_t>((int64_t)N, chunk);
+  float* tile = T.get<float>((size_t)R * G, &rc);
+  unsigned long long* topk = T.get<unsigned long long>((size_t)N * kTopK, &rc);
+  if (rc) return rc;
+  const int K = (int)std::min<uint32_t>(kTopK, G);
+  for (int64_t s = 0; s < (int64_t)N; s += R) {
+    const int64_t m = std::min<int64_t>(R, (int64_t)N - s);
+    for (int64_t s2 = 0; s2 < m; s2 += (int64_t)kNT * 65535) {
+      const int64_t m2 = std::min<int64_t>((int64_t)kNT * 65535, m - s2);
+      dim3 grid((G + kNT - 1) / kNT, (unsigned)((m2 + kNT - 1) / kNT));
+      k_nearest<true><<<grid, 256, 0, st>>>(dX + (s + s2) * d, m2, M, (int)G, (int)d, nullptr, tile + s2 * G);
+    }
+    k_topk_rows<<<(unsigned)((m * 32 + 255) / 256), 256, 0, st>>>(tile, m, (int)G, K, topk + (size_t)s * kTopK);
+    HNTL_CUDA_TRY(cudaGetLastError());
+  }
+  std::vector<unsigned long long> h_top((size_t)N * kTopK);
+  std::vector<float> h_M((size_t)G * d);
+  HNTL_CUDA_TRY(cudaMemcpyAsync(h_top.data(), topk, h_top.size() * 8, cudaMemcpyDeviceToHost, st));
+  HNTL_CUDA_TRY(cudaMemcpyAsync(h_M.data(), M, h_M.size() * 4, cudaMemcpyDeviceToHost, st));
+  HNTL_CUDA_TRY(cudaStreamSynchronize(st));
+  // held rows of each centre: a max-heap on (distance bits, row), worst on top
+  using Held = std::pair<uint32_t, uint32_t>;
+  std::vector<std::vector<Held>> heap(G);
+  std::vector<uint32_t> next(N, 0);
+  std::vector<int32_t> assign(N, -1);
+  std::unordered_map<uint32_t, std::vector<unsigned long long>> longer;  // full rankings of exhausted rows
+  std::vector<float> xrow(d);
+  std::vector<uint32_t> stack(N);
+  for (uint64_t i = 0; i < N; ++i) stack[i] = (uint32_t)(N - 1 - i);
+  while (!stack.empty()) {
+    const uint32_t i = stack.back();
+    stack.pop_back();
+    unsigned long long key;
+    if (next[i] < (uint32_t)K) {
+      key = h_top[(size_t)i * kTopK + next[i]];
+    } else {
+      auto it = longer.find(i);
+      if (it == longer.end()) {  // every centre, with the GPU's arithmetic
+        HNTL_CUDA_TRY(cudaMemcpy(xrow.data(), dX + (size_t)i * d, (size_t)d * 4, cudaMemcpyDeviceToHost));
+        std::vector<unsigned long long> all(G);
+        for (uint32_t g = 0; g < G; ++g) {
+          float acc = 0.f;
+          for (uint32_t t = 0; t < d; ++t) {
+            const float df = xrow[t] - h_M[(size_t)g * d + t];
+            acc = std::fma(df, df, acc);
+          }
+          uint32_t bits;
+          std::memcpy(&bits, &acc, 4);
+          all[g] = ((unsigned long long)bits << 32) | g;
+        }
+        std::sort(all.begin(), all.end());
+        it = longer.emplace(i, std::move(all)).first;
+      }
+      if (next[i] >= G) return fail(HNTL_ECUDA, "balanced assignment: a row was refused by every centre");
+      key = it->second[next[i]];
+    }
+    ++next[i];
+    const uint32_t g = (uint32_t)(key & 0xFFFFFFFFu);
+    const Held me{(uint32_t)(key >> 32), i};
+    auto& h = heap[g];
+    if (h.size() < cap) {
+      h.push_back(me);
+      std::push_heap(h.begin(), h.end());
+      assign[i] = (int32_t)g;
+    } else if (me < h.front()) {
+      std::pop_heap(h.begin(), h.end());
+      const uint32_t out = h.back().second;
+      h.back() = me;
+      std::push_heap(h.begin(), h.end());
+      assign[i] = (int32_t)g;
+      assign[out] = -1;
+      stack.push_back(out);
+    } else {
+      stack.push_back(i);
+    }
+  }
+  HNTL_CUDA_TRY(cudaMemcpyAsync(assign_dev, assign.data(), N * 4, cudaMemcpyHostToDevice, st));
+  HNTL_CUDA_TRY(cudaStreamSynchronize(st));
   return HNTL_OK;
 }
 
@@ -551,6 +690,8 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   const uint64_t n_t = std::min<uint64_t>(N, P.n_train ? P.n_train : 256ull * G);
   const uint64_t n_s = std::min<uint64_t>(n_t, P.n_seed ? P.n_seed : 32ull * G);
   if (n_s < G) return fail(HNTL_EINVAL, "seeding subset smaller than G");
+  if (P.max_grain_rows && (uint64_t)P.max_grain_rows * G < N)
+    return fail(HNTL_EINVAL, "max_grain_rows * G must be at least N");
   std::vector<double> u(G);
   if (P.u) {
     std::memcpy(u.data(), P.u, sizeof(double) * G);
@@ -674,12 +815,19 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
     return rc;
   }
 
-  // --- final assignment of all rows, exact means of final members
-  if ((rc = nearest(dX, (int64_t)N, M, (int)G, (int)d, packed, st))) {
-    cleanup();
-    return rc;
+  // --- final assignment of all rows (nearest centre, or capacity-bounded), exact means of final members
+  if (P.max_grain_rows) {
+    if ((rc = balanced_assign(dX, N, d, G, M, P.max_grain_rows, assign, T, st))) {
+      cleanup();
+      return rc;
+    }
+  } else {
+    if ((rc = nearest(dX, (int64_t)N, M, (int)G, (int)d, packed, st))) {
+      cleanup();
+      return rc;
+    }
+    k_unpack<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(packed, (int64_t)N, assign, nullptr, nullptr, nullptr);
   }
-  k_unpack<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(packed, (int64_t)N, assign, nullptr, nullptr, nullptr);
   HNTL_CUDA_TRY(cudaMemsetAsync(sums, 0, (size_t)G * d * 8, st));
   HNTL_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)G * 4, st));
   k_accum<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(dX, (int64_t)N, (int)d, assign, sums, counts);

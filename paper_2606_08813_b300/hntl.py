@@ -72,7 +72,7 @@ STAGES = ("route", "bucket", "project", "pilot", "scan", "select", "rerank")
 
 class BuildParams(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_uint32), ("max_iter", ctypes.c_uint32), ("n_train", ctypes.c_uint64),
-                ("n_seed", ctypes.c_uint64), ("pca_iters", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("n_seed", ctypes.c_uint64), ("pca_iters", ctypes.c_uint32), ("max_grain_rows", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("u", _P), ("d_attr", _P)]
 
 
@@ -177,7 +177,7 @@ class Index:
     @classmethod
     def build(cls, X: torch.Tensor, G: int, r: int, precision: int = PREC_FP32, u=None, seed: int = 0,
               attr: torch.Tensor | None = None, max_iter: int = 0, n_train: int = 0, n_seed: int = 0,
-              pca_iters: int = 0, stream=None) -> "Index":
+              pca_iters: int = 0, max_grain_rows: int = 0, stream=None) -> "Index":
         """Build an index on the GPU from CUDA rows X [N, d] f32 (see hntl_index_build)."""
         if not X.is_cuda or X.dtype != torch.float32 or X.dim() != 2 or not X.is_contiguous():
             raise ValueError("X must be a contiguous CUDA float32 tensor [N, d]")
@@ -194,7 +194,7 @@ class Index:
                 raise ValueError("need G uniform draws")
             u_arr = u_np
         prm = BuildParams(precision=precision, max_iter=max_iter, n_train=n_train, n_seed=n_seed,
-                          pca_iters=pca_iters, reserved=0, seed=seed,
+                          pca_iters=pca_iters, max_grain_rows=max_grain_rows, seed=seed,
                           u=None if u_arr is None else u_arr.ctypes.data_as(_P),
                           d_attr=None if attr is None else attr.data_ptr())
         h = _P()

@@ -139,3 +139,48 @@ def test_built_int16_form_matches_oracle_quantisation_and_search(hntl, plain10k)
     ref = O.search(exp, X, Q, 10, 20, 4, precision="int16")
     agree = np.mean([len(set(a.tolist()) & set(b.tolist())) / 10 for a, b in zip(ids.cpu().numpy(), ref["out_id"])])
     assert agree > 0.99, agree
+
+
+def test_basis_spans_the_oracle_eigenvectors_above_the_gap(plain10k):
+    """Principal angles against the oracle's eigendecomposition of the same
+    members: the workload's rows vary along 8 directions per cluster (stds
+    0.8^i) above an isotropic floor (0.05^2), so the top 8 eigenvectors are
+    well separated from the rest; each must lie in the GPU basis's span (its
+    projection keeps 1 - 1e-6 of its length)."""
+    X, ora, gi, exp = plain10k
+    off = exp["grain_off"]
+    for g in range(exp["G"]):
+        rows = exp["ids"][off[g]:off[g + 1]]
+        U = exp["U"][g].astype(np.float64)
+        E, _ = O.grain_pca(X, rows, exp["M"][g], 8)
+        for j in range(8):
+            e = E[j]
+            kept = np.linalg.norm(U @ e)
+            assert kept >= 1 - 1e-6, (g, j, kept)
+
+
+def test_capacity_bounded_grains_match_oracle(hntl):
+    """Zipf clusters (the largest far above N / G rows) into grains of at most
+    ceil(1.05 N / G) rows: the GPU's deferred acceptance (top-8 lists on the
+    GPU, proposals on the host) against the oracle's, from the same k-means++
+    draws and Lloyd iterations."""
+    n, d, G = 12000, 48, 96
+    m = synth.make_cluster_model(n, d, 12, sizes="zipf", seed=321)
+    X, _ = synth.sample_points(m, 322)
+    X = X.numpy()
+    cap = int(np.ceil(1.05 * n / G))
+    u = synth.uniforms(G, 323).numpy()
+    ora = O.build_index(X, G, 8, u, max_grain_rows=cap)
+    plain = O.build_index(X, G, 8, u)
+    assert np.bincount(plain["assign"], minlength=G).max() > cap  # the premise: plain grains overflow the cap
+    gi = hntl.Index.build(torch.from_numpy(X).cuda(), G, 8, u=u, n_train=n, n_seed=n, max_iter=25, seed=3,
+                          max_grain_rows=cap)
+    exp = gi.export()
+    off = exp["grain_off"]
+    assert np.diff(off).max() <= cap
+    g_assign = np.zeros(n, dtype=np.int64)
+    for g in range(G):
+        g_assign[exp["ids"][off[g]:off[g + 1]]] = g
+    assert (g_assign == ora["assign"]).mean() >= 0.999, (g_assign == ora["assign"]).mean()
+    with pytest.raises(hntl.HntlError):  # a cap below N / G cannot hold every row
+        hntl.Index.build(torch.from_numpy(X).cuda(), G, 8, u=u, max_grain_rows=n // G - 1)

@@ -238,21 +238,24 @@ def _labels(X, Q, assign, G, k=10):
 
 def test_training_gain_over_centroid_routing(hntl, tmp_path):
     """What the trained router gains over the method without it (centroid
-    routing) at the same nprobe, on Zipf clusters split by k-means into more
-    grains than clusters. Measured: the router reaches centroid routing's
-    recall (within 0.02) and is far above the same network untrained; on
-    k-means grains the nearest centre is already the best single choice for
-    the expected neighbour share, so the measured gain is about zero (printed
-    with the best-single-grain bound, which needs each query's true
-    neighbours). Training brings the loss close to its floor (the targets'
-    entropy)."""
-    d, n_clusters, G, r = 64, 24, 64, 8
-    m = synth.make_cluster_model(30000, d, n_clusters, sizes="zipf", seed=81)
-    X, _ = synth.sample_points(m, 82)
-    Qtr, _ = synth.sample_queries(m, 6144, 83)
-    Qev, _ = synth.sample_queries(m, 1000, 84)
+    routing) at the same nprobe. Grains are capacity-bounded (at most N / G
+    rows each, by deferred acceptance): Zipf-sized clusters overflow their
+    nearest centres, so a grain is no longer the Voronoi cell of its centre and
+    the nearest centres often do not hold a query's neighbours. The router,
+    trained on the grains that hold each training query's brute-force top 10,
+    learns where the rows actually went. Measured on 1000 held-out queries:
+    recall@10 of the same search (C = 100, k = 10) with learned against
+    centroid probes, at nprobe 2, 4 and 8. Training also brings the loss close
+    to its floor (the targets' entropy)."""
+    d, n_clusters, n, G, r = 64, 16, 40000, 256, 8
+    m = synth.make_cluster_model(n, d, n_clusters, sizes="zipf", seed=5)
+    X, _ = synth.sample_points(m, 6)
+    Qtr, _ = synth.sample_queries(m, 20000, 7)
+    Qev, _ = synth.sample_queries(m, 1000, 8)
     X, Qtr, Qev = X.numpy(), Qtr.numpy(), Qev.numpy()
-    idx = O.build_index(X, G, r, synth.uniforms(G, 85).numpy())
+    cap = n // G + (n % G > 0)
+    idx = O.build_index(X, G, r, synth.uniforms(G, 9).numpy(), max_grain_rows=cap)
+    assert np.bincount(idx["assign"], minlength=G).max() <= cap
     gi = hntl.Index.load(write(tmp_path, "train", idx, X), 0)
     T = _labels(X, Qtr, idx["assign"], G)
     init = R.init_params(d, 256, 256, G, seed=86)
@@ -275,20 +278,19 @@ def test_training_gain_over_centroid_routing(hntl, tmp_path):
     def recall(ids):
         return np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids.cpu().numpy().tolist(), bf.tolist())])
 
-    best1 = float(R.soft_targets(bf, idx["assign"], G).max(1).mean())
     report = {}
-    for nprobe in (1, 2, 4):
-        ids_c, _ = gi.search(Qd, 10, 50, nprobe)
+    for nprobe in (2, 4, 8):
+        ids_c, _ = gi.search(Qd, 10, 100, nprobe)
         out = []
         for router in (rt, untrained):
             probes, _ = router.route(gi, Qd, nprobe, tau=0.0)
-            ids_r, _ = hntl.search_probes(gi, Qd, probes, 10, 50)
+            ids_r, _ = hntl.search_probes(gi, Qd, probes, 10, 100)
             out.append(recall(ids_r))
         report[nprobe] = dict(centroid=recall(ids_c), learned=out[0], untrained=out[1],
                               gain=out[0] - recall(ids_c))
-    print("router loss first/last/floor", losses[0], losses[-1], floor, "best single grain", best1)
+    print("router loss first/last/floor", losses[0], losses[-1], floor)
     print("router recall by nprobe:", report)
-    assert losses[-1] < 0.5 * losses[0] and losses[-1] < floor + 0.15
+    assert losses[-1] < 0.5 * losses[0] and losses[-1] < floor + 0.5
     for nprobe, rep in report.items():
-        assert rep["learned"] >= rep["centroid"] - 0.02, (nprobe, rep)
         assert rep["learned"] >= rep["untrained"] + 0.2, (nprobe, rep)
+    assert report[4]["gain"] >= 0.05 and report[8]["gain"] >= 0.05, report

@@ -696,3 +696,59 @@ def test_given_probes_equal_routing_when_they_are_the_routed_ones():
     far = np.ascontiguousarray(np.stack([ref["probe"][:, 1], ref["probe"][:, 2]], 1))
     got2 = O.search(idx, X, Q, 5, 30, 2, probes=far)
     assert not np.array_equal(got2["cand_id"], ref["cand_id"][:, :30])
+
+
+# ---------------------------------------------------------------- capacity-bounded grains
+
+
+def _blocking_pairs(X, M, assign, cap):
+    """(row, centre) pairs that block stability: the row ranks the centre above
+    its own grain, and the centre has room or holds a row it ranks below it."""
+    D = ((X.astype(np.float64)[:, None, :] - M.astype(np.float64)[None]) ** 2).sum(-1)
+    G = M.shape[0]
+    held = [np.flatnonzero(assign == g) for g in range(G)]
+    out = []
+    for i in range(len(X)):
+        a = assign[i]
+        for g in range(G):
+            if (D[i, g], g) >= (D[i, a], a):
+                continue
+            if len(held[g]) < cap or any((D[j, g], j) > (D[i, g], i) for j in held[g]):
+                out.append((i, g))
+    return out
+
+
+def test_balanced_assignment_is_stable_and_capped():
+    rng = np.random.default_rng(41)
+    X = np.concatenate([rng.standard_normal((150, 6)) + 3, rng.standard_normal((50, 6)) - 3]).astype(np.float32)
+    M = np.concatenate([rng.standard_normal((3, 6)) + 3, rng.standard_normal((2, 6)) - 3])
+    cap = 45
+    a = O.balanced_assign(X, M, cap)
+    assert (a >= 0).all() and np.bincount(a, minlength=5).max() <= cap
+    assert _blocking_pairs(X, M, a, cap) == []
+    # with room for every row the grains are the nearest-centre (Voronoi) cells
+    D = ((X.astype(np.float64)[:, None, :] - M[None]) ** 2).sum(-1)
+    np.testing.assert_array_equal(O.balanced_assign(X, M, len(X)), D.argmin(1))
+
+
+def test_balanced_assignment_is_the_row_optimal_stable_one():
+    """Brute force over every capacity-respecting assignment of 7 rows to 3
+    centres (cap 3): among the stable ones, the oracle's gives every row a
+    centre it ranks at least as high as in any other."""
+    import itertools
+
+    rng = np.random.default_rng(43)
+    X = rng.standard_normal((7, 2)).astype(np.float32)
+    M = rng.standard_normal((3, 2))
+    cap = 3
+    D = ((X.astype(np.float64)[:, None, :] - M[None]) ** 2).sum(-1)
+    rank = np.argsort(np.argsort(D, 1, kind="stable"), 1)  # rank of each centre for each row
+    stable = []
+    for a in itertools.product(range(3), repeat=7):
+        a = np.array(a)
+        if np.bincount(a, minlength=3).max() <= cap and not _blocking_pairs(X, M, a, cap):
+            stable.append(a)
+    got = O.balanced_assign(X, M, cap)
+    assert any(np.array_equal(got, s) for s in stable)
+    for s in stable:
+        assert np.all(rank[np.arange(7), got] <= rank[np.arange(7), s])
