@@ -123,6 +123,88 @@ __global__ void k_unpack(const unsigned long long* __restrict__ packed, int64_t 
   if (prev && prev[i] != g) atomicAdd(changed, 1u);
 }
 
+// The K nearest centres of each of n rows (row i = X[rows[i]], or X[i] when
+// rows is null) as ascending (distance bits << 32 | grain) keys: one CTA per
+// 64-row block walks every 64-centre tile with k_nearest's arithmetic (so a
+// distance is bitwise the one k_nearest forms), writes the tile's distances to
+// shared memory, and the row's owner thread merges them into the row's sorted
+// list (most values fail the list's current K-th key and are skipped).
+template <int K>
+__global__ void __launch_bounds__(256) k_nearest_topk(const float* __restrict__ X, const uint64_t* __restrict__ rows,
+                                                      int64_t n, const float* __restrict__ M, int G, int d,
+                                                      unsigned long long* __restrict__ out) {
+  __shared__ __align__(16) float sX[kNK][kNT + 4];
+  __shared__ __align__(16) float sM[kNK][kNT + 4];
+  __shared__ float sD[kNT][kNT + 1];
+  __shared__ unsigned long long sTop[kNT][K];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t q0 = (int64_t)blockIdx.x * kNT;
+  for (int e = threadIdx.x; e < kNT * K; e += 256) sTop[e / K][e % K] = ~0ull;
+  for (int g0 = 0; g0 < G; g0 += kNT) {
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < d; k0 += kNK) {
+#pragma unroll
+      for (int i = 0; i < (kNT * kNK) / 256; ++i) {
+        const int e = threadIdx.x + 256 * i;
+        const int row = e / kNK, col = e % kNK;
+        const int64_t q = q0 + row;
+        const int g = g0 + row, t = k0 + col;
+        float xv = 0.f;
+        if (q < n && t < d) xv = X[(rows ? (int64_t)rows[q] : q) * d + t];
+        sX[col][row] = xv;
+        sM[col][row] = (g < G && t < d) ? M[(size_t)g * d + t] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < kNK; ++kk) {
+        const float4 a = *reinterpret_cast<const float4*>(&sX[kk][ty * 4]);
+        const float4 b = *reinterpret_cast<const float4*>(&sM[kk][tx * 4]);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float t = av[i] - bv[j];
+            acc[i][j] = fmaf(t, t, acc[i][j]);
+          }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sD[ty * 4 + i][tx * 4 + j] = acc[i][j];
+    __syncthreads();
+    if (threadIdx.x < kNT && q0 + threadIdx.x < n) {
+      unsigned long long* top = sTop[threadIdx.x];
+      unsigned long long worst = top[K - 1];
+      const int lim = min(kNT, G - g0);
+      for (int c = 0; c < lim; ++c) {
+        float v = sD[threadIdx.x][c];
+        if (!(v == v)) v = INFINITY;
+        const unsigned long long key = ((unsigned long long)__float_as_uint(v) << 32) | (uint32_t)(g0 + c);
+        if (key >= worst) continue;
+        int p = K - 1;  // insert, keeping the list sorted
+        while (p > 0 && top[p - 1] > key) {
+          top[p] = top[p - 1];
+          --p;
+        }
+        top[p] = key;
+        worst = top[K - 1];
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < kNT * K; e += 256) {
+    const int64_t q = q0 + e / K;
+    if (q < n) out[q * K + e % K] = sTop[e / K][e % K];
+  }
+}
+
 // One warp per row of a distance tile [n][G]: its K smallest (distance, grain)
 // keys in ascending order (K rounds of a warp minimum above the last pick).
 __global__ void k_topk_rows(const float* __restrict__ tile, int64_t n, int G, int K,
@@ -569,91 +651,141 @@ int nearest(const float* X, int64_t n, const float* M, int G, int d, unsigned lo
 // the centres in order of (distance, grain); a centre keeps the `cap` rows it
 // ranks best by (distance, row) and refuses the rest. The row-proposing stable
 // assignment does not depend on the order of the proposals, so the host runs
-// the classic sequential loop over lists the GPU prepares: each row's kTopK
-// nearest centres (FP32 distances summed over t = 0 .. d-1 by fmaf, as the
-// nearest-centre pass forms them). A row refused by all of them gets its full
-// ranking computed on the host with the same arithmetic. cap * G >= N.
+// the classic loop over ranked lists the GPU prepares (FP32 distances summed
+// over t = 0 .. d-1 by fmaf, as the nearest-centre pass forms them): first
+// every row's 8 nearest centres; rows refused by all of those wait until the
+// proposals stop, then get their 64, 512 and finally all G nearest centres
+// in batches and go on proposing from where they stopped. cap * G >= N.
 constexpr int kTopK = 8;
+
+// Ranked lists of `m` rows (row ids `rows`, or rows s .. s+m-1 of dX when
+// rows is null): the K nearest (distance bits << 32 | grain) keys of each.
+int ranked_lists(const float* dX, uint32_t d, uint32_t G, const float* M, const uint32_t* h_rows, int64_t s,
+                 int64_t m, int K, unsigned long long* h_out, Tmp& T, float* tile, int64_t R, float* gath,
+                 uint64_t* d_rows, unsigned long long* d_top, cudaStream_t st) {
+  if (K == kTopK) {  // fused distances and selection, no distance tile (every row's first list)
+    for (int64_t c0 = 0; c0 < m; c0 += R) {
+      const int64_t mc = std::min<int64_t>(R, m - c0);
+      const uint64_t* rows = nullptr;
+      if (h_rows) {
+        std::vector<uint64_t> rr(mc);
+        for (int64_t i = 0; i < mc; ++i) rr[i] = h_rows[c0 + i];
+        HNTL_CUDA_TRY(cudaMemcpyAsync(d_rows, rr.data(), mc * 8, cudaMemcpyHostToDevice, st));
+        HNTL_CUDA_TRY(cudaStreamSynchronize(st));
+        rows = d_rows;
+      }
+      const float* src = h_rows ? dX : dX + (size_t)(s + c0) * d;
+      const unsigned blocks = (unsigned)((mc + kNT - 1) / kNT);
+      k_nearest_topk<kTopK><<<blocks, 256, 0, st>>>(src, rows, mc, M, (int)G, (int)d, d_top);
+      HNTL_CUDA_TRY(cudaGetLastError());
+      HNTL_CUDA_TRY(cudaMemcpyAsync(h_out + (size_t)c0 * K, d_top, (size_t)mc * K * 8, cudaMemcpyDeviceToHost, st));
+      HNTL_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return HNTL_OK;
+  }
+  for (int64_t c0 = 0; c0 < m; c0 += R) {
+    const int64_t mc = std::min<int64_t>(R, m - c0);
+    const float* src = dX + (size_t)(s + c0) * d;
+    if (h_rows) {
+      std::vector<uint64_t> rr(mc);
+      for (int64_t i = 0; i < mc; ++i) rr[i] = h_rows[c0 + i];
+      HNTL_CUDA_TRY(cudaMemcpyAsync(d_rows, rr.data(), mc * 8, cudaMemcpyHostToDevice, st));
+      k_gather_rows<<<(unsigned)mc, 256, 0, st>>>(dX, d_rows, mc, (int)d, gath);
+      src = gath;
+    }
+    for (int64_t s2 = 0; s2 < mc; s2 += (int64_t)kNT * 65535) {
+      const int64_t m2 = std::min<int64_t>((int64_t)kNT * 65535, mc - s2);
+      dim3 grid((G + kNT - 1) / kNT, (unsigned)((m2 + kNT - 1) / kNT));
+      k_nearest<true><<<grid, 256, 0, st>>>(src + s2 * d, m2, M, (int)G, (int)d, nullptr, tile + s2 * G);
+    }
+    k_topk_rows<<<(unsigned)((mc * 32 + 255) / 256), 256, 0, st>>>(tile, mc, (int)G, K, d_top);
+    HNTL_CUDA_TRY(cudaGetLastError());
+    HNTL_CUDA_TRY(cudaMemcpyAsync(h_out + (size_t)c0 * K, d_top, (size_t)mc * K * 8, cudaMemcpyDeviceToHost, st));
+    HNTL_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  (void)T;
+  return HNTL_OK;
+}
 
 int balanced_assign(const float* dX, uint64_t N, uint32_t d, uint32_t G, const float* M, uint32_t cap,
                     int32_t* assign_dev, Tmp& T, cudaStream_t st) {
   int rc = HNTL_OK;
-  const int64_t chunk = std::max<int64_t>(kNT, ((int64_t)1 << 28) / (int64_t)G / kNT * kNT);
-  const int64_t R = std::min<int64_t>((int64_t)N, chunk);
+  // row chunks whose G distances fit a 1 GiB tile; a chunk's lists are at most R * G keys
+  const int64_t R = std::min<int64_t>((int64_t)N, std::max<int64_t>(kNT, ((int64_t)1 << 28) / (int64_t)G / kNT * kNT));
   float* tile = T.get<float>((size_t)R * G, &rc);
-  unsigned long long* topk = T.get<unsigned long long>((size_t)N * kTopK, &rc);
+  float* gath = T.get<float>((size_t)R * d, &rc);
+  uint64_t* d_rows = T.get<uint64_t>((size_t)R, &rc);
+  const int K0 = (int)std::min<uint32_t>(kTopK, G);
+  unsigned long long* d_top = T.get<unsigned long long>((size_t)R * G, &rc);
   if (rc) return rc;
-  const int K = (int)std::min<uint32_t>(kTopK, G);
-  for (int64_t s = 0; s < (int64_t)N; s += R) {
-    const int64_t m = std::min<int64_t>(R, (int64_t)N - s);
-    for (int64_t s2 = 0; s2 < m; s2 += (int64_t)kNT * 65535) {
-      const int64_t m2 = std::min<int64_t>((int64_t)kNT * 65535, m - s2);
-      dim3 grid((G + kNT - 1) / kNT, (unsigned)((m2 + kNT - 1) / kNT));
-      k_nearest<true><<<grid, 256, 0, st>>>(dX + (s + s2) * d, m2, M, (int)G, (int)d, nullptr, tile + s2 * G);
-    }
-    k_topk_rows<<<(unsigned)((m * 32 + 255) / 256), 256, 0, st>>>(tile, m, (int)G, K, topk + (size_t)s * kTopK);
-    HNTL_CUDA_TRY(cudaGetLastError());
-  }
-  std::vector<unsigned long long> h_top((size_t)N * kTopK);
-  std::vector<float> h_M((size_t)G * d);
-  HNTL_CUDA_TRY(cudaMemcpyAsync(h_top.data(), topk, h_top.size() * 8, cudaMemcpyDeviceToHost, st));
-  HNTL_CUDA_TRY(cudaMemcpyAsync(h_M.data(), M, h_M.size() * 4, cudaMemcpyDeviceToHost, st));
-  HNTL_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<unsigned long long> h_top((size_t)N * K0);
+  if ((rc = ranked_lists(dX, d, G, M, nullptr, 0, (int64_t)N, K0, h_top.data(), T, tile, R, gath, d_rows, d_top,
+                         st)))
+    return rc;
+  // longer lists of the rows that ran out: list index per row (0 = the first K0)
+  std::vector<int32_t> lst(N, -1);
+  std::vector<std::vector<unsigned long long>> ext;
+  std::vector<int> ext_k;
   // held rows of each centre: a max-heap on (distance bits, row), worst on top
   using Held = std::pair<uint32_t, uint32_t>;
   std::vector<std::vector<Held>> heap(G);
   std::vector<uint32_t> next(N, 0);
   std::vector<int32_t> assign(N, -1);
-  std::unordered_map<uint32_t, std::vector<unsigned long long>> longer;  // full rankings of exhausted rows
-  std::vector<float> xrow(d);
-  std::vector<uint32_t> stack(N);
+  std::vector<uint32_t> stack(N), waiting;
   for (uint64_t i = 0; i < N; ++i) stack[i] = (uint32_t)(N - 1 - i);
-  while (!stack.empty()) {
-    const uint32_t i = stack.back();
-    stack.pop_back();
-    unsigned long long key;
-    if (next[i] < (uint32_t)K) {
-      key = h_top[(size_t)i * kTopK + next[i]];
-    } else {
-      auto it = longer.find(i);
-      if (it == longer.end()) {  // every centre, with the GPU's arithmetic
-        HNTL_CUDA_TRY(cudaMemcpy(xrow.data(), dX + (size_t)i * d, (size_t)d * 4, cudaMemcpyDeviceToHost));
-        std::vector<unsigned long long> all(G);
-        for (uint32_t g = 0; g < G; ++g) {
-          float acc = 0.f;
-          for (uint32_t t = 0; t < d; ++t) {
-            const float df = xrow[t] - h_M[(size_t)g * d + t];
-            acc = std::fma(df, df, acc);
-          }
-          uint32_t bits;
-          std::memcpy(&bits, &acc, 4);
-          all[g] = ((unsigned long long)bits << 32) | g;
-        }
-        std::sort(all.begin(), all.end());
-        it = longer.emplace(i, std::move(all)).first;
+  for (;;) {
+    while (!stack.empty()) {
+      const uint32_t i = stack.back();
+      stack.pop_back();
+      const int k = lst[i] < 0 ? K0 : ext_k[lst[i]];
+      if (next[i] >= (uint32_t)k) {  // refused by every listed centre: wait for a longer list
+        if (k >= (int)G) return fail(HNTL_ECUDA, "balanced assignment: a row was refused by every centre");
+        waiting.push_back(i);
+        continue;
       }
-      if (next[i] >= G) return fail(HNTL_ECUDA, "balanced assignment: a row was refused by every centre");
-      key = it->second[next[i]];
+      const unsigned long long key =
+          lst[i] < 0 ? h_top[(size_t)i * K0 + next[i]] : ext[lst[i]][(size_t)0 + next[i]];
+      ++next[i];
+      const uint32_t g = (uint32_t)(key & 0xFFFFFFFFu);
+      const Held me{(uint32_t)(key >> 32), i};
+      auto& h = heap[g];
+      if (h.size() < cap) {
+        h.push_back(me);
+        std::push_heap(h.begin(), h.end());
+        assign[i] = (int32_t)g;
+      } else if (me < h.front()) {
+        std::pop_heap(h.begin(), h.end());
+        const uint32_t out = h.back().second;
+        h.back() = me;
+        std::push_heap(h.begin(), h.end());
+        assign[i] = (int32_t)g;
+        assign[out] = -1;
+        stack.push_back(out);
+      } else {
+        stack.push_back(i);
+      }
     }
-    ++next[i];
-    const uint32_t g = (uint32_t)(key & 0xFFFFFFFFu);
-    const Held me{(uint32_t)(key >> 32), i};
-    auto& h = heap[g];
-    if (h.size() < cap) {
-      h.push_back(me);
-      std::push_heap(h.begin(), h.end());
-      assign[i] = (int32_t)g;
-    } else if (me < h.front()) {
-      std::pop_heap(h.begin(), h.end());
-      const uint32_t out = h.back().second;
-      h.back() = me;
-      std::push_heap(h.begin(), h.end());
-      assign[i] = (int32_t)g;
-      assign[out] = -1;
-      stack.push_back(out);
-    } else {
-      stack.push_back(i);
+    if (waiting.empty()) break;
+    // the waiting rows' next lists, in one batch: 64, 512, then every centre
+    const int cur = lst[waiting[0]] < 0 ? K0 : ext_k[lst[waiting[0]]];
+    int K = cur < 64 ? 64 : (cur < 512 ? 512 : (int)G);
+    K = std::min<int>(K, (int)G);
+    for (uint32_t i : waiting) {  // rows of different list lengths: the longest one decides
+      const int ki = lst[i] < 0 ? K0 : ext_k[lst[i]];
+      if (ki >= K) K = std::min<int>((int)G, ki < 512 ? 512 : (int)G);
     }
+    std::vector<unsigned long long> h_ext(waiting.size() * (size_t)K);
+    const int64_t Rk = std::max<int64_t>(1, std::min<int64_t>(R, ((int64_t)R * G) / K));
+    if ((rc = ranked_lists(dX, d, G, M, waiting.data(), 0, (int64_t)waiting.size(), K, h_ext.data(), T, tile,
+                           std::min<int64_t>(R, Rk), gath, d_rows, d_top, st)))
+      return rc;
+    for (size_t w = 0; w < waiting.size(); ++w) {
+      ext.emplace_back(h_ext.begin() + w * K, h_ext.begin() + (w + 1) * K);
+      ext_k.push_back(K);
+      lst[waiting[w]] = (int32_t)(ext.size() - 1);
+      stack.push_back(waiting[w]);
+    }
+    waiting.clear();
   }
   HNTL_CUDA_TRY(cudaMemcpyAsync(assign_dev, assign.data(), N * 4, cudaMemcpyHostToDevice, st));
   HNTL_CUDA_TRY(cudaStreamSynchronize(st));

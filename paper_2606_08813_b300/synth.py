@@ -174,8 +174,10 @@ WORKLOADS = {
                           batch=4_096, nprobe=32, C=200, k=10, seed=1003, precision="bf16-fp8"),
     "precision-2.5m": dict(n=2_500_000, d=768, n_clusters=1_024, sizes="equal", G=1_024, r=32, nq=10_240,
                            batch=1_024, nprobe=32, C=200, k=10, seed=1005, precision="bf16-fp8"),
-    "router-5m": dict(n=5_000_000, d=768, n_clusters=4_096, sizes="equal", G=4_096, r=32, nq=20_000,
-                      nprobe=16, C=200, k=10, seed=1004),
+    # about four grains per cluster, capacity-bounded at 1.05 N / G rows: grains are no longer the
+    # Voronoi cells of their centres, which is where a learned router has something to learn
+    "router-5m": dict(n=5_000_000, d=768, n_clusters=1_024, sizes="equal", G=4_096, r=32, nq=20_000,
+                      nprobe=16, C=200, k=10, seed=1004, max_grain_rows=1_282),
 }
 
 
