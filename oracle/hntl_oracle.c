@@ -406,7 +406,7 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
                int64_t* out_id, double* out_d, int64_t mode, const int64_t* pos_of_id,
                const int32_t* grain_of_pos, const double* qdelta, const double* qdres,
                const int32_t* probe_in, const int16_t* Zc, int64_t i16_flags, const int16_t* qc_in,
-               const int32_t* qr_in) {
+               const int32_t* qr_in, const float* pz_in, const float* prho_in) {
 #pragma omp parallel
   {
     pair_t* route = (pair_t*)malloc(sizeof(pair_t) * (size_t)G);
@@ -459,6 +459,12 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
           for (int64_t t = 0; t < d; ++t) e[t] -= zq[j] * (double)Ug[j * d + t];
         double rho_q = 0.0;
         for (int64_t t = 0; t < d; ++t) rho_q += e[t] * e[t];
+        if (pz_in) {
+          /* the projection step taken elsewhere (pz_in [nq][nprobe][r], prho_in
+           * [nq][nprobe]): the scan, pool and rerank run on those values */
+          for (int64_t j = 0; j < r; ++j) zq[j] = (double)pz_in[(qi * nprobe + p) * r + j];
+          rho_q = (double)prho_in[qi * nprobe + p];
+        }
         float dl = 0.f, rq16 = 0.f;
         if (qdelta) {
           /* 16-bit form (Eq. 5): the query's coordinates and residual norm are

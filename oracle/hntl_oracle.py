@@ -75,7 +75,7 @@ def _c():
             lib.or_lloyd.restype = I
             lib.or_balanced_assign.argtypes = [P, I, I, P, I, I, P]
             lib.or_search.argtypes = [P, P, I, I, I, P, P, P, P, P, P, P, P, I, I, I, I, P,
-                                      P, P, P, P, P, P, I, P, P, P, P, P, P, I, P, P]
+                                      P, P, P, P, P, P, I, P, P, P, P, P, P, I, P, P, P, P]
             lib.or_threads.restype = ctypes.c_int
             lib.or_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -236,11 +236,15 @@ def build_index(X, G: int, r: int, u, train_idx=None, max_iter: int = 25, keep_f
 
 
 def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=None, rho=None, precision="fp32",
-           mode: str = "B", probes=None, resid_prune: bool = False, query_codes=None):
+           mode: str = "B", probes=None, resid_prune: bool = False, query_codes=None, pair_proj=None):
     """Mode B (default) or Mode A search of every query (see hntl_oracle.c or_search).
 
     probes (optional, [nq, nprobe] grain ids): replaces the centroid routing
     of step 1 (a learned router's probes); the rest of the path is unchanged.
+    pair_proj (optional, (z [nq, nprobe, r], rho [nq, nprobe]) with probes):
+    replaces the projection step (Eq. 1-4) by given values, so that the scan,
+    pool and rerank can be compared on the same inputs as another
+    implementation's.
 
     mode="B": the pool is reranked by exact L2 to the raw rows (sec. 2.1 step 4).
     mode="A": the pool is reranked by L2 to each row's reconstruction
@@ -322,6 +326,14 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
         pos_of_id = np.zeros(len(ids), dtype=np.int64)
         pos_of_id[ids] = np.arange(len(ids), dtype=np.int64)
         grain_of_pos = np.repeat(np.arange(G, dtype=np.int32), np.diff(off)).astype(np.int32)
+    pz = prho = None
+    if pair_proj is not None:
+        if probes is None:
+            raise ValueError("pair_proj needs the probes it belongs to")
+        pz = np.ascontiguousarray(pair_proj[0], dtype=np.float32)
+        prho = np.ascontiguousarray(pair_proj[1], dtype=np.float32)
+        if pz.shape != (nq, nprobe, r) or prho.shape != (nq, nprobe):
+            raise ValueError("pair_proj must be ([nq, nprobe, r], [nq, nprobe])")
     pin = None
     if probes is not None:
         pin = np.ascontiguousarray(probes, dtype=np.int32)
@@ -330,7 +342,7 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
     _c().or_search(_p(M), _p(U), G, d, r, _p(off), _p(ids), _p(Zs), _p(rhos), _p(X), _p(attr_a), _p(Q), _p(Qp), nq,
                    k, C, nprobe, _p(rng), _p(probe), _p(probe_d), _p(cand_id), _p(cand_d), _p(out_id), _p(out_d),
                    1 if mode == "A" else 0, _p(pos_of_id), _p(grain_of_pos), _p(qdelta), _p(qdres), _p(pin),
-                   _p(Zc), 1 if resid_prune else 0, _p(qc_in), _p(qr_in))
+                   _p(Zc), 1 if resid_prune else 0, _p(qc_in), _p(qr_in), _p(pz), _p(prho))
     return dict(probe=probe, probe_d=probe_d, cand_id=cand_id, cand_d=cand_d, out_id=out_id, out_d=out_d)
 
 

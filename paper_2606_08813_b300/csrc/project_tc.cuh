@@ -363,6 +363,287 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
   if (tid == 0 && s_fail) atomicOr(err, tc::kErrTimeout);
 }
 
+// ------------------------------------------------------------------ explicit residual
+
+// rho_q = ||v' - U_b^T z||^2 of every pair (Eq. 3-4 in the precision form,
+// v' = q_b - mu_b), from the z the projection wrote. The Gram identity above
+// is exact for the exact z but amplifies the FP32 error dz of the computed z
+// into rho by -2 z . dz, which for a query near a grain's subspace but far
+// from its centre (|z|^2 >> rho) exceeds 1e-5 of the distance; the explicit
+// residual moves only by 2 (z - G z) . dz + |U^T dz|^2 (G = U_b U_b^T is the
+// identity to BF16 precision), so this pass recomputes it.
+// Work items are the projection's: 4 slots of up to 32 pairs. The
+// reconstruction U_b^T z of all 128 pairs against a 128-coordinate chunk is
+// one MMA sequence: A = z split into three BF16 parts (hi, mid, lo, 24
+// significant bits), block-diagonal over the slots (row i of slot s holds its
+// z in K columns s RN .. s RN + RN - 1, zeros elsewhere); B = the slots'
+// basis rows for those 128 coordinates, TMA boxes of 64 coordinates x r
+// rows read MN-major (K = basis row, N = coordinate). TMEM lane i, column t
+// then holds (U^T z)_t of pair i; the epilogue adds (q_b - mu_b - that)^2.
+//   warp 0     TMA producer: per chunk, 2 boxes per slot into a stage ring.
+//   warp 1     one thread issues the MMAs into one of two TMEM accumulators.
+//   warps 2-9  epilogue: warp w reads lane quarter w % 4 (32 pairs), columns
+//              64 (w - 2) / 4 .. + 63 of each chunk; it also writes the A
+//              operand of each item before the item's MMAs.
+constexpr int kRThr = 320;
+constexpr int kRStg = 3;
+constexpr int kRChunk = 128;  // coordinates per MMA (N)
+
+template <int RN>
+struct ResidTc {
+  static constexpr int kK = kPSlots * RN;                       // A's K: the 4 slots' basis rows
+  static constexpr uint32_t kBytesApart = kPTM * kK * 2;         // one part of A (128 rows x kK BF16)
+  static constexpr uint32_t kBytesSlot = 2 * RN * 128;           // one slot's 2 boxes of a chunk
+  static constexpr uint32_t kStage = kPSlots * kBytesSlot;
+  static constexpr int kSmem = 3 * kBytesApart + kRStg * kStage + 1024;
+};
+
+__device__ __forceinline__ uint16_t bf16_rn(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+
+template <int RN>
+__global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
+    const uint16_t* __restrict__ Qh, const uint16_t* __restrict__ Mh, const __grid_constant__ CUtensorMap mapU,
+    int d, int r, const uint4* __restrict__ slots, const uint32_t* __restrict__ n_slots,
+    const uint32_t* __restrict__ pair_q, const float* __restrict__ zq, float* __restrict__ rhoq,
+    int* __restrict__ err) {
+  using P = ResidTc<RN>;
+  static_assert(P::kK % 64 == 0 || P::kK == 64, "A rows are whole 128-byte swizzle atoms");
+  constexpr int kAtomsK = P::kK / 64;  // 128-byte K atoms per A row
+  constexpr uint32_t kIdesc = tc::idesc_f32acc_bmn(1u, kPTM, kRChunk);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;                            // [3 parts][kAtomsK][128 rows x 128 B]
+  uint8_t* sB = smem + 3 * P::kBytesApart;       // [stage][slot][2 boxes][RN rows x 128 B]
+  __shared__ __align__(8) uint64_t full[kRStg], empty[kRStg], accf[2], acce[2], afull, fin;
+  __shared__ uint4 sslot[kPSlots];
+  __shared__ float sred[kPTM];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  __shared__ uint32_t s_it_prod, s_it_mma;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 1) tc::tmem_alloc(&tmem_base, 2 * kRChunk);
+  if (tid == 0) {
+    for (int s = 0; s < kRStg; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(&accf[a], 1);
+      tc::mbar_init(&acce[a], 8);
+    }
+    tc::mbar_init(&afull, 1);
+    tc::mbar_init(&fin, 1);
+    s_fail = 0;
+    s_it_prod = s_it_mma = 0;
+    tc::mbar_fence_init();
+  }
+  // The whole basis ring starts at zero: rows r .. RN - 1 of every box stay
+  // zero (TMA writes r rows), and a slot without pairs multiplies its (stale
+  // or never written) tile by the zeros of A, which must therefore be finite.
+  for (uint32_t e = tid; e < (uint32_t)(kRStg * P::kStage / 16); e += kRThr)
+    *reinterpret_cast<uint4*>(sB + (size_t)e * 16) = make_uint4(0, 0, 0, 0);
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t ns = *n_slots;
+  const uint32_t total = (ns + kPSlots - 1) / kPSlots;
+  const int nch = (d + kRChunk - 1) / kRChunk;
+  auto slot_of = [&](uint32_t w, int j) -> uint4 {
+    const uint32_t s = w * kPSlots + j;
+    return s < ns ? slots[s] : make_uint4(0, 0, 0, 0);
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (uint32_t w = blockIdx.x; w < total && ok; w += gridDim.x) {
+        uint4 sl[kPSlots];
+        uint32_t bytes = 0;
+#pragma unroll
+        for (int j = 0; j < kPSlots; ++j) {
+          sl[j] = slot_of(w, j);
+          bytes += sl[j].z ? 2u * (uint32_t)r * 128u : 0u;
+        }
+        for (int c = 0; c < nch; ++c, ++it) {
+          const int s = (int)(it % kRStg);
+          if (it >= (uint32_t)kRStg && !tc::mbar_wait(&empty[s], ((it / kRStg) - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = sB + s * P::kStage;
+          tc::mbar_expect_tx(&full[s], bytes);
+#pragma unroll
+          for (int j = 0; j < kPSlots; ++j)
+            if (sl[j].z) {
+              tc::tma_load_2d(&mapU, &full[s], st + j * P::kBytesSlot, c * kRChunk, (int)sl[j].x * r);
+              tc::tma_load_2d(&mapU, &full[s], st + j * P::kBytesSlot + RN * 128, c * kRChunk + 64,
+                              (int)sl[j].x * r);
+            }
+        }
+      }
+      s_it_prod = it;
+      if (!ok) atomicExch(&s_fail, 1);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      bool ok = true;
+      uint32_t it = 0, li = 0, ci = 0;  // stage uses, items, accumulator uses
+      for (uint32_t w = blockIdx.x; w < total && ok; w += gridDim.x, ++li) {
+        if (!tc::mbar_wait(&afull, li & 1)) {  // this item's A operand is written
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        for (int c = 0; c < nch; ++c, ++it, ++ci) {
+          const int s = (int)(it % kRStg), a = (int)(ci & 1);
+          if (ci >= 2 && !tc::mbar_wait(&acce[a], ((ci >> 1) - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          if (!tc::mbar_wait(&full[s], (it / kRStg) & 1)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t acc = tmem + (uint32_t)(a * kRChunk);
+          const uint32_t bst = tc::smem_u32(sB + s * P::kStage);
+          bool first = true;
+#pragma unroll
+          for (int part = 0; part < 3; ++part) {
+            const uint32_t ab = tc::smem_u32(sA + part * P::kBytesApart);
+#pragma unroll
+            for (int ks = 0; ks < P::kK / 16; ++ks) {
+              const int slot = ks / (RN / 16), kin = ks % (RN / 16);
+              const uint64_t da = tc::desc_sw128(ab + (ks / 4) * (kPTM * 128) + (ks % 4) * 32);
+              const uint64_t db = tc::desc_sw128_mn(bst + slot * P::kBytesSlot + kin * 16 * 128, RN * 128);
+              tc::mma<true>(acc, da, db, kIdesc, first ? 0u : 1u);
+              first = false;
+            }
+          }
+          tc::mma_commit(&empty[s]);
+          tc::mma_commit(&accf[a]);
+        }
+      }
+      if (!ok) atomicExch(&s_fail, 1);
+      s_it_mma = it;
+      if (it > 0) {
+        tc::mma_commit(&fin);
+        if (!tc::mbar_wait(&fin, 0)) atomicExch(&s_fail, 1);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ A operand and epilogue
+    const int et = tid - 64;                // 0 .. 255
+    const int q4 = warp & 3;                // TMEM lane quarter = slot
+    const int half = (warp - 2) >> 2;       // 0: columns 0..63 of a chunk, 1: 64..127
+    const int row = q4 * 32 + lane;         // A row = TMEM lane = pair of the item
+    bool failed = false;
+    uint32_t li = 0, ci = 0;
+    for (uint32_t w = blockIdx.x; w < total; w += gridDim.x, ++li) {
+      if (et < kPSlots) sslot[et] = slot_of(w, et);
+      tc::named_bar(1, 256);
+      // A: 3 parts x 128 rows x kK, row i of slot s holding its z at K = s RN ..; zeros elsewhere
+      for (int e = et; e < 3 * kPTM; e += 256) {
+        const int part = e / kPTM, ra = e % kPTM, sa = ra / 32, ia = ra % 32;
+        const uint4 sl = sslot[sa];
+        const bool have = (uint32_t)ia < sl.z;
+        const float* z = zq + (size_t)(sl.y + ia) * r;
+        uint8_t* abase = sA + part * P::kBytesApart;
+#pragma unroll 1
+        for (int kc = 0; kc < P::kK / 8; ++kc) {  // 16-byte chunks of 8 K values
+          const int k0 = kc * 8;
+          uint32_t wv[4] = {0, 0, 0, 0};
+          if (have && k0 >= sa * RN && k0 < sa * RN + RN) {
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              uint32_t two = 0;
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int j = k0 - sa * RN + 2 * h + u;
+                const float v = j < r ? z[j] : 0.f;
+                const float hi = __bfloat162float(__float2bfloat16_rn(v));
+                const float mid = __bfloat162float(__float2bfloat16_rn(v - hi));
+                const float lo = v - hi - mid;
+                const float pv = part == 0 ? hi : (part == 1 ? mid : lo);
+                two |= (uint32_t)bf16_rn(pv) << (16 * u);
+              }
+              wv[h] = two;
+            }
+          }
+          *reinterpret_cast<uint4*>(abase + (kc / 8) * (kPTM * 128) + sw128_off(ra, (kc % 8) * 16)) =
+              make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
+      }
+      tc::fence_proxy_async_smem();
+      tc::named_bar(1, 256);
+      if (et == 0) tc::mbar_arrive(&afull);
+      const uint4 sl = sslot[q4];
+      const bool mine = (uint32_t)lane < sl.z;
+      const uint16_t* qrow = mine ? Qh + (size_t)pair_q[sl.y + lane] * d : Qh;
+      const uint16_t* mrow = Mh + (size_t)sl.x * d;
+      float acc = 0.f;
+      for (int c = 0; c < nch; ++c, ++ci) {
+        const int a = (int)(ci & 1);
+        if (!failed && __any_sync(0xffffffffu, !tc::mbar_wait(&accf[a], (ci >> 1) & 1))) failed = true;
+        if (failed) continue;
+        tc::fence_after_sync();
+        float v0[32], v1[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(a * kRChunk + half * 64);
+        tc::tmem_ld32(taddr, v0);
+        tc::tmem_ld32(taddr + 32, v1);
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&acce[a]);
+        const int t0 = c * kRChunk + half * 64;
+        if (mine) {
+#pragma unroll
+          for (int g8 = 0; g8 < 8; ++g8) {
+            const int t = t0 + g8 * 8;
+            if (t < d) {
+              const uint4 qv = __ldg(reinterpret_cast<const uint4*>(qrow + t));
+              const uint4 mv = __ldg(reinterpret_cast<const uint4*>(mrow + t));
+              const uint32_t qw[4] = {qv.x, qv.y, qv.z, qv.w}, mw[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {
+                const int cidx = g8 * 8 + 2 * h;
+                const float rec0 = cidx < 32 ? v0[cidx] : v1[cidx - 32];
+                const float rec1 = cidx + 1 < 32 ? v0[cidx + 1] : v1[cidx + 1 - 32];
+                const float e0 = (bf16_val((uint16_t)(qw[h] & 0xFFFFu)) - bf16_val((uint16_t)(mw[h] & 0xFFFFu))) - rec0;
+                const float e1 = (bf16_val((uint16_t)(qw[h] >> 16)) - bf16_val((uint16_t)(mw[h] >> 16))) - rec1;
+                acc = fmaf(e0, e0, acc);
+                acc = fmaf(e1, e1, acc);
+              }
+            }
+          }
+        }
+      }
+      // the two column halves of each pair
+      if (half == 1) sred[row] = acc;
+      tc::named_bar(1, 256);
+      if (half == 0 && mine && !failed) rhoq[sl.y + lane] = acc + sred[row];
+      tc::named_bar(1, 256);
+    }
+    if (failed) atomicExch(&s_fail, 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid == 0 && s_fail) {
+    for (uint32_t j = s_it_mma; j < s_it_prod; ++j) tc::mbar_wait(&full[j % kRStg], (j / kRStg) & 1, 1u << 16);
+  }
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 2 * kRChunk);
+  }
+  if (tid == 0 && s_fail) atomicOr(err, tc::kErrTimeout);
+}
+
 // Per grain (BF16 form): the Gram matrix U_g U_g^T (r x r, FP32 sums of exact products).
 __global__ void k_gram(const uint16_t* __restrict__ Uh, int d, int r, float* __restrict__ gram) {
   const int g = blockIdx.x;

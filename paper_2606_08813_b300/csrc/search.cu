@@ -469,11 +469,36 @@ int launch_project_tc_n(const Index& I, uint32_t nq, uint32_t P, const Ws& w, cu
   return HNTL_OK;
 }
 
+// The explicit residual rho_q = ||v' - U_b^T z||^2 of every pair (k_resid_tc),
+// replacing the projection's Gram-identity value; bases of up to 32 rows.
+template <int RN>
+int launch_resid_tc_n(const Index& I, uint32_t P, const Ws& w, cudaStream_t st) {
+  static thread_local int attr_dev = -1;
+  if (attr_dev != I.device) {
+    HNTL_CUDA_TRY(
+        cudaFuncSetAttribute(k_resid_tc<RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, ResidTc<RN>::kSmem));
+    attr_dev = I.device;
+  }
+  const size_t max_items = ((size_t)P / kPSlot + I.G + kPSlots - 1) / kPSlots;
+  const unsigned grid = persistent_grid(std::min<size_t>(max_items, (size_t)I.num_sms));
+  k_resid_tc<RN><<<grid, kRThr, ResidTc<RN>::kSmem, st>>>(w.Qh, I.Mh, I.mapU, (int)I.d, (int)I.r, w.slots,
+                                                          w.grp2_off + I.G, w.pair_q, w.zq, w.rhoq, I.d_err);
+  HNTL_CUDA_TRY(cudaGetLastError());
+  return HNTL_OK;
+}
+
 int launch_project_tc(const Index& I, uint32_t nq, uint32_t P, const Ws& w, cudaStream_t st) {
   if (!I.tc_proj) return fail(HNTL_EINVAL, "the precision form needs tensor-core projection (d a multiple of 8)");
-  if (I.r <= 16) return launch_project_tc_n<16>(I, nq, P, w, st);
-  if (I.r <= 32) return launch_project_tc_n<32>(I, nq, P, w, st);
-  return launch_project_tc_n<64>(I, nq, P, w, st);
+  int rc;
+  if (I.r <= 16) {
+    if ((rc = launch_project_tc_n<16>(I, nq, P, w, st))) return rc;
+    return launch_resid_tc_n<16>(I, P, w, st);
+  }
+  if (I.r <= 32) {
+    if ((rc = launch_project_tc_n<32>(I, nq, P, w, st))) return rc;
+    return launch_resid_tc_n<32>(I, P, w, st);
+  }
+  return launch_project_tc_n<64>(I, nq, P, w, st);  // r > 32: the Gram identity's rho_q
 }
 
 template <int RT, int kC>

@@ -33,10 +33,29 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory descriptor of an MN-major, 128B-swizzled operand tile: each
+// 128-byte row holds 64 consecutive M (or N) elements of one K index, 8 rows
+// (8 consecutive K) form a 1024-byte atom; `mn_stride` bytes separate
+// successive 64-element groups along M (N), 1024 bytes successive 8-row
+// groups along K.
+__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr, uint32_t mn_stride) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((mn_stride >> 4) & 0x3FFF) << 16;  // leading byte offset: next 64-element group along M/N
+  d |= (uint64_t)(1024 >> 4) << 32;                   // stride byte offset: next 8 K rows
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
 // Instruction descriptor: FP32 accumulator, A and B of format `fmt`
 // (kind::f16: 0 F16, 1 BF16; kind::tf32: 2), both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_f32acc(uint32_t fmt, int M, int N) {
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// The same with B read MN-major (bit 16, "transpose B").
+__host__ __device__ constexpr uint32_t idesc_f32acc_bmn(uint32_t fmt, int M, int N) {
+  return idesc_f32acc(fmt, M, N) | (1u << 16);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {

@@ -71,18 +71,10 @@ def compare_mode_a(gpu, ora, ora_next, grain_of, k, C, nprobe, precision):
             return vmap[int(grain_of[i])]
 
         cd = ora["cand_d"][qi]
-        if precision == "bf16-fp8":  # pool distances with the expansion-scale error
-            _check_abs(gpu["pool_ids"][qi].astype(np.uint32), gpu["pool_d"][qi], ora["cand_id"][qi], cd, vn_of,
-                       max(vmap.values()), "pool", qi, 0xFFFFFFFF)
-            edge_tie = False
-            if np.isfinite(cd[Ce]):
-                a, b = int(ora_next["cand_id"][qi][Ce - 1]), int(ora_next["cand_id"][qi][Ce])
-                tol = ATOL_SCALE * (cd[Ce] + 2 * max(vn_of(a), vn_of(b)))
-                edge_tie = cd[Ce] - cd[Ce - 1] <= 2 * tol
-        else:  # the FP32 form's explicit residual: the Mode B rules
-            check_ranked(gpu["pool_ids"][qi].astype(np.uint32), gpu["pool_d"][qi], ora["cand_id"][qi], cd, "pool",
-                         qi, invalid=0xFFFFFFFF)
-            edge_tie = _rel_gap(cd[Ce - 1], cd[Ce]) <= GAP and np.isfinite(cd[Ce])
+        # pool distances: both forms form rho_q as the explicit residual, so the Mode B rules hold
+        check_ranked(gpu["pool_ids"][qi].astype(np.uint32), gpu["pool_d"][qi], ora["cand_id"][qi], cd, "pool",
+                     qi, invalid=0xFFFFFFFF)
+        edge_tie = _rel_gap(cd[Ce - 1], cd[Ce]) <= GAP and np.isfinite(cd[Ce])
         if edge_tie:
             stats["topk_excluded"] += 1  # the pool's edge is within the error: its members may differ
             continue

@@ -752,3 +752,23 @@ def test_balanced_assignment_is_the_row_optimal_stable_one():
     assert any(np.array_equal(got, s) for s in stable)
     for s in stable:
         assert np.all(rank[np.arange(7), got] <= rank[np.arange(7), s])
+
+
+def test_given_projection_reproduces_the_oracle_own():
+    """Feeding the oracle its own projection values (rounded to FP32, as another
+    implementation would hand them over) leaves every pool and top k id
+    unchanged where the ranking has gaps well above FP32 rounding, and moves
+    distances by no more than that rounding."""
+    X, Q, idx = clustered_case(1500, 16, 6, 6, 4, 25, seed=33)
+    ref = O.search(idx, X, Q, 5, 30, 3)
+    M, U = idx["M"].astype(np.float64), idx["U"].astype(np.float64)
+    z = np.zeros((len(Q), 3, 4), np.float32)
+    rho = np.zeros((len(Q), 3), np.float32)
+    for qi in range(len(Q)):
+        for p, g in enumerate(ref["probe"][qi]):
+            v = Q[qi].astype(np.float64) - M[g]
+            z[qi, p] = U[g] @ v
+            rho[qi, p] = ((v - U[g].T @ (U[g] @ v)) ** 2).sum()
+    got = O.search(idx, X, Q, 5, 30, 3, probes=ref["probe"], pair_proj=(z, rho))
+    assert np.array_equal(got["out_id"], ref["out_id"])
+    np.testing.assert_allclose(got["cand_d"][:, :30], ref["cand_d"][:, :30], rtol=1e-6)
