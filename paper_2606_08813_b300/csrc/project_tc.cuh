@@ -374,8 +374,9 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
 // identity to BF16 precision), so this pass recomputes it.
 // Work items are the projection's: 4 slots of up to 32 pairs. The
 // reconstruction U_b^T z of all 128 pairs against a 128-coordinate chunk is
-// one MMA sequence: A = z split into three BF16 parts (hi, mid, lo, 24
-// significant bits), block-diagonal over the slots (row i of slot s holds its
+// one MMA sequence: A = z split into two BF16 parts (hi, lo: 16 significant
+// bits; the dropped remainder eta moves rho by 2 (U e) . eta + |U^T eta|^2,
+// with U e = (I - G) z + dz small), block-diagonal over the slots (row i of slot s holds its
 // z in K columns s RN .. s RN + RN - 1, zeros elsewhere); B = the slots'
 // basis rows for those 128 coordinates, TMA boxes of 64 coordinates x r
 // rows read MN-major (K = basis row, N = coordinate). TMEM lane i, column t
@@ -389,13 +390,17 @@ constexpr int kRThr = 320;
 constexpr int kRStg = 3;
 constexpr int kRChunk = 128;  // coordinates per MMA (N)
 
+constexpr int kRMuD = 1024;  // centre rows of an item are staged in shared memory up to this d
+constexpr int kRParts = 2;   // BF16 parts of z (hi, lo: 16 significant bits)
+
 template <int RN>
 struct ResidTc {
   static constexpr int kK = kPSlots * RN;                       // A's K: the 4 slots' basis rows
   static constexpr uint32_t kBytesApart = kPTM * kK * 2;         // one part of A (128 rows x kK BF16)
   static constexpr uint32_t kBytesSlot = 2 * RN * 128;           // one slot's 2 boxes of a chunk
   static constexpr uint32_t kStage = kPSlots * kBytesSlot;
-  static constexpr int kSmem = 3 * kBytesApart + kRStg * kStage + 1024;
+  static constexpr uint32_t kBytesMu = kPSlots * kRMuD * 2;     // the item's 4 BF16 centre rows
+  static constexpr int kSmem = kRParts * kBytesApart + kRStg * kStage + kBytesMu + 1024;
 };
 
 __device__ __forceinline__ uint16_t bf16_rn(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
@@ -412,8 +417,9 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
   constexpr uint32_t kIdesc = tc::idesc_f32acc_bmn(1u, kPTM, kRChunk);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = smem;                            // [3 parts][kAtomsK][128 rows x 128 B]
-  uint8_t* sB = smem + 3 * P::kBytesApart;       // [stage][slot][2 boxes][RN rows x 128 B]
+  uint8_t* sA = smem;                            // [kRParts][kAtomsK][128 rows x 128 B]
+  uint8_t* sB = smem + kRParts * P::kBytesApart; // [stage][slot][2 boxes][RN rows x 128 B]
+  uint16_t* sMu = reinterpret_cast<uint16_t*>(sB + kRStg * P::kStage);  // [slot][d] when d <= kRMuD
   __shared__ __align__(8) uint64_t full[kRStg], empty[kRStg], accf[2], acce[2], afull, fin;
   __shared__ uint4 sslot[kPSlots];
   __shared__ float sred[kPTM];
@@ -440,8 +446,13 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
   // The whole basis ring starts at zero: rows r .. RN - 1 of every box stay
   // zero (TMA writes r rows), and a slot without pairs multiplies its (stale
   // or never written) tile by the zeros of A, which must therefore be finite.
+  // A starts at zero too: outside each row's own slot range it stays zero for
+  // good, and inside it a row without a pair keeps finite stale values whose
+  // output nobody reads.
   for (uint32_t e = tid; e < (uint32_t)(kRStg * P::kStage / 16); e += kRThr)
     *reinterpret_cast<uint4*>(sB + (size_t)e * 16) = make_uint4(0, 0, 0, 0);
+  for (uint32_t e = tid; e < (uint32_t)(kRParts * P::kBytesApart / 16); e += kRThr)
+    *reinterpret_cast<uint4*>(sA + (size_t)e * 16) = make_uint4(0, 0, 0, 0);
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
@@ -494,6 +505,20 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
     if (lane == 0) {
       bool ok = true;
       uint32_t it = 0, li = 0, ci = 0;  // stage uses, items, accumulator uses
+      // every MMA's operand descriptors, once: A per (part, K step); B per K step
+      // for stage 0 (another stage adds its byte offset / 16 to the start field)
+      constexpr int kKS = P::kK / 16;
+      uint64_t da[kRParts][kKS], db0[kKS];
+#pragma unroll
+      for (int part = 0; part < kRParts; ++part)
+#pragma unroll
+        for (int ks = 0; ks < kKS; ++ks)
+          da[part][ks] = tc::desc_sw128(tc::smem_u32(sA + part * P::kBytesApart) + (ks / 4) * (kPTM * 128) +
+                                        (ks % 4) * 32);
+#pragma unroll
+      for (int ks = 0; ks < kKS; ++ks)
+        db0[ks] = tc::desc_sw128_mn(tc::smem_u32(sB) + (ks / (RN / 16)) * P::kBytesSlot + (ks % (RN / 16)) * 2048,
+                                    RN * 128);
       for (uint32_t w = blockIdx.x; w < total && ok; w += gridDim.x, ++li) {
         if (!tc::mbar_wait(&afull, li & 1)) {  // this item's A operand is written
           ok = false;
@@ -512,20 +537,12 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
           }
           tc::fence_after_sync();
           const uint32_t acc = tmem + (uint32_t)(a * kRChunk);
-          const uint32_t bst = tc::smem_u32(sB + s * P::kStage);
-          bool first = true;
+          const uint64_t soff = (uint64_t)((s * P::kStage) >> 4);  // stays inside the 14-bit start field
 #pragma unroll
-          for (int part = 0; part < 3; ++part) {
-            const uint32_t ab = tc::smem_u32(sA + part * P::kBytesApart);
+          for (int part = 0; part < kRParts; ++part)
 #pragma unroll
-            for (int ks = 0; ks < P::kK / 16; ++ks) {
-              const int slot = ks / (RN / 16), kin = ks % (RN / 16);
-              const uint64_t da = tc::desc_sw128(ab + (ks / 4) * (kPTM * 128) + (ks % 4) * 32);
-              const uint64_t db = tc::desc_sw128_mn(bst + slot * P::kBytesSlot + kin * 16 * 128, RN * 128);
-              tc::mma<true>(acc, da, db, kIdesc, first ? 0u : 1u);
-              first = false;
-            }
-          }
+            for (int ks = 0; ks < kKS; ++ks)
+              tc::mma<true>(acc, da[part][ks], db0[ks] + soff, kIdesc, (part | ks) != 0);
           tc::mma_commit(&empty[s]);
           tc::mma_commit(&accf[a]);
         }
@@ -546,77 +563,125 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
     const int row = q4 * 32 + lane;         // A row = TMEM lane = pair of the item
     bool failed = false;
     uint32_t li = 0, ci = 0;
+    // this thread's A row (two threads per row, RN / 2 of its values each) and
+    // the next item's slot record and z values, loaded while the current item runs
+    const int ra = et >> 1, hf = et & 1, sa = ra / 32, ia = ra % 32;
+    constexpr int kH = RN / 2;
+    float zn[kH];
+    bool zn_have = false;
+    auto prefetch_z = [&](uint32_t w) {
+      const uint4 sla = slot_of(w, sa);
+      zn_have = (uint32_t)ia < sla.z;
+      const float* z = zq + (size_t)(sla.y + (zn_have ? ia : 0)) * r;
+#pragma unroll
+      for (int j = 0; j < kH; ++j) {
+        const int jj = hf * kH + j;
+        zn[j] = (zn_have && jj < r) ? z[jj] : 0.f;
+      }
+    };
+    if (blockIdx.x < total) prefetch_z(blockIdx.x);
     for (uint32_t w = blockIdx.x; w < total; w += gridDim.x, ++li) {
       if (et < kPSlots) sslot[et] = slot_of(w, et);
-      tc::named_bar(1, 256);
-      // A: 3 parts x 128 rows x kK, row i of slot s holding its z at K = s RN ..; zeros elsewhere
-      for (int e = et; e < 3 * kPTM; e += 256) {
-        const int part = e / kPTM, ra = e % kPTM, sa = ra / 32, ia = ra % 32;
-        const uint4 sl = sslot[sa];
-        const bool have = (uint32_t)ia < sl.z;
-        const float* z = zq + (size_t)(sl.y + ia) * r;
-        uint8_t* abase = sA + part * P::kBytesApart;
-#pragma unroll 1
-        for (int kc = 0; kc < P::kK / 8; ++kc) {  // 16-byte chunks of 8 K values
-          const int k0 = kc * 8;
-          uint32_t wv[4] = {0, 0, 0, 0};
-          if (have && k0 >= sa * RN && k0 < sa * RN + RN) {
+      // A: row i of slot s holds its z at K = s RN .. s RN + RN - 1 (kRParts BF16
+      // parts: hi = bf16(v), lo = bf16(v - hi); v - hi - lo is below 2^-16 |v|)
+      {
+        if (zn_have) {
+          float zv[kH];
+#pragma unroll
+          for (int j = 0; j < kH; ++j) zv[j] = zn[j];
+#pragma unroll
+          for (int c8 = 0; c8 < kH / 8; ++c8) {  // 16-byte chunks of 8 values
+            uint32_t wp[kRParts][4];
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-              uint32_t two = 0;
+              uint32_t w2[kRParts] = {};
 #pragma unroll
               for (int u = 0; u < 2; ++u) {
-                const int j = k0 - sa * RN + 2 * h + u;
-                const float v = j < r ? z[j] : 0.f;
-                const float hi = __bfloat162float(__float2bfloat16_rn(v));
-                const float mid = __bfloat162float(__float2bfloat16_rn(v - hi));
-                const float lo = v - hi - mid;
-                const float pv = part == 0 ? hi : (part == 1 ? mid : lo);
-                two |= (uint32_t)bf16_rn(pv) << (16 * u);
+                float v = zv[c8 * 8 + 2 * h + u];
+#pragma unroll
+                for (int part = 0; part < kRParts; ++part) {  // successive BF16 parts of the remainder
+                  const uint16_t b = bf16_rn(v);
+                  w2[part] |= (uint32_t)b << (16 * u);
+                  v -= bf16_val(b);
+                }
               }
-              wv[h] = two;
+#pragma unroll
+              for (int part = 0; part < kRParts; ++part) wp[part][h] = w2[part];
             }
+            const int kc = (sa * RN + hf * kH) / 8 + c8;  // chunk index along K
+#pragma unroll
+            for (int part = 0; part < kRParts; ++part)
+              *reinterpret_cast<uint4*>(sA + part * P::kBytesApart + (kc / 8) * (kPTM * 128) +
+                                        sw128_off(ra, (kc % 8) * 16)) =
+                  make_uint4(wp[part][0], wp[part][1], wp[part][2], wp[part][3]);
           }
-          *reinterpret_cast<uint4*>(abase + (kc / 8) * (kPTM * 128) + sw128_off(ra, (kc % 8) * 16)) =
-              make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
       }
       tc::fence_proxy_async_smem();
       tc::named_bar(1, 256);
       if (et == 0) tc::mbar_arrive(&afull);
+      if (w + gridDim.x < total) prefetch_z(w + gridDim.x);
       const uint4 sl = sslot[q4];
       const bool mine = (uint32_t)lane < sl.z;
       const uint16_t* qrow = mine ? Qh + (size_t)pair_q[sl.y + lane] * d : Qh;
-      const uint16_t* mrow = Mh + (size_t)sl.x * d;
+      // the item's centre rows, read by every pair of a slot: staged in shared memory
+      const bool mu_smem = d <= kRMuD;
+      if (mu_smem) {
+        for (int e = et; e < kPSlots * (d / 8); e += 256) {
+          const int j = e / (d / 8), c8 = e % (d / 8);
+          *reinterpret_cast<uint4*>(sMu + j * kRMuD + c8 * 8) =
+              __ldg(reinterpret_cast<const uint4*>(Mh + (size_t)sslot[j].x * d + c8 * 8));
+        }
+        tc::named_bar(1, 256);
+      }
+      const uint16_t* mrow = mu_smem ? sMu + q4 * kRMuD : Mh + (size_t)sl.x * d;
       float acc = 0.f;
+      // this thread's 64 coordinates of a chunk: q_b loaded one chunk ahead (the
+      // warp's 32 pairs share mu_b, which stays in L1)
+      uint4 qn[8];
+      auto load_q = [&](int c) {
+        const int t0 = c * kRChunk + half * 64;
+#pragma unroll
+        for (int g8 = 0; g8 < 8; ++g8) {
+          const int t = t0 + g8 * 8;
+          qn[g8] = (mine && c < nch && t < d) ? __ldg(reinterpret_cast<const uint4*>(qrow + t))
+                                              : make_uint4(0, 0, 0, 0);
+        }
+      };
+      load_q(0);
       for (int c = 0; c < nch; ++c, ++ci) {
         const int a = (int)(ci & 1);
+        uint4 qv8[8];
+#pragma unroll
+        for (int g8 = 0; g8 < 8; ++g8) qv8[g8] = qn[g8];
+        load_q(c + 1);
         if (!failed && __any_sync(0xffffffffu, !tc::mbar_wait(&accf[a], (ci >> 1) & 1))) failed = true;
         if (failed) continue;
         tc::fence_after_sync();
-        float v0[32], v1[32];
         const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(a * kRChunk + half * 64);
-        tc::tmem_ld32(taddr, v0);
-        tc::tmem_ld32(taddr + 32, v1);
-        tc::fence_before_sync();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&acce[a]);
-        const int t0 = c * kRChunk + half * 64;
-        if (mine) {
 #pragma unroll
-          for (int g8 = 0; g8 < 8; ++g8) {
-            const int t = t0 + g8 * 8;
-            if (t < d) {
-              const uint4 qv = __ldg(reinterpret_cast<const uint4*>(qrow + t));
-              const uint4 mv = __ldg(reinterpret_cast<const uint4*>(mrow + t));
-              const uint32_t qw[4] = {qv.x, qv.y, qv.z, qv.w}, mw[4] = {mv.x, mv.y, mv.z, mv.w};
+        for (int hh = 0; hh < 2; ++hh) {  // 32 columns at a time
+          float v[32];
+          tc::tmem_ld32(taddr + 32 * hh, v);
+          if (hh == 1) {
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[a]);
+          }
+          if (mine) {
 #pragma unroll
-              for (int h = 0; h < 4; ++h) {
-                const int cidx = g8 * 8 + 2 * h;
-                const float rec0 = cidx < 32 ? v0[cidx] : v1[cidx - 32];
-                const float rec1 = cidx + 1 < 32 ? v0[cidx + 1] : v1[cidx + 1 - 32];
-                const float e0 = (bf16_val((uint16_t)(qw[h] & 0xFFFFu)) - bf16_val((uint16_t)(mw[h] & 0xFFFFu))) - rec0;
-                const float e1 = (bf16_val((uint16_t)(qw[h] >> 16)) - bf16_val((uint16_t)(mw[h] >> 16))) - rec1;
+            for (int g4 = 0; g4 < 4; ++g4) {
+              const int g8 = hh * 4 + g4;
+              const int t = c * kRChunk + half * 64 + g8 * 8;
+              const uint4 mv = t < d ? *reinterpret_cast<const uint4*>(mrow + t) : make_uint4(0, 0, 0, 0);
+              const uint32_t qw[4] = {qv8[g8].x, qv8[g8].y, qv8[g8].z, qv8[g8].w};
+              const uint32_t mw[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {  // zeros past d: q = mu = reconstruction = 0
+                const float e0 =
+                    (bf16_val((uint16_t)(qw[h] & 0xFFFFu)) - bf16_val((uint16_t)(mw[h] & 0xFFFFu))) - v[g4 * 8 + 2 * h];
+                const float e1 =
+                    (bf16_val((uint16_t)(qw[h] >> 16)) - bf16_val((uint16_t)(mw[h] >> 16))) - v[g4 * 8 + 2 * h + 1];
                 acc = fmaf(e0, e0, acc);
                 acc = fmaf(e1, e1, acc);
               }
