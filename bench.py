@@ -322,6 +322,98 @@ def cpu_oracle_qps(idx_host, X_np, Q_np, k, C, nprobe, budget_s: float = 15.0, p
     return done / t, done, O.threads(), first_out
 
 
+def _err_stats(a):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    a = a[np.isfinite(a)]
+    if a.size == 0:
+        return None
+    return {"p50": float(f"{np.percentile(a, 50):.3g}"), "p99": float(f"{np.percentile(a, 99):.3g}"),
+            "max": float(f"{a.max():.3g}"), "n": int(a.size)}
+
+
+def precision_error(host, X_np, Q_np, gpu, zq, rq, route_d, k, C, nprobe, n_e2e, threads=16):
+    """Error of each stage of the GPU's search against FP64 on the same index
+    (the plain method on its FP32 rows, centres and bases): `gpu` holds one
+    batch's probes, pool and top k for the queries Q_np, zq/rq its projections
+    of those queries into their probes, route_d its routing distances.
+    Relative errors are |gpu - fp64| / fp64 of each stage's own output and,
+    for the projection and the coordinates, of the distance (Eq. 6) they
+    feed. The first n_e2e queries are also searched end to end by the
+    oracle's FP64 plain method on exact coordinates (computed for the grains
+    its routing probes), for the id agreement of pool and top k."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import hntl_oracle as O
+
+    nq = Q_np.shape[0]
+    t0 = time.perf_counter()
+    pool = gpu["pool_ids"].astype(np.int64)
+    pool[gpu["pool_ids"] == 0xFFFFFFFF] = -1
+    # the stored coordinates of each pool row (FP8 decoded and scaled) and its stored residual norm
+    pos = np.zeros(len(host["ids"]), dtype=np.int64)
+    pos[host["ids"].astype(np.int64)] = np.arange(len(host["ids"]))
+    pp = pos[np.maximum(pool, 0)]
+    sv = O.stage_values(host, X_np, Q_np, gpu["probe"], pool, pair_proj=(zq, rq),
+                        row_terms=(host["Z"][pp], host["rho"][pp]))
+    rel = lambda g, f: np.abs(np.asarray(g, np.float64) - f) / np.maximum(np.abs(f), 1e-30)
+    ref_route = O.brute_force(host["M"], Q_np, nprobe)[0]
+    g_sets = [set(x.tolist()) for x in gpu["probe"]]
+    shared = np.array([len(g & set(o.tolist())) / nprobe for g, o in zip(g_sets, ref_route)])
+    zerr = np.linalg.norm(zq - sv["z"], axis=2) / np.maximum(np.linalg.norm(sv["z"], axis=2), 1e-30)
+    # the rerank: output distances, and the top k of the GPU's own pool by FP64 exact distance
+    ex = np.where(pool >= 0, sv["exact"], np.inf)
+    order = np.lexsort((np.where(pool >= 0, pool, np.iinfo(np.int64).max), ex), axis=1)[:, :k]
+    exact_topk = np.take_along_axis(pool, order, axis=1)
+    ids_pos = {}
+    for qi in range(nq):
+        for j, i in enumerate(pool[qi].tolist()):
+            ids_pos[(qi, i)] = j
+    out_ex = np.array([[sv["exact"][qi, ids_pos[(qi, int(i))]] if (qi, int(i)) in ids_pos else np.nan
+                        for i in gpu["ids"][qi]] for qi in range(nq)])
+    exs = np.sort(ex, axis=1)
+    clear = (exs[:, k] - exs[:, k - 1]) > 1e-4 * exs[:, k - 1]
+    same = np.array([set(a.tolist()) == set(b.tolist()) for a, b in zip(gpu["ids"], exact_topk)])
+    res = {
+        "queries": int(nq), "reference": "FP64 on the FP32 rows, centres and bases of the same index (oracle)",
+        "route": {"probe_sets_equal": round(float(np.mean([g == set(o.tolist()) for g, o in zip(g_sets, ref_route)])), 4),
+                  "probes_shared": round(float(shared.mean()), 4),
+                  "dist_rel_err": _err_stats(rel(route_d, sv["route_d"]))},
+        "project": {"z_rel_err": _err_stats(zerr), "rho_rel_err": _err_stats(rel(rq, sv["rho"])),
+                    "D_rel_err": _err_stats(rel(sv["D_pair"], sv["D"]))},
+        "coordinates": {"D_rel_err": _err_stats(rel(sv["D_row"], sv["D"]))},
+        "scan": {"pool_D_rel_err": _err_stats(rel(np.where(pool >= 0, gpu["pool_d"], np.nan), sv["D"]))},
+        "rerank": {"dist_rel_err": _err_stats(rel(gpu["dist"], out_ex)),
+                   "topk_equal_fp64_rerank_of_pool": round(float(same[clear].mean()), 4) if clear.any() else None,
+                   "queries_without_near_tie_at_k": int(clear.sum())},
+    }
+    # end to end: the oracle's FP64 plain search on exact coordinates of the grains its routing probes
+    if n_e2e:
+        Qe = Q_np[:n_e2e]
+        grains = np.unique(ref_route[:n_e2e])
+        off = host["grain_off"]
+        Zx = np.zeros_like(host["Z"])
+        rx = np.zeros_like(host["rho"])
+
+        def one(g):
+            a_, b_ = int(off[g]), int(off[g + 1])
+            if b_ > a_:
+                z, rh = O.tangent(X_np, host["ids"][a_:b_].astype(np.int64), host["M"][g], host["U"][g].astype(np.float64))
+                Zx[a_:b_] = z
+                rx[a_:b_] = rh
+
+        with ThreadPoolExecutor(threads) as ex_:
+            list(ex_.map(one, grains.tolist()))
+        ora = O.search(host, X_np, Qe, k, C, nprobe, precision="fp32", Z=Zx, rho=rx)
+        pool_shared = [len(set(int(x) for x in p if x >= 0) & set(int(x) for x in o if x != 0xFFFFFFFF)) /
+                       max(1, sum(1 for x in o if x != 0xFFFFFFFF)) for p, o in zip(pool[:n_e2e], ora["cand_id"])]
+        topk_shared = [len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(gpu["ids"][:n_e2e], ora["out_id"])]
+        res["end_to_end"] = {"queries": int(n_e2e), "grains_with_exact_coordinates": int(len(grains)),
+                             "pool_ids_shared": round(float(np.mean(pool_shared)), 4),
+                             "topk_ids_shared": round(float(np.mean(topk_shared)), 4)}
+    res["cpu_s"] = round(time.perf_counter() - t0, 1)
+    return res
+
+
 ATTR_SPAN = 1 << 40
 
 
@@ -776,6 +868,9 @@ def run_ours(a, world, rank, local):
         # probes; 64 of its rows, spread over the batch, are the parity sample
         # the oracle searches first inside its timed baseline
         ids0, d0, pid0, pd0, pr0 = gi.search(batches[0], k, C, nprobe, return_pool=True, return_probe=True)
+        zq0, rq0 = hntl.search_pair_proj(gi, gi.workspace(0), B, C, nprobe)
+        ne = min(a.err_queries, B) if prec == "bf16-fp8" else 0
+        rp0, rd0 = gi.route(batches[0][:max(ne, 1)], nprobe)
         torch.cuda.synchronize()
         rows = np.arange(0, B, max(1, B // 64))[:64]
         gpu0 = dict(ids=ids0.cpu().numpy()[rows], dist=d0.cpu().numpy()[rows],
@@ -794,6 +889,21 @@ def run_ours(a, world, rank, local):
                                           "timed launch configuration, against the oracle on the exported index",
                                      rule="ids equal as sets wherever the oracle's ranking has a gap > 1e-4 "
                                           "relative; near ties at the routing or pool boundary excluded")
+        if ne:
+            # per-stage error of the precision form against FP64, the first `ne` queries of batch 0
+            pr_np = pr0.cpu().numpy()[:ne]
+            rp, rd = rp0.cpu().numpy(), rd0.cpu().numpy()
+            route_d = np.full((ne, nprobe), np.nan)
+            for qi in range(ne):
+                at = {int(g): float(x) for g, x in zip(rp[qi], rd[qi])}
+                route_d[qi] = [at.get(int(g), np.nan) for g in pr_np[qi]]
+            gpu_e = dict(ids=ids0.cpu().numpy()[:ne], dist=d0.cpu().numpy()[:ne],
+                         pool_ids=pid0.cpu().numpy().view(np.uint32)[:ne], pool_d=pd0.cpu().numpy()[:ne],
+                         probe=pr_np)
+            line["precision_error"] = precision_error(host, Xn, batches[0][:ne].cpu().numpy(), gpu_e,
+                                                      zq0.cpu().numpy()[:ne], rq0.cpu().numpy()[:ne], route_d,
+                                                      k, C, nprobe, min(a.err_e2e, ne))
+            print(f"precision error: {line['precision_error']}", file=sys.stderr)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -1029,6 +1139,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-queries", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--err-queries", type=int, default=512,
+                    help="precision form: queries of batch 0 whose per-stage error against FP64 is reported")
+    ap.add_argument("--err-e2e", type=int, default=64,
+                    help="of those, queries also searched end to end by the oracle's FP64 plain method")
     ap.add_argument("--serve-rates", default="25000,100000,200000",
                     help="offered Poisson rates (q/s) of the serving run; empty to skip it")
     ap.add_argument("--serve-seconds", type=float, default=2.0)

@@ -384,6 +384,90 @@ def int16_form(idx):
     return dict(codes=codes, rcodes=rcodes, delta=delta, dres=dres, Zf32=Zf32, rhof32=rhof32)
 
 
+def stage_values(idx, X, Q, probes, rows, pair_proj=None, row_terms=None):
+    """FP64 values of the plain method's stages at given probes and rows, on
+    the FP32 query, rows, centres and bases (X in original id order), so that
+    another implementation's stage outputs can be held against them.
+
+    probes [nq, p] grain ids; rows [nq, m] original row ids (negative = none).
+    Returns (FP64):
+      route_d [nq, p]: ||q - mu_g||^2 for each given grain (sec. 2.1 step 1);
+      z [nq, p, r], rho [nq, p]: the query in each given grain (Eq. 1-4);
+      zi [nq, m, r], rhoi [nq, m]: each row's coordinates and residual norm in
+        its own grain (Eq. 1-4);
+      D [nq, m]: Eq. 6 with both sides as above (NaN where the row is absent
+        or its grain is not among the query's probes);
+      exact [nq, m]: ||q - x||^2 (sec. 2.1 step 4).
+    pair_proj (z [nq, p, r], rho [nq, p]) adds D_pair: Eq. 6 with the given
+    query side and the rows' own FP64 side. row_terms (Z [nq, m, r], rho
+    [nq, m]) adds D_row: the query's FP64 side and the given row side."""
+    X = _f32(X)
+    Q = _f32(Q)
+    probes = np.asarray(probes, dtype=np.int64)
+    rows = np.asarray(rows, dtype=np.int64)
+    nq, p = probes.shape
+    m = rows.shape[1]
+    r = int(idx["r"])
+    M = _f32(idx["M"]).astype(np.float64)
+    U = _f32(idx["U"])
+    off = np.asarray(idx["grain_off"], dtype=np.int64)
+    ids = np.asarray(idx["ids"], dtype=np.int64)
+    grain_of_id = np.zeros(len(ids), dtype=np.int64)
+    grain_of_id[ids] = np.repeat(np.arange(int(idx["G"])), np.diff(off))
+    out = dict(route_d=np.zeros((nq, p)), z=np.zeros((nq, p, r)), rho=np.zeros((nq, p)),
+               zi=np.full((nq, m, r), np.nan), rhoi=np.full((nq, m), np.nan), D=np.full((nq, m), np.nan),
+               exact=np.full((nq, m), np.nan))
+    if pair_proj is not None:
+        out["D_pair"] = np.full((nq, m), np.nan)
+    if row_terms is not None:
+        out["D_row"] = np.full((nq, m), np.nan)
+
+    def eq6(zq, rq, zi, ri):
+        return ((zq - zi) ** 2).sum(-1) + rq + ri
+
+    for qi in range(nq):
+        q = Q[qi].astype(np.float64)
+        g = probes[qi]
+        Ug = U[g].astype(np.float64)
+        v = q[None, :] - M[g]
+        out["route_d"][qi] = (v * v).sum(1)
+        z = np.einsum("prd,pd->pr", Ug, v)
+        e = v - np.einsum("pr,prd->pd", z, Ug)
+        out["z"][qi] = z
+        out["rho"][qi] = (e * e).sum(1)
+        have = rows[qi] >= 0
+        if not have.any():
+            continue
+        rid = rows[qi][have]
+        gi = grain_of_id[rid]
+        x = X[rid].astype(np.float64)
+        Ui = U[gi].astype(np.float64)
+        w = x - M[gi]
+        zi = np.einsum("mrd,md->mr", Ui, w)
+        ei = w - np.einsum("mr,mrd->md", zi, Ui)
+        ri = (ei * ei).sum(1)
+        cols = np.nonzero(have)[0]
+        out["zi"][qi, cols] = zi
+        out["rhoi"][qi, cols] = ri
+        dq = q[None, :] - x
+        out["exact"][qi, cols] = (dq * dq).sum(1)
+        # the probe slot of each row's grain (rows of unprobed grains keep NaN)
+        slot = {int(gg): s for s, gg in enumerate(g)}
+        sl = np.array([slot.get(int(gg), -1) for gg in gi])
+        ok = sl >= 0
+        c, s = cols[ok], sl[ok]
+        out["D"][qi, c] = eq6(z[s], out["rho"][qi, s], zi[ok], ri[ok])
+        if pair_proj is not None:
+            zq_in = np.asarray(pair_proj[0][qi], dtype=np.float64)
+            rq_in = np.asarray(pair_proj[1][qi], dtype=np.float64)
+            out["D_pair"][qi, c] = eq6(zq_in[s], rq_in[s], zi[ok], ri[ok])
+        if row_terms is not None:
+            zr = np.asarray(row_terms[0][qi], dtype=np.float64)[c]
+            rr = np.asarray(row_terms[1][qi], dtype=np.float64)[c]
+            out["D_row"][qi, c] = eq6(z[s], out["rho"][qi, s], zr, rr)
+    return out
+
+
 def brute_force(X, Q, k: int, attr=None, ranges=None):
     """Exact kNN by (dist, id), FP64. Returns (ids i64 [nq,k], d f64 [nq,k], next f64 [nq])."""
     X = _f32(X)

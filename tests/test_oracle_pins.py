@@ -772,3 +772,64 @@ def test_given_projection_reproduces_the_oracle_own():
     got = O.search(idx, X, Q, 5, 30, 3, probes=ref["probe"], pair_proj=(z, rho))
     assert np.array_equal(got["out_id"], ref["out_id"])
     np.testing.assert_allclose(got["cand_d"][:, :30], ref["cand_d"][:, :30], rtol=1e-6)
+
+
+# ---------------------------------------------------------------- per-stage FP64 values
+
+
+def test_stage_values_hand_fixture():
+    """The hand-derived fixture: z_q = 1, rho_q = 1, row coordinates [1, 2, 0]
+    with residuals [0.25, 0, 1], D = [1.25, 2, 3], exact [0.25, 2, 1], and the
+    centre distance ||q||^2 = 2; rows are given out of order and with a gap."""
+    g = _load("eq6_tiny.json")
+    idx, rows = _hand_index(g)
+    Q = np.array([g["query"]], dtype=np.float32)
+    sv = O.stage_values(idx, rows, Q, [[0]], [[2, -1, 0, 1]])
+    assert sv["route_d"][0, 0] == 2.0
+    assert sv["z"][0, 0, 0] == 1.0 and sv["rho"][0, 0] == 1.0
+    np.testing.assert_allclose(sv["zi"][0, [0, 2, 3], 0], [0, 1, 2], atol=1e-12)
+    np.testing.assert_allclose(sv["rhoi"][0, [0, 2, 3]], [1, 0.25, 0], atol=1e-12)
+    D = [g["cand_d"][2], g["cand_d"][0], g["cand_d"][1]]
+    np.testing.assert_allclose(sv["D"][0, [0, 2, 3]], D, atol=1e-12)
+    np.testing.assert_allclose(sv["exact"][0, [0, 2, 3]], [1.0, 0.25, 2.0], atol=1e-12)
+    assert np.isnan(sv["D"][0, 1]) and np.isnan(sv["exact"][0, 1])
+
+
+def test_stage_values_full_basis_is_exact_and_overrides_enter_eq6():
+    """r = d: every residual is zero and Eq. 6 equals the exact distance for
+    rows of probed grains (up to the FP32 rounding of the stored basis, whose
+    rows are orthonormal to about 1e-7); rows of unprobed grains stay NaN. Given query
+    terms shifted by +1 in one coordinate move D_pair by (dz + 1)^2 - dz^2,
+    and given row residuals raised by 0.5 move D_row by 0.5."""
+    X, Q, _ = _clustered(300, 8, 3, 4, 77)
+    idx = O.build_index(X, 3, 8, synth.uniforms(3, 5).numpy())
+    probes = np.array([[0, 2]] * len(Q))
+    rows = np.tile(np.arange(0, 300, 7), (len(Q), 1))
+    sv = O.stage_values(idx, X, Q, probes, rows)
+    gid = np.zeros(300, dtype=np.int64)
+    gid[idx["ids"]] = np.repeat(np.arange(3), np.diff(idx["grain_off"]))
+    probed = np.isin(gid[rows[0]], [0, 2])
+    assert probed.any() and (~probed).any()
+    np.testing.assert_allclose(sv["D"][:, probed], sv["exact"][:, probed], rtol=1e-6)
+    assert np.isnan(sv["D"][:, ~probed]).all()
+    assert (sv["rho"] <= 1e-6 * sv["route_d"]).all()
+    zq = sv["z"].copy()
+    zq[:, :, 0] += 1.0
+    rz = sv["zi"].copy()
+    rr = sv["rhoi"] + 0.5
+    sv2 = O.stage_values(idx, X, Q, probes, rows, pair_proj=(zq, sv["rho"]), row_terms=(rz, rr))
+    slot = np.where(gid[rows[0]] == 0, 0, 1)
+    dz = sv["z"][:, slot, 0] - sv["zi"][:, :, 0]
+    want = sv["D"] + (dz + 1.0) ** 2 - dz ** 2
+    np.testing.assert_allclose(sv2["D_pair"][:, probed], want[:, probed], rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(sv2["D_row"][:, probed], sv["D"][:, probed] + 0.5, rtol=1e-9)
+
+
+def test_stage_values_route_distances_are_brute_force_over_centres():
+    """The routing distances of the probes brute force picks over the centres
+    are brute force's own distances."""
+    X, Q, _ = _clustered(400, 16, 4, 20, 91)
+    idx = O.build_index(X, 8, 4, synth.uniforms(8, 6).numpy())
+    bid, bd, _ = O.brute_force(idx["M"], Q, 3)
+    sv = O.stage_values(idx, X, Q, bid, np.full((len(Q), 1), -1))
+    np.testing.assert_allclose(sv["route_d"], bd, rtol=1e-12)
