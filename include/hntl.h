@@ -161,6 +161,53 @@ int hntl_index_info(const hntl_index* idx, hntl_index_desc* out);
 /* Free an index and its device memory (NULL is a no-op). Blocking. */
 void hntl_index_free(hntl_index* idx);
 
+/* ---- grain shards (the query path of sec. 2.1 split by grains) ----------
+ * Steps 1-4 run grain by grain, so an index splits into S shards by grains:
+ * every shard keeps all G centres and bases (it routes each query as the
+ * whole index does) and the rows, coordinates and raw rows of its own grains
+ * (the others are empty). A search of a shard returns that shard's top k of
+ * its own pool of C; hntl_merge_topk takes the k best by (distance, id) over
+ * the shards. The shards' pools together contain the whole index's pool, so
+ * the merged top k is the exact-distance top k over a superset of it (equal
+ * to the single-index result whenever that pool's top k is also each
+ * owning shard's). */
+
+/* Assign grains to S shards by rows (host only): grains in order of
+ * (rows descending, grain ascending), each to the shard with the fewest rows
+ * so far (lowest shard on ties). h_grain_rows: G row counts (as from
+ * hntl_index_grain_rows); h_shard_of_grain: G outputs in [0, S).
+ * Errors: EINVAL (null, G = 0, S = 0 or S > G). */
+int hntl_shard_assign(const uint32_t* h_grain_rows, uint32_t G, uint32_t S, uint32_t* h_shard_of_grain);
+
+/* Make shard `shard` of idx on `device` (any device; copied through host
+ * memory): the grains g with h_shard_of_grain[g] == shard keep their rows,
+ * the others are empty. The shard numbers its rows 0..n_s-1 in ascending
+ * original id (ties break as in idx) and reports local ids from its searches;
+ * hntl_shard_global_ids maps them back. *out is an ordinary index (search,
+ * Mode A, filters, server) owned by the caller (hntl_index_free). Blocking.
+ * Errors: EINVAL (null, idx itself a shard, no grain owned, bad device),
+ * ENOMEM, ECUDA. */
+int hntl_index_shard(const hntl_index* idx, const uint32_t* h_shard_of_grain, uint32_t shard, int device,
+                     hntl_index** out);
+
+/* In place on the shard's device: each local id in d_ids (count int64) is
+ * replaced by its original id; -1 (padding) and out-of-range values become -1.
+ * Asynchronous on `stream`. Errors: EINVAL (null, not a shard), ECUDA. */
+int hntl_shard_global_ids(const hntl_index* shard, int64_t* d_ids, uint64_t count, void* stream);
+
+/* Merge S result lists per query (device): d_ids/d_dist are S x nq x k
+ * (shard-major; ids distinct across shards, -1 = padding with any distance),
+ * d_out_ids/d_out_dist nq x k: the k best by (distance, id), padded with -1
+ * and +inf. Asynchronous on `stream` (the current device's). Errors: EINVAL
+ * (null with nq > 0, S = 0, k = 0, S k > 2^24), ECUDA. */
+int hntl_merge_topk(const int64_t* d_ids, const float* d_dist, uint32_t S, uint32_t nq, uint32_t k,
+                    int64_t* d_out_ids, float* d_out_dist, void* stream);
+
+/* The same merge on host arrays (for results gathered to host memory, e.g.
+ * across processes). Errors: EINVAL. */
+int hntl_merge_topk_host(const int64_t* h_ids, const float* h_dist, uint32_t S, uint32_t nq, uint32_t k,
+                         int64_t* h_out_ids, float* h_out_dist);
+
 /* Bytes of device workspace hntl_search needs for these parameters (0 if
  * the parameters are invalid; see hntl_last_error). */
 size_t hntl_search_workspace_bytes(const hntl_index* idx, uint32_t nq, uint32_t k, uint32_t C, uint32_t nprobe);

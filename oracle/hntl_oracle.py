@@ -384,6 +384,55 @@ def int16_form(idx):
     return dict(codes=codes, rcodes=rcodes, delta=delta, dres=dres, Zf32=Zf32, rhof32=rhof32)
 
 
+def shard_assign(grain_rows, S: int):
+    """Grains to S shards by rows: grains in order of (rows descending, grain
+    ascending), each to the shard holding the fewest rows so far, the lowest
+    such shard on ties (the greedy longest-first rule). Returns int [G]."""
+    rows = [int(x) for x in grain_rows]
+    if not (1 <= S <= len(rows)):
+        raise ValueError("need 1 <= S <= G")
+    load = [0] * S
+    out = np.zeros(len(rows), dtype=np.int64)
+    for g in sorted(range(len(rows)), key=lambda g: (-rows[g], g)):
+        s = min(range(S), key=lambda j: (load[j], j))
+        out[g] = s
+        load[s] += rows[g]
+    return out
+
+
+def sharded_search(idx, X, Q, k: int, C: int, nprobe: int, shard_of_grain, precision="fp32"):
+    """The query path split by grains: shard s is the index with every grain
+    of another shard emptied (all centres and bases kept, so routing is
+    unchanged); each shard searches on its own (its own pool of C, its own
+    rerank to k), then per query the k best (distance, id) over all shards'
+    lists are kept. Returns (out_id [nq, k] int64, out_d [nq, k] float64,
+    per-shard results)."""
+    sog = np.asarray(shard_of_grain)
+    off = np.asarray(idx["grain_off"], dtype=np.int64)
+    G = int(idx["G"])
+    per = []
+    for s in sorted(set(sog.tolist())):
+        keep = np.concatenate([np.arange(off[g], off[g + 1]) for g in range(G) if sog[g] == s] or [np.zeros(0, np.int64)])
+        cnt = np.array([off[g + 1] - off[g] if sog[g] == s else 0 for g in range(G)], dtype=np.int64)
+        sub = dict(idx)
+        sub["grain_off"] = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+        sub["ids"] = np.asarray(idx["ids"])[keep]
+        sub["Z"] = np.asarray(idx["Z"])[keep]
+        sub["rho"] = np.asarray(idx["rho"])[keep]
+        per.append(search(sub, X, Q, k, C, nprobe, precision=precision))
+    nq = Q.shape[0]
+    out_id = np.full((nq, k), -1, dtype=np.int64)
+    out_d = np.full((nq, k), np.inf)
+    for qi in range(nq):
+        cand = [(float(r["out_d"][qi, j]), int(r["out_id"][qi, j])) for r in per for j in range(k)
+                if r["out_id"][qi, j] >= 0]
+        cand.sort()
+        for j, (dd, ii) in enumerate(cand[:k]):
+            out_id[qi, j] = ii
+            out_d[qi, j] = dd
+    return out_id, out_d, per
+
+
 def stage_values(idx, X, Q, probes, rows, pair_proj=None, row_terms=None):
     """FP64 values of the plain method's stages at given probes and rows, on
     the FP32 query, rows, centres and bases (X in original id order), so that

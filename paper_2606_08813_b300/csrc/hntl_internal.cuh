@@ -66,6 +66,7 @@ struct Index {
   float* grain_rho_min = nullptr;  // [G] smallest residual norm of a grain's rows (precision form)
   uint32_t* ids = nullptr;       // [n_blocks][128] original ids
   int64_t* attr_b = nullptr;     // [n_blocks][128] attributes in block order
+  uint32_t* gid = nullptr;       // [n] a grain shard's original id of each local row (nullptr: not a shard)
   float* X = nullptr;            // [n][d] FP32 raw rows, id order
   uint16_t* Xh = nullptr;        // [n][d] BF16 raw rows, id order
 

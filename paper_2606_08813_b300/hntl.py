@@ -668,3 +668,124 @@ class Server:
 
     def reset_stats(self):
         _check(lib.hntl_server_reset_stats(self._h))
+
+
+# ---------------------------------------------------------------- grain shards
+
+lib.hntl_shard_assign.argtypes = [_P, _U32, _U32, _P]
+lib.hntl_index_shard.argtypes = [_P, _P, _U32, ctypes.c_int, ctypes.POINTER(_P)]
+lib.hntl_shard_global_ids.argtypes = [_P, _P, ctypes.c_uint64, _P]
+lib.hntl_merge_topk.argtypes = [_P, _P, _U32, _U32, _U32, _P, _P, _P]
+lib.hntl_merge_topk_host.argtypes = [_P, _P, _U32, _U32, _U32, _P, _P]
+
+
+def shard_assign(grain_rows, S: int):
+    """Shard of every grain, size-balanced by rows (see hntl_shard_assign): uint32 [G]."""
+    import numpy as np
+
+    rows = np.ascontiguousarray(np.asarray(grain_rows, dtype=np.uint32))
+    out = np.zeros(len(rows), dtype=np.uint32)
+    _check(lib.hntl_shard_assign(rows.ctypes.data_as(_P), len(rows), int(S), out.ctypes.data_as(_P)))
+    return out
+
+
+def index_shard(index: Index, shard_of_grain, shard: int, device: int | None = None) -> Index:
+    """Shard `shard` of `index` on `device` (default: the index's device); see hntl_index_shard."""
+    import numpy as np
+
+    sog = np.ascontiguousarray(np.asarray(shard_of_grain, dtype=np.uint32))
+    if sog.shape != (int(index.desc.G),):
+        raise ValueError("shard_of_grain must hold one shard per grain")
+    h = _P()
+    dev = index.device if device is None else int(device)
+    _check(lib.hntl_index_shard(index.handle, sog.ctypes.data_as(_P), int(shard), dev, ctypes.byref(h)))
+    return Index(h)
+
+
+def shard_global_ids(shard: Index, ids: torch.Tensor, stream=None) -> torch.Tensor:
+    """Replace a shard's local ids (CUDA int64, any shape, on the shard's device) by original ids, in place."""
+    if not ids.is_cuda or ids.dtype != torch.int64 or not ids.is_contiguous() or ids.device.index != shard.device:
+        raise ValueError("ids must be a contiguous CUDA int64 tensor on the shard's device")
+    with torch.cuda.device(ids.device):
+        _in_use(stream, ids)
+        _check(lib.hntl_shard_global_ids(shard.handle, _ptr(ids), ids.numel(), _stream(stream)))
+    return ids
+
+
+def merge_topk(ids: torch.Tensor, dist: torch.Tensor, stream=None):
+    """The k best by (distance, id) over S lists per query: ids int64 / dist f32 [S, nq, k] (CUDA, one
+    device) -> ([nq, k], [nq, k]); see hntl_merge_topk."""
+    if ids.dim() != 3 or ids.shape != dist.shape:
+        raise ValueError("ids and dist must both be [S, nq, k]")
+    S, nq, k = (int(x) for x in ids.shape)
+    _dev_tensor(ids, torch.int64, (S, nq, k), ids.device.index, "ids")
+    _dev_tensor(dist, torch.float32, (S, nq, k), ids.device.index, "dist")
+    oi = torch.empty(nq, k, dtype=torch.int64, device=ids.device)
+    od = torch.empty(nq, k, dtype=torch.float32, device=ids.device)
+    _in_use(stream, ids, dist, oi, od)
+    with torch.cuda.device(ids.device):
+        _check(lib.hntl_merge_topk(_ptr(ids), _ptr(dist), S, nq, k, _ptr(oi), _ptr(od), _stream(stream)))
+    return oi, od
+
+
+def merge_topk_host(ids, dist):
+    """hntl_merge_topk_host on host arrays [S, nq, k] (numpy or CPU tensors) -> numpy ([nq, k], [nq, k])."""
+    import numpy as np
+
+    ids = np.ascontiguousarray(np.asarray(ids, dtype=np.int64))
+    dist = np.ascontiguousarray(np.asarray(dist, dtype=np.float32))
+    if ids.ndim != 3 or ids.shape != dist.shape:
+        raise ValueError("ids and dist must both be [S, nq, k]")
+    S, nq, k = ids.shape
+    oi = np.zeros((nq, k), dtype=np.int64)
+    od = np.zeros((nq, k), dtype=np.float32)
+    _check(lib.hntl_merge_topk_host(ids.ctypes.data_as(_P), dist.ctypes.data_as(_P), S, nq, k,
+                                    oi.ctypes.data_as(_P), od.ctypes.data_as(_P)))
+    return oi, od
+
+
+def exchange_merge(ids: torch.Tensor, dist: torch.Tensor, group=None):
+    """One rank's top k (original ids, [nq, k]) against every rank's: one all-gather of k (id, distance)
+    per query over the process group, then the merge (hntl_merge_topk for CUDA tensors,
+    hntl_merge_topk_host for CPU tensors). Every rank returns the merged [nq, k]."""
+    import torch.distributed as dist_
+
+    W = dist_.get_world_size(group)
+    gi = [torch.empty_like(ids) for _ in range(W)]
+    gd = [torch.empty_like(dist) for _ in range(W)]
+    dist_.all_gather(gi, ids.contiguous(), group=group)
+    dist_.all_gather(gd, dist.contiguous(), group=group)
+    si, sd = torch.stack(gi), torch.stack(gd)
+    if si.is_cuda:
+        return merge_topk(si, sd)
+    oi, od = merge_topk_host(si.numpy(), sd.numpy())
+    return torch.from_numpy(oi), torch.from_numpy(od)
+
+
+class ShardedIndex:
+    """An index split into S grain shards (hntl_index_shard), each on its own device (or all on one).
+    search() runs every shard's search on its device, maps its ids back and merges on the first
+    shard's device."""
+
+    def __init__(self, index: Index, S: int, devices=None):
+        self.shard_of_grain = shard_assign(index.grain_rows(), S)
+        devices = [index.device] * S if devices is None else list(devices)
+        if len(devices) != S:
+            raise ValueError("one device per shard")
+        self.shards = [index_shard(index, self.shard_of_grain, s, devices[s]) for s in range(S)]
+
+    def search(self, Q: torch.Tensor, k: int, C: int, nprobe: int, return_local: bool = False):
+        dev0 = torch.device(f"cuda:{self.shards[0].device}")
+        loc = []
+        for sh in self.shards:
+            with torch.cuda.device(sh.device):
+                q = Q.to(f"cuda:{sh.device}")
+                i, d = sh.search(q, k, C, nprobe)
+                shard_global_ids(sh, i)
+                torch.cuda.current_stream().synchronize()
+            loc.append((i.to(dev0), d.to(dev0)))
+        si = torch.stack([a for a, _ in loc])
+        sd = torch.stack([b for _, b in loc])
+        with torch.cuda.device(dev0):
+            out = merge_topk(si, sd)
+        return (out, (si, sd)) if return_local else out

@@ -833,3 +833,44 @@ def test_stage_values_route_distances_are_brute_force_over_centres():
     bid, bd, _ = O.brute_force(idx["M"], Q, 3)
     sv = O.stage_values(idx, X, Q, bid, np.full((len(Q), 1), -1))
     np.testing.assert_allclose(sv["route_d"], bd, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- grain shards
+
+
+def test_shard_assign_hand_fixture_and_balance_bound():
+    """Rows [5, 4, 3, 3, 2, 1] into 2 shards, longest first to the lighter
+    shard: 5 -> s0, 4 -> s1, 3 -> s1 (4 < 5), 3 -> s0 (5 < 7), 2 -> s1
+    (7 < 8), 1 -> s0 (8 < 9); loads 9 and 9. On random sizes every shard
+    stays within the greedy rule's bound: mean load + largest grain."""
+    assert O.shard_assign([5, 4, 3, 3, 2, 1], 2).tolist() == [0, 1, 1, 0, 1, 0]
+    rows = np.random.default_rng(3).integers(0, 500, 97)
+    for S in (1, 3, 8):
+        sog = O.shard_assign(rows, S)
+        load = np.bincount(sog, weights=rows, minlength=S)
+        assert load.sum() == rows.sum()
+        assert load.max() <= rows.sum() / S + rows.max()
+
+
+def test_sharded_search_reduces_to_plain_and_to_brute_force():
+    """One shard is the plain search. With every grain probed and C = N each
+    shard's pool is all its rows, so its top k is its exact top k and the
+    merge is brute force. In between, the shards' pools together contain the
+    single index's pool, so the merged distances are at most the single
+    index's, position by position."""
+    X, Q, _ = _clustered(1200, 16, 6, 30, 57)
+    G = 12
+    idx = O.build_index(X, G, 4, synth.uniforms(G, 2).numpy())
+    rows = np.diff(idx["grain_off"])
+    plain = O.search(idx, X, Q, 10, 40, 4)
+    i1, d1, _ = O.sharded_search(idx, X, Q, 10, 40, 4, np.zeros(G, dtype=np.int64))
+    np.testing.assert_array_equal(i1, plain["out_id"])
+    np.testing.assert_allclose(d1, plain["out_d"][:, :10])
+    sog = O.shard_assign(rows, 3)
+    ia, da, _ = O.sharded_search(idx, X, Q, 10, 1200, G, sog)
+    bf, bd, _ = O.brute_force(X, Q, 10)
+    np.testing.assert_array_equal(ia, bf)
+    np.testing.assert_allclose(da, bd, rtol=1e-12)
+    ib, db, _ = O.sharded_search(idx, X, Q, 10, 40, 4, sog)
+    assert (db <= plain["out_d"][:, :10] + 1e-12).all()
+    assert (db < plain["out_d"][:, :10] - 1e-9).any() or np.array_equal(ib, plain["out_id"])
