@@ -450,7 +450,7 @@ def run_serving(a, hntl, gi, X, Q, attr, w, sd):
 
     # warm-up, untimed: bursts that make the server launch each of its graph
     # sizes once (a graph's first launch uploads it), then a clean record
-    for burst in (a.serve_batch, a.serve_batch // 4, 64, 8):
+    for burst in (a.serve_batch, a.serve_batch // 2, a.serve_batch // 4, a.serve_batch // 8, 128, 64, 8):
         nb_ = max(1, min(burst, nQ))
         kk = np.full(nb_, 100, np.uint32)
         tk = srv.submit(Qh[:nb_], kk, np.full(nb_, 1000, np.uint32))
@@ -461,7 +461,9 @@ def run_serving(a, hntl, gi, X, Q, attr, w, sd):
                 break
     srv.reset_stats()
     rates_out = []
-    for R in [int(x) for x in a.serve_rates.split(",") if x]:
+    ceiling_rates = [int(x) for x in a.serve_ceiling_rates.split(",") if x]
+    n_rates = len([x for x in a.serve_rates.split(",") if x]) + len(ceiling_rates)
+    for R in [int(x) for x in a.serve_rates.split(",") if x] + ceiling_rates:
         n = max(1, int(R * a.serve_seconds))
         qi = rng.integers(0, nQ, n)
         k = rng.choice(np.array([10, 100], np.uint32), n)
@@ -469,7 +471,7 @@ def run_serving(a, hntl, gi, X, Q, attr, w, sd):
         ranges = synth.range_filters(n, sd["serve"] + R, span=ATTR_SPAN, selectivity=0.2,
                                      frac_filtered=0.5).numpy()
         want = np.zeros(n, dtype=bool)
-        want[rng.choice(n, min(n, a.serve_recall // max(1, len(a.serve_rates.split(",")))), replace=False)] = True
+        want[rng.choice(n, min(n, a.serve_recall // max(1, n_rates)), replace=False)] = True
         tickets = np.zeros(n, dtype=np.uint64)
         done = np.zeros(n, dtype=np.uint8)
         rec = []
@@ -478,6 +480,7 @@ def run_serving(a, hntl, gi, X, Q, attr, w, sd):
         arr = start + np.cumsum(rng.exponential(1e9 / R, n)).astype(np.int64)
         i = lo = 0
         busy_refusals = 0
+        last_collect = 0
         while i < n:
             now = time.monotonic_ns()
             j = min(int(np.searchsorted(arr, now, "right")), i + 4096)
@@ -486,9 +489,11 @@ def run_serving(a, hntl, gi, X, Q, attr, w, sd):
                 tickets[i:i + len(t)] = t
                 busy_refusals += int(len(t) < j - i)
                 i += len(t)
-            collect(tickets, done, lo, i, want, rec)
-            nz = np.flatnonzero(done[lo:i] == 0)
-            lo = lo + (int(nz[0]) if len(nz) else i - lo)
+            if now - last_collect > 2_000_000:  # release finished tickets every 2 ms, not every round
+                collect(tickets, done, lo, i, want, rec)
+                nz = np.flatnonzero(done[lo:i] == 0)
+                lo = lo + (int(nz[0]) if len(nz) else i - lo)
+                last_collect = now
             if i < n and j <= i:
                 wait = (arr[i] - time.monotonic_ns()) / 1e9
                 if wait > 2e-4:
@@ -504,20 +509,32 @@ def run_serving(a, hntl, gi, X, Q, attr, w, sd):
         achieved = int(done.sum()) / ((end - start) / 1e9)
         for idx, ids in rec:
             samples.append((int(qi[idx]), ranges[idx], int(C[idx]), ids))
+        rec_R = None
+        if rec and X is not None:
+            rows = torch.tensor([qi[idx_] for idx_, _ in rec], device=dev)
+            rg = torch.from_numpy(np.stack([ranges[idx_] for idx_, _ in rec])).to(dev)
+            truth_R = exact_topk(X, Q[rows].contiguous(), 10, attr=attr, ranges=rg).numpy()
+            rec_R = round(recall_at_k(np.stack([ids_ for _, ids_ in rec]), truth_R), 4)
         rates_out.append({"offered_qps": R, "achieved_qps": round(achieved, 1), "completed": int(done.sum()),
                           "p50_ms": round(st["p50_us"] / 1e3, 3), "p99_ms": round(st["p99_us"] / 1e3, 3),
                           "max_ms": round(st["max_us"] / 1e3, 3), "mean_batch": round(st["mean_batch"], 1),
-                          "admission_refusals": busy_refusals})
+                          "admission_refusals": busy_refusals, "recall_at_10": rec_R,
+                          "parts_p50_p99_ms": {part: [round(st[f"{part}_p50_us"] / 1e3, 3),
+                                                      round(st[f"{part}_p99_us"] / 1e3, 3)]
+                                               for part in ("lag", "queue", "service")}})
         print(f"serving {R} q/s: {rates_out[-1]}", file=sys.stderr)
+        if R in ceiling_rates and not (rates_out[-1]["achieved_qps"] >= 0.97 * R
+                                       and rates_out[-1]["p99_ms"] <= a.serve_ceiling_p99_ms):
+            break  # the ceiling search stops at the first rate it misses
     srv.close()
     # stage times of one search at each graph size the server captures (k_max, C_max, unfiltered)
     sizes = []
     rows_ = a.serve_batch
     while rows_ >= 32:
         sizes.insert(0, rows_)
-        if rows_ // 4 < 32:
+        if rows_ // 2 < 32:
             break
-        rows_ //= 4
+        rows_ //= 2
     batch_profile = {}
     for rows_ in sizes:
         Qb = Q[:rows_].contiguous()
@@ -554,8 +571,14 @@ def run_serving(a, hntl, gi, X, Q, attr, w, sd):
         recall["unfiltered"] = round(recall_at_k(got[~filt], truth[~filt]), 4)
         recall["queries"] = len(samples)
     ok = [r for r in rates_out if r["achieved_qps"] >= 0.97 * r["offered_qps"] and r["p99_ms"] <= a.serve_p99_ms]
+    ceil_ok = [r for r in rates_out if r["achieved_qps"] >= 0.97 * r["offered_qps"]
+               and r["p99_ms"] <= a.serve_ceiling_p99_ms and (r["recall_at_10"] or 0) >= 0.95]
     return {"sustained_qps": max((r["offered_qps"] for r in ok), default=None),
             "sustained_rule": f"highest offered rate served at >= 97% with p99 <= {a.serve_p99_ms} ms",
+            "ceiling_qps": max((r["offered_qps"] for r in ceil_ok), default=None),
+            "ceiling_rule": f"highest offered rate served at >= 97% with p99 <= {a.serve_ceiling_p99_ms} ms and "
+                            "recall@10 >= 0.95 on that rate's sampled requests (rates above the listed ones are "
+                            "tried in order until one misses)",
             "rates": rates_out, "recall_at_10": recall, "batch": a.serve_batch, "slots": slots,
             "batch_stage_ms_k100_C1000": batch_profile,
             "mem_budget_gb": round(budget / (1 << 30), 1), "create_s": round(create_s, 2),
@@ -1151,6 +1174,9 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-recall", type=int, default=1536, help="served requests checked against brute force")
     ap.add_argument("--serve-p99-ms", type=float, default=50.0)
+    ap.add_argument("--serve-ceiling-rates", default="300000,400000,600000,800000,1200000",
+                    help="rates tried after --serve-rates, in order, until one misses the ceiling rule")
+    ap.add_argument("--serve-ceiling-p99-ms", type=float, default=5.0)
     ap.add_argument("--no-int16", dest="int16", action="store_false",
                     help="skip timing the paper's 16-bit form built from the same rows")
     ap.add_argument("--no-mode-a", dest="mode_a", action="store_false",

@@ -453,7 +453,7 @@ int hntl_router_route(hntl_router* router, const hntl_index* idx, const float* d
  * A worker thread batches admitted requests as they arrive and runs each batch
  * as one captured CUDA graph (gather from the device slot table, the whole
  * Mode B search with each query's own k and C, result copy to pinned memory)
- * on one of two lanes, so a batch can run while the next one forms. A
+ * on one of three lanes, so batches run while the next one forms. A
  * request's result is the same as hntl_search of that query alone with its k
  * and C (every stage is per query). */
 typedef struct hntl_server hntl_server;
@@ -464,10 +464,13 @@ typedef struct {
   double mean_batch;   /* requests per batch */
   double p50_us, p99_us, max_us; /* latency from arrival (or submission) to completion */
   uint32_t slots;      /* requests the memory budget admits at once */
+  /* the latency in three parts: arrival stamp to admission (the caller's lag),
+   * admission to the launch of the request's batch, launch to completion */
+  double lag_p50_us, lag_p99_us, queue_p50_us, queue_p99_us, service_p50_us, service_p99_us;
 } hntl_server_stats;
 
 /* Create a server over `idx` (which must outlive it). mem_budget (bytes of
- * device memory) pays first for two lanes (a search workspace for `batch`
+ * device memory) pays first for three lanes (a search workspace for `batch`
  * queries with k_max, C_max and nprobe, plus batch buffers), the rest for
  * request slots (at most max_slots). ENOMEM if the budget cannot hold the
  * lanes. Blocking (captures the graphs). */
@@ -505,8 +508,9 @@ int hntl_server_poll(hntl_server* server, uint64_t ticket, int64_t* h_ids, float
 
 /* Latency record since creation or the last reset: completed requests,
  * batches launched and their mean size, p50 / p99 / max latency from each
- * request's arrival stamp to its completion, and the request slots the memory
- * budget allows. hntl_server_reset_stats clears the record (not the slots). */
+ * request's arrival stamp to its completion and its three parts, and the
+ * request slots the memory budget allows. hntl_server_reset_stats clears the
+ * record (not the slots). */
 int hntl_server_get_stats(hntl_server* server, hntl_server_stats* out);
 int hntl_server_reset_stats(hntl_server* server);
 

@@ -3,14 +3,16 @@
 // Requests are admitted into slots of a device-resident table (query row, k,
 // C and attribute range stay on the device while the request lives). A host
 // worker thread forms batches from the admitted requests as they arrive and
-// launches them on one of two lanes; each lane owns a stream, a workspace
-// and CUDA graphs captured once at creation for a few batch sizes (B, B/4,
-// B/16, ... down to 32 rows): gather the batch's slots from the table, run
+// launches them on one of kLanes lanes; each lane owns a stream, a workspace
+// and CUDA graphs captured once at creation for the batch sizes B, B/2, B/4,
+// ... down to 32 rows: gather the batch's slots from the table, run
 // the whole Mode B search with each query's own k and C (k_max and C_max set
 // the strides only), and copy the results to pinned host memory. A batch
 // takes the smallest graph that holds it, padded with copies of its first
-// request, so a lightly loaded server does not pay for full batches. While one lane's batch runs on the GPU the worker fills
-// and launches the other, so requests that arrive meanwhile overlap with it.
+// request, so a lightly loaded server does not pay for full batches (at most
+// twice the rows it holds). While lanes' batches run on the GPU the worker
+// fills and launches the next free one, so requests that arrive meanwhile
+// overlap with them.
 // A request's result does not depend on the batch it rides in: every stage is
 // per query (selections are total orders on (distance, id)).
 //
@@ -82,6 +84,8 @@ struct Req {
   uint32_t slot = 0, k = 0;
   int state = 0;  // 1 queued, 2 running, 3 done
   int64_t arrival_ns = 0;
+  int64_t admit_ns = 0;   // entered the queue
+  int64_t launch_ns = 0;  // its batch was launched
   std::vector<int64_t> ids;
   std::vector<float> dist;
 };
@@ -105,6 +109,8 @@ struct Lane {
   bool busy = false;
 };
 
+constexpr int kLanes = 3;
+
 }  // namespace
 
 struct Server {
@@ -119,7 +125,7 @@ struct Server {
   float* d_slot_q = nullptr;
   uint32_t *d_slot_k = nullptr, *d_slot_C = nullptr;
   int64_t* d_slot_range = nullptr;
-  Lane lanes[2];
+  Lane lanes[kLanes];
   std::vector<void*> dev, host;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -129,7 +135,7 @@ struct Server {
   uint64_t next_ticket = 1;
   std::thread worker;
   std::atomic<bool> stop{false};
-  std::vector<double> lat_us;
+  std::vector<double> lat_us, lag_us, queue_us, service_us;
   uint64_t batches = 0, batched = 0;
   std::atomic<int> worker_error{HNTL_OK};  // set by the worker, read by any thread
 };
@@ -150,7 +156,11 @@ void retire(Server& S, Lane& L) {
     r.dist.assign(L.h_dist + i * S.kmax, L.h_dist + i * S.kmax + r.k);
     r.state = 3;
     S.free_slots.push_back(r.slot);
-    S.lat_us.push_back((double)(now_ns() - r.arrival_ns) / 1e3);
+    const int64_t t = now_ns();
+    S.lat_us.push_back((double)(t - r.arrival_ns) / 1e3);
+    S.lag_us.push_back((double)(r.admit_ns - r.arrival_ns) / 1e3);
+    S.queue_us.push_back((double)(r.launch_ns - r.admit_ns) / 1e3);
+    S.service_us.push_back((double)(t - r.launch_ns) / 1e3);
   }
   L.tickets.clear();
   L.busy = false;
@@ -180,11 +190,13 @@ void worker_main(Server* S) {
         while (L.graphs[gi].first < n) ++gi;  // the largest graph holds B rows
         const uint32_t rows = L.graphs[gi].first;
         uint32_t first_slot = 0;
+        const int64_t t_launch = now_ns();
         for (uint32_t i = 0; i < n; ++i) {
           const uint64_t t = S->queue.front();
           S->queue.pop_front();
           Req& r = S->reqs[t];
           r.state = 2;
+          r.launch_ns = t_launch;
           L.h_slots[i] = r.slot;
           if (i == 0) first_slot = r.slot;
           L.tickets.push_back(t);
@@ -211,7 +223,8 @@ void worker_main(Server* S) {
       S->cv_done.notify_all();
       continue;
     }
-    const bool any_busy = S->lanes[0].busy || S->lanes[1].busy;
+    bool any_busy = false;
+    for (const Lane& L : S->lanes) any_busy |= L.busy;
     if (any_busy) {
       lk.unlock();
       std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -269,8 +282,8 @@ extern "C" int hntl_server_create(const hntl_index* idx, size_t mem_budget, uint
   if (!ws) return HNTL_EINVAL;
   const size_t lane_bytes = ws + (size_t)batch * (I.d * 4 + 4 + 4 + 4 + 16 + k_max * 12) + 4096;
   const size_t per_slot = (size_t)I.d * 4 + 8 + 16;
-  if (2 * lane_bytes + per_slot > mem_budget) return fail(HNTL_ENOMEM, "memory budget below one lane pair");
-  const uint32_t slots = (uint32_t)std::min<size_t>(max_slots, (mem_budget - 2 * lane_bytes) / per_slot);
+  if (hntl::kLanes * lane_bytes + per_slot > mem_budget) return fail(HNTL_ENOMEM, "memory budget below the lanes");
+  const uint32_t slots = (uint32_t)std::min<size_t>(max_slots, (mem_budget - hntl::kLanes * lane_bytes) / per_slot);
   hntl_server* h = new (std::nothrow) hntl_server();
   if (!h) return fail(HNTL_ENOMEM, "host allocation");
   hntl::Server& S = h->S;
@@ -363,9 +376,9 @@ extern "C" int hntl_server_create(const hntl_index* idx, size_t mem_budget, uint
       return HNTL_OK;
     };
     std::vector<uint32_t> sizes;
-    for (uint32_t rows = batch;; rows /= 4) {
+    for (uint32_t rows = batch;; rows /= 2) {
       sizes.insert(sizes.begin(), rows);
-      if (rows / 4 < 32) break;
+      if (rows / 2 < 32) break;
     }
     for (uint32_t rows : sizes) {
       // one eager run (sets kernel attributes), then capture the same sequence as a graph
@@ -475,6 +488,7 @@ extern "C" int hntl_server_submit(hntl_server* h, const float* h_queries, uint32
     r.k = h_k[i];
     r.state = 1;
     r.arrival_ns = h_arrival_ns ? h_arrival_ns[i] : t0;
+    r.admit_ns = hntl::now_ns();
     S.reqs.emplace(t, std::move(r));
     S.queue.push_back(t);
     tickets[i] = t;
@@ -552,18 +566,23 @@ extern "C" int hntl_server_get_stats(hntl_server* h, hntl_server_stats* out) {
   if (!h || !out) return fail(HNTL_EINVAL, "null argument");
   hntl::Server& S = h->S;
   std::lock_guard<std::mutex> lk(S.mu);
-  std::vector<double> v = S.lat_us;
-  out->completed = v.size();
+  out->completed = S.lat_us.size();
   out->batches = S.batches;
   out->mean_batch = S.batches ? (double)S.batched / (double)S.batches : 0.0;
   out->slots = S.nslots;
-  out->p50_us = out->p99_us = out->max_us = 0.0;
-  if (!v.empty()) {
+  auto pct = [](std::vector<double> v, double* p50, double* p99, double* mx) {
+    *p50 = *p99 = 0.0;
+    if (mx) *mx = 0.0;
+    if (v.empty()) return;
     std::sort(v.begin(), v.end());
-    out->p50_us = v[(size_t)(0.50 * (v.size() - 1))];
-    out->p99_us = v[(size_t)(0.99 * (v.size() - 1))];
-    out->max_us = v.back();
-  }
+    *p50 = v[(size_t)(0.50 * (v.size() - 1))];
+    *p99 = v[(size_t)(0.99 * (v.size() - 1))];
+    if (mx) *mx = v.back();
+  };
+  pct(S.lat_us, &out->p50_us, &out->p99_us, &out->max_us);
+  pct(S.lag_us, &out->lag_p50_us, &out->lag_p99_us, nullptr);
+  pct(S.queue_us, &out->queue_p50_us, &out->queue_p99_us, nullptr);
+  pct(S.service_us, &out->service_p50_us, &out->service_p99_us, nullptr);
   return HNTL_OK;
 }
 
@@ -572,6 +591,9 @@ extern "C" int hntl_server_reset_stats(hntl_server* h) {
   if (!h) return fail(HNTL_EINVAL, "null server");
   std::lock_guard<std::mutex> lk(h->S.mu);
   h->S.lat_us.clear();
+  h->S.lag_us.clear();
+  h->S.queue_us.clear();
+  h->S.service_us.clear();
   h->S.batches = h->S.batched = 0;
   return HNTL_OK;
 }

@@ -511,7 +511,9 @@ lib.hntl_server_poll_many.argtypes = [_P, _P, _U32, _P, _P, _U32, _P, _U32, ctyp
 class ServerStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("mean_batch", ctypes.c_double),
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double),
-                ("slots", ctypes.c_uint32)]
+                ("slots", ctypes.c_uint32), ("lag_p50_us", ctypes.c_double), ("lag_p99_us", ctypes.c_double),
+                ("queue_p50_us", ctypes.c_double), ("queue_p99_us", ctypes.c_double),
+                ("service_p50_us", ctypes.c_double), ("service_p99_us", ctypes.c_double)]
 
 
 lib.hntl_server_get_stats.argtypes = [_P, ctypes.POINTER(ServerStats)]

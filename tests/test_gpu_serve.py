@@ -80,6 +80,10 @@ def test_mixed_stream_equals_alone(hntl, served):
     srv.close()
     assert all(g is not None for g in got)
     assert st["completed"] == nq and st["batches"] >= nq // 64
+    # the latency's parts: caller lag, queueing, service (each per request, so none exceeds the whole)
+    for part in ("lag", "queue", "service"):
+        assert 0 <= st[f"{part}_p50_us"] <= st[f"{part}_p99_us"] <= st["max_us"] + 1e-6
+    assert st["service_p50_us"] > 0
     assert hntl.device_status(gi) == 0
     for i in range(nq):
         q = torch.from_numpy(Q[i:i + 1]).cuda()
@@ -111,7 +115,7 @@ def test_admission_refuses_beyond_free_slots(hntl, served):
         srv.submit(Q[:1], np.array([11], np.uint32), np.array([20], np.uint32))  # k beyond k_max
     assert e.value.code == hntl.EINVAL
     srv.close()
-    # a budget that cannot hold the two lanes is refused at creation
+    # a budget that cannot hold the lanes is refused at creation
     with pytest.raises(hntl.HntlError) as e:
         hntl.Server(gi, mem_budget=1 << 16, max_slots=16, batch=8, nprobe=2, k_max=10, C_max=20)
     assert e.value.code == hntl.ENOMEM
