@@ -952,7 +952,7 @@ def knn_ids_bf16(X: torch.Tensor, Q: torch.Tensor, k: int, qblock: int = 2048, c
 
 def router_leg(a, hntl, dev):
     """Learned grain router at its full configuration (router-5m: 5M rows,
-    G = 4096 capacity-bounded grains over Zipf clusters): train the MLP with
+    G = 4096 capacity-bounded grains over 1024 equal clusters): train the MLP with
     the library's BF16 kernels on labels the method generates (the grains
     holding each training query's top-10), compare recall@10 with centroid
     routing at equal nprobe (equal grain sizes: equal probed rows), and state
@@ -1064,7 +1064,7 @@ def router_leg(a, hntl, dev):
     _, bf16, src = _peaks()
     tflops = samples * flop_per_sample / (train_ms / 1e3) / 1e12
     res = {"workload": "router-5m", "N": w["n"], "d": d, "G": G, "r": w["r"], "C": w["C"], "k": 10,
-           "clusters": f"{w['n_clusters']} Zipf", "max_grain_rows": w["max_grain_rows"],
+           "clusters": f"{w['n_clusters']} {w['sizes']}", "max_grain_rows": w["max_grain_rows"],
            "grain_rows_min_max": [int(rows_g.min()), int(rows_g.max())], "same_partition_both_forms": same_partition,
            "mlp": f"{d}-{a.router_hidden}-{a.router_hidden}-{G}", "train_queries": int(samples / max(a.router_epochs, 1)),
            "eval_queries": nev, "epochs": a.router_epochs, "batch": B, "lr": a.router_lr,

@@ -73,6 +73,7 @@ struct Index {
   // derived at load/build (finalize_index)
   float* mnorm = nullptr;        // [G] ||mu_g||^2 (of the BF16 centres in the precision form)
   uint16_t* Mh = nullptr;        // [G][d] BF16 centres (precision form)
+  uint16_t* Mhn = nullptr;       // [G][d] the same negated (the projection's -mu_b operand)
   int num_sms = 148;             // streaming multiprocessors of the index's device
   uint16_t* Uh = nullptr;        // [G][r][d] BF16 bases (precision form)
   float* gram = nullptr;         // [G][r][r] U_g U_g^T (of the BF16 bases in the precision form)
@@ -129,6 +130,14 @@ void clear_error();
     cudaError_t _e = (expr);                                                                 \
     if (_e != cudaSuccess)                                                                   \
       return ::hntl::fail(HNTL_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));   \
+  } while (0)
+
+// After a kernel launch: a launch error names the kernel.
+#define HNTL_LAUNCH_CHECK(name)                                                              \
+  do {                                                                                       \
+    cudaError_t _e = cudaGetLastError();                                                     \
+    if (_e != cudaSuccess)                                                                   \
+      return ::hntl::fail(HNTL_ECUDA, std::string("launch of ") + (name) + ": " + cudaGetErrorString(_e)); \
   } while (0)
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -57,29 +57,35 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int byte) {
 // quarter j, columns j*RN.., holds z of slot j's pairs; the other columns
 // (pairs against the other slots' bases) are computed and ignored.
 // CTA b takes items b, b + grid, ...
-//   warps 0-3  producers: per K block of 64 coordinates, the pairs' query
-//              rows and, on the same rows, the negated centre of each slot's
-//              grain (coalesced 16-byte loads prefetched one K block ahead,
-//              sign flip, swizzled stores, proxy fence, arrival on the
-//              stage's `full` barrier); TMA brings the 4 bases (one load
-//              each) into the same stage, counted on `full` by transaction
-//              bytes.
+//   warps 0-3  producers: per K block of 64 coordinates, 16-byte asynchronous
+//              copies (cp.async, through L2) of the pairs' query chunks and,
+//              on the same rows, of the negated centre of each slot's grain
+//              (a negated BF16 copy of the centres), straight into the
+//              stage's swizzled A tiles, with up to kPDepth K blocks in
+//              flight per thread; a thread announces a stage on `full` once
+//              its copies into it have landed (wait_group, then the proxy
+//              fence that shows them to the tensor cores). TMA brings the 4
+//              bases (one load each) into the same stage, counted on `full`
+//              by transaction bytes.
 //   warp 4     one thread issues the MMAs (+U q_b then -U mu_b per 16
 //              coordinates) into one of two TMEM accumulators, frees each
 //              stage through `empty` and hands the item on through `accf`.
 //   warps 5-8  epilogue, warp w for slot w % 4: read its z, free the
-//              accumulator through `acce`, rho from the Gram identity, store;
-//              the next item's Gram matrix and ||v'||^2 are loaded meanwhile.
+//              accumulator through `acce`, store; with kRho also rho from
+//              the Gram identity (the next item's Gram matrix and ||v'||^2
+//              are loaded meanwhile), else the explicit-residual pass
+//              (k_resid_tc) computes rho.
 // RN = basis rows padded to a multiple of 16, r <= RN; d % 8 == 0 (16-byte TMA row strides).
-template <int RN>
+template <int RN, bool kRho>
 __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
-    const uint16_t* __restrict__ Qh, const uint16_t* __restrict__ Mh,
+    const uint16_t* __restrict__ Qh, const uint16_t* __restrict__ Mhn,
     const __grid_constant__ CUtensorMap mapU, const float* __restrict__ gram, int d, int r,
     const uint4* __restrict__ slots,
     const uint32_t* __restrict__ n_slots, const uint32_t* __restrict__ pair_q, const float* __restrict__ pair_vn,
     float* __restrict__ zq, float* __restrict__ rhoq, int* __restrict__ err) {
   using P = ProjTc<RN>;
   constexpr int S = P::kStages;
+  constexpr int kPDepth = S < 3 ? S : 3;  // K blocks of copies in flight per producer thread (<= S)
   constexpr uint32_t kIdesc = tc::idesc_f32acc(1u, kPTM, P::kN);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -130,12 +136,13 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
 
   if (warp < 4) {
     // ------------------------------------------------------------ producers
-    // A row i is pair i % 32 of slot i / 32. Query rows and centre chunks move
-    // by 16-byte loads, 8 lanes per row, prefetched one K block ahead in
-    // registers, and swizzled stores; the bases move by TMA into
-    // 1024-byte aligned boxes.
-    uint32_t it = 0;  // K blocks issued by this CTA so far
-    bool failed = false;  // uniform over the producers (decided by barrier reductions)
+    // A row i is pair i % 32 of slot i / 32. Thread t copies 16-byte chunk
+    // t % 8 of rows t / 8 + 16 i, i < 8 (so every warp's copies cover 4 whole
+    // 128-byte lines), and the same chunk of the negated centre of each of
+    // those rows' slots; the bases move by TMA into 1024-byte aligned boxes.
+    uint32_t it = 0;   // K blocks issued by this CTA so far
+    uint32_t ann = 0;  // K blocks this thread has announced on `full`
+    bool failed = false;  // this thread gave up waiting (the MMA thread then gives up too)
     const int my_j = tid >> 5, my_i = tid & 31;
     uint4 nslot = make_uint4(0, 0, 0, 0);
     uint32_t q_next = 0;
@@ -143,6 +150,12 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
       const uint4 sl = slot_of(w, my_j);
       q_next = (uint32_t)my_i < sl.z ? pair_q[sl.y + my_i] : 0u;
       if (my_i == 0) nslot = sl;
+    };
+    // announce the oldest unannounced K block once its copies have landed
+    auto announce = [&]() {
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(&full[ann % S]);
+      ++ann;
     };
     if (blockIdx.x < total) prefetch(blockIdx.x);
     for (uint32_t w = blockIdx.x; w < total; w += gridDim.x) {
@@ -152,73 +165,58 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
       if (w + gridDim.x < total) prefetch(w + gridDim.x);
       tc::named_bar(1, 128);
       if (failed) continue;
-      // thread t carries chunk t % 8 of rows t / 8 + 16 i, i < 8 (so every warp
-      // load covers 4 whole 128-byte lines); row t / 8 + 16 i belongs to slot i / 2,
-      // whose centre chunk the thread also loads
       const int ch = tid & 7, rbase = tid >> 3;
       uint32_t qok = 0;  // bit i: row rbase + 16 i holds a pair
+      const uint16_t* qsrc[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int row = rbase + 16 * i;
         qok |= (uint32_t)((uint32_t)(row & 31) < sslot[row >> 5].z) << i;
+        qsrc[i] = Qh + (size_t)sq[row] * d + ch * 8;
       }
+      const uint16_t* msrc[kPSlots];
+#pragma unroll
+      for (int j = 0; j < kPSlots; ++j) msrc[j] = Mhn + (size_t)sslot[j].x * d + ch * 8;
       // TMA bytes one stage receives: the bases of the slots with pairs
       uint32_t bytes = 0;
 #pragma unroll
       for (int j = 0; j < kPSlots; ++j) bytes += sslot[j].z ? (uint32_t)r * 128u : 0u;
-      uint4 qa[8], ma[kPSlots];
-      auto load_q = [&](int kb) {
-        const int kk = kb * kPKB + ch * 8;
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-          qa[i] = ((qok >> i) & 1u) && kk < d
-                      ? __ldg(reinterpret_cast<const uint4*>(Qh + (size_t)sq[rbase + 16 * i] * d + kk))
-                      : make_uint4(0, 0, 0, 0);
-#pragma unroll
-        for (int j = 0; j < kPSlots; ++j)
-          ma[j] = ((qok >> (2 * j)) & 3u) && kk < d
-                      ? __ldg(reinterpret_cast<const uint4*>(Mh + (size_t)sslot[j].x * d + kk))
-                      : make_uint4(0, 0, 0, 0);
-      };
-      load_q(0);
       for (int kb = 0; kb < nkb; ++kb, ++it) {
         const int s = (int)(it % S);
-        if (it >= (uint32_t)S) {  // the MMAs that read this stage S K blocks ago must be done
-          const bool ok = tid != 0 || tc::mbar_wait(&empty[s], ((it / S) - 1) & 1);
-          if (tc::named_bar_or(1, 128, !ok)) {
-            failed = true;
-            break;
-          }
+        // the MMAs that read this stage S K blocks ago must be done (every
+        // producer waits for itself: no barrier between the producer warps)
+        if (it >= (uint32_t)S && !tc::mbar_wait(&empty[s], ((it / S) - 1) & 1)) {
+          failed = true;
+          break;
         }
         uint8_t* st = smem + s * P::kStage;
         const int x = kb * kPKB;
-        if (tid == 0) tc::mbar_add_tx(&full[s], bytes);  // before this thread's arrival below
+        if (tid == 0) tc::mbar_add_tx(&full[s], bytes);  // before this thread announces the stage
         if (tid < kPSlots && sslot[tid].z)
           tc::tma_load_2d(&mapU, &full[s], st + 2 * kPBytesA + tid * RN * 128, x, (int)sslot[tid].x * r);
         const uint32_t sbase = tc::smem_u32(st);
+        const bool in = x + ch * 8 < d;  // d % 8 == 0: a chunk is wholly inside or outside
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           if ((qok >> i) & 1u) {
             const uint32_t off = sbase + sw128_off(rbase + 16 * i, ch * 16);
-            const uint4 m = ma[i >> 1];  // -mu_b: flip the sign bit of each BF16 (exact)
-            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(off), "r"(qa[i].x), "r"(qa[i].y),
-                         "r"(qa[i].z), "r"(qa[i].w)
-                         : "memory");
-            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(off + kPBytesA),
-                         "r"(m.x ^ 0x80008000u), "r"(m.y ^ 0x80008000u), "r"(m.z ^ 0x80008000u),
-                         "r"(m.w ^ 0x80008000u)
-                         : "memory");
+            tc::cp_async16_cg_zfill(off, qsrc[i] + (in ? x : 0), in);  // past d: zeros, nothing read
+            // the slot's 32 rows read the same centre chunk: through L1
+            tc::cp_async16_ca_zfill(off + kPBytesA, msrc[i >> 1] + (in ? x : 0), in);
           }
         }
-        tc::fence_proxy_async_smem();
-        tc::mbar_arrive(&full[s]);
-        if (kb + 1 < nkb) load_q(kb + 1);
+        tc::cp_async_commit();
+        if (it + 1 - ann >= (uint32_t)kPDepth) {  // keep at most kPDepth - 1 blocks in flight
+          tc::cp_async_wait<kPDepth - 1>();
+          announce();
+        }
       }
     }
-    if (tid == 0) {
-      s_it_prod = it;
-      if (failed) atomicExch(&s_fail, 1);
-    }
+    // the last blocks: wait for every copy, then announce what is left
+    tc::cp_async_wait<0>();
+    while (ann < it) announce();
+    atomicMax(&s_it_prod, it);  // a thread that gave up stopped issuing early
+    if (failed) atomicExch(&s_fail, 1);
   } else if (warp == 4) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
@@ -263,19 +261,20 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
     const int j = warp & 3;  // slot = TMEM lane quarter of this warp
     float* sgram = sgram_all + j * RN * RN;
     bool failed = false;
-    float gnext[P::kGramRegs > 0 ? P::kGramRegs : 1];
+    constexpr int kG = kRho ? P::kGramRegs : 0;
+    float gnext[kG > 0 ? kG : 1];
     float vn_next = 0.f;
     uint4 sl_next = make_uint4(0, 0, 0, 0);
     auto prefetch = [&](uint32_t w) {
       sl_next = slot_of(w, j);
-      if constexpr (P::kGramRegs > 0) {
+      if constexpr (kG > 0) {
 #pragma unroll
-        for (int t = 0; t < P::kGramRegs; ++t) {
+        for (int t = 0; t < kG; ++t) {
           const int e = lane + 32 * t, ga = e / RN, gb = e % RN;
           gnext[t] = (sl_next.z && ga < r && gb < r) ? gram[((size_t)sl_next.x * r + ga) * r + gb] : 0.f;
         }
       }
-      vn_next = (uint32_t)lane < sl_next.z ? pair_vn[sl_next.y + lane] : 0.f;
+      if constexpr (kRho) vn_next = (uint32_t)lane < sl_next.z ? pair_vn[sl_next.y + lane] : 0.f;
     };
     if (blockIdx.x < total) prefetch(blockIdx.x);
     uint32_t li = 0;
@@ -283,9 +282,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
       const uint4 sl = sl_next;
       const float vn = vn_next;
       __syncwarp();  // this warp is done reading its previous Gram matrix
-      if constexpr (P::kGramRegs > 0) {
+      if constexpr (!kRho) {
+      } else if constexpr (kG > 0) {
 #pragma unroll
-        for (int t = 0; t < P::kGramRegs; ++t) sgram[lane + 32 * t] = gnext[t];
+        for (int t = 0; t < kG; ++t) sgram[lane + 32 * t] = gnext[t];
       } else {
         for (int e = lane; e < RN * RN; e += 32) {
           const int ga = e / RN, gb = e % RN;
@@ -324,18 +324,20 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acce[a]);
       if (lane < np) {
-        float zz = 0.f, qf = 0.f;
-#pragma unroll
-        for (int ia = 0; ia < RN; ++ia) {
-          zz = fmaf(z[ia], z[ia], zz);
-          float acc = 0.f;
-#pragma unroll
-          for (int ib = 0; ib < RN; ++ib) acc = fmaf(sgram[ia * RN + ib], z[ib], acc);
-          qf = fmaf(z[ia], acc, qf);
-        }
         const uint32_t pr = sl.y + lane;
-        const float rho = (vn - 2.f * zz) + qf;
-        rhoq[pr] = rho > 0.f ? rho : 0.f;
+        if constexpr (kRho) {
+          float zz = 0.f, qf = 0.f;
+#pragma unroll
+          for (int ia = 0; ia < RN; ++ia) {
+            zz = fmaf(z[ia], z[ia], zz);
+            float acc = 0.f;
+#pragma unroll
+            for (int ib = 0; ib < RN; ++ib) acc = fmaf(sgram[ia * RN + ib], z[ib], acc);
+            qf = fmaf(z[ia], acc, qf);
+          }
+          const float rho = (vn - 2.f * zz) + qf;
+          rhoq[pr] = rho > 0.f ? rho : 0.f;
+        }
         float* out = zq + (size_t)pr * r;
         if ((r & 3) == 0) {
 #pragma unroll
@@ -384,23 +386,25 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
 //   warp 0     TMA producer: per chunk, 2 boxes per slot into a stage ring.
 //   warp 1     one thread issues the MMAs into one of two TMEM accumulators.
 //   warps 2-9  epilogue: warp w reads lane quarter w % 4 (32 pairs), columns
-//              64 (w - 2) / 4 .. + 63 of each chunk; it also writes the A
-//              operand of each item before the item's MMAs.
+//              64 (w - 2) / 4 .. + 63 of each chunk. The A operand is double
+//              buffered: at the start of each item these warps write the
+//              next item's A (its z loaded during the item before), so the
+//              MMAs run on from one item into the next.
 constexpr int kRThr = 320;
 constexpr int kRStg = 3;
 constexpr int kRChunk = 128;  // coordinates per MMA (N)
 
-constexpr int kRMuD = 1024;  // centre rows of an item are staged in shared memory up to this d
 constexpr int kRParts = 2;   // BF16 parts of z (hi, lo: 16 significant bits)
 
 template <int RN>
 struct ResidTc {
   static constexpr int kK = kPSlots * RN;                       // A's K: the 4 slots' basis rows
   static constexpr uint32_t kBytesApart = kPTM * kK * 2;         // one part of A (128 rows x kK BF16)
+  static constexpr uint32_t kBytesA = kRParts * kBytesApart;     // one A buffer
   static constexpr uint32_t kBytesSlot = 2 * RN * 128;           // one slot's 2 boxes of a chunk
   static constexpr uint32_t kStage = kPSlots * kBytesSlot;
-  static constexpr uint32_t kBytesMu = kPSlots * kRMuD * 2;     // the item's 4 BF16 centre rows
-  static constexpr int kSmem = kRParts * kBytesApart + kRStg * kStage + kBytesMu + 1024;
+  static constexpr int kSmem = 2 * kBytesA + kRStg * kStage + 1024;
+  static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 };
 
 __device__ __forceinline__ uint16_t bf16_rn(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
@@ -417,11 +421,10 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
   constexpr uint32_t kIdesc = tc::idesc_f32acc_bmn(1u, kPTM, kRChunk);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = smem;                            // [kRParts][kAtomsK][128 rows x 128 B]
-  uint8_t* sB = smem + kRParts * P::kBytesApart; // [stage][slot][2 boxes][RN rows x 128 B]
-  uint16_t* sMu = reinterpret_cast<uint16_t*>(sB + kRStg * P::kStage);  // [slot][d] when d <= kRMuD
-  __shared__ __align__(8) uint64_t full[kRStg], empty[kRStg], accf[2], acce[2], afull, fin;
-  __shared__ uint4 sslot[kPSlots];
+  uint8_t* sA = smem;                            // [buffer][kRParts][kAtomsK][128 rows x 128 B]
+  uint8_t* sB = smem + 2 * P::kBytesA;           // [stage][slot][2 boxes][RN rows x 128 B]
+  __shared__ __align__(8) uint64_t full[kRStg], empty[kRStg], accf[2], acce[2], afull[2], fin;
+  __shared__ uint4 sslot[2][kPSlots];
   __shared__ float sred[kPTM];
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
@@ -437,7 +440,8 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
       tc::mbar_init(&accf[a], 1);
       tc::mbar_init(&acce[a], 8);
     }
-    tc::mbar_init(&afull, 1);
+    tc::mbar_init(&afull[0], 1);
+    tc::mbar_init(&afull[1], 1);
     tc::mbar_init(&fin, 1);
     s_fail = 0;
     s_it_prod = s_it_mma = 0;
@@ -451,7 +455,7 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
   // output nobody reads.
   for (uint32_t e = tid; e < (uint32_t)(kRStg * P::kStage / 16); e += kRThr)
     *reinterpret_cast<uint4*>(sB + (size_t)e * 16) = make_uint4(0, 0, 0, 0);
-  for (uint32_t e = tid; e < (uint32_t)(kRParts * P::kBytesApart / 16); e += kRThr)
+  for (uint32_t e = tid; e < (uint32_t)(2 * P::kBytesA / 16); e += kRThr)
     *reinterpret_cast<uint4*>(sA + (size_t)e * 16) = make_uint4(0, 0, 0, 0);
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -508,7 +512,7 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
       // every MMA's operand descriptors, once: A per (part, K step); B per K step
       // for stage 0 (another stage adds its byte offset / 16 to the start field)
       constexpr int kKS = P::kK / 16;
-      uint64_t da[kRParts][kKS], db0[kKS];
+      uint64_t da[kRParts][kKS], db0[kKS];  // A of buffer 0; buffer 1 adds kBytesA / 16
 #pragma unroll
       for (int part = 0; part < kRParts; ++part)
 #pragma unroll
@@ -520,11 +524,12 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
         db0[ks] = tc::desc_sw128_mn(tc::smem_u32(sB) + (ks / (RN / 16)) * P::kBytesSlot + (ks % (RN / 16)) * 2048,
                                     RN * 128);
       for (uint32_t w = blockIdx.x; w < total && ok; w += gridDim.x, ++li) {
-        if (!tc::mbar_wait(&afull, li & 1)) {  // this item's A operand is written
+        if (!tc::mbar_wait(&afull[li & 1], (li >> 1) & 1)) {  // this item's A operand is written
           ok = false;
           break;
         }
         tc::fence_after_sync();
+        const uint64_t aoff = (li & 1) ? (uint64_t)(P::kBytesA >> 4) : 0;
         for (int c = 0; c < nch; ++c, ++it, ++ci) {
           const int s = (int)(it % kRStg), a = (int)(ci & 1);
           if (ci >= 2 && !tc::mbar_wait(&acce[a], ((ci >> 1) - 1) & 1)) {
@@ -542,7 +547,7 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
           for (int part = 0; part < kRParts; ++part)
 #pragma unroll
             for (int ks = 0; ks < kKS; ++ks)
-              tc::mma<true>(acc, da[part][ks], db0[ks] + soff, kIdesc, (part | ks) != 0);
+              tc::mma<true>(acc, da[part][ks] + aoff, db0[ks] + soff, kIdesc, (part | ks) != 0);
           tc::mma_commit(&empty[s]);
           tc::mma_commit(&accf[a]);
         }
@@ -579,62 +584,67 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
         zn[j] = (zn_have && jj < r) ? z[jj] : 0.f;
       }
     };
-    if (blockIdx.x < total) prefetch_z(blockIdx.x);
-    for (uint32_t w = blockIdx.x; w < total; w += gridDim.x, ++li) {
-      if (et < kPSlots) sslot[et] = slot_of(w, et);
-      // A: row i of slot s holds its z at K = s RN .. s RN + RN - 1 (kRParts BF16
-      // parts: hi = bf16(v), lo = bf16(v - hi); v - hi - lo is below 2^-16 |v|)
-      {
-        if (zn_have) {
-          float zv[kH];
+    // A of item w into buffer b: row i of slot s holds its z at K = s RN .. s RN + RN - 1
+    // (kRParts BF16 parts: hi = bf16(v), lo = bf16(v - hi); v - hi - lo is below 2^-16 |v|)
+    auto build_a = [&](uint32_t w, int b) {
+      if (et < kPSlots) sslot[b][et] = slot_of(w, et);
+      if (zn_have) {
+        float zv[kH];
 #pragma unroll
-          for (int j = 0; j < kH; ++j) zv[j] = zn[j];
+        for (int j = 0; j < kH; ++j) zv[j] = zn[j];
 #pragma unroll
-          for (int c8 = 0; c8 < kH / 8; ++c8) {  // 16-byte chunks of 8 values
-            uint32_t wp[kRParts][4];
+        for (int c8 = 0; c8 < kH / 8; ++c8) {  // 16-byte chunks of 8 values
+          uint32_t wp[kRParts][4];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              uint32_t w2[kRParts] = {};
+          for (int h = 0; h < 4; ++h) {
+            uint32_t w2[kRParts] = {};
 #pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                float v = zv[c8 * 8 + 2 * h + u];
+            for (int u = 0; u < 2; ++u) {
+              float v = zv[c8 * 8 + 2 * h + u];
 #pragma unroll
-                for (int part = 0; part < kRParts; ++part) {  // successive BF16 parts of the remainder
-                  const uint16_t b = bf16_rn(v);
-                  w2[part] |= (uint32_t)b << (16 * u);
-                  v -= bf16_val(b);
-                }
+              for (int part = 0; part < kRParts; ++part) {  // successive BF16 parts of the remainder
+                const uint16_t bb = bf16_rn(v);
+                w2[part] |= (uint32_t)bb << (16 * u);
+                v -= bf16_val(bb);
               }
-#pragma unroll
-              for (int part = 0; part < kRParts; ++part) wp[part][h] = w2[part];
             }
-            const int kc = (sa * RN + hf * kH) / 8 + c8;  // chunk index along K
 #pragma unroll
-            for (int part = 0; part < kRParts; ++part)
-              *reinterpret_cast<uint4*>(sA + part * P::kBytesApart + (kc / 8) * (kPTM * 128) +
-                                        sw128_off(ra, (kc % 8) * 16)) =
-                  make_uint4(wp[part][0], wp[part][1], wp[part][2], wp[part][3]);
+            for (int part = 0; part < kRParts; ++part) wp[part][h] = w2[part];
           }
+          const int kc = (sa * RN + hf * kH) / 8 + c8;  // chunk index along K
+#pragma unroll
+          for (int part = 0; part < kRParts; ++part)
+            *reinterpret_cast<uint4*>(sA + b * P::kBytesA + part * P::kBytesApart + (kc / 8) * (kPTM * 128) +
+                                      sw128_off(ra, (kc % 8) * 16)) =
+                make_uint4(wp[part][0], wp[part][1], wp[part][2], wp[part][3]);
         }
       }
       tc::fence_proxy_async_smem();
       tc::named_bar(1, 256);
-      if (et == 0) tc::mbar_arrive(&afull);
+      if (et == 0) tc::mbar_arrive(&afull[b]);
       if (w + gridDim.x < total) prefetch_z(w + gridDim.x);
-      const uint4 sl = sslot[q4];
+    };
+    if (blockIdx.x < total) {
+      prefetch_z(blockIdx.x);
+      build_a(blockIdx.x, 0);
+    }
+    for (uint32_t w = blockIdx.x; w < total; w += gridDim.x, ++li) {
+      // the next item's A into the other buffer: its last reader, item li - 1, has
+      // completed (this thread saw that item's last accumulator through accf)
+      if (w + gridDim.x < total) build_a(w + gridDim.x, (int)((li + 1) & 1));
+      const uint4 sl = sslot[li & 1][q4];
       const bool mine = (uint32_t)lane < sl.z;
       const uint16_t* qrow = mine ? Qh + (size_t)pair_q[sl.y + lane] * d : Qh;
-      // the item's centre rows, read by every pair of a slot: staged in shared memory
-      const bool mu_smem = d <= kRMuD;
-      if (mu_smem) {
-        for (int e = et; e < kPSlots * (d / 8); e += 256) {
-          const int j = e / (d / 8), c8 = e % (d / 8);
-          *reinterpret_cast<uint4*>(sMu + j * kRMuD + c8 * 8) =
-              __ldg(reinterpret_cast<const uint4*>(Mh + (size_t)sslot[j].x * d + c8 * 8));
-        }
-        tc::named_bar(1, 256);
-      }
-      const uint16_t* mrow = mu_smem ? sMu + q4 * kRMuD : Mh + (size_t)sl.x * d;
+      // the slot's centre row, the same for the warp's 32 pairs: lane l loads
+      // 16-byte piece l % 8 of the thread's 64 columns one chunk ahead, and
+      // every lane takes piece g8 from lane g8 by shuffles
+      const uint16_t* mrow = Mh + (size_t)sl.x * d;
+      uint4 mn = make_uint4(0, 0, 0, 0);
+      auto load_m = [&](int c) {
+        const int t = c * kRChunk + half * 64 + (lane & 7) * 8;
+        mn = (c < nch && t < d) ? __ldg(reinterpret_cast<const uint4*>(mrow + t)) : make_uint4(0, 0, 0, 0);
+      };
+      load_m(0);
       float acc = 0.f;
       // this thread's 64 coordinates of a chunk: q_b loaded one chunk ahead (the
       // warp's 32 pairs share mu_b, which stays in L1)
@@ -654,7 +664,9 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
         uint4 qv8[8];
 #pragma unroll
         for (int g8 = 0; g8 < 8; ++g8) qv8[g8] = qn[g8];
+        const uint4 mc = mn;
         load_q(c + 1);
+        load_m(c + 1);
         if (!failed && __any_sync(0xffffffffu, !tc::mbar_wait(&accf[a], (ci >> 1) & 1))) failed = true;
         if (failed) continue;
         tc::fence_after_sync();
@@ -668,14 +680,14 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acce[a]);
           }
-          if (mine) {
 #pragma unroll
-            for (int g4 = 0; g4 < 4; ++g4) {
-              const int g8 = hh * 4 + g4;
-              const int t = c * kRChunk + half * 64 + g8 * 8;
-              const uint4 mv = t < d ? *reinterpret_cast<const uint4*>(mrow + t) : make_uint4(0, 0, 0, 0);
+          for (int g4 = 0; g4 < 4; ++g4) {
+            const int g8 = hh * 4 + g4;
+            // every lane takes part in the shuffles; pieces past d are zero
+            const uint32_t mw[4] = {__shfl_sync(0xffffffffu, mc.x, g8), __shfl_sync(0xffffffffu, mc.y, g8),
+                                    __shfl_sync(0xffffffffu, mc.z, g8), __shfl_sync(0xffffffffu, mc.w, g8)};
+            if (mine) {
               const uint32_t qw[4] = {qv8[g8].x, qv8[g8].y, qv8[g8].z, qv8[g8].w};
-              const uint32_t mw[4] = {mv.x, mv.y, mv.z, mv.w};
 #pragma unroll
               for (int h = 0; h < 4; ++h) {  // zeros past d: q = mu = reconstruction = 0
                 const float e0 =

@@ -535,5 +535,11 @@ __global__ void k_to_bf16_rows(const float* __restrict__ X, size_t n, uint16_t* 
   if (i < n) out[i] = __bfloat16_as_ushort(__float2bfloat16_rn(X[i]));
 }
 
+// -bf16(x): the sign bit of the rounded value flipped (exact)
+__global__ void k_to_bf16_rows_neg(const float* __restrict__ X, size_t n, uint16_t* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (uint16_t)(__bfloat16_as_ushort(__float2bfloat16_rn(X[i])) ^ 0x8000u);
+}
+
 }  // namespace
 }  // namespace hntl

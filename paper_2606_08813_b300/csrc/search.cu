@@ -432,7 +432,7 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
                                                                (int)I.d, (int)nprobe, eps_dot, eps_norm, w.probe,
                                                                w.probe_d);
     }
-    HNTL_CUDA_TRY(cudaGetLastError());
+    HNTL_LAUNCH_CHECK("k_route_tc / k_route_refine");
     return HNTL_OK;
   }
   if (bf16) return fail(HNTL_EINVAL, "the precision form needs tensor-core routing (d a multiple of 8)");
@@ -447,25 +447,25 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
   }
   k_route_select<<<(nq + kSelWarps - 1) / kSelWarps, kSelWarps * 32, smem, st>>>(w.route_d, (int)nq, (int)I.G,
                                                                                   (int)nprobe, w.probe, w.probe_d);
-  HNTL_CUDA_TRY(cudaGetLastError());
+  HNTL_LAUNCH_CHECK("k_route_dist / k_route_select");
   return HNTL_OK;
 }
 
-template <int RN>
+template <int RN, bool kRho>
 int launch_project_tc_n(const Index& I, uint32_t nq, uint32_t P, const Ws& w, cudaStream_t st) {
   static thread_local int attr_dev = -1;
   if (attr_dev != I.device) {
-    HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project_tc<RN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project_tc<RN, kRho>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        ProjTc<RN>::kSmem));
     attr_dev = I.device;
   }
   // persistent: one CTA per SM at most, never more CTAs than work items can exist
   const size_t max_items = ((size_t)P / kPSlot + I.G + kPSlots - 1) / kPSlots;
   const unsigned grid = persistent_grid(std::min<size_t>(max_items, (size_t)I.num_sms));
-  k_project_tc<RN><<<grid, kPThreads, ProjTc<RN>::kSmem, st>>>(w.Qh, I.Mh, I.mapU, I.gram, (int)I.d, (int)I.r,
-                                                               w.slots, w.grp2_off + I.G, w.pair_q, w.pair_vn,
-                                                               w.zq, w.rhoq, I.d_err);
-  HNTL_CUDA_TRY(cudaGetLastError());
+  k_project_tc<RN, kRho><<<grid, kPThreads, ProjTc<RN>::kSmem, st>>>(
+      w.Qh, I.Mhn, I.mapU, I.gram, (int)I.d, (int)I.r, w.slots, w.grp2_off + I.G, w.pair_q, w.pair_vn, w.zq, w.rhoq,
+      I.d_err);
+  HNTL_LAUNCH_CHECK("k_project_tc");
   return HNTL_OK;
 }
 
@@ -483,7 +483,7 @@ int launch_resid_tc_n(const Index& I, uint32_t P, const Ws& w, cudaStream_t st) 
   const unsigned grid = persistent_grid(std::min<size_t>(max_items, (size_t)I.num_sms));
   k_resid_tc<RN><<<grid, kRThr, ResidTc<RN>::kSmem, st>>>(w.Qh, I.Mh, I.mapU, (int)I.d, (int)I.r, w.slots,
                                                           w.grp2_off + I.G, w.pair_q, w.zq, w.rhoq, I.d_err);
-  HNTL_CUDA_TRY(cudaGetLastError());
+  HNTL_LAUNCH_CHECK("k_resid_tc");
   return HNTL_OK;
 }
 
@@ -491,14 +491,14 @@ int launch_project_tc(const Index& I, uint32_t nq, uint32_t P, const Ws& w, cuda
   if (!I.tc_proj) return fail(HNTL_EINVAL, "the precision form needs tensor-core projection (d a multiple of 8)");
   int rc;
   if (I.r <= 16) {
-    if ((rc = launch_project_tc_n<16>(I, nq, P, w, st))) return rc;
+    if ((rc = launch_project_tc_n<16, false>(I, nq, P, w, st))) return rc;
     return launch_resid_tc_n<16>(I, P, w, st);
   }
   if (I.r <= 32) {
-    if ((rc = launch_project_tc_n<32>(I, nq, P, w, st))) return rc;
+    if ((rc = launch_project_tc_n<32, false>(I, nq, P, w, st))) return rc;
     return launch_resid_tc_n<32>(I, P, w, st);
   }
-  return launch_project_tc_n<64>(I, nq, P, w, st);  // r > 32: the Gram identity's rho_q
+  return launch_project_tc_n<64, true>(I, nq, P, w, st);  // r > 32: the Gram identity's rho_q
 }
 
 template <int RT, int kC>
@@ -767,12 +767,13 @@ int finalize_index(Index& I) {
   I.blk_z0 = static_cast<float2*>(alloc(sizeof(float2) * std::max<uint64_t>(I.n_blocks, 1)));
   if (bf16) {
     I.Mh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.d));
+    I.Mhn = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.d));
     I.Uh = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * I.G * I.r * I.d));
     I.crow = static_cast<float*>(alloc(sizeof(float) * I.n_blocks * kBlockRows));
     I.grain_rho_min = static_cast<float*>(alloc(sizeof(float) * I.G));
   }
   if (!I.d_err || !I.mnorm || !I.gram || !I.pos_of_id || !I.hrow || !I.blk_z0 ||
-      (bf16 && (!I.Mh || !I.Uh || !I.crow || !I.grain_rho_min)))
+      (bf16 && (!I.Mh || !I.Mhn || !I.Uh || !I.crow || !I.grain_rho_min)))
     return fail(HNTL_ENOMEM, "index: derived arrays");
   HNTL_CUDA_TRY(cudaMemset(I.d_err, 0, sizeof(int)));
   if (bf16) k_row_norms<true><<<(I.G * 32 + 255) / 256, 256>>>(I.M, (int)I.G, (int)I.d, I.mnorm);
@@ -780,6 +781,7 @@ int finalize_index(Index& I) {
   if (bf16) {
     const size_t n = (size_t)I.G * I.d, nu = (size_t)I.G * I.r * I.d;
     k_to_bf16_rows<<<(unsigned)((n + 255) / 256), 256>>>(I.M, n, I.Mh);
+    k_to_bf16_rows_neg<<<(unsigned)((n + 255) / 256), 256>>>(I.M, n, I.Mhn);
     k_to_bf16_rows<<<(unsigned)((nu + 255) / 256), 256>>>(I.U, nu, I.Uh);
     k_gram<<<I.G, 256>>>(I.Uh, (int)I.d, (int)I.r, I.gram);  // of the BF16 bases the precision form uses
     k_grain_rho_min<<<(I.G * 32 + 255) / 256, 256>>>(I.blk_rho_min, I.blk_off, (int)I.G, I.grain_rho_min);
