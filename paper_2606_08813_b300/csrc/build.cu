@@ -1035,7 +1035,7 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
       h_grp[g + 1] = h_grp[g] + (h_goff[g + 1] - h_goff[g] + kPairsPerGroup - 1) / kPairsPerGroup;
     HNTL_CUDA_TRY(cudaMemcpyAsync(grp_off, h_grp.data(), (G + 1) * 4, cudaMemcpyHostToDevice, st));
     size_t smem = (size_t)kPairsPerGroup * d * sizeof(float);
-    if (smem > 48 * 1024)
+    if (smem > 40 * 1024)  // the kernel's static shared memory counts against the default 48 KB too
       HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     unsigned grid = (unsigned)std::min<uint64_t>(h_grp[G] ? h_grp[G] : 1, 148 * 32);
     k_project<false><<<grid, 256, smem, st>>>(dX, M, I.U, (int)d, (int)r, (int)G, grp_off, goff, ids_g, Zg, rho_g);

@@ -649,7 +649,7 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
     if ((rc = launch_project_tc(I, nq, (uint32_t)P, w, st))) return rc;
   } else {
     size_t smem = (size_t)kPairsPerGroup * I.d * sizeof(float);
-    if (smem > 48 * 1024)
+    if (smem > 40 * 1024)  // the kernel's static shared memory counts against the default 48 KB too
       HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     unsigned grid = persistent_grid(std::min<size_t>((size_t)P / kPairsPerGroup + I.G, (size_t)I.num_sms * 16));
     k_project<false><<<grid, 256, smem, st>>>(Qd, I.M, I.U, (int)I.d, (int)I.r, (int)I.G, w.grp_off, w.pair_off,
