@@ -226,11 +226,12 @@ def stage_bytes(idx, rows_g, probe: np.ndarray, w: dict, batch: int):
     }
 
 
-def traffic_from_profiles(workload: str, stage: str):
+def traffic_from_profiles(workload: str, stage: str, batch: int):
     """DRAM bytes per launch of the kernels of `stage` on `workload`, from the
     committed ncu summary (profiles/ncu_traffic.json), when it was taken on the
     current source of those kernels; else None. Entries captured on a smaller
-    case carry the factor that scales them to a full launch."""
+    case either grow with the queries of a launch (captured_queries) or carry
+    the factor that scales them to a full launch of the batch they name."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         rec = json.load(open(p))[workload][stage]
@@ -238,6 +239,10 @@ def traffic_from_profiles(workload: str, stage: str):
             data = open(os.path.join(ROOT, "paper_2606_08813_b300", "csrc", src), "rb").read()
             if hashlib.sha256(data).hexdigest()[:16] != sha:
                 return None
+        if "captured_queries" in rec:  # traffic in proportion to the queries of a launch
+            return int(rec["dram_bytes_per_launch"] * batch / rec["captured_queries"])
+        if rec.get("captured_batch", batch) != batch:
+            return None
         return int(rec["dram_bytes_per_launch"] * rec.get("scale_to_full_launch", 1.0))
     except Exception:
         return None
@@ -765,7 +770,7 @@ def run_ours(a, world, rank, local):
             surv.append(hntl.search_survivors(gi, gi.workspace(0), B, C, nprobe).cpu().numpy())
     torch.cuda.synchronize()
     surv = np.concatenate(surv).astype(np.int64)
-    cap = max(8192, 32 * C)
+    cap = max(16384, 32 * C)
     surv_stats = {"mean": round(float(surv.mean()), 1), "p50": int(np.percentile(surv, 50)),
                   "p99": int(np.percentile(surv, 99)), "max": int(surv.max()),
                   "overflowed": int((surv > cap).sum()), "queries": int(len(surv))}
@@ -842,7 +847,7 @@ def run_ours(a, world, rank, local):
     if dom in mean_bytes:
         ach = mean_bytes[dom] / (per_launch_ms[dom] / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 4), "traffic": traffic_from_profiles(a.workload, dom), "peak_source": src,
+                "frac": round(ach / hbm, 4), "traffic": traffic_from_profiles(a.workload, dom, B), "peak_source": src,
                 "algorithmic_bytes_per_launch": int(mean_bytes[dom])}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
@@ -860,7 +865,7 @@ def run_ours(a, world, rank, local):
                    "nprobe": nprobe, "C": C, "k": k, "recall_at_10": None if rec != rec else round(rec, 4), "recall_queries": n_recall,
                    "recall_note": "skipped in profile mode" if a.profile_mode else "brute force, FP64 re-rank",
                    "sizes": w["sizes"], "l2": "no flush; per-step working set (probed coordinates, bases and "
-                   "gathered rows: about 2 GB a 4096-query batch at 10M rows) exceeds the 126 MB L2", "index_build_s": round(build_s, 2),
+                   "gathered rows: about 8 GB a 16384-query batch at 10M rows) exceeds the 126 MB L2", "index_build_s": round(build_s, 2),
                    "parallelism": f"replicas x{world}", "streams": a.streams,
                    "stage_timing": "CUDA events between stages, the same K batches on one stream",
                    "pool_survivors": surv_stats, "batch_latency_ms_p50": round(float(np.percentile(step_ms, 50)), 4),

@@ -327,7 +327,7 @@ int hntl_search_probes(const hntl_index* idx, const float* d_queries, uint32_t n
  * distance passed the query's pilot bound, before the exact C-smallest
  * selection) of the last hntl_search that used this workspace with the same
  * nq, C and nprobe; copied to d_counts (device, nq uint32) on `stream`. A
- * count above max(8192, 32 C) means the survivor list overflowed and the pool
+ * count above max(16384, 32 C) means the survivor list overflowed and the pool
  * was recomputed from every probed row. */
 int hntl_search_survivors(const hntl_index* idx, const void* d_ws, size_t ws_bytes, uint32_t nq, uint32_t C,
                           uint32_t nprobe, uint32_t* d_counts, void* stream);

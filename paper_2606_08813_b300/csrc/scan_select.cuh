@@ -39,7 +39,7 @@ constexpr int kPilotMin = 1024;   // fewest (when 4 C is smaller)
 constexpr int kTieCap = 1024;
 constexpr uint32_t kInfBits = 0x7F800000u;
 
-__host__ __device__ inline uint32_t survivor_cap(uint32_t C) { return C * 32 > 8192 ? C * 32 : 8192; }
+__host__ __device__ inline uint32_t survivor_cap(uint32_t C) { return C * 32 > 16384 ? C * 32 : 16384; }
 
 __device__ __forceinline__ unsigned long long pack2(float a, float b) {
   return ((unsigned long long)__float_as_uint(b) << 32) | __float_as_uint(a);

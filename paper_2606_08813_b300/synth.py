@@ -171,7 +171,7 @@ WORKLOADS = {
     "plain-1m-zipf": dict(n=1_000_000, d=768, n_clusters=1_024, sizes="zipf", G=1_024, r=32, nq=10_000,
                           batch=1_024, nprobe=16, C=100, k=10, seed=1002),
     "precision-10m": dict(n=10_000_000, d=768, n_clusters=4_096, sizes="equal", G=4_096, r=32, nq=100_000,
-                          batch=4_096, nprobe=32, C=200, k=10, seed=1003, precision="bf16-fp8"),
+                          batch=16_384, nprobe=32, C=200, k=10, seed=1003, precision="bf16-fp8"),
     "precision-2.5m": dict(n=2_500_000, d=768, n_clusters=1_024, sizes="equal", G=1_024, r=32, nq=10_240,
                            batch=1_024, nprobe=32, C=200, k=10, seed=1005, precision="bf16-fp8"),
     # about four grains per cluster, capacity-bounded at 1.05 N / G rows: grains are no longer the

@@ -119,8 +119,9 @@ def test_stage_bytes_by_hand():
 
 def test_profile_traffic_is_dropped_once_its_kernel_source_changes(tmp_path, monkeypatch):
     """A committed DRAM-traffic figure is used only while the kernel source it
-    was captured on is unchanged (scaled to a full launch when captured on a
-    smaller case)."""
+    was captured on is unchanged; captured on a smaller case it is scaled by
+    the launch's queries (traffic in proportion to them) or by a fixed factor
+    valid for the batch it names."""
     import hashlib
     import json
 
@@ -130,10 +131,15 @@ def test_profile_traffic_is_dropped_once_its_kernel_source_changes(tmp_path, mon
     src = b"// kernel source\n"
     (csrc / "k.cuh").write_bytes(src)
     sha = hashlib.sha256(src).hexdigest()[:16]
-    rec = {"w": {"scan": {"source_sha": {"k.cuh": sha}, "dram_bytes_per_launch": 1000, "scale_to_full_launch": 4.0}}}
+    rec = {"w": {"scan": {"source_sha": {"k.cuh": sha}, "dram_bytes_per_launch": 1000, "scale_to_full_launch": 4.0,
+                          "captured_batch": 64},
+                 "rerank": {"source_sha": {"k.cuh": sha}, "dram_bytes_per_launch": 3000, "captured_queries": 16}}}
     (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.traffic_from_profiles("w", "scan") == 4000
-    assert bench.traffic_from_profiles("w", "rerank") is None
+    assert bench.traffic_from_profiles("w", "scan", 64) == 4000
+    assert bench.traffic_from_profiles("w", "scan", 128) is None  # another batch: the factor does not hold
+    assert bench.traffic_from_profiles("w", "rerank", 64) == 12000  # 3000 bytes for 16 queries, 64 queries
+    assert bench.traffic_from_profiles("w", "route", 64) is None
     (csrc / "k.cuh").write_bytes(src + b"// changed\n")
-    assert bench.traffic_from_profiles("w", "scan") is None
+    assert bench.traffic_from_profiles("w", "scan", 64) is None
+    assert bench.traffic_from_profiles("w", "rerank", 64) is None
