@@ -71,6 +71,17 @@ extern "C" {
  * residual would make that grain's rows look close. HNTL_EINVAL with the
  * other forms. */
 #define HNTL_INT16_RESID_PRUNE 0x200u
+/* OR-ed into the precision of hntl_build_params with HNTL_PREC_BF16_FP8: the
+ * index also keeps the second BF16 part of every raw row, bf16(x - bf16(x))
+ * (N x d BF16 more; with the first part it carries 16 significant bits of x
+ * exactly), and the rerank (Mode B) takes two stages: the pool by distance to
+ * the BF16 rows, then its min(C, 2k) smallest (distance, id) by distance to
+ * the sum of both parts, of which the k smallest are returned. The library's
+ * own option (the paper's rerank is on the raw rows): it wins back the
+ * ranking the BF16 rows lose at about 2k more row reads per query.
+ * HNTL_EINVAL with the other forms and at load (index files hold one BF16
+ * part). */
+#define HNTL_RERANK_REFINE 0x400u
 
 /* The 16-bit form's quantisation of stored rows (Eq. 5, the steps above) as
  * the loader and the builder apply it, on host arrays: Z [N][r] FP32

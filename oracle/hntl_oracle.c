@@ -393,7 +393,10 @@ void or_balanced_assign(const float* X, int64_t n, int64_t d, const double* M, i
  *   2. per probed grain: v' = q - mu_g, z_q = U_g v', rho_q = ||v' - U_g^T z_q||^2;
  *   3. per row i of the grain (passing the filter): D = ||z_q - z_i||^2 + rho_q + rho_i;
  *   4. pool: the C smallest (D, id);
- *   5. rerank: exact ||q - x_id||^2 of the pool, the k smallest (dist, id).
+ *   5. rerank: exact ||q - x_id||^2 of the pool, the k smallest (dist, id);
+ *      with Xl (may be NULL; [N x d], the rows' second BF16 parts widened, in
+ *      original id order) the kref smallest (dist, id) of that rerank are
+ *      ranked again by ||q - (x_id + xl_id)||^2 and the k smallest kept.
  * Outputs: probe [nq x nprobe] grain ids, probe_d [nq x (nprobe+1)] routing
  * distances (the (nprobe+1)-th, or +inf, last); cand_id [nq x C] (0xFFFFFFFF
  * pad), cand_d [nq x (C+1)] (+inf pad; the (C+1)-th last); out_id [nq x k]
@@ -406,7 +409,7 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
                int64_t* out_id, double* out_d, int64_t mode, const int64_t* pos_of_id,
                const int32_t* grain_of_pos, const double* qdelta, const double* qdres,
                const int32_t* probe_in, const int16_t* Zc, int64_t i16_flags, const int16_t* qc_in,
-               const int32_t* qr_in, const float* pz_in, const float* prho_in) {
+               const int32_t* qr_in, const float* pz_in, const float* prho_in, const float* Xl, int64_t kref) {
 #pragma omp parallel
   {
     pair_t* route = (pair_t*)malloc(sizeof(pair_t) * (size_t)G);
@@ -570,6 +573,21 @@ void or_search(const float* M, const float* U, int64_t G, int64_t d, int64_t r, 
         }
       }
       qsort(rr, (size_t)m, sizeof(pair_t), pair_cmp);
+      if (Xl && mode == 0) {
+        /* second stage: the first kref again, on both parts of each row */
+        m = m < kref ? m : kref;
+        for (int64_t j = 0; j < m; ++j) {
+          const float* x = X + rr[j].key * d;
+          const float* xl = Xl + rr[j].key * d;
+          double s = 0.0;
+          for (int64_t t = 0; t < d; ++t) {
+            const double df = (double)q[t] - ((double)x[t] + (double)xl[t]);
+            s += df * df;
+          }
+          rr[j].dist = s;
+        }
+        qsort(rr, (size_t)m, sizeof(pair_t), pair_cmp);
+      }
       for (int64_t j = 0; j < k; ++j) {
         out_id[qi * k + j] = j < m ? rr[j].key : -1;
         out_d[qi * (k + 1) + j] = j < m ? rr[j].dist : INFINITY;

@@ -75,7 +75,7 @@ def _c():
             lib.or_lloyd.restype = I
             lib.or_balanced_assign.argtypes = [P, I, I, P, I, I, P]
             lib.or_search.argtypes = [P, P, I, I, I, P, P, P, P, P, P, P, P, I, I, I, I, P,
-                                      P, P, P, P, P, P, I, P, P, P, P, P, P, I, P, P, P, P]
+                                      P, P, P, P, P, P, I, P, P, P, P, P, P, I, P, P, P, P, P, I]
             lib.or_threads.restype = ctypes.c_int
             lib.or_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -236,7 +236,8 @@ def build_index(X, G: int, r: int, u, train_idx=None, max_iter: int = 25, keep_f
 
 
 def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=None, rho=None, precision="fp32",
-           mode: str = "B", probes=None, resid_prune: bool = False, query_codes=None, pair_proj=None):
+           mode: str = "B", probes=None, resid_prune: bool = False, query_codes=None, pair_proj=None,
+           refine: bool = False):
     """Mode B (default) or Mode A search of every query (see hntl_oracle.c or_search).
 
     probes (optional, [nq, nprobe] grain ids): replaces the centroid routing
@@ -269,7 +270,12 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
     query, centres and bases are rounded to BF16 for routing and projection,
     the scan reads the FP8 coordinates decoded and scaled (fp8_coords), and the
     rerank compares the FP32 query with BF16-rounded rows. X is the FP32 rows
-    in original id order; Z/rho override the index's coordinates."""
+    in original id order; Z/rho override the index's coordinates.
+
+    refine (precision form, Mode B): a second rerank stage. Each row also
+    has a second BF16 part, xl = bf16(x - bf16(x)); the min(C, 2k) smallest
+    (distance, id) of the BF16 rerank are ranked again by the distance to
+    bf16(x) + xl, and the k smallest of those are returned."""
     X = _f32(X)
     Q = _f32(Q)
     nq, d = Q.shape
@@ -279,6 +285,16 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
     M = _f32(idx["M"])
     U = _f32(idx["U"])
     Qp = None
+    Xlo = None
+    kref = 0
+    if refine:
+        if precision != "bf16-fp8" or mode != "B":  # X must be the FP32 rows
+            raise ValueError("refine applies to the precision form's Mode B rerank (precision='bf16-fp8')")
+        Xf = _f32(X)
+        # second BF16 part of each row, from the FP32 rows (X must be FP32 here)
+        Xlo = np.ascontiguousarray(bf16_to_f32(bf16_round(Xf - bf16_to_f32(bf16_round(Xf)).reshape(Xf.shape)))
+                                   .reshape(Xf.shape))
+        kref = min(C, 2 * k)
     if precision in ("bf16-fp8", "bf16-fp8-decoded"):
         # "bf16-fp8-decoded": idx["Z"] already holds decoded FP8 values and X BF16-rounded values
         M = bf16_to_f32(bf16_round(M)).reshape(M.shape)
@@ -342,7 +358,7 @@ def search(idx, X, Q, k: int, C: int, nprobe: int, attr=None, ranges=None, Z=Non
     _c().or_search(_p(M), _p(U), G, d, r, _p(off), _p(ids), _p(Zs), _p(rhos), _p(X), _p(attr_a), _p(Q), _p(Qp), nq,
                    k, C, nprobe, _p(rng), _p(probe), _p(probe_d), _p(cand_id), _p(cand_d), _p(out_id), _p(out_d),
                    1 if mode == "A" else 0, _p(pos_of_id), _p(grain_of_pos), _p(qdelta), _p(qdres), _p(pin),
-                   _p(Zc), 1 if resid_prune else 0, _p(qc_in), _p(qr_in), _p(pz), _p(prho))
+                   _p(Zc), 1 if resid_prune else 0, _p(qc_in), _p(qr_in), _p(pz), _p(prho), _p(Xlo), kref)
     return dict(probe=probe, probe_d=probe_d, cand_id=cand_id, cand_d=cand_d, out_id=out_id, out_d=out_d)
 
 

@@ -603,6 +603,17 @@ __global__ void k_to_bf16(const float* __restrict__ X, int64_t n, uint16_t* __re
   }
 }
 
+// The second BF16 part of each value, bf16(x - bf16(x)): bf16(x) + it carries
+// 16 significant bits of x, exactly (the refined rerank's rows).
+__global__ void k_to_bf16_lo(const float* __restrict__ X, int64_t n, uint16_t* __restrict__ Xl) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float x = X[i];
+    const float hi = __bfloat162float(__float2bfloat16_rn(x));
+    Xl[i] = __bfloat16_as_ushort(__float2bfloat16_rn(x - hi));
+  }
+}
+
 __global__ void k_fill_u32(uint32_t* p, int64_t n, uint32_t v) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
@@ -810,11 +821,14 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
   hntl_build_params P{};
   if (prm) P = *prm;
   const bool rprune = P.precision & HNTL_INT16_RESID_PRUNE;
-  const uint32_t precision = P.precision & ~HNTL_INT16_RESID_PRUNE;
+  const bool refine = P.precision & HNTL_RERANK_REFINE;
+  const uint32_t precision = P.precision & ~(HNTL_INT16_RESID_PRUNE | HNTL_RERANK_REFINE);
   if (precision != HNTL_PREC_FP32 && precision != HNTL_PREC_BF16_FP8 && precision != HNTL_PREC_INT16)
     return fail(HNTL_EINVAL, "bad precision");
   if (rprune && precision != HNTL_PREC_INT16)
     return fail(HNTL_EINVAL, "residual-saturation pruning applies to the 16-bit form only");
+  if (refine && precision != HNTL_PREC_BF16_FP8)
+    return fail(HNTL_EINVAL, "the refined rerank applies to the precision form only");
   if (precision == HNTL_PREC_BF16_FP8 && d % 8)  // BF16 rows move in 16-byte pieces
     return fail(HNTL_EINVAL, "the precision form needs d to be a multiple of 8");
   const uint32_t max_iter = P.max_iter ? P.max_iter : 10;
@@ -1077,9 +1091,10 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
     I.Z8b = static_cast<uint8_t*>(own(rows_pad * I.rp));
     I.scale = static_cast<float*>(own(G * 4));
     I.Xh = static_cast<uint16_t*>(own(N * d * 2));
+    if (refine) I.Xl = static_cast<uint16_t*>(own(N * d * 2));
   }
   if (!I.blk_off || !I.grain_rows || !I.blk_grain || !I.rho || !I.blk_rho_min || !I.ids || (I.has_attr && !I.attr_b) ||
-      (precision != HNTL_PREC_BF16_FP8 ? (!I.Zb || !I.X) : (!I.Z8b || !I.scale || !I.Xh))) {
+      (precision != HNTL_PREC_BF16_FP8 ? (!I.Zb || !I.X) : (!I.Z8b || !I.scale || !I.Xh || (refine && !I.Xl)))) {
     cleanup();
     return fail(HNTL_ENOMEM, "builder: index allocation failed");
   }
@@ -1121,6 +1136,7 @@ int build_index(const float* dX, uint64_t N, uint32_t d, uint32_t G, uint32_t r,
                                                                  (int64_t)I.n_blocks, I.blk_rho_min);
   if (I.X) HNTL_CUDA_TRY(cudaMemcpyAsync(I.X, dX, N * d * 4, cudaMemcpyDeviceToDevice, st));
   if (I.Xh) k_to_bf16<<<(unsigned)((N * d + 255) / 256), 256, 0, st>>>(dX, (int64_t)(N * d), I.Xh);
+  if (I.Xl) k_to_bf16_lo<<<(unsigned)((N * d + 255) / 256), 256, 0, st>>>(dX, (int64_t)(N * d), I.Xl);
   HNTL_CUDA_TRY(cudaGetLastError());
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {

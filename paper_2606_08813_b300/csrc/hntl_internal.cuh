@@ -69,6 +69,7 @@ struct Index {
   uint32_t* gid = nullptr;       // [n] a grain shard's original id of each local row (nullptr: not a shard)
   float* X = nullptr;            // [n][d] FP32 raw rows, id order
   uint16_t* Xh = nullptr;        // [n][d] BF16 raw rows, id order
+  uint16_t* Xl = nullptr;        // [n][d] second BF16 parts bf16(x - bf16(x)) (refined rerank), or nullptr
 
   // derived at load/build (finalize_index)
   float* mnorm = nullptr;        // [G] ||mu_g||^2 (of the BF16 centres in the precision form)

@@ -10,11 +10,16 @@ namespace {
 
 // One CTA per query: exact sum_t (q_t - x_t)^2 of every pool member (one warp
 // per member, 16-byte loads of the raw row), then the k smallest (dist, id).
-template <bool kBF16>
+// kRefine (BF16 rows with their second parts Xl = bf16(x - bf16(x))): the
+// min(C, 2k) smallest of that ranking are scored again against
+// bf16(x) + xl (exact in FP32: 16 significant bits) and the k smallest of
+// those are returned.
+template <bool kBF16, bool kRefine = false>
 __global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, const void* __restrict__ Xv, int d,
                                                 int C, int k, const uint32_t* __restrict__ cand_id,
                                                 int64_t* __restrict__ out_ids, float* __restrict__ out_d,
-                                                const uint32_t* __restrict__ qk, const uint32_t* __restrict__ qC) {
+                                                const uint32_t* __restrict__ qk, const uint32_t* __restrict__ qC,
+                                                const uint16_t* __restrict__ Xl = nullptr) {
   extern __shared__ float sq[];  // [d]
   __shared__ unsigned long long keys[kMaxC];
   const int q = blockIdx.x;
@@ -85,6 +90,42 @@ __global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, con
   }
   __syncthreads();
   bitonic_sort_u64(keys, n2);
+  if constexpr (kRefine) {
+    // second stage: the first min(C, 2k) again, on both BF16 parts of each row
+    const int m = min(C, 2 * k);
+    const int m2 = pow2_at_least(m);
+    const uint16_t* Xh = reinterpret_cast<const uint16_t*>(Xv);
+    for (int c = warp; c < m2; c += 8) {
+      unsigned long long key = ~0ull;
+      const uint32_t id = c < m ? (uint32_t)(keys[c] & 0xFFFFFFFFu) : kInvalidId;
+      if (c < m && keys[c] != ~0ull) {
+        const uint16_t* xh = Xh + (size_t)id * d;
+        const uint16_t* xl = Xl + (size_t)id * d;
+        float acc = 0.f;
+        for (int t = lane * 8; t < d; t += 256) {  // d % 8 == 0 in the precision form
+          const uint4 vh = __ldg(reinterpret_cast<const uint4*>(xh + t));
+          const uint4 vl = __ldg(reinterpret_cast<const uint4*>(xl + t));
+          const uint32_t wh[4] = {vh.x, vh.y, vh.z, vh.w}, wl[4] = {vl.x, vl.y, vl.z, vl.w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float x0 = __uint_as_float(wh[h] << 16) + __uint_as_float(wl[h] << 16);
+            const float x1 = __uint_as_float(wh[h] & 0xFFFF0000u) + __uint_as_float(wl[h] & 0xFFFF0000u);
+            const float a0 = sq[t + 2 * h] - x0, a1 = sq[t + 2 * h + 1] - x1;
+            acc = fmaf(a0, a0, acc);
+            acc = fmaf(a1, a1, acc);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        key = ((unsigned long long)__float_as_uint(acc) << 32) | id;
+      }
+      __syncwarp();
+      // every warp reads its own entries only, so they can be replaced in place
+      if (lane == 0) keys[c] = key;
+    }
+    __syncthreads();
+    bitonic_sort_u64(keys, m2);
+  }
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     unsigned long long kk = i < n2 ? keys[i] : ~0ull;
     bool ok = kk != ~0ull;

@@ -690,8 +690,13 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
     if (smem > 40 * 1024) {
       HNTL_CUDA_TRY(cudaFuncSetAttribute(k_rerank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       HNTL_CUDA_TRY(cudaFuncSetAttribute(k_rerank<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      HNTL_CUDA_TRY(
+          cudaFuncSetAttribute(k_rerank<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    if (I.precision == HNTL_PREC_BF16_FP8)
+    if (I.precision == HNTL_PREC_BF16_FP8 && I.Xl)  // refined: a second stage on both BF16 parts
+      k_rerank<true, true><<<nq, 256, smem, st>>>(Qd, I.Xh, (int)I.d, (int)C, (int)k, w.cand_id, out_ids, out_d, qk,
+                                                  qC, I.Xl);
+    else if (I.precision == HNTL_PREC_BF16_FP8)
       k_rerank<true><<<nq, 256, smem, st>>>(Qd, I.Xh, (int)I.d, (int)C, (int)k, w.cand_id, out_ids, out_d, qk, qC);
     else
       k_rerank<false><<<nq, 256, smem, st>>>(Qd, I.X, (int)I.d, (int)C, (int)k, w.cand_id, out_ids, out_d, qk, qC);

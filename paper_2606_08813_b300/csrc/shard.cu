@@ -174,11 +174,12 @@ int make_shard(const Index& S, const uint32_t* shard_of, uint32_t shard, int dev
   for (uint32_t& v : ids)
     if (v != kInvalidId) v = (uint32_t)(std::lower_bound(gid.begin(), gid.end(), v) - gid.begin());
   const uint64_t n_s = gid.size();
-  // raw rows of the shard, gathered on the source device
+  // raw rows of the shard (and their second BF16 parts), gathered on the source device
   const bool has_raw = S.X || S.Xh;
   const uint32_t units = S.Xh ? d : 2 * d;  // 16-bit units per raw row
-  std::vector<uint16_t> Xs(has_raw ? n_s * units : 0);
-  if (has_raw && n_s) {
+  auto gather = [&](const uint16_t* src, std::vector<uint16_t>& out) -> int {
+    out.assign(n_s * units, 0);
+    if (!n_s) return HNTL_OK;
     const uint64_t chunk = std::min<uint64_t>(n_s, 1u << 20);
     uint32_t* dgid = nullptr;
     uint16_t* dtmp = nullptr;
@@ -187,17 +188,26 @@ int make_shard(const Index& S, const uint32_t* shard_of, uint32_t shard, int dev
       cudaFree(dgid);
       return fail(HNTL_ENOMEM, "shard: staging");
     }
-    const uint16_t* src = S.Xh ? S.Xh : reinterpret_cast<const uint16_t*>(S.X);
     cudaError_t e = cudaMemcpy(dgid, gid.data(), n_s * 4, cudaMemcpyHostToDevice);
     for (uint64_t a = 0; a < n_s && e == cudaSuccess; a += chunk) {
       const uint64_t m = std::min<uint64_t>(chunk, n_s - a);
       const uint64_t blocks = std::min<uint64_t>((m * units + 255) / 256, 65535);
       k_gather_rows<<<(unsigned)blocks, 256>>>(src, dgid + a, m, units, dtmp);
-      e = cudaMemcpy(Xs.data() + a * units, dtmp, m * units * 2, cudaMemcpyDeviceToHost);
+      e = cudaMemcpy(out.data() + a * units, dtmp, m * units * 2, cudaMemcpyDeviceToHost);
     }
     cudaFree(dgid);
     cudaFree(dtmp);
     if (e != cudaSuccess) return fail(HNTL_ECUDA, std::string("shard: raw rows: ") + cudaGetErrorString(e));
+    return HNTL_OK;
+  };
+  std::vector<uint16_t> Xs, Xls;
+  if (has_raw) {
+    const int rc0 = gather(S.Xh ? S.Xh : reinterpret_cast<const uint16_t*>(S.X), Xs);
+    if (rc0) return rc0;
+  }
+  if (S.Xl) {
+    const int rc0 = gather(S.Xl, Xls);
+    if (rc0) return rc0;
   }
 
   I.device = device;
@@ -238,6 +248,7 @@ int make_shard(const Index& S, const uint32_t* shard_of, uint32_t shard, int dev
   if (S.dres && (rc = upload(I, &I.dres, dres.data(), G * 4))) return rc;
   if (S.has_attr && (rc = upload(I, &I.attr_b, attr.data(), attr.size() * 8))) return rc;
   if (S.Xh && (rc = upload(I, &I.Xh, Xs.data(), Xs.size() * 2))) return rc;
+  if (S.Xl && (rc = upload(I, &I.Xl, Xls.data(), Xls.size() * 2))) return rc;
   if (S.X && (rc = upload(I, &I.X, Xs.data(), Xs.size() * 2))) return rc;
   return finalize_index(I);
 }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libhntl.so")
 OK, EINVAL, ENOMEM, ECUDA, EIO, EFORMAT, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 PREC_FP32, PREC_BF16_FP8, PREC_INT16 = 0, 1, 2  # INT16: the 16-bit form, built at load from an FP32 file
 INT16_RESID_PRUNE = 0x200  # OR into PREC_INT16: the library's residual-saturation pruning option
+RERANK_REFINE = 0x400  # OR into PREC_BF16_FP8 at build: second BF16 parts of the rows, two-stage rerank
 LOAD_NO_RAW = 0x100  # OR into the precision of Index.load: no raw rows on the device (Mode A only)
 INVALID_ID = 0xFFFFFFFF
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EIO: "EIO", EFORMAT: "EFORMAT",

@@ -144,3 +144,40 @@ def test_builder_precision_form(hntl):
     bf, _, _ = O.brute_force(Xn, Q.numpy(), 10)
     rec = np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids.cpu().numpy().tolist(), bf.tolist())])
     assert rec >= 0.95
+
+
+def test_refined_rerank_matches_oracle_and_recovers_recall(hntl):
+    """Precision form built on the GPU with HNTL_RERANK_REFINE: the pool is the
+    precision form's, the top k comes from the two-stage rerank (the min(C, 2k)
+    best by distance to the BF16 rows, ranked again on both BF16 parts). Pool
+    and top k against the oracle's refined search of the exported index (the
+    FP32 rows give both parts), under the gap rule; recall against brute force
+    at least the unrefined form's; one shard of the index returns the same."""
+    n, d, G, r, nq = 60_000, 128, 48, 16, 256
+    k, C, nprobe = 10, 100, 6
+    m = synth.make_cluster_model(n, d, 12, seed=731)
+    X, _ = synth.sample_points(m, 732)
+    Q, _ = synth.sample_queries(m, nq, 733)
+    u = synth.uniforms(G, 734).numpy()
+    gi = hntl.Index.build(X.cuda(), G, r, precision=hntl.PREC_BF16_FP8 | hntl.RERANK_REFINE, u=u, seed=734)
+    g0 = hntl.Index.build(X.cuda(), G, r, precision=hntl.PREC_BF16_FP8, u=u, seed=734)
+    Qd = Q.cuda()
+    ids, dist, pid, pd, probe = gi.search(Qd, k, C, nprobe, return_pool=True, return_probe=True)
+    ids0, _ = g0.search(Qd, k, C, nprobe)
+    torch.cuda.synchronize()
+    assert hntl.device_status(gi) == 0
+    gpu = dict(ids=ids.cpu().numpy(), dist=dist.cpu().numpy(), pool_ids=pid.cpu().numpy().view(np.uint32),
+               pool_d=pd.cpu().numpy(), probe=probe.cpu().numpy())
+    host = gi.export()
+    Xn, Qn = X.numpy(), Q.numpy()
+    ora = O.search(host, Xn, Qn, k, C, nprobe, precision="bf16-fp8", Z=host["Z"], refine=True)
+    st = compare_search(gpu, ora, k, C, nprobe)
+    assert st["checked"] >= 0.8 * nq, st
+    bf, _, _ = O.brute_force(Xn, Qn, k)
+    rec = lambda a: np.mean([len(set(x.tolist()) & set(y.tolist())) / k for x, y in zip(a, bf)])
+    r_ref, r_plain = rec(gpu["ids"]), rec(ids0.cpu().numpy())
+    print("recall@10 refined", r_ref, "BF16 rows", r_plain)
+    assert r_ref >= r_plain
+    one = hntl.ShardedIndex(gi, 1)
+    a = one.shards[0].search(Qd, k, C, nprobe)
+    assert torch.equal(a[0], ids) and torch.equal(a[1], dist)

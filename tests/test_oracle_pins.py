@@ -874,3 +874,48 @@ def test_sharded_search_reduces_to_plain_and_to_brute_force():
     ib, db, _ = O.sharded_search(idx, X, Q, 10, 40, 4, sog)
     assert (db <= plain["out_d"][:, :10] + 1e-12).all()
     assert (db < plain["out_d"][:, :10] - 1e-9).any() or np.array_equal(ib, plain["out_id"])
+
+
+# ---------------------------------------------------------------- refined rerank (precision form)
+
+
+def _one_grain_index(X, r):
+    return partition_index(X, np.zeros(len(X), dtype=np.int64), 1, r)
+
+
+def test_refined_rerank_hand_fixture():
+    """Rows (1 + 3 2^-10, 0) and (1 + 2^-10, 0), query at the origin: both round
+    to (1, 0) in BF16, so the BF16 rerank ties them at distance 1 and keeps
+    the lower id (row 0). Their second BF16 parts are 3 2^-10 and 2^-10
+    exactly, so the refined stage (min(C, 2k) = 2 rows) orders them by their
+    exact distances and returns row 1 at (1 + 2^-10)^2."""
+    X = np.array([[1 + 3 * 2.0 ** -10, 0.0], [1 + 2.0 ** -10, 0.0]], dtype=np.float32)
+    Q = np.zeros((1, 2), dtype=np.float32)
+    idx = _one_grain_index(X, 1)
+    plain = O.search(idx, X, Q, 1, 2, 1, precision="bf16-fp8")
+    ref = O.search(idx, X, Q, 1, 2, 1, precision="bf16-fp8", refine=True)
+    assert plain["out_id"][0].tolist() == [0] and plain["out_d"][0, 0] == 1.0
+    assert ref["out_id"][0].tolist() == [1] and ref["out_d"][0, 0] == (1 + 2.0 ** -10) ** 2
+
+
+def test_refined_rerank_reduces_to_plain_and_to_brute_force():
+    """Rows exactly representable in BF16 have a zero second part: the refined
+    rerank returns the BF16 rerank's ids and distances. Rows of 16 significant
+    bits are exactly the sum of their two parts; with C = N <= 2k the refined
+    stage sees every row and returns brute force's ids and distances."""
+    rng = np.random.default_rng(21)
+    Xb = O.bf16_to_f32(O.bf16_round(rng.standard_normal((300, 16)).astype(np.float32))).reshape(300, 16)
+    Q = rng.standard_normal((5, 16)).astype(np.float32)
+    idx = _one_grain_index(Xb, 4)
+    a = O.search(idx, Xb, Q, 10, 40, 1, precision="bf16-fp8")
+    b = O.search(idx, Xb, Q, 10, 40, 1, precision="bf16-fp8", refine=True)
+    np.testing.assert_array_equal(a["out_id"], b["out_id"])
+    np.testing.assert_array_equal(a["out_d"][:, :10], b["out_d"][:, :10])
+    # 16 significant bits: the sign, the exponent and the top 15 of the 23 stored mantissa bits
+    X16 = (rng.standard_normal((16, 8)).astype(np.float32).view(np.uint32) & np.uint32(0xFFFFFF00)).view(np.float32)
+    Q16 = rng.standard_normal((4, 8)).astype(np.float32)
+    idx16 = _one_grain_index(X16, 2)
+    c = O.search(idx16, X16, Q16, 8, 16, 1, precision="bf16-fp8", refine=True)
+    bf, bd, _ = O.brute_force(X16, Q16, 8)
+    np.testing.assert_array_equal(c["out_id"], bf)
+    np.testing.assert_allclose(c["out_d"][:, :8], bd, rtol=1e-12)
