@@ -386,24 +386,25 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
 //   warp 0     TMA producer: per chunk, 2 boxes per slot into a stage ring.
 //   warp 1     one thread issues the MMAs into one of two TMEM accumulators.
 //   warps 2-9  epilogue: warp w reads lane quarter w % 4 (32 pairs), columns
-//              64 (w - 2) / 4 .. + 63 of each chunk. The A operand is double
-//              buffered: at the start of each item these warps write the
-//              next item's A (its z loaded during the item before), so the
-//              MMAs run on from one item into the next.
+//              64 (w - 2) / 4 .. + 63 of each chunk; it also writes the A
+//              operand of each item before the item's MMAs.
 constexpr int kRThr = 320;
 constexpr int kRStg = 3;
 constexpr int kRChunk = 128;  // coordinates per MMA (N)
 
+constexpr int kRMuD = 1024;  // centre rows of an item are staged in shared memory up to this d
 constexpr int kRParts = 2;   // BF16 parts of z (hi, lo: 16 significant bits)
 
 template <int RN>
 struct ResidTc {
   static constexpr int kK = kPSlots * RN;                       // A's K: the 4 slots' basis rows
   static constexpr uint32_t kBytesApart = kPTM * kK * 2;         // one part of A (128 rows x kK BF16)
-  static constexpr uint32_t kBytesA = kRParts * kBytesApart;     // one A buffer
   static constexpr uint32_t kBytesSlot = 2 * RN * 128;           // one slot's 2 boxes of a chunk
   static constexpr uint32_t kStage = kPSlots * kBytesSlot;
-  static constexpr int kSmem = 2 * kBytesA + kRStg * kStage + 1024;
+  static constexpr uint32_t kBytesMu = kPSlots * kRMuD * 2;     // the item's 4 BF16 centre rows
+  static constexpr uint32_t kQRow = 144;                         // a pair's 64 query values, padded
+  static constexpr uint32_t kBytesQ = 8 * 32 * kQRow;            // per epilogue warp, its 32 rows
+  static constexpr int kSmem = kRParts * kBytesApart + kRStg * kStage + kBytesMu + kBytesQ + 1024;
   static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 };
 
@@ -421,10 +422,12 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
   constexpr uint32_t kIdesc = tc::idesc_f32acc_bmn(1u, kPTM, kRChunk);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = smem;                            // [buffer][kRParts][kAtomsK][128 rows x 128 B]
-  uint8_t* sB = smem + 2 * P::kBytesA;           // [stage][slot][2 boxes][RN rows x 128 B]
-  __shared__ __align__(8) uint64_t full[kRStg], empty[kRStg], accf[2], acce[2], afull[2], fin;
-  __shared__ uint4 sslot[2][kPSlots];
+  uint8_t* sA = smem;                            // [kRParts][kAtomsK][128 rows x 128 B]
+  uint8_t* sB = smem + kRParts * P::kBytesApart; // [stage][slot][2 boxes][RN rows x 128 B]
+  uint16_t* sMu = reinterpret_cast<uint16_t*>(sB + kRStg * P::kStage);  // [slot][d] when d <= kRMuD
+  uint8_t* sQall = reinterpret_cast<uint8_t*>(sMu) + P::kBytesMu;        // [epilogue warp][32 rows][kQRow]
+  __shared__ __align__(8) uint64_t full[kRStg], empty[kRStg], accf[2], acce[2], afull, fin;
+  __shared__ uint4 sslot[kPSlots];
   __shared__ float sred[kPTM];
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
@@ -440,8 +443,7 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
       tc::mbar_init(&accf[a], 1);
       tc::mbar_init(&acce[a], 8);
     }
-    tc::mbar_init(&afull[0], 1);
-    tc::mbar_init(&afull[1], 1);
+    tc::mbar_init(&afull, 1);
     tc::mbar_init(&fin, 1);
     s_fail = 0;
     s_it_prod = s_it_mma = 0;
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
   // output nobody reads.
   for (uint32_t e = tid; e < (uint32_t)(kRStg * P::kStage / 16); e += kRThr)
     *reinterpret_cast<uint4*>(sB + (size_t)e * 16) = make_uint4(0, 0, 0, 0);
-  for (uint32_t e = tid; e < (uint32_t)(2 * P::kBytesA / 16); e += kRThr)
+  for (uint32_t e = tid; e < (uint32_t)(kRParts * P::kBytesApart / 16); e += kRThr)
     *reinterpret_cast<uint4*>(sA + (size_t)e * 16) = make_uint4(0, 0, 0, 0);
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -512,7 +514,7 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
       // every MMA's operand descriptors, once: A per (part, K step); B per K step
       // for stage 0 (another stage adds its byte offset / 16 to the start field)
       constexpr int kKS = P::kK / 16;
-      uint64_t da[kRParts][kKS], db0[kKS];  // A of buffer 0; buffer 1 adds kBytesA / 16
+      uint64_t da[kRParts][kKS], db0[kKS];
 #pragma unroll
       for (int part = 0; part < kRParts; ++part)
 #pragma unroll
@@ -524,12 +526,11 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
         db0[ks] = tc::desc_sw128_mn(tc::smem_u32(sB) + (ks / (RN / 16)) * P::kBytesSlot + (ks % (RN / 16)) * 2048,
                                     RN * 128);
       for (uint32_t w = blockIdx.x; w < total && ok; w += gridDim.x, ++li) {
-        if (!tc::mbar_wait(&afull[li & 1], (li >> 1) & 1)) {  // this item's A operand is written
+        if (!tc::mbar_wait(&afull, li & 1)) {  // this item's A operand is written
           ok = false;
           break;
         }
         tc::fence_after_sync();
-        const uint64_t aoff = (li & 1) ? (uint64_t)(P::kBytesA >> 4) : 0;
         for (int c = 0; c < nch; ++c, ++it, ++ci) {
           const int s = (int)(it % kRStg), a = (int)(ci & 1);
           if (ci >= 2 && !tc::mbar_wait(&acce[a], ((ci >> 1) - 1) & 1)) {
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
           for (int part = 0; part < kRParts; ++part)
 #pragma unroll
             for (int ks = 0; ks < kKS; ++ks)
-              tc::mma<true>(acc, da[part][ks] + aoff, db0[ks] + soff, kIdesc, (part | ks) != 0);
+              tc::mma<true>(acc, da[part][ks], db0[ks] + soff, kIdesc, (part | ks) != 0);
           tc::mma_commit(&empty[s]);
           tc::mma_commit(&accf[a]);
         }
@@ -584,89 +585,94 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
         zn[j] = (zn_have && jj < r) ? z[jj] : 0.f;
       }
     };
-    // A of item w into buffer b: row i of slot s holds its z at K = s RN .. s RN + RN - 1
-    // (kRParts BF16 parts: hi = bf16(v), lo = bf16(v - hi); v - hi - lo is below 2^-16 |v|)
-    auto build_a = [&](uint32_t w, int b) {
-      if (et < kPSlots) sslot[b][et] = slot_of(w, et);
-      if (zn_have) {
-        float zv[kH];
+    if (blockIdx.x < total) prefetch_z(blockIdx.x);
+    for (uint32_t w = blockIdx.x; w < total; w += gridDim.x, ++li) {
+      if (et < kPSlots) sslot[et] = slot_of(w, et);
+      // A: row i of slot s holds its z at K = s RN .. s RN + RN - 1 (kRParts BF16
+      // parts: hi = bf16(v), lo = bf16(v - hi); v - hi - lo is below 2^-16 |v|)
+      {
+        if (zn_have) {
+          float zv[kH];
 #pragma unroll
-        for (int j = 0; j < kH; ++j) zv[j] = zn[j];
+          for (int j = 0; j < kH; ++j) zv[j] = zn[j];
 #pragma unroll
-        for (int c8 = 0; c8 < kH / 8; ++c8) {  // 16-byte chunks of 8 values
-          uint32_t wp[kRParts][4];
+          for (int c8 = 0; c8 < kH / 8; ++c8) {  // 16-byte chunks of 8 values
+            uint32_t wp[kRParts][4];
 #pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            uint32_t w2[kRParts] = {};
+            for (int h = 0; h < 4; ++h) {
+              uint32_t w2[kRParts] = {};
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              float v = zv[c8 * 8 + 2 * h + u];
+              for (int u = 0; u < 2; ++u) {
+                float v = zv[c8 * 8 + 2 * h + u];
 #pragma unroll
-              for (int part = 0; part < kRParts; ++part) {  // successive BF16 parts of the remainder
-                const uint16_t bb = bf16_rn(v);
-                w2[part] |= (uint32_t)bb << (16 * u);
-                v -= bf16_val(bb);
+                for (int part = 0; part < kRParts; ++part) {  // successive BF16 parts of the remainder
+                  const uint16_t b = bf16_rn(v);
+                  w2[part] |= (uint32_t)b << (16 * u);
+                  v -= bf16_val(b);
+                }
               }
+#pragma unroll
+              for (int part = 0; part < kRParts; ++part) wp[part][h] = w2[part];
             }
+            const int kc = (sa * RN + hf * kH) / 8 + c8;  // chunk index along K
 #pragma unroll
-            for (int part = 0; part < kRParts; ++part) wp[part][h] = w2[part];
+            for (int part = 0; part < kRParts; ++part)
+              *reinterpret_cast<uint4*>(sA + part * P::kBytesApart + (kc / 8) * (kPTM * 128) +
+                                        sw128_off(ra, (kc % 8) * 16)) =
+                  make_uint4(wp[part][0], wp[part][1], wp[part][2], wp[part][3]);
           }
-          const int kc = (sa * RN + hf * kH) / 8 + c8;  // chunk index along K
-#pragma unroll
-          for (int part = 0; part < kRParts; ++part)
-            *reinterpret_cast<uint4*>(sA + b * P::kBytesA + part * P::kBytesApart + (kc / 8) * (kPTM * 128) +
-                                      sw128_off(ra, (kc % 8) * 16)) =
-                make_uint4(wp[part][0], wp[part][1], wp[part][2], wp[part][3]);
         }
       }
       tc::fence_proxy_async_smem();
       tc::named_bar(1, 256);
-      if (et == 0) tc::mbar_arrive(&afull[b]);
+      if (et == 0) tc::mbar_arrive(&afull);
       if (w + gridDim.x < total) prefetch_z(w + gridDim.x);
-    };
-    if (blockIdx.x < total) {
-      prefetch_z(blockIdx.x);
-      build_a(blockIdx.x, 0);
-    }
-    for (uint32_t w = blockIdx.x; w < total; w += gridDim.x, ++li) {
-      // the next item's A into the other buffer: its last reader, item li - 1, has
-      // completed (this thread saw that item's last accumulator through accf)
-      if (w + gridDim.x < total) build_a(w + gridDim.x, (int)((li + 1) & 1));
-      const uint4 sl = sslot[li & 1][q4];
+      const uint4 sl = sslot[q4];
       const bool mine = (uint32_t)lane < sl.z;
-      const uint16_t* qrow = mine ? Qh + (size_t)pair_q[sl.y + lane] * d : Qh;
-      // the slot's centre row, the same for the warp's 32 pairs: lane l loads
-      // 16-byte piece l % 8 of the thread's 64 columns one chunk ahead, and
-      // every lane takes piece g8 from lane g8 by shuffles
-      const uint16_t* mrow = Mh + (size_t)sl.x * d;
-      uint4 mn = make_uint4(0, 0, 0, 0);
-      auto load_m = [&](int c) {
-        const int t = c * kRChunk + half * 64 + (lane & 7) * 8;
-        mn = (c < nch && t < d) ? __ldg(reinterpret_cast<const uint4*>(mrow + t)) : make_uint4(0, 0, 0, 0);
-      };
-      load_m(0);
+      // the warp's 32 query rows move by coalesced loads: load i brings 16-byte
+      // piece lane % 8 of row 4 i + lane / 8 (four whole 128-byte lines a load),
+      // and a pass through this warp's shared buffer hands every lane its own row
+      uint8_t* sQ = sQall + (warp - 2) * (32 * P::kQRow);
+      uint32_t qrow4[8];  // the rows this lane loads, as query indices (~0u: no pair)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint32_t rw = 4u * i + (lane >> 3);
+        qrow4[i] = rw < sl.z ? pair_q[sl.y + rw] : ~0u;
+      }
+      // the item's centre rows, read by every pair of a slot: staged in shared memory
+      const bool mu_smem = d <= kRMuD;
+      if (mu_smem) {
+        for (int e = et; e < kPSlots * (d / 8); e += 256) {
+          const int j = e / (d / 8), c8 = e % (d / 8);
+          *reinterpret_cast<uint4*>(sMu + j * kRMuD + c8 * 8) =
+              __ldg(reinterpret_cast<const uint4*>(Mh + (size_t)sslot[j].x * d + c8 * 8));
+        }
+        tc::named_bar(1, 256);
+      }
+      const uint16_t* mrow = mu_smem ? sMu + q4 * kRMuD : Mh + (size_t)sl.x * d;
       float acc = 0.f;
-      // this thread's 64 coordinates of a chunk: q_b loaded one chunk ahead (the
-      // warp's 32 pairs share mu_b, which stays in L1)
+      // the 64 coordinates of a chunk this warp handles, loaded one chunk ahead
       uint4 qn[8];
       auto load_q = [&](int c) {
-        const int t0 = c * kRChunk + half * 64;
+        const int t = c * kRChunk + half * 64 + (lane & 7) * 8;
 #pragma unroll
-        for (int g8 = 0; g8 < 8; ++g8) {
-          const int t = t0 + g8 * 8;
-          qn[g8] = (mine && c < nch && t < d) ? __ldg(reinterpret_cast<const uint4*>(qrow + t))
-                                              : make_uint4(0, 0, 0, 0);
-        }
+        for (int i = 0; i < 8; ++i)
+          qn[i] = (qrow4[i] != ~0u && c < nch && t < d)
+                      ? __ldg(reinterpret_cast<const uint4*>(Qh + (size_t)qrow4[i] * d + t))
+                      : make_uint4(0, 0, 0, 0);
       };
       load_q(0);
       for (int c = 0; c < nch; ++c, ++ci) {
         const int a = (int)(ci & 1);
         uint4 qv8[8];
+        __syncwarp();  // every lane has read the previous chunk's rows
 #pragma unroll
-        for (int g8 = 0; g8 < 8; ++g8) qv8[g8] = qn[g8];
-        const uint4 mc = mn;
+        for (int i = 0; i < 8; ++i)
+          *reinterpret_cast<uint4*>(sQ + (4 * i + (lane >> 3)) * P::kQRow + (lane & 7) * 16) = qn[i];
+        __syncwarp();
+#pragma unroll
+        for (int g8 = 0; g8 < 8; ++g8) qv8[g8] = *reinterpret_cast<const uint4*>(sQ + lane * P::kQRow + g8 * 16);
         load_q(c + 1);
-        load_m(c + 1);
         if (!failed && __any_sync(0xffffffffu, !tc::mbar_wait(&accf[a], (ci >> 1) & 1))) failed = true;
         if (failed) continue;
         tc::fence_after_sync();
@@ -680,14 +686,14 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acce[a]);
           }
+          if (mine) {
 #pragma unroll
-          for (int g4 = 0; g4 < 4; ++g4) {
-            const int g8 = hh * 4 + g4;
-            // every lane takes part in the shuffles; pieces past d are zero
-            const uint32_t mw[4] = {__shfl_sync(0xffffffffu, mc.x, g8), __shfl_sync(0xffffffffu, mc.y, g8),
-                                    __shfl_sync(0xffffffffu, mc.z, g8), __shfl_sync(0xffffffffu, mc.w, g8)};
-            if (mine) {
+            for (int g4 = 0; g4 < 4; ++g4) {
+              const int g8 = hh * 4 + g4;
+              const int t = c * kRChunk + half * 64 + g8 * 8;
+              const uint4 mv = t < d ? *reinterpret_cast<const uint4*>(mrow + t) : make_uint4(0, 0, 0, 0);
               const uint32_t qw[4] = {qv8[g8].x, qv8[g8].y, qv8[g8].z, qv8[g8].w};
+              const uint32_t mw[4] = {mv.x, mv.y, mv.z, mv.w};
 #pragma unroll
               for (int h = 0; h < 4; ++h) {  // zeros past d: q = mu = reconstruction = 0
                 const float e0 =
