@@ -166,10 +166,10 @@ __global__ void k_bucket_count(const int32_t* __restrict__ probe, int n, uint32_
 }
 
 // Single CTA: exclusive scans over grains. Offsets of the grain-major pair
-// lists, of the 8-pair groups and of the 32-pair slots, and the slot table
-// {grain, first pair, pairs} used by the tensor-core projection (slots ==
-// nullptr skips it); the tensor-core scan's work items {grain, first block,
-// blocks} over the probed grains (scan_items == nullptr skips them).
+// lists, of the projection groups and of the 32-pair slots, and of the
+// tensor-core scan's work items over the probed grains (scan_items ==
+// nullptr skips them); k_bucket_fill then writes the slot table {grain,
+// first pair, pairs} and the work items {grain, first block, blocks}.
 __global__ void __launch_bounds__(1024) k_bucket_scan(const uint32_t* __restrict__ gcnt,
                                                       int G, uint32_t* __restrict__ pair_off,
                                                       uint32_t* __restrict__ grp_off,
@@ -250,21 +250,25 @@ __global__ void __launch_bounds__(1024) k_bucket_scan(const uint32_t* __restrict
     slot_off[G] = s_tot.z;
     if (scan_items) scan_off[G] = s_tot.w;
   }
-  __syncthreads();
+}
+
+// One thread per grain: the slot table and the scan work items from the
+// offsets k_bucket_scan wrote (spread over the device rather than one CTA).
+__global__ void k_bucket_fill(int G, const uint32_t* __restrict__ pair_off, const uint32_t* __restrict__ slot_off,
+                              uint4* __restrict__ slots, const uint32_t* __restrict__ blk_off,
+                              const uint32_t* __restrict__ scan_off, uint4* __restrict__ scan_items) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
   if (slots) {
-    for (int g = threadIdx.x; g < G; g += 1024) {
-      const uint32_t p0 = pair_off[g], cnt = pair_off[g + 1] - p0, i0 = slot_off[g];
-      for (uint32_t j = 0; j * kPSlot < cnt; ++j)
-        slots[i0 + j] = make_uint4((uint32_t)g, p0 + j * kPSlot, min((uint32_t)kPSlot, cnt - j * kPSlot), 0u);
-    }
+    const uint32_t p0 = pair_off[g], cnt = pair_off[g + 1] - p0, i0 = slot_off[g];
+    for (uint32_t j = 0; j * kPSlot < cnt; ++j)
+      slots[i0 + j] = make_uint4((uint32_t)g, p0 + j * kPSlot, min((uint32_t)kPSlot, cnt - j * kPSlot), 0u);
   }
   if (scan_items) {
-    for (int g = threadIdx.x; g < G; g += 1024) {
-      const uint32_t i0 = scan_off[g], n = scan_off[g + 1] - i0, bk0 = blk_off[g], nbk = blk_off[g + 1] - bk0;
-      for (uint32_t j = 0; j < n; ++j)
-        scan_items[i0 + j] =
-            make_uint4((uint32_t)g, bk0 + j * kSTBlocks, min((uint32_t)kSTBlocks, nbk - j * kSTBlocks), 0u);
-    }
+    const uint32_t i0 = scan_off[g], n = scan_off[g + 1] - i0, bk0 = blk_off[g], nbk = blk_off[g + 1] - bk0;
+    for (uint32_t j = 0; j < n; ++j)
+      scan_items[i0 + j] =
+          make_uint4((uint32_t)g, bk0 + j * kSTBlocks, min((uint32_t)kSTBlocks, nbk - j * kSTBlocks), 0u);
   }
 }
 
@@ -642,6 +646,9 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
   k_bucket_count<<<(P + 255) / 256, 256, 0, st>>>(w.probe, P, w.gcnt);
   k_bucket_scan<<<1, 1024, 0, st>>>(w.gcnt, (int)I.G, w.pair_off, w.grp_off, w.grp2_off, w.slots, I.blk_off,
                                     w.scan_off, w.scan_items);
+  if (w.slots || w.scan_items)
+    k_bucket_fill<<<(I.G + 255) / 256, 256, 0, st>>>((int)I.G, w.pair_off, w.grp2_off, w.slots, I.blk_off, w.scan_off,
+                                                     w.scan_items);
   k_bucket_scatter<<<(P + 255) / 256, 256, 0, st>>>(w.probe, (int)nq, (int)nprobe, w.pair_off, w.gcur, w.pair_q,
                                                     w.pair_p, w.pair_of, w.probe_d, w.pair_vn);
   mark(2);
