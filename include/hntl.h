@@ -462,9 +462,12 @@ int hntl_router_route(hntl_router* router, const hntl_index* idx, const float* d
 /* ---- continuous-batching server (the library's addition; the paper serves
  * one query at a time on a CPU) ----
  * A worker thread batches admitted requests as they arrive and runs each batch
- * as one captured CUDA graph (gather from the device slot table, the whole
- * Mode B search with each query's own k and C, result copy to pinned memory)
- * on one of three lanes, so batches run while the next one forms. A
+ * as one captured CUDA graph (gather of its rows from the slot table, the
+ * whole Mode B search with each query's own k and C, result copy to pinned
+ * memory). The slot table is mapped pinned host memory: a submission stores
+ * its rows there with no CUDA call, and the gather reads them over the host
+ * link, so admitting a request never waits behind a running batch. Batches run
+ * on one of three lanes, so one forms while others run. A
  * request's result is the same as hntl_search of that query alone with its k
  * and C (every stage is per query). */
 typedef struct hntl_server hntl_server;
@@ -474,17 +477,20 @@ typedef struct {
   uint64_t batches;    /* batches launched */
   double mean_batch;   /* requests per batch */
   double p50_us, p99_us, max_us; /* latency from arrival (or submission) to completion */
-  uint32_t slots;      /* requests the memory budget admits at once */
-  /* the latency in three parts: arrival stamp to admission (the caller's lag),
+  uint32_t slots;      /* requests admitted at once (max_slots) */
+  /* the latency in four parts: arrival stamp to the submission call (the
+   * caller's lag), the call to admission (the row's copy into its slot),
    * admission to the launch of the request's batch, launch to completion */
   double lag_p50_us, lag_p99_us, queue_p50_us, queue_p99_us, service_p50_us, service_p99_us;
+  double upload_p50_us, upload_p99_us;
 } hntl_server_stats;
 
 /* Create a server over `idx` (which must outlive it). mem_budget (bytes of
- * device memory) pays first for three lanes (a search workspace for `batch`
- * queries with k_max, C_max and nprobe, plus batch buffers), the rest for
- * request slots (at most max_slots). ENOMEM if the budget cannot hold the
- * lanes. Blocking (captures the graphs). */
+ * device memory) must hold three lanes (each a search workspace for `batch`
+ * queries with k_max, C_max and nprobe, plus batch buffers): ENOMEM if it
+ * cannot. max_slots requests can be admitted at once; their slot table takes
+ * max_slots x (4 d + 24) bytes of pinned host memory (ENOMEM if that cannot
+ * be pinned). Blocking (captures the graphs). */
 int hntl_server_create(const hntl_index* idx, size_t mem_budget, uint32_t max_slots, uint32_t batch, uint32_t nprobe,
                        uint32_t k_max, uint32_t C_max, hntl_server** out);
 void hntl_server_free(hntl_server* server);
@@ -494,7 +500,8 @@ void hntl_server_free(hntl_server* server);
  * times in steady-clock nanoseconds for latency accounting). Requests are
  * admitted in order while slots are free: *n_admitted tells how many; the
  * call returns HNTL_EBUSY if fewer than n were admitted. tickets[i] identifies
- * admitted request i. Blocking only for the upload of the admitted rows. */
+ * admitted request i. Makes no CUDA call: the rows are copied into their
+ * slots with host stores. Safe to call from several threads. */
 int hntl_server_submit(hntl_server* server, const float* h_queries, uint32_t n, const uint32_t* h_k,
                        const uint32_t* h_C, const int64_t* h_ranges, const int64_t* h_arrival_ns, uint64_t* tickets,
                        uint32_t* n_admitted);
@@ -509,6 +516,21 @@ int hntl_server_submit(hntl_server* server, const float* h_queries, uint32_t n, 
 int hntl_server_poll_many(hntl_server* server, const uint64_t* tickets, uint32_t n, int64_t* h_ids,
                           float* h_dist, uint32_t stride, uint8_t* done, uint32_t timeout_ms, uint32_t* n_done);
 
+/* Open-loop replay of a request stream (for measuring the server): request
+ * i (query row i of h_queries, n x d; h_k, h_C, optional ranges n x 2) is
+ * submitted at or right after its arrival time h_arrival_ns[i] (nanoseconds
+ * after the start of the call, non-decreasing), together with the requests
+ * that have arrived by then, from the calling thread, which also releases
+ * finished requests every millisecond and whenever the slots run out. The
+ * arrival stamps are the latency record's start points. For each i with h_want[i] != 0 (h_want may be NULL) the
+ * request's k ids are copied to row i of h_ids (n x k_max). Returns HNTL_OK
+ * once every request finished (*n_done = n), HNTL_ETIMEOUT after timeout_ms,
+ * or the first error of a submission. The server's latency record covers
+ * the replayed requests. */
+int hntl_server_replay(hntl_server* server, const float* h_queries, uint32_t n, const uint32_t* h_k,
+                       const uint32_t* h_C, const int64_t* h_ranges, const int64_t* h_arrival_ns,
+                       const uint8_t* h_want, int64_t* h_ids, uint32_t timeout_ms, uint32_t* n_done);
+
 /* Wait up to timeout_ms for a request; on success copy its k ids and
  * distances to host buffers (each must hold the request's k entries; k_max
  * always suffices) and release the ticket. HNTL_ETIMEOUT if it is not done in
@@ -519,9 +541,11 @@ int hntl_server_poll(hntl_server* server, uint64_t ticket, int64_t* h_ids, float
 
 /* Latency record since creation or the last reset: completed requests,
  * batches launched and their mean size, p50 / p99 / max latency from each
- * request's arrival stamp to its completion and its three parts, and the
- * request slots the memory budget allows. hntl_server_reset_stats clears the
- * record (not the slots). */
+ * request's arrival stamp to its completion and p50 / p99 of its four parts,
+ * and the request slots. Quantiles come from log-linear histograms (64
+ * buckets per power of two nanoseconds), so each is within 1/64 of the
+ * sample it stands for; the maximum is exact. hntl_server_reset_stats clears
+ * the record (not the slots). */
 int hntl_server_get_stats(hntl_server* server, hntl_server_stats* out);
 int hntl_server_reset_stats(hntl_server* server);
 

@@ -507,6 +507,7 @@ lib.hntl_server_submit.argtypes = [_P, _P, _U32, _P, _P, _P, _P, _P, ctypes.POIN
 lib.hntl_server_poll.argtypes = [_P, ctypes.c_uint64, _P, _P, _U32]
 lib.hntl_server_reset_stats.argtypes = [_P]
 lib.hntl_server_poll_many.argtypes = [_P, _P, _U32, _P, _P, _U32, _P, _U32, ctypes.POINTER(_U32)]
+lib.hntl_server_replay.argtypes = [_P, _P, _U32, _P, _P, _P, _P, _P, _P, _U32, ctypes.POINTER(_U32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -514,7 +515,8 @@ class ServerStats(ctypes.Structure):
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double),
                 ("slots", ctypes.c_uint32), ("lag_p50_us", ctypes.c_double), ("lag_p99_us", ctypes.c_double),
                 ("queue_p50_us", ctypes.c_double), ("queue_p99_us", ctypes.c_double),
-                ("service_p50_us", ctypes.c_double), ("service_p99_us", ctypes.c_double)]
+                ("service_p50_us", ctypes.c_double), ("service_p99_us", ctypes.c_double),
+                ("upload_p50_us", ctypes.c_double), ("upload_p99_us", ctypes.c_double)]
 
 
 lib.hntl_server_get_stats.argtypes = [_P, ctypes.POINTER(ServerStats)]
@@ -622,6 +624,38 @@ class Server:
         if rc not in (OK, EBUSY):
             raise HntlError(rc, last_error())
         return tickets[: got.value]
+
+    def replay(self, Q, k, C, arrival_ns, ranges=None, want=None, timeout_ms=600000):
+        """Open-loop replay inside the library: request i is submitted at
+        arrival_ns[i] nanoseconds after the call starts (non-decreasing).
+        Returns (n_done, ids): ids int64 [n, k_max] holds the results of the
+        rows with want[i] != 0 (zeros elsewhere), or None when want is None.
+        Raises on a submission error; n_done < n after a timeout."""
+        import numpy as np
+
+        Q = np.ascontiguousarray(Q, dtype=np.float32)
+        n = Q.shape[0]
+        k = np.ascontiguousarray(k, dtype=np.uint32)
+        C = np.ascontiguousarray(C, dtype=np.uint32)
+        A = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        R = None if ranges is None else np.ascontiguousarray(ranges, dtype=np.int64)
+        W = None if want is None else np.ascontiguousarray(want, dtype=np.uint8)
+        if Q.shape != (n, self.d) or k.shape != (n,) or C.shape != (n,) or A.shape != (n,):
+            raise ValueError(f"Q must be [n, {self.d}] and k, C, arrival_ns [n]")
+        if (R is not None and R.shape != (n, 2)) or (W is not None and W.shape != (n,)):
+            raise ValueError("ranges must be [n, 2] and want [n]")
+        if n > 1 and np.any(np.diff(A) < 0):
+            raise ValueError("arrival_ns must not decrease")
+        ids = None if W is None else np.zeros((n, self.k_max), dtype=np.int64)
+        got = ctypes.c_uint32(0)
+        rc = lib.hntl_server_replay(self._h, Q.ctypes.data_as(_P), n, k.ctypes.data_as(_P), C.ctypes.data_as(_P),
+                                    None if R is None else R.ctypes.data_as(_P), A.ctypes.data_as(_P),
+                                    None if W is None else W.ctypes.data_as(_P),
+                                    None if ids is None else ids.ctypes.data_as(_P), int(timeout_ms),
+                                    ctypes.byref(got))
+        if rc not in (OK, ETIMEOUT):
+            raise HntlError(rc, last_error())
+        return got.value, ids
 
     def poll(self, ticket, k, timeout_ms=10000):
         """(ids int64 [k], dist f32 [k]) of a request submitted with this k,

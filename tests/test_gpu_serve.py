@@ -2,7 +2,8 @@
 batch it rides in. Each request served in a mixed stream (mixed k, C and
 range filters, submitted in uneven chunks so batches mix them differently)
 is compared with the same query searched alone with its own k, C and filter.
-Also: memory admission refuses requests beyond the free slots, polling an
+The library's open-loop replay gives the same answers. Also: memory
+admission refuses requests beyond the free slots, polling an
 unknown ticket is an error, and the bounded device waits report a timeout
 without losing the context."""
 import numpy as np
@@ -81,7 +82,7 @@ def test_mixed_stream_equals_alone(hntl, served):
     assert all(g is not None for g in got)
     assert st["completed"] == nq and st["batches"] >= nq // 64
     # the latency's parts: caller lag, queueing, service (each per request, so none exceeds the whole)
-    for part in ("lag", "queue", "service"):
+    for part in ("lag", "upload", "queue", "service"):
         assert 0 <= st[f"{part}_p50_us"] <= st[f"{part}_p99_us"] <= st["max_us"] + 1e-6
     assert st["service_p50_us"] > 0
     assert hntl.device_status(gi) == 0
@@ -91,6 +92,39 @@ def test_mixed_stream_equals_alone(hntl, served):
         ids, dist = gi.search(q, int(k[i]), int(C[i]), nprobe, filters=F)
         np.testing.assert_array_equal(got[i][0], ids.cpu().numpy()[0], err_msg=f"query {i}")
         np.testing.assert_array_equal(got[i][1], dist.cpu().numpy()[0], err_msg=f"query {i}")
+
+
+def test_replay_equals_alone(hntl, served):
+    """The library's open-loop replay: every request finishes, the wanted rows
+    carry the same ids as the query searched alone, and the latency record
+    covers exactly the replayed requests. 96 slots for 400 requests that all
+    arrive within a few milliseconds, so admission runs out of slots and the
+    replay has to wait for completions before it submits the rest."""
+    gi, Q, _ = served
+    nq, nprobe = len(Q), 4
+    k, C, ranges, filt = _mix(nq, 304)
+    rng = np.random.default_rng(305)
+    arrival = np.cumsum(rng.exponential(10_000, nq)).astype(np.int64)  # 100k requests/s
+    want = np.zeros(nq, dtype=np.uint8)
+    want[rng.choice(nq, 120, replace=False)] = 1
+    srv = hntl.Server(gi, mem_budget=1 << 30, max_slots=96, batch=32, nprobe=nprobe, k_max=100, C_max=1000)
+    n_done, ids = srv.replay(Q, k, C, arrival, ranges=ranges, want=want, timeout_ms=60000)
+    st = srv.stats()
+    srv.close()
+    assert n_done == nq
+    assert st["completed"] == nq
+    assert (ids[want == 0] == 0).all()
+    for i in np.flatnonzero(want):
+        q = torch.from_numpy(Q[i:i + 1]).cuda()
+        F = torch.from_numpy(ranges[i:i + 1]).cuda() if filt[i] else None
+        ref, _ = gi.search(q, int(k[i]), int(C[i]), nprobe, filters=F)
+        np.testing.assert_array_equal(ids[i, :k[i]], ref.cpu().numpy()[0], err_msg=f"query {i}")
+    with pytest.raises(ValueError):  # arrival times must not decrease
+        srv2 = hntl.Server(gi, mem_budget=1 << 30, max_slots=16, batch=8, nprobe=2, k_max=100, C_max=1000)
+        try:
+            srv2.replay(Q[:2], k[:2], C[:2], np.array([5, 1], np.int64))
+        finally:
+            srv2.close()
 
 
 def test_admission_refuses_beyond_free_slots(hntl, served):
