@@ -85,6 +85,9 @@ struct Index {
   CUtensorMap mapM;              // TMA map of the centres (FP32 or BF16), 256-row boxes
   CUtensorMap mapU;              // precision form: bases (r-row box)
   bool tc_proj = false;
+  uint16_t* U3 = nullptr;        // [3][G][r][d] BF16 parts of the FP32 bases (FP32 and 16-bit forms)
+  CUtensorMap mapU3;             // their TMA map (3 G r rows, r-row box)
+  bool tc_proj32 = false;        // FP32-accurate tensor-core projection available (r <= 32)
 
   // host copies used for workspace sizing
   std::vector<uint32_t> h_blk_off;

@@ -31,6 +31,7 @@
 #include "scan_select.cuh"
 #include "route_tc.cuh"
 #include "project_tc.cuh"
+#include "project_tc32.cuh"
 #include "scan_tc.cuh"
 #include "rerank.cuh"
 #include "recon.cuh"
@@ -359,7 +360,7 @@ Ws carve(const Index& I, uint32_t nq, uint32_t C, uint32_t nprobe, void* base) {
   w.pair_of = c.take<uint32_t>(P);
   const bool tcp = I.precision == HNTL_PREC_BF16_FP8;
   w.pair_vn = c.take<float>(P);  // the projection's ||v'||^2 (precision form) and Mode A's
-  w.slots = tcp ? c.take<uint4>(P / kPSlot + I.G) : nullptr;
+  w.slots = (tcp || I.tc_proj32) ? c.take<uint4>(P / kPSlot + I.G) : nullptr;
   w.scan_off = tcp ? c.take<uint32_t>(I.G + 1) : nullptr;
   w.scan_items = tcp ? c.take<uint4>(I.G + I.n_blocks / kSTBlocks + 1) : nullptr;
   w.dense_items = tcp ? c.take<uint4>(I.G + I.n_blocks / kSTBlocks + 1) : nullptr;
@@ -488,6 +489,30 @@ int launch_resid_tc_n(const Index& I, uint32_t P, const Ws& w, cudaStream_t st) 
   k_resid_tc<RN><<<grid, kRThr, ResidTc<RN>::kSmem, st>>>(w.Qh, I.Mh, I.mapU, (int)I.d, (int)I.r, w.slots,
                                                           w.grp2_off + I.G, w.pair_q, w.zq, w.rhoq, I.d_err);
   HNTL_LAUNCH_CHECK("k_resid_tc");
+  return HNTL_OK;
+}
+
+// The FP32-accurate projection of the FP32 and 16-bit forms: z (k_project_tc3),
+// then the explicit residual (k_resid_tc3), over the precision form's items.
+template <int RN>
+int launch_project_tc32_n(const Index& I, const float* Qd, uint32_t P, const Ws& w, cudaStream_t st) {
+  static thread_local int attr_dev = -1;
+  if (attr_dev != I.device) {
+    HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project_tc3<RN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       ProjTc3<RN>::kSmem));
+    HNTL_CUDA_TRY(
+        cudaFuncSetAttribute(k_resid_tc3<RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, ResidTc3<RN>::kSmem));
+    attr_dev = I.device;
+  }
+  const size_t max_items = ((size_t)P / kPSlot + I.G + kPSlots - 1) / kPSlots;
+  const unsigned grid = persistent_grid(std::min<size_t>(max_items, (size_t)I.num_sms));
+  k_project_tc3<RN><<<grid, kP3Thr, ProjTc3<RN>::kSmem, st>>>(Qd, I.M, I.mapU3, (int)I.G, (int)I.d, (int)I.r,
+                                                              w.slots, w.grp2_off + I.G, w.pair_q, w.zq, I.d_err);
+  HNTL_LAUNCH_CHECK("k_project_tc3");
+  k_resid_tc3<RN><<<grid, kR3Thr, ResidTc3<RN>::kSmem, st>>>(Qd, I.M, I.mapU3, (int)I.G, (int)I.d, (int)I.r,
+                                                             w.slots, w.grp2_off + I.G, w.pair_q, w.zq, w.rhoq,
+                                                             I.d_err);
+  HNTL_LAUNCH_CHECK("k_resid_tc3");
   return HNTL_OK;
 }
 
@@ -655,12 +680,18 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
   if (I.precision == HNTL_PREC_BF16_FP8) {
     if ((rc = launch_project_tc(I, nq, (uint32_t)P, w, st))) return rc;
   } else {
-    size_t smem = (size_t)kPairsPerGroup * I.d * sizeof(float);
-    if (smem > 40 * 1024)  // the kernel's static shared memory counts against the default 48 KB too
-      HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    unsigned grid = persistent_grid(std::min<size_t>((size_t)P / kPairsPerGroup + I.G, (size_t)I.num_sms * 16));
-    k_project<false><<<grid, 256, smem, st>>>(Qd, I.M, I.U, (int)I.d, (int)I.r, (int)I.G, w.grp_off, w.pair_off,
-                                              w.pair_q, w.zq, w.rhoq);
+    if (I.tc_proj32) {
+      if ((rc = I.r <= 16 ? launch_project_tc32_n<16>(I, Qd, (uint32_t)P, w, st)
+                          : launch_project_tc32_n<32>(I, Qd, (uint32_t)P, w, st)))
+        return rc;
+    } else {  // bases of more than 32 rows (or d not a multiple of 8): the direct form on the SIMT cores
+      size_t smem = (size_t)kPairsPerGroup * I.d * sizeof(float);
+      if (smem > 40 * 1024)  // the kernel's static shared memory counts against the default 48 KB too
+        HNTL_CUDA_TRY(cudaFuncSetAttribute(k_project<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      unsigned grid = persistent_grid(std::min<size_t>((size_t)P / kPairsPerGroup + I.G, (size_t)I.num_sms * 16));
+      k_project<false><<<grid, 256, smem, st>>>(Qd, I.M, I.U, (int)I.d, (int)I.r, (int)I.G, w.grp_off, w.pair_off,
+                                                w.pair_q, w.zq, w.rhoq);
+    }
     if (I.precision == HNTL_PREC_INT16)
       k_quant_pairs<<<(unsigned)(((size_t)P * 32 + 255) / 256), 256, 0, st>>>(
           (uint32_t)P, (int)nprobe, w.probe, w.pair_q, w.pair_p, (int)I.r, (int)I.rp, I.scale, I.dres,
@@ -784,9 +815,17 @@ int finalize_index(Index& I) {
     I.crow = static_cast<float*>(alloc(sizeof(float) * I.n_blocks * kBlockRows));
     I.grain_rho_min = static_cast<float*>(alloc(sizeof(float) * I.G));
   }
+  // the FP32-accurate tensor-core projection: bases of up to 32 rows, 16-byte
+  // row strides, the item's centre rows within its shared-memory stage
+  const bool tc32_shape = !bf16 && I.r <= 32 && I.d % 8 == 0 && I.d <= (uint32_t)kP3MuD && I.G > 0;
+  if (tc32_shape) I.U3 = static_cast<uint16_t*>(alloc(sizeof(uint16_t) * 3 * I.G * I.r * I.d));
   if (!I.d_err || !I.mnorm || !I.gram || !I.pos_of_id || !I.hrow || !I.blk_z0 ||
-      (bf16 && (!I.Mh || !I.Mhn || !I.Uh || !I.crow || !I.grain_rho_min)))
+      (bf16 && (!I.Mh || !I.Mhn || !I.Uh || !I.crow || !I.grain_rho_min)) || (tc32_shape && !I.U3))
     return fail(HNTL_ENOMEM, "index: derived arrays");
+  if (tc32_shape) {
+    const size_t nu = (size_t)I.G * I.r * I.d;
+    k_split3_bf16<<<(unsigned)std::min<size_t>((nu + 255) / 256, 65535), 256>>>(I.U, nu, I.U3);
+  }
   HNTL_CUDA_TRY(cudaMemset(I.d_err, 0, sizeof(int)));
   if (bf16) k_row_norms<true><<<(I.G * 32 + 255) / 256, 256>>>(I.M, (int)I.G, (int)I.d, I.mnorm);
   else k_row_norms<false><<<(I.G * 32 + 255) / 256, 256>>>(I.M, (int)I.G, (int)I.d, I.mnorm);
@@ -855,6 +894,7 @@ int finalize_index(Index& I) {
   const bool shape_ok = (bf16 ? I.d % 8 == 0 : I.d % 4 == 0) && I.d <= 8192;
   I.tc_route = shape_ok && make_tma_map(&I.mapM, bf16 ? (const void*)I.Mh : (const void*)I.M, bf16, I.G, I.d, kRTN);
   I.tc_proj = bf16 && shape_ok && make_tma_map(&I.mapU, I.Uh, true, (uint64_t)I.G * I.r, I.d, I.r);
+  I.tc_proj32 = tc32_shape && make_tma_map(&I.mapU3, I.U3, true, 3ull * I.G * I.r, I.d, I.r);
   return HNTL_OK;
 }
 
