@@ -919,6 +919,17 @@ def run_ours(a, world, rank, local):
         line["cpu_baseline"] = {"value": round(q, 2), "unit": "queries/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{nq_done} queries of the same workload against the same index "
                                           f"(FP64 oracle search, OpenMP over queries)"}
+        if a.cpu_budget_1core > 0:  # the same oracle on one host core
+            from oracle import hntl_oracle as O
+
+            O.set_threads(1)
+            try:
+                q1, n1, _, _ = cpu_oracle_qps(host, Xn, Qn, k, C, nprobe, budget_s=a.cpu_budget_1core,
+                                              precision=prec)
+            finally:
+                O.set_threads(cores)
+            line["cpu_baseline"]["one_core"] = {"value": round(q1, 2), "unit": "queries/s", "cores": 1,
+                                                "sample": f"{n1} queries, the same search on one thread"}
         line["parity_sample"] = dict(parity_vs_oracle(gpu0, ora0, k, C, nprobe),
                                      rows="64 rows of headline batch 0 (every B/64-th), as searched in the "
                                           "timed launch configuration, against the oracle on the exported index",
@@ -1188,6 +1199,8 @@ def main():
     ap.add_argument("--serve-rates", default="25000,100000,200000",
                     help="offered Poisson rates (q/s) of the serving run; empty to skip it")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--cpu-budget-1core", type=float, default=4.0,
+                    help="seconds of the oracle on one host core beside the all-core cpu_baseline (0: skip)")
     ap.add_argument("--serve-batch", type=int, default=2048)
     ap.add_argument("--serve-slots", type=int, default=1 << 18)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
