@@ -1206,7 +1206,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-recall", type=int, default=1536, help="served requests checked against brute force")
     ap.add_argument("--serve-p99-ms", type=float, default=50.0)
-    ap.add_argument("--serve-ceiling-rates", default="300000,400000,600000,800000,1200000",
+    ap.add_argument("--serve-ceiling-rates", default="300000,350000,400000,600000,800000,1200000",
                     help="rates tried after --serve-rates, in order, until one misses the ceiling rule")
     ap.add_argument("--serve-ceiling-p99-ms", type=float, default=5.0)
     ap.add_argument("--no-int16", dest="int16", action="store_false",

@@ -1,7 +1,7 @@
 """Parity of the persistent kernels on the paths full-size batches take.
 
-The routing GEMM, both projections and both scans of the precision form run
-persistent grids (about one CTA per SM) that loop over work items. Small cases
+The routing GEMM, the projections of both forms and both scans of the
+precision form run persistent grids (about one CTA per SM) that loop over work items. Small cases
 give every CTA one item at most, so these tests either cap the grids
 (hntl_debug_set_persistent_cap) until each CTA loops over many items, carrying
 its mbarrier phases, TMEM accumulators and prefetches from item to item, or
@@ -88,9 +88,10 @@ def test_precision_form_with_capped_grids(hntl, clustered256):
 
 
 def test_fp32_form_with_capped_grids(hntl, clustered256):
-    """TF32 routing tiles and the grid-stride FP32 projection over many items
-    per CTA: the capped run equals the uncapped one bit for bit, which matches
-    the oracle."""
+    """TF32 routing tiles and the FP32 tensor-core projection (z pass and
+    explicit residual, persistent over 4-slot items) with many items per CTA:
+    the capped run equals the uncapped one bit for bit, which matches the
+    oracle."""
     X, Q, idx, pf, _ = clustered256
     k, C, nprobe = 10, 100, 16
     ora = O.search(idx, X, Q, k, C, nprobe)
