@@ -449,10 +449,14 @@ int hntl_router_status(const hntl_router* router);
 /* Logits (device, B x G FP32) of a batch of rows. Asynchronous. */
 int hntl_router_logits(hntl_router* router, const float* d_X, uint32_t B, float* d_logits, void* stream);
 
-/* Router routing: each query's nprobe largest-logit grains; where their
- * softmax mass is below tau the query takes its centroid routing instead
- * (tau = 0 never falls back, tau > 1 always does). *d_nfallback (device,
- * optional) counts those queries. Workspace: hntl_router_route_workspace_bytes. */
+/* Router routing: each query's nprobe largest-logit grains (ties to the
+ * lower grain); where their softmax mass is below tau the query takes its
+ * centroid routing instead (tau <= 0 never falls back, tau > 1 always does).
+ * For nprobe <= 64 and G <= 8192 one fused kernel per query selects the
+ * probes and decides the fallback from the logits, and with tau <= 0 the
+ * centroid routing is not computed at all. *d_nfallback (device, optional)
+ * counts the queries that fell back. Workspace:
+ * hntl_router_route_workspace_bytes. */
 size_t hntl_router_route_workspace_bytes(const hntl_router* router, const hntl_index* idx, uint32_t nq,
                                          uint32_t nprobe);
 int hntl_router_route(hntl_router* router, const hntl_index* idx, const float* d_queries, uint32_t nq,

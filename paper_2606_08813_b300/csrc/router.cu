@@ -201,6 +201,95 @@ __global__ void k_router_merge(int nq, int nprobe, const float* __restrict__ neg
   }
 }
 
+// The fused selection below handles up to this many probes and 256 x 32 grains.
+constexpr int kTopMax = 64;
+
+// One CTA of 256 threads per query, straight from its G logits: the max and
+// the sum of exp(l - max) in the same per-thread order and block reduction as
+// k_logit_stats (so both are bitwise the same), the nprobe largest logits
+// (ties to the lower grain, NaN last) by nprobe rounds of a block-wide minimum
+// over (negated logit, grain) keys held in registers, their softmax mass
+// summed in selection order as k_router_merge does, and the probes: the
+// centroid probes where that mass is below tau (centroid_probe null: no query
+// falls back).
+template <int kPer>
+__global__ void __launch_bounds__(256) k_router_topk(const float* __restrict__ L, int G, int nprobe, float tau,
+                                                     const int32_t* __restrict__ centroid_probe,
+                                                     int32_t* __restrict__ probe, uint32_t* __restrict__ nfallback) {
+  __shared__ float red[32];
+  __shared__ unsigned long long wmin[8];
+  __shared__ unsigned long long pick[kTopMax];
+  __shared__ int s_fall;
+  const int q = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const float* l = L + (size_t)q * G;
+  float v[kPer];
+  float m = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int g = t + 256 * j;
+    v[j] = g < G ? l[g] : -INFINITY;
+    m = fmaxf(m, v[j]);
+  }
+  m = block_reduce(m, red, true);
+  float sum = 0.f;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j)
+    if (t + 256 * j < G) sum += expf(v[j] - m);
+  sum = block_reduce(sum, red, false);
+  unsigned long long key[kPer];
+  unsigned long long lm = ~0ull;  // this thread's smallest key left
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int g = t + 256 * j;
+    float x = -v[j];
+    if (!(x == x)) x = INFINITY;  // a NaN logit ranks last
+    if (x == 0.f) x = 0.f;        // -0 and +0 rank alike (ties go to the lower grain)
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t hi = (b & 0x80000000u) ? ~b : (b | 0x80000000u);  // order-preserving
+    key[j] = g < G ? ((unsigned long long)hi << 32) | (uint32_t)g : ~0ull;
+    lm = min(lm, key[j]);
+  }
+  for (int p = 0; p < nprobe; ++p) {
+    unsigned long long w = lm;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w = min(w, __shfl_xor_sync(0xffffffffu, w, o));
+    if (lane == 0) wmin[warp] = w;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long x = lane < 8 ? wmin[lane] : ~0ull;
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+      if (lane == 0) pick[p] = x;
+    }
+    __syncthreads();
+    const unsigned long long pk = pick[p];
+    if (lm == pk) {  // keys are distinct: one thread owns it
+      lm = ~0ull;
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        if (key[j] == pk) key[j] = ~0ull;
+        lm = min(lm, key[j]);
+      }
+    }
+  }
+  if (t == 0) {
+    float mass = 0.f;
+    for (int p = 0; p < nprobe; ++p) {
+      const uint32_t hi = (uint32_t)(pick[p] >> 32);
+      const float x = __uint_as_float((hi & 0x80000000u) ? (hi & 0x7FFFFFFFu) : ~hi);  // the negated logit
+      mass += expf(-x - m);
+    }
+    mass /= sum;
+    const bool fall = centroid_probe != nullptr && !(mass >= tau);
+    s_fall = fall;
+    if (fall && nfallback) atomicAdd(nfallback, 1u);
+  }
+  __syncthreads();
+  for (int p = t; p < nprobe; p += 256)
+    probe[(size_t)q * nprobe + p] =
+        s_fall ? centroid_probe[(size_t)q * nprobe + p] : (int32_t)(uint32_t)(pick[p] & 0xFFFFFFFFu);
+}
+
 }  // namespace
 
 struct Router {
@@ -606,8 +695,12 @@ int router_route_probes(Router& R, const Index& I, const float* Q, uint32_t nq, 
   float* negl = c.take<float>((size_t)nq * I.G);
   float* negtop = c.take<float>((size_t)nq * nprobe);
   if (ws_bytes < route_ws + align_up(c.off, 256)) return fail(HNTL_EINVAL, "router routing workspace too small");
-  int rc = route_only(I, Q, nq, nprobe, ws, route_ws, cprobe, cdist, st);
-  if (rc) return rc;
+  // the fused selection for up to kTopMax probes; with tau <= 0 no query falls
+  // back there, so the centroid probes are not computed at all
+  const bool fused = nprobe <= (uint32_t)kTopMax && I.G <= 256u * 32u;
+  const bool centroid = !fused || tau > 0.f;
+  int rc = HNTL_OK;
+  if (centroid && (rc = route_only(I, Q, nq, nprobe, ws, route_ws, cprobe, cdist, st))) return rc;
   if (nfallback) HNTL_CUDA_TRY(cudaMemsetAsync(nfallback, 0, 4, st));
   static thread_local int attr_dev = -1;  // device whose select attribute this thread has set
   if (attr_dev != I.device) {
@@ -618,6 +711,16 @@ int router_route_probes(Router& R, const Index& I, const float* Q, uint32_t nq, 
   for (uint32_t s = 0; s < nq; s += R.max_batch) {
     const uint32_t b = std::min(R.max_batch, nq - s);
     if ((rc = forward(R, Q + (size_t)s * R.d, b, st))) return rc;
+    if (fused) {
+      const int32_t* cp = centroid ? cprobe + (size_t)s * nprobe : nullptr;
+      if (R.G <= 256 * 16)
+        k_router_topk<16><<<b, 256, 0, st>>>(R.L, (int)R.G, (int)nprobe, tau, cp, probe + (size_t)s * nprobe,
+                                             nfallback);
+      else
+        k_router_topk<32><<<b, 256, 0, st>>>(R.L, (int)R.G, (int)nprobe, tau, cp, probe + (size_t)s * nprobe,
+                                             nfallback);
+      continue;
+    }
     k_logit_stats<<<b, 256, 0, st>>>(R.L, (int)R.G, negl + (size_t)s * R.G, R.mx, R.sm);
     k_route_select<<<(b + kSelWarps - 1) / kSelWarps, kSelWarps * 32, (size_t)kSelWarps * R.G * sizeof(float), st>>>(
         negl + (size_t)s * R.G, (int)b, (int)R.G, (int)nprobe, probe + (size_t)s * nprobe, negtop + (size_t)s * nprobe);

@@ -144,27 +144,19 @@ def test_router_route_fallback_and_search_with_probes(hntl, tmp_path):
     assert hntl.device_status(gi) == 0
 
 
-def test_learned_probes_and_fallback_match_oracle(hntl, tmp_path):
-    """Top-nprobe of the GPU's logits and the tau fallback against the router
-    oracle (FP64 with the same BF16 roundings): probe sets must agree unless
-    the nprobe-th and next logits are within the logits' FP32 error, and the
-    fallback decision unless the probes' softmax mass is within that error of
-    tau; fallen-back queries carry the oracle's centroid probes."""
-    d, G, nprobe = 64, 48, 4
-    m = synth.make_cluster_model(6000, d, 12, seed=91)
-    X, _ = synth.sample_points(m, 92)
-    Q, _ = synth.sample_queries(m, 300, 93)
-    X, Q = X.numpy(), Q.numpy()
-    idx = O.build_index(X, G, 8, synth.uniforms(G, 94).numpy())
-    gi = hntl.Index.load(write(tmp_path, "lp", idx, X), 0)
-    params = R.init_params(d, 128, 128, G, seed=95)
-    rng = np.random.default_rng(96)
-    params[4] = (params[4] * 6.0).astype(np.float32)  # spread the logits so the masses vary by query
-    params[5] = rng.standard_normal(G).astype(np.float32)
-    rt = hntl.Router(params, max_batch=128)
+def _route_against_oracle(hntl, gi, rt, params, Q, idx, X, nprobe, tau_mid=None):
+    """Route Q at tau 0, tau_mid (default: the median of the oracle's softmax
+    masses, so that about half the queries fall back) and 2, and compare with
+    the router oracle: probe
+    sets must agree unless the nprobe-th and next logits are within the
+    logits' FP32 error, the fallback decision unless the probes' softmax mass
+    is within that error of tau; fallen-back queries carry the oracle's
+    centroid probes."""
     Qd = torch.from_numpy(Q).cuda()
     cent = O.search(idx, X, Q, 1, 1, nprobe)
-    for tau in (0.0, 0.35, 2.0):
+    if tau_mid is None:
+        tau_mid = float(np.median(R.route(params, Q, nprobe, 0.0, cent["probe"])[2]))
+    for tau in (0.0, tau_mid, 2.0):
         probes, nfb = rt.route(gi, Qd, nprobe, tau=tau)
         got = probes.cpu().numpy()
         want, fell, mass, L = R.route(params, Q, nprobe, tau, cent["probe"])
@@ -188,11 +180,52 @@ def test_learned_probes_and_fallback_match_oracle(hntl, tmp_path):
         assert n_cmp >= 0.9 * len(Q), (tau, n_cmp)
         assert abs(int(nfb.item()) - int(fell.sum())) <= len(Q) - n_cmp, (tau, int(nfb.item()), int(fell.sum()))
         if tau == 0.0:
-            assert not fell.any()
+            assert not fell.any() and int(nfb.item()) == 0
         if tau == 2.0:
             assert fell.all()
-        if tau == 0.35:
+        if tau == tau_mid:
             assert 0 < n_fb < len(Q), n_fb  # a mix of kept and fallen-back queries
+
+
+def test_learned_probes_and_fallback_match_oracle(hntl, tmp_path):
+    """Top-nprobe of the GPU's logits and the tau fallback against the router
+    oracle (FP64 with the same BF16 roundings), over three query chunks of
+    the router's batch."""
+    d, G, nprobe = 64, 48, 4
+    m = synth.make_cluster_model(6000, d, 12, seed=91)
+    X, _ = synth.sample_points(m, 92)
+    Q, _ = synth.sample_queries(m, 300, 93)
+    X, Q = X.numpy(), Q.numpy()
+    idx = O.build_index(X, G, 8, synth.uniforms(G, 94).numpy())
+    gi = hntl.Index.load(write(tmp_path, "lp", idx, X), 0)
+    params = R.init_params(d, 128, 128, G, seed=95)
+    rng = np.random.default_rng(96)
+    params[4] = (params[4] * 6.0).astype(np.float32)  # spread the logits so the masses vary by query
+    params[5] = rng.standard_normal(G).astype(np.float32)
+    rt = hntl.Router(params, max_batch=128)
+    _route_against_oracle(hntl, gi, rt, params, Q, idx, X, nprobe, tau_mid=0.35)
+
+
+@pytest.mark.parametrize("G,nprobe", [(4096, 64), (5000, 32), (304, 65)])
+def test_learned_selection_paths_match_oracle(hntl, tmp_path, G, nprobe):
+    """The fused per-query selection at its edges (4096 grains, 16 logits a
+    thread, the largest nprobe it takes; 5000 grains, 32 logits a thread) and
+    the general path beyond 64 probes, against the router oracle."""
+    from cases import partition_index
+
+    d = 32
+    m = synth.make_cluster_model(4 * G, d, G, seed=970 + G)  # one grain per cluster: separated centres
+    X, lab = synth.sample_points(m, 971 + G)
+    Q, _ = synth.sample_queries(m, 160, 972 + G)
+    X, Q = X.numpy(), Q.numpy()
+    idx = partition_index(X, lab.numpy(), G, 4)
+    gi = hntl.Index.load(write(tmp_path, f"sel{G}", idx, X), 0)
+    params = R.init_params(d, 64, 64, G, seed=973 + G)
+    rng = np.random.default_rng(974 + G)
+    params[4] = (params[4] * 6.0).astype(np.float32)
+    params[5] = rng.standard_normal(G).astype(np.float32)
+    rt = hntl.Router(params, max_batch=128)
+    _route_against_oracle(hntl, gi, rt, params, Q, idx, X, nprobe)
 
 
 def test_gradients_at_full_router_widths(hntl):
