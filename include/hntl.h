@@ -373,8 +373,9 @@ int hntl_search_pair_proj(const hntl_index* idx, const void* d_ws, size_t ws_byt
                           uint32_t nprobe, float* d_zq, float* d_rhoq, void* stream);
 
 /* Test hook (the paper has no counterpart): caps the grid of every persistent
- * kernel of the search (tensor-core routing, both projections, both scans of
- * the precision form) at `ctas` CTAs, 0 restoring the default of about one
+ * kernel of the search (tensor-core routing, the tensor-core projection and
+ * explicit residual of either form, both scans of the precision form) at
+ * `ctas` CTAs, 0 restoring the default of about one
  * per SM. A capped kernel still processes every work item, each CTA looping
  * over many of them, so a small test case exercises the multi-item paths
  * (accumulator ping-pong, mbarrier phases carried across items, prefetch of
