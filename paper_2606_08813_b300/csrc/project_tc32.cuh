@@ -36,7 +36,16 @@ constexpr int kP3MuPer = kPSlots * kP3MuD / 4 / 256;  // 16-byte centre pieces a
 __host__ __device__ constexpr int p3_a(int q) { return q == 2 || q == 4 ? 1 : (q == 5 ? 2 : 0); }
 __host__ __device__ constexpr int p3_b(int q) { return q == 1 || q == 4 ? 1 : (q == 3 ? 2 : 0); }
 
-// three BF16 parts of 8 FP32 values, packed two to a word
+// Two FP32 values rounded to nearest-even BF16 in one conversion: `lo` into
+// the low half of the word, `hi` into the high half.
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
+  uint32_t w;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
+  return w;
+}
+
+// three BF16 parts of 8 FP32 values, packed two to a word (the even value in
+// the low half)
 __device__ __forceinline__ void split3_pack(const float (&v)[8], uint4 (&out)[kP3Parts]) {
   uint32_t w[kP3Parts][4];
 #pragma unroll
@@ -44,10 +53,10 @@ __device__ __forceinline__ void split3_pack(const float (&v)[8], uint4 (&out)[kP
     float a = v[2 * h], b = v[2 * h + 1];
 #pragma unroll
     for (int p = 0; p < kP3Parts; ++p) {
-      const uint16_t ha = bf16_bits(a), hb = bf16_bits(b);
-      w[p][h] = (uint32_t)ha | ((uint32_t)hb << 16);
-      a -= bf16_val(ha);  // exact: the remainder of a BF16 rounding
-      b -= bf16_val(hb);
+      const uint32_t x = bf16x2_rn(a, b);
+      w[p][h] = x;
+      a -= __uint_as_float(x << 16);  // exact: the remainder of a BF16 rounding
+      b -= __uint_as_float(x & 0xFFFF0000u);
     }
   }
 #pragma unroll
