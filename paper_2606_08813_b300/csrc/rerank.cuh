@@ -39,6 +39,53 @@ __global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, con
   for (int t = threadIdx.x; t < d; t += blockDim.x) sq[t] = Q[(size_t)q * d + t];
   __syncthreads();
   const int n2 = pow2_at_least(C);
+  // BF16 rows of up to 1024 values: two candidates a warp at a time, the two
+  // rows' 16-byte loads issued interleaved before the sums (six loads of 512
+  // bytes per warp in flight at d = 768, as many as one FP32 row gives; three
+  // or four rows a warp, or the two rows' loads one row after the other,
+  // measured slower)
+  if (kBF16 && !kRefine && (d & 7) == 0 && d <= 1024) {
+    for (int c = warp; c < n2; c += 16) {
+      const int c2 = c + 8;
+      const uint32_t ida = c < C ? cid[c] : kInvalidId, idb = c2 < C && c2 < n2 ? cid[c2] : kInvalidId;
+      const uint16_t* xa = reinterpret_cast<const uint16_t*>(Xv) + (size_t)(ida != kInvalidId ? ida : 0) * d;
+      const uint16_t* xb = reinterpret_cast<const uint16_t*>(Xv) + (size_t)(idb != kInvalidId ? idb : 0) * d;
+      uint4 va[4], vb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int t = lane * 8 + 256 * i;
+        va[i] = (ida != kInvalidId && t < d) ? __ldg(reinterpret_cast<const uint4*>(xa + t)) : make_uint4(0, 0, 0, 0);
+        vb[i] = (idb != kInvalidId && t < d) ? __ldg(reinterpret_cast<const uint4*>(xb + t)) : make_uint4(0, 0, 0, 0);
+      }
+      float acca = 0.f, accb = 0.f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int t = lane * 8 + 256 * i;
+        if (t < d) {
+          const uint32_t wa[4] = {va[i].x, va[i].y, va[i].z, va[i].w}, wb[4] = {vb[i].x, vb[i].y, vb[i].z, vb[i].w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float q0 = sq[t + 2 * h], q1 = sq[t + 2 * h + 1];
+            const float a0 = q0 - __uint_as_float(wa[h] << 16), a1 = q1 - __uint_as_float(wa[h] & 0xFFFF0000u);
+            const float b0 = q0 - __uint_as_float(wb[h] << 16), b1 = q1 - __uint_as_float(wb[h] & 0xFFFF0000u);
+            acca = fmaf(a0, a0, acca);
+            acca = fmaf(a1, a1, acca);
+            accb = fmaf(b0, b0, accb);
+            accb = fmaf(b1, b1, accb);
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acca += __shfl_xor_sync(0xffffffffu, acca, o);
+        accb += __shfl_xor_sync(0xffffffffu, accb, o);
+      }
+      if (lane == 0) {
+        keys[c] = ida != kInvalidId ? ((unsigned long long)__float_as_uint(acca) << 32) | ida : ~0ull;
+        if (c2 < n2) keys[c2] = idb != kInvalidId ? ((unsigned long long)__float_as_uint(accb) << 32) | idb : ~0ull;
+      }
+    }
+  } else
   for (int c = warp; c < n2; c += 8) {
     unsigned long long key = ~0ull;
     uint32_t id = c < C ? cid[c] : kInvalidId;
