@@ -42,8 +42,8 @@ __global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, con
   // BF16 rows of up to 1024 values: two candidates a warp at a time, the two
   // rows' 16-byte loads issued interleaved before the sums (six loads of 512
   // bytes per warp in flight at d = 768, as many as one FP32 row gives; three
-  // or four rows a warp, or the two rows' loads one row after the other,
-  // measured slower)
+  // or four rows a warp, the two rows' loads one row after the other, and
+  // this loop in the refined rerank's first stage measured slower)
   if (kBF16 && !kRefine && (d & 7) == 0 && d <= 1024) {
     for (int c = warp; c < n2; c += 16) {
       const int c2 = c + 8;
