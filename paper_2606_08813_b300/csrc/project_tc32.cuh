@@ -28,10 +28,13 @@ namespace {
 
 constexpr int kP3Parts = 3;
 constexpr int kP3Prod = 6;         // part products (i, j) with i + j <= 2
-constexpr int kP3Thr = 416;        // 8 producer warps, 1 MMA warp, 4 epilogue warps
-constexpr int kP3MmaWarp = 8;
+constexpr int kP3ProdThr = 512;    // 16 producer warps (four per scheduler hide the split's dependent chains)
+constexpr int kP3Thr = kP3ProdThr + 160;  // then 4 epilogue warps and 1 MMA warp
+constexpr int kP3EpiWarp = kP3ProdThr / 32;
+constexpr int kP3MmaWarp = kP3EpiWarp + 4;
+constexpr int kP3RowsPer = kPTM * 8 / kP3ProdThr;  // A rows each producer thread fills (one 16-byte piece each)
 constexpr int kP3MuD = 1024;       // the item's centre rows are staged in shared memory: d <= this
-constexpr int kP3MuPer = kPSlots * kP3MuD / 4 / 256;  // 16-byte centre pieces a producer thread copies
+constexpr int kP3MuPer = kPSlots * kP3MuD / 4 / kP3ProdThr;  // 16-byte centre pieces a producer thread copies
 
 __host__ __device__ constexpr int p3_a(int q) { return q == 2 || q == 4 ? 1 : (q == 5 ? 2 : 0); }
 __host__ __device__ constexpr int p3_b(int q) { return q == 1 || q == 4 ? 1 : (q == 3 ? 2 : 0); }
@@ -78,15 +81,15 @@ struct ProjTc3 {
 
 // Persistent and warp-specialised like k_project_tc (slot j of an item owns
 // A rows 32j..32j+31, B rows j RN..j RN + RN - 1 and TMEM lane quarter j).
-//   warps 0-7  producers: thread t forms, per K block of 64 coordinates, the
-//              16-byte pieces t % 8 of A rows t / 8 + 32 i (one row of each
-//              slot i): v' = q - mu in FP32 from the query row (registers,
+//   warps 0-15 producers: thread t forms, per K block of 64 coordinates, the
+//              16-byte pieces t % 8 of A rows t / 8 + 64 i, i < 2 (slots
+//              t / 256 and 2 + t / 256): v' = q - mu in FP32 from the query row (registers,
 //              loaded one K block ahead) and the slot's centre (staged in
 //              shared memory once per item), split into three parts written
 //              to the stage's three swizzled A tiles; it then announces the
 //              stage on `full`. TMA brings the 4 bases' three parts.
-//   warp 8     one thread issues the six part products per 16 coordinates.
-//   warps 9-12 epilogue: z of slot warp % 4 from TMEM to zq.
+//   warps 16-19 epilogue: z of slot warp % 4 from TMEM to zq.
+//   warp 20    one thread issues the six part products per 16 coordinates.
 // RN = basis rows padded to 16 or 32, r <= RN; d % 8 == 0, d <= kP3MuD.
 template <int RN>
 __global__ void __launch_bounds__(kP3Thr, 1) k_project_tc3(
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(kP3Thr, 1) k_project_tc3(
   if (warp == kP3MmaWarp) tc::tmem_alloc(&tmem_base, P::kTmemCols);
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
-      tc::mbar_init(&full[s], 256);  // every producer thread arrives once its pieces are written
+      tc::mbar_init(&full[s], kP3ProdThr);  // every producer thread arrives once its pieces are written
       tc::mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
@@ -121,9 +124,9 @@ __global__ void __launch_bounds__(kP3Thr, 1) k_project_tc3(
     s_it_prod = s_it_mma = 0;
     tc::mbar_fence_init();
   }
-  if (tid < 256 && r < RN) {  // basis rows r..RN-1 of every slot, part and stage stay zero
+  if (tid < kP3ProdThr && r < RN) {  // basis rows r..RN-1 of every slot, part and stage stay zero
     const int per = kPSlots * (RN - r) * 8;
-    for (int e = tid; e < S * kP3Parts * per; e += 256) {
+    for (int e = tid; e < S * kP3Parts * per; e += kP3ProdThr) {
       const int sp = e / per, rem = e % per, j = rem / ((RN - r) * 8), rr = rem % ((RN - r) * 8);
       const int s = sp / kP3Parts, p = sp % kP3Parts;
       const int row = j * RN + r + rr / 8, ch = rr % 8;
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(kP3Thr, 1) k_project_tc3(
     return s < ns ? slots[s] : make_uint4(0, 0, 0, 0);
   };
 
-  if (warp < 8) {
+  if (warp < kP3EpiWarp) {
     // ------------------------------------------------------------ producers
     const int pt = tid;
     uint32_t it = 0;       // stages this thread has announced
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(kP3Thr, 1) k_project_tc3(
       float* dst = sMu + buf * (kPSlots * kP3MuD);
 #pragma unroll
       for (int u = 0; u < kP3MuPer; ++u) {
-        const int e = pt + 256 * u;
+        const int e = pt + kP3ProdThr * u;
         if (e < kPSlots * d4) {
           const int j = e / d4, c4 = e % d4;
           tc::cp_async16_ca_zfill(tc::smem_u32(dst + j * kP3MuD + 4 * c4),
@@ -174,35 +177,36 @@ __global__ void __launch_bounds__(kP3Thr, 1) k_project_tc3(
       tc::cp_async_commit();
     };
     if (blockIdx.x < total) prefetch(blockIdx.x, 0);
-    const int ch = pt & 7, rbase = pt >> 3;  // pieces ch of rows rbase + 32 i, i < 4 (row of slot i)
+    const int ch = pt & 7, rbase = pt >> 3;  // pieces ch of rows rbase + 64 i, i < 2
     uint32_t li = 0;
     for (uint32_t w = blockIdx.x; w < total; w += gridDim.x, ++li) {
-      tc::named_bar(1, 256);  // every producer is done with the previous item's ids and centres
+      tc::named_bar(1, kP3ProdThr);  // every producer is done with the previous item's ids and centres
       if (pt < 128) {
         sq[pt] = q_next;
         if (my_i == 0) sslot[my_j] = nslot;
       }
       tc::cp_async_wait<0>();  // this thread's copies of this item's centres have landed
       if (w + gridDim.x < total) prefetch(w + gridDim.x, (int)((li + 1) & 1));
-      tc::named_bar(1, 256);   // and everyone else's
+      tc::named_bar(1, kP3ProdThr);   // and everyone else's
       if (failed) continue;
       const float* mu_item = sMu + (li & 1) * (kPSlots * kP3MuD);
-      uint32_t qok = 0;  // bit i: row rbase of slot i holds a pair
-      const float* qsrc[kPSlots];
+      uint32_t qok = 0;  // bit i: row rbase + 64 i holds a pair
+      const float* qsrc[kP3RowsPer];
 #pragma unroll
-      for (int i = 0; i < kPSlots; ++i) {
-        qok |= (uint32_t)((uint32_t)rbase < sslot[i].z) << i;
-        qsrc[i] = Q + (size_t)sq[rbase + 32 * i] * d + ch * 8;
+      for (int i = 0; i < kP3RowsPer; ++i) {
+        const int row = rbase + 64 * i;
+        qok |= (uint32_t)((uint32_t)(row & 31) < sslot[row >> 5].z) << i;
+        qsrc[i] = Q + (size_t)sq[row] * d + ch * 8;
       }
       uint32_t bytes = 0;  // TMA bytes one stage receives: three parts of each slot's basis
 #pragma unroll
       for (int j = 0; j < kPSlots; ++j) bytes += sslot[j].z ? (uint32_t)(kP3Parts * r * 128) : 0u;
-      float4 qa[kPSlots][2], qb[kPSlots][2];
-      auto load = [&](int kb, float4 (&dst)[kPSlots][2]) {
+      float4 qa[kP3RowsPer][2], qb[kP3RowsPer][2];
+      auto load = [&](int kb, float4 (&dst)[kP3RowsPer][2]) {
         const int t = kb * kPKB;
         const bool in = t + ch * 8 < d;  // d % 8 == 0: a piece is wholly inside or outside
 #pragma unroll
-        for (int i = 0; i < kPSlots; ++i) {
+        for (int i = 0; i < kP3RowsPer; ++i) {
           if (((qok >> i) & 1u) && in) {
             dst[i][0] = __ldg(reinterpret_cast<const float4*>(qsrc[i] + t));
             dst[i][1] = __ldg(reinterpret_cast<const float4*>(qsrc[i] + t + 4));
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(kP3Thr, 1) k_project_tc3(
           }
         }
       };
-      auto stage = [&](int kb, const float4 (&src)[kPSlots][2]) -> bool {
+      auto stage = [&](int kb, const float4 (&src)[kP3RowsPer][2]) -> bool {
         const int s = (int)(it % S);
         // the MMAs that read this stage S blocks ago must be done (each producer waits for itself)
         if (it >= (uint32_t)S && !tc::mbar_wait(&empty[s], ((it / S) - 1) & 1)) return false;
@@ -227,12 +231,14 @@ __global__ void __launch_bounds__(kP3Thr, 1) k_project_tc3(
         const bool in = x + ch * 8 < d;
         const uint32_t sbase = tc::smem_u32(st);
 #pragma unroll
-        for (int i = 0; i < kPSlots; ++i) {
+        for (int i = 0; i < kP3RowsPer; ++i) {
           if (!((qok >> i) & 1u)) continue;  // a row without a pair: its output rows are never read
+          const int row = rbase + 64 * i;
           float v[8] = {};
           if (in) {
-            const float4 m0 = *reinterpret_cast<const float4*>(mu_item + i * kP3MuD + x + ch * 8);
-            const float4 m1 = *reinterpret_cast<const float4*>(mu_item + i * kP3MuD + x + ch * 8 + 4);
+            const float* mu = mu_item + (row >> 5) * kP3MuD + x + ch * 8;
+            const float4 m0 = *reinterpret_cast<const float4*>(mu);
+            const float4 m1 = *reinterpret_cast<const float4*>(mu + 4);
             v[0] = src[i][0].x - m0.x;
             v[1] = src[i][0].y - m0.y;
             v[2] = src[i][0].z - m0.z;
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(kP3Thr, 1) k_project_tc3(
           }
           uint4 parts[kP3Parts];
           split3_pack(v, parts);
-          const uint32_t off = sw128_off(rbase + 32 * i, ch * 16);
+          const uint32_t off = sw128_off(row, ch * 16);
 #pragma unroll
           for (int p = 0; p < kP3Parts; ++p)
             asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + p * kPBytesA + off),
@@ -329,38 +335,32 @@ __global__ void __launch_bounds__(kP3Thr, 1) k_project_tc3(
       }
       tc::fence_after_sync();
       const int np = (int)sl.z;
-      float z[RN];
-      if (np > 0) {  // leading plus cross products
+      if (np > 0) {  // leading plus cross products, 16 columns at a time, straight to zq
         const uint32_t taddr = tmem + ((uint32_t)(j * 32) << 16) + (uint32_t)(a * 2 * P::kN + j * RN);
-        if constexpr (RN == 16) {
+        float* out = zq + (size_t)(sl.y + (lane < np ? lane : 0)) * r;
+#pragma unroll
+        for (int c0 = 0; c0 < RN; c0 += 16) {
           float v[16], x[16];
-          tc::tmem_ld16(taddr, v);
-          tc::tmem_ld16(taddr + P::kN, x);
+          tc::tmem_ld16(taddr + c0, v);
+          tc::tmem_ld16(taddr + P::kN + c0, x);
+          if (lane < np) {
+            if ((r & 3) == 0) {
 #pragma unroll
-          for (int c = 0; c < 16; ++c) z[c] = v[c] + x[c];
-        } else {
-          float v[32], x[32];
-          tc::tmem_ld32(taddr, v);
-          tc::tmem_ld32(taddr + P::kN, x);
+              for (int ia = 0; ia < 16; ia += 4)
+                if (c0 + ia < r)
+                  *reinterpret_cast<float4*>(out + c0 + ia) =
+                      make_float4(v[ia] + x[ia], v[ia + 1] + x[ia + 1], v[ia + 2] + x[ia + 2], v[ia + 3] + x[ia + 3]);
+            } else {
 #pragma unroll
-          for (int c = 0; c < 32; ++c) z[c] = v[c] + x[c];
+              for (int ia = 0; ia < 16; ++ia)
+                if (c0 + ia < r) out[c0 + ia] = v[ia] + x[ia];
+            }
+          }
         }
       }
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acce[a]);
-      if (lane < np) {
-        float* out = zq + (size_t)(sl.y + lane) * r;
-        if ((r & 3) == 0) {
-#pragma unroll
-          for (int ia = 0; ia < RN; ia += 4)
-            if (ia < r) *reinterpret_cast<float4*>(out + ia) = make_float4(z[ia], z[ia + 1], z[ia + 2], z[ia + 3]);
-        } else {
-#pragma unroll
-          for (int ia = 0; ia < RN; ++ia)
-            if (ia < r) out[ia] = z[ia];
-        }
-      }
     }
     if (failed) atomicExch(&s_fail, 1);
   }
