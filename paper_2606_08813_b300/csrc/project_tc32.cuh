@@ -66,6 +66,40 @@ __device__ __forceinline__ void split3_pack(const float (&v)[8], uint4 (&out)[kP
   for (int p = 0; p < kP3Parts; ++p) out[p] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
 }
 
+// The distinct grains of an item's slots: the slots with pairs come first and
+// a grain's slots are consecutive, so each new grain follows the last one
+// seen. nd of them, slot j's distinct index in u_of[j] (0 for a slot without
+// pairs), the grain of distinct index u from grain(). The residual pass
+// gives each distinct grain, not each slot, a K range of its block-diagonal A
+// and loads each distinct basis once, so the K steps of an item whose slots
+// share grains are fewer. (The z pass keeps one MMA over all 4 slots' bases:
+// one N = 4 RN product measured faster than an N = RN product per distinct
+// grain.)
+struct ItemGrains {
+  int nd;
+  int u_of[kPSlots];
+  // the grain of distinct index u (u < nd)
+  __device__ __forceinline__ uint32_t grain(const uint4* sl, int u) const {
+    uint32_t g = 0;
+#pragma unroll
+    for (int j = kPSlots - 1; j >= 0; --j)
+      if (sl[j].z && u_of[j] == u) g = sl[j].x;
+    return g;
+  }
+};
+__device__ __forceinline__ ItemGrains item_grains(const uint4* sl) {
+  ItemGrains ig;
+  ig.nd = sl[0].z ? 1 : 0;
+  ig.u_of[0] = 0;
+#pragma unroll
+  for (int j = 1; j < kPSlots; ++j) {
+    const bool fresh = sl[j].z && sl[j].x != sl[j - 1].x;
+    ig.u_of[j] = sl[j].z ? ig.u_of[j - 1] + (fresh ? 1 : 0) : 0;
+    ig.nd += fresh ? 1 : 0;
+  }
+  return ig;
+}
+
 template <int RN>
 struct ProjTc3 {
   static constexpr int kN = kPSlots * RN;                                // MMA N: the 4 slots' bases
@@ -395,9 +429,10 @@ struct ResidTc3 {
 };
 
 // rho_q = ||v' - U_g^T z||^2 of every pair in FP32 (Eq. 3-4, v' = q - mu_g).
-// A = z in three parts, block-diagonal over the item's slots (row i of slot s
-// holds its z at K = s RN .. s RN + RN - 1, zeros elsewhere); B = the slots'
-// basis parts for 64 coordinates, TMA boxes read MN-major. TMEM lane i,
+// A = z in three parts, block-diagonal over the item's distinct grains (row i
+// holds its z at K = u RN .. u RN + RN - 1, u its slot's distinct grain, zeros
+// elsewhere; only the K steps of the nd distinct grains run); B = those
+// grains' basis parts for 64 coordinates, TMA boxes read MN-major. TMEM lane i,
 // column t then holds (U^T z)_t of pair i (leading and cross products in two
 // accumulators, as in the projection).
 //   warp 0     TMA producer: per chunk, three parts of each slot's box.
@@ -473,12 +508,10 @@ __global__ void __launch_bounds__(kR3Thr, 1) k_resid_tc3(
       bool ok = true;
       for (uint32_t w = blockIdx.x; w < total && ok; w += gridDim.x) {
         uint4 sl[kPSlots];
-        uint32_t bytes = 0;
 #pragma unroll
-        for (int j = 0; j < kPSlots; ++j) {
-          sl[j] = slot_of(w, j);
-          bytes += sl[j].z ? (uint32_t)(kP3Parts * r * 128) : 0u;
-        }
+        for (int j = 0; j < kPSlots; ++j) sl[j] = slot_of(w, j);
+        const ItemGrains ig = item_grains(sl);
+        const uint32_t bytes = (uint32_t)(ig.nd * kP3Parts * r * 128);
         for (int c = 0; c < nch; ++c, ++it) {
           const int s = (int)(it % S);
           if (it >= (uint32_t)S && !tc::mbar_wait(&empty[s], ((it / S) - 1) & 1)) {
@@ -490,10 +523,10 @@ __global__ void __launch_bounds__(kR3Thr, 1) k_resid_tc3(
 #pragma unroll
           for (int p = 0; p < kP3Parts; ++p)
 #pragma unroll
-            for (int j = 0; j < kPSlots; ++j)
-              if (sl[j].z)
-                tc::tma_load_2d(&mapU3, &full[s], st + p * P::kBytesBpart + j * P::kBytesBox, c * kR3Chunk,
-                                p * G * r + (int)sl[j].x * r);
+            for (int u = 0; u < kPSlots; ++u)
+              if (u < ig.nd)
+                tc::tma_load_2d(&mapU3, &full[s], st + p * P::kBytesBpart + u * P::kBytesBox, c * kR3Chunk,
+                                p * G * r + (int)ig.grain(sl, u) * r);
         }
       }
       s_it_prod = it;
@@ -512,6 +545,10 @@ __global__ void __launch_bounds__(kR3Thr, 1) k_resid_tc3(
           break;
         }
         tc::fence_after_sync();
+        uint4 slw[kPSlots];
+#pragma unroll
+        for (int j = 0; j < kPSlots; ++j) slw[j] = slot_of(w, j);
+        const int nks = item_grains(slw).nd * (RN / 16);  // K steps of the distinct grains' ranges
         for (int c = 0; c < nch; ++c, ++it, ++ci) {
           const int s = (int)(it % S), a = (int)(ci & 1);
           if (ci >= 2 && !tc::mbar_wait(&acce[a], ((ci >> 1) - 1) & 1)) {
@@ -530,6 +567,7 @@ __global__ void __launch_bounds__(kR3Thr, 1) k_resid_tc3(
           for (int q = 0; q < kP3Prod; ++q)
 #pragma unroll
             for (int ks = 0; ks < kKS; ++ks)
+              if (ks < nks)
               tc::mma<true>(q == 0 ? acc : acc + (uint32_t)kR3Chunk,
                             tc::desc_sw128(sa0 + p3_a(q) * P::kBytesApart + (ks / 4) * (kPTM * 128) + (ks % 4) * 32),
                             tc::desc_sw128_mn(sbs + p3_b(q) * P::kBytesBpart + (ks / (RN / 16)) * P::kBytesBox +
@@ -573,9 +611,30 @@ __global__ void __launch_bounds__(kR3Thr, 1) k_resid_tc3(
       }
     };
     if (blockIdx.x < total) prefetch_z(blockIdx.x);
+    int prev_u = -1;  // the K range this thread's pieces of its row were last written to
     for (uint32_t w = blockIdx.x; w < total; w += gridDim.x, ++li) {
       if (et < kPSlots) sslot[et] = slot_of(w, et);
       if (zn_have) {
+        // the row's K range is its slot's distinct grain's: u RN .. u RN + RN - 1
+        uint4 slw[kPSlots];
+#pragma unroll
+        for (int j = 0; j < kPSlots; ++j) slw[j] = slot_of(w, j);
+        const ItemGrains igw = item_grains(slw);
+        int ua = 0;
+#pragma unroll
+        for (int j = 0; j < kPSlots; ++j)
+          if (j == sa) ua = igw.u_of[j];
+        if (prev_u >= 0 && prev_u != ua) {  // the range written last stays zero from now on
+#pragma unroll
+          for (int c8 = 0; c8 < kH / 8; ++c8) {
+            const int kc = (prev_u * RN + hf * kH) / 8 + c8;
+#pragma unroll
+            for (int p = 0; p < kP3Parts; ++p)
+              *reinterpret_cast<uint4*>(sA + p * P::kBytesApart + (kc / 8) * (kPTM * 128) +
+                                        sw128_off(ra, (kc % 8) * 16)) = make_uint4(0, 0, 0, 0);
+          }
+        }
+        prev_u = ua;
 #pragma unroll
         for (int c8 = 0; c8 < kH / 8; ++c8) {  // 16-byte pieces of 8 values
           float v8[8];
@@ -583,7 +642,7 @@ __global__ void __launch_bounds__(kR3Thr, 1) k_resid_tc3(
           for (int u = 0; u < 8; ++u) v8[u] = zn[c8 * 8 + u];
           uint4 parts[kP3Parts];
           split3_pack(v8, parts);
-          const int kc = (sa * RN + hf * kH) / 8 + c8;  // piece index along K
+          const int kc = (ua * RN + hf * kH) / 8 + c8;  // piece index along K
 #pragma unroll
           for (int p = 0; p < kP3Parts; ++p)
             *reinterpret_cast<uint4*>(sA + p * P::kBytesApart + (kc / 8) * (kPTM * 128) + sw128_off(ra, (kc % 8) * 16)) =
