@@ -365,6 +365,40 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
   if (tid == 0 && s_fail) atomicOr(err, tc::kErrTimeout);
 }
 
+// The distinct grains of an item's slots: the slots with pairs come first and
+// a grain's slots are consecutive, so each new grain follows the last one
+// seen. nd of them, slot j's distinct index in u_of[j] (0 for a slot without
+// pairs), the grain of distinct index u from grain(). The residual passes
+// give each distinct grain, not each slot, a K range of their block-diagonal
+// A and load each distinct basis once, so the K steps of an item whose slots
+// share grains are fewer. (The projections keep one MMA over all 4 slots'
+// bases: one N = 4 RN product measured faster than an N = RN product per
+// distinct grain.)
+struct ItemGrains {
+  int nd;
+  int u_of[kPSlots];
+  // the grain of distinct index u (u < nd)
+  __device__ __forceinline__ uint32_t grain(const uint4* sl, int u) const {
+    uint32_t g = 0;
+#pragma unroll
+    for (int j = kPSlots - 1; j >= 0; --j)
+      if (sl[j].z && u_of[j] == u) g = sl[j].x;
+    return g;
+  }
+};
+__device__ __forceinline__ ItemGrains item_grains(const uint4* sl) {
+  ItemGrains ig;
+  ig.nd = sl[0].z ? 1 : 0;
+  ig.u_of[0] = 0;
+#pragma unroll
+  for (int j = 1; j < kPSlots; ++j) {
+    const bool fresh = sl[j].z && sl[j].x != sl[j - 1].x;
+    ig.u_of[j] = sl[j].z ? ig.u_of[j - 1] + (fresh ? 1 : 0) : 0;
+    ig.nd += fresh ? 1 : 0;
+  }
+  return ig;
+}
+
 // ------------------------------------------------------------------ explicit residual
 
 // rho_q = ||v' - U_b^T z||^2 of every pair (Eq. 3-4 in the precision form,
@@ -378,12 +412,14 @@ __global__ void __launch_bounds__(kPThreads, 1) k_project_tc(
 // reconstruction U_b^T z of all 128 pairs against a 128-coordinate chunk is
 // one MMA sequence: A = z split into two BF16 parts (hi, lo: 16 significant
 // bits; the dropped remainder eta moves rho by 2 (U e) . eta + |U^T eta|^2,
-// with U e = (I - G) z + dz small), block-diagonal over the slots (row i of slot s holds its
-// z in K columns s RN .. s RN + RN - 1, zeros elsewhere); B = the slots'
-// basis rows for those 128 coordinates, TMA boxes of 64 coordinates x r
-// rows read MN-major (K = basis row, N = coordinate). TMEM lane i, column t
-// then holds (U^T z)_t of pair i; the epilogue adds (q_b - mu_b - that)^2.
-//   warp 0     TMA producer: per chunk, 2 boxes per slot into a stage ring.
+// with U e = (I - G) z + dz small), block-diagonal over the item's distinct
+// grains (row i holds its z in K columns u RN .. u RN + RN - 1, u its slot's
+// distinct grain, zeros elsewhere; only the K steps of those grains run);
+// B = those grains' basis rows for the 128 coordinates, TMA boxes of 64
+// coordinates x r rows read MN-major (K = basis row, N = coordinate). TMEM
+// lane i, column t then holds (U^T z)_t of pair i; the epilogue adds
+// (q_b - mu_b - that)^2.
+//   warp 0     TMA producer: per chunk, 2 boxes per distinct grain into a stage ring.
 //   warp 1     one thread issues the MMAs into one of two TMEM accumulators.
 //   warps 2-9  epilogue: warp w reads lane quarter w % 4 (32 pairs), columns
 //              64 (w - 2) / 4 .. + 63 of each chunk; it also writes the A
@@ -479,12 +515,10 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
       bool ok = true;
       for (uint32_t w = blockIdx.x; w < total && ok; w += gridDim.x) {
         uint4 sl[kPSlots];
-        uint32_t bytes = 0;
 #pragma unroll
-        for (int j = 0; j < kPSlots; ++j) {
-          sl[j] = slot_of(w, j);
-          bytes += sl[j].z ? 2u * (uint32_t)r * 128u : 0u;
-        }
+        for (int j = 0; j < kPSlots; ++j) sl[j] = slot_of(w, j);
+        const ItemGrains ig = item_grains(sl);
+        const uint32_t bytes = (uint32_t)ig.nd * 2u * (uint32_t)r * 128u;
         for (int c = 0; c < nch; ++c, ++it) {
           const int s = (int)(it % kRStg);
           if (it >= (uint32_t)kRStg && !tc::mbar_wait(&empty[s], ((it / kRStg) - 1) & 1)) {
@@ -494,11 +528,11 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
           uint8_t* st = sB + s * P::kStage;
           tc::mbar_expect_tx(&full[s], bytes);
 #pragma unroll
-          for (int j = 0; j < kPSlots; ++j)
-            if (sl[j].z) {
-              tc::tma_load_2d(&mapU, &full[s], st + j * P::kBytesSlot, c * kRChunk, (int)sl[j].x * r);
-              tc::tma_load_2d(&mapU, &full[s], st + j * P::kBytesSlot + RN * 128, c * kRChunk + 64,
-                              (int)sl[j].x * r);
+          for (int u = 0; u < kPSlots; ++u)
+            if (u < ig.nd) {
+              const int gy = (int)ig.grain(sl, u) * r;
+              tc::tma_load_2d(&mapU, &full[s], st + u * P::kBytesSlot, c * kRChunk, gy);
+              tc::tma_load_2d(&mapU, &full[s], st + u * P::kBytesSlot + RN * 128, c * kRChunk + 64, gy);
             }
         }
       }
@@ -531,6 +565,10 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
           break;
         }
         tc::fence_after_sync();
+        uint4 slw[kPSlots];
+#pragma unroll
+        for (int j = 0; j < kPSlots; ++j) slw[j] = slot_of(w, j);
+        const int nks = item_grains(slw).nd * (RN / 16);  // K steps of the distinct grains' ranges
         for (int c = 0; c < nch; ++c, ++it, ++ci) {
           const int s = (int)(it % kRStg), a = (int)(ci & 1);
           if (ci >= 2 && !tc::mbar_wait(&acce[a], ((ci >> 1) - 1) & 1)) {
@@ -548,7 +586,7 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
           for (int part = 0; part < kRParts; ++part)
 #pragma unroll
             for (int ks = 0; ks < kKS; ++ks)
-              tc::mma<true>(acc, da[part][ks], db0[ks] + soff, kIdesc, (part | ks) != 0);
+              if (ks < nks) tc::mma<true>(acc, da[part][ks], db0[ks] + soff, kIdesc, (part | ks) != 0);
           tc::mma_commit(&empty[s]);
           tc::mma_commit(&accf[a]);
         }
@@ -586,11 +624,34 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
       }
     };
     if (blockIdx.x < total) prefetch_z(blockIdx.x);
+    int prev_u = -1;  // the K range this thread's pieces of its row were last written to
     for (uint32_t w = blockIdx.x; w < total; w += gridDim.x, ++li) {
       if (et < kPSlots) sslot[et] = slot_of(w, et);
-      // A: row i of slot s holds its z at K = s RN .. s RN + RN - 1 (kRParts BF16
-      // parts: hi = bf16(v), lo = bf16(v - hi); v - hi - lo is below 2^-16 |v|)
+      // A: row i holds its z at K = u RN .. u RN + RN - 1, u the distinct grain
+      // of its slot (kRParts BF16 parts: hi = bf16(v), lo = bf16(v - hi);
+      // v - hi - lo is below 2^-16 |v|); a range a row leaves is zeroed
       {
+        int ua = 0;
+        if (zn_have) {
+          uint4 slw[kPSlots];
+#pragma unroll
+          for (int j = 0; j < kPSlots; ++j) slw[j] = slot_of(w, j);
+          const ItemGrains igw = item_grains(slw);
+#pragma unroll
+          for (int j = 0; j < kPSlots; ++j)
+            if (j == sa) ua = igw.u_of[j];
+          if (prev_u >= 0 && prev_u != ua) {
+#pragma unroll
+            for (int c8 = 0; c8 < kH / 8; ++c8) {
+              const int kc = (prev_u * RN + hf * kH) / 8 + c8;
+#pragma unroll
+              for (int part = 0; part < kRParts; ++part)
+                *reinterpret_cast<uint4*>(sA + part * P::kBytesApart + (kc / 8) * (kPTM * 128) +
+                                          sw128_off(ra, (kc % 8) * 16)) = make_uint4(0, 0, 0, 0);
+            }
+          }
+          prev_u = ua;
+        }
         if (zn_have) {
           float zv[kH];
 #pragma unroll
@@ -614,7 +675,7 @@ __global__ void __launch_bounds__(kRThr, 1) k_resid_tc(
 #pragma unroll
               for (int part = 0; part < kRParts; ++part) wp[part][h] = w2[part];
             }
-            const int kc = (sa * RN + hf * kH) / 8 + c8;  // chunk index along K
+            const int kc = (ua * RN + hf * kH) / 8 + c8;  // chunk index along K
 #pragma unroll
             for (int part = 0; part < kRParts; ++part)
               *reinterpret_cast<uint4*>(sA + part * P::kBytesApart + (kc / 8) * (kPTM * 128) +

@@ -66,40 +66,6 @@ __device__ __forceinline__ void split3_pack(const float (&v)[8], uint4 (&out)[kP
   for (int p = 0; p < kP3Parts; ++p) out[p] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
 }
 
-// The distinct grains of an item's slots: the slots with pairs come first and
-// a grain's slots are consecutive, so each new grain follows the last one
-// seen. nd of them, slot j's distinct index in u_of[j] (0 for a slot without
-// pairs), the grain of distinct index u from grain(). The residual pass
-// gives each distinct grain, not each slot, a K range of its block-diagonal A
-// and loads each distinct basis once, so the K steps of an item whose slots
-// share grains are fewer. (The z pass keeps one MMA over all 4 slots' bases:
-// one N = 4 RN product measured faster than an N = RN product per distinct
-// grain.)
-struct ItemGrains {
-  int nd;
-  int u_of[kPSlots];
-  // the grain of distinct index u (u < nd)
-  __device__ __forceinline__ uint32_t grain(const uint4* sl, int u) const {
-    uint32_t g = 0;
-#pragma unroll
-    for (int j = kPSlots - 1; j >= 0; --j)
-      if (sl[j].z && u_of[j] == u) g = sl[j].x;
-    return g;
-  }
-};
-__device__ __forceinline__ ItemGrains item_grains(const uint4* sl) {
-  ItemGrains ig;
-  ig.nd = sl[0].z ? 1 : 0;
-  ig.u_of[0] = 0;
-#pragma unroll
-  for (int j = 1; j < kPSlots; ++j) {
-    const bool fresh = sl[j].z && sl[j].x != sl[j - 1].x;
-    ig.u_of[j] = sl[j].z ? ig.u_of[j - 1] + (fresh ? 1 : 0) : 0;
-    ig.nd += fresh ? 1 : 0;
-  }
-  return ig;
-}
-
 template <int RN>
 struct ProjTc3 {
   static constexpr int kN = kPSlots * RN;                                // MMA N: the 4 slots' bases
