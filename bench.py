@@ -1077,6 +1077,24 @@ def router_leg(a, hntl, dev):
                     "gain": round(rl - rc, 4)})
         print(f"router nprobe {nprobe}: {out[-1]}", file=sys.stderr)
 
+    # training throughput at a batch whose GEMM tiles fill every SM (after the
+    # evaluation, on evaluation queries with random soft targets: a timing of
+    # the same step, not a training run)
+    B4 = 4096
+    T4 = torch.zeros(B4, G, device=dev)
+    T4.scatter_add_(1, torch.randint(0, G, (B4, 10), device=dev, generator=gen), torch.full((B4, 10), 0.1, device=dev))
+    X4 = Qev[:B4].contiguous()
+    for _ in range(3):
+        rt.step(X4, T4, lr=a.router_lr, wd=0.01)
+    torch.cuda.synchronize()
+    e4 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e4[0].record()
+    for _ in range(20):
+        rt.step(X4, T4, lr=a.router_lr, wd=0.01)
+    e4[1].record()
+    torch.cuda.synchronize()
+    ms4 = e4[0].elapsed_time(e4[1]) / 20
+
     def at_target(rk, qk):
         ok = [(o[qk], o["nprobe"]) for o in out if o[rk] >= 0.95]
         return (max(ok)[1], max(ok)[0]) if ok else (None, None)
@@ -1110,7 +1128,11 @@ def router_leg(a, hntl, dev):
            "train": {"samples_per_s": round(samples / (train_ms / 1e3), 1), "ms_per_step": round(train_ms / steps, 4),
                      "achieved_tflops": round(tflops, 1), "peak_tflops": bf16, "frac": round(tflops / bf16, 4),
                      "peak_source": src,
-                     "note": "forward + backward + AdamW, 6 flops per weight per sample (GEMMs only)"}}
+                     "note": "forward + backward + AdamW, 6 flops per weight per sample (GEMMs only)",
+                     "at_batch_4096": {"ms_per_step": round(ms4, 4), "samples_per_s": round(B4 / (ms4 / 1e3), 1),
+                                       "achieved_tflops": round(B4 * flop_per_sample / (ms4 / 1e3) / 1e12, 1),
+                                       "frac": round(B4 * flop_per_sample / (ms4 / 1e3) / 1e12 / bf16, 4),
+                                       "note": "the same step timed at 4096 samples after the evaluation"}}}
     del gi, gp, rt, X, Qev, batches, truth
     torch.cuda.empty_cache()
     return res
