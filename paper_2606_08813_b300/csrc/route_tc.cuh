@@ -325,7 +325,9 @@ __device__ __forceinline__ void warp_sort64(unsigned long long& a, unsigned long
 }
 
 // One CTA per query: margin shortlist over the approximate distances, exact
-// direct-form distances of the shortlist, the nprobe smallest (distance, g).
+// direct-form distances of the shortlist, the nprobe smallest (distance, g);
+// with gcnt, each probe also counts one pair of its grain (the bucket
+// stage's count, taken here while the kernel waits on memory anyway).
 // In the precision form q and the centres are BF16 values (Mh).
 template <bool kBF16>
 __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __restrict__ Q, const float* __restrict__ M,
@@ -335,7 +337,8 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
                                                                  const float* __restrict__ Dt, int G, int d,
                                                                  int nprobe, float eps_dot, float eps_norm,
                                                                  int32_t* __restrict__ probe,
-                                                                 float* __restrict__ probe_d) {
+                                                                 float* __restrict__ probe_d,
+                                                                 uint32_t* __restrict__ gcnt) {
   // dynamic: [d] query (BF16-rounded in the precision form), then the ordered
   // keys of approx + margin and approx - margin of every centre ([G] each), so
   // the row of approximate distances is read from memory once
@@ -510,6 +513,7 @@ __global__ void __launch_bounds__(kRefineThreads) k_route_refine(const float* __
     const unsigned long long k = keys[p];
     probe[(size_t)q * nprobe + p] = (int32_t)(k & 0xFFFFFFFFu);
     probe_d[(size_t)q * nprobe + p] = __uint_as_float((uint32_t)(k >> 32));
+    if (gcnt) atomicAdd(&gcnt[k & 0xFFFFFFFFu], 1u);  // the bucket stage's per-grain pair count
   }
 }
 

@@ -394,7 +394,10 @@ int check_params(const Index& I, uint32_t nq, uint32_t k, uint32_t& C, uint32_t 
   return HNTL_OK;
 }
 
-int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, const Ws& w, cudaStream_t st) {
+// Centroid routing into w.probe / w.probe_d. With gcnt (zeroed), the
+// tensor-core path also counts each grain's pairs there and sets *counted.
+int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, const Ws& w, cudaStream_t st,
+                 uint32_t* gcnt = nullptr, bool* counted = nullptr) {
   const bool bf16 = I.precision == HNTL_PREC_BF16_FP8;
   if (I.tc_route) {
     // tensor-core approximate distances, then the exact refine of a margin shortlist
@@ -429,15 +432,16 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
                                                         w.route_d, I.d_err);
       k_route_refine<true><<<nq, kRefineThreads, rsmem, st>>>(Qd, I.M, I.Mh, w.qn, I.mnorm, w.route_d, (int)I.G,
                                                               (int)I.d, (int)nprobe, eps_dot, eps_norm, w.probe,
-                                                              w.probe_d);
+                                                              w.probe_d, gcnt);
     } else {
       k_route_tc<false><<<grid, kRThreads, kRouteTcSmem, st>>>(mapQ, I.mapM, (int)nq, (int)I.G, (int)I.d, w.qn, I.mnorm,
                                                          w.route_d, I.d_err);
       k_route_refine<false><<<nq, kRefineThreads, rsmem, st>>>(Qd, I.M, I.Mh, w.qn, I.mnorm, w.route_d, (int)I.G,
                                                                (int)I.d, (int)nprobe, eps_dot, eps_norm, w.probe,
-                                                               w.probe_d);
+                                                               w.probe_d, gcnt);
     }
     HNTL_LAUNCH_CHECK("k_route_tc / k_route_refine");
+    if (counted) *counted = gcnt != nullptr;
     return HNTL_OK;
   }
   if (bf16) return fail(HNTL_EINVAL, "the precision form needs tensor-core routing (d a multiple of 8)");
@@ -649,6 +653,7 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
   mark(0);
   HNTL_CUDA_TRY(cudaMemsetAsync(w.gcnt, 0, sizeof(uint32_t) * I.G, st));
   HNTL_CUDA_TRY(cudaMemsetAsync(w.gcur, 0, sizeof(uint32_t) * I.G, st));
+  bool counted = false;  // the routing refine counted each grain's pairs
   if (probe_in) {
     const bool bf16 = I.precision == HNTL_PREC_BF16_FP8;
     if (bf16) {
@@ -663,12 +668,12 @@ int search(const Index& I, const float* Qd, uint32_t nq, uint32_t k, uint32_t C,
       k_probe_dist<false><<<blocks, 256, 0, st>>>(Qd, I.M, I.Mh, (int)nq, (int)nprobe, (int)I.G, (int)I.d, probe_in,
                                                  w.probe, w.probe_d, I.d_err);
     HNTL_CUDA_TRY(cudaGetLastError());
-  } else if ((rc = launch_route(I, Qd, nq, nprobe, w, st))) {
+  } else if ((rc = launch_route(I, Qd, nq, nprobe, w, st, w.gcnt, &counted))) {
     return rc;
   }
   mark(1);
   const int P = (int)(nq * nprobe);
-  k_bucket_count<<<(P + 255) / 256, 256, 0, st>>>(w.probe, P, w.gcnt);
+  if (!counted) k_bucket_count<<<(P + 255) / 256, 256, 0, st>>>(w.probe, P, w.gcnt);
   k_bucket_scan<<<1, 1024, 0, st>>>(w.gcnt, (int)I.G, w.pair_off, w.grp_off, w.grp2_off, w.slots, I.blk_off,
                                     w.scan_off, w.scan_items);
   if (w.slots || w.scan_items)
