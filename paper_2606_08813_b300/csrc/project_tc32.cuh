@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(kR3Thr, 1) k_resid_tc3(
         tc::tmem_ld32(taddr, v);
         tc::tmem_ld32(taddr + kR3Chunk, x);
 #pragma unroll
-        for (int c = 0; c < 32; ++c) v[c] += x[c];
+        for (int col = 0; col < 32; ++col) v[col] += x[col];
         tc::fence_before_sync();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&acce[a]);

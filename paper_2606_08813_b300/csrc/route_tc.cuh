@@ -533,6 +533,40 @@ __global__ void k_row_norms(const float* __restrict__ X, int n, int d, float* __
   if (lane == 0) out[w] = acc;
 }
 
+// The precision form's query preparation in one pass, one warp per row
+// (d % 8 == 0): the BF16 copy of the row (round to nearest even) and the
+// squared norm of the rounded values. Lane l takes the 8 values at
+// 8 l + 256 j, j = 0, 1, ..., and adds their squares in that order: d / 32
+// sequential additions per lane, then five butterfly levels, the rounding the
+// routing margin allows for (as k_row_norms, in another order of the values).
+__global__ void k_query_bf16(const float* __restrict__ X, int n, int d, uint16_t* __restrict__ out,
+                             float* __restrict__ nrm) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const float* x = X + (size_t)w * d;
+  uint16_t* o = out + (size_t)w * d;
+  float acc = 0.f;
+#pragma unroll 4
+  for (int t = lane * 8; t < d; t += 256) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(x + t));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(x + t + 4));
+    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t pk[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);  // .x low half, .y high half
+      pk[h] = *reinterpret_cast<const uint32_t*>(&p2);
+      const float lo = __uint_as_float(pk[h] << 16), hi = __uint_as_float(pk[h] & 0xFFFF0000u);
+      acc = fmaf(lo, lo, acc);
+      acc = fmaf(hi, hi, acc);
+    }
+    *reinterpret_cast<uint4*>(o + t) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o2);
+  if (lane == 0) nrm[w] = acc;
+}
+
 // BF16 copy of FP32 rows (round to nearest even).
 __global__ void k_to_bf16_rows(const float* __restrict__ X, size_t n, uint16_t* __restrict__ out) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -401,10 +401,8 @@ int launch_route(const Index& I, const float* Qd, uint32_t nq, uint32_t nprobe, 
   const bool bf16 = I.precision == HNTL_PREC_BF16_FP8;
   if (I.tc_route) {
     // tensor-core approximate distances, then the exact refine of a margin shortlist
-    if (bf16) {
-      k_row_norms<true><<<(nq * 32 + 255) / 256, 256, 0, st>>>(Qd, (int)nq, (int)I.d, w.qn);
-      const size_t n = (size_t)nq * I.d;
-      k_to_bf16_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Qd, n, w.Qh);
+    if (bf16) {  // d % 8 == 0 on this path (tensor-core routing)
+      k_query_bf16<<<(nq * 32 + 255) / 256, 256, 0, st>>>(Qd, (int)nq, (int)I.d, w.Qh, w.qn);
     } else {
       k_row_norms<false><<<(nq * 32 + 255) / 256, 256, 0, st>>>(Qd, (int)nq, (int)I.d, w.qn);
     }
