@@ -787,11 +787,13 @@ __device__ void select_topc(const Src& src, int C, SelSmem& S, uint32_t* __restr
 
 constexpr int kFinalThreads = 128;  // small CTAs: many queries in flight per SM
 
-// One CTA per query: the pool from the survivors (kFallback = false), or,
-// for the queries whose survivors overflowed their buffer, from every probed
-// row recomputed (kFallback = true). Both are launched; each CTA returns at
-// once for the queries of the other kind. Keeping the rare recompute out of
-// the common kernel keeps its registers low, and its occupancy high.
+// The pool from the survivors (kFallback = false: one CTA per query), or, for
+// the queries whose survivors overflowed their buffer, from every probed row
+// recomputed (kFallback = true: a small grid; each CTA checks 128 queries at
+// a time and selects for the overflowed ones, which are rare). A CTA of the
+// common kernel returns at once for an overflowed query. Keeping the rare
+// recompute out of the common kernel keeps its registers low, and its
+// occupancy high.
 template <int RT, int kC, bool kFallback>
 __global__ void __launch_bounds__(kFinalThreads, kFallback ? 1 : 8) k_final_select(
     int nprobe, int C, uint32_t cap, const uint32_t* __restrict__ cnt, const unsigned long long* __restrict__ surv,
@@ -800,28 +802,49 @@ __global__ void __launch_bounds__(kFinalThreads, kFallback ? 1 : 8) k_final_sele
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r, int rp,
     const float* __restrict__ zq, const float* __restrict__ rhoq, const int64_t* __restrict__ filter,
     uint32_t* __restrict__ cand_id, float* __restrict__ cand_d, const uint32_t* __restrict__ qC,
-    const I16Pairs q16) {
+    const I16Pairs q16, uint32_t nq) {
   __shared__ SelSmem S;
-  const int q = blockIdx.x;
-  const uint32_t n = cnt[q];
-  if ((n > cap) != kFallback) return;
-  uint32_t* oid = cand_id + (size_t)q * C;  // rows are C (the batch's largest pool) apart
-  float* od = cand_d + (size_t)q * C;
-  if (qC) {  // mixed batch: this query's own pool size, the rest of its row padded
-    const int Cq = (int)qC[q];
-    for (int i = Cq + threadIdx.x; i < C; i += blockDim.x) {
-      oid[i] = kInvalidId;
-      od[i] = INFINITY;
+  auto select_one = [&](int q) {
+    const uint32_t n = cnt[q];
+    uint32_t* oid = cand_id + (size_t)q * C;  // rows are C (the batch's largest pool) apart
+    float* od = cand_d + (size_t)q * C;
+    int Cq = C;
+    if (qC) {  // mixed batch: this query's own pool size, the rest of its row padded
+      Cq = (int)qC[q];
+      for (int i = Cq + threadIdx.x; i < C; i += blockDim.x) {
+        oid[i] = kInvalidId;
+        od[i] = INFINITY;
+      }
     }
-    C = Cq;
-  }
+    if constexpr (!kFallback) {
+      SurvivorSrc src{surv + (size_t)q * cap, n};
+      select_topc(src, Cq, S, oid, od);
+    } else {
+      ProbedRowsSrc<RT, kC> src{q,  nprobe, r,   rp,     probe, pair_of, blk_off, grain_rows,
+                                  cz, rho,    ids, attr_b, zq,    rhoq,    filter,  q16};
+      select_topc(src, Cq, S, oid, od);
+    }
+  };
   if constexpr (!kFallback) {
-    SurvivorSrc src{surv + (size_t)q * cap, n};
-    select_topc(src, C, S, oid, od);
+    const int q = blockIdx.x;
+    if (cnt[q] > cap) return;
+    select_one(q);
   } else {
-    ProbedRowsSrc<RT, kC> src{q,  nprobe, r,   rp,     probe, pair_of, blk_off, grain_rows,
-                                cz, rho,    ids, attr_b, zq,    rhoq,    filter,  q16};
-    select_topc(src, C, S, oid, od);
+    __shared__ uint32_t s_over[kFinalThreads];
+    __shared__ uint32_t s_nover;
+    for (uint32_t q0 = blockIdx.x * kFinalThreads; q0 < nq; q0 += gridDim.x * kFinalThreads) {
+      if (threadIdx.x == 0) s_nover = 0;
+      __syncthreads();
+      const uint32_t qq = q0 + threadIdx.x;
+      if (qq < nq && cnt[qq] > cap) s_over[atomicAdd(&s_nover, 1u)] = qq;
+      __syncthreads();
+      const uint32_t nover = s_nover;
+      for (uint32_t i = 0; i < nover; ++i) {
+        select_one((int)s_over[i]);
+        __syncthreads();
+      }
+      __syncthreads();  // every thread has read s_nover before the next pass resets it
+    }
   }
 }
 

@@ -570,10 +570,12 @@ void launch_scan_select(const Index& I, const Ws& w, int nq, int nprobe, int C, 
   mark(5);
   k_final_select<RT, kC, false><<<nq, kFinalThreads, 0, st>>>(
       nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b,
-      (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id, w.cand_d, qC, q16);
-  k_final_select<RT, kC, true><<<nq, kFinalThreads, 0, st>>>(
+      (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id, w.cand_d, qC, q16, (uint32_t)nq);
+  const unsigned fb_grid =
+      (unsigned)std::min<size_t>(((size_t)nq + kFinalThreads - 1) / kFinalThreads, (size_t)I.num_sms);
+  k_final_select<RT, kC, true><<<fb_grid, kFinalThreads, 0, st>>>(
       nprobe, C, w.cap, w.cnt, w.surv, w.probe, w.pair_of, I.blk_off, I.grain_rows, cz, I.rho, I.ids, I.attr_b,
-      (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id, w.cand_d, qC, q16);
+      (int)I.r, (int)I.rp, w.zq, w.rhoq, filter, w.cand_id, w.cand_d, qC, q16, (uint32_t)nq);
 }
 
 template <int RT>
