@@ -392,12 +392,16 @@ void refresh_bf16(Router& R, cudaStream_t st) {
   transpose(R.W3b, R.G, R.h2, R.W3bT, st);
 }
 
-int forward(Router& R, const float* X, uint32_t B, cudaStream_t st) {
+// The MLP's forward pass into R.L. With train, the FP32 pre-activations A1, A2
+// are kept for the GELU backward; inference writes only the BF16 activations.
+int forward(Router& R, const float* X, uint32_t B, cudaStream_t st, bool train = true) {
   int rc;
   to_bf16(X, (size_t)B * R.d, R.Xb, st);
-  if ((rc = gemm(R, R.Xb, R.W1b, (int)B, (int)R.h1, (int)R.d, GemmEpi{R.A1, R.H1b, R.W[1], 1, (int)R.h1}, st)))
+  if ((rc = gemm(R, R.Xb, R.W1b, (int)B, (int)R.h1, (int)R.d,
+                 GemmEpi{train ? R.A1 : nullptr, R.H1b, R.W[1], 1, (int)R.h1}, st)))
     return rc;
-  if ((rc = gemm(R, R.H1b, R.W2b, (int)B, (int)R.h2, (int)R.h1, GemmEpi{R.A2, R.H2b, R.W[3], 1, (int)R.h2}, st)))
+  if ((rc = gemm(R, R.H1b, R.W2b, (int)B, (int)R.h2, (int)R.h1,
+                 GemmEpi{train ? R.A2 : nullptr, R.H2b, R.W[3], 1, (int)R.h2}, st)))
     return rc;
   return gemm(R, R.H2b, R.W3b, (int)B, (int)R.G, (int)R.h2, GemmEpi{R.L, nullptr, R.W[5], 0, (int)R.G}, st);
 }
@@ -671,7 +675,7 @@ extern "C" int hntl_router_logits(hntl_router* h, const float* d_X, uint32_t B, 
     const uint32_t b = std::min(R.max_batch, B - s);
     int rc = hntl::check_dims(R.d, R.h1, R.h2, R.G, (b + 7) / 8 * 8);
     if (rc) return rc;
-    if ((rc = hntl::forward(R, d_X + (size_t)s * R.d, b, st))) return rc;
+    if ((rc = hntl::forward(R, d_X + (size_t)s * R.d, b, st, false))) return rc;
     HNTL_CUDA_TRY(cudaMemcpyAsync(d_logits + (size_t)s * R.G, R.L, sizeof(float) * b * R.G, cudaMemcpyDeviceToDevice, st));
   }
   return HNTL_OK;
@@ -710,7 +714,7 @@ int router_route_probes(Router& R, const Index& I, const float* Q, uint32_t nq, 
   }
   for (uint32_t s = 0; s < nq; s += R.max_batch) {
     const uint32_t b = std::min(R.max_batch, nq - s);
-    if ((rc = forward(R, Q + (size_t)s * R.d, b, st))) return rc;
+    if ((rc = forward(R, Q + (size_t)s * R.d, b, st, false))) return rc;
     if (fused) {
       const int32_t* cp = centroid ? cprobe + (size_t)s * nprobe : nullptr;
       if (R.G <= 256 * 16)
