@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(256) k_pilot(int nprobe, int C, const int32_t*
 constexpr int kMaxNeed = 1024;  // pairs of one grain a block can list after pruning
 
 template <int RT, int kC>
-__global__ void __launch_bounds__(kBlockRows) k_scan_filter(
+__global__ void __launch_bounds__(kBlockRows, 8) k_scan_filter(
     const uint32_t* __restrict__ blk_grain, const uint32_t* __restrict__ blk_off,
     const uint32_t* __restrict__ grain_rows, const Coords cz, const float* __restrict__ rho,
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ attr_b, int r, int rp,
